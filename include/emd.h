@@ -1,0 +1,192 @@
+/*
+ * emd.h -- C ABI of the GB300 (sm_103a) library for the linear-complexity EMD lower
+ * bounds of Atasu & Mittelholzer, "Low-Complexity Data-Parallel Earth Mover's Distance
+ * Approximations" (ICML 2019): LC-RWMD, OMR (Alg. 1), LC-ACT (Alg. 3, Section 4) and
+ * ICT (Alg. 2), for query histograms against a device-resident database of sparse
+ * histograms, in either direction or the maximum of both, plus top-K neighbours.
+ *
+ * Problem statement (Section 2.2 and Section 5): one query histogram q is compared with
+ * n database histograms over a vocabulary of v coordinates with m-dimensional
+ * embeddings; the ground cost is the Euclidean distance between embeddings (Section 5)
+ * or, in cost-matrix mode, any nonnegative v x v matrix (Section 3, remark on p-th
+ * Wasserstein distances).  Every histogram is L1-normalised (Section 2).
+ *
+ * Conventions shared by every entry point
+ *   - Status codes only; nothing throws across the ABI.  On failure the thread-local
+ *     message behind emd_last_error() says why.
+ *   - Ownership: the caller owns every buffer it passes.  Host inputs are copied during
+ *     the call; nothing keeps a caller pointer after the call returns.  Handles are
+ *     released only by the matching *_destroy call.
+ *   - Threads: one handle must not be used by two host threads at the same time.
+ *   - Index types: vocabulary ids and per-histogram sizes are int32; offsets int64.
+ */
+#ifndef EMD_GB300_H
+#define EMD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EMD_OK = 0,
+    EMD_ERR_INVALID_ARG = 1,   /* a size, index, weight or option is out of range */
+    EMD_ERR_OUT_OF_MEMORY = 2, /* a device or pinned-host allocation failed */
+    EMD_ERR_CUDA = 3,          /* a CUDA call or kernel reported an error */
+    EMD_ERR_TIMEOUT = 4,       /* a bounded wait ran out */
+    EMD_ERR_BUSY = 5,          /* admission refused: no free slot or workspace */
+    EMD_ERR_SHUTDOWN = 6,      /* the server is shutting down */
+    EMD_ERR_UNSUPPORTED = 7    /* a valid request this build does not serve */
+} emd_status;
+
+/* Which lower bound.  RWMD is ACT with k = 1 (Alg. 3); OMR is Alg. 1 (k ignored);
+ * ACT is Alg. 3 with top-k width k, i.e. k-1 capacity-limited transfers and the rest of
+ * the mass to the k-th nearest (the evaluation's "ACT-j" is k = j+1); ICT is Alg. 2,
+ * equal to ACT with k = the destination's histogram size. */
+typedef enum { EMD_RWMD = 0, EMD_OMR = 1, EMD_ACT = 2, EMD_ICT = 3 } emd_measure;
+
+/* FWD moves each database histogram's mass into the query (the direction of the
+ * linear-complexity Phase 2, Section 4); REV moves the query's mass into each database
+ * histogram; MAX is the symmetric bound max(FWD, REV) of Sections 3 and 5. */
+typedef enum { EMD_DIR_FWD = 0, EMD_DIR_REV = 1, EMD_DIR_MAX = 2 } emd_direction;
+
+/* Arithmetic of the Phase-1 distance matrix (Section 4).  FP32 is the plain method. */
+typedef enum { EMD_PREC_FP32 = 0, EMD_PREC_BF16 = 1, EMD_PREC_FP8_E4M3 = 2 } emd_precision;
+
+typedef struct emd_db emd_db; /* opaque; owns device memory on one GPU */
+
+typedef struct {
+    int32_t device;          /* CUDA device ordinal (default 0) */
+    emd_precision precision; /* default EMD_PREC_FP32 */
+    int32_t rerank_margin;   /* BF16/FP8 only: extra candidates re-ranked in FP32 (default 8) */
+    int32_t max_query_h;     /* largest query histogram accepted; sizes the workspace (default 2048) */
+    int32_t max_table_k;     /* largest forward top-k table width; ICT needs h_q <= this (default 64) */
+    int32_t max_batch;       /* queries staged per device pass (default 64) */
+} emd_db_options;
+
+typedef struct {
+    int64_t v, v_used, n_docs, nnz; /* vocabulary, used vocabulary (Section 2.2), database size */
+    int32_t m;                      /* embedding width (0 in cost-matrix mode) */
+    int32_t cost_matrix_mode;       /* 1 when a v x v ground-cost matrix replaced embeddings */
+    int64_t device_bytes;           /* device memory held by the handle */
+} emd_db_info;
+
+/* A batch of query histograms in CSR form: query i has bins
+ * idx[row_ptr[i] .. row_ptr[i+1]) with weights w[...]. */
+typedef struct {
+    int64_t n_queries;
+    const int64_t* row_ptr; /* [n_queries + 1], row_ptr[0] == 0 */
+    const int32_t* idx;     /* vocabulary ids, distinct within a query */
+    const float* w;         /* weights, >= 0, summing to 1 per query (|sum - 1| <= 1e-5) */
+} emd_queries;
+
+/* Per-phase device time (CUDA events on the launch stream) and launch counts collected
+ * while profiling is on.  Phases: 0 query staging, 1 distance matrix (Phase 1), 2 top-k
+ * table (Phase 1), 3 forward sparse pass (Phase 2+3), 4 reverse pass + max, 5 top-K
+ * selection, 6 other. */
+#define EMD_N_PHASES 7
+typedef struct {
+    double ms[EMD_N_PHASES];
+    int64_t launches[EMD_N_PHASES];
+    int64_t total_launches; /* every kernel launch since creation, profiling on or off */
+} emd_profile;
+
+/* Fill *opt with the defaults listed above.  Never fails. */
+void emd_db_options_default(emd_db_options* opt);
+
+/* Build the device-resident database (Section 4: X in CSR form; V, the embeddings).
+ *   emb          host float [v * m] row-major embeddings, or NULL in cost-matrix mode
+ *   v, m         vocabulary size (>= 1) and embedding width (1..4096; ignored if emb NULL)
+ *   cost_matrix  host float [v * v] row-major nonnegative ground costs with a zero
+ *                diagonal, or NULL (then emb is required).  Exactly one of emb and
+ *                cost_matrix is non-NULL.
+ *   row_ptr      host int64 [n_docs + 1], row_ptr[0] == 0, non-decreasing, nnz < 2^31
+ *   col, val     host int32 / float [nnz]: vocabulary ids (0 <= col < v, distinct
+ *                within a row) and weights (> 0, each row summing to 1 within 1e-5)
+ *   n_docs       >= 1; every row must have at least one bin
+ *   opt          options or NULL for the defaults
+ *   out          receives the handle
+ * The used vocabulary (the union of database coordinates, Section 2.2) is compacted on
+ * the device; database columns are renumbered into it.
+ * Errors: INVALID_ARG for any violated condition above (nothing is allocated),
+ * OUT_OF_MEMORY, CUDA. */
+emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* cost_matrix,
+                         const int64_t* row_ptr, const int32_t* col, const float* val,
+                         int64_t n_docs, const emd_db_options* opt, emd_db** out);
+
+/* Release every device and host resource of the handle.  NULL is accepted. */
+emd_status emd_db_destroy(emd_db* db);
+
+/* Sizes and memory of the handle.  INVALID_ARG on NULL arguments. */
+emd_status emd_db_info_get(const emd_db* db, emd_db_info* out);
+
+/* Distances from each query to every database histogram (Section 4: the vector t of
+ * size n per query; Section 5: the maximum of both directions for EMD_DIR_MAX).
+ *   q         host query batch (see emd_queries); every h_q in 1..max_query_h
+ *   meas, k   measure and top-k width (k >= 1; ignored by RWMD, OMR, ICT)
+ *   dir       direction
+ *   out_dist  host float [n_queries * n_docs], row-major by query
+ * Synchronous: returns after the results are in out_dist.
+ * Errors: INVALID_ARG (bad query: weight < 0, sum off by > 1e-5, id out of range or
+ * repeated, h_q out of range, k < 1), UNSUPPORTED (ICT forward with h_q > max_table_k),
+ * CUDA. */
+emd_status emd_query_batch(emd_db* db, const emd_queries* q, emd_measure meas, int32_t k,
+                           emd_direction dir, float* out_dist);
+
+/* The K nearest database histograms of each query (Section 5, top-l neighbours), in
+ * ascending (distance, document id) order.
+ *   K         1..min(n_docs, 256)
+ *   out_idx   host int64 [n_queries * K]; out_dist host float [n_queries * K]
+ * Otherwise as emd_query_batch. */
+emd_status emd_topk(emd_db* db, const emd_queries* q, emd_measure meas, int32_t k,
+                    emd_direction dir, int32_t K, int64_t* out_idx, float* out_dist);
+
+/* Device-resident variants: the same computations with inputs and outputs already in
+ * device memory, stream-ordered on `stream` (a cudaStream_t; NULL means the handle's
+ * own stream).  They return once the work is enqueued.
+ *   q_row_ptr_host  HOST int64 [n_queries + 1] (launch sizes are taken from it)
+ *   q_idx_dev, q_w_dev  DEVICE int32 / float [q_row_ptr_host[n_queries]]
+ *   out_*_dev       DEVICE outputs with the host variants' layouts
+ * Query weights are not validated (the caller guarantees them); ids outside 0..v-1 are
+ * caught by a device-side bounds check that skips the access and latches an error read
+ * by emd_db_check_device_errors. */
+emd_status emd_query_batch_device(emd_db* db, int64_t n_queries, const int64_t* q_row_ptr_host,
+                                  const int32_t* q_idx_dev, const float* q_w_dev,
+                                  emd_measure meas, int32_t k, emd_direction dir,
+                                  float* out_dist_dev, void* stream);
+emd_status emd_topk_device(emd_db* db, int64_t n_queries, const int64_t* q_row_ptr_host,
+                           const int32_t* q_idx_dev, const float* q_w_dev, emd_measure meas,
+                           int32_t k, emd_direction dir, int32_t K, int64_t* out_idx_dev,
+                           float* out_dist_dev, void* stream);
+
+/* Synchronise the handle's streams and report (then clear) a latched device-side error:
+ * EMD_OK, or INVALID_ARG when a kernel met an out-of-range id, or CUDA. */
+emd_status emd_db_check_device_errors(emd_db* db);
+
+/* Phase-1 table of one query, for inspection (Section 4: Z, S and W, each v_used x k,
+ * rows in used-vocabulary order = ascending vocabulary id).
+ *   used_ids  host int32 [v_used] (may be NULL): vocabulary id of each table row
+ *   z, w      host float [v_used * k]; s host int32 [v_used * k] (query bin index)
+ * Entries l >= h_q hold z = +inf, s = -1, w = 0.  k in 1..max_table_k. */
+emd_status emd_phase1_table(emd_db* db, const int32_t* q_idx, const float* q_w, int32_t h_q,
+                            int32_t k, int32_t* used_ids, float* z, int32_t* s, float* w);
+
+/* Profiling: when on, every kernel launch is bracketed by CUDA events on its stream and
+ * its time is added to its phase.  emd_db_profile_get synchronises and reads the sums;
+ * emd_db_profile_reset clears them. */
+emd_status emd_db_set_profiling(emd_db* db, int32_t on);
+emd_status emd_db_profile_get(emd_db* db, emd_profile* out);
+emd_status emd_db_profile_reset(emd_db* db);
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* emd_last_error(void);
+
+/* Library version string. */
+const char* emd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EMD_GB300_H */

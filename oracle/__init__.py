@@ -194,3 +194,37 @@ def lc_queries(emb, cost, db, queries, qids, meas: str, k: int, fwd=True, rev=Tr
 
     with concurrent.futures.ThreadPoolExecutor(max_workers=threads) as ex:
         return list(ex.map(one, list(qids)))
+
+
+def _slice(db, d0: int, d1: int):
+    """Documents d0..d1-1 of a CSR set as a view (no copy of col/val)."""
+    a, b = int(db.row_ptr[d0]), int(db.row_ptr[d1])
+
+    class _S:
+        pass
+    s = _S()
+    s.row_ptr = db.row_ptr[d0:d1 + 1] - a
+    s.col = db.col[a:b]
+    s.val = db.val[a:b]
+    return s
+
+
+def lc_query_split(emb, cost, db, q_idx, q_w, meas: str, k: int = 1, fwd=True, rev=True,
+                   threads: int | None = None):
+    """lc_query for one query, with the database cut into `threads` contiguous document
+    slices evaluated concurrently.  Each slice runs the unchanged oracle on its own used
+    vocabulary; every document's value is computed exactly as in one call, so the
+    concatenation equals lc_query on the whole database."""
+    threads = max(1, min(threads or os.cpu_count() or 1, db.n if hasattr(db, "n") else len(db.row_ptr) - 1))
+    n = len(db.row_ptr) - 1
+    bounds = np.linspace(0, n, threads + 1).astype(np.int64)
+    lib()
+
+    def one(i):
+        return lc_query(emb, cost, _slice(db, bounds[i], bounds[i + 1]), q_idx, q_w, meas, k, fwd, rev)
+
+    with concurrent.futures.ThreadPoolExecutor(max_workers=threads) as ex:
+        parts = list(ex.map(one, range(threads)))
+    tf = np.concatenate([p[0] for p in parts]) if fwd else None
+    tr = np.concatenate([p[1] for p in parts]) if rev else None
+    return tf, tr

@@ -1,0 +1,685 @@
+// C ABI (include/emd.h): argument checks, the device-resident database, the workspace,
+// and the per-query sequence of kernels.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "emd_internal.cuh"
+
+using namespace emd;
+
+namespace {
+
+thread_local std::string g_err;
+
+emd_status fail(emd_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+emd_status cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? EMD_ERR_OUT_OF_MEMORY : EMD_ERR_CUDA,
+                "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define EMD_CUDA(call, what)                              \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+}  // namespace
+
+struct emd_db {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    emd_db_options opt{};
+    int64_t v = 0, v_used = 0, n = 0, nnz = 0;
+    int m = 0, ldm = 0;
+    bool cost_mode = false;
+
+    // resident database
+    float* emb = nullptr;        // v x ldm, full vocabulary (queries gather from it)
+    float* emb_used = nullptr;   // v_used x ldm, used vocabulary (Section 2.2)
+    float* norm_used = nullptr;  // v_used, squared norms
+    int32_t* used_ids = nullptr; // v_used, vocabulary id of each used row (ascending)
+    float* cost = nullptr;       // v x v ground costs (cost-matrix mode)
+    int32_t* row_ptr = nullptr;  // n + 1
+    int32_t* col = nullptr;      // nnz, renumbered into the used vocabulary
+    float* val = nullptr;        // nnz
+
+    // workspace
+    int ldd_max = 0, qrows_max = 0;
+    float* Q = nullptr;          // qrows_max x ldm
+    float* qnorm = nullptr;      // qrows_max
+    float* D = nullptr;          // v_used x ldd (ldd <= ldd_max)
+    float2* tab = nullptr;       // v_used x max_table_k
+    int32_t* tab_s = nullptr;    // v_used x max_table_k
+    float* t_fwd = nullptr;      // n
+    float* t_rev = nullptr;      // n
+    float* t_out = nullptr;      // n
+    unsigned long long* topk_scratch = nullptr;
+    int* err = nullptr;
+
+    // staging for the host-buffer entry points
+    int64_t stage_bins = 0;
+    int32_t* stage_idx = nullptr;
+    float* stage_w = nullptr;
+    float* stage_out = nullptr;      // max_batch x n
+    int64_t* stage_oidx = nullptr;   // max_batch x kMaxTopK
+    float* stage_odist = nullptr;    // max_batch x kMaxTopK
+
+    int64_t bytes = 0;
+    std::vector<void*> allocs;
+
+    // profiling
+    bool profiling = false;
+    struct Rec { int phase; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    double ms[EMD_N_PHASES] = {};
+    int64_t launches[EMD_N_PHASES] = {};
+    int64_t total_launches = 0;
+};
+
+namespace {
+
+template <typename T>
+emd_status dalloc(emd_db* db, T** p, int64_t count)
+{
+    size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(T);
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(EMD_ERR_OUT_OF_MEMORY, "cudaMalloc of %zu bytes failed: %s", bytes,
+                    cudaGetErrorString(e));
+    }
+    db->allocs.push_back(q);
+    db->bytes += (int64_t)bytes;
+    *p = (T*)q;
+    return EMD_OK;
+}
+
+void release(emd_db* db)
+{
+    if (!db) return;
+    cudaSetDevice(db->dev);
+    if (db->stream) cudaStreamSynchronize(db->stream);
+    for (void* p : db->allocs) cudaFree(p);
+    for (auto& r : db->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : db->pool) cudaEventDestroy(e);
+    if (db->stream) cudaStreamDestroy(db->stream);
+    delete db;
+}
+
+cudaEvent_t take_event(emd_db* db)
+{
+    if (!db->pool.empty()) {
+        cudaEvent_t e = db->pool.back();
+        db->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets the kernels of one phase with events (when profiling) and counts launches.
+struct Phase {
+    emd_db* db;
+    int ph;
+    int nlaunch;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    Phase(emd_db* d, int p, int nl, cudaStream_t s) : db(d), ph(p), nlaunch(nl), st(s)
+    {
+        if (db->profiling) {
+            a = take_event(db);
+            cudaEventRecord(a, st);
+        }
+    }
+    ~Phase()
+    {
+        db->launches[ph] += nlaunch;
+        db->total_launches += nlaunch;
+        if (db->profiling) {
+            cudaEvent_t b = take_event(db);
+            cudaEventRecord(b, st);
+            db->recs.push_back({ph, a, b});
+        }
+    }
+};
+
+int topk_launch_count(int64_t n)
+{
+    int blocks = (int)std::min<int64_t>(kTopkMaxBlocks, std::max<int64_t>(1, n / 8192));
+    return blocks > 1 ? 2 : 1;
+}
+
+int table_width(int meas, int k, int h)
+{
+    switch (meas) {
+    case M_RWMD: return 1;
+    case M_OMR: return std::min(2, h);
+    case M_ICT: return h;
+    default: return std::min(k, h);
+    }
+}
+
+emd_status check_request(const emd_db* db, int meas, int k, int dir)
+{
+    if (meas < EMD_RWMD || meas > EMD_ICT) return fail(EMD_ERR_INVALID_ARG, "unknown measure %d", meas);
+    if (dir < EMD_DIR_FWD || dir > EMD_DIR_MAX) return fail(EMD_ERR_INVALID_ARG, "unknown direction %d", dir);
+    if (meas == EMD_ACT && k < 1) return fail(EMD_ERR_INVALID_ARG, "k must be >= 1 (got %d)", k);
+    (void)db;
+    return EMD_OK;
+}
+
+emd_status check_sizes(const emd_db* db, int64_t nq, const int64_t* rp, int meas, int k, int dir)
+{
+    if (nq < 0) return fail(EMD_ERR_INVALID_ARG, "n_queries < 0");
+    if (nq == 0) return EMD_OK;
+    if (!rp) return fail(EMD_ERR_INVALID_ARG, "query row_ptr is NULL");
+    if (rp[0] != 0) return fail(EMD_ERR_INVALID_ARG, "query row_ptr[0] != 0");
+    for (int64_t i = 0; i < nq; ++i) {
+        int64_t h = rp[i + 1] - rp[i];
+        if (h < 1 || h > db->opt.max_query_h)
+            return fail(EMD_ERR_INVALID_ARG, "query %lld has %lld bins (allowed 1..%d)", (long long)i,
+                        (long long)h, db->opt.max_query_h);
+        if (dir != EMD_DIR_REV && table_width(meas, k, (int)h) > db->opt.max_table_k)
+            return fail(EMD_ERR_UNSUPPORTED, "forward table width %d exceeds max_table_k %d",
+                        table_width(meas, k, (int)h), db->opt.max_table_k);
+    }
+    return EMD_OK;
+}
+
+emd_status check_query_values(const emd_db* db, const emd_queries* q)
+{
+    if (q->n_queries == 0) return EMD_OK;
+    if (!q->idx || !q->w) return fail(EMD_ERR_INVALID_ARG, "query idx or w is NULL");
+    std::vector<int64_t> stamp((size_t)db->v, -1);
+    for (int64_t i = 0; i < q->n_queries; ++i) {
+        double s = 0.0;
+        for (int64_t e = q->row_ptr[i]; e < q->row_ptr[i + 1]; ++e) {
+            int32_t id = q->idx[e];
+            float w = q->w[e];
+            if (id < 0 || id >= db->v)
+                return fail(EMD_ERR_INVALID_ARG, "query %lld: id %d out of range", (long long)i, id);
+            if (stamp[id] == i)
+                return fail(EMD_ERR_INVALID_ARG, "query %lld: id %d repeated", (long long)i, id);
+            stamp[id] = i;
+            if (!(w >= 0.f) || !isfinite(w))
+                return fail(EMD_ERR_INVALID_ARG, "query %lld: weight %g invalid", (long long)i, (double)w);
+            s += w;
+        }
+        if (fabs(s - 1.0) > 1e-5)
+            return fail(EMD_ERR_INVALID_ARG, "query %lld: weights sum to %.9g, not 1", (long long)i, s);
+    }
+    return EMD_OK;
+}
+
+// One query through the whole path.  out_t (n floats) receives the distances; with
+// K > 0 the top-K goes to out_idx / out_dist and out_t may be the workspace.
+emd_status run_query(emd_db* db, const int32_t* qidx, const float* qw, int h, int meas, int k,
+                     int dir, float* out_t, int K, int64_t* out_idx, float* out_dist,
+                     cudaStream_t st)
+{
+    const int ldd = (int)round_up(h, 32);
+    const int qrows = (int)round_up(ldd, kDistBN);
+    if (db->cost_mode) {
+        Phase p(db, 1, 1, st);
+        EMD_CUDA(launch_dist_gather(db->cost, db->v, db->used_ids, db->v_used, qidx, h, db->D, ldd,
+                                    db->err, st), "distance gather");
+    } else {
+        {
+            Phase p(db, 0, 1, st);
+            EMD_CUDA(launch_gather_rows(db->emb, db->v, db->ldm, db->m, qidx, h, qrows, db->Q,
+                                        db->qnorm, db->err, st), "query gather");
+        }
+        Phase p(db, 1, 1, st);
+        EMD_CUDA(launch_dist_fp32(db->emb_used, db->v_used, db->ldm, db->norm_used, db->used_ids,
+                                  db->Q, h, db->ldm, db->qnorm, qidx, db->m, db->D, ldd, st),
+                 "distance matrix");
+    }
+    float* target = out_t ? out_t : db->t_out;
+    if (dir != EMD_DIR_REV) {
+        const int tk = table_width(meas, k, h);
+        {
+            Phase p(db, 2, 1, st);
+            EMD_CUDA(launch_table(db->D, ldd, db->v_used, h, tk, qw, db->tab, nullptr, st), "top-k table");
+        }
+        Phase p(db, 3, 1, st);
+        EMD_CUDA(launch_fwd(meas, db->row_ptr, db->col, db->val, db->n, db->tab, tk, tk,
+                            dir == EMD_DIR_FWD ? target : db->t_fwd, st), "forward pass");
+    }
+    if (dir != EMD_DIR_FWD) {
+        Phase p(db, 4, 1, st);
+        EMD_CUDA(launch_rev(meas, k, db->row_ptr, db->col, db->val, db->n, db->D, ldd, h, qw,
+                            db->t_fwd, dir == EMD_DIR_REV ? target : db->t_rev,
+                            dir == EMD_DIR_MAX ? target : nullptr, st), "reverse pass");
+    }
+    if (K > 0) {
+        Phase p(db, 5, topk_launch_count(db->n), st);
+        EMD_CUDA(launch_topk(target, db->n, K, db->topk_scratch, out_idx, out_dist, st), "top-K");
+    }
+    return EMD_OK;
+}
+
+emd_status read_device_errors(emd_db* db)
+{
+    int h_err = 0;
+    EMD_CUDA(cudaMemcpyAsync(&h_err, db->err, sizeof(int), cudaMemcpyDeviceToHost, db->stream), "error read");
+    EMD_CUDA(cudaStreamSynchronize(db->stream), "synchronize");
+    if (h_err) {
+        int zero = 0;
+        cudaMemcpy(db->err, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        return fail(EMD_ERR_INVALID_ARG, "a kernel met a vocabulary id outside 0..%lld", (long long)db->v - 1);
+    }
+    return EMD_OK;
+}
+
+// Host-buffer driver shared by emd_query_batch and emd_topk.
+emd_status host_batches(emd_db* db, const emd_queries* q, int meas, int k, int dir, int K,
+                        float* out_dist_all, int64_t* out_idx, float* out_dist)
+{
+    EMD_CUDA(cudaSetDevice(db->dev), "cudaSetDevice");
+    cudaStream_t st = db->stream;
+    int64_t i0 = 0;
+    while (i0 < q->n_queries) {
+        int64_t i1 = i0;
+        while (i1 < q->n_queries && i1 - i0 < db->opt.max_batch &&
+               q->row_ptr[i1 + 1] - q->row_ptr[i0] <= db->stage_bins)
+            ++i1;
+        const int64_t base = q->row_ptr[i0];
+        const int64_t bins = q->row_ptr[i1] - base;
+        EMD_CUDA(cudaMemcpyAsync(db->stage_idx, q->idx + base, bins * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, st), "query copy");
+        EMD_CUDA(cudaMemcpyAsync(db->stage_w, q->w + base, bins * sizeof(float),
+                                 cudaMemcpyHostToDevice, st), "query copy");
+        for (int64_t i = i0; i < i1; ++i) {
+            const int64_t off = q->row_ptr[i] - base;
+            const int h = (int)(q->row_ptr[i + 1] - q->row_ptr[i]);
+            emd_status s = run_query(db, db->stage_idx + off, db->stage_w + off, h, meas, k, dir,
+                                     K > 0 ? nullptr : db->stage_out + (i - i0) * db->n, K,
+                                     db->stage_oidx + (i - i0) * K, db->stage_odist + (i - i0) * K, st);
+            if (s != EMD_OK) return s;
+        }
+        if (K > 0) {
+            EMD_CUDA(cudaMemcpyAsync(out_idx + i0 * K, db->stage_oidx, (i1 - i0) * K * sizeof(int64_t),
+                                     cudaMemcpyDeviceToHost, st), "result copy");
+            EMD_CUDA(cudaMemcpyAsync(out_dist + i0 * K, db->stage_odist, (i1 - i0) * K * sizeof(float),
+                                     cudaMemcpyDeviceToHost, st), "result copy");
+        } else {
+            EMD_CUDA(cudaMemcpyAsync(out_dist_all + i0 * db->n, db->stage_out,
+                                     (i1 - i0) * db->n * sizeof(float), cudaMemcpyDeviceToHost, st),
+                     "result copy");
+        }
+        EMD_CUDA(cudaStreamSynchronize(st), "synchronize");
+        i0 = i1;
+    }
+    return read_device_errors(db);
+}
+
+}  // namespace
+
+extern "C" {
+
+void emd_db_options_default(emd_db_options* opt)
+{
+    if (!opt) return;
+    opt->device = 0;
+    opt->precision = EMD_PREC_FP32;
+    opt->rerank_margin = 8;
+    opt->max_query_h = 2048;
+    opt->max_table_k = 64;
+    opt->max_batch = 64;
+}
+
+emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* cost_matrix,
+                         const int64_t* row_ptr, const int32_t* col, const float* val,
+                         int64_t n_docs, const emd_db_options* opt_in, emd_db** out)
+{
+    g_err.clear();
+    if (!out) return fail(EMD_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    emd_db_options opt;
+    emd_db_options_default(&opt);
+    if (opt_in) opt = *opt_in;
+    if ((emb == nullptr) == (cost_matrix == nullptr))
+        return fail(EMD_ERR_INVALID_ARG, "exactly one of emb and cost_matrix must be given");
+    if (v < 1 || v >= (1ll << 31)) return fail(EMD_ERR_INVALID_ARG, "v out of range");
+    if (emb && (m < 1 || m > 4096)) return fail(EMD_ERR_INVALID_ARG, "m out of range (1..4096)");
+    if (n_docs < 1) return fail(EMD_ERR_INVALID_ARG, "n_docs must be >= 1");
+    if (!row_ptr || !col || !val) return fail(EMD_ERR_INVALID_ARG, "CSR arrays must be non-NULL");
+    if (opt.precision != EMD_PREC_FP32)
+        return fail(EMD_ERR_UNSUPPORTED, "precision %d is not available in this build", (int)opt.precision);
+    if (opt.max_query_h < 1 || opt.max_query_h > (1 << 16) || opt.max_table_k < 1 ||
+        opt.max_table_k > (1 << 16) || opt.max_batch < 1 || opt.max_batch > 4096)
+        return fail(EMD_ERR_INVALID_ARG, "option out of range");
+    if (row_ptr[0] != 0) return fail(EMD_ERR_INVALID_ARG, "row_ptr[0] != 0");
+    const int64_t nnz = row_ptr[n_docs];
+    if (nnz >= (1ll << 31)) return fail(EMD_ERR_UNSUPPORTED, "nnz must be < 2^31");
+    std::vector<int64_t> stamp((size_t)v, -1);
+    std::vector<char> used((size_t)v, 0);
+    for (int64_t d = 0; d < n_docs; ++d) {
+        if (row_ptr[d + 1] <= row_ptr[d])
+            return fail(EMD_ERR_INVALID_ARG, "document %lld is empty or row_ptr decreases", (long long)d);
+        double s = 0.0;
+        for (int64_t e = row_ptr[d]; e < row_ptr[d + 1]; ++e) {
+            int32_t c = col[e];
+            if (c < 0 || c >= v) return fail(EMD_ERR_INVALID_ARG, "document %lld: id %d out of range", (long long)d, c);
+            if (stamp[c] == d) return fail(EMD_ERR_INVALID_ARG, "document %lld: id %d repeated", (long long)d, c);
+            stamp[c] = d;
+            if (!(val[e] > 0.f) || !isfinite(val[e]))
+                return fail(EMD_ERR_INVALID_ARG, "document %lld: weight %g invalid", (long long)d, (double)val[e]);
+            s += val[e];
+            used[c] = 1;
+        }
+        if (fabs(s - 1.0) > 1e-5)
+            return fail(EMD_ERR_INVALID_ARG, "document %lld: weights sum to %.9g, not 1", (long long)d, s);
+    }
+    if (cost_matrix) {
+        for (int64_t a = 0; a < v; ++a)
+            for (int64_t b = 0; b < v; ++b) {
+                float c = cost_matrix[a * v + b];
+                if (!(c >= 0.f) || !isfinite(c) || (a == b && c != 0.f))
+                    return fail(EMD_ERR_INVALID_ARG, "cost matrix entry (%lld,%lld) invalid", (long long)a, (long long)b);
+            }
+    }
+
+    // used vocabulary (Section 2.2) and renumbered columns
+    std::vector<int32_t> slot((size_t)v, -1), used_ids;
+    for (int64_t u = 0; u < v; ++u)
+        if (used[u]) { slot[u] = (int32_t)used_ids.size(); used_ids.push_back((int32_t)u); }
+    std::vector<int32_t> col_used((size_t)nnz), rp32((size_t)n_docs + 1);
+    for (int64_t e = 0; e < nnz; ++e) col_used[e] = slot[col[e]];
+    for (int64_t d = 0; d <= n_docs; ++d) rp32[d] = (int32_t)row_ptr[d];
+
+    emd_db* db = new emd_db();
+    db->opt = opt;
+    db->dev = opt.device;
+    db->v = v;
+    db->v_used = (int64_t)used_ids.size();
+    db->n = n_docs;
+    db->nnz = nnz;
+    db->cost_mode = cost_matrix != nullptr;
+    db->m = db->cost_mode ? 0 : m;
+    db->ldm = db->cost_mode ? 0 : (int)round_up(m, 4);
+
+    emd_status s = EMD_OK;
+#define TRY(x)                          \
+    do {                                \
+        s = (x);                        \
+        if (s != EMD_OK) { release(db); return s; } \
+    } while (0)
+#define TRYC(x, what)                                        \
+    do {                                                     \
+        cudaError_t e_ = (x);                                \
+        if (e_ != cudaSuccess) { release(db); return cuda_fail(e_, what); } \
+    } while (0)
+
+    TRYC(cudaSetDevice(db->dev), "cudaSetDevice");
+    TRYC(cudaStreamCreateWithFlags(&db->stream, cudaStreamNonBlocking), "stream");
+    cudaStream_t st = db->stream;
+
+    const int64_t vu = db->v_used;
+    TRY(dalloc(db, &db->used_ids, vu));
+    TRY(dalloc(db, &db->row_ptr, n_docs + 1));
+    TRY(dalloc(db, &db->col, nnz));
+    TRY(dalloc(db, &db->val, nnz));
+    TRY(dalloc(db, &db->err, 1));
+    TRYC(cudaMemsetAsync(db->err, 0, sizeof(int), st), "memset");
+    TRYC(cudaMemcpyAsync(db->used_ids, used_ids.data(), vu * sizeof(int32_t), cudaMemcpyHostToDevice, st), "copy");
+    TRYC(cudaMemcpyAsync(db->row_ptr, rp32.data(), (n_docs + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st), "copy");
+    TRYC(cudaMemcpyAsync(db->col, col_used.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st), "copy");
+    TRYC(cudaMemcpyAsync(db->val, val, nnz * sizeof(float), cudaMemcpyHostToDevice, st), "copy");
+
+    if (db->cost_mode) {
+        TRY(dalloc(db, &db->cost, v * v));
+        TRYC(cudaMemcpyAsync(db->cost, cost_matrix, v * v * sizeof(float), cudaMemcpyHostToDevice, st), "copy");
+    } else {
+        const int ldm = db->ldm;
+        TRY(dalloc(db, &db->emb, v * ldm));
+        TRY(dalloc(db, &db->emb_used, vu * ldm));
+        TRY(dalloc(db, &db->norm_used, vu));
+        TRYC(cudaMemcpy2DAsync(db->emb, ldm * sizeof(float), emb, m * sizeof(float), m * sizeof(float), v,
+                               cudaMemcpyHostToDevice, st), "copy");
+        if (ldm > m)
+            TRYC(cudaMemset2DAsync(db->emb + m, ldm * sizeof(float), 0, (ldm - m) * sizeof(float), v, st), "memset");
+        TRYC(launch_gather_rows(db->emb, v, ldm, ldm, db->used_ids, vu, vu, db->emb_used, db->norm_used,
+                                db->err, st), "embedding gather");
+        db->total_launches += 1;
+        db->launches[6] += 1;
+        db->qrows_max = (int)round_up(round_up(opt.max_query_h, 32), kDistBN);
+        TRY(dalloc(db, &db->Q, (int64_t)db->qrows_max * ldm));
+        TRY(dalloc(db, &db->qnorm, db->qrows_max));
+    }
+
+    db->ldd_max = (int)round_up(opt.max_query_h, 32);
+    TRY(dalloc(db, &db->D, vu * db->ldd_max));
+    TRY(dalloc(db, &db->tab, vu * opt.max_table_k));
+    TRY(dalloc(db, &db->tab_s, vu * opt.max_table_k));
+    TRY(dalloc(db, &db->t_fwd, n_docs));
+    TRY(dalloc(db, &db->t_rev, n_docs));
+    TRY(dalloc(db, &db->t_out, n_docs));
+    TRY(dalloc(db, &db->topk_scratch, (int64_t)kTopkMaxBlocks * kMaxTopK));
+    db->stage_bins = (int64_t)opt.max_batch * opt.max_query_h;
+    TRY(dalloc(db, &db->stage_idx, db->stage_bins));
+    TRY(dalloc(db, &db->stage_w, db->stage_bins));
+    TRY(dalloc(db, &db->stage_out, (int64_t)opt.max_batch * n_docs));
+    TRY(dalloc(db, &db->stage_oidx, (int64_t)opt.max_batch * kMaxTopK));
+    TRY(dalloc(db, &db->stage_odist, (int64_t)opt.max_batch * kMaxTopK));
+    TRYC(cudaStreamSynchronize(st), "synchronize");
+#undef TRY
+#undef TRYC
+    *out = db;
+    return EMD_OK;
+}
+
+emd_status emd_db_destroy(emd_db* db)
+{
+    release(db);
+    return EMD_OK;
+}
+
+emd_status emd_db_info_get(const emd_db* db, emd_db_info* out)
+{
+    if (!db || !out) return fail(EMD_ERR_INVALID_ARG, "NULL argument");
+    out->v = db->v;
+    out->v_used = db->v_used;
+    out->n_docs = db->n;
+    out->nnz = db->nnz;
+    out->m = db->m;
+    out->cost_matrix_mode = db->cost_mode ? 1 : 0;
+    out->device_bytes = db->bytes;
+    return EMD_OK;
+}
+
+emd_status emd_query_batch(emd_db* db, const emd_queries* q, emd_measure meas, int32_t k,
+                           emd_direction dir, float* out_dist)
+{
+    g_err.clear();
+    if (!db || !q) return fail(EMD_ERR_INVALID_ARG, "NULL argument");
+    emd_status s = check_request(db, meas, k, dir);
+    if (s != EMD_OK) return s;
+    if ((s = check_sizes(db, q->n_queries, q->row_ptr, meas, k, dir)) != EMD_OK) return s;
+    if ((s = check_query_values(db, q)) != EMD_OK) return s;
+    if (q->n_queries == 0) return EMD_OK;
+    if (!out_dist) return fail(EMD_ERR_INVALID_ARG, "out_dist is NULL");
+    return host_batches(db, q, meas, k, dir, 0, out_dist, nullptr, nullptr);
+}
+
+emd_status emd_topk(emd_db* db, const emd_queries* q, emd_measure meas, int32_t k,
+                    emd_direction dir, int32_t K, int64_t* out_idx, float* out_dist)
+{
+    g_err.clear();
+    if (!db || !q) return fail(EMD_ERR_INVALID_ARG, "NULL argument");
+    emd_status s = check_request(db, meas, k, dir);
+    if (s != EMD_OK) return s;
+    if (K < 1 || K > kMaxTopK || K > db->n)
+        return fail(EMD_ERR_INVALID_ARG, "K must be in 1..min(n_docs, %d)", kMaxTopK);
+    if ((s = check_sizes(db, q->n_queries, q->row_ptr, meas, k, dir)) != EMD_OK) return s;
+    if ((s = check_query_values(db, q)) != EMD_OK) return s;
+    if (q->n_queries == 0) return EMD_OK;
+    if (!out_idx || !out_dist) return fail(EMD_ERR_INVALID_ARG, "output is NULL");
+    return host_batches(db, q, meas, k, dir, K, nullptr, out_idx, out_dist);
+}
+
+emd_status emd_query_batch_device(emd_db* db, int64_t n_queries, const int64_t* q_row_ptr_host,
+                                  const int32_t* q_idx_dev, const float* q_w_dev,
+                                  emd_measure meas, int32_t k, emd_direction dir,
+                                  float* out_dist_dev, void* stream)
+{
+    g_err.clear();
+    if (!db) return fail(EMD_ERR_INVALID_ARG, "NULL handle");
+    emd_status s = check_request(db, meas, k, dir);
+    if (s != EMD_OK) return s;
+    if ((s = check_sizes(db, n_queries, q_row_ptr_host, meas, k, dir)) != EMD_OK) return s;
+    if (n_queries == 0) return EMD_OK;
+    if (!q_idx_dev || !q_w_dev || !out_dist_dev) return fail(EMD_ERR_INVALID_ARG, "NULL device pointer");
+    EMD_CUDA(cudaSetDevice(db->dev), "cudaSetDevice");
+    cudaStream_t st = stream ? (cudaStream_t)stream : db->stream;
+    for (int64_t i = 0; i < n_queries; ++i) {
+        const int64_t off = q_row_ptr_host[i];
+        const int h = (int)(q_row_ptr_host[i + 1] - off);
+        s = run_query(db, q_idx_dev + off, q_w_dev + off, h, meas, k, dir, out_dist_dev + i * db->n,
+                      0, nullptr, nullptr, st);
+        if (s != EMD_OK) return s;
+    }
+    return EMD_OK;
+}
+
+emd_status emd_topk_device(emd_db* db, int64_t n_queries, const int64_t* q_row_ptr_host,
+                           const int32_t* q_idx_dev, const float* q_w_dev, emd_measure meas,
+                           int32_t k, emd_direction dir, int32_t K, int64_t* out_idx_dev,
+                           float* out_dist_dev, void* stream)
+{
+    g_err.clear();
+    if (!db) return fail(EMD_ERR_INVALID_ARG, "NULL handle");
+    emd_status s = check_request(db, meas, k, dir);
+    if (s != EMD_OK) return s;
+    if (K < 1 || K > kMaxTopK || K > db->n)
+        return fail(EMD_ERR_INVALID_ARG, "K must be in 1..min(n_docs, %d)", kMaxTopK);
+    if ((s = check_sizes(db, n_queries, q_row_ptr_host, meas, k, dir)) != EMD_OK) return s;
+    if (n_queries == 0) return EMD_OK;
+    if (!q_idx_dev || !q_w_dev || !out_idx_dev || !out_dist_dev)
+        return fail(EMD_ERR_INVALID_ARG, "NULL device pointer");
+    EMD_CUDA(cudaSetDevice(db->dev), "cudaSetDevice");
+    cudaStream_t st = stream ? (cudaStream_t)stream : db->stream;
+    for (int64_t i = 0; i < n_queries; ++i) {
+        const int64_t off = q_row_ptr_host[i];
+        const int h = (int)(q_row_ptr_host[i + 1] - off);
+        s = run_query(db, q_idx_dev + off, q_w_dev + off, h, meas, k, dir, nullptr, K,
+                      out_idx_dev + i * K, out_dist_dev + i * K, st);
+        if (s != EMD_OK) return s;
+    }
+    return EMD_OK;
+}
+
+emd_status emd_db_check_device_errors(emd_db* db)
+{
+    g_err.clear();
+    if (!db) return fail(EMD_ERR_INVALID_ARG, "NULL handle");
+    EMD_CUDA(cudaSetDevice(db->dev), "cudaSetDevice");
+    EMD_CUDA(cudaDeviceSynchronize(), "synchronize");
+    return read_device_errors(db);
+}
+
+emd_status emd_phase1_table(emd_db* db, const int32_t* q_idx, const float* q_w, int32_t h_q,
+                            int32_t k, int32_t* used_ids, float* z, int32_t* s_out, float* w)
+{
+    g_err.clear();
+    if (!db || !q_idx || !q_w || !z || !s_out || !w) return fail(EMD_ERR_INVALID_ARG, "NULL argument");
+    if (h_q < 1 || h_q > db->opt.max_query_h) return fail(EMD_ERR_INVALID_ARG, "h_q out of range");
+    if (k < 1 || k > db->opt.max_table_k) return fail(EMD_ERR_INVALID_ARG, "k out of range");
+    int64_t rp[2] = {0, h_q};
+    emd_queries q{1, rp, q_idx, q_w};
+    emd_status s = check_query_values(db, &q);
+    if (s != EMD_OK) return s;
+    EMD_CUDA(cudaSetDevice(db->dev), "cudaSetDevice");
+    cudaStream_t st = db->stream;
+    EMD_CUDA(cudaMemcpyAsync(db->stage_idx, q_idx, h_q * sizeof(int32_t), cudaMemcpyHostToDevice, st), "copy");
+    EMD_CUDA(cudaMemcpyAsync(db->stage_w, q_w, h_q * sizeof(float), cudaMemcpyHostToDevice, st), "copy");
+    const int ldd = (int)round_up(h_q, 32);
+    if (db->cost_mode) {
+        Phase p(db, 1, 1, st);
+        EMD_CUDA(launch_dist_gather(db->cost, db->v, db->used_ids, db->v_used, db->stage_idx, h_q, db->D,
+                                    ldd, db->err, st), "distance gather");
+    } else {
+        {
+            Phase p(db, 0, 1, st);
+            EMD_CUDA(launch_gather_rows(db->emb, db->v, db->ldm, db->m, db->stage_idx, h_q,
+                                        round_up(ldd, kDistBN), db->Q, db->qnorm, db->err, st), "gather");
+        }
+        Phase p(db, 1, 1, st);
+        EMD_CUDA(launch_dist_fp32(db->emb_used, db->v_used, db->ldm, db->norm_used, db->used_ids, db->Q,
+                                  h_q, db->ldm, db->qnorm, db->stage_idx, db->m, db->D, ldd, st), "distance");
+    }
+    {
+        Phase p(db, 2, 1, st);
+        EMD_CUDA(launch_table(db->D, ldd, db->v_used, h_q, k, db->stage_w, db->tab, db->tab_s, st), "table");
+    }
+    const int64_t cnt = db->v_used * k;
+    std::vector<float2> tz((size_t)cnt);
+    EMD_CUDA(cudaMemcpyAsync(tz.data(), db->tab, cnt * sizeof(float2), cudaMemcpyDeviceToHost, st), "copy");
+    EMD_CUDA(cudaMemcpyAsync(s_out, db->tab_s, cnt * sizeof(int32_t), cudaMemcpyDeviceToHost, st), "copy");
+    if (used_ids)
+        EMD_CUDA(cudaMemcpyAsync(used_ids, db->used_ids, db->v_used * sizeof(int32_t), cudaMemcpyDeviceToHost, st), "copy");
+    EMD_CUDA(cudaStreamSynchronize(st), "synchronize");
+    for (int64_t i = 0; i < cnt; ++i) { z[i] = tz[i].x; w[i] = tz[i].y; }
+    return read_device_errors(db);
+}
+
+emd_status emd_db_set_profiling(emd_db* db, int32_t on)
+{
+    if (!db) return fail(EMD_ERR_INVALID_ARG, "NULL handle");
+    db->profiling = on != 0;
+    return EMD_OK;
+}
+
+emd_status emd_db_profile_get(emd_db* db, emd_profile* out)
+{
+    if (!db || !out) return fail(EMD_ERR_INVALID_ARG, "NULL argument");
+    EMD_CUDA(cudaSetDevice(db->dev), "cudaSetDevice");
+    for (auto& r : db->recs) {
+        EMD_CUDA(cudaEventSynchronize(r.b), "event synchronize");
+        float ms = 0.f;
+        EMD_CUDA(cudaEventElapsedTime(&ms, r.a, r.b), "event time");
+        db->ms[r.phase] += ms;
+        db->pool.push_back(r.a);
+        db->pool.push_back(r.b);
+    }
+    db->recs.clear();
+    for (int p = 0; p < EMD_N_PHASES; ++p) { out->ms[p] = db->ms[p]; out->launches[p] = db->launches[p]; }
+    out->total_launches = db->total_launches;
+    return EMD_OK;
+}
+
+emd_status emd_db_profile_reset(emd_db* db)
+{
+    if (!db) return fail(EMD_ERR_INVALID_ARG, "NULL handle");
+    emd_profile tmp;
+    emd_status s = emd_db_profile_get(db, &tmp);
+    if (s != EMD_OK) return s;
+    for (int p = 0; p < EMD_N_PHASES; ++p) { db->ms[p] = 0.0; db->launches[p] = 0; }
+    return EMD_OK;
+}
+
+const char* emd_last_error(void) { return g_err.c_str(); }
+
+const char* emd_version(void) { return "emd-lc-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

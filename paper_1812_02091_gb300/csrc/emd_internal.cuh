@@ -1,0 +1,80 @@
+// Internal declarations shared by the CUDA translation units of the library.
+// Nothing here is part of the C ABI (include/emd.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/emd.h"
+
+namespace emd {
+
+constexpr int kWarp = 32;
+
+// Measures as kernel template arguments (same numbering as emd_measure).
+enum : int { M_RWMD = 0, M_OMR = 1, M_ACT = 2, M_ICT = 3 };
+
+// Device error latch bits (written by kernels, read by emd_db_check_device_errors).
+enum : int { ERR_BAD_INDEX = 1 };
+
+// Distance-matrix tiling of the FP32 SIMT kernel.
+constexpr int kDistBM = 128;
+constexpr int kDistBN = 64;
+constexpr int kDistBK = 16;
+
+// Row strides: embeddings are padded to a multiple of 4 floats (16-byte rows); the
+// distance matrix D to a multiple of 32 columns (one warp-wide chunk); staged query
+// coordinates to a multiple of the distance tile width.
+__host__ __device__ inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+// Largest top-K of the neighbour selection and largest register top-k width.
+constexpr int kMaxTopK = 64;
+constexpr int kMaxRegK = 16;
+constexpr int kTopkThreads = 128;
+constexpr int kTopkMaxBlocks = 64;
+
+// ---------------------------------------------------------------- launchers
+// Every launcher enqueues on `st` and returns cudaGetLastError().
+
+// Gather rows of `src` (ld floats per row) into `dst` (ld floats per row) and write
+// their squared L2 norms; ids outside [0, v) latch ERR_BAD_INDEX and produce zero rows.
+// Rows nrows..nrows_pad-1 of dst are zero-filled with zero norm.
+cudaError_t launch_gather_rows(const float* src, int64_t v, int ld, int m, const int32_t* ids,
+                               int64_t nrows, int64_t nrows_pad, float* dst, float* norm2,
+                               int* err, cudaStream_t st);
+
+// D[u, j] = Euclidean distance between A row u and B row j by the norm expansion,
+// exactly 0 when a_ids[u] == b_ids[j]; +inf for j in [N, ldd).
+cudaError_t launch_dist_fp32(const float* A, int64_t M, int lda, const float* anorm,
+                             const int32_t* a_ids, const float* B, int N, int ldb,
+                             const float* bnorm, const int32_t* b_ids, int K, float* D,
+                             int ldd, cudaStream_t st);
+
+// Cost-matrix mode: D[u, j] = cost[a_ids[u] * v + b_ids[j]]; +inf for j in [N, ldd).
+cudaError_t launch_dist_gather(const float* cost, int64_t v, const int32_t* a_ids, int64_t M,
+                               const int32_t* b_ids, int N, float* D, int ldd, int* err,
+                               cudaStream_t st);
+
+// Phase-1 table (Section 4): per row u the k smallest D[u, 0..h) (ties by column),
+// written as tab[u * k + l] = (z, w = q_w[s]) and optionally tab_s[u * k + l] = s.
+cudaError_t launch_table(const float* D, int ldd, int64_t M, int h, int k, const float* q_w,
+                         float2* tab, int32_t* tab_s, cudaStream_t st);
+
+// Forward direction (Phase 2 and 3, Eq. 6-9): t_fwd[d] for every document.
+cudaError_t launch_fwd(int meas, const int32_t* row_ptr, const int32_t* col, const float* val,
+                       int64_t n, const float2* tab, int k, int keff, float* t_fwd,
+                       cudaStream_t st);
+
+// Reverse direction: the query's mass moved into each document, cost block gathered
+// from D; t_rev[d], and t_max[d] = max(t_fwd[d], t_rev[d]) when t_max != nullptr.
+cudaError_t launch_rev(int meas, int k, const int32_t* row_ptr, const int32_t* col,
+                       const float* val, int64_t n, const float* D, int ldd, int h,
+                       const float* q_w, const float* t_fwd, float* t_rev, float* t_max,
+                       cudaStream_t st);
+
+// Top-K smallest of t[0..n) by (value, index), into out_idx / out_dist (K <= kMaxTopK).
+// scratch must hold kTopkMaxBlocks * kMaxTopK uint64 keys.
+cudaError_t launch_topk(const float* t, int64_t n, int K, unsigned long long* scratch,
+                        int64_t* out_idx, float* out_dist, cudaStream_t st);
+
+}  // namespace emd

@@ -1,0 +1,337 @@
+// Phase 1 of LC-ACT (Section 4): the distance matrix D between the used vocabulary and
+// the query's coordinates, and the per-row top-k table (Z, S, W).
+//
+// This file holds the plain FP32 path: a register-tiled SIMT distance kernel (FP32 FFMA,
+// norm expansion ||a||^2 + ||b||^2 - 2<a,b>), the cost-matrix gather of the image
+// workloads, and a warp-per-row top-k selection.
+#include <math.h>
+
+#include "emd_internal.cuh"
+
+namespace emd {
+namespace {
+
+__device__ __forceinline__ float warp_sum(float x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// ------------------------------------------------------------------ row gather + norms
+
+__global__ void k_gather_rows(const float* __restrict__ src, int64_t v, int ld, int m,
+                              const int32_t* __restrict__ ids, int64_t nrows, int64_t nrows_pad,
+                              float* __restrict__ dst, float* __restrict__ norm2, int* err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= nrows_pad) return;
+    float* out = dst + r * ld;
+    int64_t id = -1;
+    if (r < nrows) {
+        id = ids[r];
+        if (id < 0 || id >= v) {
+            if (lane == 0) atomicOr(err, ERR_BAD_INDEX);
+            id = -1;
+        }
+    }
+    float s = 0.f;
+    for (int c = lane; c < ld; c += 32) {
+        float x = (id >= 0 && c < m) ? src[id * ld + c] : 0.f;
+        out[c] = x;
+        s = fmaf(x, x, s);
+    }
+    s = warp_sum(s);
+    if (lane == 0) norm2[r] = s;
+}
+
+// ------------------------------------------------------------------ FP32 distance tile
+//
+// Block tile 128 (vocabulary rows) x 64 (query columns), K step 16, 128 threads, each
+// thread an 8 x 8 register tile (rows tr*4+{0..3} and 64+tr*4+{0..3}, columns tc*4+{0..3}
+// and 32+tc*4+{0..3}).  Both operands are staged k-major in shared memory (double
+// buffered, one barrier per K step) so that the inner loop is 4 LDS.128 + 64 FFMA.
+// Operand rows are zero-padded to a multiple of 4 floats, so the K tail reads zeros.
+
+__global__ void __launch_bounds__(128)
+k_dist_fp32(const float* __restrict__ A, int64_t M, int lda, const float* __restrict__ anorm,
+            const int32_t* __restrict__ a_ids, const float* __restrict__ B, int N, int ldb,
+            const float* __restrict__ bnorm, const int32_t* __restrict__ b_ids, int K,
+            float* __restrict__ D, int ldd)
+{
+    constexpr int BM = kDistBM, BN = kDistBN, BK = kDistBK;
+    __shared__ __align__(16) float As[2][BK][BM];
+    __shared__ __align__(16) float Bs[2][BK][BN];
+
+    const int tid = threadIdx.x;
+    const int64_t m0 = (int64_t)blockIdx.x * BM;
+    const int n0 = blockIdx.y * BN;
+    const int tr = tid >> 3, tc = tid & 7;
+
+    // loader mapping: A row tid (16 floats); B row tid>>1, half (tid&1)
+    const int64_t arow = m0 + tid;
+    const bool a_ok = arow < M;
+    const float* Ap = A + (a_ok ? arow : 0) * lda;
+    const int brow = n0 + (tid >> 1);
+    const int bk = (tid & 1) * 8;
+    const float* Bp = B + (int64_t)brow * ldb;
+
+    float4 ra[4], rb[2];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int kk = k0 + q * 4;
+            ra[q] = (a_ok && kk < lda) ? *reinterpret_cast<const float4*>(Ap + kk)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            int kk = k0 + bk + q * 4;
+            rb[q] = (kk < ldb) ? *reinterpret_cast<const float4*>(Bp + kk)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            As[buf][q * 4 + 0][tid] = ra[q].x;
+            As[buf][q * 4 + 1][tid] = ra[q].y;
+            As[buf][q * 4 + 2][tid] = ra[q].z;
+            As[buf][q * 4 + 3][tid] = ra[q].w;
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            Bs[buf][bk + q * 4 + 0][tid >> 1] = rb[q].x;
+            Bs[buf][bk + q * 4 + 1][tid >> 1] = rb[q].y;
+            Bs[buf][bk + q * 4 + 2][tid >> 1] = rb[q].z;
+            Bs[buf][bk + q * 4 + 3][tid >> 1] = rb[q].w;
+        }
+    };
+
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+    const int Kpad = (int)round_up(K, BK);
+    load(0);
+    store(0);
+    __syncthreads();
+    for (int k0 = 0; k0 < Kpad; k0 += BK) {
+        const int buf = (k0 / BK) & 1;
+        const bool more = k0 + BK < Kpad;
+        if (more) load(k0 + BK);
+#pragma unroll
+        for (int k = 0; k < BK; ++k) {
+            float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][tr * 4]);
+            float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][64 + tr * 4]);
+            float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][k][tc * 4]);
+            float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][k][32 + tc * 4]);
+            float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        if (more) store(buf ^ 1);
+        __syncthreads();
+    }
+
+    // epilogue: d = sqrt(max(|a|^2 + |b|^2 - 2<a,b>, 0)); identical ids give exactly 0
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t row = m0 + (i < 4 ? tr * 4 + i : 64 + tr * 4 + (i - 4));
+        if (row >= M) continue;
+        const float an = anorm[row];
+        const int32_t aid = a_ids[row];
+#pragma unroll
+        for (int jh = 0; jh < 2; ++jh) {
+            const int col0 = n0 + jh * 32 + tc * 4;
+            if (col0 >= ldd) continue;
+            float o[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int col = col0 + e;
+                float d = INFINITY;
+                if (col < N) {
+                    float d2 = fmaf(-2.f, acc[i][jh * 4 + e], an + bnorm[col]);
+                    d = (aid == b_ids[col]) ? 0.f : sqrtf(fmaxf(d2, 0.f));
+                }
+                o[e] = d;
+            }
+            *reinterpret_cast<float4*>(D + row * ldd + col0) = make_float4(o[0], o[1], o[2], o[3]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ cost-matrix gather
+
+__global__ void k_dist_gather(const float* __restrict__ cost, int64_t v,
+                              const int32_t* __restrict__ a_ids, int64_t M,
+                              const int32_t* __restrict__ b_ids, int N, float* __restrict__ D,
+                              int ldd, int* err)
+{
+    const int64_t u = blockIdx.x;
+    if (u >= M) return;
+    const int64_t a = a_ids[u];
+    for (int j = threadIdx.x; j < ldd; j += blockDim.x) {
+        float d = INFINITY;
+        if (j < N) {
+            const int64_t b = b_ids[j];
+            if (b < 0 || b >= v || a < 0 || a >= v) {
+                atomicOr(err, ERR_BAD_INDEX);
+                d = 0.f;
+            } else {
+                d = cost[a * v + b];
+            }
+        }
+        D[u * ldd + j] = d;
+    }
+}
+
+// ------------------------------------------------------------------ top-k table
+//
+// One warp per vocabulary row.  Each lane keeps a sorted register list of its KT
+// smallest (d, j) over the columns it visits (j = lane, lane+32, ...; increasing j, and
+// strict '<' keeps the earlier column first on equal d).  The warp then pops the k
+// smallest heads in (d, j) order; every member of the row's top-k is inside its lane's
+// top-KT because k <= KT.
+
+template <int KT>
+__global__ void k_table(const float* __restrict__ D, int ldd, int64_t M, int h, int k,
+                        const float* __restrict__ q_w, float2* __restrict__ tab,
+                        int32_t* __restrict__ tab_s)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= M) return;
+    const float* Dr = D + row * ldd;
+    float z[KT];
+    int s[KT];
+#pragma unroll
+    for (int l = 0; l < KT; ++l) { z[l] = INFINITY; s[l] = INT32_MAX; }
+    for (int j = lane; j < h; j += 32) {
+        float d = Dr[j];
+        if (d < z[KT - 1]) {
+            z[KT - 1] = d;
+            s[KT - 1] = j;
+#pragma unroll
+            for (int l = KT - 1; l > 0; --l) {
+                if (z[l] < z[l - 1]) {
+                    float tz = z[l]; z[l] = z[l - 1]; z[l - 1] = tz;
+                    int ts = s[l]; s[l] = s[l - 1]; s[l - 1] = ts;
+                }
+            }
+        }
+    }
+    for (int l = 0; l < k; ++l) {
+        float bz = z[0];
+        int bs = s[0];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float oz = __shfl_xor_sync(0xffffffffu, bz, o);
+            int os = __shfl_xor_sync(0xffffffffu, bs, o);
+            if (oz < bz || (oz == bz && os < bs)) { bz = oz; bs = os; }
+        }
+        if (bs != INT32_MAX && s[0] == bs) {  // the owning lane pops its head
+#pragma unroll
+            for (int t = 0; t < KT - 1; ++t) { z[t] = z[t + 1]; s[t] = s[t + 1]; }
+            z[KT - 1] = INFINITY;
+            s[KT - 1] = INT32_MAX;
+        }
+        if (lane == 0) {
+            const bool valid = bs != INT32_MAX;
+            tab[row * k + l] = make_float2(valid ? bz : INFINITY, valid ? q_w[bs] : 0.f);
+            if (tab_s) tab_s[row * k + l] = valid ? bs : -1;
+        }
+    }
+}
+
+// k larger than the register lists: successive minima, each strictly after the previous
+// in (d, j) order.  O(k * h / 32) per lane; used for ICT on small queries.
+__global__ void k_table_generic(const float* __restrict__ D, int ldd, int64_t M, int h, int k,
+                                const float* __restrict__ q_w, float2* __restrict__ tab,
+                                int32_t* __restrict__ tab_s)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= M) return;
+    const float* Dr = D + row * ldd;
+    float pz = -INFINITY;
+    int ps = -1;
+    for (int l = 0; l < k; ++l) {
+        float bz = INFINITY;
+        int bs = INT32_MAX;
+        for (int j = lane; j < h; j += 32) {
+            float d = Dr[j];
+            bool after = d > pz || (d == pz && j > ps);
+            if (after && (d < bz || (d == bz && j < bs))) { bz = d; bs = j; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float oz = __shfl_xor_sync(0xffffffffu, bz, o);
+            int os = __shfl_xor_sync(0xffffffffu, bs, o);
+            if (oz < bz || (oz == bz && os < bs)) { bz = oz; bs = os; }
+        }
+        if (lane == 0) {
+            const bool valid = bs != INT32_MAX;
+            tab[row * k + l] = make_float2(valid ? bz : INFINITY, valid ? q_w[bs] : 0.f);
+            if (tab_s) tab_s[row * k + l] = valid ? bs : -1;
+        }
+        pz = bz;
+        ps = bs;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_gather_rows(const float* src, int64_t v, int ld, int m, const int32_t* ids,
+                               int64_t nrows, int64_t nrows_pad, float* dst, float* norm2,
+                               int* err, cudaStream_t st)
+{
+    if (nrows_pad <= 0) return cudaSuccess;
+    const int warps = 8;
+    dim3 grid((unsigned)((nrows_pad + warps - 1) / warps));
+    k_gather_rows<<<grid, warps * 32, 0, st>>>(src, v, ld, m, ids, nrows, nrows_pad, dst, norm2, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dist_fp32(const float* A, int64_t M, int lda, const float* anorm,
+                             const int32_t* a_ids, const float* B, int N, int ldb,
+                             const float* bnorm, const int32_t* b_ids, int K, float* D,
+                             int ldd, cudaStream_t st)
+{
+    if (M <= 0 || ldd <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((M + kDistBM - 1) / kDistBM), (unsigned)((ldd + kDistBN - 1) / kDistBN));
+    k_dist_fp32<<<grid, 128, 0, st>>>(A, M, lda, anorm, a_ids, B, N, ldb, bnorm, b_ids, K, D, ldd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dist_gather(const float* cost, int64_t v, const int32_t* a_ids, int64_t M,
+                               const int32_t* b_ids, int N, float* D, int ldd, int* err,
+                               cudaStream_t st)
+{
+    if (M <= 0) return cudaSuccess;
+    k_dist_gather<<<(unsigned)M, 128, 0, st>>>(cost, v, a_ids, M, b_ids, N, D, ldd, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_table(const float* D, int ldd, int64_t M, int h, int k, const float* q_w,
+                         float2* tab, int32_t* tab_s, cudaStream_t st)
+{
+    if (M <= 0) return cudaSuccess;
+    const int warps = 8;
+    dim3 grid((unsigned)((M + warps - 1) / warps));
+    if (k <= 1) k_table<1><<<grid, warps * 32, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
+    else if (k <= 2) k_table<2><<<grid, warps * 32, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
+    else if (k <= 4) k_table<4><<<grid, warps * 32, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
+    else if (k <= 8) k_table<8><<<grid, warps * 32, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
+    else if (k <= 16) k_table<16><<<grid, warps * 32, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
+    else k_table_generic<<<grid, warps * 32, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
+    return cudaGetLastError();
+}
+
+}  // namespace emd
