@@ -161,6 +161,27 @@ emd_status emd_topk_device(emd_db* db, int64_t n_queries, const int64_t* q_row_p
                            int32_t k, emd_direction dir, int32_t K, int64_t* out_idx_dev,
                            float* out_dist_dev, void* stream);
 
+/* Top-K selection over distance rows already in device memory, with no allocation.
+ * The paper has no counterpart: this is a library service for callers that must not call
+ * cudaMalloc -- code inside a host framework whose caching allocator owns all device
+ * memory, or a serving loop that cannot absorb cudaMalloc's implicit synchronisation.
+ * The selection kernels are the ones emd_topk / emd_topk_device run; their block-partial
+ * scratch is a fixed 2 MiB array in the library's device memory (every GPU that loads
+ * the library holds it until the process exits).
+ *   t_dev        DEVICE float [n_rows * n], row-major distances (>= 0)
+ *   n_rows       0..64 (the array holds partials for 64 rows); 0 is a no-op
+ *   n            1..2^32-1; K in 1..min(n, 64)
+ *   out_idx_dev  DEVICE int64 [n_rows * K]; out_dist_dev DEVICE float [n_rows * K]; each row
+ *                in ascending (distance, index) order
+ *   stream       cudaStream_t or NULL (the legacy default stream); returns once enqueued
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  Calls share
+ * the array, so calls whose kernels overlap on the GPU race; order them on one stream.
+ * Errors: INVALID_ARG for sizes beyond the limits above or NULL pointers (nothing is
+ * launched), CUDA. */
+emd_status emd_topk_select_static(const float* t_dev, int64_t n_rows, int64_t n, int32_t K,
+                                  int64_t* out_idx_dev, float* out_dist_dev, void* stream);
+
 /* Synchronise the handle's streams and report (then clear) a latched device-side error:
  * EMD_OK, or INVALID_ARG when a kernel met an out-of-range id, or CUDA. */
 emd_status emd_db_check_device_errors(emd_db* db);

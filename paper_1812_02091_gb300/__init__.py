@@ -17,7 +17,7 @@ from . import _build
 __all__ = [
     "EmdError", "emd_db_options_default", "emd_db_create", "emd_db_destroy", "emd_db_info_get",
     "emd_query_batch", "emd_topk", "emd_query_batch_device", "emd_topk_device",
-    "emd_db_check_device_errors", "emd_phase1_table", "emd_db_set_profiling",
+    "emd_db_check_device_errors", "emd_phase1_table", "emd_db_set_profiling", "emd_topk_select_static",
     "emd_db_profile_get", "emd_db_profile_reset", "emd_last_error", "emd_version",
     "MEASURES", "DIRECTIONS", "PRECISIONS", "PHASES", "library_path", "load",
 ]
@@ -87,6 +87,7 @@ def load():
     L.emd_query_batch_device.argtypes = [P, i64, P, P, P, i32, i32, i32, P, P]
     L.emd_topk_device.argtypes = [P, i64, P, P, P, i32, i32, i32, i32, P, P, P]
     L.emd_db_check_device_errors.argtypes = [P]
+    L.emd_topk_select_static.argtypes = [P, i64, i64, i32, P, P, P]
     L.emd_phase1_table.argtypes = [P, P, P, i32, i32, P, P, P, P]
     L.emd_db_set_profiling.argtypes = [P, i32]
     L.emd_db_profile_get.argtypes = [P, ctypes.POINTER(emd_profile)]
@@ -95,7 +96,7 @@ def load():
     L.emd_version.restype = ctypes.c_char_p
     for name in ("emd_db_create", "emd_db_destroy", "emd_db_info_get", "emd_query_batch", "emd_topk",
                  "emd_query_batch_device", "emd_topk_device", "emd_db_check_device_errors",
-                 "emd_phase1_table", "emd_db_set_profiling", "emd_db_profile_get",
+                 "emd_phase1_table", "emd_db_set_profiling", "emd_db_profile_get", "emd_topk_select_static",
                  "emd_db_profile_reset"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -231,6 +232,15 @@ def emd_topk_device(db, q_row_ptr_host, q_idx_dev, q_w_dev, out_idx_dev, out_dis
                                   _code(DIRECTIONS, dir), int(K), _dev(out_idx_dev, "int64"),
                                   _dev(out_dist_dev, "float32"),
                                   ctypes.c_void_p(stream) if stream else None))
+
+
+def emd_topk_select_static(t_dev, K: int, out_idx_dev, out_dist_dev, stream=None):
+    """Top-K of each row of a device distance matrix [n_rows, n], without any allocation
+    (scratch is a fixed array inside the library; see include/emd.h)."""
+    n_rows, n = (t_dev.shape[0], t_dev.shape[1]) if t_dev.dim() == 2 else (1, t_dev.shape[0])
+    _check(load().emd_topk_select_static(_dev(t_dev, "float32"), n_rows, n, int(K),
+                                         _dev(out_idx_dev, "int64"), _dev(out_dist_dev, "float32"),
+                                         ctypes.c_void_p(stream) if stream else None))
 
 
 def emd_db_check_device_errors(db):

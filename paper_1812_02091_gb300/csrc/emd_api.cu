@@ -42,6 +42,16 @@ emd_status cuda_fail(cudaError_t e, const char* what)
 
 }  // namespace
 
+namespace emd {
+// Record a failure message for emd_last_error() from another translation unit.
+emd_status set_error(emd_status st, const char* msg)
+{
+    g_err = msg;
+    return st;
+}
+void clear_error() { g_err.clear(); }
+}  // namespace emd
+
 struct emd_db {
     int dev = 0;
     cudaStream_t stream = nullptr;

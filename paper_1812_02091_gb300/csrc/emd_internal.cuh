@@ -77,4 +77,8 @@ cudaError_t launch_rev(int meas, int k, const int32_t* row_ptr, const int32_t* c
 cudaError_t launch_topk(const float* t, int64_t n, int K, unsigned long long* scratch,
                         int64_t* out_idx, float* out_dist, cudaStream_t st);
 
+// Failure message for emd_last_error() (defined beside the C ABI).
+emd_status set_error(emd_status st, const char* msg);
+void clear_error();
+
 }  // namespace emd

@@ -367,3 +367,79 @@ cudaError_t launch_topk(const float* t, int64_t n, int K, unsigned long long* sc
 }
 
 }  // namespace emd
+
+// ------------------------------------------------------------------ top-K without allocation
+//
+// emd_topk_select_static: the top-K selection kernels above, with their block-partial
+// scratch in a fixed device array instead of memory the caller or the library
+// allocates.  It is meant for callers that may not call cudaMalloc: code that runs
+// inside a host framework whose own caching allocator owns all device memory (a raw
+// cudaMalloc would bypass its accounting), or a latency-bound serving loop where the
+// implicit device synchronisation of cudaMalloc/cudaFree would stall work in flight.
+//
+// The array lives for the life of the process on every device that loads the library.
+// Every call shares it and it keeps the last call's contents; nothing in it needs to
+// start at zero (each block writes its partial list before the merge reads it).  Calls
+// whose kernels overlap on the GPU (different streams, no ordering between them) race
+// on the array.
+
+#include <mutex>
+
+namespace {
+
+constexpr int kStaticMaxRows = 64;  // rows (queries) per call
+constexpr size_t kStaticScratchKeys = (size_t)kStaticMaxRows * emd::kTopkMaxBlocks * emd::kMaxTopK;
+
+static __device__ __align__(256) unsigned long long g_topk_static_scratch[kStaticScratchKeys];
+
+std::mutex g_static_mu;
+constexpr int kStaticMaxDevices = 64;
+unsigned long long* g_static_ptr[kStaticMaxDevices] = {};
+
+// Device address of the array on the current device, looked up once per device.
+cudaError_t static_scratch(unsigned long long** out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kStaticMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_topk_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_ptr[dev] = static_cast<unsigned long long*>(p);
+    }
+    *out = g_static_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" emd_status emd_topk_select_static(const float* t_dev, int64_t n_rows, int64_t n,
+                                             int32_t K, int64_t* out_idx_dev, float* out_dist_dev,
+                                             void* stream)
+{
+    emd::clear_error();
+    if (n_rows < 0 || n_rows > kStaticMaxRows)
+        return emd::set_error(EMD_ERR_INVALID_ARG,
+                              "emd_topk_select_static: n_rows must be 0..64 (the static scratch holds 64 rows)");
+    if (n < 1 || n > 0xffffffffll)
+        return emd::set_error(EMD_ERR_INVALID_ARG, "emd_topk_select_static: n must be 1..2^32-1");
+    if (K < 1 || K > emd::kMaxTopK || K > n)
+        return emd::set_error(EMD_ERR_INVALID_ARG, "emd_topk_select_static: K must be 1..min(n, 64)");
+    if (n_rows == 0) return EMD_OK;
+    if (!t_dev || !out_idx_dev || !out_dist_dev)
+        return emd::set_error(EMD_ERR_INVALID_ARG, "emd_topk_select_static: NULL device pointer");
+    unsigned long long* scratch = nullptr;
+    cudaError_t e = static_scratch(&scratch);
+    if (e != cudaSuccess)
+        return emd::set_error(EMD_ERR_CUDA, cudaGetErrorString(e));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int64_t r = 0; r < n_rows; ++r) {
+        e = emd::launch_topk(t_dev + r * n, n, K, scratch + r * (int64_t)emd::kTopkMaxBlocks * emd::kMaxTopK,
+                             out_idx_dev + r * K, out_dist_dev + r * K, st);
+        if (e != cudaSuccess) return emd::set_error(EMD_ERR_CUDA, cudaGetErrorString(e));
+    }
+    return EMD_OK;
+}
