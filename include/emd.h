@@ -52,8 +52,19 @@ typedef enum { EMD_RWMD = 0, EMD_OMR = 1, EMD_ACT = 2, EMD_ICT = 3 } emd_measure
  * histogram; MAX is the symmetric bound max(FWD, REV) of Sections 3 and 5. */
 typedef enum { EMD_DIR_FWD = 0, EMD_DIR_REV = 1, EMD_DIR_MAX = 2 } emd_direction;
 
-/* Arithmetic of the Phase-1 distance matrix (Section 4).  FP32 is the plain method. */
-typedef enum { EMD_PREC_FP32 = 0, EMD_PREC_BF16 = 1, EMD_PREC_FP8_E4M3 = 2 } emd_precision;
+/* Arithmetic of the Phase-1 distance matrix (Section 4).  FP32 is the plain method (FP32
+ * FFMA on the CUDA cores).  FP32_TC computes the same FP32-grade distances on the tensor
+ * cores: each embedding row is scaled by its absmax and split into two FP16 parts
+ * (hi + lo * 2^-11), and the three products hi*hi, hi*lo, lo*hi are accumulated in FP32,
+ * which reproduces the dot product to about 2^-22 relative.  BF16 and FP8_E4M3 (a single
+ * low-precision product followed by an exact FP32 re-rank of each row's candidates) are
+ * not available in this build (EMD_ERR_UNSUPPORTED). */
+typedef enum {
+    EMD_PREC_FP32 = 0,
+    EMD_PREC_BF16 = 1,
+    EMD_PREC_FP8_E4M3 = 2,
+    EMD_PREC_FP32_TC = 3
+} emd_precision;
 
 typedef struct emd_db emd_db; /* opaque; owns device memory on one GPU */
 
@@ -64,6 +75,7 @@ typedef struct {
     int32_t max_query_h;     /* largest query histogram accepted; sizes the workspace (default 2048) */
     int32_t max_table_k;     /* largest forward top-k table width; ICT needs h_q <= this (default 64) */
     int32_t max_batch;       /* queries staged per device pass (default 64) */
+    int32_t prune_topk;      /* 1 (default): exact pruned max-direction top-K for K <= 16 */
 } emd_db_options;
 
 typedef struct {
@@ -91,6 +103,8 @@ typedef struct {
     double ms[EMD_N_PHASES];
     int64_t launches[EMD_N_PHASES];
     int64_t total_launches; /* every kernel launch since creation, profiling on or off */
+    int64_t pruned_queries; /* max-direction top-K queries answered by the pruned path */
+    int64_t prune_fallbacks; /* of those, queries recomputed over all documents */
 } emd_profile;
 
 /* Fill *opt with the defaults listed above.  Never fails. */
@@ -137,6 +151,11 @@ emd_status emd_query_batch(emd_db* db, const emd_queries* q, emd_measure meas, i
 
 /* The K nearest database histograms of each query (Section 5, top-l neighbours), in
  * ascending (distance, document id) order.
+ * For EMD_DIR_MAX with K <= 16 (and prune_topk set) the reverse direction is evaluated
+ * only where it can matter: max(fwd, rev) >= fwd, so the documents are taken in ascending
+ * forward order, the reverse pass runs on the 63 best, and the answer is certified when the
+ * K-th symmetric value is strictly below the 64th forward value; a query that fails the
+ * test is recomputed over all documents.  The result equals the unpruned one.
  *   K         1..min(n_docs, 256)
  *   out_idx   host int64 [n_queries * K]; out_dist host float [n_queries * K]
  * Otherwise as emd_query_batch. */
@@ -144,14 +163,18 @@ emd_status emd_topk(emd_db* db, const emd_queries* q, emd_measure meas, int32_t 
                     emd_direction dir, int32_t K, int64_t* out_idx, float* out_dist);
 
 /* Device-resident variants: the same computations with inputs and outputs already in
- * device memory, stream-ordered on `stream` (a cudaStream_t; NULL means the handle's
- * own stream).  They return once the work is enqueued.
+ * device memory, stream-ordered on `stream` (a cudaStream_t; NULL is the CUDA default
+ * stream, as in the CUDA runtime).  They return once the work is enqueued; the
+ * workspace they use belongs to the handle, so two calls on one handle must be ordered
+ * (same stream, or synchronised).
  *   q_row_ptr_host  HOST int64 [n_queries + 1] (launch sizes are taken from it)
  *   q_idx_dev, q_w_dev  DEVICE int32 / float [q_row_ptr_host[n_queries]]
  *   out_*_dev       DEVICE outputs with the host variants' layouts
  * Query weights are not validated (the caller guarantees them); ids outside 0..v-1 are
  * caught by a device-side bounds check that skips the access and latches an error read
- * by emd_db_check_device_errors. */
+ * by emd_db_check_device_errors.  The pruned top-K path (see emd_topk) reads one
+ * certification flag per batch of max_batch queries, so emd_topk_device synchronises
+ * `stream` once per such batch. */
 emd_status emd_query_batch_device(emd_db* db, int64_t n_queries, const int64_t* q_row_ptr_host,
                                   const int32_t* q_idx_dev, const float* q_w_dev,
                                   emd_measure meas, int32_t k, emd_direction dir,

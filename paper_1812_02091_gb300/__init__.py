@@ -24,7 +24,7 @@ __all__ = [
 
 MEASURES = {"rwmd": 0, "omr": 1, "act": 2, "ict": 3}
 DIRECTIONS = {"fwd": 0, "rev": 1, "max": 2}
-PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2}
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2, "fp32_tc": 3}
 PHASES = ("stage", "distance", "table", "fwd", "rev", "topk", "other")
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "TIMEOUT", 5: "BUSY",
           6: "SHUTDOWN", 7: "UNSUPPORTED"}
@@ -40,7 +40,8 @@ class EmdError(RuntimeError):
 class emd_db_options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("rerank_margin", ctypes.c_int32), ("max_query_h", ctypes.c_int32),
-                ("max_table_k", ctypes.c_int32), ("max_batch", ctypes.c_int32)]
+                ("max_table_k", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("prune_topk", ctypes.c_int32)]
 
 
 class emd_db_info(ctypes.Structure):
@@ -56,7 +57,8 @@ class emd_queries(ctypes.Structure):
 
 class emd_profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 7), ("launches", ctypes.c_int64 * 7),
-                ("total_launches", ctypes.c_int64)]
+                ("total_launches", ctypes.c_int64), ("pruned_queries", ctypes.c_int64),
+                ("prune_fallbacks", ctypes.c_int64)]
 
 
 _lib = None
@@ -123,6 +125,12 @@ def _dev(t, dtype_name: str):
     if str(t.dtype) != f"torch.{dtype_name}":
         raise TypeError(f"expected torch.{dtype_name}, got {t.dtype}")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    """cudaStream_t handle: an int (torch's `cuda_stream`; 0 is the default stream) or None
+    (also the default stream)."""
+    return ctypes.c_void_p(int(stream)) if stream is not None else None
 
 
 def _code(table, x):
@@ -221,7 +229,7 @@ def emd_query_batch_device(db, q_row_ptr_host, q_idx_dev, q_w_dev, out_dev, meas
     _check(load().emd_query_batch_device(db, len(rp) - 1, prp, _dev(q_idx_dev, "int32"),
                                          _dev(q_w_dev, "float32"), _code(MEASURES, meas), int(k),
                                          _code(DIRECTIONS, dir), _dev(out_dev, "float32"),
-                                         ctypes.c_void_p(stream) if stream else None))
+                                         _stream(stream)))
 
 
 def emd_topk_device(db, q_row_ptr_host, q_idx_dev, q_w_dev, out_idx_dev, out_dist_dev, meas="act",
@@ -231,7 +239,7 @@ def emd_topk_device(db, q_row_ptr_host, q_idx_dev, q_w_dev, out_idx_dev, out_dis
                                   _dev(q_w_dev, "float32"), _code(MEASURES, meas), int(k),
                                   _code(DIRECTIONS, dir), int(K), _dev(out_idx_dev, "int64"),
                                   _dev(out_dist_dev, "float32"),
-                                  ctypes.c_void_p(stream) if stream else None))
+                                  _stream(stream)))
 
 
 def emd_topk_select_static(t_dev, K: int, out_idx_dev, out_dist_dev, stream=None):
@@ -240,7 +248,7 @@ def emd_topk_select_static(t_dev, K: int, out_idx_dev, out_dist_dev, stream=None
     n_rows, n = (t_dev.shape[0], t_dev.shape[1]) if t_dev.dim() == 2 else (1, t_dev.shape[0])
     _check(load().emd_topk_select_static(_dev(t_dev, "float32"), n_rows, n, int(K),
                                          _dev(out_idx_dev, "int64"), _dev(out_dist_dev, "float32"),
-                                         ctypes.c_void_p(stream) if stream else None))
+                                         _stream(stream)))
 
 
 def emd_db_check_device_errors(db):
@@ -269,7 +277,8 @@ def emd_db_profile_get(db) -> dict:
     p = emd_profile()
     _check(load().emd_db_profile_get(db, ctypes.byref(p)))
     return {"ms": dict(zip(PHASES, list(p.ms))), "launches": dict(zip(PHASES, list(p.launches))),
-            "total_launches": int(p.total_launches)}
+            "total_launches": int(p.total_launches), "pruned_queries": int(p.pruned_queries),
+            "prune_fallbacks": int(p.prune_fallbacks)}
 
 
 def emd_db_profile_reset(db):

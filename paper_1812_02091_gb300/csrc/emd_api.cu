@@ -79,9 +79,25 @@ struct emd_db {
     int32_t* tab_s = nullptr;    // v_used x max_table_k
     float* t_fwd = nullptr;      // n
     float* t_rev = nullptr;      // n
-    float* t_out = nullptr;      // n
-    unsigned long long* topk_scratch = nullptr;
+    unsigned long long* topk_scratch = nullptr;  // max_batch x kTopkScratchRow
+    int64_t* sel_idx = nullptr;    // kPruneMaxK: forward top-K of the query being pruned
+    float* sel_val = nullptr;      // kPruneMaxK
+    int64_t* cand_idx = nullptr;   // kPruneCap candidate documents
+    float* cand_sym = nullptr;     // 2 x kPruneCap: symmetric values, then reverse values
+    int* cand_count = nullptr;     // 1
+    int* cand_ok = nullptr;        // max_batch certification flags
     int* err = nullptr;
+
+    // tensor-core operands (precision EMD_PREC_FP32_TC)
+    bool tc = false;
+    int kpad = 0;
+    int64_t mpad = 0;
+    __half* a_hi = nullptr;      // mpad x kpad packed panels of the used vocabulary
+    __half* a_lo = nullptr;
+    float* a_scale = nullptr;    // mpad
+    __half* q_hi = nullptr;      // npad_max x kpad packed panels of the query
+    __half* q_lo = nullptr;
+    float* q_scale = nullptr;    // npad_max
 
     // staging for the host-buffer entry points
     int64_t stage_bins = 0;
@@ -102,6 +118,7 @@ struct emd_db {
     double ms[EMD_N_PHASES] = {};
     int64_t launches[EMD_N_PHASES] = {};
     int64_t total_launches = 0;
+    int64_t pruned_queries = 0, prune_fallbacks = 0;
 };
 
 namespace {
@@ -173,11 +190,7 @@ struct Phase {
     }
 };
 
-int topk_launch_count(int64_t n)
-{
-    int blocks = (int)std::min<int64_t>(kTopkMaxBlocks, std::max<int64_t>(1, n / 8192));
-    return blocks > 1 ? 2 : 1;
-}
+int topk_launch_count(int64_t n) { return topk_blocks(n) > 1 ? 2 : 1; }
 
 int table_width(int meas, int k, int h)
 {
@@ -241,30 +254,17 @@ emd_status check_query_values(const emd_db* db, const emd_queries* q)
     return EMD_OK;
 }
 
-// One query through the whole path.  out_t (n floats) receives the distances; with
-// K > 0 the top-K goes to out_idx / out_dist and out_t may be the workspace.
+emd_status run_phase1(emd_db* db, const int32_t* qidx, int h, cudaStream_t st);
+
+// One query through Phase 1, the forward and/or reverse pass; out_t (n floats) receives
+// the distances.
 emd_status run_query(emd_db* db, const int32_t* qidx, const float* qw, int h, int meas, int k,
-                     int dir, float* out_t, int K, int64_t* out_idx, float* out_dist,
-                     cudaStream_t st)
+                     int dir, float* out_t, cudaStream_t st)
 {
+    emd_status s0 = run_phase1(db, qidx, h, st);
+    if (s0 != EMD_OK) return s0;
     const int ldd = (int)round_up(h, 32);
-    const int qrows = (int)round_up(ldd, kDistBN);
-    if (db->cost_mode) {
-        Phase p(db, 1, 1, st);
-        EMD_CUDA(launch_dist_gather(db->cost, db->v, db->used_ids, db->v_used, qidx, h, db->D, ldd,
-                                    db->err, st), "distance gather");
-    } else {
-        {
-            Phase p(db, 0, 1, st);
-            EMD_CUDA(launch_gather_rows(db->emb, db->v, db->ldm, db->m, qidx, h, qrows, db->Q,
-                                        db->qnorm, db->err, st), "query gather");
-        }
-        Phase p(db, 1, 1, st);
-        EMD_CUDA(launch_dist_fp32(db->emb_used, db->v_used, db->ldm, db->norm_used, db->used_ids,
-                                  db->Q, h, db->ldm, db->qnorm, qidx, db->m, db->D, ldd, st),
-                 "distance matrix");
-    }
-    float* target = out_t ? out_t : db->t_out;
+    float* target = out_t;
     if (dir != EMD_DIR_REV) {
         const int tk = table_width(meas, k, h);
         {
@@ -279,11 +279,118 @@ emd_status run_query(emd_db* db, const int32_t* qidx, const float* qw, int h, in
         Phase p(db, 4, 1, st);
         EMD_CUDA(launch_rev(meas, k, db->row_ptr, db->col, db->val, db->n, db->D, ldd, h, qw,
                             db->t_fwd, dir == EMD_DIR_REV ? target : db->t_rev,
-                            dir == EMD_DIR_MAX ? target : nullptr, st), "reverse pass");
+                            dir == EMD_DIR_MAX ? target : nullptr, nullptr, st), "reverse pass");
     }
-    if (K > 0) {
+    return EMD_OK;
+}
+
+// Phase 1 (distances, or the cost-matrix gather) for one query into db->D.
+emd_status run_phase1(emd_db* db, const int32_t* qidx, int h, cudaStream_t st)
+{
+    const int ldd = (int)round_up(h, 32);
+    const int qrows = (int)round_up(ldd, kDistBN);
+    if (db->cost_mode) {
+        Phase p(db, 1, 1, st);
+        EMD_CUDA(launch_dist_gather(db->cost, db->v, db->used_ids, db->v_used, qidx, h, db->D, ldd,
+                                    db->err, st), "distance gather");
+        return EMD_OK;
+    }
+    {
+        Phase p(db, 0, db->tc ? 2 : 1, st);
+        EMD_CUDA(launch_gather_rows(db->emb, db->v, db->ldm, db->m, qidx, h, qrows, db->Q, db->qnorm,
+                                    db->err, st), "query gather");
+        if (db->tc)
+            EMD_CUDA(launch_pack_f16(db->Q, db->ldm, db->m, h, round_up(h, 128), db->kpad, db->q_hi, db->q_lo,
+                                     db->q_scale, st), "query pack");
+    }
+    Phase p(db, 1, 1, st);
+    if (db->tc)
+        EMD_CUDA(launch_tc_dist(true, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used, db->used_ids,
+                                db->v_used, db->q_hi, db->q_lo, round_up(h, 128), db->q_scale, db->qnorm, qidx,
+                                h, db->kpad, db->D, ldd, db->err, st), "distance matrix (tensor cores)");
+    else
+        EMD_CUDA(launch_dist_fp32(db->emb_used, db->v_used, db->ldm, db->norm_used, db->used_ids, db->Q, h,
+                                  db->ldm, db->qnorm, qidx, db->m, db->D, ldd, st), "distance matrix");
+    return EMD_OK;
+}
+
+bool prunable(const emd_db* db, int meas, int k, int dir, int K)
+{
+    return db->opt.prune_topk != 0 && dir == EMD_DIR_MAX && K <= kPruneMaxK && meas != EMD_ICT &&
+           (meas != EMD_ACT || k <= kMaxRegK);
+}
+
+// Pruned symmetric top-K of one query (see emd_topk in include/emd.h): forward pass over
+// all documents, forward top-K, candidates within the margin, reverse pass on them, final
+// selection with the certification flag in cand_ok[slot].
+emd_status run_topk_pruned(emd_db* db, const int32_t* qidx, const float* qw, int h, int meas, int k,
+                           int K, int64_t slot, int64_t* out_idx, float* out_dist, cudaStream_t st)
+{
+    emd_status s = run_phase1(db, qidx, h, st);
+    if (s != EMD_OK) return s;
+    const int ldd = (int)round_up(h, 32);
+    const int tk = table_width(meas, k, h);
+    {
+        Phase p(db, 2, 1, st);
+        EMD_CUDA(launch_table(db->D, ldd, db->v_used, h, tk, qw, db->tab, nullptr, st), "top-k table");
+    }
+    {
+        Phase p(db, 3, 1, st);
+        EMD_CUDA(launch_fwd(meas, db->row_ptr, db->col, db->val, db->n, db->tab, tk, tk, db->t_fwd, st),
+                 "forward pass");
+    }
+    {
         Phase p(db, 5, topk_launch_count(db->n), st);
-        EMD_CUDA(launch_topk(target, db->n, K, db->topk_scratch, out_idx, out_dist, st), "top-K");
+        EMD_CUDA(launch_topk(db->t_fwd, db->n, K, db->topk_scratch, db->sel_idx, db->sel_val, st),
+                 "forward top-K");
+    }
+    Phase p(db, 4, 3, st);
+    EMD_CUDA(launch_prune(meas, k, db->row_ptr, db->col, db->val, db->n, db->D, ldd, h, qw, db->t_fwd,
+                          db->sel_idx, db->sel_val, K, db->cand_idx, db->cand_count, db->cand_sym, out_idx,
+                          out_dist, db->cand_ok + slot, st), "pruned reverse pass");
+    return EMD_OK;
+}
+
+// Queries i0..i1-1 of a batch through the pruned top-K path; queries whose answer is not
+// certified are recomputed over all documents (one synchronisation per batch).
+emd_status topk_batch_pruned(emd_db* db, const int64_t* rp, const int32_t* qidx, const float* qw,
+                             int64_t i0, int64_t i1, int meas, int k, int K, int64_t* out_idx,
+                             float* out_dist, cudaStream_t st);
+
+// Top-K of `rows` distance rows (row stride n) in one selection launch.
+emd_status select_topk(emd_db* db, const float* t, int64_t rows, int K, int64_t* out_idx,
+                       float* out_dist, cudaStream_t st)
+{
+    Phase p(db, 5, topk_launch_count(db->n), st);
+    EMD_CUDA(launch_topk_rows(t, rows, db->n, db->n, K, db->topk_scratch, out_idx, out_dist, st), "top-K");
+    return EMD_OK;
+}
+
+emd_status topk_batch_pruned(emd_db* db, const int64_t* rp, const int32_t* qidx, const float* qw,
+                             int64_t i0, int64_t i1, int meas, int k, int K, int64_t* out_idx,
+                             float* out_dist, cudaStream_t st)
+{
+    for (int64_t i = i0; i < i1; ++i) {
+        const int64_t off = rp[i] - rp[i0];
+        const int h = (int)(rp[i + 1] - rp[i]);
+        emd_status s = run_topk_pruned(db, qidx + off, qw + off, h, meas, k, K, i - i0,
+                                       out_idx + (i - i0) * K, out_dist + (i - i0) * K, st);
+        if (s != EMD_OK) return s;
+    }
+    std::vector<int> ok((size_t)(i1 - i0), 0);
+    EMD_CUDA(cudaMemcpyAsync(ok.data(), db->cand_ok, (i1 - i0) * sizeof(int), cudaMemcpyDeviceToHost, st),
+             "flag read");
+    EMD_CUDA(cudaStreamSynchronize(st), "synchronize");
+    db->pruned_queries += i1 - i0;
+    for (int64_t i = i0; i < i1; ++i) {
+        if (ok[i - i0]) continue;
+        ++db->prune_fallbacks;
+        const int64_t off = rp[i] - rp[i0];
+        const int h = (int)(rp[i + 1] - rp[i]);
+        emd_status s = run_query(db, qidx + off, qw + off, h, meas, k, EMD_DIR_MAX, db->stage_out, st);
+        if (s != EMD_OK) return s;
+        s = select_topk(db, db->stage_out, 1, K, out_idx + (i - i0) * K, out_dist + (i - i0) * K, st);
+        if (s != EMD_OK) return s;
     }
     return EMD_OK;
 }
@@ -296,6 +403,8 @@ emd_status read_device_errors(emd_db* db)
     if (h_err) {
         int zero = 0;
         cudaMemcpy(db->err, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        if (h_err & ERR_TIMEOUT)
+            return fail(EMD_ERR_TIMEOUT, "a tensor-core pipeline wait exceeded its time limit");
         return fail(EMD_ERR_INVALID_ARG, "a kernel met a vocabulary id outside 0..%lld", (long long)db->v - 1);
     }
     return EMD_OK;
@@ -319,13 +428,22 @@ emd_status host_batches(emd_db* db, const emd_queries* q, int meas, int k, int d
                                  cudaMemcpyHostToDevice, st), "query copy");
         EMD_CUDA(cudaMemcpyAsync(db->stage_w, q->w + base, bins * sizeof(float),
                                  cudaMemcpyHostToDevice, st), "query copy");
-        for (int64_t i = i0; i < i1; ++i) {
-            const int64_t off = q->row_ptr[i] - base;
-            const int h = (int)(q->row_ptr[i + 1] - q->row_ptr[i]);
-            emd_status s = run_query(db, db->stage_idx + off, db->stage_w + off, h, meas, k, dir,
-                                     K > 0 ? nullptr : db->stage_out + (i - i0) * db->n, K,
-                                     db->stage_oidx + (i - i0) * K, db->stage_odist + (i - i0) * K, st);
+        if (K > 0 && prunable(db, meas, k, dir, K)) {
+            emd_status s = topk_batch_pruned(db, q->row_ptr, db->stage_idx, db->stage_w, i0, i1, meas, k, K,
+                                             db->stage_oidx, db->stage_odist, st);
             if (s != EMD_OK) return s;
+        } else {
+            for (int64_t i = i0; i < i1; ++i) {
+                const int64_t off = q->row_ptr[i] - base;
+                const int h = (int)(q->row_ptr[i + 1] - q->row_ptr[i]);
+                emd_status s = run_query(db, db->stage_idx + off, db->stage_w + off, h, meas, k, dir,
+                                         db->stage_out + (i - i0) * db->n, st);
+                if (s != EMD_OK) return s;
+            }
+            if (K > 0) {
+                emd_status s = select_topk(db, db->stage_out, i1 - i0, K, db->stage_oidx, db->stage_odist, st);
+                if (s != EMD_OK) return s;
+            }
         }
         if (K > 0) {
             EMD_CUDA(cudaMemcpyAsync(out_idx + i0 * K, db->stage_oidx, (i1 - i0) * K * sizeof(int64_t),
@@ -356,6 +474,7 @@ void emd_db_options_default(emd_db_options* opt)
     opt->max_query_h = 2048;
     opt->max_table_k = 64;
     opt->max_batch = 64;
+    opt->prune_topk = 1;
 }
 
 emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* cost_matrix,
@@ -374,7 +493,7 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
     if (emb && (m < 1 || m > 4096)) return fail(EMD_ERR_INVALID_ARG, "m out of range (1..4096)");
     if (n_docs < 1) return fail(EMD_ERR_INVALID_ARG, "n_docs must be >= 1");
     if (!row_ptr || !col || !val) return fail(EMD_ERR_INVALID_ARG, "CSR arrays must be non-NULL");
-    if (opt.precision != EMD_PREC_FP32)
+    if (opt.precision != EMD_PREC_FP32 && opt.precision != EMD_PREC_FP32_TC)
         return fail(EMD_ERR_UNSUPPORTED, "precision %d is not available in this build", (int)opt.precision);
     if (opt.max_query_h < 1 || opt.max_query_h > (1 << 16) || opt.max_table_k < 1 ||
         opt.max_table_k > (1 << 16) || opt.max_batch < 1 || opt.max_batch > 4096)
@@ -476,6 +595,22 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
         db->qrows_max = (int)round_up(round_up(opt.max_query_h, 32), kDistBN);
         TRY(dalloc(db, &db->Q, (int64_t)db->qrows_max * ldm));
         TRY(dalloc(db, &db->qnorm, db->qrows_max));
+        if (opt.precision == EMD_PREC_FP32_TC) {
+            db->tc = true;
+            db->kpad = (int)round_up(m, 64);
+            db->mpad = round_up(vu, 128);
+            const int64_t npad = round_up(opt.max_query_h, 128);
+            TRY(dalloc(db, &db->a_hi, db->mpad * db->kpad));
+            TRY(dalloc(db, &db->a_lo, db->mpad * db->kpad));
+            TRY(dalloc(db, &db->a_scale, db->mpad));
+            TRY(dalloc(db, &db->q_hi, npad * db->kpad));
+            TRY(dalloc(db, &db->q_lo, npad * db->kpad));
+            TRY(dalloc(db, &db->q_scale, npad));
+            TRYC(launch_pack_f16(db->emb_used, ldm, m, vu, db->mpad, db->kpad, db->a_hi, db->a_lo, db->a_scale, st),
+                 "embedding pack");
+            db->total_launches += 1;
+            db->launches[6] += 1;
+        }
     }
 
     db->ldd_max = (int)round_up(opt.max_query_h, 32);
@@ -484,8 +619,13 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
     TRY(dalloc(db, &db->tab_s, vu * opt.max_table_k));
     TRY(dalloc(db, &db->t_fwd, n_docs));
     TRY(dalloc(db, &db->t_rev, n_docs));
-    TRY(dalloc(db, &db->t_out, n_docs));
-    TRY(dalloc(db, &db->topk_scratch, (int64_t)kTopkMaxBlocks * kMaxTopK));
+    TRY(dalloc(db, &db->topk_scratch, (int64_t)opt.max_batch * kTopkScratchRow));
+    TRY(dalloc(db, &db->sel_idx, kPruneMaxK));
+    TRY(dalloc(db, &db->sel_val, kPruneMaxK));
+    TRY(dalloc(db, &db->cand_idx, kPruneCap));
+    TRY(dalloc(db, &db->cand_sym, 2 * kPruneCap));
+    TRY(dalloc(db, &db->cand_count, 1));
+    TRY(dalloc(db, &db->cand_ok, opt.max_batch));
     db->stage_bins = (int64_t)opt.max_batch * opt.max_query_h;
     TRY(dalloc(db, &db->stage_idx, db->stage_bins));
     TRY(dalloc(db, &db->stage_w, db->stage_bins));
@@ -561,12 +701,11 @@ emd_status emd_query_batch_device(emd_db* db, int64_t n_queries, const int64_t* 
     if (n_queries == 0) return EMD_OK;
     if (!q_idx_dev || !q_w_dev || !out_dist_dev) return fail(EMD_ERR_INVALID_ARG, "NULL device pointer");
     EMD_CUDA(cudaSetDevice(db->dev), "cudaSetDevice");
-    cudaStream_t st = stream ? (cudaStream_t)stream : db->stream;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);  // NULL: the default stream
     for (int64_t i = 0; i < n_queries; ++i) {
         const int64_t off = q_row_ptr_host[i];
         const int h = (int)(q_row_ptr_host[i + 1] - off);
-        s = run_query(db, q_idx_dev + off, q_w_dev + off, h, meas, k, dir, out_dist_dev + i * db->n,
-                      0, nullptr, nullptr, st);
+        s = run_query(db, q_idx_dev + off, q_w_dev + off, h, meas, k, dir, out_dist_dev + i * db->n, st);
         if (s != EMD_OK) return s;
     }
     return EMD_OK;
@@ -588,12 +727,23 @@ emd_status emd_topk_device(emd_db* db, int64_t n_queries, const int64_t* q_row_p
     if (!q_idx_dev || !q_w_dev || !out_idx_dev || !out_dist_dev)
         return fail(EMD_ERR_INVALID_ARG, "NULL device pointer");
     EMD_CUDA(cudaSetDevice(db->dev), "cudaSetDevice");
-    cudaStream_t st = stream ? (cudaStream_t)stream : db->stream;
-    for (int64_t i = 0; i < n_queries; ++i) {
-        const int64_t off = q_row_ptr_host[i];
-        const int h = (int)(q_row_ptr_host[i + 1] - off);
-        s = run_query(db, q_idx_dev + off, q_w_dev + off, h, meas, k, dir, nullptr, K,
-                      out_idx_dev + i * K, out_dist_dev + i * K, st);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);  // NULL: the default stream
+    for (int64_t i0 = 0; i0 < n_queries; i0 += db->opt.max_batch) {
+        const int64_t i1 = std::min<int64_t>(n_queries, i0 + db->opt.max_batch);
+        if (prunable(db, meas, k, dir, K)) {
+            s = topk_batch_pruned(db, q_row_ptr_host, q_idx_dev + q_row_ptr_host[i0], q_w_dev + q_row_ptr_host[i0],
+                                  i0, i1, meas, k, K, out_idx_dev + i0 * K, out_dist_dev + i0 * K, st);
+            if (s != EMD_OK) return s;
+            continue;
+        }
+        for (int64_t i = i0; i < i1; ++i) {
+            const int64_t off = q_row_ptr_host[i];
+            const int h = (int)(q_row_ptr_host[i + 1] - off);
+            s = run_query(db, q_idx_dev + off, q_w_dev + off, h, meas, k, dir,
+                          db->stage_out + (i - i0) * db->n, st);
+            if (s != EMD_OK) return s;
+        }
+        s = select_topk(db, db->stage_out, i1 - i0, K, out_idx_dev + i0 * K, out_dist_dev + i0 * K, st);
         if (s != EMD_OK) return s;
     }
     return EMD_OK;
@@ -675,6 +825,8 @@ emd_status emd_db_profile_get(emd_db* db, emd_profile* out)
     db->recs.clear();
     for (int p = 0; p < EMD_N_PHASES; ++p) { out->ms[p] = db->ms[p]; out->launches[p] = db->launches[p]; }
     out->total_launches = db->total_launches;
+    out->pruned_queries = db->pruned_queries;
+    out->prune_fallbacks = db->prune_fallbacks;
     return EMD_OK;
 }
 
@@ -685,6 +837,7 @@ emd_status emd_db_profile_reset(emd_db* db)
     emd_status s = emd_db_profile_get(db, &tmp);
     if (s != EMD_OK) return s;
     for (int p = 0; p < EMD_N_PHASES; ++p) { db->ms[p] = 0.0; db->launches[p] = 0; }
+    db->pruned_queries = db->prune_fallbacks = 0;
     return EMD_OK;
 }
 

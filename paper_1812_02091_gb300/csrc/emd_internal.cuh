@@ -2,6 +2,7 @@
 // Nothing here is part of the C ABI (include/emd.h is).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -15,7 +16,7 @@ constexpr int kWarp = 32;
 enum : int { M_RWMD = 0, M_OMR = 1, M_ACT = 2, M_ICT = 3 };
 
 // Device error latch bits (written by kernels, read by emd_db_check_device_errors).
-enum : int { ERR_BAD_INDEX = 1 };
+enum : int { ERR_BAD_INDEX = 1, ERR_TIMEOUT = 2 };
 
 // Distance-matrix tiling of the FP32 SIMT kernel.
 constexpr int kDistBM = 128;
@@ -32,6 +33,14 @@ constexpr int kMaxTopK = 64;
 constexpr int kMaxRegK = 16;
 constexpr int kTopkThreads = 128;
 constexpr int kTopkMaxBlocks = 64;
+constexpr int64_t kTopkScratchRow = (int64_t)kTopkMaxBlocks * kMaxTopK;  // keys per selection row
+
+// Blocks per row of the top-K selection (one block per 8192 values, at most 64).
+__host__ __device__ inline int topk_blocks(int64_t n)
+{
+    int64_t b = n / 8192;
+    return (int)(b < 1 ? 1 : (b > kTopkMaxBlocks ? kTopkMaxBlocks : b));
+}
 
 // ---------------------------------------------------------------- launchers
 // Every launcher enqueues on `st` and returns cudaGetLastError().
@@ -66,16 +75,53 @@ cudaError_t launch_fwd(int meas, const int32_t* row_ptr, const int32_t* col, con
                        cudaStream_t st);
 
 // Reverse direction: the query's mass moved into each document, cost block gathered
-// from D; t_rev[d], and t_max[d] = max(t_fwd[d], t_rev[d]) when t_max != nullptr.
+// from D; t_rev[d], and t_max[d] = max(t_fwd[d], t_rev[d]) when t_max != nullptr.  With
+// doc_ids, output slot i holds document doc_ids[i] (n slots) and t_fwd is indexed by
+// document.
 cudaError_t launch_rev(int meas, int k, const int32_t* row_ptr, const int32_t* col,
                        const float* val, int64_t n, const float* D, int ldd, int h,
                        const float* q_w, const float* t_fwd, float* t_rev, float* t_max,
-                       cudaStream_t st);
+                       const int64_t* doc_ids, cudaStream_t st);
+
+// Exact pruned symmetric top-K (K <= kPruneMaxK).  sel_val holds the K smallest forward
+// values (ascending); the candidates are the documents with fwd <= fwd_K (1 + 2^-7), at
+// most kPruneCap of them, and the reverse pass runs only there.  Writes the K smallest
+// (max(fwd, rev), id) among the candidates and ok = 1 when the K-th is <= that threshold
+// (then no other document can enter) and the candidates did not overflow.  cand holds
+// kPruneCap ids, sym 2 * kPruneCap values, count one int (all workspace).  ICT (k beyond
+// the register lists) is not served here.
+constexpr int kPruneMaxK = 16;
+constexpr int kPruneCap = 256;
+cudaError_t launch_prune(int meas, int k, const int32_t* row_ptr, const int32_t* col, const float* val,
+                         int64_t n, const float* D, int ldd, int h, const float* q_w, const float* t_fwd,
+                         const int64_t* sel_idx, const float* sel_val, int K, int64_t* cand, int* count,
+                         float* sym, int64_t* out_idx, float* out_dist, int* ok, cudaStream_t st);
 
 // Top-K smallest of t[0..n) by (value, index), into out_idx / out_dist (K <= kMaxTopK).
-// scratch must hold kTopkMaxBlocks * kMaxTopK uint64 keys.
+// scratch must hold kTopkScratchRow uint64 keys.
 cudaError_t launch_topk(const float* t, int64_t n, int K, unsigned long long* scratch,
                         int64_t* out_idx, float* out_dist, cudaStream_t st);
+
+// The same for `rows` rows of t (row stride ldt) in one launch; outputs are rows x K and
+// scratch holds rows * kTopkScratchRow keys.
+cudaError_t launch_topk_rows(const float* t, int64_t rows, int64_t n, int64_t ldt, int K,
+                             unsigned long long* scratch, int64_t* out_idx, float* out_dist,
+                             cudaStream_t st);
+
+// Tensor-core distance matrix (k_tc_dist.cu).  Operands are FP16 panels in the canonical
+// K-major core-matrix layout (see launch_pack_f16) with Mpad / Npad rows (multiples of 128)
+// and Kpad = m rounded up to 64; split = hi + lo * 2^-11 with three products (FP32-grade),
+// else hi only.  D[u, j] as launch_dist_fp32, +inf for j in [N, ldd).
+cudaError_t launch_tc_dist(bool split, const __half* A_hi, const __half* A_lo, int64_t Mpad, const float* a_scale,
+                           const float* a_norm, const int32_t* a_ids, int64_t M, const __half* B_hi,
+                           const __half* B_lo, int64_t Npad, const float* b_scale, const float* b_norm,
+                           const int32_t* b_ids, int N, int Kpad, float* D, int ldd, int* err, cudaStream_t st);
+
+// Pack R rows of an FP32 matrix (ld floats per row, m used) into FP16 panels of Rpad rows
+// and Kpad columns with per-row absmax scales; lo (may be null) receives the scaled
+// remainder (x/s - hi) * 2^11.
+cudaError_t launch_pack_f16(const float* src, int ld, int m, int64_t R, int64_t Rpad, int Kpad, __half* hi,
+                            __half* lo, float* scale, cudaStream_t st);
 
 // Failure message for emd_last_error() (defined beside the C ABI).
 emd_status set_error(emd_status st, const char* msg);

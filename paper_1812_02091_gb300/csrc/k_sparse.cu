@@ -70,80 +70,136 @@ __global__ void k_fwd(const int32_t* __restrict__ row_ptr, const int32_t* __rest
 //
 // The query's bins are the sources (mass q_j), the document's bins the destinations
 // (capacities x_u), the cost block D[supp(d), j] is gathered from the Phase-1 matrix.
-// One warp per document; lane j' of chunk c handles query bin j = 32c + j' and keeps a
-// register top-KT of (distance, capacity) over the document's bins, visited in CSR
-// order (strict '<' keeps the earlier bin first on equal distance).  Reads of
-// D[u, 32c .. 32c+31] are one 128-byte line per bin.
+// One warp per document.  Lane l of a pass handles the NJ consecutive query bins
+// j = jbase + NJ*l .. +NJ-1 and keeps, for each, a register list of the KT smallest
+// (distance, capacity) over the document's bins, visited in CSR order.  A D row segment
+// for one document bin is one NJ-float vector load per lane (a warp reads 128*NJ
+// contiguous bytes); four bins' loads are issued before their insertions.  Insertion is
+// branch-free: with 32*NJ lists per warp some list almost always changes, so a branch
+// would diverge on nearly every bin.  Strict '<' keeps the earlier bin first on equal
+// distance.
 
-template <int MEAS>
-__device__ __forceinline__ float rev_cost_sorted(float qj, const float* z, const float* cap,
+// Cost of moving source mass qj along a sorted destination list (Alg. 3 / Alg. 1).  The loop
+// runs over the compile-time width with predicates so that the lists stay in registers;
+// transfers after the residual reaches zero add exactly zero.
+template <int MEAS, int KT>
+__device__ __forceinline__ float rev_cost_sorted(float qj, const float (&z)[KT], const float (&cap)[KT],
                                                  int keff)
 {
     if (MEAS == M_RWMD) return qj * z[0];
     if (MEAS == M_OMR) {
-        if (z[0] == 0.f && keff >= 2) {
+        if (KT >= 2 && z[0] == 0.f && keff >= 2) {
             const float r = qj - fminf(qj, cap[0]);
-            return r != 0.f ? r * z[1] : 0.f;
+            return r != 0.f ? r * z[KT >= 2 ? 1 : 0] : 0.f;
         }
         return qj * z[0];
     }
-    float r = qj, c = 0.f;
-    for (int l = 0; l < keff - 1; ++l) {
+    // z is ascending, so z[keff-1] is the largest of the first keff entries (distances >= 0)
+    float r = qj, c = 0.f, zlast = 0.f;
+#pragma unroll
+    for (int l = 0; l < KT; ++l) {
+        const bool capped = l < keff - 1;
         const float tau = fminf(r, cap[l]);
-        c = fmaf(tau, z[l], c);
-        r -= tau;
-        if (r == 0.f) return c;
+        c = capped ? fmaf(tau, z[l], c) : c;
+        r = capped ? r - tau : r;
+        zlast = fmaxf(zlast, l < keff ? z[l] : 0.f);
     }
-    return fmaf(r, z[keff - 1], c);
+    return r != 0.f ? fmaf(r, zlast, c) : c;
 }
 
-template <int MEAS, int KT>
-__global__ void k_rev(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                      const float* __restrict__ val, int64_t n, const float* __restrict__ D,
-                      int ldd, int h, const float* __restrict__ q_w, int k,
-                      const float* __restrict__ t_fwd, float* __restrict__ t_rev,
-                      float* __restrict__ t_max)
+// Insert (d, x) into the ascending list z (payload c), keeping the KT smallest.
+template <int KT>
+__device__ __forceinline__ void insert_sorted(float (&z)[KT], float (&c)[KT], float d, float x)
 {
+    bool p[KT];
+#pragma unroll
+    for (int l = 0; l < KT; ++l) p[l] = d < z[l];
+#pragma unroll
+    for (int l = KT - 1; l > 0; --l) {
+        z[l] = p[l - 1] ? z[l - 1] : (p[l] ? d : z[l]);
+        c[l] = p[l - 1] ? c[l - 1] : (p[l] ? x : c[l]);
+    }
+    z[0] = p[0] ? d : z[0];
+    c[0] = p[0] ? x : c[0];
+}
+
+__device__ __forceinline__ void load_vec(const float* p, bool ok, float (&o)[1])
+{
+    o[0] = ok ? *p : INFINITY;
+}
+__device__ __forceinline__ void load_vec(const float* p, bool ok, float (&o)[2])
+{
+    const float2 v = ok ? *reinterpret_cast<const float2*>(p) : make_float2(INFINITY, INFINITY);
+    o[0] = v.x; o[1] = v.y;
+}
+__device__ __forceinline__ void load_vec(const float* p, bool ok, float (&o)[4])
+{
+    const float4 v = ok ? *reinterpret_cast<const float4*>(p) : make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+
+template <int MEAS, int KT, int NJ>
+__global__ void __launch_bounds__(256, 2)
+k_rev(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+      const float* __restrict__ val, int64_t n, const float* __restrict__ D, int ldd, int h,
+      const float* __restrict__ q_w, int k, const float* __restrict__ t_fwd,
+      float* __restrict__ t_rev, float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
+      const int* __restrict__ n_dev)
+{
+    constexpr int U = 4;  // bins whose loads are in flight together
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    if (n_dev) n = min(n, (int64_t)*n_dev);  // slots filled on the device (candidate lists)
     for (int64_t d = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); d < n; d += warps) {
-        const int32_t a = row_ptr[d], b = row_ptr[d + 1];
+        const int64_t dd = doc_ids ? doc_ids[d] : d;  // document of this output slot
+        const int32_t a = row_ptr[dd], b = row_ptr[dd + 1];
         const int hd = b - a;
         const int keff = MEAS == M_RWMD ? 1 : (MEAS == M_OMR ? min(2, hd) : min(k, hd));
         float total = 0.f;
-        for (int jc = 0; jc < h; jc += 32) {
-            const int j = jc + lane;
-            float z[KT], cap[KT];
+        for (int jbase = 0; jbase < h; jbase += 32 * NJ) {
+            const int j0 = jbase + lane * NJ;
+            const bool jin = j0 < ldd;  // ldd % 32 == 0 and NJ | 32: the whole vector is in the row
+            float z[NJ][KT], cap[NJ][KT];
 #pragma unroll
-            for (int l = 0; l < KT; ++l) { z[l] = INFINITY; cap[l] = 0.f; }
+            for (int t = 0; t < NJ; ++t)
+#pragma unroll
+                for (int l = 0; l < KT; ++l) { z[t][l] = INFINITY; cap[t][l] = 0.f; }
             for (int32_t eb = a; eb < b; eb += 32) {
                 const int32_t e = eb + lane;
                 const int32_t u = e < b ? col[e] : 0;
                 const float x = e < b ? val[e] : 0.f;
                 const int cnt = min(32, b - eb);
-                for (int i = 0; i < cnt; ++i) {
+                int i = 0;
+                for (; i + U <= cnt; i += U) {
+                    float dv[U][NJ], xv[U];
+#pragma unroll
+                    for (int s = 0; s < U; ++s) {
+                        const int32_t ui = __shfl_sync(0xffffffffu, u, i + s);
+                        xv[s] = __shfl_sync(0xffffffffu, x, i + s);
+                        load_vec(D + (int64_t)ui * ldd + j0, jin, dv[s]);
+                    }
+#pragma unroll
+                    for (int s = 0; s < U; ++s)
+#pragma unroll
+                        for (int t = 0; t < NJ; ++t) insert_sorted<KT>(z[t], cap[t], dv[s][t], xv[s]);
+                }
+                for (; i < cnt; ++i) {
                     const int32_t ui = __shfl_sync(0xffffffffu, u, i);
                     const float xi = __shfl_sync(0xffffffffu, x, i);
-                    const float dd = D[(int64_t)ui * ldd + j];  // j < ldd: padding holds +inf
-                    if (dd < z[KT - 1]) {
-                        z[KT - 1] = dd;
-                        cap[KT - 1] = xi;
+                    float dv[NJ];
+                    load_vec(D + (int64_t)ui * ldd + j0, jin, dv);
 #pragma unroll
-                        for (int l = KT - 1; l > 0; --l) {
-                            if (z[l] < z[l - 1]) {
-                                float tz = z[l]; z[l] = z[l - 1]; z[l - 1] = tz;
-                                float tc = cap[l]; cap[l] = cap[l - 1]; cap[l - 1] = tc;
-                            }
-                        }
-                    }
+                    for (int t = 0; t < NJ; ++t) insert_sorted<KT>(z[t], cap[t], dv[t], xi);
                 }
             }
-            if (j < h) total += rev_cost_sorted<MEAS>(q_w[j], z, cap, keff);
+#pragma unroll
+            for (int t = 0; t < NJ; ++t)
+                if (j0 + t < h) total += rev_cost_sorted<MEAS, KT>(q_w[j0 + t], z[t], cap[t], keff);
         }
         total = warp_sum(total);
         if (lane == 0) {
             t_rev[d] = total;
-            if (t_max) t_max[d] = fmaxf(t_fwd[d], total);
+            if (t_max) t_max[d] = fmaxf(t_fwd[dd], total);
         }
     }
 }
@@ -156,12 +212,15 @@ __global__ void k_rev_generic(const int32_t* __restrict__ row_ptr, const int32_t
                               const float* __restrict__ val, int64_t n, const float* __restrict__ D,
                               int ldd, int h, const float* __restrict__ q_w, int k,
                               const float* __restrict__ t_fwd, float* __restrict__ t_rev,
-                              float* __restrict__ t_max)
+                              float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
+                              const int* __restrict__ n_dev)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    if (n_dev) n = min(n, (int64_t)*n_dev);
     for (int64_t d = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); d < n; d += warps) {
-        const int32_t a = row_ptr[d], b = row_ptr[d + 1];
+        const int64_t dd = doc_ids ? doc_ids[d] : d;
+        const int32_t a = row_ptr[dd], b = row_ptr[dd + 1];
         const int hd = b - a;
         const int keff = MEAS == M_ICT ? hd : min(k, hd);
         float total = 0.f;
@@ -194,7 +253,7 @@ __global__ void k_rev_generic(const int32_t* __restrict__ row_ptr, const int32_t
         total = warp_sum(total);
         if (lane == 0) {
             t_rev[d] = total;
-            if (t_max) t_max[d] = fmaxf(t_fwd[d], total);
+            if (t_max) t_max[d] = fmaxf(t_fwd[dd], total);
         }
     }
 }
@@ -259,10 +318,12 @@ __device__ void block_merge_and_emit(unsigned long long (&L)[KT], int K, unsigne
 
 template <int KT>
 __global__ void __launch_bounds__(kTopkThreads)
-k_topk_values(const float* __restrict__ t, int64_t n, int K, int64_t per_block,
+k_topk_values(const float* __restrict__ t, int64_t n, int64_t ldt, int K, int64_t per_block,
               unsigned long long* __restrict__ scratch, int64_t* __restrict__ out_idx,
               float* __restrict__ out_dist)
 {
+    const int64_t row = blockIdx.y;
+    t += row * ldt;
     unsigned long long L[KT];
 #pragma unroll
     for (int l = 0; l < KT; ++l) L[l] = ~0ull;
@@ -274,9 +335,10 @@ k_topk_values(const float* __restrict__ t, int64_t n, int K, int64_t per_block,
         list_insert<KT>(L, key);
     }
     if (gridDim.x == 1)
-        block_merge_and_emit<KT>(L, K, nullptr, out_idx, out_dist);
+        block_merge_and_emit<KT>(L, K, nullptr, out_idx + row * K, out_dist + row * K);
     else
-        block_merge_and_emit<KT>(L, KT, scratch + (int64_t)blockIdx.x * KT, nullptr, nullptr);
+        block_merge_and_emit<KT>(L, KT, scratch + row * kTopkScratchRow + (int64_t)blockIdx.x * KT,
+                                 nullptr, nullptr);
 }
 
 template <int KT>
@@ -284,45 +346,103 @@ __global__ void __launch_bounds__(kTopkThreads)
 k_topk_keys(const unsigned long long* __restrict__ keys, int64_t count, int K,
             int64_t* __restrict__ out_idx, float* __restrict__ out_dist)
 {
+    const int64_t row = blockIdx.x;
+    keys += row * kTopkScratchRow;
     unsigned long long L[KT];
 #pragma unroll
     for (int l = 0; l < KT; ++l) L[l] = ~0ull;
     for (int64_t i = threadIdx.x; i < count; i += blockDim.x) list_insert<KT>(L, keys[i]);
-    block_merge_and_emit<KT>(L, K, nullptr, out_idx, out_dist);
+    block_merge_and_emit<KT>(L, K, nullptr, out_idx + row * K, out_dist + row * K);
 }
 
 template <int KT>
-cudaError_t topk_kt(const float* t, int64_t n, int K, unsigned long long* scratch,
-                    int64_t* out_idx, float* out_dist, cudaStream_t st)
+cudaError_t topk_kt(const float* t, int64_t rows, int64_t n, int64_t ldt, int K,
+                    unsigned long long* scratch, int64_t* out_idx, float* out_dist, cudaStream_t st)
 {
     const size_t smem = (size_t)kTopkThreads * KT * sizeof(unsigned long long);
-    int blocks = (int)std::min<int64_t>(kTopkMaxBlocks, std::max<int64_t>(1, n / 8192));
+    const int blocks = topk_blocks(n);
     const int64_t per_block = (n + blocks - 1) / blocks;
     if (smem > 48 * 1024) {
         cudaFuncSetAttribute(k_topk_values<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_topk_keys<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
-    k_topk_values<KT><<<blocks, kTopkThreads, smem, st>>>(t, n, K, per_block, scratch, out_idx, out_dist);
+    k_topk_values<KT><<<dim3(blocks, (unsigned)rows), kTopkThreads, smem, st>>>(t, n, ldt, K, per_block, scratch,
+                                                                                 out_idx, out_dist);
     if (blocks > 1)
-        k_topk_keys<KT><<<1, kTopkThreads, smem, st>>>(scratch, (int64_t)blocks * KT, K, out_idx, out_dist);
+        k_topk_keys<KT><<<(unsigned)rows, kTopkThreads, smem, st>>>(scratch, (int64_t)blocks * KT, K, out_idx,
+                                                                     out_dist);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ pruned symmetric top-K
+//
+// max(fwd, rev) >= fwd.  With theta = fwd_K * (1 + 2^-7) (fwd_K the K-th smallest forward
+// value), the candidates are the documents with fwd <= theta; every other document has
+// sym >= fwd > theta.  Once the K-th smallest symmetric value among the candidates is
+// <= theta, no other document can enter the top-K, not even by the id tie-break.
+
+__device__ __forceinline__ float prune_theta(float fwd_k) { return fwd_k * (1.0f + 0.0078125f); }
+
+__global__ void k_prune_compact(const float* __restrict__ t_fwd, int64_t n, const float* __restrict__ sel_val,
+                                int K, int cap, int64_t* __restrict__ cand, int* __restrict__ count)
+{
+    const float theta = prune_theta(sel_val[K - 1]);
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < n; d += (int64_t)gridDim.x * blockDim.x) {
+        if (t_fwd[d] <= theta) {
+            const int pos = atomicAdd(count, 1);
+            if (pos < cap) cand[pos] = d;
+        }
+    }
+}
+
+// Final selection over the candidates: thread i ranks candidate i in (sym, id) order
+// against all others; ranks < K are written; ok = no overflow and K-th <= theta.
+__global__ void k_prune_select(const int64_t* __restrict__ cand, const float* __restrict__ sym,
+                               const int* __restrict__ count, int cap, const float* __restrict__ sel_val,
+                               int K, int64_t* __restrict__ out_idx, float* __restrict__ out_dist,
+                               int* __restrict__ ok)
+{
+    __shared__ float ss[kPruneCap];
+    __shared__ int64_t si[kPruneCap];
+    __shared__ float kth;
+    const int c = min(*count, cap);
+    const int i = threadIdx.x;
+    ss[i] = i < c ? sym[i] : INFINITY;
+    si[i] = i < c ? cand[i] : INT64_MAX;
+    if (i == 0) kth = INFINITY;
+    __syncthreads();
+    int r = 0;
+    const float me = ss[i];
+    const int64_t mi = si[i];
+    for (int j = 0; j < kPruneCap; ++j) {
+        const float o = ss[j];
+        r += (o < me || (o == me && si[j] < mi)) ? 1 : 0;
+    }
+    if (i < c && r < K) { out_idx[r] = mi; out_dist[r] = me; }
+    if (i < c && r == K - 1) kth = me;
+    __syncthreads();
+    if (i == 0) *ok = (*count <= cap && c >= K && kth <= prune_theta(sel_val[K - 1])) ? 1 : 0;
 }
 
 template <int MEAS>
 cudaError_t rev_meas(int k, const int32_t* row_ptr, const int32_t* col, const float* val,
                      int64_t n, const float* D, int ldd, int h, const float* q_w,
-                     const float* t_fwd, float* t_rev, float* t_max, cudaStream_t st)
+                     const float* t_fwd, float* t_rev, float* t_max, const int64_t* doc_ids,
+                     const int* n_dev, cudaStream_t st)
 {
     const int warps = 8;
     const int64_t blocks = std::min<int64_t>((n + warps - 1) / warps, 152 * 64);
     dim3 grid((unsigned)std::max<int64_t>(1, blocks));
     const int kt = MEAS == M_RWMD ? 1 : (MEAS == M_OMR ? 2 : (MEAS == M_ICT ? 1 << 30 : k));
-    if (kt <= 1) k_rev<MEAS, 1><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, D, ldd, h, q_w, k, t_fwd, t_rev, t_max);
-    else if (kt <= 2) k_rev<MEAS, 2><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, D, ldd, h, q_w, k, t_fwd, t_rev, t_max);
-    else if (kt <= 4) k_rev<MEAS, 4><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, D, ldd, h, q_w, k, t_fwd, t_rev, t_max);
-    else if (kt <= 8) k_rev<MEAS, 8><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, D, ldd, h, q_w, k, t_fwd, t_rev, t_max);
-    else if (kt <= 16) k_rev<MEAS, 16><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, D, ldd, h, q_w, k, t_fwd, t_rev, t_max);
-    else k_rev_generic<MEAS><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, D, ldd, h, q_w, k, t_fwd, t_rev, t_max);
+    const bool wide = h > 32;  // several 32-bin chunks: vector loads of consecutive bins
+#define EMD_REV(KT, NJ) k_rev<MEAS, KT, NJ><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev)
+    if (kt <= 1) { if (wide) EMD_REV(1, 4); else EMD_REV(1, 1); }
+    else if (kt <= 2) { if (wide) EMD_REV(2, 4); else EMD_REV(2, 1); }
+    else if (kt <= 4) { if (wide) EMD_REV(4, 4); else EMD_REV(4, 1); }
+    else if (kt <= 8) { if (wide) EMD_REV(8, 2); else EMD_REV(8, 1); }
+    else if (kt <= 16) EMD_REV(16, 1);
+    else k_rev_generic<MEAS><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev);
+#undef EMD_REV
     return cudaGetLastError();
 }
 
@@ -347,23 +467,52 @@ cudaError_t launch_fwd(int meas, const int32_t* row_ptr, const int32_t* col, con
 cudaError_t launch_rev(int meas, int k, const int32_t* row_ptr, const int32_t* col,
                        const float* val, int64_t n, const float* D, int ldd, int h,
                        const float* q_w, const float* t_fwd, float* t_rev, float* t_max,
-                       cudaStream_t st)
+                       const int64_t* doc_ids, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     switch (meas) {
-    case M_RWMD: return rev_meas<M_RWMD>(k, row_ptr, col, val, n, D, ldd, h, q_w, t_fwd, t_rev, t_max, st);
-    case M_OMR: return rev_meas<M_OMR>(k, row_ptr, col, val, n, D, ldd, h, q_w, t_fwd, t_rev, t_max, st);
-    case M_ICT: return rev_meas<M_ICT>(k, row_ptr, col, val, n, D, ldd, h, q_w, t_fwd, t_rev, t_max, st);
-    default: return rev_meas<M_ACT>(k, row_ptr, col, val, n, D, ldd, h, q_w, t_fwd, t_rev, t_max, st);
+    case M_RWMD: return rev_meas<M_RWMD>(k, row_ptr, col, val, n, D, ldd, h, q_w, t_fwd, t_rev, t_max, doc_ids, nullptr, st);
+    case M_OMR: return rev_meas<M_OMR>(k, row_ptr, col, val, n, D, ldd, h, q_w, t_fwd, t_rev, t_max, doc_ids, nullptr, st);
+    case M_ICT: return rev_meas<M_ICT>(k, row_ptr, col, val, n, D, ldd, h, q_w, t_fwd, t_rev, t_max, doc_ids, nullptr, st);
+    default: return rev_meas<M_ACT>(k, row_ptr, col, val, n, D, ldd, h, q_w, t_fwd, t_rev, t_max, doc_ids, nullptr, st);
     }
+}
+
+cudaError_t launch_prune(int meas, int k, const int32_t* row_ptr, const int32_t* col, const float* val,
+                         int64_t n, const float* D, int ldd, int h, const float* q_w, const float* t_fwd,
+                         const int64_t* sel_idx, const float* sel_val, int K, int64_t* cand, int* count,
+                         float* sym, int64_t* out_idx, float* out_dist, int* ok, cudaStream_t st)
+{
+    (void)sel_idx;
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    const int blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256), 152 * 4);
+    k_prune_compact<<<blocks, 256, 0, st>>>(t_fwd, n, sel_val, K, kPruneCap, cand, count);
+    // reverse pass on the candidate slots (t_rev into sym + kPruneCap, max into sym)
+    switch (meas) {
+    case M_RWMD: e = rev_meas<M_RWMD>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, st); break;
+    case M_OMR: e = rev_meas<M_OMR>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, st); break;
+    default: e = rev_meas<M_ACT>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, st); break;
+    }
+    if (e != cudaSuccess) return e;
+    k_prune_select<<<1, kPruneCap, 0, st>>>(cand, sym, count, kPruneCap, sel_val, K, out_idx, out_dist, ok);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_topk_rows(const float* t, int64_t rows, int64_t n, int64_t ldt, int K,
+                             unsigned long long* scratch, int64_t* out_idx, float* out_dist,
+                             cudaStream_t st)
+{
+    if (rows <= 0) return cudaSuccess;
+    if (K <= 16) return topk_kt<16>(t, rows, n, ldt, K, scratch, out_idx, out_dist, st);
+    if (K <= 32) return topk_kt<32>(t, rows, n, ldt, K, scratch, out_idx, out_dist, st);
+    return topk_kt<64>(t, rows, n, ldt, K, scratch, out_idx, out_dist, st);
 }
 
 cudaError_t launch_topk(const float* t, int64_t n, int K, unsigned long long* scratch,
                         int64_t* out_idx, float* out_dist, cudaStream_t st)
 {
-    if (K <= 16) return topk_kt<16>(t, n, K, scratch, out_idx, out_dist, st);
-    if (K <= 32) return topk_kt<32>(t, n, K, scratch, out_idx, out_dist, st);
-    return topk_kt<64>(t, n, K, scratch, out_idx, out_dist, st);
+    return launch_topk_rows(t, 1, n, n, K, scratch, out_idx, out_dist, st);
 }
 
 }  // namespace emd
@@ -388,7 +537,7 @@ cudaError_t launch_topk(const float* t, int64_t n, int K, unsigned long long* sc
 namespace {
 
 constexpr int kStaticMaxRows = 64;  // rows (queries) per call
-constexpr size_t kStaticScratchKeys = (size_t)kStaticMaxRows * emd::kTopkMaxBlocks * emd::kMaxTopK;
+constexpr size_t kStaticScratchKeys = (size_t)kStaticMaxRows * emd::kTopkScratchRow;
 
 static __device__ __align__(256) unsigned long long g_topk_static_scratch[kStaticScratchKeys];
 
@@ -436,10 +585,7 @@ extern "C" emd_status emd_topk_select_static(const float* t_dev, int64_t n_rows,
     if (e != cudaSuccess)
         return emd::set_error(EMD_ERR_CUDA, cudaGetErrorString(e));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    for (int64_t r = 0; r < n_rows; ++r) {
-        e = emd::launch_topk(t_dev + r * n, n, K, scratch + r * (int64_t)emd::kTopkMaxBlocks * emd::kMaxTopK,
-                             out_idx_dev + r * K, out_dist_dev + r * K, st);
-        if (e != cudaSuccess) return emd::set_error(EMD_ERR_CUDA, cudaGetErrorString(e));
-    }
+    e = emd::launch_topk_rows(t_dev, n_rows, n, n, K, scratch, out_idx_dev, out_dist_dev, st);
+    if (e != cudaSuccess) return emd::set_error(EMD_ERR_CUDA, cudaGetErrorString(e));
     return EMD_OK;
 }

@@ -1,0 +1,384 @@
+// Phase 1 of LC-ACT (Section 4) on the 5th-generation tensor cores of sm_103a: the
+// distance matrix D = dist(V, Q) from the product V Q^T (Section 4: "a matrix-matrix
+// multiplication between V and the transpose of Q") with FP32 accumulators in TMEM.
+//
+// Operands are FP16 with a per-row absmax scale.  In the split form every operand is held
+// as hi + lo * 2^-11 (hi = fp16(x/s), lo = fp16((x/s - hi) * 2^11)) and three products
+// hi*hi (accumulator 0) and hi*lo + lo*hi (accumulator 1) reconstruct the dot product to
+// about 2^-22 relative: FP32-grade distances on the tensor pipe.  The plain form uses the
+// hi parts only.
+//
+// Data movement: both operands are pre-packed in global memory in the canonical K-major,
+// no-swizzle UMMA layout -- 8x8 core matrices of 128 contiguous bytes; inside a 64-element
+// K chunk the 8 core matrices of a row group are adjacent (leading byte offset 128 B) and
+// row groups follow each other 1 KB apart (stride byte offset).  A tile's K chunk is
+// therefore one contiguous block and moves with one 1-D bulk copy (cp.async.bulk, the TMA
+// engine) completing on an mbarrier.
+//
+// Roles (192 threads): warp 0 lane 0 issues the copies into a ring of stages; warp 1
+// allocates TMEM and its lane 0 issues tcgen05.mma (M = 128 rows of V, N <= 128 query
+// columns, K = 16 per instruction) and tcgen05.commit; warps 2..5 wait for the final
+// commit, read their TMEM lane quarter with tcgen05.ld and write
+// d = sqrt(max(|v|^2 + |q|^2 - 2 v.q, 0)), exactly 0 for identical vocabulary ids.
+// Every wait is bounded in time; a timeout latches ERR_TIMEOUT and the block tears down.
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "emd_internal.cuh"
+
+namespace emd {
+namespace {
+
+constexpr int TC_BM = 128;          // rows per tile = TMEM lanes
+constexpr int TC_BN = 128;          // largest column tile
+constexpr int TC_THREADS = 192;
+constexpr uint32_t TC_A_BYTES = TC_BM * 128;  // one 64-wide K chunk of 128 rows
+constexpr uint32_t TC_B_BYTES = TC_BN * 128;
+constexpr uint64_t TC_TIMEOUT_NS = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity; false once the deadline has passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t deadline)
+{
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() > deadline) return false;
+    return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Shared-memory matrix descriptor: canonical K-major layout without swizzle, leading
+// byte offset 128 (next core matrix along K), stride byte offset 1024 (next 8-row group),
+// descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (FP16 inputs, FP32 accumulate).
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                        uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrive on the mbarrier once every tcgen05.mma issued so far by this thread is done.
+__device__ __forceinline__ void mma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+// 32 consecutive TMEM columns of this thread's lane (32x32b shape, 32 repetitions).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_tc_dist(const __half* __restrict__ A_hi, const __half* __restrict__ A_lo, int64_t Mpad,
+          const float* __restrict__ a_scale, const float* __restrict__ a_norm, const int32_t* __restrict__ a_ids,
+          int64_t M, const __half* __restrict__ B_hi, const __half* __restrict__ B_lo, int64_t Npad,
+          const float* __restrict__ b_scale, const float* __restrict__ b_norm, const int32_t* __restrict__ b_ids,
+          int N, int KC, int stages, float* __restrict__ D, int ldd, int* __restrict__ err)
+{
+    constexpr uint32_t kStage = SPLIT ? 2 * (TC_A_BYTES + TC_B_BYTES) : (TC_A_BYTES + TC_B_BYTES);
+    constexpr uint32_t kCols = SPLIT ? 256 : 128;  // TMEM columns: accumulator 0 at 0, 1 at 128
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)stages * kStage);
+    uint64_t* empty = full + stages;
+    uint64_t* done = empty + stages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t m0 = (int64_t)blockIdx.x * TC_BM;
+    const int n0 = blockIdx.y * TC_BN;
+    const int Nt = min(TC_BN, (int)round_up(N - n0, 16));
+    const uint32_t b_bytes = (uint32_t)Nt * 128u;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        mbar_fence_init();
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, kCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint64_t deadline = global_ns() + TC_TIMEOUT_NS;
+
+    if (warp == 0 && lane == 0) {
+        // producer: K chunk c of this tile's rows and columns into stage c % stages
+        int issued = 0;
+        for (int c = 0; c < KC; ++c) {
+            const int s = c % stages;
+            if (c >= stages && !mbar_wait(&empty[s], (uint32_t)((c / stages) - 1) & 1u, deadline)) {
+                atomicOr(err, ERR_TIMEOUT);
+                break;
+            }
+            issued = c + 1;
+            uint8_t* st = smem + (size_t)s * kStage;
+            mbar_expect_tx(&full[s], (SPLIT ? 2u : 1u) * (TC_A_BYTES + b_bytes));
+            bulk_g2s(st, A_hi + ((int64_t)c * Mpad + m0) * 64, TC_A_BYTES, &full[s]);
+            if (SPLIT) bulk_g2s(st + TC_A_BYTES, A_lo + ((int64_t)c * Mpad + m0) * 64, TC_A_BYTES, &full[s]);
+            uint8_t* bst = st + (SPLIT ? 2 : 1) * TC_A_BYTES;
+            bulk_g2s(bst, B_hi + ((int64_t)c * Npad + n0) * 64, b_bytes, &full[s]);
+            if (SPLIT) bulk_g2s(bst + TC_B_BYTES, B_lo + ((int64_t)c * Npad + n0) * 64, b_bytes, &full[s]);
+        }
+        // no copy may still be landing in shared memory when the block leaves: the last
+        // `stages` chunks are the only ones nobody else has waited for (bounded again)
+        const uint64_t tail = global_ns() + TC_TIMEOUT_NS;
+        for (int c = max(0, issued - stages); c < issued; ++c)
+            if (!mbar_wait(&full[c % stages], (uint32_t)(c / stages) & 1u, tail)) atomicOr(err, ERR_TIMEOUT);
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: kind::f16, D format F32 (bit 4), A/B format F16 (0), K-major A and B,
+        // N >> 3 at bit 17, M >> 4 at bit 24
+        const uint32_t idesc = (1u << 4) | ((uint32_t)(Nt >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+        for (int c = 0; c < KC; ++c) {
+            const int s = c % stages;
+            if (!mbar_wait(&full[s], (uint32_t)(c / stages) & 1u, deadline)) {
+                atomicOr(err, ERR_TIMEOUT);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + (size_t)s * kStage);
+            const uint32_t sa_lo = sa + TC_A_BYTES;
+            const uint32_t sb = sa + (SPLIT ? 2 : 1) * TC_A_BYTES;
+            const uint32_t sb_lo = sb + TC_B_BYTES;
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {  // 4 x K=16 per 64-wide chunk: 2 core matrices = 256 B
+                const uint32_t ko = (uint32_t)ks * 256u;
+                const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+                const uint64_t da = smem_desc(sa + ko), db = smem_desc(sb + ko);
+                mma_f16(tmem, da, db, idesc, acc);
+                if (SPLIT) {
+                    mma_f16(tmem + 128, da, smem_desc(sb_lo + ko), idesc, acc);
+                    mma_f16(tmem + 128, smem_desc(sa_lo + ko), db, idesc, 1u);
+                }
+            }
+            mma_commit(&empty[s]);
+        }
+        mma_commit(done);
+    } else if (warp >= 2) {
+        // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 = tile rows
+        const int q = warp & 3;
+        const int row = q * 32 + lane;
+        const int64_t u = m0 + row;
+        const bool row_ok = u < M;
+        if (!mbar_wait(done, 0u, deadline)) {
+            atomicOr(err, ERR_TIMEOUT);
+        } else {
+            tc_fence_after();
+            const float su = row_ok ? a_scale[u] : 0.f;
+            const float nu = row_ok ? a_norm[u] : 0.f;
+            const int32_t idu = row_ok ? a_ids[u] : -1;
+            const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16);
+            for (int cc = 0; cc < Nt; cc += 32) {
+                uint32_t r0[32], r1[32];
+                tmem_ld32(tbase + (uint32_t)cc, r0);
+                if (SPLIT) tmem_ld32(tbase + 128u + (uint32_t)cc, r1);
+                tmem_wait_ld();
+                if (!row_ok) continue;
+                float* out = D + u * ldd + n0 + cc;
+#pragma unroll
+                for (int e4 = 0; e4 < 8; ++e4) {
+                    float o[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int e = e4 * 4 + t;
+                        const int col = n0 + cc + e;
+                        float d = INFINITY;
+                        if (col < N) {
+                            float dot = __uint_as_float(r0[e]);
+                            if (SPLIT) dot = fmaf(__uint_as_float(r1[e]), 1.0f / 2048.0f, dot);
+                            dot *= su * b_scale[col];
+                            const float d2 = fmaf(-2.f, dot, nu + b_norm[col]);
+                            d = (idu == b_ids[col]) ? 0.f : sqrtf(fmaxf(d2, 0.f));
+                        }
+                        o[t] = d;
+                    }
+                    if (n0 + cc + e4 * 4 < ldd)
+                        *reinterpret_cast<float4*>(out + e4 * 4) = make_float4(o[0], o[1], o[2], o[3]);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kCols);
+    }
+}
+
+// Pack rows of an FP32 matrix (ld floats per row, first m used) into the canonical layout
+// above: element (r, k) of a matrix with Rpad rows lives at half offset
+// (k/64)*Rpad*64 + (r/8)*512 + ((k%64)/8)*64 + (r%8)*8 + k%8.  One warp per row; rows
+// R..Rpad-1 and columns m..Kpad-1 are zero.  scale[r] = max |x| (0 for a zero row).
+__global__ void k_pack_f16(const float* __restrict__ src, int ld, int m, int64_t R, int64_t Rpad, int Kpad,
+                           __half* __restrict__ hi, __half* __restrict__ lo, float* __restrict__ scale)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= Rpad) return;
+    const bool live = r < R;
+    float amax = 0.f;
+    if (live)
+        for (int k = lane; k < m; k += 32) amax = fmaxf(amax, fabsf(src[r * ld + k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    const float inv = amax > 0.f ? 1.0f / amax : 0.f;
+    const int64_t rbase = (r >> 3) * 512 + (r & 7) * 8;
+    for (int k = lane; k < Kpad; k += 32) {
+        const float y = (live && k < m) ? src[r * ld + k] * inv : 0.f;
+        const __half h = __float2half_rn(y);
+        const int64_t off = (int64_t)(k >> 6) * Rpad * 64 + rbase + ((k & 63) >> 3) * 64 + (k & 7);
+        hi[off] = h;
+        if (lo) lo[off] = __float2half_rn((y - __half2float(h)) * 2048.0f);
+    }
+    if (lane == 0) scale[r] = amax;
+}
+
+}  // namespace
+
+size_t tc_dist_smem_bytes(bool split, int stages)
+{
+    const size_t stage = split ? 2 * (TC_A_BYTES + TC_B_BYTES) : (TC_A_BYTES + TC_B_BYTES);
+    return 1024 + (size_t)stages * stage + (2 * (size_t)stages + 1) * 8 + 16;
+}
+
+int tc_dist_stages(bool split, int KC)
+{
+    return std::max(1, std::min(KC, split ? 3 : 5));
+}
+
+cudaError_t launch_pack_f16(const float* src, int ld, int m, int64_t R, int64_t Rpad, int Kpad, __half* hi,
+                            __half* lo, float* scale, cudaStream_t st)
+{
+    if (Rpad <= 0) return cudaSuccess;
+    const int warps = 8;
+    k_pack_f16<<<(unsigned)((Rpad + warps - 1) / warps), warps * 32, 0, st>>>(src, ld, m, R, Rpad, Kpad, hi, lo,
+                                                                              scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_dist(bool split, const __half* A_hi, const __half* A_lo, int64_t Mpad, const float* a_scale,
+                           const float* a_norm, const int32_t* a_ids, int64_t M, const __half* B_hi,
+                           const __half* B_lo, int64_t Npad, const float* b_scale, const float* b_norm,
+                           const int32_t* b_ids, int N, int Kpad, float* D, int ldd, int* err, cudaStream_t st)
+{
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    const int KC = Kpad / 64;
+    const int stages = tc_dist_stages(split, KC);
+    const size_t smem = tc_dist_smem_bytes(split, stages);
+    dim3 grid((unsigned)(Mpad / TC_BM), (unsigned)((N + TC_BN - 1) / TC_BN));
+    cudaError_t e;
+    if (split) {
+        e = cudaFuncSetAttribute(k_tc_dist<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_tc_dist<true><<<grid, TC_THREADS, smem, st>>>(A_hi, A_lo, Mpad, a_scale, a_norm, a_ids, M, B_hi, B_lo,
+                                                         Npad, b_scale, b_norm, b_ids, N, KC, stages, D, ldd, err);
+    } else {
+        e = cudaFuncSetAttribute(k_tc_dist<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_tc_dist<false><<<grid, TC_THREADS, smem, st>>>(A_hi, nullptr, Mpad, a_scale, a_norm, a_ids, M, B_hi,
+                                                          nullptr, Npad, b_scale, b_norm, b_ids, N, KC, stages, D,
+                                                          ldd, err);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace emd

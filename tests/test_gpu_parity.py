@@ -324,3 +324,89 @@ def test_text_full_size_forward_sampled_docs(emd, text_full, meas, k):
     sub = w.db.subset(docs)
     tf, tr = oracle.pair_db(w.emb, None, sub, qidx, qw, meas, k)
     np.testing.assert_allclose(got[docs], np.maximum(tf, tr), rtol=RTOL, atol=ATOL)
+
+
+# --------------------------------------------------------------------- pruned symmetric top-K
+
+def test_pruned_topk_equals_unpruned_full_size(emd, text_full):
+    """max(fwd, rev) >= fwd: the pruned top-K (reverse pass on the forward candidates only)
+    must equal the top-K over all documents."""
+    w, db = text_full
+    q = w.queries
+    emd.emd_db_profile_reset(db)
+    for K in (1, 10, 16):
+        for meas, k in (("act", 4), ("omr", 1), ("act", 2)):
+            pi, pd = emd.emd_topk(db, q.row_ptr, q.col, q.val, meas, k, "max", K)
+            full = emd.emd_query_batch(db, q.row_ptr, q.col, q.val, meas, k, "max")
+            for r in range(q.n):
+                order = np.lexsort((np.arange(w.db.n), full[r]))[:K]
+                np.testing.assert_array_equal(pi[r], order)
+                np.testing.assert_array_equal(pd[r], full[r][order])
+    prof = emd.emd_db_profile_get(db)
+    assert prof["pruned_queries"] >= 9 * q.n
+
+
+def test_pruning_fallback_on_ties(emd):
+    """Identical documents tie at every distance, so every one of them is a candidate;
+    more candidates than the pruned path holds (256) means no certificate, and the query
+    is recomputed over all documents.  The answer is the lowest ids either way."""
+    rng = np.random.default_rng(12)
+    emb = emd_synth.unit_embeddings(rng, 300, 16)
+    c = np.sort(rng.choice(300, 12, replace=False)).astype(np.int32)
+    x = np.full(12, 1 / 12, np.float32)
+    n = 300
+    rp = np.arange(n + 1, dtype=np.int64) * 12
+    db = emd.emd_db_create(emb, None, rp, np.tile(c, n), np.tile(x, n), emd.emd_db_options_default(max_query_h=32))
+    try:
+        qc = np.sort(rng.choice(300, 9, replace=False)).astype(np.int32)
+        qw = np.full(9, 1 / 9, np.float32)
+        emd.emd_db_profile_reset(db)
+        idx, dist = emd.emd_topk(db, np.array([0, 9]), qc, qw, "act", 3, "max", 10)
+        np.testing.assert_array_equal(idx[0], np.arange(10))
+        assert np.all(dist[0] == dist[0][0])
+        prof = emd.emd_db_profile_get(db)
+        assert prof["prune_fallbacks"] == 1 and prof["pruned_queries"] == 1
+    finally:
+        emd.emd_db_destroy(db)
+
+
+def test_device_topk_is_ordered_on_the_callers_stream(emd, text_full):
+    """Results of the device entry point are visible to later work on the same stream
+    without any explicit synchronisation (torch's current stream, here the default one)."""
+    import torch
+    w, db = text_full
+    q = w.queries
+    qi = torch.from_numpy(q.col).cuda()
+    qw = torch.from_numpy(q.val).cuda()
+    for K in (16, 32):  # 16: pruned path; 32: all documents, fully asynchronous
+        hi, hd = emd.emd_topk(db, q.row_ptr, q.col, q.val, "act", 4, "max", K)
+        for s in (torch.cuda.current_stream(), torch.cuda.Stream()):
+            with torch.cuda.stream(s):
+                oi = torch.full((q.n, K), -5, dtype=torch.int64, device="cuda")
+                od = torch.full((q.n, K), -5.0, dtype=torch.float32, device="cuda")
+                emd.emd_topk_device(db, q.row_ptr, qi, qw, oi, od, "act", 4, "max", K, stream=s.cuda_stream)
+                ci, cd = oi.clone(), od.clone()  # same stream, no synchronize in between
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(ci.cpu().numpy(), hi)
+            np.testing.assert_array_equal(cd.cpu().numpy(), hd)
+
+
+@pytest.mark.parametrize("meas,k", [("rwmd", 1), ("omr", 1), ("act", 2), ("act", 4), ("act", 16)])
+def test_pruned_topk_equals_unpruned_small_queries(emd, meas, k):
+    """Queries of 5..45 bins (one 32-bin chunk or several), where the reverse and forward
+    bounds differ most; every K up to the pruning limit."""
+    w = emd_synth.small_text(4242, V=600, m=48, n=300, n_queries=6, lo=5, hi=45)
+    q = w.queries
+    dbp = make_db(emd, w, max_query_h=64)
+    dbf = make_db(emd, w, max_query_h=64, prune_topk=0)
+    try:
+        for K in (1, 8, 16):
+            pi, pd = emd.emd_topk(dbp, q.row_ptr, q.col, q.val, meas, k, "max", K)
+            fi, fd = emd.emd_topk(dbf, q.row_ptr, q.col, q.val, meas, k, "max", K)
+            np.testing.assert_array_equal(pi, fi)
+            np.testing.assert_array_equal(pd, fd)
+        for qi in range(q.n):
+            assert_topk_matches(pi[qi], pd[qi], oracle_dir(w, qi, meas, k, "max"), 16)
+    finally:
+        emd.emd_db_destroy(dbp)
+        emd.emd_db_destroy(dbf)
