@@ -173,6 +173,7 @@ def main():
     ap.add_argument("--cpu-queries", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0, help="default: same as --steps")
+    ap.add_argument("--precision", default="fp32_tc", choices=["fp32", "fp32_tc"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -193,7 +194,8 @@ def main():
 
     w = emd_synth.config(2)
     opts = dict(device=local, max_query_h=1024, max_batch=args.batch)
-    db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val, emd.emd_db_options_default(**opts))
+    db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
+                           emd.emd_db_options_default(precision=args.precision, **opts))
     info = emd.emd_db_info_get(db)
     my_ids = shard(w.queries.n, rank, world)
     total_steps = args.warmup + args.steps
@@ -211,9 +213,10 @@ def main():
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
     stream = torch.cuda.current_stream()
 
-    def run_steps(handle, steps, keep=0):
+    def run_steps(handle, steps, keep=0, profile=False):
         """Warm up, then time `steps` batches with CUDA events on the launch stream, L2
-        flushed between steps outside the events; per-phase times from the library."""
+        flushed between steps outside the events; with `profile`, per-phase times from the
+        library's own events (on the streams the kernels run on)."""
         def step(s):
             rp, qi, qw, _, _ = dev_batches[s]
             emd.emd_topk_device(handle, rp, qi, qw, oi, od, "act", args.k, "max", K, stream=stream.cuda_stream)
@@ -222,7 +225,7 @@ def main():
         torch.cuda.synchronize()
         emd.emd_db_check_device_errors(handle)
         emd.emd_db_profile_reset(handle)
-        emd.emd_db_set_profiling(handle, True)
+        emd.emd_db_set_profiling(handle, profile)
         launches0 = emd.emd_db_profile_get(handle)["total_launches"]
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -255,33 +258,63 @@ def main():
     queries_done = args.batch * args.steps * world
     value = queries_done / (total_ms / 1e3)
 
+    # per-kernel durations: the same batches on one lane (no overlap between queries), so
+    # each phase's events bracket its own kernels only
+    db_serial = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
+                                  emd.emd_db_options_default(precision=args.precision, lanes=1, **opts))
+    steps_serial = min(args.steps, 5)
+    step_s, total_s, prof, _, _ = run_steps(db_serial, steps_serial, profile=True)
+    emd.emd_db_destroy(db_serial)
+
+    # the plain FP32 path (FP32 FFMA distance tiles) on the same batches
+    plain, res_p = None, None
+    if args.precision != "fp32":
+        db_plain = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
+                                     emd.emd_db_options_default(precision="fp32", **opts))
+        steps_plain = min(args.steps, 5)
+        step_p, total_p, prof_p, _, res_p = run_steps(db_plain, steps_plain, keep=1)
+        emd.emd_db_destroy(db_plain)
+        plain = {"value": args.batch * steps_plain * world / (total_p / 1e3), "unit": UNIT,
+                 "ms_per_step": total_p / steps_plain, "steps": steps_plain,
+                 "top16_identical_to_main": bool(torch.equal(res_p[0][1], results[0][1]))}
+
     # the same batches with the reverse pass over every document (no pruning)
     db_all = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
-                               emd.emd_db_options_default(prune_topk=0, **opts))
+                               emd.emd_db_options_default(prune_topk=0, precision=args.precision, **opts))
     steps_all = min(args.steps, 5)
     step_all, total_all, prof_all, _, res_all = run_steps(db_all, steps_all, keep=1)
     emd.emd_db_destroy(db_all)
     same_as_pruned = bool(torch.equal(res_all[0][1], results[0][1]))
     unpruned = {"value": args.batch * steps_all * world / (total_all / 1e3), "unit": UNIT,
                 "ms_per_step": total_all / steps_all, "steps": steps_all,
-                "phases_ms_per_step": {p: prof_all["ms"][p] / steps_all for p in
-                                       ("stage", "distance", "table", "fwd", "rev", "topk")},
                 "top16_identical_to_pruned": same_as_pruned}
 
     # per-phase achieved figures over the timed region
-    timed = dev_batches[args.warmup:]
+    timed = dev_batches[args.warmup:args.warmup + steps_serial]
     sum_h = sum(int(b[4].sum()) for b in timed)
-    nq = args.batch * args.steps
+    nq = args.batch * steps_serial
     m, vu, nnz, n = w.m, info["v_used"], info["nnz"], info["n_docs"]
     pk = peaks()
     alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12  # TFLOP/s
     phase = prof["ms"]
     dist_flops = 2.0 * vu * m * sum_h
+    kpad = -(-m // 64) * 64
+    # tensor-core form: the packed FP16 hi+lo panels of the used vocabulary are streamed
+    # once per query (2 x 2 bytes per element); that stream bounds the kernel
+    tc_bytes = nq * (4.0 * (-(-vu // 128) * 128) * kpad)
     fwd_bytes = nq * (8.0 * nnz + 4.0 * (n + 1) + 4.0 * n)
+    if args.precision == "fp32":
+        dist_row = {"bound": "alu", "achieved": dist_flops / (phase["distance"] / 1e3) / 1e12,
+                    "peak": alu_peak, "unit": "TFLOP/s", "kernel_file": "k_phase1.cu",
+                    "per_launch": dist_flops / nq,
+                    "peak_source": "FP32 SIMT: 152 SMs x 128 lanes x 2 FLOP x max SM clock"}
+    else:
+        dist_row = {"bound": "hbm", "achieved": tc_bytes / (phase["distance"] / 1e3) / 1e9,
+                    "peak": pk["hbm_gbs"], "unit": "GB/s", "kernel_file": "k_tc_dist.cu",
+                    "per_launch": tc_bytes / nq,
+                    "peak_source": f"{pk['source']} HBM copy; operand stream = 4 B x padded used rows x K"}
     rows = {
-        "distance": {"bound": "alu", "achieved": dist_flops / (phase["distance"] / 1e3) / 1e12,
-                     "peak": alu_peak, "unit": "TFLOP/s", "kernel_file": "k_phase1.cu",
-                     "per_launch": dist_flops / nq},
+        "distance": dist_row,
         "fwd": {"bound": "hbm", "achieved": fwd_bytes / (phase["fwd"] / 1e3) / 1e9,
                 "peak": pk["hbm_gbs"], "unit": "GB/s", "kernel_file": "k_sparse.cu",
                 "per_launch": fwd_bytes / nq},
@@ -291,24 +324,23 @@ def main():
         r = rows[dominant]
         roofline = {"bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"], "unit": r["unit"],
                     "frac": r["achieved"] / r["peak"], "kernel": dominant,
-                    "peak_source": ("FP32 SIMT: 152 SMs x 128 lanes x 2 FLOP x max SM clock"
-                                    if r["bound"] == "alu" else f"{pk['source']} HBM copy"),
+                    "peak_source": r.get("peak_source", f"{pk['source']} HBM copy"),
                     "traffic": recorded_traffic(r["kernel_file"], dominant)}
     else:
         # the reverse pass gathers D rows from L2 and the table kernel reads L2-resident D:
         # neither has an HBM or ALU roofline claim
         roofline = {"bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": None,
                     "kernel": dominant, "traffic": None, "note": f"{dominant} dominates (L2-bound)"}
-    phases = {p: {"ms_per_step": phase[p] / args.steps, "launches": prof["launches"][p]}
+    phases = {p: {"ms_per_step": phase[p] / steps_serial, "launches": prof["launches"][p]}
               for p in ("stage", "distance", "table", "fwd", "rev", "topk")}
+    phases["measured_on"] = f"{steps_serial} steps on one lane (serial), profiling events"
+    phases["serial_ms_per_step"] = total_s / steps_serial
     phases["pruned_queries"] = prof["pruned_queries"]
     phases["prune_fallbacks"] = prof["prune_fallbacks"]
-    phases["distance"]["tflops"] = rows["distance"]["achieved"]
+    phases["distance"]["algorithmic_tflops"] = dist_flops / (phase["distance"] / 1e3) / 1e12
+    if args.precision != "fp32":
+        phases["distance"]["tensor_tflops_executed"] = 3 * 2.0 * nq * (-(-vu // 128) * 128) * kpad * 128 / (phase["distance"] / 1e3) / 1e12
     phases["fwd"]["gbs"] = rows["fwd"]["achieved"]
-    if prof_all["ms"]["rev"]:
-        unpruned["rev_pair_evals_per_s"] = (float(nnz) * sum(int(b[4].sum()) for b in dev_batches[args.warmup:args.warmup + steps_all])
-                                            / (prof_all["ms"]["rev"] / 1e3))
-
     # end to end through the public host API, pinned host buffers
     e2e_steps = args.e2e_steps or args.steps
     host_in = []
@@ -352,17 +384,24 @@ def main():
         g = gi.cpu().numpy()
         recall = {"top16_recall": float(np.mean([recall_at(g[i], want[i], K) for i in range(len(want))])),
                   "queries": len(want), "vs": "FP64 oracle"}
+        if plain is not None:
+            gp = res_p[0][1].cpu().numpy()
+            plain["top16_recall"] = float(np.mean([recall_at(gp[i], want[i], K) for i in range(len(want))]))
 
     lat = np.array(step_ms) / args.batch
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f16x3-split/f32-acc",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "measure": f"LC-ACT k={args.k} (Alg. 3 top-k width)",
                        "direction": "max(fwd, rev); exact pruned top-K (reverse pass on the 63 best forward candidates, certified)",
                        "top_k": K, "batch_queries": args.batch,
-                       "precision": "fp32 plain", "parallelism": f"replicas x{world}, queries sharded",
+                       "precision": {"fp32": "fp32 plain (FFMA tiles)",
+                                     "fp32_tc": "FP32-grade on tcgen05: FP16 hi+lo split, 3 products, FP32 TMEM accumulators"}[args.precision],
+                       "parallelism": f"replicas x{world}, queries sharded",
                        "l2": "flushed between steps (256 MB write outside the timed events)",
                        "v_used": vu, "nnz": nnz, "mean_h_q_timed": sum_h / nq},
             "roofline": roofline,
@@ -375,6 +414,7 @@ def main():
             "phases": phases,
             "recall": recall,
             "unpruned_all_docs": unpruned,
+            "plain_fp32": plain,
         }
         print(json.dumps(line))
     emd.emd_db_destroy(db)

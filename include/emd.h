@@ -76,6 +76,9 @@ typedef struct {
     int32_t max_table_k;     /* largest forward top-k table width; ICT needs h_q <= this (default 64) */
     int32_t max_batch;       /* queries staged per device pass (default 64) */
     int32_t prune_topk;      /* 1 (default): exact pruned max-direction top-K for K <= 16 */
+    int32_t lanes;           /* concurrent per-query pipelines, each with its own stream and
+                                workspace (default 4, 1..16); a batch's queries are spread over
+                                them and joined back into the caller's stream */
 } emd_db_options;
 
 typedef struct {

@@ -41,7 +41,7 @@ class emd_db_options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("rerank_margin", ctypes.c_int32), ("max_query_h", ctypes.c_int32),
                 ("max_table_k", ctypes.c_int32), ("max_batch", ctypes.c_int32),
-                ("prune_topk", ctypes.c_int32)]
+                ("prune_topk", ctypes.c_int32), ("lanes", ctypes.c_int32)]
 
 
 class emd_db_info(ctypes.Structure):
@@ -150,7 +150,10 @@ def emd_last_error() -> str:
 def emd_db_options_default(**over) -> emd_db_options:
     o = emd_db_options()
     load().emd_db_options_default(ctypes.byref(o))
+    names = {f[0] for f in emd_db_options._fields_}
     for k, v in over.items():
+        if k not in names:
+            raise TypeError(f"unknown option {k!r}")
         setattr(o, k, _code(PRECISIONS, v) if k == "precision" else int(v))
     return o
 

@@ -52,9 +52,38 @@ emd_status set_error(emd_status st, const char* msg)
 void clear_error() { g_err.clear(); }
 }  // namespace emd
 
+struct emd_db;
+
+namespace {
+
+// One concurrent per-query pipeline: its stream and the workspace a query needs from
+// Phase 1 to its distances (or its pruned top-K).
+struct Lane {
+    cudaStream_t st = nullptr;
+    cudaEvent_t done = nullptr;
+    float* Q = nullptr;          // qrows_max x ldm
+    float* qnorm = nullptr;      // qrows_max
+    __half* q_hi = nullptr;      // npad_max x kpad (tensor-core precision)
+    __half* q_lo = nullptr;
+    float* q_scale = nullptr;    // npad_max
+    float* D = nullptr;          // v_used x ldd (ldd <= ldd_max)
+    float2* tab = nullptr;       // v_used x max_table_k
+    float* t_fwd = nullptr;      // n
+    float* t_rev = nullptr;      // n
+    int64_t* sel_idx = nullptr;  // kPruneMaxK forward top-K
+    float* sel_val = nullptr;
+    int64_t* cand_idx = nullptr; // kPruneCap candidates
+    float* cand_sym = nullptr;   // 2 x kPruneCap
+    int* cand_count = nullptr;
+    unsigned long long* scratch = nullptr;  // kTopkScratchRow selection partials
+};
+
+}  // namespace
+
 struct emd_db {
     int dev = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;  // host-buffer entry points run here
+    cudaEvent_t fork = nullptr;
     emd_db_options opt{};
     int64_t v = 0, v_used = 0, n = 0, nnz = 0;
     int m = 0, ldm = 0;
@@ -69,37 +98,24 @@ struct emd_db {
     int32_t* row_ptr = nullptr;  // n + 1
     int32_t* col = nullptr;      // nnz, renumbered into the used vocabulary
     float* val = nullptr;        // nnz
-
-    // workspace
-    int ldd_max = 0, qrows_max = 0;
-    float* Q = nullptr;          // qrows_max x ldm
-    float* qnorm = nullptr;      // qrows_max
-    float* D = nullptr;          // v_used x ldd (ldd <= ldd_max)
-    float2* tab = nullptr;       // v_used x max_table_k
-    int32_t* tab_s = nullptr;    // v_used x max_table_k
-    float* t_fwd = nullptr;      // n
-    float* t_rev = nullptr;      // n
-    unsigned long long* topk_scratch = nullptr;  // max_batch x kTopkScratchRow
-    int64_t* sel_idx = nullptr;    // kPruneMaxK: forward top-K of the query being pruned
-    float* sel_val = nullptr;      // kPruneMaxK
-    int64_t* cand_idx = nullptr;   // kPruneCap candidate documents
-    float* cand_sym = nullptr;     // 2 x kPruneCap: symmetric values, then reverse values
-    int* cand_count = nullptr;     // 1
-    int* cand_ok = nullptr;        // max_batch certification flags
     int* err = nullptr;
 
-    // tensor-core operands (precision EMD_PREC_FP32_TC)
+    // tensor-core operands of the used vocabulary (precision EMD_PREC_FP32_TC)
     bool tc = false;
     int kpad = 0;
     int64_t mpad = 0;
-    __half* a_hi = nullptr;      // mpad x kpad packed panels of the used vocabulary
+    __half* a_hi = nullptr;      // mpad x kpad packed panels
     __half* a_lo = nullptr;
     float* a_scale = nullptr;    // mpad
-    __half* q_hi = nullptr;      // npad_max x kpad packed panels of the query
-    __half* q_lo = nullptr;
-    float* q_scale = nullptr;    // npad_max
 
-    // staging for the host-buffer entry points
+    // per-lane workspace
+    int ldd_max = 0, qrows_max = 0;
+    std::vector<Lane> lanes;
+    int32_t* tab_s = nullptr;    // v_used x max_table_k (inspection entry point only)
+
+    // batch workspace (shared by the lanes, one row per query of a batch)
+    unsigned long long* topk_scratch = nullptr;  // max_batch x kTopkScratchRow
+    int* cand_ok = nullptr;        // max_batch certification flags
     int64_t stage_bins = 0;
     int32_t* stage_idx = nullptr;
     float* stage_w = nullptr;
@@ -144,10 +160,15 @@ void release(emd_db* db)
 {
     if (!db) return;
     cudaSetDevice(db->dev);
-    if (db->stream) cudaStreamSynchronize(db->stream);
+    cudaDeviceSynchronize();
     for (void* p : db->allocs) cudaFree(p);
     for (auto& r : db->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : db->pool) cudaEventDestroy(e);
+    for (auto& L : db->lanes) {
+        if (L.done) cudaEventDestroy(L.done);
+        if (L.st) cudaStreamDestroy(L.st);
+    }
+    if (db->fork) cudaEventDestroy(db->fork);
     if (db->stream) cudaStreamDestroy(db->stream);
     delete db;
 }
@@ -165,6 +186,8 @@ cudaEvent_t take_event(emd_db* db)
 }
 
 // Brackets the kernels of one phase with events (when profiling) and counts launches.
+// With several lanes the phases of different queries overlap, so phase sums can exceed
+// the wall time of a batch.
 struct Phase {
     emd_db* db;
     int ph;
@@ -254,63 +277,60 @@ emd_status check_query_values(const emd_db* db, const emd_queries* q)
     return EMD_OK;
 }
 
-emd_status run_phase1(emd_db* db, const int32_t* qidx, int h, cudaStream_t st);
-
-// One query through Phase 1, the forward and/or reverse pass; out_t (n floats) receives
-// the distances.
-emd_status run_query(emd_db* db, const int32_t* qidx, const float* qw, int h, int meas, int k,
-                     int dir, float* out_t, cudaStream_t st)
-{
-    emd_status s0 = run_phase1(db, qidx, h, st);
-    if (s0 != EMD_OK) return s0;
-    const int ldd = (int)round_up(h, 32);
-    float* target = out_t;
-    if (dir != EMD_DIR_REV) {
-        const int tk = table_width(meas, k, h);
-        {
-            Phase p(db, 2, 1, st);
-            EMD_CUDA(launch_table(db->D, ldd, db->v_used, h, tk, qw, db->tab, nullptr, st), "top-k table");
-        }
-        Phase p(db, 3, 1, st);
-        EMD_CUDA(launch_fwd(meas, db->row_ptr, db->col, db->val, db->n, db->tab, tk, tk,
-                            dir == EMD_DIR_FWD ? target : db->t_fwd, st), "forward pass");
-    }
-    if (dir != EMD_DIR_FWD) {
-        Phase p(db, 4, 1, st);
-        EMD_CUDA(launch_rev(meas, k, db->row_ptr, db->col, db->val, db->n, db->D, ldd, h, qw,
-                            db->t_fwd, dir == EMD_DIR_REV ? target : db->t_rev,
-                            dir == EMD_DIR_MAX ? target : nullptr, nullptr, st), "reverse pass");
-    }
-    return EMD_OK;
-}
-
-// Phase 1 (distances, or the cost-matrix gather) for one query into db->D.
-emd_status run_phase1(emd_db* db, const int32_t* qidx, int h, cudaStream_t st)
+// Phase 1 (distances, or the cost-matrix gather) for one query into the lane's D.
+emd_status run_phase1(emd_db* db, Lane& L, const int32_t* qidx, int h, cudaStream_t st)
 {
     const int ldd = (int)round_up(h, 32);
     const int qrows = (int)round_up(ldd, kDistBN);
     if (db->cost_mode) {
         Phase p(db, 1, 1, st);
-        EMD_CUDA(launch_dist_gather(db->cost, db->v, db->used_ids, db->v_used, qidx, h, db->D, ldd,
+        EMD_CUDA(launch_dist_gather(db->cost, db->v, db->used_ids, db->v_used, qidx, h, L.D, ldd,
                                     db->err, st), "distance gather");
         return EMD_OK;
     }
     {
         Phase p(db, 0, db->tc ? 2 : 1, st);
-        EMD_CUDA(launch_gather_rows(db->emb, db->v, db->ldm, db->m, qidx, h, qrows, db->Q, db->qnorm,
+        EMD_CUDA(launch_gather_rows(db->emb, db->v, db->ldm, db->m, qidx, h, qrows, L.Q, L.qnorm,
                                     db->err, st), "query gather");
         if (db->tc)
-            EMD_CUDA(launch_pack_f16(db->Q, db->ldm, db->m, h, round_up(h, 128), db->kpad, db->q_hi, db->q_lo,
-                                     db->q_scale, st), "query pack");
+            EMD_CUDA(launch_pack_f16(L.Q, db->ldm, db->m, h, round_up(h, 128), db->kpad, L.q_hi, L.q_lo,
+                                     L.q_scale, st), "query pack");
     }
     Phase p(db, 1, 1, st);
     if (db->tc)
         EMD_CUDA(launch_tc_dist(true, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used, db->used_ids,
-                                db->v_used, db->q_hi, db->q_lo, round_up(h, 128), db->q_scale, db->qnorm, qidx,
-                                h, db->kpad, db->D, ldd, db->err, st), "distance matrix (tensor cores)");
+                                db->v_used, L.q_hi, L.q_lo, round_up(h, 128), L.q_scale, L.qnorm, qidx,
+                                h, db->kpad, L.D, ldd, db->err, st), "distance matrix (tensor cores)");
     else
-        EMD_CUDA(launch_dist_fp32(db->emb_used, db->v_used, db->ldm, db->norm_used, db->used_ids, db->Q, h,
-                                  db->ldm, db->qnorm, qidx, db->m, db->D, ldd, st), "distance matrix");
+        EMD_CUDA(launch_dist_fp32(db->emb_used, db->v_used, db->ldm, db->norm_used, db->used_ids, L.Q, h,
+                                  db->ldm, L.qnorm, qidx, db->m, L.D, ldd, st), "distance matrix");
+    return EMD_OK;
+}
+
+// One query through Phase 1, the forward and/or reverse pass; out_t (n floats) receives
+// the distances.
+emd_status run_query(emd_db* db, Lane& L, const int32_t* qidx, const float* qw, int h, int meas, int k,
+                     int dir, float* out_t, cudaStream_t st)
+{
+    emd_status s0 = run_phase1(db, L, qidx, h, st);
+    if (s0 != EMD_OK) return s0;
+    const int ldd = (int)round_up(h, 32);
+    if (dir != EMD_DIR_REV) {
+        const int tk = table_width(meas, k, h);
+        {
+            Phase p(db, 2, 1, st);
+            EMD_CUDA(launch_table(L.D, ldd, db->v_used, h, tk, qw, L.tab, nullptr, st), "top-k table");
+        }
+        Phase p(db, 3, 1, st);
+        EMD_CUDA(launch_fwd(meas, db->row_ptr, db->col, db->val, db->n, L.tab, tk, tk,
+                            dir == EMD_DIR_FWD ? out_t : L.t_fwd, st), "forward pass");
+    }
+    if (dir != EMD_DIR_FWD) {
+        Phase p(db, 4, 1, st);
+        EMD_CUDA(launch_rev(meas, k, db->row_ptr, db->col, db->val, db->n, L.D, ldd, h, qw,
+                            L.t_fwd, dir == EMD_DIR_REV ? out_t : L.t_rev,
+                            dir == EMD_DIR_MAX ? out_t : nullptr, nullptr, st), "reverse pass");
+    }
     return EMD_OK;
 }
 
@@ -322,40 +342,33 @@ bool prunable(const emd_db* db, int meas, int k, int dir, int K)
 
 // Pruned symmetric top-K of one query (see emd_topk in include/emd.h): forward pass over
 // all documents, forward top-K, candidates within the margin, reverse pass on them, final
-// selection with the certification flag in cand_ok[slot].
-emd_status run_topk_pruned(emd_db* db, const int32_t* qidx, const float* qw, int h, int meas, int k,
-                           int K, int64_t slot, int64_t* out_idx, float* out_dist, cudaStream_t st)
+// selection with the certification flag in *ok.
+emd_status run_topk_pruned(emd_db* db, Lane& L, const int32_t* qidx, const float* qw, int h, int meas, int k,
+                           int K, int* ok, int64_t* out_idx, float* out_dist, cudaStream_t st)
 {
-    emd_status s = run_phase1(db, qidx, h, st);
+    emd_status s = run_phase1(db, L, qidx, h, st);
     if (s != EMD_OK) return s;
     const int ldd = (int)round_up(h, 32);
     const int tk = table_width(meas, k, h);
     {
         Phase p(db, 2, 1, st);
-        EMD_CUDA(launch_table(db->D, ldd, db->v_used, h, tk, qw, db->tab, nullptr, st), "top-k table");
+        EMD_CUDA(launch_table(L.D, ldd, db->v_used, h, tk, qw, L.tab, nullptr, st), "top-k table");
     }
     {
         Phase p(db, 3, 1, st);
-        EMD_CUDA(launch_fwd(meas, db->row_ptr, db->col, db->val, db->n, db->tab, tk, tk, db->t_fwd, st),
+        EMD_CUDA(launch_fwd(meas, db->row_ptr, db->col, db->val, db->n, L.tab, tk, tk, L.t_fwd, st),
                  "forward pass");
     }
     {
         Phase p(db, 5, topk_launch_count(db->n), st);
-        EMD_CUDA(launch_topk(db->t_fwd, db->n, K, db->topk_scratch, db->sel_idx, db->sel_val, st),
-                 "forward top-K");
+        EMD_CUDA(launch_topk(L.t_fwd, db->n, K, L.scratch, L.sel_idx, L.sel_val, st), "forward top-K");
     }
     Phase p(db, 4, 3, st);
-    EMD_CUDA(launch_prune(meas, k, db->row_ptr, db->col, db->val, db->n, db->D, ldd, h, qw, db->t_fwd,
-                          db->sel_idx, db->sel_val, K, db->cand_idx, db->cand_count, db->cand_sym, out_idx,
-                          out_dist, db->cand_ok + slot, st), "pruned reverse pass");
+    EMD_CUDA(launch_prune(meas, k, db->row_ptr, db->col, db->val, db->n, L.D, ldd, h, qw, L.t_fwd,
+                          L.sel_idx, L.sel_val, K, L.cand_idx, L.cand_count, L.cand_sym, out_idx,
+                          out_dist, ok, st), "pruned reverse pass");
     return EMD_OK;
 }
-
-// Queries i0..i1-1 of a batch through the pruned top-K path; queries whose answer is not
-// certified are recomputed over all documents (one synchronisation per batch).
-emd_status topk_batch_pruned(emd_db* db, const int64_t* rp, const int32_t* qidx, const float* qw,
-                             int64_t i0, int64_t i1, int meas, int k, int K, int64_t* out_idx,
-                             float* out_dist, cudaStream_t st);
 
 // Top-K of `rows` distance rows (row stride n) in one selection launch.
 emd_status select_topk(emd_db* db, const float* t, int64_t rows, int K, int64_t* out_idx,
@@ -366,17 +379,38 @@ emd_status select_topk(emd_db* db, const float* t, int64_t rows, int K, int64_t*
     return EMD_OK;
 }
 
-emd_status topk_batch_pruned(emd_db* db, const int64_t* rp, const int32_t* qidx, const float* qw,
-                             int64_t i0, int64_t i1, int meas, int k, int K, int64_t* out_idx,
-                             float* out_dist, cudaStream_t st)
+// Queries i0..i1-1 (at most max_batch) on the lanes, ordered after and joined back into
+// `st`.  qidx / qw point at query i0's bins (rp gives every query's offset).  With K > 0
+// the top-K goes to out_idx / out_dist (rows relative to i0); otherwise the distances go
+// to out_t (rows relative to i0, row stride n).  The pruned path reads its certification
+// flags once (synchronising `st`) and recomputes uncertified queries over all documents.
+emd_status run_batch(emd_db* db, const int64_t* rp, const int32_t* qidx, const float* qw, int64_t i0,
+                     int64_t i1, int meas, int k, int dir, int K, float* out_t, int64_t* out_idx,
+                     float* out_dist, cudaStream_t st)
 {
+    const bool pruned = K > 0 && prunable(db, meas, k, dir, K);
+    const int nl = (int)std::min<int64_t>((int64_t)db->lanes.size(), i1 - i0);
+    EMD_CUDA(cudaEventRecord(db->fork, st), "fork");
+    for (int l = 0; l < nl; ++l) EMD_CUDA(cudaStreamWaitEvent(db->lanes[l].st, db->fork, 0), "fork");
     for (int64_t i = i0; i < i1; ++i) {
+        Lane& L = db->lanes[(i - i0) % nl];
         const int64_t off = rp[i] - rp[i0];
         const int h = (int)(rp[i + 1] - rp[i]);
-        emd_status s = run_topk_pruned(db, qidx + off, qw + off, h, meas, k, K, i - i0,
-                                       out_idx + (i - i0) * K, out_dist + (i - i0) * K, st);
+        emd_status s;
+        if (pruned)
+            s = run_topk_pruned(db, L, qidx + off, qw + off, h, meas, k, K, db->cand_ok + (i - i0),
+                                out_idx + (i - i0) * K, out_dist + (i - i0) * K, L.st);
+        else
+            s = run_query(db, L, qidx + off, qw + off, h, meas, k, dir,
+                          (K > 0 ? db->stage_out : out_t) + (i - i0) * db->n, L.st);
         if (s != EMD_OK) return s;
     }
+    for (int l = 0; l < nl; ++l) {
+        EMD_CUDA(cudaEventRecord(db->lanes[l].done, db->lanes[l].st), "join");
+        EMD_CUDA(cudaStreamWaitEvent(st, db->lanes[l].done, 0), "join");
+    }
+    if (K > 0 && !pruned) return select_topk(db, db->stage_out, i1 - i0, K, out_idx, out_dist, st);
+    if (!pruned) return EMD_OK;
     std::vector<int> ok((size_t)(i1 - i0), 0);
     EMD_CUDA(cudaMemcpyAsync(ok.data(), db->cand_ok, (i1 - i0) * sizeof(int), cudaMemcpyDeviceToHost, st),
              "flag read");
@@ -387,7 +421,8 @@ emd_status topk_batch_pruned(emd_db* db, const int64_t* rp, const int32_t* qidx,
         ++db->prune_fallbacks;
         const int64_t off = rp[i] - rp[i0];
         const int h = (int)(rp[i + 1] - rp[i]);
-        emd_status s = run_query(db, qidx + off, qw + off, h, meas, k, EMD_DIR_MAX, db->stage_out, st);
+        emd_status s = run_query(db, db->lanes[0], qidx + off, qw + off, h, meas, k, EMD_DIR_MAX,
+                                 db->stage_out, st);
         if (s != EMD_OK) return s;
         s = select_topk(db, db->stage_out, 1, K, out_idx + (i - i0) * K, out_dist + (i - i0) * K, st);
         if (s != EMD_OK) return s;
@@ -428,23 +463,9 @@ emd_status host_batches(emd_db* db, const emd_queries* q, int meas, int k, int d
                                  cudaMemcpyHostToDevice, st), "query copy");
         EMD_CUDA(cudaMemcpyAsync(db->stage_w, q->w + base, bins * sizeof(float),
                                  cudaMemcpyHostToDevice, st), "query copy");
-        if (K > 0 && prunable(db, meas, k, dir, K)) {
-            emd_status s = topk_batch_pruned(db, q->row_ptr, db->stage_idx, db->stage_w, i0, i1, meas, k, K,
-                                             db->stage_oidx, db->stage_odist, st);
-            if (s != EMD_OK) return s;
-        } else {
-            for (int64_t i = i0; i < i1; ++i) {
-                const int64_t off = q->row_ptr[i] - base;
-                const int h = (int)(q->row_ptr[i + 1] - q->row_ptr[i]);
-                emd_status s = run_query(db, db->stage_idx + off, db->stage_w + off, h, meas, k, dir,
-                                         db->stage_out + (i - i0) * db->n, st);
-                if (s != EMD_OK) return s;
-            }
-            if (K > 0) {
-                emd_status s = select_topk(db, db->stage_out, i1 - i0, K, db->stage_oidx, db->stage_odist, st);
-                if (s != EMD_OK) return s;
-            }
-        }
+        emd_status s = run_batch(db, q->row_ptr, db->stage_idx, db->stage_w, i0, i1, meas, k, dir, K,
+                                 db->stage_out, db->stage_oidx, db->stage_odist, st);
+        if (s != EMD_OK) return s;
         if (K > 0) {
             EMD_CUDA(cudaMemcpyAsync(out_idx + i0 * K, db->stage_oidx, (i1 - i0) * K * sizeof(int64_t),
                                      cudaMemcpyDeviceToHost, st), "result copy");
@@ -475,6 +496,7 @@ void emd_db_options_default(emd_db_options* opt)
     opt->max_table_k = 64;
     opt->max_batch = 64;
     opt->prune_topk = 1;
+    opt->lanes = 4;
 }
 
 emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* cost_matrix,
@@ -496,7 +518,8 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
     if (opt.precision != EMD_PREC_FP32 && opt.precision != EMD_PREC_FP32_TC)
         return fail(EMD_ERR_UNSUPPORTED, "precision %d is not available in this build", (int)opt.precision);
     if (opt.max_query_h < 1 || opt.max_query_h > (1 << 16) || opt.max_table_k < 1 ||
-        opt.max_table_k > (1 << 16) || opt.max_batch < 1 || opt.max_batch > 4096)
+        opt.max_table_k > (1 << 16) || opt.max_batch < 1 || opt.max_batch > 4096 || opt.lanes < 1 ||
+        opt.lanes > 16)
         return fail(EMD_ERR_INVALID_ARG, "option out of range");
     if (row_ptr[0] != 0) return fail(EMD_ERR_INVALID_ARG, "row_ptr[0] != 0");
     const int64_t nnz = row_ptr[n_docs];
@@ -562,6 +585,12 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
 
     TRYC(cudaSetDevice(db->dev), "cudaSetDevice");
     TRYC(cudaStreamCreateWithFlags(&db->stream, cudaStreamNonBlocking), "stream");
+    TRYC(cudaEventCreateWithFlags(&db->fork, cudaEventDisableTiming), "event");
+    db->lanes.resize((size_t)opt.lanes);
+    for (auto& L : db->lanes) {
+        TRYC(cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking), "stream");
+        TRYC(cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming), "event");
+    }
     cudaStream_t st = db->stream;
 
     const int64_t vu = db->v_used;
@@ -593,19 +622,13 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
         db->total_launches += 1;
         db->launches[6] += 1;
         db->qrows_max = (int)round_up(round_up(opt.max_query_h, 32), kDistBN);
-        TRY(dalloc(db, &db->Q, (int64_t)db->qrows_max * ldm));
-        TRY(dalloc(db, &db->qnorm, db->qrows_max));
         if (opt.precision == EMD_PREC_FP32_TC) {
             db->tc = true;
             db->kpad = (int)round_up(m, 64);
             db->mpad = round_up(vu, 128);
-            const int64_t npad = round_up(opt.max_query_h, 128);
             TRY(dalloc(db, &db->a_hi, db->mpad * db->kpad));
             TRY(dalloc(db, &db->a_lo, db->mpad * db->kpad));
             TRY(dalloc(db, &db->a_scale, db->mpad));
-            TRY(dalloc(db, &db->q_hi, npad * db->kpad));
-            TRY(dalloc(db, &db->q_lo, npad * db->kpad));
-            TRY(dalloc(db, &db->q_scale, npad));
             TRYC(launch_pack_f16(db->emb_used, ldm, m, vu, db->mpad, db->kpad, db->a_hi, db->a_lo, db->a_scale, st),
                  "embedding pack");
             db->total_launches += 1;
@@ -614,17 +637,30 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
     }
 
     db->ldd_max = (int)round_up(opt.max_query_h, 32);
-    TRY(dalloc(db, &db->D, vu * db->ldd_max));
-    TRY(dalloc(db, &db->tab, vu * opt.max_table_k));
+    const int64_t npad = round_up(opt.max_query_h, 128);
+    for (auto& L : db->lanes) {
+        if (!db->cost_mode) {
+            TRY(dalloc(db, &L.Q, (int64_t)db->qrows_max * db->ldm));
+            TRY(dalloc(db, &L.qnorm, db->qrows_max));
+            if (db->tc) {
+                TRY(dalloc(db, &L.q_hi, npad * db->kpad));
+                TRY(dalloc(db, &L.q_lo, npad * db->kpad));
+                TRY(dalloc(db, &L.q_scale, npad));
+            }
+        }
+        TRY(dalloc(db, &L.D, vu * db->ldd_max));
+        TRY(dalloc(db, &L.tab, vu * opt.max_table_k));
+        TRY(dalloc(db, &L.t_fwd, n_docs));
+        TRY(dalloc(db, &L.t_rev, n_docs));
+        TRY(dalloc(db, &L.sel_idx, kPruneMaxK));
+        TRY(dalloc(db, &L.sel_val, kPruneMaxK));
+        TRY(dalloc(db, &L.cand_idx, kPruneCap));
+        TRY(dalloc(db, &L.cand_sym, 2 * kPruneCap));
+        TRY(dalloc(db, &L.cand_count, 1));
+        TRY(dalloc(db, &L.scratch, kTopkScratchRow));
+    }
     TRY(dalloc(db, &db->tab_s, vu * opt.max_table_k));
-    TRY(dalloc(db, &db->t_fwd, n_docs));
-    TRY(dalloc(db, &db->t_rev, n_docs));
     TRY(dalloc(db, &db->topk_scratch, (int64_t)opt.max_batch * kTopkScratchRow));
-    TRY(dalloc(db, &db->sel_idx, kPruneMaxK));
-    TRY(dalloc(db, &db->sel_val, kPruneMaxK));
-    TRY(dalloc(db, &db->cand_idx, kPruneCap));
-    TRY(dalloc(db, &db->cand_sym, 2 * kPruneCap));
-    TRY(dalloc(db, &db->cand_count, 1));
     TRY(dalloc(db, &db->cand_ok, opt.max_batch));
     db->stage_bins = (int64_t)opt.max_batch * opt.max_query_h;
     TRY(dalloc(db, &db->stage_idx, db->stage_bins));
@@ -702,10 +738,10 @@ emd_status emd_query_batch_device(emd_db* db, int64_t n_queries, const int64_t* 
     if (!q_idx_dev || !q_w_dev || !out_dist_dev) return fail(EMD_ERR_INVALID_ARG, "NULL device pointer");
     EMD_CUDA(cudaSetDevice(db->dev), "cudaSetDevice");
     cudaStream_t st = static_cast<cudaStream_t>(stream);  // NULL: the default stream
-    for (int64_t i = 0; i < n_queries; ++i) {
-        const int64_t off = q_row_ptr_host[i];
-        const int h = (int)(q_row_ptr_host[i + 1] - off);
-        s = run_query(db, q_idx_dev + off, q_w_dev + off, h, meas, k, dir, out_dist_dev + i * db->n, st);
+    for (int64_t i0 = 0; i0 < n_queries; i0 += db->opt.max_batch) {
+        const int64_t i1 = std::min<int64_t>(n_queries, i0 + db->opt.max_batch);
+        s = run_batch(db, q_row_ptr_host, q_idx_dev + q_row_ptr_host[i0], q_w_dev + q_row_ptr_host[i0], i0, i1,
+                      meas, k, dir, 0, out_dist_dev + i0 * db->n, nullptr, nullptr, st);
         if (s != EMD_OK) return s;
     }
     return EMD_OK;
@@ -730,20 +766,8 @@ emd_status emd_topk_device(emd_db* db, int64_t n_queries, const int64_t* q_row_p
     cudaStream_t st = static_cast<cudaStream_t>(stream);  // NULL: the default stream
     for (int64_t i0 = 0; i0 < n_queries; i0 += db->opt.max_batch) {
         const int64_t i1 = std::min<int64_t>(n_queries, i0 + db->opt.max_batch);
-        if (prunable(db, meas, k, dir, K)) {
-            s = topk_batch_pruned(db, q_row_ptr_host, q_idx_dev + q_row_ptr_host[i0], q_w_dev + q_row_ptr_host[i0],
-                                  i0, i1, meas, k, K, out_idx_dev + i0 * K, out_dist_dev + i0 * K, st);
-            if (s != EMD_OK) return s;
-            continue;
-        }
-        for (int64_t i = i0; i < i1; ++i) {
-            const int64_t off = q_row_ptr_host[i];
-            const int h = (int)(q_row_ptr_host[i + 1] - off);
-            s = run_query(db, q_idx_dev + off, q_w_dev + off, h, meas, k, dir,
-                          db->stage_out + (i - i0) * db->n, st);
-            if (s != EMD_OK) return s;
-        }
-        s = select_topk(db, db->stage_out, i1 - i0, K, out_idx_dev + i0 * K, out_dist_dev + i0 * K, st);
+        s = run_batch(db, q_row_ptr_host, q_idx_dev + q_row_ptr_host[i0], q_w_dev + q_row_ptr_host[i0], i0, i1,
+                      meas, k, dir, K, nullptr, out_idx_dev + i0 * K, out_dist_dev + i0 * K, st);
         if (s != EMD_OK) return s;
     }
     return EMD_OK;
@@ -771,30 +795,19 @@ emd_status emd_phase1_table(emd_db* db, const int32_t* q_idx, const float* q_w, 
     if (s != EMD_OK) return s;
     EMD_CUDA(cudaSetDevice(db->dev), "cudaSetDevice");
     cudaStream_t st = db->stream;
+    Lane& L = db->lanes[0];
     EMD_CUDA(cudaMemcpyAsync(db->stage_idx, q_idx, h_q * sizeof(int32_t), cudaMemcpyHostToDevice, st), "copy");
     EMD_CUDA(cudaMemcpyAsync(db->stage_w, q_w, h_q * sizeof(float), cudaMemcpyHostToDevice, st), "copy");
     const int ldd = (int)round_up(h_q, 32);
-    if (db->cost_mode) {
-        Phase p(db, 1, 1, st);
-        EMD_CUDA(launch_dist_gather(db->cost, db->v, db->used_ids, db->v_used, db->stage_idx, h_q, db->D,
-                                    ldd, db->err, st), "distance gather");
-    } else {
-        {
-            Phase p(db, 0, 1, st);
-            EMD_CUDA(launch_gather_rows(db->emb, db->v, db->ldm, db->m, db->stage_idx, h_q,
-                                        round_up(ldd, kDistBN), db->Q, db->qnorm, db->err, st), "gather");
-        }
-        Phase p(db, 1, 1, st);
-        EMD_CUDA(launch_dist_fp32(db->emb_used, db->v_used, db->ldm, db->norm_used, db->used_ids, db->Q,
-                                  h_q, db->ldm, db->qnorm, db->stage_idx, db->m, db->D, ldd, st), "distance");
-    }
+    s = run_phase1(db, L, db->stage_idx, h_q, st);
+    if (s != EMD_OK) return s;
     {
         Phase p(db, 2, 1, st);
-        EMD_CUDA(launch_table(db->D, ldd, db->v_used, h_q, k, db->stage_w, db->tab, db->tab_s, st), "table");
+        EMD_CUDA(launch_table(L.D, ldd, db->v_used, h_q, k, db->stage_w, L.tab, db->tab_s, st), "table");
     }
     const int64_t cnt = db->v_used * k;
     std::vector<float2> tz((size_t)cnt);
-    EMD_CUDA(cudaMemcpyAsync(tz.data(), db->tab, cnt * sizeof(float2), cudaMemcpyDeviceToHost, st), "copy");
+    EMD_CUDA(cudaMemcpyAsync(tz.data(), L.tab, cnt * sizeof(float2), cudaMemcpyDeviceToHost, st), "copy");
     EMD_CUDA(cudaMemcpyAsync(s_out, db->tab_s, cnt * sizeof(int32_t), cudaMemcpyDeviceToHost, st), "copy");
     if (used_ids)
         EMD_CUDA(cudaMemcpyAsync(used_ids, db->used_ids, db->v_used * sizeof(int32_t), cudaMemcpyDeviceToHost, st), "copy");

@@ -35,10 +35,10 @@ constexpr int kTopkThreads = 128;
 constexpr int kTopkMaxBlocks = 64;
 constexpr int64_t kTopkScratchRow = (int64_t)kTopkMaxBlocks * kMaxTopK;  // keys per selection row
 
-// Blocks per row of the top-K selection (one block per 8192 values, at most 64).
+// Blocks per row of the top-K selection (one block per 2048 values, at most 64).
 __host__ __device__ inline int topk_blocks(int64_t n)
 {
-    int64_t b = n / 8192;
+    int64_t b = n / 2048;
     return (int)(b < 1 ? 1 : (b > kTopkMaxBlocks ? kTopkMaxBlocks : b));
 }
 

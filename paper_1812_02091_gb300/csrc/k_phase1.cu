@@ -3,7 +3,7 @@
 //
 // This file holds the plain FP32 path: a register-tiled SIMT distance kernel (FP32 FFMA,
 // norm expansion ||a||^2 + ||b||^2 - 2<a,b>), the cost-matrix gather of the image
-// workloads, and a warp-per-row top-k selection.
+// workloads, and the per-row top-k selection shared by every precision.
 #include <math.h>
 
 #include "emd_internal.cuh"
@@ -194,58 +194,50 @@ __global__ void k_dist_gather(const float* __restrict__ cost, int64_t v,
 
 // ------------------------------------------------------------------ top-k table
 //
-// One warp per vocabulary row.  Each lane keeps a sorted register list of its KT
-// smallest (d, j) over the columns it visits (j = lane, lane+32, ...; increasing j, and
-// strict '<' keeps the earlier column first on equal d).  The warp then pops the k
-// smallest heads in (d, j) order; every member of the row's top-k is inside its lane's
-// top-KT because k <= KT.
+// One thread per vocabulary row: the row of D is read with 16-byte loads in column order
+// and kept in a branch-free sorted register list of the KT smallest (d, j); strict '<'
+// keeps the earlier column first on equal d, the order the definition uses.
 
 template <int KT>
-__global__ void k_table(const float* __restrict__ D, int ldd, int64_t M, int h, int k,
-                        const float* __restrict__ q_w, float2* __restrict__ tab,
-                        int32_t* __restrict__ tab_s)
+__device__ __forceinline__ void insert_dj(float (&z)[KT], int (&s)[KT], float d, int j)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    bool p[KT];
+#pragma unroll
+    for (int l = 0; l < KT; ++l) p[l] = d < z[l];
+#pragma unroll
+    for (int l = KT - 1; l > 0; --l) {
+        z[l] = p[l - 1] ? z[l - 1] : (p[l] ? d : z[l]);
+        s[l] = p[l - 1] ? s[l - 1] : (p[l] ? j : s[l]);
+    }
+    z[0] = p[0] ? d : z[0];
+    s[0] = p[0] ? j : s[0];
+}
+
+template <int KT>
+__global__ void __launch_bounds__(128)
+k_table(const float* __restrict__ D, int ldd, int64_t M, int h, int k, const float* __restrict__ q_w,
+        float2* __restrict__ tab, int32_t* __restrict__ tab_s)
+{
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= M) return;
     const float* Dr = D + row * ldd;
     float z[KT];
     int s[KT];
 #pragma unroll
     for (int l = 0; l < KT; ++l) { z[l] = INFINITY; s[l] = INT32_MAX; }
-    for (int j = lane; j < h; j += 32) {
-        float d = Dr[j];
-        if (d < z[KT - 1]) {
-            z[KT - 1] = d;
-            s[KT - 1] = j;
-#pragma unroll
-            for (int l = KT - 1; l > 0; --l) {
-                if (z[l] < z[l - 1]) {
-                    float tz = z[l]; z[l] = z[l - 1]; z[l - 1] = tz;
-                    int ts = s[l]; s[l] = s[l - 1]; s[l - 1] = ts;
-                }
-            }
-        }
+    for (int j = 0; j < h; j += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(Dr + j);  // ldd % 32 == 0, padding +inf
+        insert_dj<KT>(z, s, v.x, j);
+        if (j + 1 < h) insert_dj<KT>(z, s, v.y, j + 1);
+        if (j + 2 < h) insert_dj<KT>(z, s, v.z, j + 2);
+        if (j + 3 < h) insert_dj<KT>(z, s, v.w, j + 3);
     }
-    for (int l = 0; l < k; ++l) {
-        float bz = z[0];
-        int bs = s[0];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            float oz = __shfl_xor_sync(0xffffffffu, bz, o);
-            int os = __shfl_xor_sync(0xffffffffu, bs, o);
-            if (oz < bz || (oz == bz && os < bs)) { bz = oz; bs = os; }
-        }
-        if (bs != INT32_MAX && s[0] == bs) {  // the owning lane pops its head
-#pragma unroll
-            for (int t = 0; t < KT - 1; ++t) { z[t] = z[t + 1]; s[t] = s[t + 1]; }
-            z[KT - 1] = INFINITY;
-            s[KT - 1] = INT32_MAX;
-        }
-        if (lane == 0) {
-            const bool valid = bs != INT32_MAX;
-            tab[row * k + l] = make_float2(valid ? bz : INFINITY, valid ? q_w[bs] : 0.f);
-            if (tab_s) tab_s[row * k + l] = valid ? bs : -1;
+    for (int l = 0; l < KT; ++l) {
+        if (l < k) {
+            const bool valid = s[l] != INT32_MAX;
+            tab[row * k + l] = make_float2(valid ? z[l] : INFINITY, valid ? q_w[s[l]] : 0.f);
+            if (tab_s) tab_s[row * k + l] = valid ? s[l] : -1;
         }
     }
 }
@@ -323,14 +315,17 @@ cudaError_t launch_table(const float* D, int ldd, int64_t M, int h, int k, const
                          float2* tab, int32_t* tab_s, cudaStream_t st)
 {
     if (M <= 0) return cudaSuccess;
-    const int warps = 8;
-    dim3 grid((unsigned)((M + warps - 1) / warps));
-    if (k <= 1) k_table<1><<<grid, warps * 32, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
-    else if (k <= 2) k_table<2><<<grid, warps * 32, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
-    else if (k <= 4) k_table<4><<<grid, warps * 32, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
-    else if (k <= 8) k_table<8><<<grid, warps * 32, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
-    else if (k <= 16) k_table<16><<<grid, warps * 32, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
-    else k_table_generic<<<grid, warps * 32, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
+    const dim3 tgrid((unsigned)((M + 127) / 128));
+    if (k <= 1) k_table<1><<<tgrid, 128, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
+    else if (k <= 2) k_table<2><<<tgrid, 128, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
+    else if (k <= 4) k_table<4><<<tgrid, 128, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
+    else if (k <= 8) k_table<8><<<tgrid, 128, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
+    else if (k <= 16) k_table<16><<<tgrid, 128, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
+    else {
+        const int warps = 8;
+        dim3 grid((unsigned)((M + warps - 1) / warps));
+        k_table_generic<<<grid, warps * 32, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
+    }
     return cudaGetLastError();
 }
 

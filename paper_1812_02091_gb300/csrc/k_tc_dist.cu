@@ -15,12 +15,12 @@
 // therefore one contiguous block and moves with one 1-D bulk copy (cp.async.bulk, the TMA
 // engine) completing on an mbarrier.
 //
-// Roles (192 threads): warp 0 lane 0 issues the copies into a ring of stages; warp 1
-// allocates TMEM and its lane 0 issues tcgen05.mma (M = 128 rows of V, N <= 128 query
-// columns, K = 16 per instruction) and tcgen05.commit; warps 2..5 wait for the final
-// commit, read their TMEM lane quarter with tcgen05.ld and write
-// d = sqrt(max(|v|^2 + |q|^2 - 2 v.q, 0)), exactly 0 for identical vocabulary ids.
-// Every wait is bounded in time; a timeout latches ERR_TIMEOUT and the block tears down.
+// Roles (320 threads, one persistent CTA per SM): warp 0 lane 0 issues the copies into a
+// ring of stages; warp 1 allocates TMEM and its lane 0 issues tcgen05.mma (M = 128 rows of
+// V, N <= 128 query columns, K = 16 per instruction) and tcgen05.commit; warps 2..9 read
+// their TMEM lane quarter with tcgen05.ld and write d = sqrt(max(|v|^2 + |q|^2 - 2 v.q, 0)),
+// exactly 0 for identical vocabulary ids.  Every wait is bounded in time; a timeout
+// latches ERR_TIMEOUT, raises a block-wide abort flag and the block tears down.
 #include <cuda_fp16.h>
 #include <math.h>
 
@@ -33,7 +33,7 @@ namespace {
 
 constexpr int TC_BM = 128;          // rows per tile = TMEM lanes
 constexpr int TC_BN = 128;          // largest column tile
-constexpr int TC_THREADS = 192;
+constexpr int TC_THREADS = 320;  // warp 0 copies, warp 1 MMA, warps 2..9 epilogue
 constexpr uint32_t TC_A_BYTES = TC_BM * 128;  // one 64-wide K chunk of 128 rows
 constexpr uint32_t TC_B_BYTES = TC_BN * 128;
 constexpr uint64_t TC_TIMEOUT_NS = 2000000000ull;
@@ -162,6 +162,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Persistent form: each CTA (one per SM) walks tiles t = blockIdx.x, += gridDim.x in
+// column-tile-major order (t -> column tile t / m_tiles, row tile t % m_tiles), so a CTA's
+// consecutive tiles nearly always share their query columns.  The query panel (all K
+// chunks of the tile's columns, hi and lo) is loaded once into shared memory and reloaded
+// only when the column tile changes; the vocabulary panels stream through a ring of
+// `stages` stages.  Every SM reading the same small query panel for every tile would
+// otherwise concentrate the L2 traffic on a few slices.  The accumulators alternate
+// between two TMEM buffers, so the MMA warp fills one while the eight epilogue warps drain
+// the other (two warps per TMEM lane quarter, each taking half of the columns).
 template <bool SPLIT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_tc_dist(const __half* __restrict__ A_hi, const __half* __restrict__ A_lo, int64_t Mpad,
@@ -170,27 +184,40 @@ k_tc_dist(const __half* __restrict__ A_hi, const __half* __restrict__ A_lo, int6
           const float* __restrict__ b_scale, const float* __restrict__ b_norm, const int32_t* __restrict__ b_ids,
           int N, int KC, int stages, float* __restrict__ D, int ldd, int* __restrict__ err)
 {
-    constexpr uint32_t kStage = SPLIT ? 2 * (TC_A_BYTES + TC_B_BYTES) : (TC_A_BYTES + TC_B_BYTES);
-    constexpr uint32_t kCols = SPLIT ? 256 : 128;  // TMEM columns: accumulator 0 at 0, 1 at 128
+    constexpr int kParts = SPLIT ? 2 : 1;
+    constexpr uint32_t kStage = kParts * TC_A_BYTES;               // vocabulary chunk: hi (and lo)
+    constexpr uint32_t kBChunk = kParts * TC_B_BYTES;              // query chunk: hi (and lo)
+    constexpr uint32_t kAcc = SPLIT ? 256 : 128;  // TMEM columns per accumulator buffer (acc0 | acc1)
+    constexpr uint32_t kCols = 2 * kAcc;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)stages * kStage);
+    uint8_t* bpanel = smem + (size_t)stages * kStage;              // KC query chunks
+    uint64_t* full = reinterpret_cast<uint64_t*>(bpanel + (size_t)KC * kBChunk);
     uint64_t* empty = full + stages;
-    uint64_t* done = empty + stages;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    uint64_t* tfull = empty + stages;   // [2] accumulator ready (MMA commit)
+    uint64_t* tempty = tfull + 2;       // [2] accumulator drained (8 epilogue warps)
+    uint64_t* bfull = tempty + 2;       // query panel loaded
+    uint64_t* bfree = bfull + 1;        // MMAs reading the query panel done
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bfree + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t m0 = (int64_t)blockIdx.x * TC_BM;
-    const int n0 = blockIdx.y * TC_BN;
-    const int Nt = min(TC_BN, (int)round_up(N - n0, 16));
-    const uint32_t b_bytes = (uint32_t)Nt * 128u;
+    const int m_tiles = (int)(Mpad / TC_BM);
+    const int n_tiles = (N + TC_BN - 1) / TC_BN;
+    const int total = m_tiles * n_tiles;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 8);
+        }
+        mbar_init(bfull, 1);
+        mbar_init(bfree, 1);
+        *abort_flag = 0;
         mbar_fence_init();
     }
     if (warp == 1) tmem_alloc(tmem_slot, kCols);
@@ -198,102 +225,167 @@ k_tc_dist(const __half* __restrict__ A_hi, const __half* __restrict__ A_lo, int6
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint64_t deadline = global_ns() + TC_TIMEOUT_NS;
+
+    auto fail = [&]() {
+        atomicOr(err, ERR_TIMEOUT);
+        *abort_flag = 1;
+    };
 
     if (warp == 0 && lane == 0) {
-        // producer: K chunk c of this tile's rows and columns into stage c % stages
-        int issued = 0;
-        for (int c = 0; c < KC; ++c) {
-            const int s = c % stages;
-            if (c >= stages && !mbar_wait(&empty[s], (uint32_t)((c / stages) - 1) & 1u, deadline)) {
-                atomicOr(err, ERR_TIMEOUT);
-                break;
+        // producer: the query panel when the column tile changes, vocabulary chunks always
+        int64_t g = 0;
+        int cur_n = -1, reloads = 0;
+        for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
+            const int64_t m0 = (int64_t)(t % m_tiles) * TC_BM;
+            const int nt = t / m_tiles;
+            if (nt != cur_n) {
+                if (reloads > 0 && !mbar_wait(bfree, (uint32_t)(reloads - 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                    fail();
+                    break;
+                }
+                const int n0 = nt * TC_BN;
+                const int Nt = min(TC_BN, (int)round_up(N - n0, 16));
+                const uint32_t b_bytes = (uint32_t)Nt * 128u;
+                mbar_expect_tx(bfull, (uint32_t)(kParts * KC) * b_bytes);
+                for (int c = 0; c < KC; ++c) {
+                    uint8_t* bst = bpanel + (size_t)c * kBChunk;
+                    bulk_g2s(bst, B_hi + ((int64_t)c * Npad + n0) * 64, b_bytes, bfull);
+                    if (SPLIT) bulk_g2s(bst + TC_B_BYTES, B_lo + ((int64_t)c * Npad + n0) * 64, b_bytes, bfull);
+                }
+                cur_n = nt;
+                ++reloads;
             }
-            issued = c + 1;
-            uint8_t* st = smem + (size_t)s * kStage;
-            mbar_expect_tx(&full[s], (SPLIT ? 2u : 1u) * (TC_A_BYTES + b_bytes));
-            bulk_g2s(st, A_hi + ((int64_t)c * Mpad + m0) * 64, TC_A_BYTES, &full[s]);
-            if (SPLIT) bulk_g2s(st + TC_A_BYTES, A_lo + ((int64_t)c * Mpad + m0) * 64, TC_A_BYTES, &full[s]);
-            uint8_t* bst = st + (SPLIT ? 2 : 1) * TC_A_BYTES;
-            bulk_g2s(bst, B_hi + ((int64_t)c * Npad + n0) * 64, b_bytes, &full[s]);
-            if (SPLIT) bulk_g2s(bst + TC_B_BYTES, B_lo + ((int64_t)c * Npad + n0) * 64, b_bytes, &full[s]);
+            for (int c = 0; c < KC; ++c, ++g) {
+                const int s = (int)(g % stages);
+                if (g >= stages && !mbar_wait(&empty[s], (uint32_t)((g / stages) - 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                    fail();
+                    break;
+                }
+                uint8_t* st = smem + (size_t)s * kStage;
+                mbar_expect_tx(&full[s], kStage);
+                bulk_g2s(st, A_hi + ((int64_t)c * Mpad + m0) * 64, TC_A_BYTES, &full[s]);
+                if (SPLIT) bulk_g2s(st + TC_A_BYTES, A_lo + ((int64_t)c * Mpad + m0) * 64, TC_A_BYTES, &full[s]);
+            }
         }
-        // no copy may still be landing in shared memory when the block leaves: the last
-        // `stages` chunks are the only ones nobody else has waited for (bounded again)
+        // no copy may still be landing in shared memory when the block leaves
         const uint64_t tail = global_ns() + TC_TIMEOUT_NS;
-        for (int c = max(0, issued - stages); c < issued; ++c)
+        for (int64_t c = g > stages ? g - stages : 0; c < g; ++c)
             if (!mbar_wait(&full[c % stages], (uint32_t)(c / stages) & 1u, tail)) atomicOr(err, ERR_TIMEOUT);
+        if (reloads > 0 && !mbar_wait(bfull, (uint32_t)(reloads - 1) & 1u, tail)) atomicOr(err, ERR_TIMEOUT);
     } else if (warp == 1 && lane == 0) {
         // MMA issuer: kind::f16, D format F32 (bit 4), A/B format F16 (0), K-major A and B,
         // N >> 3 at bit 17, M >> 4 at bit 24
-        const uint32_t idesc = (1u << 4) | ((uint32_t)(Nt >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
-        for (int c = 0; c < KC; ++c) {
-            const int s = c % stages;
-            if (!mbar_wait(&full[s], (uint32_t)(c / stages) & 1u, deadline)) {
-                atomicOr(err, ERR_TIMEOUT);
+        int64_t g = 0;
+        int it = 0, cur_n = -1, reloads = 0;
+        for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++it) {
+            const int nt = t / m_tiles;
+            const int n0 = nt * TC_BN;
+            const int Nt = min(TC_BN, (int)round_up(N - n0, 16));
+            const uint32_t idesc = (1u << 4) | ((uint32_t)(Nt >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+            if (nt != cur_n) {
+                if (reloads > 0) mma_commit(bfree);  // the old panel is released once its MMAs finish
+                if (!mbar_wait(bfull, (uint32_t)reloads & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                    fail();
+                    break;
+                }
+                cur_n = nt;
+                ++reloads;
+            }
+            const int buf = it & 1;
+            if (it >= 2 && !mbar_wait(&tempty[buf], (uint32_t)((it >> 1) - 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                fail();
                 break;
             }
             tc_fence_after();
-            const uint32_t sa = smem_u32(smem + (size_t)s * kStage);
-            const uint32_t sa_lo = sa + TC_A_BYTES;
-            const uint32_t sb = sa + (SPLIT ? 2 : 1) * TC_A_BYTES;
-            const uint32_t sb_lo = sb + TC_B_BYTES;
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {  // 4 x K=16 per 64-wide chunk: 2 core matrices = 256 B
-                const uint32_t ko = (uint32_t)ks * 256u;
-                const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
-                const uint64_t da = smem_desc(sa + ko), db = smem_desc(sb + ko);
-                mma_f16(tmem, da, db, idesc, acc);
-                if (SPLIT) {
-                    mma_f16(tmem + 128, da, smem_desc(sb_lo + ko), idesc, acc);
-                    mma_f16(tmem + 128, smem_desc(sa_lo + ko), db, idesc, 1u);
+            const uint32_t acc0 = tmem + (uint32_t)buf * kAcc;
+            bool ok = true;
+            for (int c = 0; c < KC; ++c, ++g) {
+                const int s = (int)(g % stages);
+                if (!mbar_wait(&full[s], (uint32_t)(g / stages) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                    fail();
+                    ok = false;
+                    break;
                 }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(smem + (size_t)s * kStage);
+                const uint32_t sa_lo = sa + TC_A_BYTES;
+                const uint32_t sb = smem_u32(bpanel + (size_t)c * kBChunk);
+                const uint32_t sb_lo = sb + TC_B_BYTES;
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks) {  // 4 x K=16 per 64-wide chunk: 2 core matrices = 256 B
+                    const uint32_t ko = (uint32_t)ks * 256u;
+                    const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+                    const uint64_t da = smem_desc(sa + ko), db = smem_desc(sb + ko);
+                    mma_f16(acc0, da, db, idesc, acc);
+                    if (SPLIT) {
+                        mma_f16(acc0 + 128, da, smem_desc(sb_lo + ko), idesc, acc);
+                        mma_f16(acc0 + 128, smem_desc(sa_lo + ko), db, idesc, 1u);
+                    }
+                }
+                mma_commit(&empty[s]);
             }
-            mma_commit(&empty[s]);
+            mma_commit(&tfull[buf]);
+            if (!ok) break;
         }
-        mma_commit(done);
     } else if (warp >= 2) {
-        // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 = tile rows
+        // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 = tile rows, columns of its half
         const int q = warp & 3;
+        const int half = (warp - 2) >> 2;
         const int row = q * 32 + lane;
-        const int64_t u = m0 + row;
-        const bool row_ok = u < M;
-        if (!mbar_wait(done, 0u, deadline)) {
-            atomicOr(err, ERR_TIMEOUT);
-        } else {
+        int it = 0;
+        for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++it) {
+            const int64_t m0 = (int64_t)(t % m_tiles) * TC_BM;
+            const int n0 = (t / m_tiles) * TC_BN;
+            const int Nt = min(TC_BN, (int)round_up(N - n0, 16));
+            const int buf = it & 1;
+            if (!mbar_wait(&tfull[buf], (uint32_t)(it >> 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                fail();
+                break;
+            }
             tc_fence_after();
+            const int64_t u = m0 + row;
+            const bool row_ok = u < M;
             const float su = row_ok ? a_scale[u] : 0.f;
             const float nu = row_ok ? a_norm[u] : 0.f;
             const int32_t idu = row_ok ? a_ids[u] : -1;
-            const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16);
-            for (int cc = 0; cc < Nt; cc += 32) {
+            const uint32_t tbase = tmem + (uint32_t)buf * kAcc + ((uint32_t)(q * 32) << 16);
+            for (int cc = half * 64; cc < half * 64 + 64 && cc < Nt; cc += 32) {
                 uint32_t r0[32], r1[32];
                 tmem_ld32(tbase + (uint32_t)cc, r0);
                 if (SPLIT) tmem_ld32(tbase + 128u + (uint32_t)cc, r1);
                 tmem_wait_ld();
-                if (!row_ok) continue;
-                float* out = D + u * ldd + n0 + cc;
+                // lane l fetches the constants of column n0 + cc + l once (coalesced); inside
+                // the element loop they are broadcast by shuffles
+                const int lcol = n0 + cc + lane;
+                const bool lok = lcol < N;
+                const float cb_l = lok ? -2.f * b_scale[lcol] : 0.f;
+                const float nb_l = lok ? b_norm[lcol] : 0.f;
+                const int id_l = lok ? b_ids[lcol] : -2;
+                // every lane runs the loop (full-warp shuffles); rows past M only skip the stores
+                const float su2 = su;
+                float* out = D + (row_ok ? u : 0) * ldd + n0 + cc;
 #pragma unroll
                 for (int e4 = 0; e4 < 8; ++e4) {
                     float o[4];
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const int e = e4 * 4 + t;
-                        const int col = n0 + cc + e;
-                        float d = INFINITY;
-                        if (col < N) {
-                            float dot = __uint_as_float(r0[e]);
-                            if (SPLIT) dot = fmaf(__uint_as_float(r1[e]), 1.0f / 2048.0f, dot);
-                            dot *= su * b_scale[col];
-                            const float d2 = fmaf(-2.f, dot, nu + b_norm[col]);
-                            d = (idu == b_ids[col]) ? 0.f : sqrtf(fmaxf(d2, 0.f));
-                        }
-                        o[t] = d;
+                    for (int tt = 0; tt < 4; ++tt) {
+                        const int e = e4 * 4 + tt;
+                        const float cb = __shfl_sync(0xffffffffu, cb_l, e);
+                        const float nb = __shfl_sync(0xffffffffu, nb_l, e);
+                        const int idc = __shfl_sync(0xffffffffu, id_l, e);
+                        float dot = __uint_as_float(r0[e]);
+                        if (SPLIT) dot = fmaf(__uint_as_float(r1[e]), 1.0f / 2048.0f, dot);
+                        const float d2 = fmaf(cb * su2, dot, nu + nb);
+                        const float d = (idu == idc) ? 0.f : __fsqrt_rn(fmaxf(d2, 0.f));
+                        o[tt] = (n0 + cc + e < N) ? d : INFINITY;
                     }
-                    if (n0 + cc + e4 * 4 < ldd)
+                    if (row_ok && n0 + cc + e4 * 4 < ldd)
                         *reinterpret_cast<float4*>(out + e4 * 4) = make_float4(o[0], o[1], o[2], o[3]);
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
         }
     }
     tc_fence_before();
@@ -334,15 +426,32 @@ __global__ void k_pack_f16(const float* __restrict__ src, int ld, int m, int64_t
 
 }  // namespace
 
-size_t tc_dist_smem_bytes(bool split, int stages)
+size_t tc_dist_smem_bytes(bool split, int stages, int KC)
 {
-    const size_t stage = split ? 2 * (TC_A_BYTES + TC_B_BYTES) : (TC_A_BYTES + TC_B_BYTES);
-    return 1024 + (size_t)stages * stage + (2 * (size_t)stages + 1) * 8 + 16;
+    const size_t parts = split ? 2 : 1;
+    return 1024 + (size_t)stages * parts * TC_A_BYTES + (size_t)KC * parts * TC_B_BYTES +
+           (2 * (size_t)stages + 6) * 8 + 16;
 }
 
+int sm_count()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    }
+    return n;
+}
+
+// Vocabulary stages that fit beside the resident query panel (0 when the panel alone
+// does not leave room for two stages).
 int tc_dist_stages(bool split, int KC)
 {
-    return std::max(1, std::min(KC, split ? 3 : 5));
+    const size_t budget = 227 * 1024;
+    int s = 4;
+    while (s >= 2 && tc_dist_smem_bytes(split, s, KC) > budget) --s;
+    return s >= 2 ? s : 0;
 }
 
 cudaError_t launch_pack_f16(const float* src, int ld, int m, int64_t R, int64_t Rpad, int Kpad, __half* hi,
@@ -363,8 +472,10 @@ cudaError_t launch_tc_dist(bool split, const __half* A_hi, const __half* A_lo, i
     if (M <= 0 || N <= 0) return cudaSuccess;
     const int KC = Kpad / 64;
     const int stages = tc_dist_stages(split, KC);
-    const size_t smem = tc_dist_smem_bytes(split, stages);
-    dim3 grid((unsigned)(Mpad / TC_BM), (unsigned)((N + TC_BN - 1) / TC_BN));
+    if (stages < 2) return cudaErrorInvalidValue;  // embeddings wider than the resident panel allows
+    const size_t smem = tc_dist_smem_bytes(split, stages, KC);
+    const int64_t tiles = (Mpad / TC_BM) * ((N + TC_BN - 1) / TC_BN);
+    dim3 grid((unsigned)std::min<int64_t>(tiles, sm_count()));
     cudaError_t e;
     if (split) {
         e = cudaFuncSetAttribute(k_tc_dist<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
