@@ -204,6 +204,102 @@ k_rev(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
     }
 }
 
+// Candidate-list form: a block of W warps per candidate slot.  Warp w scans the w-th
+// contiguous chunk of the document's bins; warp 0 then inserts the other chunks' lists in
+// chunk order.  Strict '<' keeps an earlier chunk's entry ahead of an equal distance from a
+// later one, so the merged list (and the cost, summed in the same lane order) is
+// bit-identical to the one-warp kernel above.  W times the warps on a few hundred
+// documents, whose single-warp scans are latency-bound.
+template <int MEAS, int KT, int NJ, int W>
+__global__ void __launch_bounds__(W * 32, 4)
+k_rev_blk(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+          const float* __restrict__ val, const float* __restrict__ D, int ldd, int h,
+          const float* __restrict__ q_w, int k, const float* __restrict__ t_fwd,
+          float* __restrict__ t_rev, float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
+          const int* __restrict__ n_dev)
+{
+    constexpr int U = 4;
+    __shared__ float sz[W - 1][32 * NJ][KT];
+    __shared__ float sc[W - 1][32 * NJ][KT];
+    const int slot = blockIdx.x;
+    if (slot >= min(*n_dev, (int)gridDim.x)) return;  // uniform over the block
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t dd = doc_ids[slot];
+    const int32_t a = row_ptr[dd], b = row_ptr[dd + 1];
+    const int hd = b - a;
+    const int keff = MEAS == M_RWMD ? 1 : (MEAS == M_OMR ? min(2, hd) : min(k, hd));
+    const int chunk = (hd + W - 1) / W;
+    const int32_t ca = a + min(hd, warp * chunk), cb = a + min(hd, (warp + 1) * chunk);
+    float total = 0.f;
+    for (int jbase = 0; jbase < h; jbase += 32 * NJ) {
+        const int j0 = jbase + lane * NJ;
+        const bool jin = j0 < ldd;
+        float z[NJ][KT], cap[NJ][KT];
+#pragma unroll
+        for (int t = 0; t < NJ; ++t)
+#pragma unroll
+            for (int l = 0; l < KT; ++l) { z[t][l] = INFINITY; cap[t][l] = 0.f; }
+        for (int32_t eb = ca; eb < cb; eb += 32) {
+            const int32_t e = eb + lane;
+            const int32_t u = e < cb ? col[e] : 0;
+            const float x = e < cb ? val[e] : 0.f;
+            const int cnt = min(32, cb - eb);
+            int i = 0;
+            for (; i + U <= cnt; i += U) {
+                float dv[U][NJ], xv[U];
+#pragma unroll
+                for (int s = 0; s < U; ++s) {
+                    const int32_t ui = __shfl_sync(0xffffffffu, u, i + s);
+                    xv[s] = __shfl_sync(0xffffffffu, x, i + s);
+                    load_vec(D + (int64_t)ui * ldd + j0, jin, dv[s]);
+                }
+#pragma unroll
+                for (int s = 0; s < U; ++s)
+#pragma unroll
+                    for (int t = 0; t < NJ; ++t) insert_sorted<KT>(z[t], cap[t], dv[s][t], xv[s]);
+            }
+            for (; i < cnt; ++i) {
+                const int32_t ui = __shfl_sync(0xffffffffu, u, i);
+                const float xi = __shfl_sync(0xffffffffu, x, i);
+                float dv[NJ];
+                load_vec(D + (int64_t)ui * ldd + j0, jin, dv);
+#pragma unroll
+                for (int t = 0; t < NJ; ++t) insert_sorted<KT>(z[t], cap[t], dv[t], xi);
+            }
+        }
+        if (warp > 0) {
+#pragma unroll
+            for (int t = 0; t < NJ; ++t)
+#pragma unroll
+                for (int l = 0; l < KT; ++l) {
+                    sz[warp - 1][lane * NJ + t][l] = z[t][l];
+                    sc[warp - 1][lane * NJ + t][l] = cap[t][l];
+                }
+        }
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int w = 0; w < W - 1; ++w)
+#pragma unroll
+                for (int t = 0; t < NJ; ++t)
+#pragma unroll
+                    for (int l = 0; l < KT; ++l)
+                        insert_sorted<KT>(z[t], cap[t], sz[w][lane * NJ + t][l], sc[w][lane * NJ + t][l]);
+#pragma unroll
+            for (int t = 0; t < NJ; ++t)
+                if (j0 + t < h) total += rev_cost_sorted<MEAS, KT>(q_w[j0 + t], z[t], cap[t], keff);
+        }
+        __syncthreads();
+    }
+    if (warp == 0) {
+        total = warp_sum(total);
+        if (lane == 0) {
+            t_rev[slot] = total;
+            if (t_max) t_max[slot] = fmaxf(t_fwd[dd], total);
+        }
+    }
+}
+
 // k above the register width (ICT, large k): per lane, successive minima over the
 // document's bins, each strictly after the previous in (distance, bin position) order,
 // until the source mass is placed.  O(steps * h_d) per query bin.
@@ -396,32 +492,51 @@ __global__ void k_prune_compact(const float* __restrict__ t_fwd, int64_t n, cons
 }
 
 // Final selection over the candidates: thread i ranks candidate i in (sym, id) order
-// against all others; ranks < K are written; ok = no overflow and K-th <= theta.
+// against the other filled slots (one 64-bit key compare each: distances are >= 0, so the
+// key order is the (distance, id) order); ranks < K are written; ok = no overflow and
+// K-th <= theta.
 __global__ void k_prune_select(const int64_t* __restrict__ cand, const float* __restrict__ sym,
                                const int* __restrict__ count, int cap, const float* __restrict__ sel_val,
                                int K, int64_t* __restrict__ out_idx, float* __restrict__ out_dist,
                                int* __restrict__ ok)
 {
-    __shared__ float ss[kPruneCap];
-    __shared__ int64_t si[kPruneCap];
+    __shared__ unsigned long long key[kPruneCap];
     __shared__ float kth;
     const int c = min(*count, cap);
     const int i = threadIdx.x;
-    ss[i] = i < c ? sym[i] : INFINITY;
-    si[i] = i < c ? cand[i] : INT64_MAX;
+    const unsigned long long me =
+        i < c ? ((unsigned long long)__float_as_uint(sym[i]) << 32) | (unsigned long long)(uint32_t)cand[i] : ~0ull;
+    key[i] = me;
     if (i == 0) kth = INFINITY;
     __syncthreads();
     int r = 0;
-    const float me = ss[i];
-    const int64_t mi = si[i];
-    for (int j = 0; j < kPruneCap; ++j) {
-        const float o = ss[j];
-        r += (o < me || (o == me && si[j] < mi)) ? 1 : 0;
+    for (int j = 0; j < c; ++j) r += key[j] < me ? 1 : 0;
+    if (i < c && r < K) {
+        out_idx[r] = (int64_t)(me & 0xffffffffull);
+        out_dist[r] = __uint_as_float((unsigned)(me >> 32));
     }
-    if (i < c && r < K) { out_idx[r] = mi; out_dist[r] = me; }
-    if (i < c && r == K - 1) kth = me;
+    if (i < c && r == K - 1) kth = __uint_as_float((unsigned)(me >> 32));
     __syncthreads();
     if (i == 0) *ok = (*count <= cap && c >= K && kth <= prune_theta(sel_val[K - 1])) ? 1 : 0;
+}
+
+template <int MEAS>
+cudaError_t rev_meas_blk(int k, const int32_t* row_ptr, const int32_t* col, const float* val, int slots,
+                         const float* D, int ldd, int h, const float* q_w, const float* t_fwd,
+                         float* t_rev, float* t_max, const int64_t* doc_ids, const int* n_dev,
+                         cudaStream_t st)
+{
+    constexpr int W = 4;
+    const int kt = MEAS == M_RWMD ? 1 : (MEAS == M_OMR ? 2 : k);
+    const bool wide = h > 32;
+#define EMD_REVB(KT, NJ) k_rev_blk<MEAS, KT, NJ, W><<<slots, W * 32, 0, st>>>(row_ptr, col, val, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev)
+    if (kt <= 1) { if (wide) EMD_REVB(1, 4); else EMD_REVB(1, 1); }
+    else if (kt <= 2) { if (wide) EMD_REVB(2, 4); else EMD_REVB(2, 1); }
+    else if (kt <= 4) { if (wide) EMD_REVB(4, 4); else EMD_REVB(4, 1); }
+    else if (kt <= 8) { if (wide) EMD_REVB(8, 2); else EMD_REVB(8, 1); }
+    else EMD_REVB(16, 1);
+#undef EMD_REVB
+    return cudaGetLastError();
 }
 
 template <int MEAS>
@@ -490,9 +605,9 @@ cudaError_t launch_prune(int meas, int k, const int32_t* row_ptr, const int32_t*
     k_prune_compact<<<blocks, 256, 0, st>>>(t_fwd, n, sel_val, K, kPruneCap, cand, count);
     // reverse pass on the candidate slots (t_rev into sym + kPruneCap, max into sym)
     switch (meas) {
-    case M_RWMD: e = rev_meas<M_RWMD>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, st); break;
-    case M_OMR: e = rev_meas<M_OMR>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, st); break;
-    default: e = rev_meas<M_ACT>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, st); break;
+    case M_RWMD: e = rev_meas_blk<M_RWMD>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, st); break;
+    case M_OMR: e = rev_meas_blk<M_OMR>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, st); break;
+    default: e = rev_meas_blk<M_ACT>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, st); break;
     }
     if (e != cudaSuccess) return e;
     k_prune_select<<<1, kPruneCap, 0, st>>>(cand, sym, count, kPruneCap, sel_val, K, out_idx, out_dist, ok);
