@@ -159,6 +159,87 @@ def recall_at(gpu_idx, want, K):
     return hits / K
 
 
+# ------------------------------------------------------------------ serving
+
+def serve_point(emd, srv, queries, order, rate, n_req, k, K, seed):
+    """Open-loop Poisson arrivals at `rate` requests/s (rate None: all submitted at once),
+    one submitting and one collecting thread; latency = submit -> result on the device,
+    measured by the server's own steady clock."""
+    import threading
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, n_req) if rate else np.zeros(n_req)
+    due = np.cumsum(gaps)
+    rows = [queries.row(int(order[i % len(order)])) for i in range(n_req)]
+    tickets = []
+    cv = threading.Condition()
+    busy = [0]
+
+    def submitter():
+        t0 = time.perf_counter()
+        for i in range(n_req):
+            while time.perf_counter() - t0 < due[i]:
+                pass
+            while True:
+                try:
+                    t = emd.emd_server_submit(srv, rows[i][0], rows[i][1], "act", k, K)
+                    break
+                except emd.EmdError as e:
+                    if e.name != "BUSY":
+                        raise
+                    busy[0] += 1
+                    time.sleep(50e-6)
+            with cv:
+                tickets.append(t)
+                cv.notify()
+
+    emd.emd_server_stats_reset(srv)
+    th = threading.Thread(target=submitter)
+    t_start = time.perf_counter()
+    th.start()
+    oi, od = np.empty(K, np.int64), np.empty(K, np.float32)
+    for i in range(n_req):
+        with cv:
+            while len(tickets) <= i:
+                cv.wait()
+            t = tickets[i]
+        emd.emd_server_poll(srv, t, -1, oi, od)
+    th.join()
+    wall = time.perf_counter() - t_start
+    st = emd.emd_server_stats_get(srv)
+    return {"offered_qps": rate, "requests": n_req, "achieved_qps": st["qps"], "wall_s": wall,
+            "p50_ms": st["latency_p50_us"] / 1e3, "p99_ms": st["latency_p99_us"] / 1e3,
+            "mean_ms": st["latency_mean_us"] / 1e3, "max_in_flight": st["max_in_flight"],
+            "busy_retries": busy[0], "prune_fallbacks": st["prune_fallbacks"]}
+
+
+def serving_sweep(emd, w, opts, precision, rates, n_req, k, K, plain_saturation=True):
+    import emd_synth
+    queries = emd_synth.mixed_queries()
+    order = np.random.default_rng(7).permutation(queries.n)
+    out = {"database": "workload 2 (text V=1e5, n=2e4)",
+           "requests": "workload 4 queries: h_q log-uniform 5..2000, cycled in a fixed shuffled order",
+           "measure": f"LC-ACT k={k}, max of both directions, top-{K}",
+           "server": "8 slots, workspace pool 8 x max request, admission in arrival order",
+           "points": []}
+    forms = [(precision, True)] + ([("fp32", False)] if plain_saturation and precision != "fp32" else [])
+    for prec, sweep in forms:
+        db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
+                               emd.emd_db_options_default(precision=prec, **opts))
+        srv = emd.emd_server_create(db, emd.emd_server_options_default(max_inflight=8))
+        serve_point(emd, srv, queries, order, None, 256, k, K, 1)  # warm-up
+        if sweep:
+            for j, r in enumerate(rates):
+                p = serve_point(emd, srv, queries, order, r, n_req, k, K, 100 + j)
+                p["precision"] = prec
+                out["points"].append(p)
+        sat = serve_point(emd, srv, queries, order, None, min(n_req, 4096), k, K, 99)
+        sat["precision"] = prec
+        out["saturation_" + prec] = sat
+        emd.emd_server_destroy(srv)
+        emd.emd_db_destroy(db)
+    return out
+
+
 # ------------------------------------------------------------------ main
 
 def main():
@@ -174,6 +255,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0, help="default: same as --steps")
     ap.add_argument("--precision", default="fp32_tc", choices=["fp32", "fp32_tc"])
+    ap.add_argument("--serve-rates", default="1000,2000,3000",
+                    help="offered request rates (requests/s) of the serving sweep; empty: skip it")
+    ap.add_argument("--serve-requests", type=int, default=6000, help="requests per serving rate point")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -193,7 +277,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     w = emd_synth.config(2)
-    opts = dict(device=local, max_query_h=1024, max_batch=args.batch)
+    opts = dict(device=local, max_query_h=2048, max_batch=args.batch)
     db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
                            emd.emd_db_options_default(precision=args.precision, **opts))
     info = emd.emd_db_info_get(db)
@@ -369,6 +453,12 @@ def main():
     e2e = {"value": args.batch * e2e_steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "api": "emd_topk (host buffers, synchronous)"}
 
+    # serving: open-loop arrivals of mixed-size queries through emd_server_* (rank 0 only)
+    serving = None
+    rates = [float(x) for x in args.serve_rates.split(",") if x.strip()]
+    if rank == 0 and rates:
+        serving = serving_sweep(emd, w, opts, args.precision, rates, args.serve_requests, args.k, K)
+
     # CPU oracle baseline + recall on the same sampled queries (rank 0, N = 1 only)
     cpu = None
     recall = None
@@ -414,6 +504,7 @@ def main():
             "phases": phases,
             "recall": recall,
             "unpruned_all_docs": unpruned,
+            "serving": serving,
             "plain_fp32": plain,
         }
         print(json.dumps(line))

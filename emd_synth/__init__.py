@@ -230,12 +230,22 @@ def text_workload(name, seed, V, m, n, doc_law, n_queries, query_law, k_list, to
     rng = np.random.Generator(np.random.PCG64(seed))
     emb = unit_embeddings(rng, V, m)
     db = zipf_histograms(rng, V, _lengths(rng, n, doc_law))
-    qrng = np.random.Generator(np.random.PCG64(query_seed if query_seed is not None
-                                               else seed + QUERY_SEED_OFFSET))
+    queries = text_queries(V, n_queries, query_law, query_seed if query_seed is not None
+                           else seed + QUERY_SEED_OFFSET, query_limit)
+    return Workload(name, V, m, emb, None, db, queries, tuple(k_list), top_k)
+
+
+def text_queries(V, n_queries, query_law, query_seed, query_limit=None) -> Histograms:
+    qrng = np.random.Generator(np.random.PCG64(query_seed))
     nq = n_queries if query_limit is None else min(n_queries, query_limit)
     qlens = _lengths(qrng, n_queries, query_law)[:nq]
-    queries = zipf_histograms(qrng, V, qlens)
-    return Workload(name, V, m, emb, None, db, queries, tuple(k_list), top_k)
+    return zipf_histograms(qrng, V, qlens)
+
+
+def mixed_queries(query_limit: int | None = None) -> Histograms:
+    """The queries of workload 4 (h_q log-uniform 5..2000 over the vocabulary of workload 2)
+    without generating its database, which is workload 2's."""
+    return text_queries(100000, 4096, QUERY_LEN_MIXED, BASE_SEED + 4 + QUERY_SEED_OFFSET, query_limit)
 
 
 def image_workload(name, seed, n, n_queries, k_list, top_k, query_limit=None) -> Workload:

@@ -133,7 +133,8 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
                          const int64_t* row_ptr, const int32_t* col, const float* val,
                          int64_t n_docs, const emd_db_options* opt, emd_db** out);
 
-/* Release every device and host resource of the handle.  NULL is accepted. */
+/* Release every device and host resource of the handle.  NULL is accepted.  BUSY while a
+ * server (below) is attached to the handle. */
 emd_status emd_db_destroy(emd_db* db);
 
 /* Sizes and memory of the handle.  INVALID_ARG on NULL arguments. */
@@ -226,6 +227,73 @@ emd_status emd_phase1_table(emd_db* db, const int32_t* q_idx, const float* q_w, 
 emd_status emd_db_set_profiling(emd_db* db, int32_t on);
 emd_status emd_db_profile_get(emd_db* db, emd_profile* out);
 emd_status emd_db_profile_reset(emd_db* db);
+
+/* ------------------------------------------------------------------ serving
+ *
+ * A request loop over a resident database: single queries are submitted as they arrive and
+ * run, each on its own stream, as soon as a slot and enough device workspace are free, so
+ * requests that arrive while others are on the GPU overlap with them (continuous
+ * batching).  Every request computes the symmetric top-K of Section 5 (max of both
+ * directions, measure `meas`, Alg. 3 width k) with the same kernel sequence as emd_topk, so
+ * a result does not depend on which other requests were in flight: it is bit-identical to
+ * the same query served alone and to emd_topk with direction EMD_DIR_MAX.
+ *
+ * Admission: a request needs workspace_bytes(h_q) of device memory (its staged bins, the
+ * Phase-1 matrix v_used x round_up(h_q, 32) FP32, the k-wide table, three n-float document
+ * vectors, pruning buffers and its top-K).  Requests are admitted in arrival order while
+ * a slot is free and the workspace pool can hold the head of the queue; a request larger
+ * than the whole pool is refused at submit.
+ *
+ * Threads: submit, poll and stats may be called from any host threads; one worker thread
+ * per server issues the GPU work.  Calls on the database handle made while a server is
+ * attached are serialised with the worker's launches. */
+typedef struct emd_server emd_server;
+
+typedef struct {
+    int32_t max_inflight;    /* slots (streams) with requests on the device, default 8 (1..64) */
+    int32_t queue_capacity;  /* submitted but not yet admitted requests; beyond it submit
+                                returns BUSY.  Default 4096 */
+    int64_t workspace_bytes; /* device workspace pool; 0 (default) = max_inflight requests of
+                                the database's max_query_h, capped at half the free memory */
+    int32_t max_query_h;     /* largest accepted h_q; 0 (default) = the database's */
+} emd_server_options;
+
+typedef struct {
+    int64_t submitted, completed, rejected_busy, failed, prune_fallbacks;
+    int64_t queued, in_flight, max_in_flight;
+    int64_t pool_bytes, pool_used_max;
+    double qps;              /* completed / (last completion - first submit), since reset */
+    double latency_p50_us, latency_p99_us, latency_mean_us, latency_max_us; /* submit -> done */
+} emd_server_stats;
+
+void emd_server_options_default(emd_server_options* opt);
+
+/* Attach a server to db (the handle must outlive it).  K is limited to 64 per request.
+ * INVALID_ARG on bad options, OUT_OF_MEMORY if the pool or the pinned staging cannot be
+ * allocated, CUDA. */
+emd_status emd_server_create(emd_db* db, const emd_server_options* opt, emd_server** out);
+
+/* Queue one query (h_q bins: vocabulary ids idx, weights w summing to 1, host memory, copied
+ * during the call) for the symmetric top-K with measure meas and width k.  *ticket
+ * identifies the result.  INVALID_ARG for the argument checks of emd_topk or a request
+ * larger than the pool, BUSY when the queue is full, SHUTDOWN after destroy began. */
+emd_status emd_server_submit(emd_server* s, const int32_t* idx, const float* w, int32_t h_q,
+                             emd_measure meas, int32_t k, int32_t K, uint64_t* ticket);
+
+/* Wait up to timeout_ms (negative: no limit, 0: do not wait) for the result of ticket.
+ * Ready: out_idx / out_dist (K entries each, host) are written, the ticket is released and
+ * the status is OK (or the request's own failure status).  TIMEOUT if not ready yet (the
+ * ticket stays valid); INVALID_ARG for an unknown or already collected ticket. */
+emd_status emd_server_poll(emd_server* s, uint64_t ticket, int32_t timeout_ms, int64_t* out_idx,
+                           float* out_dist);
+
+/* Counters and latency percentiles since creation or the last reset. */
+emd_status emd_server_stats_get(emd_server* s, emd_server_stats* out);
+emd_status emd_server_stats_reset(emd_server* s);
+
+/* Stop accepting requests, finish every admitted and queued request, release the server.
+ * Results not collected are discarded.  NULL is accepted. */
+emd_status emd_server_destroy(emd_server* s);
 
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* emd_last_error(void);

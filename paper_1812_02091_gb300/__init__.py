@@ -19,6 +19,8 @@ __all__ = [
     "emd_query_batch", "emd_topk", "emd_query_batch_device", "emd_topk_device",
     "emd_db_check_device_errors", "emd_phase1_table", "emd_db_set_profiling", "emd_topk_select_static",
     "emd_db_profile_get", "emd_db_profile_reset", "emd_last_error", "emd_version",
+    "emd_server_options_default", "emd_server_create", "emd_server_submit", "emd_server_poll",
+    "emd_server_stats_get", "emd_server_stats_reset", "emd_server_destroy", "EmdError",
     "MEASURES", "DIRECTIONS", "PRECISIONS", "PHASES", "library_path", "load",
 ]
 
@@ -61,6 +63,19 @@ class emd_profile(ctypes.Structure):
                 ("prune_fallbacks", ctypes.c_int64)]
 
 
+class emd_server_options(ctypes.Structure):
+    _fields_ = [("max_inflight", ctypes.c_int32), ("queue_capacity", ctypes.c_int32),
+                ("workspace_bytes", ctypes.c_int64), ("max_query_h", ctypes.c_int32)]
+
+
+class emd_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "rejected_busy", "failed",
+                                              "prune_fallbacks", "queued", "in_flight", "max_in_flight",
+                                              "pool_bytes", "pool_used_max")] + \
+               [(n, ctypes.c_double) for n in ("qps", "latency_p50_us", "latency_p99_us", "latency_mean_us",
+                                               "latency_max_us")]
+
+
 _lib = None
 
 
@@ -94,12 +109,21 @@ def load():
     L.emd_db_set_profiling.argtypes = [P, i32]
     L.emd_db_profile_get.argtypes = [P, ctypes.POINTER(emd_profile)]
     L.emd_db_profile_reset.argtypes = [P]
+    L.emd_server_options_default.argtypes = [ctypes.POINTER(emd_server_options)]
+    L.emd_server_options_default.restype = None
+    L.emd_server_create.argtypes = [P, ctypes.POINTER(emd_server_options), ctypes.POINTER(P)]
+    L.emd_server_submit.argtypes = [P, P, P, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_uint64)]
+    L.emd_server_poll.argtypes = [P, ctypes.c_uint64, i32, P, P]
+    L.emd_server_stats_get.argtypes = [P, ctypes.POINTER(emd_server_stats)]
+    L.emd_server_stats_reset.argtypes = [P]
+    L.emd_server_destroy.argtypes = [P]
     L.emd_last_error.restype = ctypes.c_char_p
     L.emd_version.restype = ctypes.c_char_p
     for name in ("emd_db_create", "emd_db_destroy", "emd_db_info_get", "emd_query_batch", "emd_topk",
                  "emd_query_batch_device", "emd_topk_device", "emd_db_check_device_errors",
                  "emd_phase1_table", "emd_db_set_profiling", "emd_db_profile_get", "emd_topk_select_static",
-                 "emd_db_profile_reset"):
+                 "emd_db_profile_reset", "emd_server_create", "emd_server_submit", "emd_server_poll",
+                 "emd_server_stats_get", "emd_server_stats_reset", "emd_server_destroy"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -286,3 +310,65 @@ def emd_db_profile_get(db) -> dict:
 
 def emd_db_profile_reset(db):
     _check(load().emd_db_profile_reset(db))
+
+
+# ------------------------------------------------------------------------ serving
+
+def emd_server_options_default(**over) -> emd_server_options:
+    o = emd_server_options()
+    load().emd_server_options_default(ctypes.byref(o))
+    names = {f[0] for f in emd_server_options._fields_}
+    for k, v in over.items():
+        if k not in names:
+            raise TypeError(f"unknown option {k!r}")
+        setattr(o, k, int(v))
+    return o
+
+
+def emd_server_create(db, options: emd_server_options | None = None):
+    h = ctypes.c_void_p()
+    _check(load().emd_server_create(db, ctypes.byref(options) if options is not None else None,
+                                    ctypes.byref(h)))
+    return h
+
+
+def emd_server_submit(server, idx, w, meas="act", k: int = 1, K: int = 16) -> int:
+    """Queue one query (vocabulary ids idx, weights w); returns its ticket.  Raises EmdError
+    (name "BUSY" when the queue is full)."""
+    i, pi = _np(idx, np.int32)
+    ww, pw = _np(w, np.float32)
+    if i.shape != ww.shape or i.ndim != 1:
+        raise ValueError("idx and w must be 1-D of the same length")
+    t = ctypes.c_uint64()
+    _check(load().emd_server_submit(server, pi, pw, int(i.shape[0]), _code(MEASURES, meas), int(k), int(K),
+                                    ctypes.byref(t)))
+    return int(t.value)
+
+
+def emd_server_poll(server, ticket: int, timeout_ms: int, out_idx, out_dist) -> bool:
+    """Wait up to timeout_ms (-1: no limit) for a result; writes out_idx (int64[K]) and
+    out_dist (float32[K]) and returns True when ready, False on timeout."""
+    if out_idx.dtype != np.int64 or out_dist.dtype != np.float32:
+        raise TypeError("out_idx must be int64 and out_dist float32")
+    if not (out_idx.flags.c_contiguous and out_dist.flags.c_contiguous):
+        raise ValueError("outputs must be contiguous")
+    st = load().emd_server_poll(server, ctypes.c_uint64(ticket), int(timeout_ms),
+                                out_idx.ctypes.data_as(ctypes.c_void_p), out_dist.ctypes.data_as(ctypes.c_void_p))
+    if st == 4:  # TIMEOUT
+        return False
+    _check(st)
+    return True
+
+
+def emd_server_stats_get(server) -> dict:
+    st = emd_server_stats()
+    _check(load().emd_server_stats_get(server, ctypes.byref(st)))
+    return {f[0]: (float if f[1] is ctypes.c_double else int)(getattr(st, f[0])) for f in emd_server_stats._fields_}
+
+
+def emd_server_stats_reset(server):
+    _check(load().emd_server_stats_reset(server))
+
+
+def emd_server_destroy(server):
+    _check(load().emd_server_destroy(server))

@@ -9,13 +9,15 @@
 #include <string>
 #include <vector>
 
-#include "emd_internal.cuh"
+#include "emd_db.cuh"
 
 using namespace emd;
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+namespace emd {
 
 emd_status fail(emd_status st, const char* fmt, ...)
 {
@@ -34,13 +36,7 @@ emd_status cuda_fail(cudaError_t e, const char* what)
                 "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define EMD_CUDA(call, what)                              \
-    do {                                                  \
-        cudaError_t e_ = (call);                          \
-        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-    } while (0)
-
-}  // namespace
+}  // namespace emd
 
 namespace emd {
 // Record a failure message for emd_last_error() from another translation unit.
@@ -52,92 +48,7 @@ emd_status set_error(emd_status st, const char* msg)
 void clear_error() { g_err.clear(); }
 }  // namespace emd
 
-struct emd_db;
-
-namespace {
-
-// One concurrent per-query pipeline: its stream and the workspace a query needs from
-// Phase 1 to its distances (or its pruned top-K).
-struct Lane {
-    cudaStream_t st = nullptr;
-    cudaEvent_t done = nullptr;
-    float* Q = nullptr;          // qrows_max x ldm
-    float* qnorm = nullptr;      // qrows_max
-    __half* q_hi = nullptr;      // npad_max x kpad (tensor-core precision)
-    __half* q_lo = nullptr;
-    float* q_scale = nullptr;    // npad_max
-    float* D = nullptr;          // v_used x ldd (ldd <= ldd_max)
-    float2* tab = nullptr;       // v_used x max_table_k
-    float* t_fwd = nullptr;      // n
-    float* t_rev = nullptr;      // n
-    int64_t* sel_idx = nullptr;  // kPruneMaxK forward top-K
-    float* sel_val = nullptr;
-    int64_t* cand_idx = nullptr; // kPruneCap candidates
-    float* cand_sym = nullptr;   // 2 x kPruneCap
-    int* cand_count = nullptr;
-    unsigned long long* scratch = nullptr;  // kTopkScratchRow selection partials
-};
-
-}  // namespace
-
-struct emd_db {
-    int dev = 0;
-    cudaStream_t stream = nullptr;  // host-buffer entry points run here
-    cudaEvent_t fork = nullptr;
-    emd_db_options opt{};
-    int64_t v = 0, v_used = 0, n = 0, nnz = 0;
-    int m = 0, ldm = 0;
-    bool cost_mode = false;
-
-    // resident database
-    float* emb = nullptr;        // v x ldm, full vocabulary (queries gather from it)
-    float* emb_used = nullptr;   // v_used x ldm, used vocabulary (Section 2.2)
-    float* norm_used = nullptr;  // v_used, squared norms
-    int32_t* used_ids = nullptr; // v_used, vocabulary id of each used row (ascending)
-    float* cost = nullptr;       // v x v ground costs (cost-matrix mode)
-    int32_t* row_ptr = nullptr;  // n + 1
-    int32_t* col = nullptr;      // nnz, renumbered into the used vocabulary
-    float* val = nullptr;        // nnz
-    int* err = nullptr;
-
-    // tensor-core operands of the used vocabulary (precision EMD_PREC_FP32_TC)
-    bool tc = false;
-    int kpad = 0;
-    int64_t mpad = 0;
-    __half* a_hi = nullptr;      // mpad x kpad packed panels
-    __half* a_lo = nullptr;
-    float* a_scale = nullptr;    // mpad
-
-    // per-lane workspace
-    int ldd_max = 0, qrows_max = 0;
-    std::vector<Lane> lanes;
-    int32_t* tab_s = nullptr;    // v_used x max_table_k (inspection entry point only)
-
-    // batch workspace (shared by the lanes, one row per query of a batch)
-    unsigned long long* topk_scratch = nullptr;  // max_batch x kTopkScratchRow
-    int* cand_ok = nullptr;        // max_batch certification flags
-    int64_t stage_bins = 0;
-    int32_t* stage_idx = nullptr;
-    float* stage_w = nullptr;
-    float* stage_out = nullptr;      // max_batch x n
-    int64_t* stage_oidx = nullptr;   // max_batch x kMaxTopK
-    float* stage_odist = nullptr;    // max_batch x kMaxTopK
-
-    int64_t bytes = 0;
-    std::vector<void*> allocs;
-
-    // profiling
-    bool profiling = false;
-    struct Rec { int phase; cudaEvent_t a, b; };
-    std::vector<Rec> recs;
-    std::vector<cudaEvent_t> pool;
-    double ms[EMD_N_PHASES] = {};
-    int64_t launches[EMD_N_PHASES] = {};
-    int64_t total_launches = 0;
-    int64_t pruned_queries = 0, prune_fallbacks = 0;
-};
-
-namespace {
+namespace emd {
 
 template <typename T>
 emd_status dalloc(emd_db* db, T** p, int64_t count)
@@ -445,6 +356,22 @@ emd_status read_device_errors(emd_db* db)
     return EMD_OK;
 }
 
+// Folds the finished profiling event pairs into the per-phase sums.
+emd_status collect_profile(emd_db* db)
+{
+    EMD_CUDA(cudaSetDevice(db->dev), "cudaSetDevice");
+    for (auto& r : db->recs) {
+        EMD_CUDA(cudaEventSynchronize(r.b), "event synchronize");
+        float ms = 0.f;
+        EMD_CUDA(cudaEventElapsedTime(&ms, r.a, r.b), "event time");
+        db->ms[r.phase] += ms;
+        db->pool.push_back(r.a);
+        db->pool.push_back(r.b);
+    }
+    db->recs.clear();
+    return EMD_OK;
+}
+
 // Host-buffer driver shared by emd_query_batch and emd_topk.
 emd_status host_batches(emd_db* db, const emd_queries* q, int meas, int k, int dir, int K,
                         float* out_dist_all, int64_t* out_idx, float* out_dist)
@@ -482,7 +409,7 @@ emd_status host_batches(emd_db* db, const emd_queries* q, int meas, int k, int d
     return read_device_errors(db);
 }
 
-}  // namespace
+}  // namespace emd
 
 extern "C" {
 
@@ -677,6 +604,8 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
 
 emd_status emd_db_destroy(emd_db* db)
 {
+    g_err.clear();
+    if (db && db->servers.load() > 0) return fail(EMD_ERR_BUSY, "a server is attached to the database");
     release(db);
     return EMD_OK;
 }
@@ -699,6 +628,7 @@ emd_status emd_query_batch(emd_db* db, const emd_queries* q, emd_measure meas, i
 {
     g_err.clear();
     if (!db || !q) return fail(EMD_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lock(db->mu);
     emd_status s = check_request(db, meas, k, dir);
     if (s != EMD_OK) return s;
     if ((s = check_sizes(db, q->n_queries, q->row_ptr, meas, k, dir)) != EMD_OK) return s;
@@ -713,6 +643,7 @@ emd_status emd_topk(emd_db* db, const emd_queries* q, emd_measure meas, int32_t 
 {
     g_err.clear();
     if (!db || !q) return fail(EMD_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lock(db->mu);
     emd_status s = check_request(db, meas, k, dir);
     if (s != EMD_OK) return s;
     if (K < 1 || K > kMaxTopK || K > db->n)
@@ -732,6 +663,7 @@ emd_status emd_query_batch_device(emd_db* db, int64_t n_queries, const int64_t* 
     g_err.clear();
     if (!db) return fail(EMD_ERR_INVALID_ARG, "NULL handle");
     emd_status s = check_request(db, meas, k, dir);
+    std::lock_guard<std::mutex> lock(db->mu);
     if (s != EMD_OK) return s;
     if ((s = check_sizes(db, n_queries, q_row_ptr_host, meas, k, dir)) != EMD_OK) return s;
     if (n_queries == 0) return EMD_OK;
@@ -755,6 +687,7 @@ emd_status emd_topk_device(emd_db* db, int64_t n_queries, const int64_t* q_row_p
     g_err.clear();
     if (!db) return fail(EMD_ERR_INVALID_ARG, "NULL handle");
     emd_status s = check_request(db, meas, k, dir);
+    std::lock_guard<std::mutex> lock(db->mu);
     if (s != EMD_OK) return s;
     if (K < 1 || K > kMaxTopK || K > db->n)
         return fail(EMD_ERR_INVALID_ARG, "K must be in 1..min(n_docs, %d)", kMaxTopK);
@@ -777,6 +710,7 @@ emd_status emd_db_check_device_errors(emd_db* db)
 {
     g_err.clear();
     if (!db) return fail(EMD_ERR_INVALID_ARG, "NULL handle");
+    std::lock_guard<std::mutex> lock(db->mu);
     EMD_CUDA(cudaSetDevice(db->dev), "cudaSetDevice");
     EMD_CUDA(cudaDeviceSynchronize(), "synchronize");
     return read_device_errors(db);
@@ -789,6 +723,7 @@ emd_status emd_phase1_table(emd_db* db, const int32_t* q_idx, const float* q_w, 
     if (!db || !q_idx || !q_w || !z || !s_out || !w) return fail(EMD_ERR_INVALID_ARG, "NULL argument");
     if (h_q < 1 || h_q > db->opt.max_query_h) return fail(EMD_ERR_INVALID_ARG, "h_q out of range");
     if (k < 1 || k > db->opt.max_table_k) return fail(EMD_ERR_INVALID_ARG, "k out of range");
+    std::lock_guard<std::mutex> lock(db->mu);
     int64_t rp[2] = {0, h_q};
     emd_queries q{1, rp, q_idx, q_w};
     emd_status s = check_query_values(db, &q);
@@ -819,6 +754,7 @@ emd_status emd_phase1_table(emd_db* db, const int32_t* q_idx, const float* q_w, 
 emd_status emd_db_set_profiling(emd_db* db, int32_t on)
 {
     if (!db) return fail(EMD_ERR_INVALID_ARG, "NULL handle");
+    std::lock_guard<std::mutex> lock(db->mu);
     db->profiling = on != 0;
     return EMD_OK;
 }
@@ -826,16 +762,9 @@ emd_status emd_db_set_profiling(emd_db* db, int32_t on)
 emd_status emd_db_profile_get(emd_db* db, emd_profile* out)
 {
     if (!db || !out) return fail(EMD_ERR_INVALID_ARG, "NULL argument");
-    EMD_CUDA(cudaSetDevice(db->dev), "cudaSetDevice");
-    for (auto& r : db->recs) {
-        EMD_CUDA(cudaEventSynchronize(r.b), "event synchronize");
-        float ms = 0.f;
-        EMD_CUDA(cudaEventElapsedTime(&ms, r.a, r.b), "event time");
-        db->ms[r.phase] += ms;
-        db->pool.push_back(r.a);
-        db->pool.push_back(r.b);
-    }
-    db->recs.clear();
+    std::lock_guard<std::mutex> lock(db->mu);
+    emd_status s = collect_profile(db);
+    if (s != EMD_OK) return s;
     for (int p = 0; p < EMD_N_PHASES; ++p) { out->ms[p] = db->ms[p]; out->launches[p] = db->launches[p]; }
     out->total_launches = db->total_launches;
     out->pruned_queries = db->pruned_queries;
@@ -846,8 +775,8 @@ emd_status emd_db_profile_get(emd_db* db, emd_profile* out)
 emd_status emd_db_profile_reset(emd_db* db)
 {
     if (!db) return fail(EMD_ERR_INVALID_ARG, "NULL handle");
-    emd_profile tmp;
-    emd_status s = emd_db_profile_get(db, &tmp);
+    std::lock_guard<std::mutex> lock(db->mu);
+    emd_status s = collect_profile(db);
     if (s != EMD_OK) return s;
     for (int p = 0; p < EMD_N_PHASES; ++p) { db->ms[p] = 0.0; db->launches[p] = 0; }
     db->pruned_queries = db->prune_fallbacks = 0;

@@ -1,0 +1,129 @@
+// The database handle and the per-query kernel sequence, shared by the query entry points
+// (emd_api.cu) and the server (emd_server.cu).  Internal to the library.
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "emd_internal.cuh"
+
+namespace emd {
+
+// Record a formatted failure for emd_last_error() and return st.
+emd_status fail(emd_status st, const char* fmt, ...);
+emd_status cuda_fail(cudaError_t e, const char* what);
+
+// One concurrent per-query pipeline: its stream and the workspace a query needs from
+// Phase 1 to its distances (or its pruned top-K).
+struct Lane {
+    cudaStream_t st = nullptr;
+    cudaEvent_t done = nullptr;
+    float* Q = nullptr;          // qrows_max x ldm
+    float* qnorm = nullptr;      // qrows_max
+    __half* q_hi = nullptr;      // npad_max x kpad (tensor-core precision)
+    __half* q_lo = nullptr;
+    float* q_scale = nullptr;    // npad_max
+    float* D = nullptr;          // v_used x ldd (ldd <= ldd_max)
+    float2* tab = nullptr;       // v_used x max_table_k
+    float* t_fwd = nullptr;      // n
+    float* t_rev = nullptr;      // n
+    int64_t* sel_idx = nullptr;  // kPruneMaxK forward top-K
+    float* sel_val = nullptr;
+    int64_t* cand_idx = nullptr; // kPruneCap candidates
+    float* cand_sym = nullptr;   // 2 x kPruneCap
+    int* cand_count = nullptr;
+    unsigned long long* scratch = nullptr;  // kTopkScratchRow selection partials
+};
+
+}  // namespace emd
+
+#define EMD_CUDA(call, what)                                   \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return emd::cuda_fail(e_, what); \
+    } while (0)
+
+struct emd_db {
+    int dev = 0;
+    cudaStream_t stream = nullptr;  // host-buffer entry points run here
+    cudaEvent_t fork = nullptr;
+    emd_db_options opt{};
+    int64_t v = 0, v_used = 0, n = 0, nnz = 0;
+    int m = 0, ldm = 0;
+    bool cost_mode = false;
+
+    // resident database
+    float* emb = nullptr;        // v x ldm, full vocabulary (queries gather from it)
+    float* emb_used = nullptr;   // v_used x ldm, used vocabulary (Section 2.2)
+    float* norm_used = nullptr;  // v_used, squared norms
+    int32_t* used_ids = nullptr; // v_used, vocabulary id of each used row (ascending)
+    float* cost = nullptr;       // v x v ground costs (cost-matrix mode)
+    int32_t* row_ptr = nullptr;  // n + 1
+    int32_t* col = nullptr;      // nnz, renumbered into the used vocabulary
+    float* val = nullptr;        // nnz
+    int* err = nullptr;
+
+    // tensor-core operands of the used vocabulary (precision EMD_PREC_FP32_TC)
+    bool tc = false;
+    int kpad = 0;
+    int64_t mpad = 0;
+    __half* a_hi = nullptr;      // mpad x kpad packed panels
+    __half* a_lo = nullptr;
+    float* a_scale = nullptr;    // mpad
+
+    // per-lane workspace
+    int ldd_max = 0, qrows_max = 0;
+    std::vector<emd::Lane> lanes;
+    int32_t* tab_s = nullptr;    // v_used x max_table_k (inspection entry point only)
+
+    // batch workspace (shared by the lanes, one row per query of a batch)
+    unsigned long long* topk_scratch = nullptr;  // max_batch x kTopkScratchRow
+    int* cand_ok = nullptr;        // max_batch certification flags
+    int64_t stage_bins = 0;
+    int32_t* stage_idx = nullptr;
+    float* stage_w = nullptr;
+    float* stage_out = nullptr;      // max_batch x n
+    int64_t* stage_oidx = nullptr;   // max_batch x kMaxTopK
+    float* stage_odist = nullptr;    // max_batch x kMaxTopK
+
+    int64_t bytes = 0;
+    std::vector<void*> allocs;
+
+    // profiling
+    bool profiling = false;
+    struct Rec { int phase; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    double ms[EMD_N_PHASES] = {};
+    int64_t launches[EMD_N_PHASES] = {};
+    int64_t total_launches = 0;
+    int64_t pruned_queries = 0, prune_fallbacks = 0;
+
+    // Serialises the entry points that launch work or touch the counters above (host
+    // threads, and the server's worker thread).
+    std::mutex mu;
+    std::atomic<int> servers{0};  // attached servers (emd_server_create)
+};
+
+
+namespace emd {
+
+int table_width(int meas, int k, int h);
+emd_status check_query_values(const emd_db* db, const emd_queries* q);
+bool prunable(const emd_db* db, int meas, int k, int dir, int K);
+int topk_launch_count(int64_t n);
+
+// One query through Phase 1 and the forward and/or reverse pass on lane L's workspace;
+// out_t (n floats, device) receives the distances.  Caller holds db->mu.
+emd_status run_query(emd_db* db, Lane& L, const int32_t* qidx, const float* qw, int h, int meas, int k,
+                     int dir, float* out_t, cudaStream_t st);
+
+// Pruned max-direction top-K of one query (K <= kPruneMaxK); *ok (device) receives the
+// certificate.  Caller holds db->mu.
+emd_status run_topk_pruned(emd_db* db, Lane& L, const int32_t* qidx, const float* qw, int h, int meas, int k,
+                           int K, int* ok, int64_t* out_idx, float* out_dist, cudaStream_t st);
+
+}  // namespace emd
