@@ -159,6 +159,56 @@ def recall_at(gpu_idx, want, K):
     return hits / K
 
 
+# ------------------------------------------------------------------ precision forms
+
+def precision_forms(emd, torch, w, opts, k, K, steps, batch, flush, threads, n_oracle=2):
+    """Workload 4: mixed-size queries (h_q log-uniform 5..2000) on the workload-2 database,
+    pruned symmetric top-K in each Phase-1 arithmetic on the same batches; queries/s from
+    CUDA events (L2 flushed between batches), top-K recall and the relative error of the
+    returned distances against the FP64 oracle on sampled queries."""
+    import types
+    import emd_synth
+    mixed = emd_synth.mixed_queries(steps * batch)
+    hs = np.diff(mixed.row_ptr)
+    dev = []
+    for s in range(steps):
+        sub = mixed.subset(np.arange(s * batch, (s + 1) * batch))
+        dev.append((sub.row_ptr, torch.from_numpy(sub.col).cuda(), torch.from_numpy(sub.val).cuda()))
+    oq = [i for i in range(batch) if hs[i] <= 400][:n_oracle]
+    _, want = oracle_sample(types.SimpleNamespace(emb=w.emb, db=w.db, queries=mixed), oq, "act", k, threads)
+    stream = torch.cuda.current_stream()
+    out = {"queries": f"{steps} batches of {batch} workload-4 queries (h_q log-uniform 5..2000, mean "
+                      f"{hs.mean():.0f} here)",
+           "oracle_queries": [int(hs[i]) for i in oq], "forms": {}}
+    for prec in ("fp32", "fp32_tc", "bf16", "fp8"):
+        db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
+                               emd.emd_db_options_default(precision=prec, **opts))
+        oi = torch.empty((batch, K), dtype=torch.int64, device="cuda")
+        od = torch.empty((batch, K), dtype=torch.float32, device="cuda")
+        for s in range(min(2, steps)):
+            emd.emd_topk_device(db, *dev[s], oi, od, "act", k, "max", K, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        first = None
+        for s in range(steps):
+            flush.fill_(float(s))
+            ev[s][0].record(stream)
+            emd.emd_topk_device(db, *dev[s], oi, od, "act", k, "max", K, stream=stream.cuda_stream)
+            ev[s][1].record(stream)
+            if s == 0:
+                first = (oi.clone(), od.clone())
+        torch.cuda.synchronize()
+        emd.emd_db_check_device_errors(db)
+        total = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+        gi, gd = first[0].cpu().numpy(), first[1].cpu().numpy()
+        rec = [recall_at(gi[q], want[j], K) for j, q in enumerate(oq)]
+        err = [float(np.max(np.abs(gd[q] - want[j][gi[q]]) / want[j][gi[q]])) for j, q in enumerate(oq)]
+        out["forms"][prec] = {"queries_per_s": batch * steps / total, "ms_per_batch": 1e3 * total / steps,
+                              "top16_recall": float(np.mean(rec)), "max_rel_err_top16_dist": max(err)}
+        emd.emd_db_destroy(db)
+    return out
+
+
 # ------------------------------------------------------------------ serving
 
 def serve_point(emd, srv, queries, order, rate, n_req, k, K, seed):
@@ -258,6 +308,8 @@ def main():
     ap.add_argument("--serve-rates", default="1000,2000,3000",
                     help="offered request rates (requests/s) of the serving sweep; empty: skip it")
     ap.add_argument("--serve-requests", type=int, default=6000, help="requests per serving rate point")
+    ap.add_argument("--precision-steps", type=int, default=5,
+                    help="batches per arithmetic in the precision comparison; 0: skip it")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -372,6 +424,12 @@ def main():
     unpruned = {"value": args.batch * steps_all * world / (total_all / 1e3), "unit": UNIT,
                 "ms_per_step": total_all / steps_all, "steps": steps_all,
                 "top16_identical_to_pruned": same_as_pruned}
+
+    # the Phase-1 arithmetics side by side on mixed-size queries (rank 0, N = 1 only)
+    forms = None
+    if rank == 0 and world == 1 and args.precision_steps > 0:
+        forms = precision_forms(emd, torch, w, opts, args.k, K, args.precision_steps, args.batch, flush,
+                                os.cpu_count() or 1)
 
     # per-phase achieved figures over the timed region
     timed = dev_batches[args.warmup:args.warmup + steps_serial]
@@ -505,6 +563,7 @@ def main():
             "recall": recall,
             "unpruned_all_docs": unpruned,
             "serving": serving,
+            "precision_forms": forms,
             "plain_fp32": plain,
         }
         print(json.dumps(line))

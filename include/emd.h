@@ -56,9 +56,15 @@ typedef enum { EMD_DIR_FWD = 0, EMD_DIR_REV = 1, EMD_DIR_MAX = 2 } emd_direction
  * FFMA on the CUDA cores).  FP32_TC computes the same FP32-grade distances on the tensor
  * cores: each embedding row is scaled by its absmax and split into two FP16 parts
  * (hi + lo * 2^-11), and the three products hi*hi, hi*lo, lo*hi are accumulated in FP32,
- * which reproduces the dot product to about 2^-22 relative.  BF16 and FP8_E4M3 (a single
- * low-precision product followed by an exact FP32 re-rank of each row's candidates) are
- * not available in this build (EMD_ERR_UNSUPPORTED). */
+ * which reproduces the dot product to about 2^-22 relative.  BF16 and FP8_E4M3 compute the
+ * matrix from one low-precision product on the tensor cores (operands scaled per row by
+ * their absmax; E4M3 maps the absmax to 448), FP32 accumulation; the Phase-1 table then
+ * takes each row's k + rerank_margin smallest approximate distances and recomputes them
+ * exactly in FP32 as sqrt(sum (v - q)^2) before keeping the k smallest.  Forward distances
+ * are exact whenever the true k nearest are among those candidates; reverse distances use
+ * the approximate matrix except for the re-ranked entries.  These two forms require
+ * min(table width + rerank_margin, h_q) <= 32 for forward directions (else UNSUPPORTED).
+ * Cost-matrix databases ignore the precision. */
 typedef enum {
     EMD_PREC_FP32 = 0,
     EMD_PREC_BF16 = 1,

@@ -159,6 +159,9 @@ emd_status check_sizes(const emd_db* db, int64_t nq, const int64_t* rp, int meas
         if (dir != EMD_DIR_REV && table_width(meas, k, (int)h) > db->opt.max_table_k)
             return fail(EMD_ERR_UNSUPPORTED, "forward table width %d exceeds max_table_k %d",
                         table_width(meas, k, (int)h), db->opt.max_table_k);
+        if (dir != EMD_DIR_REV && db->approx && rerank_width(db, table_width(meas, k, (int)h), (int)h) > kRerankMax)
+            return fail(EMD_ERR_UNSUPPORTED, "re-rank width %d exceeds %d (approximate precisions)",
+                        rerank_width(db, table_width(meas, k, (int)h), (int)h), kRerankMax);
     }
     return EMD_OK;
 }
@@ -204,17 +207,33 @@ emd_status run_phase1(emd_db* db, Lane& L, const int32_t* qidx, int h, cudaStrea
         EMD_CUDA(launch_gather_rows(db->emb, db->v, db->ldm, db->m, qidx, h, qrows, L.Q, L.qnorm,
                                     db->err, st), "query gather");
         if (db->tc)
-            EMD_CUDA(launch_pack_f16(L.Q, db->ldm, db->m, h, round_up(h, 128), db->kpad, L.q_hi, L.q_lo,
-                                     L.q_scale, st), "query pack");
+            EMD_CUDA(launch_pack(db->tcfmt, L.Q, db->ldm, db->m, h, round_up(h, 128), db->kpad, L.q_hi,
+                                 db->tcfmt == TC_SPLIT ? L.q_lo : nullptr, L.q_scale, st), "query pack");
     }
     Phase p(db, 1, 1, st);
     if (db->tc)
-        EMD_CUDA(launch_tc_dist(true, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used, db->used_ids,
-                                db->v_used, L.q_hi, L.q_lo, round_up(h, 128), L.q_scale, L.qnorm, qidx,
-                                h, db->kpad, L.D, ldd, db->err, st), "distance matrix (tensor cores)");
+        EMD_CUDA(launch_tc_dist(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used, db->used_ids,
+                                db->v_used, L.q_hi, db->tcfmt == TC_SPLIT ? L.q_lo : nullptr, round_up(h, 128),
+                                L.q_scale, L.qnorm, qidx, h, db->kpad, L.D, ldd, db->err, st),
+                 "distance matrix (tensor cores)");
     else
         EMD_CUDA(launch_dist_fp32(db->emb_used, db->v_used, db->ldm, db->norm_used, db->used_ids, L.Q, h,
                                   db->ldm, L.qnorm, qidx, db->m, L.D, ldd, st), "distance matrix");
+    return EMD_OK;
+}
+
+int rerank_width(const emd_db* db, int tk, int h) { return std::min(tk + db->margin, h); }
+
+// The Phase-1 table of width tk from lane L's D (re-ranked for the approximate precisions).
+emd_status run_table(emd_db* db, Lane& L, const float* qw, int h, int tk, int32_t* tab_s, cudaStream_t st)
+{
+    const int ldd = (int)round_up(h, 32);
+    Phase p(db, 2, 1, st);
+    if (db->approx)
+        EMD_CUDA(launch_table_rerank(L.D, ldd, db->v_used, h, tk, rerank_width(db, tk, h), db->emb_used, L.Q,
+                                     db->ldm, qw, L.tab, tab_s, st), "top-k table (re-ranked)");
+    else
+        EMD_CUDA(launch_table(L.D, ldd, db->v_used, h, tk, qw, L.tab, tab_s, st), "top-k table");
     return EMD_OK;
 }
 
@@ -228,10 +247,8 @@ emd_status run_query(emd_db* db, Lane& L, const int32_t* qidx, const float* qw, 
     const int ldd = (int)round_up(h, 32);
     if (dir != EMD_DIR_REV) {
         const int tk = table_width(meas, k, h);
-        {
-            Phase p(db, 2, 1, st);
-            EMD_CUDA(launch_table(L.D, ldd, db->v_used, h, tk, qw, L.tab, nullptr, st), "top-k table");
-        }
+        emd_status s1 = run_table(db, L, qw, h, tk, nullptr, st);
+        if (s1 != EMD_OK) return s1;
         Phase p(db, 3, 1, st);
         EMD_CUDA(launch_fwd(meas, db->row_ptr, db->col, db->val, db->n, L.tab, tk, tk,
                             dir == EMD_DIR_FWD ? out_t : L.t_fwd, st), "forward pass");
@@ -261,10 +278,8 @@ emd_status run_topk_pruned(emd_db* db, Lane& L, const int32_t* qidx, const float
     if (s != EMD_OK) return s;
     const int ldd = (int)round_up(h, 32);
     const int tk = table_width(meas, k, h);
-    {
-        Phase p(db, 2, 1, st);
-        EMD_CUDA(launch_table(L.D, ldd, db->v_used, h, tk, qw, L.tab, nullptr, st), "top-k table");
-    }
+    s = run_table(db, L, qw, h, tk, nullptr, st);
+    if (s != EMD_OK) return s;
     {
         Phase p(db, 3, 1, st);
         EMD_CUDA(launch_fwd(meas, db->row_ptr, db->col, db->val, db->n, L.tab, tk, tk, L.t_fwd, st),
@@ -442,8 +457,10 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
     if (emb && (m < 1 || m > 4096)) return fail(EMD_ERR_INVALID_ARG, "m out of range (1..4096)");
     if (n_docs < 1) return fail(EMD_ERR_INVALID_ARG, "n_docs must be >= 1");
     if (!row_ptr || !col || !val) return fail(EMD_ERR_INVALID_ARG, "CSR arrays must be non-NULL");
-    if (opt.precision != EMD_PREC_FP32 && opt.precision != EMD_PREC_FP32_TC)
-        return fail(EMD_ERR_UNSUPPORTED, "precision %d is not available in this build", (int)opt.precision);
+    if (opt.precision < EMD_PREC_FP32 || opt.precision > EMD_PREC_FP32_TC)
+        return fail(EMD_ERR_INVALID_ARG, "unknown precision %d", (int)opt.precision);
+    if (opt.rerank_margin < 0 || opt.rerank_margin > kRerankMax)
+        return fail(EMD_ERR_INVALID_ARG, "rerank_margin must be 0..%d", kRerankMax);
     if (opt.max_query_h < 1 || opt.max_query_h > (1 << 16) || opt.max_table_k < 1 ||
         opt.max_table_k > (1 << 16) || opt.max_batch < 1 || opt.max_batch > 4096 || opt.lanes < 1 ||
         opt.lanes > 16)
@@ -490,6 +507,7 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
     emd_db* db = new emd_db();
     db->opt = opt;
     db->dev = opt.device;
+    db->margin = opt.rerank_margin;
     db->v = v;
     db->v_used = (int64_t)used_ids.size();
     db->n = n_docs;
@@ -549,14 +567,19 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
         db->total_launches += 1;
         db->launches[6] += 1;
         db->qrows_max = (int)round_up(round_up(opt.max_query_h, 32), kDistBN);
-        if (opt.precision == EMD_PREC_FP32_TC) {
+        if (opt.precision != EMD_PREC_FP32) {
             db->tc = true;
+            db->tcfmt = opt.precision == EMD_PREC_FP32_TC ? TC_SPLIT
+                        : opt.precision == EMD_PREC_BF16  ? TC_BF16
+                                                          : TC_E4M3;
+            db->approx = db->tcfmt != TC_SPLIT;
             db->kpad = (int)round_up(m, 64);
             db->mpad = round_up(vu, 128);
             TRY(dalloc(db, &db->a_hi, db->mpad * db->kpad));
-            TRY(dalloc(db, &db->a_lo, db->mpad * db->kpad));
+            if (db->tcfmt == TC_SPLIT) TRY(dalloc(db, &db->a_lo, db->mpad * db->kpad));
             TRY(dalloc(db, &db->a_scale, db->mpad));
-            TRYC(launch_pack_f16(db->emb_used, ldm, m, vu, db->mpad, db->kpad, db->a_hi, db->a_lo, db->a_scale, st),
+            TRYC(launch_pack(db->tcfmt, db->emb_used, ldm, m, vu, db->mpad, db->kpad, db->a_hi, db->a_lo,
+                             db->a_scale, st),
                  "embedding pack");
             db->total_launches += 1;
             db->launches[6] += 1;
@@ -571,7 +594,7 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
             TRY(dalloc(db, &L.qnorm, db->qrows_max));
             if (db->tc) {
                 TRY(dalloc(db, &L.q_hi, npad * db->kpad));
-                TRY(dalloc(db, &L.q_lo, npad * db->kpad));
+                if (db->tcfmt == TC_SPLIT) TRY(dalloc(db, &L.q_lo, npad * db->kpad));
                 TRY(dalloc(db, &L.q_scale, npad));
             }
         }
@@ -736,10 +759,10 @@ emd_status emd_phase1_table(emd_db* db, const int32_t* q_idx, const float* q_w, 
     const int ldd = (int)round_up(h_q, 32);
     s = run_phase1(db, L, db->stage_idx, h_q, st);
     if (s != EMD_OK) return s;
-    {
-        Phase p(db, 2, 1, st);
-        EMD_CUDA(launch_table(L.D, ldd, db->v_used, h_q, k, db->stage_w, L.tab, db->tab_s, st), "table");
-    }
+    if (db->approx && rerank_width(db, k, h_q) > kRerankMax)
+        return fail(EMD_ERR_UNSUPPORTED, "re-rank width %d exceeds %d", rerank_width(db, k, h_q), kRerankMax);
+    s = run_table(db, L, db->stage_w, h_q, k, db->tab_s, st);
+    if (s != EMD_OK) return s;
     const int64_t cnt = db->v_used * k;
     std::vector<float2> tz((size_t)cnt);
     EMD_CUDA(cudaMemcpyAsync(tz.data(), L.tab, cnt * sizeof(float2), cudaMemcpyDeviceToHost, st), "copy");

@@ -66,12 +66,15 @@ struct emd_db {
     float* val = nullptr;        // nnz
     int* err = nullptr;
 
-    // tensor-core operands of the used vocabulary (precision EMD_PREC_FP32_TC)
+    // tensor-core operands of the used vocabulary (precisions FP32_TC, BF16, FP8_E4M3)
     bool tc = false;
+    int tcfmt = -1;              // TC_SPLIT, TC_BF16, TC_E4M3 (TC_NONE: SIMT FP32)
+    bool approx = false;         // BF16 / E4M3: the table re-ranks with exact FP32 distances
+    int margin = 8;              // re-rank candidates beyond k
     int kpad = 0;
     int64_t mpad = 0;
-    __half* a_hi = nullptr;      // mpad x kpad packed panels
-    __half* a_lo = nullptr;
+    __half* a_hi = nullptr;      // mpad x kpad packed panels (2-byte elements; E4M3 uses half the bytes)
+    __half* a_lo = nullptr;      // TC_SPLIT only
     float* a_scale = nullptr;    // mpad
 
     // per-lane workspace
@@ -112,6 +115,8 @@ struct emd_db {
 namespace emd {
 
 int table_width(int meas, int k, int h);
+// Candidates per row re-ranked by the table kernel of the approximate precisions.
+int rerank_width(const emd_db* db, int tk, int h);
 emd_status check_query_values(const emd_db* db, const emd_queries* q);
 bool prunable(const emd_db* db, int meas, int k, int dir, int K);
 int topk_launch_count(int64_t n);

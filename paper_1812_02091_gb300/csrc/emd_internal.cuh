@@ -108,20 +108,36 @@ cudaError_t launch_topk_rows(const float* t, int64_t rows, int64_t n, int64_t ld
                              unsigned long long* scratch, int64_t* out_idx, float* out_dist,
                              cudaStream_t st);
 
-// Tensor-core distance matrix (k_tc_dist.cu).  Operands are FP16 panels in the canonical
-// K-major core-matrix layout (see launch_pack_f16) with Mpad / Npad rows (multiples of 128)
-// and Kpad = m rounded up to 64; split = hi + lo * 2^-11 with three products (FP32-grade),
-// else hi only.  D[u, j] as launch_dist_fp32, +inf for j in [N, ldd).
-cudaError_t launch_tc_dist(bool split, const __half* A_hi, const __half* A_lo, int64_t Mpad, const float* a_scale,
-                           const float* a_norm, const int32_t* a_ids, int64_t M, const __half* B_hi,
-                           const __half* B_lo, int64_t Npad, const float* b_scale, const float* b_norm,
-                           const int32_t* b_ids, int N, int Kpad, float* D, int ldd, int* err, cudaStream_t st);
+// Tensor-core operand formats (k_tc_dist.cu).
+constexpr int TC_NONE = -1;
+constexpr int TC_SPLIT = 0;  // FP16 hi + lo * 2^-11, three products: FP32-grade
+constexpr int TC_BF16 = 1;   // BF16, one product: approximate
+constexpr int TC_E4M3 = 2;   // FP8 E4M3, one product: approximate
 
-// Pack R rows of an FP32 matrix (ld floats per row, m used) into FP16 panels of Rpad rows
-// and Kpad columns with per-row absmax scales; lo (may be null) receives the scaled
-// remainder (x/s - hi) * 2^11.
-cudaError_t launch_pack_f16(const float* src, int ld, int m, int64_t R, int64_t Rpad, int Kpad, __half* hi,
-                            __half* lo, float* scale, cudaStream_t st);
+// Tensor-core distance matrix.  Operands are panels in the canonical K-major core-matrix
+// layout (see launch_pack) with Mpad / Npad rows (multiples of 128) and Kpad = m rounded
+// up to 64; A_lo / B_lo only for TC_SPLIT.  D[u, j] as launch_dist_fp32, +inf for j in
+// [N, ldd).
+cudaError_t launch_tc_dist(int fmt, const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
+                           const float* a_norm, const int32_t* a_ids, int64_t M, const void* B_hi, const void* B_lo,
+                           int64_t Npad, const float* b_scale, const float* b_norm, const int32_t* b_ids, int N,
+                           int Kpad, float* D, int ldd, int* err, cudaStream_t st);
+
+// Pack R rows of an FP32 matrix (ld floats per row, m used) into format `fmt` panels of
+// Rpad rows and Kpad columns with per-row scales (x = scale * stored); lo (TC_SPLIT only,
+// may be null) receives the scaled remainder (x/s - hi) * 2^11.  Panel bytes: Rpad * Kpad
+// * (2 for FP16/BF16, 1 for E4M3) per part.
+cudaError_t launch_pack(int fmt, const float* src, int ld, int m, int64_t R, int64_t Rpad, int Kpad, void* hi,
+                        void* lo, float* scale, cudaStream_t st);
+
+// Table from an approximate D: per row the kc smallest approximate values are re-ranked
+// with exact FP32 distances sqrt(sum (V_u - Q_j)^2) (V: M rows, Q: h rows, both ldv floats
+// per row, zero beyond m), which are also written back into D; then the k smallest exact
+// values form the table (as launch_table).  k <= kc <= min(h, kRerankMax).
+constexpr int kRerankMax = 32;
+cudaError_t launch_table_rerank(float* D, int ldd, int64_t M, int h, int k, int kc, const float* V,
+                                const float* Q, int ldv, const float* q_w, float2* tab, int32_t* tab_s,
+                                cudaStream_t st);
 
 // Failure message for emd_last_error() (defined beside the C ABI).
 emd_status set_error(emd_status st, const char* msg);

@@ -116,7 +116,7 @@ int64_t layout(const emd_db* db, int h, int tk, char* base, ReqDev* r)
         take(&d.L.qnorm, (int64_t)qrows * 4);
         if (db->tc) {
             take(&d.L.q_hi, npad * db->kpad * 2);
-            take(&d.L.q_lo, npad * db->kpad * 2);
+            if (db->tcfmt == TC_SPLIT) take(&d.L.q_lo, npad * db->kpad * 2);
             take(&d.L.q_scale, npad * 4);
         }
     }
@@ -475,6 +475,8 @@ emd_status emd_server_submit(emd_server* s, const int32_t* idx, const float* w, 
     const int tk = table_width(meas, k, h_q);
     if (tk > db->opt.max_table_k)
         return fail(EMD_ERR_UNSUPPORTED, "forward table width %d exceeds max_table_k %d", tk, db->opt.max_table_k);
+    if (db->approx && rerank_width(db, tk, h_q) > kRerankMax)
+        return fail(EMD_ERR_UNSUPPORTED, "re-rank width %d exceeds %d", rerank_width(db, tk, h_q), kRerankMax);
     emd_status st = check_bins(db, idx, w, h_q);
     if (st != EMD_OK) return st;
     auto r = std::make_unique<Request>();

@@ -278,6 +278,101 @@ __global__ void k_table_generic(const float* __restrict__ D, int ldd, int64_t M,
     }
 }
 
+// Re-rank form of the table, for approximate distance matrices (BF16 / E4M3 Phase 1).
+// Per vocabulary row u: the kc smallest approximate D[u, .] (ties: lower j) are the
+// candidates; their distances are recomputed exactly in FP32 as sqrt(sum_i (V_u,i -
+// Q_j,i)^2) -- differences, not the norm expansion -- and written back into D; the k
+// smallest exact values (ties: lower j) form the table.  Selection runs one thread per
+// row, the recomputation one warp per row (lanes over float4 slices of the embedding;
+// rows are zero beyond m, so the padded width adds nothing).
+template <int KCT>
+__device__ __forceinline__ void insert_dj_tie(float (&z)[KCT], int (&s)[KCT], float d, int j)
+{
+    bool p[KCT];
+#pragma unroll
+    for (int l = 0; l < KCT; ++l) p[l] = d < z[l] || (d == z[l] && j < s[l]);
+#pragma unroll
+    for (int l = KCT - 1; l > 0; --l) {
+        z[l] = p[l - 1] ? z[l - 1] : (p[l] ? d : z[l]);
+        s[l] = p[l - 1] ? s[l - 1] : (p[l] ? j : s[l]);
+    }
+    z[0] = p[0] ? d : z[0];
+    s[0] = p[0] ? j : s[0];
+}
+
+template <int KCT>
+__global__ void __launch_bounds__(128)
+k_table_rerank(float* __restrict__ D, int ldd, int64_t M, int h, int k, int kc, const float* __restrict__ V,
+               const float* __restrict__ Q, int ldv, const float* __restrict__ q_w, float2* __restrict__ tab,
+               int32_t* __restrict__ tab_s)
+{
+    __shared__ int cj[128][KCT + 1];
+    __shared__ float cz[128][KCT + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t row = (int64_t)blockIdx.x * 128 + tid;
+    {
+        float z[KCT];
+        int s[KCT];
+#pragma unroll
+        for (int l = 0; l < KCT; ++l) { z[l] = INFINITY; s[l] = INT32_MAX; }
+        if (row < M) {
+            const float* Dr = D + row * ldd;
+            for (int j = 0; j < h; j += 4) {
+                const float4 v = *reinterpret_cast<const float4*>(Dr + j);
+                insert_dj<KCT>(z, s, v.x, j);
+                if (j + 1 < h) insert_dj<KCT>(z, s, v.y, j + 1);
+                if (j + 2 < h) insert_dj<KCT>(z, s, v.z, j + 2);
+                if (j + 3 < h) insert_dj<KCT>(z, s, v.w, j + 3);
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < KCT; ++l) cj[tid][l] = s[l];
+    }
+    __syncwarp();
+    const int nv4 = ldv >> 2;
+    for (int r = 0; r < 32; ++r) {
+        const int64_t ur = (int64_t)blockIdx.x * 128 + warp * 32 + r;
+        if (ur >= M) break;  // uniform over the warp
+        const float4* vr = reinterpret_cast<const float4*>(V + ur * ldv);
+        for (int c = 0; c < kc; ++c) {
+            const int j = cj[warp * 32 + r][c];
+            const float4* qr = reinterpret_cast<const float4*>(Q + (int64_t)j * ldv);
+            float acc = 0.f;
+            for (int i = lane; i < nv4; i += 32) {
+                const float4 a = vr[i], b = qr[i];
+                const float t0 = a.x - b.x, t1 = a.y - b.y, t2 = a.z - b.z, t3 = a.w - b.w;
+                acc = fmaf(t0, t0, acc);
+                acc = fmaf(t1, t1, acc);
+                acc = fmaf(t2, t2, acc);
+                acc = fmaf(t3, t3, acc);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) cz[warp * 32 + r][c] = __fsqrt_rn(acc);
+        }
+    }
+    __syncwarp();
+    if (row >= M) return;
+    float z[KCT];
+    int s[KCT];
+#pragma unroll
+    for (int l = 0; l < KCT; ++l) { z[l] = INFINITY; s[l] = INT32_MAX; }
+    for (int c = 0; c < kc; ++c) {
+        const float d = cz[tid][c];
+        const int j = cj[tid][c];
+        D[row * ldd + j] = d;
+        insert_dj_tie<KCT>(z, s, d, j);
+    }
+#pragma unroll
+    for (int l = 0; l < KCT; ++l) {
+        if (l < k) {
+            const bool valid = s[l] != INT32_MAX;
+            tab[row * k + l] = make_float2(valid ? z[l] : INFINITY, valid ? q_w[s[l]] : 0.f);
+            if (tab_s) tab_s[row * k + l] = valid ? s[l] : -1;
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_gather_rows(const float* src, int64_t v, int ld, int m, const int32_t* ids,
@@ -326,6 +421,23 @@ cudaError_t launch_table(const float* D, int ldd, int64_t M, int h, int k, const
         dim3 grid((unsigned)((M + warps - 1) / warps));
         k_table_generic<<<grid, warps * 32, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
     }
+    return cudaGetLastError();
+}
+
+}  // namespace emd
+
+namespace emd {
+
+cudaError_t launch_table_rerank(float* D, int ldd, int64_t M, int h, int k, int kc, const float* V,
+                                const float* Q, int ldv, const float* q_w, float2* tab, int32_t* tab_s,
+                                cudaStream_t st)
+{
+    if (M <= 0) return cudaSuccess;
+    if (k < 1 || kc < k || kc > h || kc > kRerankMax) return cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)((M + 127) / 128);
+    if (kc <= 8) k_table_rerank<8><<<grid, 128, 0, st>>>(D, ldd, M, h, k, kc, V, Q, ldv, q_w, tab, tab_s);
+    else if (kc <= 16) k_table_rerank<16><<<grid, 128, 0, st>>>(D, ldd, M, h, k, kc, V, Q, ldv, q_w, tab, tab_s);
+    else k_table_rerank<32><<<grid, 128, 0, st>>>(D, ldd, M, h, k, kc, V, Q, ldv, q_w, tab, tab_s);
     return cudaGetLastError();
 }
 

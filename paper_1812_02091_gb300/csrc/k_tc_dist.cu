@@ -2,26 +2,33 @@
 // distance matrix D = dist(V, Q) from the product V Q^T (Section 4: "a matrix-matrix
 // multiplication between V and the transpose of Q") with FP32 accumulators in TMEM.
 //
-// Operands are FP16 with a per-row absmax scale.  In the split form every operand is held
-// as hi + lo * 2^-11 (hi = fp16(x/s), lo = fp16((x/s - hi) * 2^11)) and three products
-// hi*hi (accumulator 0) and hi*lo + lo*hi (accumulator 1) reconstruct the dot product to
-// about 2^-22 relative: FP32-grade distances on the tensor pipe.  The plain form uses the
-// hi parts only.
+// Operands carry a per-row absmax scale s (x = s * stored value).  Three operand formats:
+//  * TC_SPLIT: FP16 hi + lo * 2^-11 (hi = fp16(x/s), lo = fp16((x/s - hi) * 2^11)); three
+//    products hi*hi (accumulator 0) and hi*lo + lo*hi (accumulator 1) reconstruct the dot
+//    product to about 2^-22 relative: FP32-grade distances on the tensor pipe (kind::f16).
+//  * TC_BF16: bf16(x/s), one product (kind::f16 with BF16 inputs).
+//  * TC_E4M3: e4m3(448 x / amax), s = amax / 448, one product (kind::f8f6f4).
+// The BF16 and E4M3 distances are approximate; the top-k table kernel re-ranks each row's
+// candidates with exact FP32 sums of squared differences.
 //
 // Data movement: both operands are pre-packed in global memory in the canonical K-major,
-// no-swizzle UMMA layout -- 8x8 core matrices of 128 contiguous bytes; inside a 64-element
-// K chunk the 8 core matrices of a row group are adjacent (leading byte offset 128 B) and
-// row groups follow each other 1 KB apart (stride byte offset).  A tile's K chunk is
+// no-swizzle UMMA layout -- core matrices of 8 rows x 16 bytes (128 contiguous bytes);
+// inside a 64-element K chunk the core matrices of a row group are adjacent (leading byte
+// offset 128 B) and row groups follow each other 8 x (bytes of a 64-element row segment)
+// apart (stride byte offset: 1 KB for 2-byte types, 512 B for E4M3).  A tile's K chunk is
 // therefore one contiguous block and moves with one 1-D bulk copy (cp.async.bulk, the TMA
 // engine) completing on an mbarrier.
 //
 // Roles (320 threads, one persistent CTA per SM): warp 0 lane 0 issues the copies into a
 // ring of stages; warp 1 allocates TMEM and its lane 0 issues tcgen05.mma (M = 128 rows of
-// V, N <= 128 query columns, K = 16 per instruction) and tcgen05.commit; warps 2..9 read
+// V, N <= 128 query columns, K = 16 (32 for E4M3) per instruction) and tcgen05.commit;
+// warps 2..9 read
 // their TMEM lane quarter with tcgen05.ld and write d = sqrt(max(|v|^2 + |q|^2 - 2 v.q, 0)),
 // exactly 0 for identical vocabulary ids.  Every wait is bounded in time; a timeout
 // latches ERR_TIMEOUT, raises a block-wide abort flag and the block tears down.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <math.h>
 
 #include <algorithm>
@@ -34,9 +41,14 @@ namespace {
 constexpr int TC_BM = 128;          // rows per tile = TMEM lanes
 constexpr int TC_BN = 128;          // largest column tile
 constexpr int TC_THREADS = 320;  // warp 0 copies, warp 1 MMA, warps 2..9 epilogue
-constexpr uint32_t TC_A_BYTES = TC_BM * 128;  // one 64-wide K chunk of 128 rows
-constexpr uint32_t TC_B_BYTES = TC_BN * 128;
 constexpr uint64_t TC_TIMEOUT_NS = 2000000000ull;
+
+// Per-format constants: bytes of a 64-element row segment, operand parts, MMAs per
+// 64-element chunk (each advances 2 core matrices = 256 B along K).
+template <int FMT> struct TcFmt;
+template <> struct TcFmt<TC_SPLIT> { static constexpr uint32_t EB = 128, parts = 2, mmas = 4, atype = 0; };
+template <> struct TcFmt<TC_BF16> { static constexpr uint32_t EB = 128, parts = 1, mmas = 4, atype = 1; };
+template <> struct TcFmt<TC_E4M3> { static constexpr uint32_t EB = 64, parts = 1, mmas = 2, atype = 0; };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -113,28 +125,38 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
 }
 
 // Shared-memory matrix descriptor: canonical K-major layout without swizzle, leading
-// byte offset 128 (next core matrix along K), stride byte offset 1024 (next 8-row group),
+// byte offset 128 (next core matrix along K), stride byte offset `sbo` (next 8-row group),
 // descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t sbo)
 {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
     d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;
     return d;
 }
 
-// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (FP16 inputs, FP32 accumulate).
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                        uint32_t accumulate)
+// D[tmem] (+)= A[smem] * B[smem]^T with FP32 accumulation: kind::f16 (FP16 or BF16 inputs,
+// both the same type) or kind::f8f6f4 (E4M3 inputs).
+template <int FMT>
+__device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                          uint32_t accumulate)
 {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-        : "memory");
+    if (FMT == TC_E4M3)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+            : "memory");
 }
 
 // Arrive on the mbarrier once every tcgen05.mma issued so far by this thread is done.
@@ -176,17 +198,22 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 // otherwise concentrate the L2 traffic on a few slices.  The accumulators alternate
 // between two TMEM buffers, so the MMA warp fills one while the eight epilogue warps drain
 // the other (two warps per TMEM lane quarter, each taking half of the columns).
-template <bool SPLIT>
+template <int FMT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-k_tc_dist(const __half* __restrict__ A_hi, const __half* __restrict__ A_lo, int64_t Mpad,
+k_tc_dist(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_lo, int64_t Mpad,
           const float* __restrict__ a_scale, const float* __restrict__ a_norm, const int32_t* __restrict__ a_ids,
-          int64_t M, const __half* __restrict__ B_hi, const __half* __restrict__ B_lo, int64_t Npad,
+          int64_t M, const uint8_t* __restrict__ B_hi, const uint8_t* __restrict__ B_lo, int64_t Npad,
           const float* __restrict__ b_scale, const float* __restrict__ b_norm, const int32_t* __restrict__ b_ids,
           int N, int KC, int stages, float* __restrict__ D, int ldd, int* __restrict__ err)
 {
-    constexpr int kParts = SPLIT ? 2 : 1;
-    constexpr uint32_t kStage = kParts * TC_A_BYTES;               // vocabulary chunk: hi (and lo)
-    constexpr uint32_t kBChunk = kParts * TC_B_BYTES;              // query chunk: hi (and lo)
+    constexpr bool SPLIT = FMT == TC_SPLIT;
+    constexpr uint32_t EB = TcFmt<FMT>::EB;
+    constexpr int kParts = (int)TcFmt<FMT>::parts;
+    constexpr uint32_t kABytes = TC_BM * EB;                       // one 64-element K chunk of 128 rows
+    constexpr uint32_t kBBytes = TC_BN * EB;
+    constexpr uint32_t kSbo = 8 * EB;
+    constexpr uint32_t kStage = kParts * kABytes;                  // vocabulary chunk: hi (and lo)
+    constexpr uint32_t kBChunk = kParts * kBBytes;                 // query chunk: hi (and lo)
     constexpr uint32_t kAcc = SPLIT ? 256 : 128;  // TMEM columns per accumulator buffer (acc0 | acc1)
     constexpr uint32_t kCols = 2 * kAcc;
     extern __shared__ uint8_t smem_raw[];
@@ -245,12 +272,12 @@ k_tc_dist(const __half* __restrict__ A_hi, const __half* __restrict__ A_lo, int6
                 }
                 const int n0 = nt * TC_BN;
                 const int Nt = min(TC_BN, (int)round_up(N - n0, 16));
-                const uint32_t b_bytes = (uint32_t)Nt * 128u;
+                const uint32_t b_bytes = (uint32_t)Nt * EB;
                 mbar_expect_tx(bfull, (uint32_t)(kParts * KC) * b_bytes);
                 for (int c = 0; c < KC; ++c) {
                     uint8_t* bst = bpanel + (size_t)c * kBChunk;
-                    bulk_g2s(bst, B_hi + ((int64_t)c * Npad + n0) * 64, b_bytes, bfull);
-                    if (SPLIT) bulk_g2s(bst + TC_B_BYTES, B_lo + ((int64_t)c * Npad + n0) * 64, b_bytes, bfull);
+                    bulk_g2s(bst, B_hi + ((int64_t)c * Npad + n0) * EB, b_bytes, bfull);
+                    if (SPLIT) bulk_g2s(bst + kBBytes, B_lo + ((int64_t)c * Npad + n0) * EB, b_bytes, bfull);
                 }
                 cur_n = nt;
                 ++reloads;
@@ -263,8 +290,8 @@ k_tc_dist(const __half* __restrict__ A_hi, const __half* __restrict__ A_lo, int6
                 }
                 uint8_t* st = smem + (size_t)s * kStage;
                 mbar_expect_tx(&full[s], kStage);
-                bulk_g2s(st, A_hi + ((int64_t)c * Mpad + m0) * 64, TC_A_BYTES, &full[s]);
-                if (SPLIT) bulk_g2s(st + TC_A_BYTES, A_lo + ((int64_t)c * Mpad + m0) * 64, TC_A_BYTES, &full[s]);
+                bulk_g2s(st, A_hi + ((int64_t)c * Mpad + m0) * EB, kABytes, &full[s]);
+                if (SPLIT) bulk_g2s(st + kABytes, A_lo + ((int64_t)c * Mpad + m0) * EB, kABytes, &full[s]);
             }
         }
         // no copy may still be landing in shared memory when the block leaves
@@ -273,15 +300,16 @@ k_tc_dist(const __half* __restrict__ A_hi, const __half* __restrict__ A_lo, int6
             if (!mbar_wait(&full[c % stages], (uint32_t)(c / stages) & 1u, tail)) atomicOr(err, ERR_TIMEOUT);
         if (reloads > 0 && !mbar_wait(bfull, (uint32_t)(reloads - 1) & 1u, tail)) atomicOr(err, ERR_TIMEOUT);
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer: kind::f16, D format F32 (bit 4), A/B format F16 (0), K-major A and B,
-        // N >> 3 at bit 17, M >> 4 at bit 24
+        // MMA issuer: D format F32 (bit 4), A/B format at bits 7 and 10 (F16 or E4M3 = 0,
+        // BF16 = 1), K-major A and B, N >> 3 at bit 17, M >> 4 at bit 24
         int64_t g = 0;
         int it = 0, cur_n = -1, reloads = 0;
         for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++it) {
             const int nt = t / m_tiles;
             const int n0 = nt * TC_BN;
             const int Nt = min(TC_BN, (int)round_up(N - n0, 16));
-            const uint32_t idesc = (1u << 4) | ((uint32_t)(Nt >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+            const uint32_t idesc = (1u << 4) | (TcFmt<FMT>::atype << 7) | (TcFmt<FMT>::atype << 10) |
+                                   ((uint32_t)(Nt >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
             if (nt != cur_n) {
                 if (reloads > 0) mma_commit(bfree);  // the old panel is released once its MMAs finish
                 if (!mbar_wait(bfull, (uint32_t)reloads & 1u, global_ns() + TC_TIMEOUT_NS)) {
@@ -308,18 +336,18 @@ k_tc_dist(const __half* __restrict__ A_hi, const __half* __restrict__ A_lo, int6
                 }
                 tc_fence_after();
                 const uint32_t sa = smem_u32(smem + (size_t)s * kStage);
-                const uint32_t sa_lo = sa + TC_A_BYTES;
+                const uint32_t sa_lo = sa + kABytes;
                 const uint32_t sb = smem_u32(bpanel + (size_t)c * kBChunk);
-                const uint32_t sb_lo = sb + TC_B_BYTES;
+                const uint32_t sb_lo = sb + kBBytes;
 #pragma unroll
-                for (int ks = 0; ks < 4; ++ks) {  // 4 x K=16 per 64-wide chunk: 2 core matrices = 256 B
+                for (int ks = 0; ks < (int)TcFmt<FMT>::mmas; ++ks) {  // each MMA: 2 core matrices = 256 B of K
                     const uint32_t ko = (uint32_t)ks * 256u;
                     const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
-                    const uint64_t da = smem_desc(sa + ko), db = smem_desc(sb + ko);
-                    mma_f16(acc0, da, db, idesc, acc);
+                    const uint64_t da = smem_desc(sa + ko, kSbo), db = smem_desc(sb + ko, kSbo);
+                    mma_issue<FMT>(acc0, da, db, idesc, acc);
                     if (SPLIT) {
-                        mma_f16(acc0 + 128, da, smem_desc(sb_lo + ko), idesc, acc);
-                        mma_f16(acc0 + 128, smem_desc(sa_lo + ko), db, idesc, 1u);
+                        mma_issue<FMT>(acc0 + 128, da, smem_desc(sb_lo + ko, kSbo), idesc, acc);
+                        mma_issue<FMT>(acc0 + 128, smem_desc(sa_lo + ko, kSbo), db, idesc, 1u);
                     }
                 }
                 mma_commit(&empty[s]);
@@ -397,11 +425,14 @@ k_tc_dist(const __half* __restrict__ A_hi, const __half* __restrict__ A_lo, int6
 }
 
 // Pack rows of an FP32 matrix (ld floats per row, first m used) into the canonical layout
-// above: element (r, k) of a matrix with Rpad rows lives at half offset
-// (k/64)*Rpad*64 + (r/8)*512 + ((k%64)/8)*64 + (r%8)*8 + k%8.  One warp per row; rows
-// R..Rpad-1 and columns m..Kpad-1 are zero.  scale[r] = max |x| (0 for a zero row).
-__global__ void k_pack_f16(const float* __restrict__ src, int ld, int m, int64_t R, int64_t Rpad, int Kpad,
-                           __half* __restrict__ hi, __half* __restrict__ lo, float* __restrict__ scale)
+// above.  For 2-byte formats element (r, k) of a matrix with Rpad rows lives at byte
+// 2 * ((k/64)*Rpad*64 + (r/8)*512 + ((k%64)/8)*64 + (r%8)*8 + k%8); for E4M3 at byte
+// (k/64)*Rpad*64 + (r/8)*512 + ((k%64)/16)*128 + (r%8)*16 + k%16.  One warp per row; rows
+// R..Rpad-1 and columns m..Kpad-1 are zero.  scale[r]: the factor that turns stored
+// values back into x (amax for FP16/BF16, amax / 448 for E4M3; 0 for a zero row).
+template <int FMT>
+__global__ void k_pack(const float* __restrict__ src, int ld, int m, int64_t R, int64_t Rpad, int Kpad,
+                       uint8_t* __restrict__ hi, uint8_t* __restrict__ lo, float* __restrict__ scale)
 {
     const int lane = threadIdx.x & 31;
     const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -412,24 +443,35 @@ __global__ void k_pack_f16(const float* __restrict__ src, int ld, int m, int64_t
         for (int k = lane; k < m; k += 32) amax = fmaxf(amax, fabsf(src[r * ld + k]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    const float inv = amax > 0.f ? 1.0f / amax : 0.f;
-    const int64_t rbase = (r >> 3) * 512 + (r & 7) * 8;
+    constexpr float kTop = FMT == TC_E4M3 ? 448.0f : 1.0f;  // largest stored magnitude
+    const float inv = amax > 0.f ? kTop / amax : 0.f;
     for (int k = lane; k < Kpad; k += 32) {
         const float y = (live && k < m) ? src[r * ld + k] * inv : 0.f;
-        const __half h = __float2half_rn(y);
-        const int64_t off = (int64_t)(k >> 6) * Rpad * 64 + rbase + ((k & 63) >> 3) * 64 + (k & 7);
-        hi[off] = h;
-        if (lo) lo[off] = __float2half_rn((y - __half2float(h)) * 2048.0f);
+        const int64_t chunk = (int64_t)(k >> 6) * Rpad * 64;
+        if (FMT == TC_E4M3) {
+            const int64_t off = chunk + (r >> 3) * 512 + ((k & 63) >> 4) * 128 + (r & 7) * 16 + (k & 15);
+            hi[off] = (uint8_t)__nv_cvt_float_to_fp8(y, __NV_SATFINITE, __NV_E4M3);
+        } else {
+            const int64_t off = chunk + (r >> 3) * 512 + ((k & 63) >> 3) * 64 + (r & 7) * 8 + (k & 7);
+            if (FMT == TC_BF16) {
+                reinterpret_cast<__nv_bfloat16*>(hi)[off] = __float2bfloat16_rn(y);
+            } else {
+                const __half h = __float2half_rn(y);
+                reinterpret_cast<__half*>(hi)[off] = h;
+                if (lo) reinterpret_cast<__half*>(lo)[off] = __float2half_rn((y - __half2float(h)) * 2048.0f);
+            }
+        }
     }
-    if (lane == 0) scale[r] = amax;
+    if (lane == 0) scale[r] = amax / kTop;
 }
 
 }  // namespace
 
-size_t tc_dist_smem_bytes(bool split, int stages, int KC)
+size_t tc_dist_smem_bytes(int fmt, int stages, int KC)
 {
-    const size_t parts = split ? 2 : 1;
-    return 1024 + (size_t)stages * parts * TC_A_BYTES + (size_t)KC * parts * TC_B_BYTES +
+    const size_t eb = fmt == TC_E4M3 ? 64 : 128;
+    const size_t parts = fmt == TC_SPLIT ? 2 : 1;
+    return 1024 + (size_t)stages * parts * TC_BM * eb + (size_t)KC * parts * TC_BN * eb +
            (2 * (size_t)stages + 6) * 8 + 16;
 }
 
@@ -444,52 +486,73 @@ int sm_count()
     return n;
 }
 
-// Vocabulary stages that fit beside the resident query panel (0 when the panel alone
-// does not leave room for two stages).
-int tc_dist_stages(bool split, int KC)
+// Vocabulary stages (2..8) that fit beside the resident query panel (0 when the panel
+// alone does not leave room for two stages).
+int tc_dist_stages(int fmt, int KC)
 {
     const size_t budget = 227 * 1024;
-    int s = 4;
-    while (s >= 2 && tc_dist_smem_bytes(split, s, KC) > budget) --s;
+    int s = 8;
+    while (s >= 2 && tc_dist_smem_bytes(fmt, s, KC) > budget) --s;
     return s >= 2 ? s : 0;
 }
 
-cudaError_t launch_pack_f16(const float* src, int ld, int m, int64_t R, int64_t Rpad, int Kpad, __half* hi,
-                            __half* lo, float* scale, cudaStream_t st)
+cudaError_t launch_pack(int fmt, const float* src, int ld, int m, int64_t R, int64_t Rpad, int Kpad, void* hi,
+                        void* lo, float* scale, cudaStream_t st)
 {
     if (Rpad <= 0) return cudaSuccess;
     const int warps = 8;
-    k_pack_f16<<<(unsigned)((Rpad + warps - 1) / warps), warps * 32, 0, st>>>(src, ld, m, R, Rpad, Kpad, hi, lo,
-                                                                              scale);
+    const unsigned blocks = (unsigned)((Rpad + warps - 1) / warps);
+    uint8_t* h = static_cast<uint8_t*>(hi);
+    uint8_t* l = static_cast<uint8_t*>(lo);
+    switch (fmt) {
+    case TC_SPLIT: k_pack<TC_SPLIT><<<blocks, warps * 32, 0, st>>>(src, ld, m, R, Rpad, Kpad, h, l, scale); break;
+    case TC_BF16: k_pack<TC_BF16><<<blocks, warps * 32, 0, st>>>(src, ld, m, R, Rpad, Kpad, h, nullptr, scale); break;
+    case TC_E4M3: k_pack<TC_E4M3><<<blocks, warps * 32, 0, st>>>(src, ld, m, R, Rpad, Kpad, h, nullptr, scale); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_dist(bool split, const __half* A_hi, const __half* A_lo, int64_t Mpad, const float* a_scale,
-                           const float* a_norm, const int32_t* a_ids, int64_t M, const __half* B_hi,
-                           const __half* B_lo, int64_t Npad, const float* b_scale, const float* b_norm,
-                           const int32_t* b_ids, int N, int Kpad, float* D, int ldd, int* err, cudaStream_t st)
+template <int FMT>
+static cudaError_t tc_launch(dim3 grid, size_t smem, cudaStream_t st, const void* A_hi, const void* A_lo,
+                             int64_t Mpad, const float* a_scale, const float* a_norm, const int32_t* a_ids, int64_t M,
+                             const void* B_hi, const void* B_lo, int64_t Npad, const float* b_scale,
+                             const float* b_norm, const int32_t* b_ids, int N, int KC, int stages, float* D, int ldd,
+                             int* err)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_tc_dist<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_tc_dist<FMT><<<grid, TC_THREADS, smem, st>>>(
+        static_cast<const uint8_t*>(A_hi), static_cast<const uint8_t*>(A_lo), Mpad, a_scale, a_norm, a_ids, M,
+        static_cast<const uint8_t*>(B_hi), static_cast<const uint8_t*>(B_lo), Npad, b_scale, b_norm, b_ids, N, KC,
+        stages, D, ldd, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_dist(int fmt, const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
+                           const float* a_norm, const int32_t* a_ids, int64_t M, const void* B_hi, const void* B_lo,
+                           int64_t Npad, const float* b_scale, const float* b_norm, const int32_t* b_ids, int N,
+                           int Kpad, float* D, int ldd, int* err, cudaStream_t st)
 {
     if (M <= 0 || N <= 0) return cudaSuccess;
     const int KC = Kpad / 64;
-    const int stages = tc_dist_stages(split, KC);
+    const int stages = tc_dist_stages(fmt, KC);
     if (stages < 2) return cudaErrorInvalidValue;  // embeddings wider than the resident panel allows
-    const size_t smem = tc_dist_smem_bytes(split, stages, KC);
+    const size_t smem = tc_dist_smem_bytes(fmt, stages, KC);
     const int64_t tiles = (Mpad / TC_BM) * ((N + TC_BN - 1) / TC_BN);
     dim3 grid((unsigned)std::min<int64_t>(tiles, sm_count()));
-    cudaError_t e;
-    if (split) {
-        e = cudaFuncSetAttribute(k_tc_dist<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_tc_dist<true><<<grid, TC_THREADS, smem, st>>>(A_hi, A_lo, Mpad, a_scale, a_norm, a_ids, M, B_hi, B_lo,
-                                                         Npad, b_scale, b_norm, b_ids, N, KC, stages, D, ldd, err);
-    } else {
-        e = cudaFuncSetAttribute(k_tc_dist<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_tc_dist<false><<<grid, TC_THREADS, smem, st>>>(A_hi, nullptr, Mpad, a_scale, a_norm, a_ids, M, B_hi,
-                                                          nullptr, Npad, b_scale, b_norm, b_ids, N, KC, stages, D,
-                                                          ldd, err);
+    switch (fmt) {
+    case TC_SPLIT:
+        return tc_launch<TC_SPLIT>(grid, smem, st, A_hi, A_lo, Mpad, a_scale, a_norm, a_ids, M, B_hi, B_lo, Npad,
+                                   b_scale, b_norm, b_ids, N, KC, stages, D, ldd, err);
+    case TC_BF16:
+        return tc_launch<TC_BF16>(grid, smem, st, A_hi, nullptr, Mpad, a_scale, a_norm, a_ids, M, B_hi, nullptr,
+                                  Npad, b_scale, b_norm, b_ids, N, KC, stages, D, ldd, err);
+    case TC_E4M3:
+        return tc_launch<TC_E4M3>(grid, smem, st, A_hi, nullptr, Mpad, a_scale, a_norm, a_ids, M, B_hi, nullptr,
+                                  Npad, b_scale, b_norm, b_ids, N, KC, stages, D, ldd, err);
+    default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace emd

@@ -61,7 +61,7 @@ def serve_alone(emd, srv, w, ids, meas, k, K):
     return out
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp32_tc"])
+@pytest.mark.parametrize("precision", ["fp32", "fp32_tc", "bf16", "fp8"])
 def test_alone_equals_mix_equals_topk(emd, work, precision):
     w = work
     db = make_db(emd, w, precision=precision, max_query_h=256)
