@@ -82,9 +82,15 @@ typedef struct {
     int32_t max_table_k;     /* largest forward top-k table width; ICT needs h_q <= this (default 64) */
     int32_t max_batch;       /* queries staged per device pass (default 64) */
     int32_t prune_topk;      /* 1 (default): exact pruned max-direction top-K for K <= 16 */
-    int32_t lanes;           /* concurrent per-query pipelines, each with its own stream and
-                                workspace (default 4, 1..16); a batch's queries are spread over
-                                them and joined back into the caller's stream */
+    int32_t lanes;           /* per-query pipelines, each with its own stream and workspace
+                                (default 1, 1..16); with batched = 0 a batch's queries are spread
+                                over them and joined back into the caller's stream */
+    int32_t batched;         /* 1 (default): each step of a batch is one launch over all its
+                                queries; 0: one query after another on the lanes.  Results are
+                                bit-identical either way */
+    int32_t batch_columns;   /* batched form: distance-matrix columns of one batch (sum over its
+                                queries of h_q rounded up to 32; default 16384, at least
+                                max_query_h).  Device memory: 4 x v_used x batch_columns bytes */
 } emd_db_options;
 
 typedef struct {

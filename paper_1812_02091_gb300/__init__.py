@@ -43,7 +43,8 @@ class emd_db_options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("rerank_margin", ctypes.c_int32), ("max_query_h", ctypes.c_int32),
                 ("max_table_k", ctypes.c_int32), ("max_batch", ctypes.c_int32),
-                ("prune_topk", ctypes.c_int32), ("lanes", ctypes.c_int32)]
+                ("prune_topk", ctypes.c_int32), ("lanes", ctypes.c_int32), ("batched", ctypes.c_int32),
+                ("batch_columns", ctypes.c_int32)]
 
 
 class emd_db_info(ctypes.Structure):

@@ -73,6 +73,10 @@ void release(emd_db* db)
     cudaSetDevice(db->dev);
     cudaDeviceSynchronize();
     for (void* p : db->allocs) cudaFree(p);
+    if (db->qd_host) cudaFreeHost(db->qd_host);
+    if (db->nq_host) cudaFreeHost(db->nq_host);
+    for (auto e : db->desc_ev)
+        if (e) cudaEventDestroy(e);
     for (auto& r : db->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : db->pool) cudaEventDestroy(e);
     for (auto& L : db->lanes) {
@@ -310,11 +314,211 @@ emd_status select_topk(emd_db* db, const float* t, int64_t rows, int K, int64_t*
 // the top-K goes to out_idx / out_dist (rows relative to i0); otherwise the distances go
 // to out_t (rows relative to i0, row stride n).  The pruned path reads its certification
 // flags once (synchronising `st`) and recomputes uncertified queries over all documents.
+emd_status run_lanes(emd_db* db, const int64_t* rp, const int32_t* qidx, const float* qw, int64_t i0,
+                     int64_t i1, int meas, int k, int dir, int K, bool pruned, float* out_t, int64_t* out_idx,
+                     float* out_dist, cudaStream_t st);
+
+// Queries j0..j1-1 of the batch i0.. as one launch per step (the batch fits the batch
+// workspace).  Outputs as run_batch.  Uses descriptor ring slot `slot`.
+emd_status run_subbatch_launch(int slot, emd_db* db, const int64_t* rp, const int32_t* qidx, const float* qw, int64_t i0,
+                        int64_t j0, int64_t j1, int meas, int k, int dir, int K, bool pruned, float* out_t,
+                        int64_t* out_idx, float* out_dist, cudaStream_t st)
+{
+    const int nb = (int)(j1 - j0);
+    QDesc* hd = db->qd_host + (int64_t)slot * db->opt.max_batch;
+    QDesc* dd = db->qd_dev + (int64_t)slot * db->opt.max_batch;
+    int* nqd = db->nq_dev + slot;
+    const int64_t n = db->n;
+    int max_rows = 0, max_npad = 0, max_ldd = 0, max_tk = 0, max_kc = 0;
+    int64_t c_D = 0, c_Q = 0, c_P = 0, c_T = 0;
+    for (int64_t i = j0; i < j1; ++i) {
+        QDesc& d = hd[i - j0];
+        memset(&d, 0, sizeof(d));
+        const int64_t off = rp[i] - rp[i0];
+        const int b = (int)(i - i0);
+        d.h = (int)(rp[i + 1] - rp[i]);
+        d.ldd = (int)round_up(d.h, 32);
+        d.qrows = (int)round_up(d.ldd, kDistBN);
+        d.npad = (int)round_up(d.h, 128);
+        d.tk = dir != EMD_DIR_REV ? table_width(meas, k, d.h) : 0;
+        d.kc = db->approx && d.tk > 0 ? rerank_width(db, d.tk, d.h) : d.tk;
+        d.qidx = qidx + off;
+        d.qw = qw + off;
+        if (!db->cost_mode) {
+            d.Q = db->bQ + c_Q * db->ldm;
+            d.qnorm = db->bqnorm + c_Q;
+            if (db->tc) {
+                d.q_hi = db->bq_hi + c_P * db->kpad;
+                d.q_lo = db->tcfmt == TC_SPLIT ? db->bq_lo + c_P * db->kpad : nullptr;
+                d.q_scale = db->bq_scale + c_P;
+            }
+        }
+        d.D = db->bD + c_D * db->v_used;
+        d.tab = db->btab + c_T * db->v_used;
+        d.t_fwd = db->bt_fwd + (int64_t)b * n;
+        d.t_rev = db->bt_rev + (int64_t)b * n;
+        d.t_out = (K > 0 ? db->stage_out : out_t) + (int64_t)b * n;
+        if (pruned) {
+            d.sel_idx = db->bsel_idx + (int64_t)b * K;
+            d.sel_val = db->bsel_val + (int64_t)b * K;
+            d.cand = db->bcand + (int64_t)b * kPruneCap;
+            d.cand_sym = db->bcand_sym + (int64_t)b * 2 * kPruneCap;
+            d.cand_count = db->bcand_count + b;
+            d.ok = db->cand_ok + b;
+            d.out_idx = out_idx + (int64_t)b * K;
+            d.out_dist = out_dist + (int64_t)b * K;
+        }
+        c_D += d.ldd;
+        c_Q += d.qrows;
+        c_P += d.npad;
+        c_T += d.tk;
+        max_rows = std::max(max_rows, d.qrows);
+        max_npad = std::max(max_npad, d.npad);
+        max_ldd = std::max(max_ldd, d.ldd);
+        max_tk = std::max(max_tk, d.tk);
+        max_kc = std::max(max_kc, d.kc);
+    }
+    db->nq_host[slot] = nb;
+    EMD_CUDA(cudaMemcpyAsync(dd, hd, sizeof(QDesc) * nb, cudaMemcpyHostToDevice, st), "descriptor upload");
+    EMD_CUDA(cudaMemcpyAsync(nqd, db->nq_host + slot, sizeof(int), cudaMemcpyHostToDevice, st), "descriptor upload");
+    const QDesc* D_ = dd;
+    // Phase 1
+    if (db->cost_mode) {
+        Phase p(db, 1, 1, st);
+        EMD_CUDA(launch_dist_gather_b(D_, nqd, nb, db->cost, db->v, db->used_ids, db->v_used, db->err, st),
+                 "distance gather");
+    } else {
+        {
+            Phase p(db, 0, db->tc ? 2 : 1, st);
+            EMD_CUDA(launch_gather_rows_b(D_, nqd, nb, max_rows, db->emb, db->v, db->ldm, db->m, db->err, st),
+                     "query gather");
+            if (db->tc)
+                EMD_CUDA(launch_pack_b(db->tcfmt, D_, nqd, nb, max_npad, db->ldm, db->m, db->kpad, st), "query pack");
+        }
+        if (db->tc) {
+            Phase p(db, 1, nb, st);
+            for (int q = 0; q < nb; ++q) {
+                const QDesc& d = hd[q];
+                EMD_CUDA(launch_tc_dist(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
+                                        db->used_ids, db->v_used, d.q_hi, d.q_lo, d.npad, d.q_scale, d.qnorm, d.qidx,
+                                        d.h, db->kpad, d.D, d.ldd, db->err, st),
+                         "distance matrix (tensor cores)");
+            }
+        } else {
+            Phase p(db, 1, 1, st);
+            EMD_CUDA(launch_dist_fp32_b(D_, nqd, nb, max_ldd, db->emb_used, db->v_used, db->ldm, db->norm_used,
+                                        db->used_ids, db->m, st),
+                     "distance matrix");
+        }
+    }
+    if (dir != EMD_DIR_REV) {
+        {
+            Phase p(db, 2, 1, st);
+            EMD_CUDA(launch_table_b(D_, nqd, nb, db->v_used, max_tk, db->approx, max_kc, db->emb_used, db->ldm, st),
+                     "top-k table");
+        }
+        Phase p(db, 3, 1, st);
+        EMD_CUDA(launch_fwd_b(meas, D_, nqd, nb, db->row_ptr, db->col, db->val, n, dir == EMD_DIR_FWD, st),
+                 "forward pass");
+    }
+    if (pruned) {
+        {
+            Phase p(db, 5, topk_launch_count(n), st);
+            EMD_CUDA(launch_topk_rows(db->bt_fwd, nb, n, n, K, db->topk_scratch, db->bsel_idx, db->bsel_val, st),
+                     "forward top-K");
+        }
+        EMD_CUDA(cudaMemsetAsync(db->bcand_count, 0, sizeof(int) * nb, st), "candidate counts");
+        Phase p(db, 4, 3, st);
+        EMD_CUDA(launch_prune_b(meas, k, D_, nqd, nb, db->row_ptr, db->col, db->val, n, K, st),
+                 "pruned reverse pass");
+        return EMD_OK;
+    }
+    if (dir != EMD_DIR_FWD) {
+        Phase p(db, 4, 1, st);
+        EMD_CUDA(launch_rev_b(meas, k, dir, D_, nqd, nb, db->row_ptr, db->col, db->val, n, st), "reverse pass");
+    }
+    if (K > 0) {
+        Phase p(db, 5, topk_launch_count(n), st);
+        EMD_CUDA(launch_topk_rows(db->stage_out + (j0 - i0) * n, nb, n, n, K, db->topk_scratch,
+                                  out_idx + (j0 - i0) * K, out_dist + (j0 - i0) * K, st),
+                 "top-K");
+    }
+    return EMD_OK;
+}
+
+// Ring slots are reused only after the work that reads them (pinned host copy and device
+// descriptors) has finished, whatever stream it ran on.
+emd_status run_subbatch(emd_db* db, const int64_t* rp, const int32_t* qidx, const float* qw, int64_t i0,
+                        int64_t j0, int64_t j1, int meas, int k, int dir, int K, bool pruned, float* out_t,
+                        int64_t* out_idx, float* out_dist, cudaStream_t st)
+{
+    const int slot = db->desc_slot;
+    db->desc_slot = (slot + 1) % emd_db::kDescRing;
+    EMD_CUDA(cudaEventSynchronize(db->desc_ev[slot]), "descriptor ring");
+    emd_status s = run_subbatch_launch(slot, db, rp, qidx, qw, i0, j0, j1, meas, k, dir, K, pruned, out_t, out_idx,
+                                       out_dist, st);
+    EMD_CUDA(cudaEventRecord(db->desc_ev[slot], st), "descriptor ring");
+    return s;
+}
+
 emd_status run_batch(emd_db* db, const int64_t* rp, const int32_t* qidx, const float* qw, int64_t i0,
                      int64_t i1, int meas, int k, int dir, int K, float* out_t, int64_t* out_idx,
                      float* out_dist, cudaStream_t st)
 {
     const bool pruned = K > 0 && prunable(db, meas, k, dir, K);
+    if (db->opt.batched) {
+        // split into sub-batches that fit the batch workspace
+        int64_t j0 = i0;
+        while (j0 < i1) {
+            int64_t j1 = j0, cD = 0, cQ = 0, cP = 0, cT = 0;
+            while (j1 < i1) {
+                const int h = (int)(rp[j1 + 1] - rp[j1]);
+                const int64_t ldd = round_up(h, 32);
+                const int64_t tk = dir != EMD_DIR_REV ? table_width(meas, k, h) : 0;
+                if (j1 > j0 && (cD + ldd > db->b_cols || cQ + round_up(ldd, kDistBN) > db->b_qrows ||
+                                cP + round_up(h, 128) > db->b_prows || cT + tk > db->b_tabcols))
+                    break;
+                cD += ldd;
+                cQ += round_up(ldd, kDistBN);
+                cP += round_up(h, 128);
+                cT += tk;
+                ++j1;
+            }
+            emd_status s = run_subbatch(db, rp, qidx, qw, i0, j0, j1, meas, k, dir, K, pruned, out_t, out_idx,
+                                        out_dist, st);
+            if (s != EMD_OK) return s;
+            j0 = j1;
+        }
+    } else {
+        emd_status s = run_lanes(db, rp, qidx, qw, i0, i1, meas, k, dir, K, pruned, out_t, out_idx, out_dist, st);
+        if (s != EMD_OK) return s;
+    }
+    if (K > 0 && !pruned && !db->opt.batched) return select_topk(db, db->stage_out, i1 - i0, K, out_idx, out_dist, st);
+    if (!pruned) return EMD_OK;
+    std::vector<int> ok((size_t)(i1 - i0), 0);
+    EMD_CUDA(cudaMemcpyAsync(ok.data(), db->cand_ok, (i1 - i0) * sizeof(int), cudaMemcpyDeviceToHost, st),
+             "flag read");
+    EMD_CUDA(cudaStreamSynchronize(st), "synchronize");
+    db->pruned_queries += i1 - i0;
+    for (int64_t i = i0; i < i1; ++i) {
+        if (ok[i - i0]) continue;
+        ++db->prune_fallbacks;
+        const int64_t off = rp[i] - rp[i0];
+        const int h = (int)(rp[i + 1] - rp[i]);
+        emd_status s = run_query(db, db->lanes[0], qidx + off, qw + off, h, meas, k, EMD_DIR_MAX,
+                                 db->stage_out, st);
+        if (s != EMD_OK) return s;
+        s = select_topk(db, db->stage_out, 1, K, out_idx + (i - i0) * K, out_dist + (i - i0) * K, st);
+        if (s != EMD_OK) return s;
+    }
+    return EMD_OK;
+}
+
+// Queries i0..i1-1 one after another on the lanes (opt.batched = 0).
+emd_status run_lanes(emd_db* db, const int64_t* rp, const int32_t* qidx, const float* qw, int64_t i0,
+                     int64_t i1, int meas, int k, int dir, int K, bool pruned, float* out_t, int64_t* out_idx,
+                     float* out_dist, cudaStream_t st)
+{
     const int nl = (int)std::min<int64_t>((int64_t)db->lanes.size(), i1 - i0);
     EMD_CUDA(cudaEventRecord(db->fork, st), "fork");
     for (int l = 0; l < nl; ++l) EMD_CUDA(cudaStreamWaitEvent(db->lanes[l].st, db->fork, 0), "fork");
@@ -334,24 +538,6 @@ emd_status run_batch(emd_db* db, const int64_t* rp, const int32_t* qidx, const f
     for (int l = 0; l < nl; ++l) {
         EMD_CUDA(cudaEventRecord(db->lanes[l].done, db->lanes[l].st), "join");
         EMD_CUDA(cudaStreamWaitEvent(st, db->lanes[l].done, 0), "join");
-    }
-    if (K > 0 && !pruned) return select_topk(db, db->stage_out, i1 - i0, K, out_idx, out_dist, st);
-    if (!pruned) return EMD_OK;
-    std::vector<int> ok((size_t)(i1 - i0), 0);
-    EMD_CUDA(cudaMemcpyAsync(ok.data(), db->cand_ok, (i1 - i0) * sizeof(int), cudaMemcpyDeviceToHost, st),
-             "flag read");
-    EMD_CUDA(cudaStreamSynchronize(st), "synchronize");
-    db->pruned_queries += i1 - i0;
-    for (int64_t i = i0; i < i1; ++i) {
-        if (ok[i - i0]) continue;
-        ++db->prune_fallbacks;
-        const int64_t off = rp[i] - rp[i0];
-        const int h = (int)(rp[i + 1] - rp[i]);
-        emd_status s = run_query(db, db->lanes[0], qidx + off, qw + off, h, meas, k, EMD_DIR_MAX,
-                                 db->stage_out, st);
-        if (s != EMD_OK) return s;
-        s = select_topk(db, db->stage_out, 1, K, out_idx + (i - i0) * K, out_dist + (i - i0) * K, st);
-        if (s != EMD_OK) return s;
     }
     return EMD_OK;
 }
@@ -438,7 +624,9 @@ void emd_db_options_default(emd_db_options* opt)
     opt->max_table_k = 64;
     opt->max_batch = 64;
     opt->prune_topk = 1;
-    opt->lanes = 4;
+    opt->lanes = 1;
+    opt->batched = 1;
+    opt->batch_columns = 16384;
 }
 
 emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* cost_matrix,
@@ -463,7 +651,7 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
         return fail(EMD_ERR_INVALID_ARG, "rerank_margin must be 0..%d", kRerankMax);
     if (opt.max_query_h < 1 || opt.max_query_h > (1 << 16) || opt.max_table_k < 1 ||
         opt.max_table_k > (1 << 16) || opt.max_batch < 1 || opt.max_batch > 4096 || opt.lanes < 1 ||
-        opt.lanes > 16)
+        opt.lanes > 16 || opt.batch_columns < 1)
         return fail(EMD_ERR_INVALID_ARG, "option out of range");
     if (row_ptr[0] != 0) return fail(EMD_ERR_INVALID_ARG, "row_ptr[0] != 0");
     const int64_t nnz = row_ptr[n_docs];
@@ -612,6 +800,38 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
     TRY(dalloc(db, &db->tab_s, vu * opt.max_table_k));
     TRY(dalloc(db, &db->topk_scratch, (int64_t)opt.max_batch * kTopkScratchRow));
     TRY(dalloc(db, &db->cand_ok, opt.max_batch));
+    if (opt.batched) {
+        const int64_t B = opt.max_batch;
+        db->b_cols = std::max<int64_t>(round_up(opt.batch_columns, 32), db->ldd_max);
+        db->b_qrows = db->b_cols + 32 * B;
+        db->b_prows = db->b_cols + 96 * B;
+        db->b_tabcols = std::max<int64_t>(opt.max_table_k, 16 * B);
+        TRY(dalloc(db, &db->bD, vu * db->b_cols));
+        if (!db->cost_mode) {
+            TRY(dalloc(db, &db->bQ, db->b_qrows * db->ldm));
+            TRY(dalloc(db, &db->bqnorm, db->b_qrows));
+            if (db->tc) {
+                TRY(dalloc(db, &db->bq_hi, db->b_prows * db->kpad));
+                if (db->tcfmt == TC_SPLIT) TRY(dalloc(db, &db->bq_lo, db->b_prows * db->kpad));
+                TRY(dalloc(db, &db->bq_scale, db->b_prows));
+            }
+        }
+        TRY(dalloc(db, &db->btab, vu * db->b_tabcols));
+        TRY(dalloc(db, &db->bt_fwd, B * n_docs));
+        TRY(dalloc(db, &db->bt_rev, B * n_docs));
+        TRY(dalloc(db, &db->bsel_idx, B * kPruneMaxK));
+        TRY(dalloc(db, &db->bsel_val, B * kPruneMaxK));
+        TRY(dalloc(db, &db->bcand, B * kPruneCap));
+        TRY(dalloc(db, &db->bcand_sym, B * 2 * kPruneCap));
+        TRY(dalloc(db, &db->bcand_count, B));
+        TRY(dalloc(db, &db->qd_dev, emd_db::kDescRing * B));
+        TRY(dalloc(db, &db->nq_dev, emd_db::kDescRing));
+        TRYC(cudaHostAlloc((void**)&db->qd_host, sizeof(QDesc) * emd_db::kDescRing * B, cudaHostAllocDefault),
+             "pinned descriptors");
+        TRYC(cudaHostAlloc((void**)&db->nq_host, sizeof(int) * emd_db::kDescRing, cudaHostAllocDefault),
+             "pinned descriptors");
+        for (auto& e : db->desc_ev) TRYC(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    }
     db->stage_bins = (int64_t)opt.max_batch * opt.max_query_h;
     TRY(dalloc(db, &db->stage_idx, db->stage_bins));
     TRY(dalloc(db, &db->stage_w, db->stage_bins));

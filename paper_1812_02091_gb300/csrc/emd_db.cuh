@@ -105,6 +105,30 @@ struct emd_db {
     int64_t total_launches = 0;
     int64_t pruned_queries = 0, prune_fallbacks = 0;
 
+    // batched form: one launch per step for a whole batch (opt.batched)
+    static constexpr int kDescRing = 4;
+    int64_t b_cols = 0, b_qrows = 0, b_prows = 0, b_tabcols = 0;
+    float* bD = nullptr;          // v_used x b_cols: the batch's distance matrices side by side
+    float* bQ = nullptr;          // b_qrows x ldm
+    float* bqnorm = nullptr;      // b_qrows
+    __half* bq_hi = nullptr;      // b_prows x kpad packed panels
+    __half* bq_lo = nullptr;
+    float* bq_scale = nullptr;    // b_prows
+    float2* btab = nullptr;       // v_used x b_tabcols tables
+    float* bt_fwd = nullptr;      // max_batch x n
+    float* bt_rev = nullptr;      // max_batch x n
+    int64_t* bsel_idx = nullptr;  // max_batch x kPruneMaxK
+    float* bsel_val = nullptr;
+    int64_t* bcand = nullptr;     // max_batch x kPruneCap
+    float* bcand_sym = nullptr;   // max_batch x 2 kPruneCap
+    int* bcand_count = nullptr;   // max_batch
+    emd::QDesc* qd_dev = nullptr; // kDescRing x max_batch descriptors
+    int* nq_dev = nullptr;        // kDescRing counts
+    emd::QDesc* qd_host = nullptr;  // pinned mirror of the ring
+    int* nq_host = nullptr;
+    cudaEvent_t desc_ev[kDescRing] = {};
+    int desc_slot = 0;
+
     // Serialises the entry points that launch work or touch the counters above (host
     // threads, and the server's worker thread).
     std::mutex mu;

@@ -139,6 +139,61 @@ cudaError_t launch_table_rerank(float* D, int ldd, int64_t M, int h, int k, int 
                                 const float* Q, int ldv, const float* q_w, float2* tab, int32_t* tab_s,
                                 cudaStream_t st);
 
+// ------------------------------------------------------------------ batched forms
+//
+// A batch of queries runs each step as one launch: query q of the batch is blockIdx.y
+// (blockIdx.z for the SIMT distance tile), its pointers and sizes are qd[q] (device
+// memory), and blocks of queries q >= *nq exit at once.  Every batched kernel calls the
+// same device body as its per-query form with the same template widths, so a query's
+// results are bit-identical either way.
+struct QDesc {
+    const int32_t* qidx;    // h bins: vocabulary ids and weights
+    const float* qw;
+    float* Q;               // qrows x ldm gathered rows (zero beyond h and m)
+    float* qnorm;           // qrows squared norms
+    void* q_hi;             // npad x Kpad packed panel(s) (tensor-core precisions)
+    void* q_lo;
+    float* q_scale;
+    float* D;               // v_used x ldd distance matrix
+    float2* tab;            // v_used x tk table
+    float* t_fwd;           // n forward values
+    float* t_rev;           // n reverse values
+    float* t_out;           // n requested distances (FWD, REV or MAX)
+    int64_t* sel_idx;       // kPruneMaxK forward top-K (pruned top-K)
+    float* sel_val;
+    int64_t* cand;          // kPruneCap candidate documents
+    float* cand_sym;        // 2 * kPruneCap: max values, then reverse values
+    int* cand_count;
+    int* ok;                // certification flag
+    int64_t* out_idx;       // K top-K result
+    float* out_dist;
+    int h, ldd, qrows, npad, tk, kc;
+};
+
+cudaError_t launch_gather_rows_b(const QDesc* qd, const int* nq, int max_q, int max_rows, const float* src,
+                                 int64_t v, int ld, int m, int* err, cudaStream_t st);
+cudaError_t launch_pack_b(int fmt, const QDesc* qd, const int* nq, int max_q, int max_rows, int ld, int m,
+                          int Kpad, cudaStream_t st);
+cudaError_t launch_dist_fp32_b(const QDesc* qd, const int* nq, int max_q, int max_ldd, const float* A, int64_t M,
+                               int lda, const float* anorm, const int32_t* a_ids, int K, cudaStream_t st);
+cudaError_t launch_dist_gather_b(const QDesc* qd, const int* nq, int max_q, const float* cost, int64_t v,
+                                 const int32_t* a_ids, int64_t M, int* err, cudaStream_t st);
+// max_tk: the largest table width of the batch; rerank: the approximate precisions' form
+// (V: the used vocabulary rows, ldv floats each).
+cudaError_t launch_table_b(const QDesc* qd, const int* nq, int max_q, int64_t M, int max_tk, bool rerank,
+                           int max_kc, const float* V, int ldv, cudaStream_t st);
+// Forward values into t_out (to_out) or t_fwd.
+cudaError_t launch_fwd_b(int meas, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
+                         const int32_t* col, const float* val, int64_t n, bool to_out, cudaStream_t st);
+// Reverse pass over all documents; dir FWD is not accepted, REV writes t_out, MAX writes
+// t_rev and max(t_fwd, t_rev) into t_out.
+cudaError_t launch_rev_b(int meas, int k, int dir, const QDesc* qd, const int* nq, int max_q,
+                         const int32_t* row_ptr, const int32_t* col, const float* val, int64_t n, cudaStream_t st);
+// Pruned top-K after the forward top-K (sel_idx / sel_val): candidate compaction (counts
+// must be zeroed), reverse pass on the candidates, final selection and certificate.
+cudaError_t launch_prune_b(int meas, int k, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
+                           const int32_t* col, const float* val, int64_t n, int K, cudaStream_t st);
+
 // Failure message for emd_last_error() (defined beside the C ABI).
 emd_status set_error(emd_status st, const char* msg);
 void clear_error();

@@ -20,7 +20,7 @@ __device__ __forceinline__ float warp_sum(float x)
 
 // ------------------------------------------------------------------ row gather + norms
 
-__global__ void k_gather_rows(const float* __restrict__ src, int64_t v, int ld, int m,
+__device__ __forceinline__ void gather_rows_body(const float* __restrict__ src, int64_t v, int ld, int m,
                               const int32_t* __restrict__ ids, int64_t nrows, int64_t nrows_pad,
                               float* __restrict__ dst, float* __restrict__ norm2, int* err)
 {
@@ -46,6 +46,13 @@ __global__ void k_gather_rows(const float* __restrict__ src, int64_t v, int ld, 
     if (lane == 0) norm2[r] = s;
 }
 
+__global__ void k_gather_rows(const float* __restrict__ src, int64_t v, int ld, int m,
+                              const int32_t* __restrict__ ids, int64_t nrows, int64_t nrows_pad,
+                              float* __restrict__ dst, float* __restrict__ norm2, int* err)
+{
+    gather_rows_body(src, v, ld, m, ids, nrows, nrows_pad, dst, norm2, err);
+}
+
 // ------------------------------------------------------------------ FP32 distance tile
 //
 // Block tile 128 (vocabulary rows) x 64 (query columns), K step 16, 128 threads, each
@@ -54,8 +61,7 @@ __global__ void k_gather_rows(const float* __restrict__ src, int64_t v, int ld, 
 // buffered, one barrier per K step) so that the inner loop is 4 LDS.128 + 64 FFMA.
 // Operand rows are zero-padded to a multiple of 4 floats, so the K tail reads zeros.
 
-__global__ void __launch_bounds__(128)
-k_dist_fp32(const float* __restrict__ A, int64_t M, int lda, const float* __restrict__ anorm,
+__device__ __forceinline__ void dist_fp32_body(const float* __restrict__ A, int64_t M, int lda, const float* __restrict__ anorm,
             const int32_t* __restrict__ a_ids, const float* __restrict__ B, int N, int ldb,
             const float* __restrict__ bnorm, const int32_t* __restrict__ b_ids, int K,
             float* __restrict__ D, int ldd)
@@ -167,9 +173,17 @@ k_dist_fp32(const float* __restrict__ A, int64_t M, int lda, const float* __rest
     }
 }
 
+__global__ void __launch_bounds__(128) k_dist_fp32(const float* __restrict__ A, int64_t M, int lda, const float* __restrict__ anorm,
+            const int32_t* __restrict__ a_ids, const float* __restrict__ B, int N, int ldb,
+            const float* __restrict__ bnorm, const int32_t* __restrict__ b_ids, int K,
+            float* __restrict__ D, int ldd)
+{
+    dist_fp32_body(A, M, lda, anorm, a_ids, B, N, ldb, bnorm, b_ids, K, D, ldd);
+}
+
 // ------------------------------------------------------------------ cost-matrix gather
 
-__global__ void k_dist_gather(const float* __restrict__ cost, int64_t v,
+__device__ __forceinline__ void dist_gather_body(const float* __restrict__ cost, int64_t v,
                               const int32_t* __restrict__ a_ids, int64_t M,
                               const int32_t* __restrict__ b_ids, int N, float* __restrict__ D,
                               int ldd, int* err)
@@ -190,6 +204,14 @@ __global__ void k_dist_gather(const float* __restrict__ cost, int64_t v,
         }
         D[u * ldd + j] = d;
     }
+}
+
+__global__ void k_dist_gather(const float* __restrict__ cost, int64_t v,
+                              const int32_t* __restrict__ a_ids, int64_t M,
+                              const int32_t* __restrict__ b_ids, int N, float* __restrict__ D,
+                              int ldd, int* err)
+{
+    dist_gather_body(cost, v, a_ids, M, b_ids, N, D, ldd, err);
 }
 
 // ------------------------------------------------------------------ top-k table
@@ -214,8 +236,7 @@ __device__ __forceinline__ void insert_dj(float (&z)[KT], int (&s)[KT], float d,
 }
 
 template <int KT>
-__global__ void __launch_bounds__(128)
-k_table(const float* __restrict__ D, int ldd, int64_t M, int h, int k, const float* __restrict__ q_w,
+__device__ __forceinline__ void table_body(const float* __restrict__ D, int ldd, int64_t M, int h, int k, const float* __restrict__ q_w,
         float2* __restrict__ tab, int32_t* __restrict__ tab_s)
 {
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -242,9 +263,16 @@ k_table(const float* __restrict__ D, int ldd, int64_t M, int h, int k, const flo
     }
 }
 
+template <int KT>
+__global__ void __launch_bounds__(128) k_table(const float* __restrict__ D, int ldd, int64_t M, int h, int k, const float* __restrict__ q_w,
+        float2* __restrict__ tab, int32_t* __restrict__ tab_s)
+{
+    table_body<KT>(D, ldd, M, h, k, q_w, tab, tab_s);
+}
+
 // k larger than the register lists: successive minima, each strictly after the previous
 // in (d, j) order.  O(k * h / 32) per lane; used for ICT on small queries.
-__global__ void k_table_generic(const float* __restrict__ D, int ldd, int64_t M, int h, int k,
+__device__ __forceinline__ void table_generic_body(const float* __restrict__ D, int ldd, int64_t M, int h, int k,
                                 const float* __restrict__ q_w, float2* __restrict__ tab,
                                 int32_t* __restrict__ tab_s)
 {
@@ -278,6 +306,13 @@ __global__ void k_table_generic(const float* __restrict__ D, int ldd, int64_t M,
     }
 }
 
+__global__ void k_table_generic(const float* __restrict__ D, int ldd, int64_t M, int h, int k,
+                                const float* __restrict__ q_w, float2* __restrict__ tab,
+                                int32_t* __restrict__ tab_s)
+{
+    table_generic_body(D, ldd, M, h, k, q_w, tab, tab_s);
+}
+
 // Re-rank form of the table, for approximate distance matrices (BF16 / E4M3 Phase 1).
 // Per vocabulary row u: the kc smallest approximate D[u, .] (ties: lower j) are the
 // candidates; their distances are recomputed exactly in FP32 as sqrt(sum_i (V_u,i -
@@ -301,8 +336,7 @@ __device__ __forceinline__ void insert_dj_tie(float (&z)[KCT], int (&s)[KCT], fl
 }
 
 template <int KCT>
-__global__ void __launch_bounds__(128)
-k_table_rerank(float* __restrict__ D, int ldd, int64_t M, int h, int k, int kc, const float* __restrict__ V,
+__device__ __forceinline__ void table_rerank_body(float* __restrict__ D, int ldd, int64_t M, int h, int k, int kc, const float* __restrict__ V,
                const float* __restrict__ Q, int ldv, const float* __restrict__ q_w, float2* __restrict__ tab,
                int32_t* __restrict__ tab_s)
 {
@@ -373,6 +407,68 @@ k_table_rerank(float* __restrict__ D, int ldd, int64_t M, int h, int k, int kc, 
     }
 }
 
+template <int KCT>
+__global__ void __launch_bounds__(128) k_table_rerank(float* __restrict__ D, int ldd, int64_t M, int h, int k, int kc, const float* __restrict__ V,
+               const float* __restrict__ Q, int ldv, const float* __restrict__ q_w, float2* __restrict__ tab,
+               int32_t* __restrict__ tab_s)
+{
+    table_rerank_body<KCT>(D, ldd, M, h, k, kc, V, Q, ldv, q_w, tab, tab_s);
+}
+
+// ------------------------------------------------------------------ batched forms
+
+__global__ void k_gather_rows_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, const float* __restrict__ src,
+                                int64_t v, int ld, int m, int* err)
+{
+    if ((int)blockIdx.y >= *nq) return;
+    const QDesc& d = qd[blockIdx.y];
+    gather_rows_body(src, v, ld, m, d.qidx, d.h, d.qrows, d.Q, d.qnorm, err);
+}
+
+__global__ void __launch_bounds__(128)
+k_dist_fp32_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, const float* __restrict__ A, int64_t M,
+              int lda, const float* __restrict__ anorm, const int32_t* __restrict__ a_ids, int K)
+{
+    if ((int)blockIdx.z >= *nq) return;
+    const QDesc& d = qd[blockIdx.z];
+    if ((int)blockIdx.y * kDistBN >= d.ldd) return;
+    dist_fp32_body(A, M, lda, anorm, a_ids, d.Q, d.h, lda, d.qnorm, d.qidx, K, d.D, d.ldd);
+}
+
+__global__ void k_dist_gather_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, const float* __restrict__ cost,
+                                int64_t v, const int32_t* __restrict__ a_ids, int64_t M, int* err)
+{
+    if ((int)blockIdx.y >= *nq) return;
+    const QDesc& d = qd[blockIdx.y];
+    dist_gather_body(cost, v, a_ids, M, d.qidx, d.h, d.D, d.ldd, err);
+}
+
+template <int KT>
+__global__ void __launch_bounds__(128)
+k_table_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t M)
+{
+    if ((int)blockIdx.y >= *nq) return;
+    const QDesc& d = qd[blockIdx.y];
+    table_body<KT>(d.D, d.ldd, M, d.h, d.tk, d.qw, d.tab, nullptr);
+}
+
+__global__ void k_table_generic_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t M)
+{
+    if ((int)blockIdx.y >= *nq) return;
+    const QDesc& d = qd[blockIdx.y];
+    table_generic_body(d.D, d.ldd, M, d.h, d.tk, d.qw, d.tab, nullptr);
+}
+
+template <int KCT>
+__global__ void __launch_bounds__(128)
+k_table_rerank_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t M, const float* __restrict__ V,
+                 int ldv)
+{
+    if ((int)blockIdx.y >= *nq) return;
+    const QDesc& d = qd[blockIdx.y];
+    table_rerank_body<KCT>(d.D, d.ldd, M, d.h, d.tk, d.kc, V, d.Q, ldv, d.qw, d.tab, nullptr);
+}
+
 }  // namespace
 
 cudaError_t launch_gather_rows(const float* src, int64_t v, int ld, int m, const int32_t* ids,
@@ -438,6 +534,59 @@ cudaError_t launch_table_rerank(float* D, int ldd, int64_t M, int h, int k, int 
     if (kc <= 8) k_table_rerank<8><<<grid, 128, 0, st>>>(D, ldd, M, h, k, kc, V, Q, ldv, q_w, tab, tab_s);
     else if (kc <= 16) k_table_rerank<16><<<grid, 128, 0, st>>>(D, ldd, M, h, k, kc, V, Q, ldv, q_w, tab, tab_s);
     else k_table_rerank<32><<<grid, 128, 0, st>>>(D, ldd, M, h, k, kc, V, Q, ldv, q_w, tab, tab_s);
+    return cudaGetLastError();
+}
+
+}  // namespace emd
+
+namespace emd {
+
+cudaError_t launch_gather_rows_b(const QDesc* qd, const int* nq, int max_q, int max_rows, const float* src,
+                                 int64_t v, int ld, int m, int* err, cudaStream_t st)
+{
+    if (max_q <= 0 || max_rows <= 0) return cudaSuccess;
+    const int warps = 8;
+    k_gather_rows_b<<<dim3((unsigned)((max_rows + warps - 1) / warps), (unsigned)max_q), warps * 32, 0, st>>>(
+        qd, nq, src, v, ld, m, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dist_fp32_b(const QDesc* qd, const int* nq, int max_q, int max_ldd, const float* A, int64_t M,
+                               int lda, const float* anorm, const int32_t* a_ids, int K, cudaStream_t st)
+{
+    if (max_q <= 0 || M <= 0 || max_ldd <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((M + kDistBM - 1) / kDistBM), (unsigned)((max_ldd + kDistBN - 1) / kDistBN), (unsigned)max_q);
+    k_dist_fp32_b<<<grid, 128, 0, st>>>(qd, nq, A, M, lda, anorm, a_ids, K);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dist_gather_b(const QDesc* qd, const int* nq, int max_q, const float* cost, int64_t v,
+                                 const int32_t* a_ids, int64_t M, int* err, cudaStream_t st)
+{
+    if (max_q <= 0 || M <= 0) return cudaSuccess;
+    k_dist_gather_b<<<dim3((unsigned)M, (unsigned)max_q), 128, 0, st>>>(qd, nq, cost, v, a_ids, M, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_table_b(const QDesc* qd, const int* nq, int max_q, int64_t M, int max_tk, bool rerank,
+                           int max_kc, const float* V, int ldv, cudaStream_t st)
+{
+    if (max_q <= 0 || M <= 0) return cudaSuccess;
+    const dim3 g((unsigned)((M + 127) / 128), (unsigned)max_q);
+    if (rerank) {
+        if (max_kc > kRerankMax) return cudaErrorInvalidValue;
+        if (max_kc <= 8) k_table_rerank_b<8><<<g, 128, 0, st>>>(qd, nq, M, V, ldv);
+        else if (max_kc <= 16) k_table_rerank_b<16><<<g, 128, 0, st>>>(qd, nq, M, V, ldv);
+        else k_table_rerank_b<32><<<g, 128, 0, st>>>(qd, nq, M, V, ldv);
+    } else if (max_tk <= 1) k_table_b<1><<<g, 128, 0, st>>>(qd, nq, M);
+    else if (max_tk <= 2) k_table_b<2><<<g, 128, 0, st>>>(qd, nq, M);
+    else if (max_tk <= 4) k_table_b<4><<<g, 128, 0, st>>>(qd, nq, M);
+    else if (max_tk <= 8) k_table_b<8><<<g, 128, 0, st>>>(qd, nq, M);
+    else if (max_tk <= 16) k_table_b<16><<<g, 128, 0, st>>>(qd, nq, M);
+    else {
+        const int warps = 8;
+        k_table_generic_b<<<dim3((unsigned)((M + warps - 1) / warps), (unsigned)max_q), warps * 32, 0, st>>>(qd, nq, M);
+    }
     return cudaGetLastError();
 }
 

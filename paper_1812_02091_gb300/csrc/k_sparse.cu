@@ -48,7 +48,7 @@ __device__ __forceinline__ float fwd_cost(float x, const float2* __restrict__ T,
 }
 
 template <int MEAS>
-__global__ void k_fwd(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+__device__ __forceinline__ void fwd_body(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                       const float* __restrict__ val, int64_t n, const float2* __restrict__ tab,
                       int k, int keff, float* __restrict__ t_fwd)
 {
@@ -64,6 +64,14 @@ __global__ void k_fwd(const int32_t* __restrict__ row_ptr, const int32_t* __rest
         acc = warp_sum(acc);
         if (lane == 0) t_fwd[d] = acc;
     }
+}
+
+template <int MEAS>
+__global__ void k_fwd(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                      const float* __restrict__ val, int64_t n, const float2* __restrict__ tab,
+                      int k, int keff, float* __restrict__ t_fwd)
+{
+    fwd_body<MEAS>(row_ptr, col, val, n, tab, k, keff, t_fwd);
 }
 
 // ------------------------------------------------------------------ reverse pass
@@ -139,8 +147,7 @@ __device__ __forceinline__ void load_vec(const float* p, bool ok, float (&o)[4])
 }
 
 template <int MEAS, int KT, int NJ>
-__global__ void __launch_bounds__(256, 2)
-k_rev(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+__device__ __forceinline__ void rev_body(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
       const float* __restrict__ val, int64_t n, const float* __restrict__ D, int ldd, int h,
       const float* __restrict__ q_w, int k, const float* __restrict__ t_fwd,
       float* __restrict__ t_rev, float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
@@ -204,6 +211,16 @@ k_rev(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
     }
 }
 
+template <int MEAS, int KT, int NJ>
+__global__ void __launch_bounds__(256, 2) k_rev(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+      const float* __restrict__ val, int64_t n, const float* __restrict__ D, int ldd, int h,
+      const float* __restrict__ q_w, int k, const float* __restrict__ t_fwd,
+      float* __restrict__ t_rev, float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
+      const int* __restrict__ n_dev)
+{
+    rev_body<MEAS, KT, NJ>(row_ptr, col, val, n, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev);
+}
+
 // Candidate-list form: a block of W warps per candidate slot.  Warp w scans the w-th
 // contiguous chunk of the document's bins; warp 0 then inserts the other chunks' lists in
 // chunk order.  Strict '<' keeps an earlier chunk's entry ahead of an equal distance from a
@@ -211,8 +228,7 @@ k_rev(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
 // bit-identical to the one-warp kernel above.  W times the warps on a few hundred
 // documents, whose single-warp scans are latency-bound.
 template <int MEAS, int KT, int NJ, int W>
-__global__ void __launch_bounds__(W * 32, 4)
-k_rev_blk(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+__device__ __forceinline__ void rev_blk_body(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
           const float* __restrict__ val, const float* __restrict__ D, int ldd, int h,
           const float* __restrict__ q_w, int k, const float* __restrict__ t_fwd,
           float* __restrict__ t_rev, float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
@@ -300,11 +316,21 @@ k_rev_blk(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
     }
 }
 
+template <int MEAS, int KT, int NJ, int W>
+__global__ void __launch_bounds__(W * 32, 4) k_rev_blk(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+          const float* __restrict__ val, const float* __restrict__ D, int ldd, int h,
+          const float* __restrict__ q_w, int k, const float* __restrict__ t_fwd,
+          float* __restrict__ t_rev, float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
+          const int* __restrict__ n_dev)
+{
+    rev_blk_body<MEAS, KT, NJ, W>(row_ptr, col, val, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev);
+}
+
 // k above the register width (ICT, large k): per lane, successive minima over the
 // document's bins, each strictly after the previous in (distance, bin position) order,
 // until the source mass is placed.  O(steps * h_d) per query bin.
 template <int MEAS>
-__global__ void k_rev_generic(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+__device__ __forceinline__ void rev_generic_body(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                               const float* __restrict__ val, int64_t n, const float* __restrict__ D,
                               int ldd, int h, const float* __restrict__ q_w, int k,
                               const float* __restrict__ t_fwd, float* __restrict__ t_rev,
@@ -352,6 +378,17 @@ __global__ void k_rev_generic(const int32_t* __restrict__ row_ptr, const int32_t
             if (t_max) t_max[d] = fmaxf(t_fwd[dd], total);
         }
     }
+}
+
+template <int MEAS>
+__global__ void k_rev_generic(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                              const float* __restrict__ val, int64_t n, const float* __restrict__ D,
+                              int ldd, int h, const float* __restrict__ q_w, int k,
+                              const float* __restrict__ t_fwd, float* __restrict__ t_rev,
+                              float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
+                              const int* __restrict__ n_dev)
+{
+    rev_generic_body<MEAS>(row_ptr, col, val, n, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev);
 }
 
 // ------------------------------------------------------------------ top-K selection
@@ -479,7 +516,7 @@ cudaError_t topk_kt(const float* t, int64_t rows, int64_t n, int64_t ldt, int K,
 
 __device__ __forceinline__ float prune_theta(float fwd_k) { return fwd_k * (1.0f + 0.0078125f); }
 
-__global__ void k_prune_compact(const float* __restrict__ t_fwd, int64_t n, const float* __restrict__ sel_val,
+__device__ __forceinline__ void prune_compact_body(const float* __restrict__ t_fwd, int64_t n, const float* __restrict__ sel_val,
                                 int K, int cap, int64_t* __restrict__ cand, int* __restrict__ count)
 {
     const float theta = prune_theta(sel_val[K - 1]);
@@ -491,11 +528,17 @@ __global__ void k_prune_compact(const float* __restrict__ t_fwd, int64_t n, cons
     }
 }
 
+__global__ void k_prune_compact(const float* __restrict__ t_fwd, int64_t n, const float* __restrict__ sel_val,
+                                int K, int cap, int64_t* __restrict__ cand, int* __restrict__ count)
+{
+    prune_compact_body(t_fwd, n, sel_val, K, cap, cand, count);
+}
+
 // Final selection over the candidates: thread i ranks candidate i in (sym, id) order
 // against the other filled slots (one 64-bit key compare each: distances are >= 0, so the
 // key order is the (distance, id) order); ranks < K are written; ok = no overflow and
 // K-th <= theta.
-__global__ void k_prune_select(const int64_t* __restrict__ cand, const float* __restrict__ sym,
+__device__ __forceinline__ void prune_select_body(const int64_t* __restrict__ cand, const float* __restrict__ sym,
                                const int* __restrict__ count, int cap, const float* __restrict__ sel_val,
                                int K, int64_t* __restrict__ out_idx, float* __restrict__ out_dist,
                                int* __restrict__ ok)
@@ -520,6 +563,14 @@ __global__ void k_prune_select(const int64_t* __restrict__ cand, const float* __
     if (i == 0) *ok = (*count <= cap && c >= K && kth <= prune_theta(sel_val[K - 1])) ? 1 : 0;
 }
 
+__global__ void k_prune_select(const int64_t* __restrict__ cand, const float* __restrict__ sym,
+                               const int* __restrict__ count, int cap, const float* __restrict__ sel_val,
+                               int K, int64_t* __restrict__ out_idx, float* __restrict__ out_dist,
+                               int* __restrict__ ok)
+{
+    prune_select_body(cand, sym, count, cap, sel_val, K, out_idx, out_dist, ok);
+}
+
 template <int MEAS>
 cudaError_t rev_meas_blk(int k, const int32_t* row_ptr, const int32_t* col, const float* val, int slots,
                          const float* D, int ldd, int h, const float* q_w, const float* t_fwd,
@@ -536,6 +587,112 @@ cudaError_t rev_meas_blk(int k, const int32_t* row_ptr, const int32_t* col, cons
     else if (kt <= 8) { if (wide) EMD_REVB(8, 2); else EMD_REVB(8, 1); }
     else EMD_REVB(16, 1);
 #undef EMD_REVB
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ batched forms
+
+template <int MEAS>
+__global__ void k_fwd_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t* __restrict__ row_ptr,
+                        const int32_t* __restrict__ col, const float* __restrict__ val, int64_t n, bool to_out)
+{
+    if ((int)blockIdx.y >= *nq) return;
+    const QDesc& d = qd[blockIdx.y];
+    fwd_body<MEAS>(row_ptr, col, val, n, d.tab, d.tk, d.tk, to_out ? d.t_out : d.t_fwd);
+}
+
+// NJ follows the per-query launcher: NJW bins per lane when h > 32, else one.
+template <int MEAS, int KT, int NJW>
+__global__ void __launch_bounds__(256, 2)
+k_rev_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t* __restrict__ row_ptr,
+        const int32_t* __restrict__ col, const float* __restrict__ val, int64_t n, int k, int dir)
+{
+    if ((int)blockIdx.y >= *nq) return;
+    const QDesc& d = qd[blockIdx.y];
+    float* t_rev = dir == EMD_DIR_REV ? d.t_out : d.t_rev;
+    float* t_max = dir == EMD_DIR_MAX ? d.t_out : nullptr;
+    if (d.h > 32)
+        rev_body<MEAS, KT, NJW>(row_ptr, col, val, n, d.D, d.ldd, d.h, d.qw, k, d.t_fwd, t_rev, t_max, nullptr,
+                                nullptr);
+    else
+        rev_body<MEAS, KT, 1>(row_ptr, col, val, n, d.D, d.ldd, d.h, d.qw, k, d.t_fwd, t_rev, t_max, nullptr,
+                              nullptr);
+}
+
+template <int MEAS>
+__global__ void k_rev_generic_b(const QDesc* __restrict__ qd, const int* __restrict__ nq,
+                                const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                const float* __restrict__ val, int64_t n, int k, int dir)
+{
+    if ((int)blockIdx.y >= *nq) return;
+    const QDesc& d = qd[blockIdx.y];
+    float* t_rev = dir == EMD_DIR_REV ? d.t_out : d.t_rev;
+    float* t_max = dir == EMD_DIR_MAX ? d.t_out : nullptr;
+    rev_generic_body<MEAS>(row_ptr, col, val, n, d.D, d.ldd, d.h, d.qw, k, d.t_fwd, t_rev, t_max, nullptr, nullptr);
+}
+
+__global__ void k_prune_compact_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t n, int K)
+{
+    if ((int)blockIdx.y >= *nq) return;
+    const QDesc& d = qd[blockIdx.y];
+    prune_compact_body(d.t_fwd, n, d.sel_val, K, kPruneCap, d.cand, d.cand_count);
+}
+
+template <int MEAS, int KT, int NJW, int W>
+__global__ void __launch_bounds__(W * 32, 4)
+k_rev_blk_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t* __restrict__ row_ptr,
+            const int32_t* __restrict__ col, const float* __restrict__ val, int k)
+{
+    if ((int)blockIdx.y >= *nq) return;
+    const QDesc& d = qd[blockIdx.y];
+    if (d.h > 32)
+        rev_blk_body<MEAS, KT, NJW, W>(row_ptr, col, val, d.D, d.ldd, d.h, d.qw, k, d.t_fwd, d.cand_sym + kPruneCap,
+                                       d.cand_sym, d.cand, d.cand_count);
+    else
+        rev_blk_body<MEAS, KT, 1, W>(row_ptr, col, val, d.D, d.ldd, d.h, d.qw, k, d.t_fwd, d.cand_sym + kPruneCap,
+                                     d.cand_sym, d.cand, d.cand_count);
+}
+
+__global__ void k_prune_select_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int K)
+{
+    if ((int)blockIdx.x >= *nq) return;
+    const QDesc& d = qd[blockIdx.x];
+    prune_select_body(d.cand, d.cand_sym, d.cand_count, kPruneCap, d.sel_val, K, d.out_idx, d.out_dist, d.ok);
+}
+
+template <int MEAS>
+cudaError_t rev_meas_b(int k, int dir, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
+                       const int32_t* col, const float* val, int64_t n, cudaStream_t st)
+{
+    const int warps = 8;
+    const int64_t blocks = std::min<int64_t>((n + warps - 1) / warps, 152 * 64);
+    dim3 grid((unsigned)std::max<int64_t>(1, blocks), (unsigned)max_q);
+    const int kt = MEAS == M_RWMD ? 1 : (MEAS == M_OMR ? 2 : (MEAS == M_ICT ? 1 << 30 : k));
+#define EMD_REVQ(KT, NJ) k_rev_b<MEAS, KT, NJ><<<grid, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, k, dir)
+    if (kt <= 1) EMD_REVQ(1, 4);
+    else if (kt <= 2) EMD_REVQ(2, 4);
+    else if (kt <= 4) EMD_REVQ(4, 4);
+    else if (kt <= 8) EMD_REVQ(8, 2);
+    else if (kt <= 16) EMD_REVQ(16, 1);
+    else k_rev_generic_b<MEAS><<<grid, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, k, dir);
+#undef EMD_REVQ
+    return cudaGetLastError();
+}
+
+template <int MEAS>
+cudaError_t rev_meas_blk_b(int k, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
+                           const int32_t* col, const float* val, cudaStream_t st)
+{
+    constexpr int W = 4;
+    const int kt = MEAS == M_RWMD ? 1 : (MEAS == M_OMR ? 2 : k);
+    const dim3 grid(kPruneCap, (unsigned)max_q);
+#define EMD_REVBQ(KT, NJ) k_rev_blk_b<MEAS, KT, NJ, W><<<grid, W * 32, 0, st>>>(qd, nq, row_ptr, col, val, k)
+    if (kt <= 1) EMD_REVBQ(1, 4);
+    else if (kt <= 2) EMD_REVBQ(2, 4);
+    else if (kt <= 4) EMD_REVBQ(4, 4);
+    else if (kt <= 8) EMD_REVBQ(8, 2);
+    else EMD_REVBQ(16, 1);
+#undef EMD_REVBQ
     return cudaGetLastError();
 }
 
@@ -611,6 +768,51 @@ cudaError_t launch_prune(int meas, int k, const int32_t* row_ptr, const int32_t*
     }
     if (e != cudaSuccess) return e;
     k_prune_select<<<1, kPruneCap, 0, st>>>(cand, sym, count, kPruneCap, sel_val, K, out_idx, out_dist, ok);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_b(int meas, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
+                         const int32_t* col, const float* val, int64_t n, bool to_out, cudaStream_t st)
+{
+    if (max_q <= 0 || n <= 0) return cudaSuccess;
+    const int warps = 8;
+    const int64_t blocks = std::min<int64_t>((n + warps - 1) / warps, 152 * 64);
+    dim3 grid((unsigned)std::max<int64_t>(1, blocks), (unsigned)max_q);
+    switch (meas) {
+    case M_RWMD: k_fwd_b<M_RWMD><<<grid, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
+    case M_OMR: k_fwd_b<M_OMR><<<grid, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
+    default: k_fwd_b<M_ACT><<<grid, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rev_b(int meas, int k, int dir, const QDesc* qd, const int* nq, int max_q,
+                         const int32_t* row_ptr, const int32_t* col, const float* val, int64_t n, cudaStream_t st)
+{
+    if (max_q <= 0 || n <= 0) return cudaSuccess;
+    if (dir != EMD_DIR_REV && dir != EMD_DIR_MAX) return cudaErrorInvalidValue;
+    switch (meas) {
+    case M_RWMD: return rev_meas_b<M_RWMD>(k, dir, qd, nq, max_q, row_ptr, col, val, n, st);
+    case M_OMR: return rev_meas_b<M_OMR>(k, dir, qd, nq, max_q, row_ptr, col, val, n, st);
+    case M_ICT: return rev_meas_b<M_ICT>(k, dir, qd, nq, max_q, row_ptr, col, val, n, st);
+    default: return rev_meas_b<M_ACT>(k, dir, qd, nq, max_q, row_ptr, col, val, n, st);
+    }
+}
+
+cudaError_t launch_prune_b(int meas, int k, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
+                           const int32_t* col, const float* val, int64_t n, int K, cudaStream_t st)
+{
+    if (max_q <= 0) return cudaSuccess;
+    const int blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256), 152 * 4);
+    k_prune_compact_b<<<dim3((unsigned)blocks, (unsigned)max_q), 256, 0, st>>>(qd, nq, n, K);
+    cudaError_t e;
+    switch (meas) {
+    case M_RWMD: e = rev_meas_blk_b<M_RWMD>(k, qd, nq, max_q, row_ptr, col, val, st); break;
+    case M_OMR: e = rev_meas_blk_b<M_OMR>(k, qd, nq, max_q, row_ptr, col, val, st); break;
+    default: e = rev_meas_blk_b<M_ACT>(k, qd, nq, max_q, row_ptr, col, val, st); break;
+    }
+    if (e != cudaSuccess) return e;
+    k_prune_select_b<<<(unsigned)max_q, kPruneCap, 0, st>>>(qd, nq, K);
     return cudaGetLastError();
 }
 

@@ -431,7 +431,7 @@ k_tc_dist(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_lo, in
 // R..Rpad-1 and columns m..Kpad-1 are zero.  scale[r]: the factor that turns stored
 // values back into x (amax for FP16/BF16, amax / 448 for E4M3; 0 for a zero row).
 template <int FMT>
-__global__ void k_pack(const float* __restrict__ src, int ld, int m, int64_t R, int64_t Rpad, int Kpad,
+__device__ __forceinline__ void pack_body(const float* __restrict__ src, int ld, int m, int64_t R, int64_t Rpad, int Kpad,
                        uint8_t* __restrict__ hi, uint8_t* __restrict__ lo, float* __restrict__ scale)
 {
     const int lane = threadIdx.x & 31;
@@ -465,6 +465,22 @@ __global__ void k_pack(const float* __restrict__ src, int ld, int m, int64_t R, 
     if (lane == 0) scale[r] = amax / kTop;
 }
 
+template <int FMT>
+__global__ void k_pack(const float* __restrict__ src, int ld, int m, int64_t R, int64_t Rpad, int Kpad,
+                       uint8_t* __restrict__ hi, uint8_t* __restrict__ lo, float* __restrict__ scale)
+{
+    pack_body<FMT>(src, ld, m, R, Rpad, Kpad, hi, lo, scale);
+}
+
+template <int FMT>
+__global__ void k_pack_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int ld, int m, int Kpad)
+{
+    if ((int)blockIdx.y >= *nq) return;
+    const QDesc& d = qd[blockIdx.y];
+    pack_body<FMT>(d.Q, ld, m, d.h, d.npad, Kpad, static_cast<uint8_t*>(d.q_hi), static_cast<uint8_t*>(d.q_lo),
+                   d.q_scale);
+}
+
 }  // namespace
 
 size_t tc_dist_smem_bytes(int fmt, int stages, int KC)
@@ -494,6 +510,21 @@ int tc_dist_stages(int fmt, int KC)
     int s = 8;
     while (s >= 2 && tc_dist_smem_bytes(fmt, s, KC) > budget) --s;
     return s >= 2 ? s : 0;
+}
+
+cudaError_t launch_pack_b(int fmt, const QDesc* qd, const int* nq, int max_q, int max_rows, int ld, int m,
+                          int Kpad, cudaStream_t st)
+{
+    if (max_q <= 0 || max_rows <= 0) return cudaSuccess;
+    const int warps = 8;
+    const dim3 g((unsigned)((max_rows + warps - 1) / warps), (unsigned)max_q);
+    switch (fmt) {
+    case TC_SPLIT: k_pack_b<TC_SPLIT><<<g, warps * 32, 0, st>>>(qd, nq, ld, m, Kpad); break;
+    case TC_BF16: k_pack_b<TC_BF16><<<g, warps * 32, 0, st>>>(qd, nq, ld, m, Kpad); break;
+    case TC_E4M3: k_pack_b<TC_E4M3><<<g, warps * 32, 0, st>>>(qd, nq, ld, m, Kpad); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pack(int fmt, const float* src, int ld, int m, int64_t R, int64_t Rpad, int Kpad, void* hi,

@@ -410,3 +410,33 @@ def test_pruned_topk_equals_unpruned_small_queries(emd, meas, k):
     finally:
         emd.emd_db_destroy(dbp)
         emd.emd_db_destroy(dbf)
+
+
+# --------------------------------------------------------------------- batched form
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32_tc", "bf16"])
+def test_batched_equals_per_query(emd, precision):
+    """One launch per step over a batch (batched=1) against the per-query kernels
+    (batched=0): the same device bodies, so every distance and top-K is bit-identical.
+    A small batch_columns forces several sub-batches per call."""
+    w = emd_synth.small_text(99, 2500, 48, 900, 23, 4, 50, 1, 150)
+    rp, qi, qw = w.queries.row_ptr, w.queries.col, w.queries.val
+    db_q = make_db(emd, w, precision=precision, max_query_h=160, max_table_k=160, batched=0)
+    db_b = make_db(emd, w, precision=precision, max_query_h=160, max_table_k=160, batch_columns=512, max_batch=8)
+    try:
+        cases = [("rwmd", 1), ("omr", 1), ("act", 2), ("act", 4), ("act", 8)]
+        if precision != "bf16":
+            cases += [("act", 16), ("ict", 1)]
+        for meas, k in cases:
+            dirs = ("fwd", "rev", "max") if not (meas == "ict" and precision == "bf16") else ("rev",)
+            for d in dirs:
+                a = emd.emd_query_batch(db_q, rp, qi, qw, meas, k, d)
+                b = emd.emd_query_batch(db_b, rp, qi, qw, meas, k, d)
+                assert np.array_equal(a, b), (meas, k, d)
+            for K in (10, 32):
+                ai, ad = emd.emd_topk(db_q, rp, qi, qw, meas, k, "max", K)
+                bi, bd = emd.emd_topk(db_b, rp, qi, qw, meas, k, "max", K)
+                assert np.array_equal(ai, bi) and np.array_equal(ad, bd), (meas, k, K)
+    finally:
+        emd.emd_db_destroy(db_q)
+        emd.emd_db_destroy(db_b)
