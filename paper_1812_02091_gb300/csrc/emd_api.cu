@@ -395,7 +395,12 @@ emd_status run_subbatch_launch(int slot, emd_db* db, const int64_t* rp, const in
             if (db->tc)
                 EMD_CUDA(launch_pack_b(db->tcfmt, D_, nqd, nb, max_npad, db->ldm, db->m, db->kpad, st), "query pack");
         }
-        if (db->tc) {
+        if (db->tc && tc_batch_stages(db->tcfmt, db->kpad / 64) >= 2) {
+            Phase p(db, 1, 1, st);
+            EMD_CUDA(launch_tc_dist_batch(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
+                                          db->used_ids, db->v_used, D_, nqd, nb, db->kpad, db->err, st),
+                     "distance matrices (tensor cores, batched)");
+        } else if (db->tc) {
             Phase p(db, 1, nb, st);
             for (int q = 0; q < nb; ++q) {
                 const QDesc& d = hd[q];

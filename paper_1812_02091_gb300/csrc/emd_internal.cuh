@@ -178,6 +178,15 @@ cudaError_t launch_dist_fp32_b(const QDesc* qd, const int* nq, int max_q, int ma
                                int lda, const float* anorm, const int32_t* a_ids, int K, cudaStream_t st);
 cudaError_t launch_dist_gather_b(const QDesc* qd, const int* nq, int max_q, const float* cost, int64_t v,
                                  const int32_t* a_ids, int64_t M, int* err, cudaStream_t st);
+// Tensor-core distance matrices of every query of a batch (qd[q].q_hi / q_lo / q_scale /
+// qnorm / qidx / h / npad -> qd[q].D, ldd); the vocabulary panel stays resident while the
+// batch's column tiles stream past it.  max_q: queries the grid is sized for (the actual
+// count is *nq).  cudaErrorInvalidValue when the panel does not fit in shared memory
+// (tc_batch_stages == 0): use launch_tc_dist per query instead.
+int tc_batch_stages(int fmt, int KC);
+cudaError_t launch_tc_dist_batch(int fmt, const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
+                                 const float* a_norm, const int32_t* a_ids, int64_t M, const QDesc* qd, const int* nq,
+                                 int max_q, int Kpad, int* err, cudaStream_t st);
 // max_tk: the largest table width of the batch; rerank: the approximate precisions' form
 // (V: the used vocabulary rows, ldv floats each).
 cudaError_t launch_table_b(const QDesc* qd, const int* nq, int max_q, int64_t M, int max_tk, bool rerank,

@@ -424,6 +424,254 @@ k_tc_dist(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_lo, in
     }
 }
 
+// Batched form: every query of a batch against the same vocabulary.  Work item = (row tile
+// r, query group g): the CTA loads all K chunks of the vocabulary tile once into shared
+// memory (the "A panel", resident for the whole item) and streams the column tiles of the
+// group's queries (each query's tiles n0 = 0, 128, ... < h) through a ring of B-chunk
+// stages.  The vocabulary is thus read from HBM once per batch (once per group) instead of
+// once per query.  MMA order, accumulators and epilogue are those of k_tc_dist, so each
+// D[u, j] is bit-identical to the per-query kernel's.  Barriers: afull (A panel landed),
+// afree (the item's MMAs are done with it), full/empty per B stage, tfull/tempty per TMEM
+// accumulator buffer; every wait is bounded as in k_tc_dist.
+template <int FMT>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_tc_dist_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_lo, int64_t Mpad,
+                const float* __restrict__ a_scale, const float* __restrict__ a_norm,
+                const int32_t* __restrict__ a_ids, int64_t M, const QDesc* __restrict__ qd,
+                const int* __restrict__ nq_dev, int groups, int KC, int stages, int* __restrict__ err)
+{
+    constexpr bool SPLIT = FMT == TC_SPLIT;
+    constexpr uint32_t EB = TcFmt<FMT>::EB;
+    constexpr int kParts = (int)TcFmt<FMT>::parts;
+    constexpr uint32_t kABytes = TC_BM * EB;
+    constexpr uint32_t kBBytes = TC_BN * EB;
+    constexpr uint32_t kSbo = 8 * EB;
+    constexpr uint32_t kAChunk = kParts * kABytes;
+    constexpr uint32_t kBStage = kParts * kBBytes;
+    constexpr uint32_t kAcc = SPLIT ? 256 : 128;
+    constexpr uint32_t kCols = 2 * kAcc;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* apanel = smem;                                   // KC A chunks (hi | lo)
+    uint8_t* bring = apanel + (size_t)KC * kAChunk;           // stages B chunks (hi | lo)
+    uint64_t* full = reinterpret_cast<uint64_t*>(bring + (size_t)stages * kBStage);
+    uint64_t* empty = full + stages;
+    uint64_t* tfull = empty + stages;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* afull = tempty + 2;
+    uint64_t* afree = afull + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(afree + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nq = *nq_dev;
+    const int m_tiles = (int)(Mpad / TC_BM);
+    const int total = m_tiles * groups;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 8);
+        }
+        mbar_init(afull, 1);
+        mbar_init(afree, 1);
+        *abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, kCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    auto fail = [&]() {
+        atomicOr(err, ERR_TIMEOUT);
+        *abort_flag = 1;
+    };
+    auto qrange = [&](int g, int& qa, int& qb) {
+        qa = (int)((int64_t)g * nq / groups);
+        qb = (int)((int64_t)(g + 1) * nq / groups);
+    };
+
+    if (warp == 0 && lane == 0) {
+        int64_t gb = 0;
+        int items = 0;
+        bool ok = true;
+        for (int w = blockIdx.x; w < total && ok && !*abort_flag; w += gridDim.x, ++items) {
+            const int64_t m0 = (int64_t)(w % m_tiles) * TC_BM;
+            if (items > 0 && !mbar_wait(afree, (uint32_t)(items - 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                fail();
+                break;
+            }
+            mbar_expect_tx(afull, (uint32_t)KC * kAChunk);
+            for (int c = 0; c < KC; ++c) {
+                uint8_t* ast = apanel + (size_t)c * kAChunk;
+                bulk_g2s(ast, A_hi + ((int64_t)c * Mpad + m0) * EB, kABytes, afull);
+                if (SPLIT) bulk_g2s(ast + kABytes, A_lo + ((int64_t)c * Mpad + m0) * EB, kABytes, afull);
+            }
+            int qa, qb;
+            qrange(w / m_tiles, qa, qb);
+            for (int q = qa; q < qb && ok; ++q) {
+                const QDesc& d = qd[q];
+                const uint8_t* bh = static_cast<const uint8_t*>(d.q_hi);
+                const uint8_t* bl = static_cast<const uint8_t*>(d.q_lo);
+                for (int n0 = 0; n0 < d.h && ok; n0 += TC_BN) {
+                    const int Nt = min(TC_BN, (int)round_up(d.h - n0, 16));
+                    const uint32_t b_bytes = (uint32_t)Nt * EB;
+                    for (int c = 0; c < KC; ++c, ++gb) {
+                        const int s = (int)(gb % stages);
+                        if (gb >= stages &&
+                            !mbar_wait(&empty[s], (uint32_t)((gb / stages) - 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                            fail();
+                            ok = false;
+                            break;
+                        }
+                        uint8_t* bst = bring + (size_t)s * kBStage;
+                        mbar_expect_tx(&full[s], (uint32_t)kParts * b_bytes);
+                        bulk_g2s(bst, bh + ((int64_t)c * d.npad + n0) * EB, b_bytes, &full[s]);
+                        if (SPLIT) bulk_g2s(bst + kBBytes, bl + ((int64_t)c * d.npad + n0) * EB, b_bytes, &full[s]);
+                    }
+                }
+            }
+        }
+        // no copy may still be landing in shared memory when the block leaves
+        const uint64_t tail = global_ns() + TC_TIMEOUT_NS;
+        for (int64_t c = gb > stages ? gb - stages : 0; c < gb; ++c)
+            if (!mbar_wait(&full[c % stages], (uint32_t)(c / stages) & 1u, tail)) atomicOr(err, ERR_TIMEOUT);
+        if (items > 0 && !mbar_wait(afull, (uint32_t)(items - 1) & 1u, tail)) atomicOr(err, ERR_TIMEOUT);
+    } else if (warp == 1 && lane == 0) {
+        int64_t gb = 0;
+        int it = 0, items = 0;
+        bool ok = true;
+        for (int w = blockIdx.x; w < total && ok && !*abort_flag; w += gridDim.x, ++items) {
+            if (!mbar_wait(afull, (uint32_t)items & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                fail();
+                break;
+            }
+            int qa, qb;
+            qrange(w / m_tiles, qa, qb);
+            for (int q = qa; q < qb && ok; ++q) {
+                const int h = qd[q].h;
+                for (int n0 = 0; n0 < h && ok; n0 += TC_BN, ++it) {
+                    const int Nt = min(TC_BN, (int)round_up(h - n0, 16));
+                    const uint32_t idesc = (1u << 4) | (TcFmt<FMT>::atype << 7) | (TcFmt<FMT>::atype << 10) |
+                                           ((uint32_t)(Nt >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+                    const int buf = it & 1;
+                    if (it >= 2 && !mbar_wait(&tempty[buf], (uint32_t)((it >> 1) - 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t acc0 = tmem + (uint32_t)buf * kAcc;
+                    for (int c = 0; c < KC; ++c, ++gb) {
+                        const int s = (int)(gb % stages);
+                        if (!mbar_wait(&full[s], (uint32_t)(gb / stages) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                            fail();
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t sa = smem_u32(apanel + (size_t)c * kAChunk);
+                        const uint32_t sa_lo = sa + kABytes;
+                        const uint32_t sb = smem_u32(bring + (size_t)s * kBStage);
+                        const uint32_t sb_lo = sb + kBBytes;
+#pragma unroll
+                        for (int ks = 0; ks < (int)TcFmt<FMT>::mmas; ++ks) {
+                            const uint32_t ko = (uint32_t)ks * 256u;
+                            const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+                            const uint64_t da = smem_desc(sa + ko, kSbo), db = smem_desc(sb + ko, kSbo);
+                            mma_issue<FMT>(acc0, da, db, idesc, acc);
+                            if (SPLIT) {
+                                mma_issue<FMT>(acc0 + 128, da, smem_desc(sb_lo + ko, kSbo), idesc, acc);
+                                mma_issue<FMT>(acc0 + 128, smem_desc(sa_lo + ko, kSbo), db, idesc, 1u);
+                            }
+                        }
+                        mma_commit(&empty[s]);
+                    }
+                    mma_commit(&tfull[buf]);
+                }
+            }
+            mma_commit(afree);  // the A panel is free once this item's MMAs complete
+        }
+    } else if (warp >= 2) {
+        const int qw4 = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const int row = qw4 * 32 + lane;
+        int it = 0;
+        bool ok = true;
+        for (int w = blockIdx.x; w < total && ok && !*abort_flag; w += gridDim.x) {
+            const int64_t m0 = (int64_t)(w % m_tiles) * TC_BM;
+            const int64_t u = m0 + row;
+            const bool row_ok = u < M;
+            const float su = row_ok ? a_scale[u] : 0.f;
+            const float nu = row_ok ? a_norm[u] : 0.f;
+            const int32_t idu = row_ok ? a_ids[u] : -1;
+            int qa, qb;
+            qrange(w / m_tiles, qa, qb);
+            for (int q = qa; q < qb && ok; ++q) {
+                const QDesc& d = qd[q];
+                const int N = d.h, ldd = d.ldd;
+                for (int n0 = 0; n0 < N; n0 += TC_BN, ++it) {
+                    const int Nt = min(TC_BN, (int)round_up(N - n0, 16));
+                    const int buf = it & 1;
+                    if (!mbar_wait(&tfull[buf], (uint32_t)(it >> 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t tbase = tmem + (uint32_t)buf * kAcc + ((uint32_t)(qw4 * 32) << 16);
+                    for (int cc = half * 64; cc < half * 64 + 64 && cc < Nt; cc += 32) {
+                        uint32_t r0[32], r1[32];
+                        tmem_ld32(tbase + (uint32_t)cc, r0);
+                        if (SPLIT) tmem_ld32(tbase + 128u + (uint32_t)cc, r1);
+                        tmem_wait_ld();
+                        const int lcol = n0 + cc + lane;
+                        const bool lok = lcol < N;
+                        const float cb_l = lok ? -2.f * d.q_scale[lcol] : 0.f;
+                        const float nb_l = lok ? d.qnorm[lcol] : 0.f;
+                        const int id_l = lok ? d.qidx[lcol] : -2;
+                        const float su2 = su;
+                        float* out = d.D + (row_ok ? u : 0) * ldd + n0 + cc;
+#pragma unroll
+                        for (int e4 = 0; e4 < 8; ++e4) {
+                            float o[4];
+#pragma unroll
+                            for (int tt = 0; tt < 4; ++tt) {
+                                const int e = e4 * 4 + tt;
+                                const float cb = __shfl_sync(0xffffffffu, cb_l, e);
+                                const float nb = __shfl_sync(0xffffffffu, nb_l, e);
+                                const int idc = __shfl_sync(0xffffffffu, id_l, e);
+                                float dot = __uint_as_float(r0[e]);
+                                if (SPLIT) dot = fmaf(__uint_as_float(r1[e]), 1.0f / 2048.0f, dot);
+                                const float d2 = fmaf(cb * su2, dot, nu + nb);
+                                const float dd = (idu == idc) ? 0.f : __fsqrt_rn(fmaxf(d2, 0.f));
+                                o[tt] = (n0 + cc + e < N) ? dd : INFINITY;
+                            }
+                            if (row_ok && n0 + cc + e4 * 4 < ldd)
+                                *reinterpret_cast<float4*>(out + e4 * 4) = make_float4(o[0], o[1], o[2], o[3]);
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tempty[buf]);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kCols);
+    }
+}
+
 // Pack rows of an FP32 matrix (ld floats per row, first m used) into the canonical layout
 // above.  For 2-byte formats element (r, k) of a matrix with Rpad rows lives at byte
 // 2 * ((k/64)*Rpad*64 + (r/8)*512 + ((k%64)/8)*64 + (r%8)*8 + k%8); for E4M3 at byte
@@ -558,6 +806,62 @@ static cudaError_t tc_launch(dim3 grid, size_t smem, cudaStream_t st, const void
         static_cast<const uint8_t*>(B_hi), static_cast<const uint8_t*>(B_lo), Npad, b_scale, b_norm, b_ids, N, KC,
         stages, D, ldd, err);
     return cudaGetLastError();
+}
+
+size_t tc_batch_smem_bytes(int fmt, int stages, int KC)
+{
+    const size_t eb = fmt == TC_E4M3 ? 64 : 128;
+    const size_t parts = fmt == TC_SPLIT ? 2 : 1;
+    return 1024 + (size_t)KC * parts * TC_BM * eb + (size_t)stages * parts * TC_BN * eb + (2 * (size_t)stages + 6) * 8 + 16;
+}
+
+// B stages (2..8) beside the resident vocabulary panel; 0 when the panel leaves no room.
+int tc_batch_stages(int fmt, int KC)
+{
+    const size_t budget = 227 * 1024;
+    int s = 8;
+    while (s >= 2 && tc_batch_smem_bytes(fmt, s, KC) > budget) --s;
+    return s >= 2 ? s : 0;
+}
+
+template <int FMT>
+static cudaError_t tc_batch_launch(dim3 grid, size_t smem, cudaStream_t st, const void* A_hi, const void* A_lo,
+                                   int64_t Mpad, const float* a_scale, const float* a_norm, const int32_t* a_ids,
+                                   int64_t M, const QDesc* qd, const int* nq, int groups, int KC, int stages, int* err)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_tc_dist_batch<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_tc_dist_batch<FMT><<<grid, TC_THREADS, smem, st>>>(static_cast<const uint8_t*>(A_hi),
+                                                         static_cast<const uint8_t*>(A_lo), Mpad, a_scale, a_norm,
+                                                         a_ids, M, qd, nq, groups, KC, stages, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_dist_batch(int fmt, const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
+                                 const float* a_norm, const int32_t* a_ids, int64_t M, const QDesc* qd, const int* nq,
+                                 int max_q, int Kpad, int* err, cudaStream_t st)
+{
+    if (M <= 0 || max_q <= 0) return cudaSuccess;
+    const int KC = Kpad / 64;
+    const int stages = tc_batch_stages(fmt, KC);
+    if (stages < 2) return cudaErrorInvalidValue;
+    const size_t smem = tc_batch_smem_bytes(fmt, stages, KC);
+    const int m_tiles = (int)(Mpad / TC_BM);
+    const int sms = sm_count();
+    const int groups = std::max(1, std::min(max_q, (2 * sms + m_tiles - 1) / m_tiles));
+    dim3 grid((unsigned)std::min<int64_t>((int64_t)m_tiles * groups, sms));
+    switch (fmt) {
+    case TC_SPLIT:
+        return tc_batch_launch<TC_SPLIT>(grid, smem, st, A_hi, A_lo, Mpad, a_scale, a_norm, a_ids, M, qd, nq, groups,
+                                         KC, stages, err);
+    case TC_BF16:
+        return tc_batch_launch<TC_BF16>(grid, smem, st, A_hi, nullptr, Mpad, a_scale, a_norm, a_ids, M, qd, nq,
+                                        groups, KC, stages, err);
+    case TC_E4M3:
+        return tc_batch_launch<TC_E4M3>(grid, smem, st, A_hi, nullptr, Mpad, a_scale, a_norm, a_ids, M, qd, nq,
+                                        groups, KC, stages, err);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_tc_dist(int fmt, const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
