@@ -308,6 +308,9 @@ def main():
     ap.add_argument("--serve-rates", default="1000,2000,3000",
                     help="offered request rates (requests/s) of the serving sweep; empty: skip it")
     ap.add_argument("--serve-requests", type=int, default=6000, help="requests per serving rate point")
+    ap.add_argument("--probe", action="store_true",
+                    help="small fixed case for profiler captures: the bench workload's database, --batch "
+                         "queries per batch (16 suggested), --warmup + --steps batches, ~1.5 GB on the device")
     ap.add_argument("--precision-steps", type=int, default=5,
                     help="batches per arithmetic in the precision comparison; 0: skip it")
     args = ap.parse_args()
@@ -318,6 +321,8 @@ def main():
 
     if args.impl == "reference":
         return main_reference(args, rank, world)
+    if args.probe:
+        return main_probe(args, local)
 
     import torch
     import paper_1812_02091_gb300 as emd
@@ -570,6 +575,39 @@ def main():
     emd.emd_db_destroy(db)
     if dist:
         dist.destroy_process_group()
+
+
+def main_probe(args, local):
+    """Runs the pruned top-K path on a few batches with a small batch workspace, for ncu
+    captures of single launches; prints the step times (not a bench line)."""
+    import torch
+    import emd_synth
+    import paper_1812_02091_gb300 as emd
+    torch.cuda.set_device(local)
+    w = emd_synth.config(2)
+    B = args.batch
+    db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
+                           emd.emd_db_options_default(precision=args.precision, device=local, max_query_h=1024,
+                                                      max_batch=B, batch_columns=max(B * 128, 1024)))
+    stream = torch.cuda.current_stream()
+    oi = torch.empty((B, args.topk), dtype=torch.int64, device="cuda")
+    od = torch.empty((B, args.topk), dtype=torch.float32, device="cuda")
+    times = []
+    small = np.nonzero(np.diff(w.queries.row_ptr) <= 128)[0]  # one column tile each: fixed batches
+    for s in range(args.warmup + args.steps):
+        sub = w.queries.subset(small[np.arange(s * B, (s + 1) * B) % len(small)])
+        qi, qw = torch.from_numpy(sub.col).cuda(), torch.from_numpy(sub.val).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        emd.emd_topk_device(db, sub.row_ptr, qi, qw, oi, od, "act", args.k, "max", args.topk,
+                            stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    emd.emd_db_check_device_errors(db)
+    emd.emd_db_destroy(db)
+    print(json.dumps({"probe": "pruned top-K batches of queries with h_q <= 128", "batch": B,
+                      "precision": args.precision,
+                      "ms_per_batch": [round(1e3 * t, 3) for t in times]}))
 
 
 def main_reference(args, rank, world):

@@ -42,6 +42,8 @@ constexpr int TC_BM = 128;          // rows per tile = TMEM lanes
 constexpr int TC_BN = 128;          // largest column tile
 constexpr int TC_THREADS = 320;  // warp 0 copies, warp 1 MMA, warps 2..9 epilogue
 constexpr uint64_t TC_TIMEOUT_NS = 2000000000ull;
+constexpr int TCB_EPI_WARPS = 16;                  // batched form: epilogue warps
+constexpr int TCB_THREADS = 64 + 32 * TCB_EPI_WARPS;  // + copy warp + MMA warp
 
 // Per-format constants: bytes of a 64-element row segment, operand parts, MMAs per
 // 64-element chunk (each advances 2 core matrices = 256 B along K).
@@ -182,7 +184,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
         : "r"(taddr));
 }
 
+// 16 consecutive TMEM columns of this thread's lane (32x32b shape, 16 repetitions).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15])
+        : "r"(taddr));
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// sqrt(max(x, 0)), correctly rounded; shared by the per-query and batched epilogues.
+__device__ __forceinline__ float dist_sqrt(float x) { return __fsqrt_rn(fmaxf(x, 0.f)); }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 {
@@ -404,7 +421,7 @@ k_tc_dist(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_lo, in
                         float dot = __uint_as_float(r0[e]);
                         if (SPLIT) dot = fmaf(__uint_as_float(r1[e]), 1.0f / 2048.0f, dot);
                         const float d2 = fmaf(cb * su2, dot, nu + nb);
-                        const float d = (idu == idc) ? 0.f : __fsqrt_rn(fmaxf(d2, 0.f));
+                        const float d = (idu == idc) ? 0.f : dist_sqrt(d2);
                         o[tt] = (n0 + cc + e < N) ? d : INFINITY;
                     }
                     if (row_ok && n0 + cc + e4 * 4 < ldd)
@@ -434,7 +451,7 @@ k_tc_dist(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_lo, in
 // afree (the item's MMAs are done with it), full/empty per B stage, tfull/tempty per TMEM
 // accumulator buffer; every wait is bounded as in k_tc_dist.
 template <int FMT>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TCB_THREADS, 1)
 k_tc_dist_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_lo, int64_t Mpad,
                 const float* __restrict__ a_scale, const float* __restrict__ a_norm,
                 const int32_t* __restrict__ a_ids, int64_t M, const QDesc* __restrict__ qd,
@@ -475,7 +492,7 @@ k_tc_dist_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 8);
+            mbar_init(&tempty[b], TCB_EPI_WARPS);
         }
         mbar_init(afull, 1);
         mbar_init(afree, 1);
@@ -599,8 +616,10 @@ k_tc_dist_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
             mma_commit(afree);  // the A panel is free once this item's MMAs complete
         }
     } else if (warp >= 2) {
+        // epilogue: 16 warps, four per TMEM lane quarter (warp w reads lanes 32*(w%4) ..
+        // +31 = tile rows), each draining 32 of the tile's columns
         const int qw4 = warp & 3;
-        const int half = (warp - 2) >> 2;
+        const int cc = ((warp - 2) >> 2) * 32;
         const int row = qw4 * 32 + lane;
         int it = 0;
         bool ok = true;
@@ -616,45 +635,54 @@ k_tc_dist_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
             for (int q = qa; q < qb && ok; ++q) {
                 const QDesc& d = qd[q];
                 const int N = d.h, ldd = d.ldd;
+                const float* qsc = d.q_scale;
+                const float* qnm = d.qnorm;
+                const int32_t* qid = d.qidx;
+                float* Dq = d.D;
                 for (int n0 = 0; n0 < N; n0 += TC_BN, ++it) {
                     const int Nt = min(TC_BN, (int)round_up(N - n0, 16));
                     const int buf = it & 1;
+                    // this warp's column constants, fetched before the wait (coalesced)
+                    const int lcol = n0 + cc + lane;
+                    const bool lok = lcol < N;
+                    const float cb_l = lok ? -2.f * qsc[lcol] : 0.f;
+                    const float nb_l = lok ? qnm[lcol] : 0.f;
+                    const int id_l = lok ? qid[lcol] : -2;
                     if (!mbar_wait(&tfull[buf], (uint32_t)(it >> 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
                         fail();
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t tbase = tmem + (uint32_t)buf * kAcc + ((uint32_t)(qw4 * 32) << 16);
-                    for (int cc = half * 64; cc < half * 64 + 64 && cc < Nt; cc += 32) {
-                        uint32_t r0[32], r1[32];
-                        tmem_ld32(tbase + (uint32_t)cc, r0);
-                        if (SPLIT) tmem_ld32(tbase + 128u + (uint32_t)cc, r1);
-                        tmem_wait_ld();
-                        const int lcol = n0 + cc + lane;
-                        const bool lok = lcol < N;
-                        const float cb_l = lok ? -2.f * d.q_scale[lcol] : 0.f;
-                        const float nb_l = lok ? d.qnorm[lcol] : 0.f;
-                        const int id_l = lok ? d.qidx[lcol] : -2;
+                    if (cc < Nt) {
+                        const uint32_t tbase = tmem + (uint32_t)buf * kAcc + ((uint32_t)(qw4 * 32) << 16);
                         const float su2 = su;
-                        float* out = d.D + (row_ok ? u : 0) * ldd + n0 + cc;
+                        float* out = Dq + (row_ok ? u : 0) * ldd + n0 + cc;
 #pragma unroll
-                        for (int e4 = 0; e4 < 8; ++e4) {
+                        for (int hh = 0; hh < 2; ++hh) {  // two halves of 16 columns
+                        uint32_t r0[16], r1[16];
+                        tmem_ld16(tbase + (uint32_t)(cc + 16 * hh), r0);
+                        if (SPLIT) tmem_ld16(tbase + 128u + (uint32_t)(cc + 16 * hh), r1);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int e4 = 4 * hh; e4 < 4 * hh + 4; ++e4) {
                             float o[4];
 #pragma unroll
                             for (int tt = 0; tt < 4; ++tt) {
                                 const int e = e4 * 4 + tt;
+                                const int er = e - 16 * hh;
                                 const float cb = __shfl_sync(0xffffffffu, cb_l, e);
                                 const float nb = __shfl_sync(0xffffffffu, nb_l, e);
                                 const int idc = __shfl_sync(0xffffffffu, id_l, e);
-                                float dot = __uint_as_float(r0[e]);
-                                if (SPLIT) dot = fmaf(__uint_as_float(r1[e]), 1.0f / 2048.0f, dot);
+                                float dot = __uint_as_float(r0[er]);
+                                if (SPLIT) dot = fmaf(__uint_as_float(r1[er]), 1.0f / 2048.0f, dot);
                                 const float d2 = fmaf(cb * su2, dot, nu + nb);
-                                const float dd = (idu == idc) ? 0.f : __fsqrt_rn(fmaxf(d2, 0.f));
+                                const float dd = (idu == idc) ? 0.f : dist_sqrt(d2);
                                 o[tt] = (n0 + cc + e < N) ? dd : INFINITY;
                             }
                             if (row_ok && n0 + cc + e4 * 4 < ldd)
                                 *reinterpret_cast<float4*>(out + e4 * 4) = make_float4(o[0], o[1], o[2], o[3]);
+                        }
                         }
                     }
                     tc_fence_before();
@@ -831,7 +859,7 @@ static cudaError_t tc_batch_launch(dim3 grid, size_t smem, cudaStream_t st, cons
 {
     cudaError_t e = cudaFuncSetAttribute(k_tc_dist_batch<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_tc_dist_batch<FMT><<<grid, TC_THREADS, smem, st>>>(static_cast<const uint8_t*>(A_hi),
+    k_tc_dist_batch<FMT><<<grid, TCB_THREADS, smem, st>>>(static_cast<const uint8_t*>(A_hi),
                                                          static_cast<const uint8_t*>(A_lo), Mpad, a_scale, a_norm,
                                                          a_ids, M, qd, nq, groups, KC, stages, err);
     return cudaGetLastError();
