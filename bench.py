@@ -395,7 +395,7 @@ def main():
         return step_ms, total, prof, prof["total_launches"] - launches0, kept
 
     with ClockSampler(local) as clk:
-        step_ms, total_ms, prof, gpu_launches, results = run_steps(db, args.steps, keep=4)
+        step_ms, total_ms, prof_main, gpu_launches, results = run_steps(db, args.steps, keep=4)
     queries_done = args.batch * args.steps * world
     value = queries_done / (total_ms / 1e3)
 
@@ -561,6 +561,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(gpu_launches),
+            "graph_replays": int(prof_main["graph_launches"]),
             "clocks": clk.summary(),
             "latency_ms_per_query_in_batch": {"p50": float(np.percentile(lat, 50)),
                                               "p99": float(np.percentile(lat, 99))},

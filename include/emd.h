@@ -91,6 +91,9 @@ typedef struct {
     int32_t batch_columns;   /* batched form: distance-matrix columns of one batch (sum over its
                                 queries of h_q rounded up to 32; default 16384, at least
                                 max_query_h).  Device memory: 4 x v_used x batch_columns bytes */
+    int32_t graphs;          /* batched form: 1 (default) replays each (measure, k, K, direction)
+                                sequence from a captured CUDA graph; 0: launches directly.
+                                Profiling (emd_db_set_profiling) launches directly */
 } emd_db_options;
 
 typedef struct {
@@ -120,6 +123,8 @@ typedef struct {
     int64_t total_launches; /* every kernel launch since creation, profiling on or off */
     int64_t pruned_queries; /* max-direction top-K queries answered by the pruned path */
     int64_t prune_fallbacks; /* of those, queries recomputed over all documents */
+    int64_t graph_launches;  /* batch sequences replayed from captured graphs (their kernels are
+                                included in the launch counts) */
 } emd_profile;
 
 /* Fill *opt with the defaults listed above.  Never fails. */

@@ -44,7 +44,7 @@ class emd_db_options(ctypes.Structure):
                 ("rerank_margin", ctypes.c_int32), ("max_query_h", ctypes.c_int32),
                 ("max_table_k", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("prune_topk", ctypes.c_int32), ("lanes", ctypes.c_int32), ("batched", ctypes.c_int32),
-                ("batch_columns", ctypes.c_int32)]
+                ("batch_columns", ctypes.c_int32), ("graphs", ctypes.c_int32)]
 
 
 class emd_db_info(ctypes.Structure):
@@ -61,7 +61,7 @@ class emd_queries(ctypes.Structure):
 class emd_profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 7), ("launches", ctypes.c_int64 * 7),
                 ("total_launches", ctypes.c_int64), ("pruned_queries", ctypes.c_int64),
-                ("prune_fallbacks", ctypes.c_int64)]
+                ("prune_fallbacks", ctypes.c_int64), ("graph_launches", ctypes.c_int64)]
 
 
 class emd_server_options(ctypes.Structure):
@@ -306,7 +306,7 @@ def emd_db_profile_get(db) -> dict:
     _check(load().emd_db_profile_get(db, ctypes.byref(p)))
     return {"ms": dict(zip(PHASES, list(p.ms))), "launches": dict(zip(PHASES, list(p.launches))),
             "total_launches": int(p.total_launches), "pruned_queries": int(p.pruned_queries),
-            "prune_fallbacks": int(p.prune_fallbacks)}
+            "prune_fallbacks": int(p.prune_fallbacks), "graph_launches": int(p.graph_launches)}
 
 
 def emd_db_profile_reset(db):

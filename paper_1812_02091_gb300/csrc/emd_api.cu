@@ -83,6 +83,9 @@ void release(emd_db* db)
         if (L.done) cudaEventDestroy(L.done);
         if (L.st) cudaStreamDestroy(L.st);
     }
+    for (auto& kv : db->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (db->cap_stream) cudaStreamDestroy(db->cap_stream);
     if (db->fork) cudaEventDestroy(db->fork);
     if (db->stream) cudaStreamDestroy(db->stream);
     delete db;
@@ -318,6 +321,119 @@ emd_status run_lanes(emd_db* db, const int64_t* rp, const int32_t* qidx, const f
                      int64_t i1, int meas, int k, int dir, int K, bool pruned, float* out_t, int64_t* out_idx,
                      float* out_dist, cudaStream_t st);
 
+// The kernels of one sub-batch whose descriptors sit in ring slot `slot`.  Grids are sized
+// from the handle's limits (max_batch queries, max_query_h bins, the table width of k)
+// and every block checks the query count on the device, so the same sequence serves every
+// batch with these parameters and can be captured into a graph.  hd (host descriptors of
+// nb queries) only when Phase 1 must run per query.
+emd_status launch_sequence(emd_db* db, int slot, int meas, int k, int K, int dir, bool pruned, const QDesc* hd,
+                           int nb, cudaStream_t st)
+{
+    const int B = db->opt.max_batch;
+    const QDesc* D_ = db->qd_dev + (int64_t)slot * B;
+    const int* nqd = db->nq_dev + slot;
+    const int64_t n = db->n;
+    const int H = db->opt.max_query_h;
+    const int tk_b = dir != EMD_DIR_REV ? table_width(meas, k, H) : 0;
+    const int kc_b = db->approx ? std::min(rerank_width(db, tk_b, H), kRerankMax) : tk_b;
+    if (db->cost_mode) {
+        Phase p(db, 1, 1, st);
+        EMD_CUDA(launch_dist_gather_b(D_, nqd, B, db->cost, db->v, db->used_ids, db->v_used, db->err, st),
+                 "distance gather");
+    } else {
+        {
+            Phase p(db, 0, db->tc ? 2 : 1, st);
+            EMD_CUDA(launch_gather_rows_b(D_, nqd, B, db->qrows_max, db->emb, db->v, db->ldm, db->m, db->err, st),
+                     "query gather");
+            if (db->tc)
+                EMD_CUDA(launch_pack_b(db->tcfmt, D_, nqd, B, (int)round_up(H, 128), db->ldm, db->m, db->kpad, st),
+                         "query pack");
+        }
+        if (db->tc && !hd) {
+            Phase p(db, 1, 1, st);
+            EMD_CUDA(launch_tc_dist_batch(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
+                                          db->used_ids, db->v_used, D_, nqd, B, db->kpad, db->err, st),
+                     "distance matrices (tensor cores, batched)");
+        } else if (db->tc) {
+            Phase p(db, 1, nb, st);
+            for (int q = 0; q < nb; ++q) {
+                const QDesc& d = hd[q];
+                EMD_CUDA(launch_tc_dist(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
+                                        db->used_ids, db->v_used, d.q_hi, d.q_lo, d.npad, d.q_scale, d.qnorm, d.qidx,
+                                        d.h, db->kpad, d.D, d.ldd, db->err, st),
+                         "distance matrix (tensor cores)");
+            }
+        } else {
+            Phase p(db, 1, 1, st);
+            EMD_CUDA(launch_dist_fp32_b(D_, nqd, B, db->ldd_max, db->emb_used, db->v_used, db->ldm, db->norm_used,
+                                        db->used_ids, db->m, st),
+                     "distance matrix");
+        }
+    }
+    if (dir != EMD_DIR_REV) {
+        {
+            Phase p(db, 2, 1, st);
+            EMD_CUDA(launch_table_b(D_, nqd, B, db->v_used, tk_b, db->approx, kc_b, db->emb_used, db->ldm, st),
+                     "top-k table");
+        }
+        Phase p(db, 3, 1, st);
+        EMD_CUDA(launch_fwd_b(meas, D_, nqd, B, db->row_ptr, db->col, db->val, n, dir == EMD_DIR_FWD, st),
+                 "forward pass");
+    }
+    if (pruned) {
+        {
+            Phase p(db, 5, topk_launch_count(n), st);
+            EMD_CUDA(launch_topk_b(D_, nqd, B, n, K, db->topk_scratch, true, st), "forward top-K");
+        }
+        EMD_CUDA(cudaMemsetAsync(db->bcand_count, 0, sizeof(int) * B, st), "candidate counts");
+        Phase p(db, 4, 3, st);
+        EMD_CUDA(launch_prune_b(meas, k, D_, nqd, B, db->row_ptr, db->col, db->val, n, K, st),
+                 "pruned reverse pass");
+        return EMD_OK;
+    }
+    if (dir != EMD_DIR_FWD) {
+        Phase p(db, 4, 1, st);
+        EMD_CUDA(launch_rev_b(meas, k, dir, D_, nqd, B, db->row_ptr, db->col, db->val, n, st), "reverse pass");
+    }
+    if (K > 0) {
+        Phase p(db, 5, topk_launch_count(n), st);
+        EMD_CUDA(launch_topk_b(D_, nqd, B, n, K, db->topk_scratch, false, st), "top-K");
+    }
+    return EMD_OK;
+}
+
+// Captures launch_sequence for these parameters into an executable graph (on the handle's
+// capture stream); the launch counts of one replay are kept beside it.
+emd_status capture_sequence(emd_db* db, int slot, int meas, int k, int K, int dir, bool pruned, GraphEntry* g)
+{
+    int64_t l0[EMD_N_PHASES], t0 = db->total_launches;
+    for (int p = 0; p < EMD_N_PHASES; ++p) l0[p] = db->launches[p];
+    cudaStream_t cs = db->cap_stream;
+    EMD_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "graph capture");
+    emd_status s = launch_sequence(db, slot, meas, k, K, dir, pruned, nullptr, 0, cs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    for (int p = 0; p < EMD_N_PHASES; ++p) {
+        g->launches[p] = db->launches[p] - l0[p];
+        db->launches[p] = l0[p];
+    }
+    g->total = db->total_launches - t0;
+    db->total_launches = t0;
+    if (s != EMD_OK || e != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return s != EMD_OK ? s : cuda_fail(e, "graph capture");
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        g->exec = nullptr;
+        cudaGetLastError();
+        return cuda_fail(ei, "graph instantiate");
+    }
+    return EMD_OK;
+}
+
 // Queries j0..j1-1 of the batch i0.. as one launch per step (the batch fits the batch
 // workspace).  Outputs as run_batch.  Uses descriptor ring slot `slot`.
 emd_status run_subbatch_launch(int slot, emd_db* db, const int64_t* rp, const int32_t* qidx, const float* qw, int64_t i0,
@@ -365,6 +481,8 @@ emd_status run_subbatch_launch(int slot, emd_db* db, const int64_t* rp, const in
             d.cand_sym = db->bcand_sym + (int64_t)b * 2 * kPruneCap;
             d.cand_count = db->bcand_count + b;
             d.ok = db->cand_ok + b;
+        }
+        if (K > 0) {
             d.out_idx = out_idx + (int64_t)b * K;
             d.out_dist = out_dist + (int64_t)b * K;
         }
@@ -381,73 +499,28 @@ emd_status run_subbatch_launch(int slot, emd_db* db, const int64_t* rp, const in
     db->nq_host[slot] = nb;
     EMD_CUDA(cudaMemcpyAsync(dd, hd, sizeof(QDesc) * nb, cudaMemcpyHostToDevice, st), "descriptor upload");
     EMD_CUDA(cudaMemcpyAsync(nqd, db->nq_host + slot, sizeof(int), cudaMemcpyHostToDevice, st), "descriptor upload");
-    const QDesc* D_ = dd;
-    // Phase 1
-    if (db->cost_mode) {
-        Phase p(db, 1, 1, st);
-        EMD_CUDA(launch_dist_gather_b(D_, nqd, nb, db->cost, db->v, db->used_ids, db->v_used, db->err, st),
-                 "distance gather");
-    } else {
-        {
-            Phase p(db, 0, db->tc ? 2 : 1, st);
-            EMD_CUDA(launch_gather_rows_b(D_, nqd, nb, max_rows, db->emb, db->v, db->ldm, db->m, db->err, st),
-                     "query gather");
-            if (db->tc)
-                EMD_CUDA(launch_pack_b(db->tcfmt, D_, nqd, nb, max_npad, db->ldm, db->m, db->kpad, st), "query pack");
+    (void)max_rows; (void)max_npad; (void)max_ldd; (void)max_tk; (void)max_kc;
+    if (db->tc && tc_batch_stages(db->tcfmt, db->kpad / 64) < 2) {
+        // embeddings too wide for the batched panel: Phase 1 per query, the rest batched
+        return launch_sequence(db, slot, meas, k, K, dir, pruned, hd, nb, st);
+    }
+    if (!db->opt.graphs || db->profiling) return launch_sequence(db, slot, meas, k, K, dir, pruned, nullptr, 0, st);
+    const GraphKey key{meas, k, K, dir, pruned ? 1 : 0, slot};
+    auto it = db->graphs.find(key);
+    if (it == db->graphs.end()) {
+        GraphEntry g;
+        emd_status cs = capture_sequence(db, slot, meas, k, K, dir, pruned, &g);
+        if (cs != EMD_OK) {
+            g_err.clear();
+            g.exec = nullptr;  // capture refused: this key launches directly from now on
         }
-        if (db->tc && tc_batch_stages(db->tcfmt, db->kpad / 64) >= 2) {
-            Phase p(db, 1, 1, st);
-            EMD_CUDA(launch_tc_dist_batch(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
-                                          db->used_ids, db->v_used, D_, nqd, nb, db->kpad, db->err, st),
-                     "distance matrices (tensor cores, batched)");
-        } else if (db->tc) {
-            Phase p(db, 1, nb, st);
-            for (int q = 0; q < nb; ++q) {
-                const QDesc& d = hd[q];
-                EMD_CUDA(launch_tc_dist(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
-                                        db->used_ids, db->v_used, d.q_hi, d.q_lo, d.npad, d.q_scale, d.qnorm, d.qidx,
-                                        d.h, db->kpad, d.D, d.ldd, db->err, st),
-                         "distance matrix (tensor cores)");
-            }
-        } else {
-            Phase p(db, 1, 1, st);
-            EMD_CUDA(launch_dist_fp32_b(D_, nqd, nb, max_ldd, db->emb_used, db->v_used, db->ldm, db->norm_used,
-                                        db->used_ids, db->m, st),
-                     "distance matrix");
-        }
+        it = db->graphs.emplace(key, g).first;
     }
-    if (dir != EMD_DIR_REV) {
-        {
-            Phase p(db, 2, 1, st);
-            EMD_CUDA(launch_table_b(D_, nqd, nb, db->v_used, max_tk, db->approx, max_kc, db->emb_used, db->ldm, st),
-                     "top-k table");
-        }
-        Phase p(db, 3, 1, st);
-        EMD_CUDA(launch_fwd_b(meas, D_, nqd, nb, db->row_ptr, db->col, db->val, n, dir == EMD_DIR_FWD, st),
-                 "forward pass");
-    }
-    if (pruned) {
-        {
-            Phase p(db, 5, topk_launch_count(n), st);
-            EMD_CUDA(launch_topk_rows(db->bt_fwd, nb, n, n, K, db->topk_scratch, db->bsel_idx, db->bsel_val, st),
-                     "forward top-K");
-        }
-        EMD_CUDA(cudaMemsetAsync(db->bcand_count, 0, sizeof(int) * nb, st), "candidate counts");
-        Phase p(db, 4, 3, st);
-        EMD_CUDA(launch_prune_b(meas, k, D_, nqd, nb, db->row_ptr, db->col, db->val, n, K, st),
-                 "pruned reverse pass");
-        return EMD_OK;
-    }
-    if (dir != EMD_DIR_FWD) {
-        Phase p(db, 4, 1, st);
-        EMD_CUDA(launch_rev_b(meas, k, dir, D_, nqd, nb, db->row_ptr, db->col, db->val, n, st), "reverse pass");
-    }
-    if (K > 0) {
-        Phase p(db, 5, topk_launch_count(n), st);
-        EMD_CUDA(launch_topk_rows(db->stage_out + (j0 - i0) * n, nb, n, n, K, db->topk_scratch,
-                                  out_idx + (j0 - i0) * K, out_dist + (j0 - i0) * K, st),
-                 "top-K");
-    }
+    if (!it->second.exec) return launch_sequence(db, slot, meas, k, K, dir, pruned, nullptr, 0, st);
+    EMD_CUDA(cudaGraphLaunch(it->second.exec, st), "graph launch");
+    for (int p = 0; p < EMD_N_PHASES; ++p) db->launches[p] += it->second.launches[p];
+    db->total_launches += it->second.total;
+    db->graph_launches += 1;
     return EMD_OK;
 }
 
@@ -632,6 +705,7 @@ void emd_db_options_default(emd_db_options* opt)
     opt->lanes = 1;
     opt->batched = 1;
     opt->batch_columns = 16384;
+    opt->graphs = 1;
 }
 
 emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* cost_matrix,
@@ -724,6 +798,7 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
     TRYC(cudaSetDevice(db->dev), "cudaSetDevice");
     TRYC(cudaStreamCreateWithFlags(&db->stream, cudaStreamNonBlocking), "stream");
     TRYC(cudaEventCreateWithFlags(&db->fork, cudaEventDisableTiming), "event");
+    TRYC(cudaStreamCreateWithFlags(&db->cap_stream, cudaStreamNonBlocking), "stream");
     db->lanes.resize((size_t)opt.lanes);
     for (auto& L : db->lanes) {
         TRYC(cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking), "stream");
@@ -1017,6 +1092,7 @@ emd_status emd_db_profile_get(emd_db* db, emd_profile* out)
     out->total_launches = db->total_launches;
     out->pruned_queries = db->pruned_queries;
     out->prune_fallbacks = db->prune_fallbacks;
+    out->graph_launches = db->graph_launches;
     return EMD_OK;
 }
 
@@ -1027,7 +1103,7 @@ emd_status emd_db_profile_reset(emd_db* db)
     emd_status s = collect_profile(db);
     if (s != EMD_OK) return s;
     for (int p = 0; p < EMD_N_PHASES; ++p) { db->ms[p] = 0.0; db->launches[p] = 0; }
-    db->pruned_queries = db->prune_fallbacks = 0;
+    db->pruned_queries = db->prune_fallbacks = db->graph_launches = 0;
     return EMD_OK;
 }
 

@@ -5,6 +5,7 @@
 #include <cuda_fp16.h>
 
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -45,6 +46,27 @@ struct Lane {
         cudaError_t e_ = (call);                               \
         if (e_ != cudaSuccess) return emd::cuda_fail(e_, what); \
     } while (0)
+
+namespace emd {
+// One captured batch sequence (launch_sequence) and the kernel launches it holds.
+struct GraphKey {
+    int meas, k, K, dir, pruned, slot;
+    bool operator<(const GraphKey& o) const
+    {
+        if (meas != o.meas) return meas < o.meas;
+        if (k != o.k) return k < o.k;
+        if (K != o.K) return K < o.K;
+        if (dir != o.dir) return dir < o.dir;
+        if (pruned != o.pruned) return pruned < o.pruned;
+        return slot < o.slot;
+    }
+};
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches[EMD_N_PHASES] = {};
+    int64_t total = 0;
+};
+}  // namespace emd
 
 struct emd_db {
     int dev = 0;
@@ -128,6 +150,9 @@ struct emd_db {
     int* nq_host = nullptr;
     cudaEvent_t desc_ev[kDescRing] = {};
     int desc_slot = 0;
+    cudaStream_t cap_stream = nullptr;              // graph capture
+    std::map<emd::GraphKey, emd::GraphEntry> graphs;
+    int64_t graph_launches = 0;
 
     // Serialises the entry points that launch work or touch the counters above (host
     // threads, and the server's worker thread).

@@ -198,6 +198,11 @@ cudaError_t launch_fwd_b(int meas, const QDesc* qd, const int* nq, int max_q, co
 // t_rev and max(t_fwd, t_rev) into t_out.
 cudaError_t launch_rev_b(int meas, int k, int dir, const QDesc* qd, const int* nq, int max_q,
                          const int32_t* row_ptr, const int32_t* col, const float* val, int64_t n, cudaStream_t st);
+// Top-K of each query of a batch: from t_fwd into sel_idx / sel_val (fwd_rows: the
+// forward top-K of the pruned path) or from t_out into out_idx / out_dist.  scratch holds
+// max_q * kTopkScratchRow keys.
+cudaError_t launch_topk_b(const QDesc* qd, const int* nq, int max_q, int64_t n, int K,
+                          unsigned long long* scratch, bool fwd_rows, cudaStream_t st);
 // Pruned top-K after the forward top-K (sel_idx / sel_val): candidate compaction (counts
 // must be zeroed), reverse pass on the candidates, final selection and certificate.
 cudaError_t launch_prune_b(int meas, int k, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,

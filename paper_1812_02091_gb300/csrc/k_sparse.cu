@@ -450,13 +450,10 @@ __device__ void block_merge_and_emit(unsigned long long (&L)[KT], int K, unsigne
 }
 
 template <int KT>
-__global__ void __launch_bounds__(kTopkThreads)
-k_topk_values(const float* __restrict__ t, int64_t n, int64_t ldt, int K, int64_t per_block,
-              unsigned long long* __restrict__ scratch, int64_t* __restrict__ out_idx,
-              float* __restrict__ out_dist)
+__device__ __forceinline__ void topk_values_body(const float* __restrict__ t, int64_t n, int K, int64_t per_block,
+                                                 unsigned long long* __restrict__ scratch_row,
+                                                 int64_t* __restrict__ out_idx, float* __restrict__ out_dist)
 {
-    const int64_t row = blockIdx.y;
-    t += row * ldt;
     unsigned long long L[KT];
 #pragma unroll
     for (int l = 0; l < KT; ++l) L[l] = ~0ull;
@@ -468,10 +465,31 @@ k_topk_values(const float* __restrict__ t, int64_t n, int64_t ldt, int K, int64_
         list_insert<KT>(L, key);
     }
     if (gridDim.x == 1)
-        block_merge_and_emit<KT>(L, K, nullptr, out_idx + row * K, out_dist + row * K);
+        block_merge_and_emit<KT>(L, K, nullptr, out_idx, out_dist);
     else
-        block_merge_and_emit<KT>(L, KT, scratch + row * kTopkScratchRow + (int64_t)blockIdx.x * KT,
-                                 nullptr, nullptr);
+        block_merge_and_emit<KT>(L, KT, scratch_row + (int64_t)blockIdx.x * KT, nullptr, nullptr);
+}
+
+template <int KT>
+__device__ __forceinline__ void topk_keys_body(const unsigned long long* __restrict__ keys, int64_t count, int K,
+                                               int64_t* __restrict__ out_idx, float* __restrict__ out_dist)
+{
+    unsigned long long L[KT];
+#pragma unroll
+    for (int l = 0; l < KT; ++l) L[l] = ~0ull;
+    for (int64_t i = threadIdx.x; i < count; i += blockDim.x) list_insert<KT>(L, keys[i]);
+    block_merge_and_emit<KT>(L, K, nullptr, out_idx, out_dist);
+}
+
+template <int KT>
+__global__ void __launch_bounds__(kTopkThreads)
+k_topk_values(const float* __restrict__ t, int64_t n, int64_t ldt, int K, int64_t per_block,
+              unsigned long long* __restrict__ scratch, int64_t* __restrict__ out_idx,
+              float* __restrict__ out_dist)
+{
+    const int64_t row = blockIdx.y;
+    topk_values_body<KT>(t + row * ldt, n, K, per_block, scratch + row * kTopkScratchRow, out_idx + row * K,
+                         out_dist + row * K);
 }
 
 template <int KT>
@@ -480,12 +498,51 @@ k_topk_keys(const unsigned long long* __restrict__ keys, int64_t count, int K,
             int64_t* __restrict__ out_idx, float* __restrict__ out_dist)
 {
     const int64_t row = blockIdx.x;
-    keys += row * kTopkScratchRow;
-    unsigned long long L[KT];
-#pragma unroll
-    for (int l = 0; l < KT; ++l) L[l] = ~0ull;
-    for (int64_t i = threadIdx.x; i < count; i += blockDim.x) list_insert<KT>(L, keys[i]);
-    block_merge_and_emit<KT>(L, K, nullptr, out_idx + row * K, out_dist + row * K);
+    topk_keys_body<KT>(keys + row * kTopkScratchRow, count, K, out_idx + row * K, out_dist + row * K);
+}
+
+// Batched forms: row q of the batch reads qd[q].t_fwd and writes sel_idx / sel_val (the
+// forward top-K of the pruned path, fwd_rows) or reads t_out and writes out_idx / out_dist.
+template <int KT>
+__global__ void __launch_bounds__(kTopkThreads)
+k_topk_values_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t n, int K, int64_t per_block,
+                unsigned long long* __restrict__ scratch, bool fwd_rows)
+{
+    if ((int)blockIdx.y >= *nq) return;
+    const QDesc& d = qd[blockIdx.y];
+    topk_values_body<KT>(fwd_rows ? d.t_fwd : d.t_out, n, K, per_block,
+                         scratch + (int64_t)blockIdx.y * kTopkScratchRow, fwd_rows ? d.sel_idx : d.out_idx,
+                         fwd_rows ? d.sel_val : d.out_dist);
+}
+
+template <int KT>
+__global__ void __launch_bounds__(kTopkThreads)
+k_topk_keys_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t count, int K,
+              const unsigned long long* __restrict__ scratch, bool fwd_rows)
+{
+    if ((int)blockIdx.x >= *nq) return;
+    const QDesc& d = qd[blockIdx.x];
+    topk_keys_body<KT>(scratch + (int64_t)blockIdx.x * kTopkScratchRow, count, K, fwd_rows ? d.sel_idx : d.out_idx,
+                       fwd_rows ? d.sel_val : d.out_dist);
+}
+
+template <int KT>
+cudaError_t topk_kt_b(const QDesc* qd, const int* nq, int max_q, int64_t n, int K, unsigned long long* scratch,
+                      bool fwd_rows, cudaStream_t st)
+{
+    const size_t smem = (size_t)kTopkThreads * KT * sizeof(unsigned long long);
+    const int blocks = topk_blocks(n);
+    const int64_t per_block = (n + blocks - 1) / blocks;
+    if (smem > 48 * 1024) {
+        cudaFuncSetAttribute(k_topk_values_b<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_topk_keys_b<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    k_topk_values_b<KT><<<dim3(blocks, (unsigned)max_q), kTopkThreads, smem, st>>>(qd, nq, n, K, per_block, scratch,
+                                                                                    fwd_rows);
+    if (blocks > 1)
+        k_topk_keys_b<KT><<<(unsigned)max_q, kTopkThreads, smem, st>>>(qd, nq, (int64_t)blocks * KT, K, scratch,
+                                                                        fwd_rows);
+    return cudaGetLastError();
 }
 
 template <int KT>
@@ -814,6 +871,15 @@ cudaError_t launch_prune_b(int meas, int k, const QDesc* qd, const int* nq, int 
     if (e != cudaSuccess) return e;
     k_prune_select_b<<<(unsigned)max_q, kPruneCap, 0, st>>>(qd, nq, K);
     return cudaGetLastError();
+}
+
+cudaError_t launch_topk_b(const QDesc* qd, const int* nq, int max_q, int64_t n, int K,
+                          unsigned long long* scratch, bool fwd_rows, cudaStream_t st)
+{
+    if (max_q <= 0) return cudaSuccess;
+    if (K <= 16) return topk_kt_b<16>(qd, nq, max_q, n, K, scratch, fwd_rows, st);
+    if (K <= 32) return topk_kt_b<32>(qd, nq, max_q, n, K, scratch, fwd_rows, st);
+    return topk_kt_b<64>(qd, nq, max_q, n, K, scratch, fwd_rows, st);
 }
 
 cudaError_t launch_topk_rows(const float* t, int64_t rows, int64_t n, int64_t ldt, int K,

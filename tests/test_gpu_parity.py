@@ -423,6 +423,8 @@ def test_batched_equals_per_query(emd, precision):
     rp, qi, qw = w.queries.row_ptr, w.queries.col, w.queries.val
     db_q = make_db(emd, w, precision=precision, max_query_h=160, max_table_k=160, batched=0)
     db_b = make_db(emd, w, precision=precision, max_query_h=160, max_table_k=160, batch_columns=512, max_batch=8)
+    db_c = make_db(emd, w, precision=precision, max_query_h=160, max_table_k=160, batch_columns=512, max_batch=8,
+                   graphs=0)
     try:
         cases = [("rwmd", 1), ("omr", 1), ("act", 2), ("act", 4), ("act", 8)]
         if precision != "bf16":
@@ -431,12 +433,17 @@ def test_batched_equals_per_query(emd, precision):
             dirs = ("fwd", "rev", "max") if not (meas == "ict" and precision == "bf16") else ("rev",)
             for d in dirs:
                 a = emd.emd_query_batch(db_q, rp, qi, qw, meas, k, d)
-                b = emd.emd_query_batch(db_b, rp, qi, qw, meas, k, d)
-                assert np.array_equal(a, b), (meas, k, d)
+                for dbx in (db_b, db_c, db_b):  # graph captured, direct launches, graph replayed
+                    b = emd.emd_query_batch(dbx, rp, qi, qw, meas, k, d)
+                    assert np.array_equal(a, b), (meas, k, d)
             for K in (10, 32):
                 ai, ad = emd.emd_topk(db_q, rp, qi, qw, meas, k, "max", K)
-                bi, bd = emd.emd_topk(db_b, rp, qi, qw, meas, k, "max", K)
-                assert np.array_equal(ai, bi) and np.array_equal(ad, bd), (meas, k, K)
+                for dbx in (db_b, db_c, db_b):
+                    bi, bd = emd.emd_topk(dbx, rp, qi, qw, meas, k, "max", K)
+                    assert np.array_equal(ai, bi) and np.array_equal(ad, bd), (meas, k, K)
+        assert emd.emd_db_profile_get(db_b)["graph_launches"] > 0
+        assert emd.emd_db_profile_get(db_c)["graph_launches"] == 0
     finally:
         emd.emd_db_destroy(db_q)
         emd.emd_db_destroy(db_b)
+        emd.emd_db_destroy(db_c)
