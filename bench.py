@@ -556,7 +556,8 @@ def main():
                                      "fp32_tc": "FP32-grade on tcgen05: FP16 hi+lo split, 3 products, FP32 TMEM accumulators"}[args.precision],
                        "parallelism": f"replicas x{world}, queries sharded",
                        "l2": "flushed between steps (256 MB write outside the timed events)",
-                       "v_used": vu, "nnz": nnz, "mean_h_q_timed": sum_h / nq},
+                       "v_used": vu, "nnz": nnz, "mean_h_q_timed": sum_h / nq,
+                       "autotuned": {kk: info[kk] for kk in ("autotuned", "tc_group_mult", "tc_stages", "rev_warps")}},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

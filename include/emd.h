@@ -94,6 +94,9 @@ typedef struct {
     int32_t graphs;          /* batched form: 1 (default) replays each (measure, k, K, direction)
                                 sequence from a captured CUDA graph; 0: launches directly.
                                 Profiling (emd_db_set_profiling) launches directly */
+    int32_t autotune;        /* batched form: 1 (default) times the free parameters of the batched
+                                kernels on a synthetic batch at creation and keeps the fastest
+                                (results do not depend on them); 0: fixed defaults */
 } emd_db_options;
 
 typedef struct {
@@ -101,6 +104,11 @@ typedef struct {
     int32_t m;                      /* embedding width (0 in cost-matrix mode) */
     int32_t cost_matrix_mode;       /* 1 when a v x v ground-cost matrix replaced embeddings */
     int64_t device_bytes;           /* device memory held by the handle */
+    int32_t autotuned;              /* 1 when the parameters below were timed at creation */
+    int32_t tc_group_mult;          /* batched tensor-core Phase 1: query groups per vocabulary tile
+                                       (multiple of the load-balance minimum) */
+    int32_t tc_stages;              /* its query-chunk stages (0: as many as fit) */
+    int32_t rev_warps;              /* pruned reverse pass: warps per candidate document */
 } emd_db_info;
 
 /* A batch of query histograms in CSR form: query i has bins

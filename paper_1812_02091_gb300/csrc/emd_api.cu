@@ -352,7 +352,8 @@ emd_status launch_sequence(emd_db* db, int slot, int meas, int k, int K, int dir
         if (db->tc && !hd) {
             Phase p(db, 1, 1, st);
             EMD_CUDA(launch_tc_dist_batch(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
-                                          db->used_ids, db->v_used, D_, nqd, B, db->kpad, db->err, st),
+                                          db->used_ids, db->v_used, D_, nqd, B, db->kpad, db->tune_group_mult,
+                                          db->tune_stages, db->err, st),
                      "distance matrices (tensor cores, batched)");
         } else if (db->tc) {
             Phase p(db, 1, nb, st);
@@ -387,7 +388,7 @@ emd_status launch_sequence(emd_db* db, int slot, int meas, int k, int K, int dir
         }
         EMD_CUDA(cudaMemsetAsync(db->bcand_count, 0, sizeof(int) * B, st), "candidate counts");
         Phase p(db, 4, 3, st);
-        EMD_CUDA(launch_prune_b(meas, k, D_, nqd, B, db->row_ptr, db->col, db->val, n, K, st),
+        EMD_CUDA(launch_prune_b(meas, k, D_, nqd, B, db->row_ptr, db->col, db->val, n, K, db->tune_rev_warps, st),
                  "pruned reverse pass");
         return EMD_OK;
     }
@@ -434,9 +435,9 @@ emd_status capture_sequence(emd_db* db, int slot, int meas, int k, int K, int di
     return EMD_OK;
 }
 
-// Queries j0..j1-1 of the batch i0.. as one launch per step (the batch fits the batch
-// workspace).  Outputs as run_batch.  Uses descriptor ring slot `slot`.
-emd_status run_subbatch_launch(int slot, emd_db* db, const int64_t* rp, const int32_t* qidx, const float* qw, int64_t i0,
+// Fills ring slot `slot` with the descriptors of queries j0..j1-1 of the batch i0.. (the
+// batch fits the batch workspace) and uploads them on st.  Outputs as run_batch.
+emd_status fill_descriptors(int slot, emd_db* db, const int64_t* rp, const int32_t* qidx, const float* qw, int64_t i0,
                         int64_t j0, int64_t j1, int meas, int k, int dir, int K, bool pruned, float* out_t,
                         int64_t* out_idx, float* out_dist, cudaStream_t st)
 {
@@ -500,6 +501,14 @@ emd_status run_subbatch_launch(int slot, emd_db* db, const int64_t* rp, const in
     EMD_CUDA(cudaMemcpyAsync(dd, hd, sizeof(QDesc) * nb, cudaMemcpyHostToDevice, st), "descriptor upload");
     EMD_CUDA(cudaMemcpyAsync(nqd, db->nq_host + slot, sizeof(int), cudaMemcpyHostToDevice, st), "descriptor upload");
     (void)max_rows; (void)max_npad; (void)max_ldd; (void)max_tk; (void)max_kc;
+    return EMD_OK;
+}
+
+// Runs the sub-batch whose descriptors fill_descriptors put in `slot` (nb queries).
+emd_status run_subbatch_launch(int slot, emd_db* db, int nb, int meas, int k, int dir, int K, bool pruned,
+                               cudaStream_t st)
+{
+    const QDesc* hd = db->qd_host + (int64_t)slot * db->opt.max_batch;
     if (db->tc && tc_batch_stages(db->tcfmt, db->kpad / 64) < 2) {
         // embeddings too wide for the batched panel: Phase 1 per query, the rest batched
         return launch_sequence(db, slot, meas, k, K, dir, pruned, hd, nb, st);
@@ -533,8 +542,9 @@ emd_status run_subbatch(emd_db* db, const int64_t* rp, const int32_t* qidx, cons
     const int slot = db->desc_slot;
     db->desc_slot = (slot + 1) % emd_db::kDescRing;
     EMD_CUDA(cudaEventSynchronize(db->desc_ev[slot]), "descriptor ring");
-    emd_status s = run_subbatch_launch(slot, db, rp, qidx, qw, i0, j0, j1, meas, k, dir, K, pruned, out_t, out_idx,
-                                       out_dist, st);
+    emd_status s = fill_descriptors(slot, db, rp, qidx, qw, i0, j0, j1, meas, k, dir, K, pruned, out_t, out_idx,
+                                    out_dist, st);
+    if (s == EMD_OK) s = run_subbatch_launch(slot, db, (int)(j1 - j0), meas, k, dir, K, pruned, st);
     EMD_CUDA(cudaEventRecord(db->desc_ev[slot], st), "descriptor ring");
     return s;
 }
@@ -688,6 +698,97 @@ emd_status host_batches(emd_db* db, const emd_queries* q, int meas, int k, int d
     return read_device_errors(db);
 }
 
+// Picks the batched kernels' free parameters (query groups per vocabulary tile and B
+// stages of the tensor-core Phase 1, warps per candidate in the pruned reverse pass) by
+// timing them on a synthetic batch: queries of up to 128 consecutive used vocabulary rows,
+// uniform weights.  Every choice gives bit-identical results; only the time differs.
+emd_status autotune(emd_db* db, const std::vector<int32_t>& used_host)
+{
+    const int nb = std::min(db->opt.max_batch, 32);
+    const int h = (int)std::min<int64_t>(std::min<int64_t>(128, db->opt.max_query_h), db->v_used);
+    const int k = std::min(4, db->opt.max_table_k);
+    const int K = (int)std::min<int64_t>(16, db->n);
+    std::vector<int64_t> rp((size_t)nb + 1);
+    std::vector<int32_t> idx((size_t)nb * h);
+    std::vector<float> w((size_t)nb * h, 1.0f / (float)h);
+    for (int i = 0; i <= nb; ++i) rp[(size_t)i] = (int64_t)i * h;
+    for (int i = 0; i < nb; ++i) {
+        const int64_t start = (int64_t)i * (db->v_used / nb);
+        for (int j = 0; j < h; ++j) idx[(size_t)i * h + j] = used_host[(size_t)((start + j) % db->v_used)];
+    }
+    cudaStream_t st = db->stream;
+    EMD_CUDA(cudaMemcpyAsync(db->stage_idx, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice, st), "tune copy");
+    EMD_CUDA(cudaMemcpyAsync(db->stage_w, w.data(), w.size() * 4, cudaMemcpyHostToDevice, st), "tune copy");
+    const bool pruned = prunable(db, EMD_ACT, k, EMD_DIR_MAX, K);
+    emd_status s = fill_descriptors(0, db, rp.data(), db->stage_idx, db->stage_w, 0, 0, nb, EMD_ACT, k, EMD_DIR_MAX, K,
+                                    pruned, nullptr, db->stage_oidx, db->stage_odist, st);
+    if (s != EMD_OK) return s;
+    const bool per_query_tc = db->tc && tc_batch_stages(db->tcfmt, db->kpad / 64) < 2;
+    s = launch_sequence(db, 0, EMD_ACT, k, K, EMD_DIR_MAX, pruned, per_query_tc ? db->qd_host : nullptr, nb, st);
+    if (s != EMD_OK) return s;
+    EMD_CUDA(cudaStreamSynchronize(st), "synchronize");
+    cudaEvent_t a = nullptr, b = nullptr;
+    EMD_CUDA(cudaEventCreate(&a), "event");
+    EMD_CUDA(cudaEventCreate(&b), "event");
+    auto timed = [&](auto&& launch) -> float {
+        float best = 1e30f;
+        for (int r = 0; r < 8; ++r) {
+            cudaEventRecord(a, st);
+            launch();
+            cudaEventRecord(b, st);
+            cudaEventSynchronize(b);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (r > 0) best = std::min(best, ms);
+        }
+        return best;
+    };
+    const QDesc* D_ = db->qd_dev;
+    const int* nqd = db->nq_dev;
+    if (db->tc && tc_batch_stages(db->tcfmt, db->kpad / 64) >= 2) {
+        // a candidate replaces the current choice only when at least 5% faster (timing noise
+        // on short launches would otherwise pick at random)
+        const int fit = tc_batch_stages(db->tcfmt, db->kpad / 64);
+        float best = 1e30f;
+        for (int gm : {1, 2, 4})
+            for (int sg : {fit, (fit + 2) / 2, 2}) {
+                if (sg < 2 || sg > fit) continue;
+                const float ms = timed([&] {
+                    launch_tc_dist_batch(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
+                                         db->used_ids, db->v_used, D_, nqd, db->opt.max_batch, db->kpad, gm, sg,
+                                         db->err, st);
+                });
+                if (ms < 0.95f * best) {
+                    best = ms;
+                    db->tune_group_mult = gm;
+                    db->tune_stages = sg;
+                }
+            }
+    }
+    if (pruned) {
+        float best = 1e30f;
+        for (int wp : {4, 2, 8}) {  // the default first
+            const float ms = timed([&] {
+                cudaMemsetAsync(db->bcand_count, 0, sizeof(int) * db->opt.max_batch, st);
+                launch_prune_b(EMD_ACT, k, D_, nqd, db->opt.max_batch, db->row_ptr, db->col, db->val, db->n, K, wp,
+                               st);
+            });
+            if (ms < 0.95f * best) {
+                best = ms;
+                db->tune_rev_warps = wp;
+            }
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    EMD_CUDA(cudaStreamSynchronize(st), "synchronize");
+    EMD_CUDA(cudaGetLastError(), "autotune");
+    db->autotuned = true;
+    for (int p = 0; p < EMD_N_PHASES; ++p) db->launches[p] = 0;
+    db->total_launches = 0;
+    return EMD_OK;
+}
+
 }  // namespace emd
 
 extern "C" {
@@ -706,6 +807,7 @@ void emd_db_options_default(emd_db_options* opt)
     opt->batched = 1;
     opt->batch_columns = 16384;
     opt->graphs = 1;
+    opt->autotune = 1;
 }
 
 emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* cost_matrix,
@@ -919,6 +1021,7 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
     TRY(dalloc(db, &db->stage_oidx, (int64_t)opt.max_batch * kMaxTopK));
     TRY(dalloc(db, &db->stage_odist, (int64_t)opt.max_batch * kMaxTopK));
     TRYC(cudaStreamSynchronize(st), "synchronize");
+    if (opt.batched && opt.autotune) TRY(autotune(db, used_ids));
 #undef TRY
 #undef TRYC
     *out = db;
@@ -943,6 +1046,10 @@ emd_status emd_db_info_get(const emd_db* db, emd_db_info* out)
     out->m = db->m;
     out->cost_matrix_mode = db->cost_mode ? 1 : 0;
     out->device_bytes = db->bytes;
+    out->autotuned = db->autotuned ? 1 : 0;
+    out->tc_group_mult = db->tune_group_mult;
+    out->tc_stages = db->tune_stages;
+    out->rev_warps = db->tune_rev_warps;
     return EMD_OK;
 }
 

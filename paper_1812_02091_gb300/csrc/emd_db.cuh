@@ -151,6 +151,11 @@ struct emd_db {
     cudaEvent_t desc_ev[kDescRing] = {};
     int desc_slot = 0;
     cudaStream_t cap_stream = nullptr;              // graph capture
+    // free parameters of the batched kernels (autotune at creation)
+    bool autotuned = false;
+    int tune_group_mult = 1;   // query groups per vocabulary tile, times the balance minimum
+    int tune_stages = 0;       // B stages of the batched tensor-core kernel (0: as many as fit)
+    int tune_rev_warps = 4;    // warps per candidate document in the pruned reverse pass
     std::map<emd::GraphKey, emd::GraphEntry> graphs;
     int64_t graph_launches = 0;
 

@@ -184,9 +184,12 @@ cudaError_t launch_dist_gather_b(const QDesc* qd, const int* nq, int max_q, cons
 // count is *nq).  cudaErrorInvalidValue when the panel does not fit in shared memory
 // (tc_batch_stages == 0): use launch_tc_dist per query instead.
 int tc_batch_stages(int fmt, int KC);
+// group_mult scales the number of query groups per row tile (load balance against
+// vocabulary re-reads); stages caps the B ring (0: as many as fit).  Same results for any
+// choice.
 cudaError_t launch_tc_dist_batch(int fmt, const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
                                  const float* a_norm, const int32_t* a_ids, int64_t M, const QDesc* qd, const int* nq,
-                                 int max_q, int Kpad, int* err, cudaStream_t st);
+                                 int max_q, int Kpad, int group_mult, int stages, int* err, cudaStream_t st);
 // max_tk: the largest table width of the batch; rerank: the approximate precisions' form
 // (V: the used vocabulary rows, ldv floats each).
 cudaError_t launch_table_b(const QDesc* qd, const int* nq, int max_q, int64_t M, int max_tk, bool rerank,
@@ -205,8 +208,9 @@ cudaError_t launch_topk_b(const QDesc* qd, const int* nq, int max_q, int64_t n, 
                           unsigned long long* scratch, bool fwd_rows, cudaStream_t st);
 // Pruned top-K after the forward top-K (sel_idx / sel_val): candidate compaction (counts
 // must be zeroed), reverse pass on the candidates, final selection and certificate.
+// rev_warps: warps per candidate document in the reverse pass (2, 4 or 8; same results).
 cudaError_t launch_prune_b(int meas, int k, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
-                           const int32_t* col, const float* val, int64_t n, int K, cudaStream_t st);
+                           const int32_t* col, const float* val, int64_t n, int K, int rev_warps, cudaStream_t st);
 
 // Failure message for emd_last_error() (defined beside the C ABI).
 emd_status set_error(emd_status st, const char* msg);

@@ -736,11 +736,10 @@ cudaError_t rev_meas_b(int k, int dir, const QDesc* qd, const int* nq, int max_q
     return cudaGetLastError();
 }
 
-template <int MEAS>
-cudaError_t rev_meas_blk_b(int k, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
-                           const int32_t* col, const float* val, cudaStream_t st)
+template <int MEAS, int W>
+cudaError_t rev_meas_blk_bw(int k, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
+                            const int32_t* col, const float* val, cudaStream_t st)
 {
-    constexpr int W = 4;
     const int kt = MEAS == M_RWMD ? 1 : (MEAS == M_OMR ? 2 : k);
     const dim3 grid(kPruneCap, (unsigned)max_q);
 #define EMD_REVBQ(KT, NJ) k_rev_blk_b<MEAS, KT, NJ, W><<<grid, W * 32, 0, st>>>(qd, nq, row_ptr, col, val, k)
@@ -751,6 +750,17 @@ cudaError_t rev_meas_blk_b(int k, const QDesc* qd, const int* nq, int max_q, con
     else EMD_REVBQ(16, 1);
 #undef EMD_REVBQ
     return cudaGetLastError();
+}
+
+// Warps per candidate document: 2, 4 or 8 (the merge in chunk order makes the result
+// independent of the choice).
+template <int MEAS>
+cudaError_t rev_meas_blk_b(int k, int warps, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
+                           const int32_t* col, const float* val, cudaStream_t st)
+{
+    if (warps <= 2) return rev_meas_blk_bw<MEAS, 2>(k, qd, nq, max_q, row_ptr, col, val, st);
+    if (warps <= 4) return rev_meas_blk_bw<MEAS, 4>(k, qd, nq, max_q, row_ptr, col, val, st);
+    return rev_meas_blk_bw<MEAS, 8>(k, qd, nq, max_q, row_ptr, col, val, st);
 }
 
 template <int MEAS>
@@ -857,16 +867,16 @@ cudaError_t launch_rev_b(int meas, int k, int dir, const QDesc* qd, const int* n
 }
 
 cudaError_t launch_prune_b(int meas, int k, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
-                           const int32_t* col, const float* val, int64_t n, int K, cudaStream_t st)
+                           const int32_t* col, const float* val, int64_t n, int K, int rev_warps, cudaStream_t st)
 {
     if (max_q <= 0) return cudaSuccess;
     const int blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256), 152 * 4);
     k_prune_compact_b<<<dim3((unsigned)blocks, (unsigned)max_q), 256, 0, st>>>(qd, nq, n, K);
     cudaError_t e;
     switch (meas) {
-    case M_RWMD: e = rev_meas_blk_b<M_RWMD>(k, qd, nq, max_q, row_ptr, col, val, st); break;
-    case M_OMR: e = rev_meas_blk_b<M_OMR>(k, qd, nq, max_q, row_ptr, col, val, st); break;
-    default: e = rev_meas_blk_b<M_ACT>(k, qd, nq, max_q, row_ptr, col, val, st); break;
+    case M_RWMD: e = rev_meas_blk_b<M_RWMD>(k, rev_warps, qd, nq, max_q, row_ptr, col, val, st); break;
+    case M_OMR: e = rev_meas_blk_b<M_OMR>(k, rev_warps, qd, nq, max_q, row_ptr, col, val, st); break;
+    default: e = rev_meas_blk_b<M_ACT>(k, rev_warps, qd, nq, max_q, row_ptr, col, val, st); break;
     }
     if (e != cudaSuccess) return e;
     k_prune_select_b<<<(unsigned)max_q, kPruneCap, 0, st>>>(qd, nq, K);

@@ -867,16 +867,18 @@ static cudaError_t tc_batch_launch(dim3 grid, size_t smem, cudaStream_t st, cons
 
 cudaError_t launch_tc_dist_batch(int fmt, const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
                                  const float* a_norm, const int32_t* a_ids, int64_t M, const QDesc* qd, const int* nq,
-                                 int max_q, int Kpad, int* err, cudaStream_t st)
+                                 int max_q, int Kpad, int group_mult, int stages_req, int* err, cudaStream_t st)
 {
     if (M <= 0 || max_q <= 0) return cudaSuccess;
     const int KC = Kpad / 64;
-    const int stages = tc_batch_stages(fmt, KC);
-    if (stages < 2) return cudaErrorInvalidValue;
+    const int fit = tc_batch_stages(fmt, KC);
+    if (fit < 2) return cudaErrorInvalidValue;
+    const int stages = stages_req >= 2 ? std::min(stages_req, fit) : fit;
     const size_t smem = tc_batch_smem_bytes(fmt, stages, KC);
     const int m_tiles = (int)(Mpad / TC_BM);
     const int sms = sm_count();
-    const int groups = std::max(1, std::min(max_q, (2 * sms + m_tiles - 1) / m_tiles));
+    const int groups =
+        std::max(1, std::min(max_q, std::max(1, group_mult) * ((2 * sms + m_tiles - 1) / m_tiles)));
     dim3 grid((unsigned)std::min<int64_t>((int64_t)m_tiles * groups, sms));
     switch (fmt) {
     case TC_SPLIT:

@@ -417,14 +417,18 @@ def test_pruned_topk_equals_unpruned_small_queries(emd, meas, k):
 @pytest.mark.parametrize("precision", ["fp32", "fp32_tc", "bf16"])
 def test_batched_equals_per_query(emd, precision):
     """One launch per step over a batch (batched=1) against the per-query kernels
-    (batched=0): the same device bodies, so every distance and top-K is bit-identical.
-    A small batch_columns forces several sub-batches per call."""
+    (batched=0): the same device bodies, so every distance and top-K is bit-identical,
+    with the autotuned parameters and graph replay (db_b) as with fixed defaults and
+    direct launches (db_c).  A small batch_columns forces several sub-batches per call."""
     w = emd_synth.small_text(99, 2500, 48, 900, 23, 4, 50, 1, 150)
     rp, qi, qw = w.queries.row_ptr, w.queries.col, w.queries.val
     db_q = make_db(emd, w, precision=precision, max_query_h=160, max_table_k=160, batched=0)
     db_b = make_db(emd, w, precision=precision, max_query_h=160, max_table_k=160, batch_columns=512, max_batch=8)
     db_c = make_db(emd, w, precision=precision, max_query_h=160, max_table_k=160, batch_columns=512, max_batch=8,
-                   graphs=0)
+                   graphs=0, autotune=0)
+    info_b, info_c = emd.emd_db_info_get(db_b), emd.emd_db_info_get(db_c)
+    assert info_b["autotuned"] == 1 and info_c["autotuned"] == 0
+    assert info_b["rev_warps"] in (2, 4, 8) and info_b["tc_group_mult"] in (1, 2, 4)
     try:
         cases = [("rwmd", 1), ("omr", 1), ("act", 2), ("act", 4), ("act", 8)]
         if precision != "bf16":
