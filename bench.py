@@ -269,13 +269,14 @@ def serving_sweep(emd, w, opts, precision, rates, n_req, k, K, plain_saturation=
     out = {"database": "workload 2 (text V=1e5, n=2e4)",
            "requests": "workload 4 queries: h_q log-uniform 5..2000, cycled in a fixed shuffled order",
            "measure": f"LC-ACT k={k}, max of both directions, top-{K}",
-           "server": "8 slots, workspace pool 8 x max request, admission in arrival order",
+           "server": "continuous batching: two executors, batches formed from the queue head while the "
+                     "executor's distance-matrix columns hold them (16384 columns each), graph-replayed",
            "points": []}
     forms = [(precision, True)] + ([("fp32", False)] if plain_saturation and precision != "fp32" else [])
     for prec, sweep in forms:
         db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
                                emd.emd_db_options_default(precision=prec, **opts))
-        srv = emd.emd_server_create(db, emd.emd_server_options_default(max_inflight=8))
+        srv = emd.emd_server_create(db, emd.emd_server_options_default())
         serve_point(emd, srv, queries, order, None, 256, k, K, 1)  # warm-up
         if sweep:
             for j, r in enumerate(rates):
@@ -305,7 +306,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0, help="default: same as --steps")
     ap.add_argument("--precision", default="fp32_tc", choices=["fp32", "fp32_tc"])
-    ap.add_argument("--serve-rates", default="1000,2000,3000",
+    ap.add_argument("--serve-rates", default="1000,2000,4000",
                     help="offered request rates (requests/s) of the serving sweep; empty: skip it")
     ap.add_argument("--serve-requests", type=int, default=6000, help="requests per serving rate point")
     ap.add_argument("--probe", action="store_true",

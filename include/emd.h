@@ -255,19 +255,20 @@ emd_status emd_db_profile_reset(emd_db* db);
 
 /* ------------------------------------------------------------------ serving
  *
- * A request loop over a resident database: single queries are submitted as they arrive and
- * run, each on its own stream, as soon as a slot and enough device workspace are free, so
- * requests that arrive while others are on the GPU overlap with them (continuous
- * batching).  Every request computes the symmetric top-K of Section 5 (max of both
- * directions, measure `meas`, Alg. 3 width k) with the same kernel sequence as emd_topk, so
- * a result does not depend on which other requests were in flight: it is bit-identical to
- * the same query served alone and to emd_topk with direction EMD_DIR_MAX.
+ * A request loop over a resident database.  Single queries are submitted as they arrive; a
+ * worker thread forms batches from the head of the queue -- requests with the head's
+ * (measure, k, K), in arrival order -- and runs each on one of two executors, each with its
+ * own batch workspace and stream, with the batched kernel sequence of emd_topk (direction
+ * EMD_DIR_MAX, Section 5).  Requests that arrive while a batch is on the GPU join the next
+ * batch as soon as an executor is free (continuous batching).  Every query of a batch is
+ * computed exactly as alone, so a result is bit-identical whether it was served alone or in
+ * any mix, and equals emd_topk's.
  *
- * Admission: a request needs workspace_bytes(h_q) of device memory (its staged bins, the
- * Phase-1 matrix v_used x round_up(h_q, 32) FP32, the k-wide table, three n-float document
- * vectors, pruning buffers and its top-K).  Requests are admitted in arrival order while
- * a slot is free and the workspace pool can hold the head of the queue; a request larger
- * than the whole pool is refused at submit.
+ * Admission: a batch takes requests while its executor's workspace holds them: the sum over
+ * the batch of round_up(h_q, 32) distance-matrix columns (4 x v_used bytes each) may not
+ * exceed the executor's columns (workspace_bytes / 2, or the database's batch_columns), at
+ * most max_batch requests, and at most max_inflight requests on the device in all.  A
+ * request that does not fit an empty executor is refused at submit.
  *
  * Threads: submit, poll and stats may be called from any host threads; one worker thread
  * per server issues the GPU work.  Calls on the database handle made while a server is
@@ -275,33 +276,34 @@ emd_status emd_db_profile_reset(emd_db* db);
 typedef struct emd_server emd_server;
 
 typedef struct {
-    int32_t max_inflight;    /* slots (streams) with requests on the device, default 8 (1..64) */
+    int32_t max_inflight;    /* requests on the device at once, over both executors (default 128) */
     int32_t queue_capacity;  /* submitted but not yet admitted requests; beyond it submit
                                 returns BUSY.  Default 4096 */
-    int64_t workspace_bytes; /* device workspace pool; 0 (default) = max_inflight requests of
-                                the database's max_query_h, capped at half the free memory */
+    int64_t workspace_bytes; /* device memory for the two executors' distance matrices; 0
+                                (default): each gets the database's batch_columns.  Must hold at
+                                least one request of max_query_h per executor */
     int32_t max_query_h;     /* largest accepted h_q; 0 (default) = the database's */
 } emd_server_options;
 
 typedef struct {
     int64_t submitted, completed, rejected_busy, failed, prune_fallbacks;
     int64_t queued, in_flight, max_in_flight;
-    int64_t pool_bytes, pool_used_max;
+    int64_t pool_bytes, pool_used_max;  /* executors' distance-matrix bytes; the most one batch used */
     double qps;              /* completed / (last completion - first submit), since reset */
     double latency_p50_us, latency_p99_us, latency_mean_us, latency_max_us; /* submit -> done */
 } emd_server_stats;
 
 void emd_server_options_default(emd_server_options* opt);
 
-/* Attach a server to db (the handle must outlive it).  K is limited to 64 per request.
- * INVALID_ARG on bad options, OUT_OF_MEMORY if the pool or the pinned staging cannot be
- * allocated, CUDA. */
+/* Attach a server to db (the handle must outlive it).  K is limited to 64 per request.  INVALID_ARG on bad options,
+ * OUT_OF_MEMORY if the executors' workspaces or pinned staging cannot be allocated, CUDA. */
 emd_status emd_server_create(emd_db* db, const emd_server_options* opt, emd_server** out);
 
 /* Queue one query (h_q bins: vocabulary ids idx, weights w summing to 1, host memory, copied
  * during the call) for the symmetric top-K with measure meas and width k.  *ticket
  * identifies the result.  INVALID_ARG for the argument checks of emd_topk or a request
- * larger than the pool, BUSY when the queue is full, SHUTDOWN after destroy began. */
+ * larger than an executor's workspace, BUSY when the queue is full, SHUTDOWN after destroy
+ * began. */
 emd_status emd_server_submit(emd_server* s, const int32_t* idx, const float* w, int32_t h_q,
                              emd_measure meas, int32_t k, int32_t K, uint64_t* ticket);
 

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -73,19 +74,13 @@ void release(emd_db* db)
     cudaSetDevice(db->dev);
     cudaDeviceSynchronize();
     for (void* p : db->allocs) cudaFree(p);
-    if (db->qd_host) cudaFreeHost(db->qd_host);
-    if (db->nq_host) cudaFreeHost(db->nq_host);
-    for (auto e : db->desc_ev)
-        if (e) cudaEventDestroy(e);
+    free_batch_ws(db->bw);
     for (auto& r : db->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : db->pool) cudaEventDestroy(e);
     for (auto& L : db->lanes) {
         if (L.done) cudaEventDestroy(L.done);
         if (L.st) cudaStreamDestroy(L.st);
     }
-    for (auto& kv : db->graphs)
-        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
-    if (db->cap_stream) cudaStreamDestroy(db->cap_stream);
     if (db->fork) cudaEventDestroy(db->fork);
     if (db->stream) cudaStreamDestroy(db->stream);
     delete db;
@@ -322,16 +317,16 @@ emd_status run_lanes(emd_db* db, const int64_t* rp, const int32_t* qidx, const f
                      float* out_dist, cudaStream_t st);
 
 // The kernels of one sub-batch whose descriptors sit in ring slot `slot`.  Grids are sized
-// from the handle's limits (max_batch queries, max_query_h bins, the table width of k)
-// and every block checks the query count on the device, so the same sequence serves every
-// batch with these parameters and can be captured into a graph.  hd (host descriptors of
+// from bounds (qcap queries, max_query_h bins, the table width of k) and every block checks
+// the query count on the device, so the same sequence serves every batch of at most qcap
+// queries with these parameters and can be captured into a graph.  hd (host descriptors of
 // nb queries) only when Phase 1 must run per query.
-emd_status launch_sequence(emd_db* db, int slot, int meas, int k, int K, int dir, bool pruned, const QDesc* hd,
-                           int nb, cudaStream_t st)
+emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, int K, int dir, bool pruned, const QDesc* hd,
+                           int nb, int qcap, cudaStream_t st)
 {
-    const int B = db->opt.max_batch;
-    const QDesc* D_ = db->qd_dev + (int64_t)slot * B;
-    const int* nqd = db->nq_dev + slot;
+    const int B = qcap;  // grids cover qcap queries (>= the batch's count)
+    const QDesc* D_ = ws.qd_dev + (int64_t)slot * ws.max_batch;
+    const int* nqd = ws.nq_dev + slot;
     const int64_t n = db->n;
     const int H = db->opt.max_query_h;
     const int tk_b = dir != EMD_DIR_REV ? table_width(meas, k, H) : 0;
@@ -384,9 +379,9 @@ emd_status launch_sequence(emd_db* db, int slot, int meas, int k, int K, int dir
     if (pruned) {
         {
             Phase p(db, 5, topk_launch_count(n), st);
-            EMD_CUDA(launch_topk_b(D_, nqd, B, n, K, db->topk_scratch, true, st), "forward top-K");
+            EMD_CUDA(launch_topk_b(D_, nqd, B, n, K, ws.topk_scratch, true, st), "forward top-K");
         }
-        EMD_CUDA(cudaMemsetAsync(db->bcand_count, 0, sizeof(int) * B, st), "candidate counts");
+        EMD_CUDA(cudaMemsetAsync(ws.bcand_count, 0, sizeof(int) * B, st), "candidate counts");
         Phase p(db, 4, 3, st);
         EMD_CUDA(launch_prune_b(meas, k, D_, nqd, B, db->row_ptr, db->col, db->val, n, K, db->tune_rev_warps, st),
                  "pruned reverse pass");
@@ -398,20 +393,21 @@ emd_status launch_sequence(emd_db* db, int slot, int meas, int k, int K, int dir
     }
     if (K > 0) {
         Phase p(db, 5, topk_launch_count(n), st);
-        EMD_CUDA(launch_topk_b(D_, nqd, B, n, K, db->topk_scratch, false, st), "top-K");
+        EMD_CUDA(launch_topk_b(D_, nqd, B, n, K, ws.topk_scratch, false, st), "top-K");
     }
     return EMD_OK;
 }
 
 // Captures launch_sequence for these parameters into an executable graph (on the handle's
 // capture stream); the launch counts of one replay are kept beside it.
-emd_status capture_sequence(emd_db* db, int slot, int meas, int k, int K, int dir, bool pruned, GraphEntry* g)
+emd_status capture_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, int K, int dir, bool pruned, int qcap,
+                            GraphEntry* g)
 {
     int64_t l0[EMD_N_PHASES], t0 = db->total_launches;
     for (int p = 0; p < EMD_N_PHASES; ++p) l0[p] = db->launches[p];
-    cudaStream_t cs = db->cap_stream;
+    cudaStream_t cs = ws.cap_stream;
     EMD_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "graph capture");
-    emd_status s = launch_sequence(db, slot, meas, k, K, dir, pruned, nullptr, 0, cs);
+    emd_status s = launch_sequence(ws, db, slot, meas, k, K, dir, pruned, nullptr, 0, qcap, cs);
     cudaGraph_t graph = nullptr;
     const cudaError_t e = cudaStreamEndCapture(cs, &graph);
     for (int p = 0; p < EMD_N_PHASES; ++p) {
@@ -435,16 +431,90 @@ emd_status capture_sequence(emd_db* db, int slot, int meas, int k, int K, int di
     return EMD_OK;
 }
 
+emd_status alloc_batch_ws(emd_db* db, BatchWS& ws, int max_batch, int64_t cols, std::vector<void*>& allocs,
+                          int64_t* bytes)
+{
+    auto dal = [&](auto** p, int64_t count) -> emd_status {
+        using T = std::remove_reference_t<decltype(**p)>;
+        const size_t nb = (size_t)std::max<int64_t>(count, 1) * sizeof(T);
+        void* q = nullptr;
+        const cudaError_t e = cudaMalloc(&q, nb);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(EMD_ERR_OUT_OF_MEMORY, "cudaMalloc of %zu bytes failed: %s", nb, cudaGetErrorString(e));
+        }
+        allocs.push_back(q);
+        *bytes += (int64_t)nb;
+        *p = static_cast<T*>(q);
+        return EMD_OK;
+    };
+#define TRYW(x)                           \
+    do {                                  \
+        emd_status s_ = (x);              \
+        if (s_ != EMD_OK) return s_;      \
+    } while (0)
+    const int64_t B = max_batch, vu = db->v_used, n = db->n;
+    ws.max_batch = max_batch;
+    ws.b_cols = std::max<int64_t>(round_up(cols, 32), round_up(db->opt.max_query_h, 32));
+    ws.b_qrows = ws.b_cols + 32 * B;
+    ws.b_prows = ws.b_cols + 96 * B;
+    ws.b_tabcols = std::max<int64_t>(db->opt.max_table_k, 16 * B);
+    TRYW(dal(&ws.bD, vu * ws.b_cols));
+    if (!db->cost_mode) {
+        TRYW(dal(&ws.bQ, ws.b_qrows * db->ldm));
+        TRYW(dal(&ws.bqnorm, ws.b_qrows));
+        if (db->tc) {
+            TRYW(dal(&ws.bq_hi, ws.b_prows * db->kpad));
+            if (db->tcfmt == TC_SPLIT) TRYW(dal(&ws.bq_lo, ws.b_prows * db->kpad));
+            TRYW(dal(&ws.bq_scale, ws.b_prows));
+        }
+    }
+    TRYW(dal(&ws.btab, vu * ws.b_tabcols));
+    TRYW(dal(&ws.bt_fwd, B * n));
+    TRYW(dal(&ws.bt_rev, B * n));
+    TRYW(dal(&ws.bt_out, B * n));
+    TRYW(dal(&ws.bsel_idx, B * kPruneMaxK));
+    TRYW(dal(&ws.bsel_val, B * kPruneMaxK));
+    TRYW(dal(&ws.bcand, B * kPruneCap));
+    TRYW(dal(&ws.bcand_sym, B * 2 * kPruneCap));
+    TRYW(dal(&ws.bcand_count, B));
+    TRYW(dal(&ws.cand_ok, B));
+    TRYW(dal(&ws.topk_scratch, B * kTopkScratchRow));
+    TRYW(dal(&ws.qd_dev, BatchWS::kDescRing * B));
+    TRYW(dal(&ws.nq_dev, BatchWS::kDescRing));
+#undef TRYW
+    EMD_CUDA(cudaHostAlloc((void**)&ws.qd_host, sizeof(QDesc) * BatchWS::kDescRing * B, cudaHostAllocDefault),
+             "pinned descriptors");
+    EMD_CUDA(cudaHostAlloc((void**)&ws.nq_host, sizeof(int) * BatchWS::kDescRing, cudaHostAllocDefault),
+             "pinned descriptors");
+    for (auto& e : ws.desc_ev) EMD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    EMD_CUDA(cudaStreamCreateWithFlags(&ws.cap_stream, cudaStreamNonBlocking), "stream");
+    return EMD_OK;
+}
+
+void free_batch_ws(BatchWS& ws)
+{
+    for (auto& kv : ws.graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    ws.graphs.clear();
+    if (ws.cap_stream) cudaStreamDestroy(ws.cap_stream);
+    for (auto& e : ws.desc_ev)
+        if (e) cudaEventDestroy(e);
+    if (ws.qd_host) cudaFreeHost(ws.qd_host);
+    if (ws.nq_host) cudaFreeHost(ws.nq_host);
+    ws = BatchWS();
+}
+
 // Fills ring slot `slot` with the descriptors of queries j0..j1-1 of the batch i0.. (the
 // batch fits the batch workspace) and uploads them on st.  Outputs as run_batch.
-emd_status fill_descriptors(int slot, emd_db* db, const int64_t* rp, const int32_t* qidx, const float* qw, int64_t i0,
+emd_status fill_descriptors(BatchWS& ws, int slot, emd_db* db, const int64_t* rp, const int32_t* qidx, const float* qw, int64_t i0,
                         int64_t j0, int64_t j1, int meas, int k, int dir, int K, bool pruned, float* out_t,
                         int64_t* out_idx, float* out_dist, cudaStream_t st)
 {
     const int nb = (int)(j1 - j0);
-    QDesc* hd = db->qd_host + (int64_t)slot * db->opt.max_batch;
-    QDesc* dd = db->qd_dev + (int64_t)slot * db->opt.max_batch;
-    int* nqd = db->nq_dev + slot;
+    QDesc* hd = ws.qd_host + (int64_t)slot * ws.max_batch;
+    QDesc* dd = ws.qd_dev + (int64_t)slot * ws.max_batch;
+    int* nqd = ws.nq_dev + slot;
     const int64_t n = db->n;
     int max_rows = 0, max_npad = 0, max_ldd = 0, max_tk = 0, max_kc = 0;
     int64_t c_D = 0, c_Q = 0, c_P = 0, c_T = 0;
@@ -462,26 +532,26 @@ emd_status fill_descriptors(int slot, emd_db* db, const int64_t* rp, const int32
         d.qidx = qidx + off;
         d.qw = qw + off;
         if (!db->cost_mode) {
-            d.Q = db->bQ + c_Q * db->ldm;
-            d.qnorm = db->bqnorm + c_Q;
+            d.Q = ws.bQ + c_Q * db->ldm;
+            d.qnorm = ws.bqnorm + c_Q;
             if (db->tc) {
-                d.q_hi = db->bq_hi + c_P * db->kpad;
-                d.q_lo = db->tcfmt == TC_SPLIT ? db->bq_lo + c_P * db->kpad : nullptr;
-                d.q_scale = db->bq_scale + c_P;
+                d.q_hi = ws.bq_hi + c_P * db->kpad;
+                d.q_lo = db->tcfmt == TC_SPLIT ? ws.bq_lo + c_P * db->kpad : nullptr;
+                d.q_scale = ws.bq_scale + c_P;
             }
         }
-        d.D = db->bD + c_D * db->v_used;
-        d.tab = db->btab + c_T * db->v_used;
-        d.t_fwd = db->bt_fwd + (int64_t)b * n;
-        d.t_rev = db->bt_rev + (int64_t)b * n;
-        d.t_out = (K > 0 ? db->stage_out : out_t) + (int64_t)b * n;
+        d.D = ws.bD + c_D * db->v_used;
+        d.tab = ws.btab + c_T * db->v_used;
+        d.t_fwd = ws.bt_fwd + (int64_t)b * n;
+        d.t_rev = ws.bt_rev + (int64_t)b * n;
+        d.t_out = (K > 0 ? ws.bt_out : out_t) + (int64_t)b * n;
         if (pruned) {
-            d.sel_idx = db->bsel_idx + (int64_t)b * K;
-            d.sel_val = db->bsel_val + (int64_t)b * K;
-            d.cand = db->bcand + (int64_t)b * kPruneCap;
-            d.cand_sym = db->bcand_sym + (int64_t)b * 2 * kPruneCap;
-            d.cand_count = db->bcand_count + b;
-            d.ok = db->cand_ok + b;
+            d.sel_idx = ws.bsel_idx + (int64_t)b * K;
+            d.sel_val = ws.bsel_val + (int64_t)b * K;
+            d.cand = ws.bcand + (int64_t)b * kPruneCap;
+            d.cand_sym = ws.bcand_sym + (int64_t)b * 2 * kPruneCap;
+            d.cand_count = ws.bcand_count + b;
+            d.ok = ws.cand_ok + b;
         }
         if (K > 0) {
             d.out_idx = out_idx + (int64_t)b * K;
@@ -497,35 +567,38 @@ emd_status fill_descriptors(int slot, emd_db* db, const int64_t* rp, const int32
         max_tk = std::max(max_tk, d.tk);
         max_kc = std::max(max_kc, d.kc);
     }
-    db->nq_host[slot] = nb;
+    ws.nq_host[slot] = nb;
     EMD_CUDA(cudaMemcpyAsync(dd, hd, sizeof(QDesc) * nb, cudaMemcpyHostToDevice, st), "descriptor upload");
-    EMD_CUDA(cudaMemcpyAsync(nqd, db->nq_host + slot, sizeof(int), cudaMemcpyHostToDevice, st), "descriptor upload");
+    EMD_CUDA(cudaMemcpyAsync(nqd, ws.nq_host + slot, sizeof(int), cudaMemcpyHostToDevice, st), "descriptor upload");
     (void)max_rows; (void)max_npad; (void)max_ldd; (void)max_tk; (void)max_kc;
     return EMD_OK;
 }
 
 // Runs the sub-batch whose descriptors fill_descriptors put in `slot` (nb queries).
-emd_status run_subbatch_launch(int slot, emd_db* db, int nb, int meas, int k, int dir, int K, bool pruned,
+emd_status run_subbatch_launch(BatchWS& ws, int slot, emd_db* db, int nb, int meas, int k, int dir, int K, bool pruned,
                                cudaStream_t st)
 {
-    const QDesc* hd = db->qd_host + (int64_t)slot * db->opt.max_batch;
+    const QDesc* hd = ws.qd_host + (int64_t)slot * ws.max_batch;
+    int qcap = 1;  // size class of the batch: the next power of two
+    while (qcap < nb) qcap *= 2;
+    qcap = std::min(qcap, ws.max_batch);
     if (db->tc && tc_batch_stages(db->tcfmt, db->kpad / 64) < 2) {
         // embeddings too wide for the batched panel: Phase 1 per query, the rest batched
-        return launch_sequence(db, slot, meas, k, K, dir, pruned, hd, nb, st);
+        return launch_sequence(ws, db, slot, meas, k, K, dir, pruned, hd, nb, qcap, st);
     }
-    if (!db->opt.graphs || db->profiling) return launch_sequence(db, slot, meas, k, K, dir, pruned, nullptr, 0, st);
-    const GraphKey key{meas, k, K, dir, pruned ? 1 : 0, slot};
-    auto it = db->graphs.find(key);
-    if (it == db->graphs.end()) {
+    if (!db->opt.graphs || db->profiling) return launch_sequence(ws, db, slot, meas, k, K, dir, pruned, nullptr, 0, qcap, st);
+    const GraphKey key{meas, k, K, dir, pruned ? 1 : 0, slot, qcap};
+    auto it = ws.graphs.find(key);
+    if (it == ws.graphs.end()) {
         GraphEntry g;
-        emd_status cs = capture_sequence(db, slot, meas, k, K, dir, pruned, &g);
+        emd_status cs = capture_sequence(ws, db, slot, meas, k, K, dir, pruned, qcap, &g);
         if (cs != EMD_OK) {
             g_err.clear();
             g.exec = nullptr;  // capture refused: this key launches directly from now on
         }
-        it = db->graphs.emplace(key, g).first;
+        it = ws.graphs.emplace(key, g).first;
     }
-    if (!it->second.exec) return launch_sequence(db, slot, meas, k, K, dir, pruned, nullptr, 0, st);
+    if (!it->second.exec) return launch_sequence(ws, db, slot, meas, k, K, dir, pruned, nullptr, 0, qcap, st);
     EMD_CUDA(cudaGraphLaunch(it->second.exec, st), "graph launch");
     for (int p = 0; p < EMD_N_PHASES; ++p) db->launches[p] += it->second.launches[p];
     db->total_launches += it->second.total;
@@ -535,18 +608,35 @@ emd_status run_subbatch_launch(int slot, emd_db* db, int nb, int meas, int k, in
 
 // Ring slots are reused only after the work that reads them (pinned host copy and device
 // descriptors) has finished, whatever stream it ran on.
-emd_status run_subbatch(emd_db* db, const int64_t* rp, const int32_t* qidx, const float* qw, int64_t i0,
+emd_status run_subbatch(emd_db* db, BatchWS& ws, const int64_t* rp, const int32_t* qidx, const float* qw, int64_t i0,
                         int64_t j0, int64_t j1, int meas, int k, int dir, int K, bool pruned, float* out_t,
                         int64_t* out_idx, float* out_dist, cudaStream_t st)
 {
-    const int slot = db->desc_slot;
-    db->desc_slot = (slot + 1) % emd_db::kDescRing;
-    EMD_CUDA(cudaEventSynchronize(db->desc_ev[slot]), "descriptor ring");
-    emd_status s = fill_descriptors(slot, db, rp, qidx, qw, i0, j0, j1, meas, k, dir, K, pruned, out_t, out_idx,
+    const int slot = ws.desc_slot;
+    ws.desc_slot = (slot + 1) % BatchWS::kDescRing;
+    EMD_CUDA(cudaEventSynchronize(ws.desc_ev[slot]), "descriptor ring");
+    emd_status s = fill_descriptors(ws, slot, db, rp, qidx, qw, i0, j0, j1, meas, k, dir, K, pruned, out_t, out_idx,
                                     out_dist, st);
-    if (s == EMD_OK) s = run_subbatch_launch(slot, db, (int)(j1 - j0), meas, k, dir, K, pruned, st);
-    EMD_CUDA(cudaEventRecord(db->desc_ev[slot], st), "descriptor ring");
+    if (s == EMD_OK) s = run_subbatch_launch(ws, slot, db, (int)(j1 - j0), meas, k, dir, K, pruned, st);
+    EMD_CUDA(cudaEventRecord(ws.desc_ev[slot], st), "descriptor ring");
     return s;
+}
+
+bool batch_fits(const emd_db* db, const BatchWS& ws, const int64_t* rp, int64_t i0, int64_t i1, int meas, int k,
+                int dir)
+{
+    int64_t cD = 0, cQ = 0, cP = 0, cT = 0;
+    if (i1 - i0 > ws.max_batch) return false;
+    for (int64_t i = i0; i < i1; ++i) {
+        const int h = (int)(rp[i + 1] - rp[i]);
+        const int64_t ldd = round_up(h, 32);
+        cD += ldd;
+        cQ += round_up(ldd, kDistBN);
+        cP += round_up(h, 128);
+        cT += dir != EMD_DIR_REV ? table_width(meas, k, h) : 0;
+    }
+    (void)db;
+    return cD <= ws.b_cols && cQ <= ws.b_qrows && cP <= ws.b_prows && cT <= ws.b_tabcols;
 }
 
 emd_status run_batch(emd_db* db, const int64_t* rp, const int32_t* qidx, const float* qw, int64_t i0,
@@ -556,23 +646,12 @@ emd_status run_batch(emd_db* db, const int64_t* rp, const int32_t* qidx, const f
     const bool pruned = K > 0 && prunable(db, meas, k, dir, K);
     if (db->opt.batched) {
         // split into sub-batches that fit the batch workspace
+        BatchWS& ws = db->bw;
         int64_t j0 = i0;
         while (j0 < i1) {
-            int64_t j1 = j0, cD = 0, cQ = 0, cP = 0, cT = 0;
-            while (j1 < i1) {
-                const int h = (int)(rp[j1 + 1] - rp[j1]);
-                const int64_t ldd = round_up(h, 32);
-                const int64_t tk = dir != EMD_DIR_REV ? table_width(meas, k, h) : 0;
-                if (j1 > j0 && (cD + ldd > db->b_cols || cQ + round_up(ldd, kDistBN) > db->b_qrows ||
-                                cP + round_up(h, 128) > db->b_prows || cT + tk > db->b_tabcols))
-                    break;
-                cD += ldd;
-                cQ += round_up(ldd, kDistBN);
-                cP += round_up(h, 128);
-                cT += tk;
-                ++j1;
-            }
-            emd_status s = run_subbatch(db, rp, qidx, qw, i0, j0, j1, meas, k, dir, K, pruned, out_t, out_idx,
+            int64_t j1 = j0 + 1;
+            while (j1 < i1 && batch_fits(db, ws, rp, j0, j1 + 1, meas, k, dir)) ++j1;
+            emd_status s = run_subbatch(db, ws, rp, qidx, qw, i0, j0, j1, meas, k, dir, K, pruned, out_t, out_idx,
                                         out_dist, st);
             if (s != EMD_OK) return s;
             j0 = j1;
@@ -584,7 +663,8 @@ emd_status run_batch(emd_db* db, const int64_t* rp, const int32_t* qidx, const f
     if (K > 0 && !pruned && !db->opt.batched) return select_topk(db, db->stage_out, i1 - i0, K, out_idx, out_dist, st);
     if (!pruned) return EMD_OK;
     std::vector<int> ok((size_t)(i1 - i0), 0);
-    EMD_CUDA(cudaMemcpyAsync(ok.data(), db->cand_ok, (i1 - i0) * sizeof(int), cudaMemcpyDeviceToHost, st),
+    EMD_CUDA(cudaMemcpyAsync(ok.data(), db->opt.batched ? db->bw.cand_ok : db->cand_ok, (i1 - i0) * sizeof(int),
+                             cudaMemcpyDeviceToHost, st),
              "flag read");
     EMD_CUDA(cudaStreamSynchronize(st), "synchronize");
     db->pruned_queries += i1 - i0;
@@ -717,14 +797,16 @@ emd_status autotune(emd_db* db, const std::vector<int32_t>& used_host)
         for (int j = 0; j < h; ++j) idx[(size_t)i * h + j] = used_host[(size_t)((start + j) % db->v_used)];
     }
     cudaStream_t st = db->stream;
+    BatchWS& ws = db->bw;
     EMD_CUDA(cudaMemcpyAsync(db->stage_idx, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice, st), "tune copy");
     EMD_CUDA(cudaMemcpyAsync(db->stage_w, w.data(), w.size() * 4, cudaMemcpyHostToDevice, st), "tune copy");
     const bool pruned = prunable(db, EMD_ACT, k, EMD_DIR_MAX, K);
-    emd_status s = fill_descriptors(0, db, rp.data(), db->stage_idx, db->stage_w, 0, 0, nb, EMD_ACT, k, EMD_DIR_MAX, K,
+    emd_status s = fill_descriptors(ws, 0, db, rp.data(), db->stage_idx, db->stage_w, 0, 0, nb, EMD_ACT, k, EMD_DIR_MAX, K,
                                     pruned, nullptr, db->stage_oidx, db->stage_odist, st);
     if (s != EMD_OK) return s;
     const bool per_query_tc = db->tc && tc_batch_stages(db->tcfmt, db->kpad / 64) < 2;
-    s = launch_sequence(db, 0, EMD_ACT, k, K, EMD_DIR_MAX, pruned, per_query_tc ? db->qd_host : nullptr, nb, st);
+    s = launch_sequence(ws, db, 0, EMD_ACT, k, K, EMD_DIR_MAX, pruned, per_query_tc ? ws.qd_host : nullptr, nb,
+                        ws.max_batch, st);
     if (s != EMD_OK) return s;
     EMD_CUDA(cudaStreamSynchronize(st), "synchronize");
     cudaEvent_t a = nullptr, b = nullptr;
@@ -743,8 +825,8 @@ emd_status autotune(emd_db* db, const std::vector<int32_t>& used_host)
         }
         return best;
     };
-    const QDesc* D_ = db->qd_dev;
-    const int* nqd = db->nq_dev;
+    const QDesc* D_ = ws.qd_dev;
+    const int* nqd = ws.nq_dev;
     if (db->tc && tc_batch_stages(db->tcfmt, db->kpad / 64) >= 2) {
         // a candidate replaces the current choice only when at least 5% faster (timing noise
         // on short launches would otherwise pick at random)
@@ -769,7 +851,7 @@ emd_status autotune(emd_db* db, const std::vector<int32_t>& used_host)
         float best = 1e30f;
         for (int wp : {4, 2, 8}) {  // the default first
             const float ms = timed([&] {
-                cudaMemsetAsync(db->bcand_count, 0, sizeof(int) * db->opt.max_batch, st);
+                cudaMemsetAsync(ws.bcand_count, 0, sizeof(int) * db->opt.max_batch, st);
                 launch_prune_b(EMD_ACT, k, D_, nqd, db->opt.max_batch, db->row_ptr, db->col, db->val, db->n, K, wp,
                                st);
             });
@@ -900,7 +982,6 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
     TRYC(cudaSetDevice(db->dev), "cudaSetDevice");
     TRYC(cudaStreamCreateWithFlags(&db->stream, cudaStreamNonBlocking), "stream");
     TRYC(cudaEventCreateWithFlags(&db->fork, cudaEventDisableTiming), "event");
-    TRYC(cudaStreamCreateWithFlags(&db->cap_stream, cudaStreamNonBlocking), "stream");
     db->lanes.resize((size_t)opt.lanes);
     for (auto& L : db->lanes) {
         TRYC(cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking), "stream");
@@ -982,38 +1063,7 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
     TRY(dalloc(db, &db->tab_s, vu * opt.max_table_k));
     TRY(dalloc(db, &db->topk_scratch, (int64_t)opt.max_batch * kTopkScratchRow));
     TRY(dalloc(db, &db->cand_ok, opt.max_batch));
-    if (opt.batched) {
-        const int64_t B = opt.max_batch;
-        db->b_cols = std::max<int64_t>(round_up(opt.batch_columns, 32), db->ldd_max);
-        db->b_qrows = db->b_cols + 32 * B;
-        db->b_prows = db->b_cols + 96 * B;
-        db->b_tabcols = std::max<int64_t>(opt.max_table_k, 16 * B);
-        TRY(dalloc(db, &db->bD, vu * db->b_cols));
-        if (!db->cost_mode) {
-            TRY(dalloc(db, &db->bQ, db->b_qrows * db->ldm));
-            TRY(dalloc(db, &db->bqnorm, db->b_qrows));
-            if (db->tc) {
-                TRY(dalloc(db, &db->bq_hi, db->b_prows * db->kpad));
-                if (db->tcfmt == TC_SPLIT) TRY(dalloc(db, &db->bq_lo, db->b_prows * db->kpad));
-                TRY(dalloc(db, &db->bq_scale, db->b_prows));
-            }
-        }
-        TRY(dalloc(db, &db->btab, vu * db->b_tabcols));
-        TRY(dalloc(db, &db->bt_fwd, B * n_docs));
-        TRY(dalloc(db, &db->bt_rev, B * n_docs));
-        TRY(dalloc(db, &db->bsel_idx, B * kPruneMaxK));
-        TRY(dalloc(db, &db->bsel_val, B * kPruneMaxK));
-        TRY(dalloc(db, &db->bcand, B * kPruneCap));
-        TRY(dalloc(db, &db->bcand_sym, B * 2 * kPruneCap));
-        TRY(dalloc(db, &db->bcand_count, B));
-        TRY(dalloc(db, &db->qd_dev, emd_db::kDescRing * B));
-        TRY(dalloc(db, &db->nq_dev, emd_db::kDescRing));
-        TRYC(cudaHostAlloc((void**)&db->qd_host, sizeof(QDesc) * emd_db::kDescRing * B, cudaHostAllocDefault),
-             "pinned descriptors");
-        TRYC(cudaHostAlloc((void**)&db->nq_host, sizeof(int) * emd_db::kDescRing, cudaHostAllocDefault),
-             "pinned descriptors");
-        for (auto& e : db->desc_ev) TRYC(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
-    }
+    if (opt.batched) TRY(alloc_batch_ws(db, db->bw, opt.max_batch, opt.batch_columns, db->allocs, &db->bytes));
     db->stage_bins = (int64_t)opt.max_batch * opt.max_query_h;
     TRY(dalloc(db, &db->stage_idx, db->stage_bins));
     TRY(dalloc(db, &db->stage_w, db->stage_bins));

@@ -50,7 +50,7 @@ struct Lane {
 namespace emd {
 // One captured batch sequence (launch_sequence) and the kernel launches it holds.
 struct GraphKey {
-    int meas, k, K, dir, pruned, slot;
+    int meas, k, K, dir, pruned, slot, qcap;  // qcap: queries the grids cover (power of two)
     bool operator<(const GraphKey& o) const
     {
         if (meas != o.meas) return meas < o.meas;
@@ -58,13 +58,51 @@ struct GraphKey {
         if (K != o.K) return K < o.K;
         if (dir != o.dir) return dir < o.dir;
         if (pruned != o.pruned) return pruned < o.pruned;
-        return slot < o.slot;
+        if (slot != o.slot) return slot < o.slot;
+        return qcap < o.qcap;
     }
 };
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     int64_t launches[EMD_N_PHASES] = {};
     int64_t total = 0;
+};
+}  // namespace emd
+
+namespace emd {
+// Workspace of the batched form: every buffer a batch of up to max_batch queries and
+// b_cols distance-matrix columns needs, the descriptor ring and the captured graphs (which
+// bake these pointers in).  The database handle owns one for the host-API calls; each
+// server executor owns its own.
+struct BatchWS {
+    static constexpr int kDescRing = 4;
+    int max_batch = 0;
+    int64_t b_cols = 0, b_qrows = 0, b_prows = 0, b_tabcols = 0;
+    float* bD = nullptr;          // v_used x b_cols: the batch's distance matrices side by side
+    float* bQ = nullptr;          // b_qrows x ldm
+    float* bqnorm = nullptr;      // b_qrows
+    __half* bq_hi = nullptr;      // b_prows x kpad packed panels
+    __half* bq_lo = nullptr;
+    float* bq_scale = nullptr;    // b_prows
+    float2* btab = nullptr;       // v_used x b_tabcols tables
+    float* bt_fwd = nullptr;      // max_batch x n
+    float* bt_rev = nullptr;      // max_batch x n
+    float* bt_out = nullptr;      // max_batch x n (distances of unpruned top-K batches)
+    int64_t* bsel_idx = nullptr;  // max_batch x kPruneMaxK
+    float* bsel_val = nullptr;
+    int64_t* bcand = nullptr;     // max_batch x kPruneCap
+    float* bcand_sym = nullptr;   // max_batch x 2 kPruneCap
+    int* bcand_count = nullptr;   // max_batch
+    int* cand_ok = nullptr;       // max_batch certification flags
+    unsigned long long* topk_scratch = nullptr;  // max_batch x kTopkScratchRow
+    QDesc* qd_dev = nullptr;      // kDescRing x max_batch descriptors
+    int* nq_dev = nullptr;        // kDescRing counts
+    QDesc* qd_host = nullptr;     // pinned mirror of the ring
+    int* nq_host = nullptr;
+    cudaEvent_t desc_ev[kDescRing] = {};
+    int desc_slot = 0;
+    cudaStream_t cap_stream = nullptr;  // graph capture
+    std::map<GraphKey, GraphEntry> graphs;
 };
 }  // namespace emd
 
@@ -127,37 +165,16 @@ struct emd_db {
     int64_t total_launches = 0;
     int64_t pruned_queries = 0, prune_fallbacks = 0;
 
-    // batched form: one launch per step for a whole batch (opt.batched)
-    static constexpr int kDescRing = 4;
-    int64_t b_cols = 0, b_qrows = 0, b_prows = 0, b_tabcols = 0;
-    float* bD = nullptr;          // v_used x b_cols: the batch's distance matrices side by side
-    float* bQ = nullptr;          // b_qrows x ldm
-    float* bqnorm = nullptr;      // b_qrows
-    __half* bq_hi = nullptr;      // b_prows x kpad packed panels
-    __half* bq_lo = nullptr;
-    float* bq_scale = nullptr;    // b_prows
-    float2* btab = nullptr;       // v_used x b_tabcols tables
-    float* bt_fwd = nullptr;      // max_batch x n
-    float* bt_rev = nullptr;      // max_batch x n
-    int64_t* bsel_idx = nullptr;  // max_batch x kPruneMaxK
-    float* bsel_val = nullptr;
-    int64_t* bcand = nullptr;     // max_batch x kPruneCap
-    float* bcand_sym = nullptr;   // max_batch x 2 kPruneCap
-    int* bcand_count = nullptr;   // max_batch
-    emd::QDesc* qd_dev = nullptr; // kDescRing x max_batch descriptors
-    int* nq_dev = nullptr;        // kDescRing counts
-    emd::QDesc* qd_host = nullptr;  // pinned mirror of the ring
-    int* nq_host = nullptr;
-    cudaEvent_t desc_ev[kDescRing] = {};
-    int desc_slot = 0;
-    cudaStream_t cap_stream = nullptr;              // graph capture
+    // batched form (opt.batched): the workspace of the host-API batches
+    emd::BatchWS bw;
+    int64_t graph_launches = 0;   // batch sequences replayed from graphs (all workspaces)
+
     // free parameters of the batched kernels (autotune at creation)
     bool autotuned = false;
     int tune_group_mult = 1;   // query groups per vocabulary tile, times the balance minimum
     int tune_stages = 0;       // B stages of the batched tensor-core kernel (0: as many as fit)
     int tune_rev_warps = 4;    // warps per candidate document in the pruned reverse pass
     std::map<emd::GraphKey, emd::GraphEntry> graphs;
-    int64_t graph_launches = 0;
 
     // Serialises the entry points that launch work or touch the counters above (host
     // threads, and the server's worker thread).
@@ -184,5 +201,23 @@ emd_status run_query(emd_db* db, Lane& L, const int32_t* qidx, const float* qw, 
 // certificate.  Caller holds db->mu.
 emd_status run_topk_pruned(emd_db* db, Lane& L, const int32_t* qidx, const float* qw, int h, int meas, int k,
                            int K, int* ok, int64_t* out_idx, float* out_dist, cudaStream_t st);
+
+// Batch workspaces (emd_api.cu).  alloc_batch_ws records its device allocations in
+// `allocs` (freed by the owner) and adds their size to *bytes; free_batch_ws releases the
+// rest (pinned ring, events, capture stream, graphs).
+emd_status alloc_batch_ws(emd_db* db, BatchWS& ws, int max_batch, int64_t cols, std::vector<void*>& allocs,
+                          int64_t* bytes);
+void free_batch_ws(BatchWS& ws);
+
+// Sub-batch j0..j1-1 of the queries i0.. (host rp, device qidx / qw relative to query i0)
+// on ws, in ring slot order: descriptors, then the batched sequence (graph replay when
+// enabled) on st.  Outputs: out_t rows (K = 0), else out_idx / out_dist rows, relative to
+// i0; certification flags in ws.cand_ok[i - i0] on the pruned path.  Caller holds db->mu.
+emd_status run_subbatch(emd_db* db, BatchWS& ws, const int64_t* rp, const int32_t* qidx, const float* qw,
+                        int64_t i0, int64_t j0, int64_t j1, int meas, int k, int dir, int K, bool pruned,
+                        float* out_t, int64_t* out_idx, float* out_dist, cudaStream_t st);
+// Whether the batch (rp entries i0..i1) fits one sub-batch of ws.
+bool batch_fits(const emd_db* db, const BatchWS& ws, const int64_t* rp, int64_t i0, int64_t i1, int meas, int k,
+                int dir);
 
 }  // namespace emd

@@ -1,13 +1,14 @@
 // Serving (include/emd.h, emd_server_*): a request loop over a resident database.
 //
-// Requests are single queries.  A worker thread admits them in arrival order onto slots --
-// each slot a stream with pinned staging -- as long as a slot is free and the device
-// workspace pool can hold the request, and runs on the slot the same kernel sequence as
-// the batch entry points (Phase 1, table, forward pass, pruned reverse pass and top-K of
-// Section 4/5; the unpruned path with a full top-K otherwise).  Requests that arrive while
-// others are on the device are admitted as slots and workspace free up, so their kernels
-// overlap on the GPU.  A request's arithmetic depends only on its own inputs: no sum or
-// selection crosses requests, hence a result is the same alone and in any mix.
+// Requests are single queries.  A worker thread forms batches from the head of the queue
+// and runs each on one of two executors -- a batch workspace of its own, pinned staging
+// and a stream -- with the same batched kernel sequence as the host entry points (Phase 1,
+// table, forward pass, pruned reverse pass and top-K of Sections 4-5, replayed from a
+// captured graph).  While one batch is on the GPU the next one collects the requests that
+// arrived meanwhile (continuous batching), admitted in arrival order as long as the
+// executor's workspace -- its distance-matrix columns, i.e. device memory -- can hold them.
+// The batched kernels compute every query exactly as the per-query ones do (no sum or
+// selection crosses queries), so a result is the same alone and in any mix.
 #include <math.h>
 #include <string.h>
 
@@ -16,7 +17,6 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
-#include <map>
 #include <memory>
 #include <string>
 #include <thread>
@@ -32,110 +32,7 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-constexpr int64_t kAlign = 256;
-
-int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
-
-// First-fit allocator over the workspace pool: free blocks keyed by offset, coalesced on
-// release.  Sizes are multiples of kAlign.
-class PoolAllocator {
-public:
-    void reset(int64_t bytes)
-    {
-        free_.clear();
-        if (bytes > 0) free_[0] = bytes;
-        used_ = 0;
-    }
-    bool alloc(int64_t size, int64_t* off)
-    {
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second < size) continue;
-            *off = it->first;
-            const int64_t rest = it->second - size;
-            const int64_t next = it->first + size;
-            free_.erase(it);
-            if (rest > 0) free_[next] = rest;
-            used_ += size;
-            return true;
-        }
-        return false;
-    }
-    void release(int64_t off, int64_t size)
-    {
-        auto it = free_.emplace(off, size).first;
-        auto nx = std::next(it);
-        if (nx != free_.end() && it->first + it->second == nx->first) {
-            it->second += nx->second;
-            free_.erase(nx);
-        }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free_.erase(it);
-            }
-        }
-        used_ -= size;
-    }
-    int64_t used() const { return used_; }
-
-private:
-    std::map<int64_t, int64_t> free_;
-    int64_t used_ = 0;
-};
-
-// Device buffers of one request, carved from the pool.
-struct ReqDev {
-    int32_t* idx = nullptr;
-    float* w = nullptr;
-    Lane L;
-    float* t_out = nullptr;
-    int64_t* out_idx = nullptr;
-    float* out_dist = nullptr;
-    int* ok = nullptr;
-};
-
-// Lays out a request's buffers from `base` (nullptr: sizes only) and returns the bytes.
-int64_t layout(const emd_db* db, int h, int tk, char* base, ReqDev* r)
-{
-    int64_t off = 0;
-    auto take = [&](auto** p, int64_t bytes) {
-        using T = std::remove_reference_t<decltype(**p)>;
-        if (base) *p = reinterpret_cast<T*>(base + off);
-        off += align_up(std::max<int64_t>(bytes, 1));
-    };
-    ReqDev tmp;
-    ReqDev& d = r ? *r : tmp;
-    const int ldd = (int)round_up(h, 32);
-    const int qrows = (int)round_up(ldd, kDistBN);
-    const int64_t npad = round_up(h, 128);
-    take(&d.idx, (int64_t)h * 4);
-    take(&d.w, (int64_t)h * 4);
-    if (!db->cost_mode) {
-        take(&d.L.Q, (int64_t)qrows * db->ldm * 4);
-        take(&d.L.qnorm, (int64_t)qrows * 4);
-        if (db->tc) {
-            take(&d.L.q_hi, npad * db->kpad * 2);
-            if (db->tcfmt == TC_SPLIT) take(&d.L.q_lo, npad * db->kpad * 2);
-            take(&d.L.q_scale, npad * 4);
-        }
-    }
-    take(&d.L.D, db->v_used * ldd * 4);
-    take(&d.L.tab, db->v_used * tk * 8);
-    take(&d.L.t_fwd, db->n * 4);
-    take(&d.L.t_rev, db->n * 4);
-    take(&d.t_out, db->n * 4);
-    take(&d.L.sel_idx, kPruneMaxK * 8);
-    take(&d.L.sel_val, kPruneMaxK * 4);
-    take(&d.L.cand_idx, kPruneCap * 8);
-    take(&d.L.cand_sym, 2 * kPruneCap * 4);
-    take(&d.L.cand_count, 4);
-    take(&d.L.scratch, kTopkScratchRow * 8);
-    take(&d.out_idx, kMaxTopK * 8);
-    take(&d.out_dist, kMaxTopK * 4);
-    take(&d.ok, 4);
-    return off;
-}
+constexpr int kExecs = 2;
 
 enum ReqState { QUEUED = 0, RUNNING = 1, DONE = 2 };
 
@@ -146,7 +43,6 @@ struct Request {
     std::vector<int32_t> idx;
     std::vector<float> w;
     Clock::time_point t_submit;
-    int64_t ws_off = -1, ws_bytes = 0;
     int state = QUEUED;
     emd_status status = EMD_OK;
     std::string err;
@@ -154,18 +50,27 @@ struct Request {
     std::vector<float> out_dist;
 };
 
-struct Slot {
+// One batch executor.
+struct Exec {
+    BatchWS ws;
     cudaStream_t st = nullptr;
-    cudaEvent_t ev = nullptr;
-    char* pinned = nullptr;  // idx | w | out_idx | out_dist | ok
+    cudaEvent_t done = nullptr;
+    char* pinned = nullptr;  // rp | idx | w | out_idx | out_dist | ok
+    int64_t* h_rp = nullptr;
     int32_t* h_idx = nullptr;
     float* h_w = nullptr;
     int64_t* h_oidx = nullptr;
     float* h_odist = nullptr;
     int* h_ok = nullptr;
-    Request* req = nullptr;
-    ReqDev dev;
-    bool fallback = false;  // the unpruned recomputation is in flight
+    int32_t* d_idx = nullptr;
+    float* d_w = nullptr;
+    int64_t* d_oidx = nullptr;
+    float* d_odist = nullptr;
+    std::vector<Request*> batch;
+    int meas = 0, k = 0, K = 0;
+    bool pruned = false;
+    int64_t cols = 0;
+    bool busy = false;
 };
 
 double pct(std::vector<double> v, double p)
@@ -176,16 +81,18 @@ double pct(std::vector<double> v, double p)
     return v[i];
 }
 
+int64_t align256(int64_t x) { return (x + 255) / 256 * 256; }
+
 }  // namespace
 
 struct emd_server {
     emd_db* db = nullptr;
     emd_server_options opt{};
-    char* pool = nullptr;
-    int64_t pool_bytes = 0;
-    PoolAllocator alloc;
-    std::vector<Slot> slots;
-    std::vector<int> free_slots;
+    Exec ex[kExecs];
+    Lane fb;                        // per-query workspace for uncertified pruned requests
+    float* fb_out = nullptr;        // its n symmetric distances
+    std::vector<void*> allocs;      // device memory of the executors and the fallback lane
+    int64_t bytes = 0, pool_bytes = 0;
 
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -193,7 +100,7 @@ struct emd_server {
     std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
     uint64_t next_ticket = 1;
     bool stop = false;
-    int running = 0;
+    int in_flight = 0;
     std::thread worker;
 
     // statistics since the last reset
@@ -206,87 +113,151 @@ struct emd_server {
 
 namespace {
 
-void finish(emd_server* s, Slot& sl, emd_status st, const char* why)
+template <typename T>
+emd_status sdal(emd_server* s, T** p, int64_t count)
 {
-    // caller holds s->mu
-    Request* r = sl.req;
-    r->status = st;
-    if (st != EMD_OK) {
-        r->err = why ? why : "";
-        ++s->failed;
-    } else {
-        r->out_idx.assign(sl.h_oidx, sl.h_oidx + r->K);
-        r->out_dist.assign(sl.h_odist, sl.h_odist + r->K);
-        ++s->completed;
-        const Clock::time_point now = Clock::now();
-        s->lat_us.push_back(std::chrono::duration<double, std::micro>(now - r->t_submit).count());
-        s->t_last = now;
+    const size_t nb = (size_t)std::max<int64_t>(count, 1) * sizeof(T);
+    void* q = nullptr;
+    const cudaError_t e = cudaMalloc(&q, nb);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(EMD_ERR_OUT_OF_MEMORY, "server: cudaMalloc of %zu bytes failed", nb);
     }
-    r->state = DONE;
-    s->alloc.release(r->ws_off, r->ws_bytes);
-    sl.req = nullptr;
-    sl.fallback = false;
-    --s->running;
-    s->free_slots.push_back((int)(&sl - s->slots.data()));
+    s->allocs.push_back(q);
+    s->bytes += (int64_t)nb;
+    *p = static_cast<T*>(q);
+    return EMD_OK;
+}
+
+void destroy_resources(emd_server* s)
+{
+    for (Exec& e : s->ex) {
+        free_batch_ws(e.ws);
+        if (e.done) cudaEventDestroy(e.done);
+        if (e.st) cudaStreamDestroy(e.st);
+        if (e.pinned) cudaFreeHost(e.pinned);
+    }
+    for (void* p : s->allocs) cudaFree(p);
+    s->allocs.clear();
+}
+
+// Marks every request of the executor's batch finished (caller holds s->mu).
+void finish_batch(emd_server* s, Exec& e, emd_status st, const char* why)
+{
+    const Clock::time_point now = Clock::now();
+    for (size_t i = 0; i < e.batch.size(); ++i) {
+        Request* r = e.batch[i];
+        r->status = st;
+        if (st != EMD_OK) {
+            r->err = why ? why : "";
+            ++s->failed;
+        } else {
+            r->out_idx.assign(e.h_oidx + i * r->K, e.h_oidx + (i + 1) * r->K);
+            r->out_dist.assign(e.h_odist + i * r->K, e.h_odist + (i + 1) * r->K);
+            ++s->completed;
+            s->lat_us.push_back(std::chrono::duration<double, std::micro>(now - r->t_submit).count());
+            s->t_last = now;
+        }
+        r->state = DONE;
+    }
+    s->in_flight -= (int)e.batch.size();
+    e.batch.clear();
+    e.busy = false;
     s->cv_done.notify_all();
 }
 
-// Issues a request's kernels on its slot (worker thread, s->mu not held).
-emd_status launch(emd_server* s, Slot& sl)
+// Stages the batch's bins and issues its kernels and result copies (worker thread, s->mu
+// not held).
+emd_status launch_batch(emd_server* s, Exec& e)
 {
     emd_db* db = s->db;
-    Request* r = sl.req;
-    layout(db, r->h, table_width(r->meas, r->k, r->h), s->pool + r->ws_off, &sl.dev);
-    memcpy(sl.h_idx, r->idx.data(), (size_t)r->h * 4);
-    memcpy(sl.h_w, r->w.data(), (size_t)r->h * 4);
-    EMD_CUDA(cudaMemcpyAsync(sl.dev.idx, sl.h_idx, (size_t)r->h * 4, cudaMemcpyHostToDevice, sl.st), "query copy");
-    EMD_CUDA(cudaMemcpyAsync(sl.dev.w, sl.h_w, (size_t)r->h * 4, cudaMemcpyHostToDevice, sl.st), "query copy");
+    const int nb = (int)e.batch.size();
+    int64_t bins = 0;
+    e.h_rp[0] = 0;
+    for (int i = 0; i < nb; ++i) {
+        const Request* r = e.batch[(size_t)i];
+        memcpy(e.h_idx + bins, r->idx.data(), (size_t)r->h * 4);
+        memcpy(e.h_w + bins, r->w.data(), (size_t)r->h * 4);
+        bins += r->h;
+        e.h_rp[i + 1] = bins;
+    }
+    EMD_CUDA(cudaMemcpyAsync(e.d_idx, e.h_idx, (size_t)bins * 4, cudaMemcpyHostToDevice, e.st), "query copy");
+    EMD_CUDA(cudaMemcpyAsync(e.d_w, e.h_w, (size_t)bins * 4, cudaMemcpyHostToDevice, e.st), "query copy");
     {
         std::lock_guard<std::mutex> lock(db->mu);
-        emd_status st;
-        if (r->pruned) {
-            st = run_topk_pruned(db, sl.dev.L, sl.dev.idx, sl.dev.w, r->h, r->meas, r->k, r->K, sl.dev.ok,
-                                 sl.dev.out_idx, sl.dev.out_dist, sl.st);
-            if (st == EMD_OK) db->pruned_queries += 1;
-        } else {
-            st = run_query(db, sl.dev.L, sl.dev.idx, sl.dev.w, r->h, r->meas, r->k, EMD_DIR_MAX, sl.dev.t_out, sl.st);
-            if (st == EMD_OK) {
-                db->launches[5] += topk_launch_count(db->n);
-                db->total_launches += topk_launch_count(db->n);
-                EMD_CUDA(launch_topk(sl.dev.t_out, db->n, r->K, sl.dev.L.scratch, sl.dev.out_idx, sl.dev.out_dist,
-                                     sl.st), "top-K");
-            }
-        }
+        emd_status st = run_subbatch(db, e.ws, e.h_rp, e.d_idx, e.d_w, 0, 0, nb, e.meas, e.k, EMD_DIR_MAX, e.K,
+                                     e.pruned, nullptr, e.d_oidx, e.d_odist, e.st);
         if (st != EMD_OK) return st;
+        if (e.pruned) db->pruned_queries += nb;
     }
-    EMD_CUDA(cudaMemcpyAsync(sl.h_oidx, sl.dev.out_idx, (size_t)r->K * 8, cudaMemcpyDeviceToHost, sl.st), "result copy");
-    EMD_CUDA(cudaMemcpyAsync(sl.h_odist, sl.dev.out_dist, (size_t)r->K * 4, cudaMemcpyDeviceToHost, sl.st), "result copy");
-    if (r->pruned)
-        EMD_CUDA(cudaMemcpyAsync(sl.h_ok, sl.dev.ok, 4, cudaMemcpyDeviceToHost, sl.st), "flag copy");
-    EMD_CUDA(cudaEventRecord(sl.ev, sl.st), "event");
+    EMD_CUDA(cudaMemcpyAsync(e.h_oidx, e.d_oidx, (size_t)nb * e.K * 8, cudaMemcpyDeviceToHost, e.st), "result copy");
+    EMD_CUDA(cudaMemcpyAsync(e.h_odist, e.d_odist, (size_t)nb * e.K * 4, cudaMemcpyDeviceToHost, e.st),
+             "result copy");
+    if (e.pruned)
+        EMD_CUDA(cudaMemcpyAsync(e.h_ok, e.ws.cand_ok, (size_t)nb * 4, cudaMemcpyDeviceToHost, e.st), "flag copy");
+    EMD_CUDA(cudaEventRecord(e.done, e.st), "event");
     return EMD_OK;
 }
 
-// The unpruned recomputation of a request whose pruning certificate failed.
-emd_status launch_fallback(emd_server* s, Slot& sl)
+// Recomputes the batch's uncertified pruned requests over all documents (rare), in place in
+// the pinned results; *count receives how many.
+emd_status run_fallbacks(emd_server* s, Exec& e, int* count)
 {
     emd_db* db = s->db;
-    Request* r = sl.req;
-    {
-        std::lock_guard<std::mutex> lock(db->mu);
-        emd_status st = run_query(db, sl.dev.L, sl.dev.idx, sl.dev.w, r->h, r->meas, r->k, EMD_DIR_MAX,
-                                  sl.dev.t_out, sl.st);
-        if (st != EMD_OK) return st;
-        db->prune_fallbacks += 1;
-        db->launches[5] += topk_launch_count(db->n);
-        db->total_launches += topk_launch_count(db->n);
-        EMD_CUDA(launch_topk(sl.dev.t_out, db->n, r->K, sl.dev.L.scratch, sl.dev.out_idx, sl.dev.out_dist, sl.st),
-                 "top-K");
+    *count = 0;
+    if (!e.pruned) return EMD_OK;
+    for (size_t i = 0; i < e.batch.size(); ++i) {
+        if (e.h_ok[i]) continue;
+        const Request* r = e.batch[i];
+        const int64_t off = e.h_rp[i];
+        {
+            std::lock_guard<std::mutex> lock(db->mu);
+            emd_status st = run_query(db, s->fb, e.d_idx + off, e.d_w + off, r->h, r->meas, r->k, EMD_DIR_MAX,
+                                      s->fb_out, e.st);
+            if (st != EMD_OK) return st;
+            EMD_CUDA(launch_topk(s->fb_out, db->n, r->K, s->fb.scratch, e.d_oidx + i * r->K, e.d_odist + i * r->K,
+                                 e.st),
+                     "top-K");
+            db->prune_fallbacks += 1;
+        }
+        EMD_CUDA(cudaMemcpyAsync(e.h_oidx + i * r->K, e.d_oidx + i * r->K, (size_t)r->K * 8, cudaMemcpyDeviceToHost,
+                                 e.st),
+                 "result copy");
+        EMD_CUDA(cudaMemcpyAsync(e.h_odist + i * r->K, e.d_odist + i * r->K, (size_t)r->K * 4,
+                                 cudaMemcpyDeviceToHost, e.st),
+                 "result copy");
+        EMD_CUDA(cudaStreamSynchronize(e.st), "synchronize");
+        ++*count;
     }
-    EMD_CUDA(cudaMemcpyAsync(sl.h_oidx, sl.dev.out_idx, (size_t)r->K * 8, cudaMemcpyDeviceToHost, sl.st), "result copy");
-    EMD_CUDA(cudaMemcpyAsync(sl.h_odist, sl.dev.out_dist, (size_t)r->K * 4, cudaMemcpyDeviceToHost, sl.st), "result copy");
-    EMD_CUDA(cudaEventRecord(sl.ev, sl.st), "event");
     return EMD_OK;
+}
+
+// Takes the batch for executor e from the head of the queue: requests with the head's
+// (measure, k, K), in arrival order, while the executor's workspace and the in-flight limit
+// allow (caller holds s->mu).
+void form_batch(emd_server* s, Exec& e)
+{
+    const Request* head = s->queue.front();
+    e.meas = head->meas;
+    e.k = head->k;
+    e.K = head->K;
+    e.pruned = head->pruned;
+    std::vector<int64_t> rp(1, 0);
+    while (!s->queue.empty() && (int)e.batch.size() < e.ws.max_batch && s->in_flight < s->opt.max_inflight) {
+        Request* r = s->queue.front();
+        if (r->meas != e.meas || r->k != e.k || r->K != e.K) break;
+        rp.push_back(rp.back() + r->h);
+        if (!batch_fits(s->db, e.ws, rp.data(), 0, (int64_t)rp.size() - 1, e.meas, e.k, EMD_DIR_MAX)) break;
+        s->queue.pop_front();
+        r->state = RUNNING;
+        e.batch.push_back(r);
+        ++s->in_flight;
+    }
+    e.cols = 0;
+    for (const Request* r : e.batch) e.cols += round_up(r->h, 32);
+    e.busy = true;
+    s->max_running = std::max<int64_t>(s->max_running, s->in_flight);
+    s->pool_used_max = std::max<int64_t>(s->pool_used_max, e.cols * 4 * s->db->v_used);
 }
 
 void worker_main(emd_server* s)
@@ -294,64 +265,47 @@ void worker_main(emd_server* s)
     cudaSetDevice(s->db->dev);
     std::unique_lock<std::mutex> lk(s->mu);
     for (;;) {
-        // admit the head of the queue while a slot and workspace are free
-        while (!s->queue.empty() && !s->free_slots.empty()) {
-            Request* r = s->queue.front();
-            int64_t off = 0;
-            if (!s->alloc.alloc(r->ws_bytes, &off)) break;
-            s->queue.pop_front();
-            r->ws_off = off;
-            r->state = RUNNING;
-            const int si = s->free_slots.back();
-            s->free_slots.pop_back();
-            Slot& sl = s->slots[si];
-            sl.req = r;
-            sl.fallback = false;
-            ++s->running;
-            s->max_running = std::max<int64_t>(s->max_running, s->running);
-            s->pool_used_max = std::max(s->pool_used_max, s->alloc.used());
+        // launch batches on free executors
+        for (Exec& e : s->ex) {
+            if (e.busy || s->queue.empty() || s->in_flight >= s->opt.max_inflight) continue;
+            form_batch(s, e);
             lk.unlock();
-            emd_status st = launch(s, sl);
-            std::string why = st != EMD_OK ? emd_last_error() : "";
+            const emd_status st = launch_batch(s, e);
+            const std::string why = st != EMD_OK ? emd_last_error() : "";
             lk.lock();
             if (st != EMD_OK) {
-                cudaStreamSynchronize(sl.st);  // nothing of the request may still use its workspace
-                finish(s, sl, st, why.c_str());
+                cudaStreamSynchronize(e.st);
+                finish_batch(s, e, st, why.c_str());
             }
         }
-        if (s->running == 0) {
+        bool busy = false;
+        for (Exec& e : s->ex) busy |= e.busy;
+        if (!busy) {
             if (s->stop && s->queue.empty()) break;
             s->cv_work.wait(lk, [s] { return s->stop || !s->queue.empty(); });
             continue;
         }
         // completions
         bool progressed = false;
-        for (Slot& sl : s->slots) {
-            if (!sl.req) continue;
-            const cudaError_t e = cudaEventQuery(sl.ev);
-            if (e == cudaErrorNotReady) continue;
+        for (Exec& e : s->ex) {
+            if (!e.busy) continue;
+            const cudaError_t q = cudaEventQuery(e.done);
+            if (q == cudaErrorNotReady) continue;
             progressed = true;
-            if (e != cudaSuccess) {
-                finish(s, sl, EMD_ERR_CUDA, cudaGetErrorString(e));
+            if (q != cudaSuccess) {
+                finish_batch(s, e, EMD_ERR_CUDA, cudaGetErrorString(q));
                 continue;
             }
-            if (sl.req->pruned && !sl.fallback && !*sl.h_ok) {
-                sl.fallback = true;
-                ++s->fallbacks;
-                lk.unlock();
-                emd_status st = launch_fallback(s, sl);
-                std::string why = st != EMD_OK ? emd_last_error() : "";
-                lk.lock();
-                if (st != EMD_OK) {
-                    cudaStreamSynchronize(sl.st);
-                    finish(s, sl, st, why.c_str());
-                }
-                continue;
-            }
-            finish(s, sl, EMD_OK, nullptr);
+            lk.unlock();
+            int nfb = 0;
+            const emd_status st = run_fallbacks(s, e, &nfb);
+            const std::string why = st != EMD_OK ? emd_last_error() : "";
+            lk.lock();
+            s->fallbacks += nfb;
+            finish_batch(s, e, st, why.c_str());
         }
         if (!progressed) {
-            // requests in flight: poll again soon, admitting new arrivals in between
+            // batches in flight: poll again soon, admitting new arrivals in between
             lk.unlock();
             std::this_thread::yield();
             lk.lock();
@@ -375,14 +329,39 @@ emd_status check_bins(const emd_db* db, const int32_t* idx, const float* w, int 
     return EMD_OK;
 }
 
-void destroy_resources(emd_server* s)
+// Per-query workspace of the fallback lane (sizes as the handle's own lanes).
+emd_status alloc_lane(emd_server* s, Lane& L)
 {
-    for (Slot& sl : s->slots) {
-        if (sl.ev) cudaEventDestroy(sl.ev);
-        if (sl.st) cudaStreamDestroy(sl.st);
-        if (sl.pinned) cudaFreeHost(sl.pinned);
+    emd_db* db = s->db;
+    const int64_t npad = round_up(s->opt.max_query_h, 128);
+    const int64_t ldd = round_up(s->opt.max_query_h, 32);
+    const int64_t qrows = round_up(ldd, kDistBN);
+    emd_status st;
+#define TRYL(x)                               \
+    do {                                      \
+        if ((st = (x)) != EMD_OK) return st;  \
+    } while (0)
+    if (!db->cost_mode) {
+        TRYL(sdal(s, &L.Q, qrows * db->ldm));
+        TRYL(sdal(s, &L.qnorm, qrows));
+        if (db->tc) {
+            TRYL(sdal(s, &L.q_hi, npad * db->kpad));
+            if (db->tcfmt == TC_SPLIT) TRYL(sdal(s, &L.q_lo, npad * db->kpad));
+            TRYL(sdal(s, &L.q_scale, npad));
+        }
     }
-    if (s->pool) cudaFree(s->pool);
+    TRYL(sdal(s, &L.D, db->v_used * ldd));
+    TRYL(sdal(s, &L.tab, db->v_used * db->opt.max_table_k));
+    TRYL(sdal(s, &L.t_fwd, db->n));
+    TRYL(sdal(s, &L.t_rev, db->n));
+    TRYL(sdal(s, &L.sel_idx, kPruneMaxK));
+    TRYL(sdal(s, &L.sel_val, kPruneMaxK));
+    TRYL(sdal(s, &L.cand_idx, kPruneCap));
+    TRYL(sdal(s, &L.cand_sym, 2 * kPruneCap));
+    TRYL(sdal(s, &L.cand_count, 1));
+    TRYL(sdal(s, &L.scratch, kTopkScratchRow));
+#undef TRYL
+    return EMD_OK;
 }
 
 }  // namespace
@@ -392,7 +371,7 @@ extern "C" {
 void emd_server_options_default(emd_server_options* opt)
 {
     if (!opt) return;
-    opt->max_inflight = 8;
+    opt->max_inflight = 128;
     opt->queue_capacity = 4096;
     opt->workspace_bytes = 0;
     opt->max_query_h = 0;
@@ -406,53 +385,66 @@ emd_status emd_server_create(emd_db* db, const emd_server_options* opt_in, emd_s
     emd_server_options opt;
     emd_server_options_default(&opt);
     if (opt_in) opt = *opt_in;
-    if (opt.max_inflight < 1 || opt.max_inflight > 64) return fail(EMD_ERR_INVALID_ARG, "max_inflight must be 1..64");
+    if (opt.max_inflight < 1) return fail(EMD_ERR_INVALID_ARG, "max_inflight must be >= 1");
     if (opt.queue_capacity < 1) return fail(EMD_ERR_INVALID_ARG, "queue_capacity must be >= 1");
     if (opt.workspace_bytes < 0) return fail(EMD_ERR_INVALID_ARG, "workspace_bytes < 0");
     if (opt.max_query_h == 0) opt.max_query_h = db->opt.max_query_h;
     if (opt.max_query_h < 1 || opt.max_query_h > db->opt.max_query_h)
         return fail(EMD_ERR_INVALID_ARG, "max_query_h must be 1..%d (the database's limit)", db->opt.max_query_h);
+    // distance-matrix columns per executor: the pool split in two, at least one request
+    const int64_t col_bytes = 4 * db->v_used;
+    const int64_t min_cols = round_up(opt.max_query_h, 32);
+    const int64_t cols = opt.workspace_bytes > 0 ? (opt.workspace_bytes / kExecs) / col_bytes / 32 * 32
+                                                 : std::max<int64_t>(db->opt.batch_columns, min_cols);
+    if (cols < min_cols)
+        return fail(EMD_ERR_INVALID_ARG, "workspace_bytes too small: %lld bytes hold less than one request of %d bins",
+                    (long long)opt.workspace_bytes, opt.max_query_h);
     EMD_CUDA(cudaSetDevice(db->dev), "cudaSetDevice");
     auto s = std::make_unique<emd_server>();
     s->db = db;
     s->opt = opt;
-    const int tk_max = std::min(db->opt.max_table_k, opt.max_query_h);
-    const int64_t per_req = layout(db, opt.max_query_h, tk_max, nullptr, nullptr);
-    int64_t bytes = opt.workspace_bytes;
-    if (bytes == 0) {
-        size_t fr = 0, tot = 0;
-        EMD_CUDA(cudaMemGetInfo(&fr, &tot), "memory info");
-        bytes = std::min<int64_t>(per_req * opt.max_inflight, (int64_t)(fr / 2));
-    }
-    bytes = bytes / kAlign * kAlign;
-    if (bytes < kAlign) return fail(EMD_ERR_INVALID_ARG, "workspace pool too small");
-    cudaError_t e = cudaMalloc(&s->pool, (size_t)bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(EMD_ERR_OUT_OF_MEMORY, "workspace pool of %lld bytes: %s", (long long)bytes, cudaGetErrorString(e));
-    }
-    s->pool_bytes = bytes;
-    s->alloc.reset(bytes);
-    s->slots.resize((size_t)opt.max_inflight);
-    const size_t hbytes = align_up((int64_t)opt.max_query_h * 4) * 2 + kMaxTopK * 8 + kMaxTopK * 4 + 64;
-    for (size_t i = 0; i < s->slots.size(); ++i) {
-        Slot& sl = s->slots[i];
-        e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl.pinned, hbytes, cudaHostAllocDefault);
-        if (e != cudaSuccess) {
+    const int mb = std::min(db->opt.max_batch, opt.max_inflight);
+    emd_status st = EMD_OK;
+    for (Exec& e : s->ex) {
+        int64_t wsb = 0;
+        st = alloc_batch_ws(db, e.ws, mb, cols, s->allocs, &wsb);
+        s->bytes += wsb;
+        s->pool_bytes += e.ws.b_cols * col_bytes;
+        if (st == EMD_OK) st = sdal(s.get(), &e.d_idx, e.ws.b_cols);
+        if (st == EMD_OK) st = sdal(s.get(), &e.d_w, e.ws.b_cols);
+        if (st == EMD_OK) st = sdal(s.get(), &e.d_oidx, (int64_t)mb * kMaxTopK);
+        if (st == EMD_OK) st = sdal(s.get(), &e.d_odist, (int64_t)mb * kMaxTopK);
+        cudaError_t ce = cudaSuccess;
+        const int64_t hb = align256(8 * ((int64_t)mb + 1)) + 2 * align256(4 * e.ws.b_cols) +
+                           align256(8 * (int64_t)mb * kMaxTopK) + align256(4 * (int64_t)mb * kMaxTopK) +
+                           align256(4 * (int64_t)mb);
+        if (st == EMD_OK) ce = cudaStreamCreateWithFlags(&e.st, cudaStreamNonBlocking);
+        if (st == EMD_OK && ce == cudaSuccess) ce = cudaEventCreateWithFlags(&e.done, cudaEventDisableTiming);
+        if (st == EMD_OK && ce == cudaSuccess) ce = cudaHostAlloc((void**)&e.pinned, (size_t)hb, cudaHostAllocDefault);
+        if (st == EMD_OK && ce != cudaSuccess) {
             cudaGetLastError();
-            destroy_resources(s.get());
-            return fail(e == cudaErrorMemoryAllocation ? EMD_ERR_OUT_OF_MEMORY : EMD_ERR_CUDA, "server slot: %s",
-                        cudaGetErrorString(e));
+            st = fail(EMD_ERR_OUT_OF_MEMORY, "server executor: %s", cudaGetErrorString(ce));
         }
-        const int64_t hb = align_up((int64_t)opt.max_query_h * 4);
-        sl.h_idx = reinterpret_cast<int32_t*>(sl.pinned);
-        sl.h_w = reinterpret_cast<float*>(sl.pinned + hb);
-        sl.h_oidx = reinterpret_cast<int64_t*>(sl.pinned + 2 * hb);
-        sl.h_odist = reinterpret_cast<float*>(sl.pinned + 2 * hb + kMaxTopK * 8);
-        sl.h_ok = reinterpret_cast<int*>(sl.pinned + 2 * hb + kMaxTopK * 12);
-        s->free_slots.push_back((int)(s->slots.size() - 1 - i));
+        if (st != EMD_OK) {
+            destroy_resources(s.get());
+            return st;
+        }
+        char* p = e.pinned;
+        e.h_rp = reinterpret_cast<int64_t*>(p);
+        p += align256(8 * ((int64_t)mb + 1));
+        e.h_idx = reinterpret_cast<int32_t*>(p);
+        p += align256(4 * e.ws.b_cols);
+        e.h_w = reinterpret_cast<float*>(p);
+        p += align256(4 * e.ws.b_cols);
+        e.h_oidx = reinterpret_cast<int64_t*>(p);
+        p += align256(8 * (int64_t)mb * kMaxTopK);
+        e.h_odist = reinterpret_cast<float*>(p);
+        p += align256(4 * (int64_t)mb * kMaxTopK);
+        e.h_ok = reinterpret_cast<int*>(p);
+    }
+    if ((st = alloc_lane(s.get(), s->fb)) != EMD_OK || (st = sdal(s.get(), &s->fb_out, db->n)) != EMD_OK) {
+        destroy_resources(s.get());
+        return st;
     }
     db->servers.fetch_add(1);
     emd_server* raw = s.release();
@@ -477,6 +469,9 @@ emd_status emd_server_submit(emd_server* s, const int32_t* idx, const float* w, 
         return fail(EMD_ERR_UNSUPPORTED, "forward table width %d exceeds max_table_k %d", tk, db->opt.max_table_k);
     if (db->approx && rerank_width(db, tk, h_q) > kRerankMax)
         return fail(EMD_ERR_UNSUPPORTED, "re-rank width %d exceeds %d", rerank_width(db, tk, h_q), kRerankMax);
+    const int64_t one[2] = {0, h_q};
+    if (!batch_fits(db, s->ex[0].ws, one, 0, 1, meas, k, EMD_DIR_MAX))
+        return fail(EMD_ERR_INVALID_ARG, "the request does not fit an executor's workspace");
     emd_status st = check_bins(db, idx, w, h_q);
     if (st != EMD_OK) return st;
     auto r = std::make_unique<Request>();
@@ -487,10 +482,6 @@ emd_status emd_server_submit(emd_server* s, const int32_t* idx, const float* w, 
     r->pruned = prunable(db, meas, k, EMD_DIR_MAX, K);
     r->idx.assign(idx, idx + h_q);
     r->w.assign(w, w + h_q);
-    r->ws_bytes = layout(db, h_q, tk, nullptr, nullptr);
-    if (r->ws_bytes > s->pool_bytes)
-        return fail(EMD_ERR_INVALID_ARG, "request needs %lld bytes of workspace, the pool has %lld",
-                    (long long)r->ws_bytes, (long long)s->pool_bytes);
     {
         std::lock_guard<std::mutex> lock(s->mu);
         if (s->stop) return fail(EMD_ERR_SHUTDOWN, "server is shutting down");
@@ -551,7 +542,7 @@ emd_status emd_server_stats_get(emd_server* s, emd_server_stats* out)
         out->failed = s->failed;
         out->prune_fallbacks = s->fallbacks;
         out->queued = (int64_t)s->queue.size();
-        out->in_flight = s->running;
+        out->in_flight = s->in_flight;
         out->max_in_flight = s->max_running;
         out->pool_bytes = s->pool_bytes;
         out->pool_used_max = s->pool_used_max;
@@ -576,8 +567,8 @@ emd_status emd_server_stats_reset(emd_server* s)
     if (!s) return fail(EMD_ERR_INVALID_ARG, "NULL argument");
     std::lock_guard<std::mutex> lock(s->mu);
     s->submitted = s->completed = s->rejected = s->failed = s->fallbacks = 0;
-    s->max_running = s->running;
-    s->pool_used_max = s->alloc.used();
+    s->max_running = s->in_flight;
+    s->pool_used_max = 0;
     s->have_first = false;
     s->lat_us.clear();
     return EMD_OK;
@@ -594,8 +585,8 @@ emd_status emd_server_destroy(emd_server* s)
     s->cv_work.notify_all();
     if (s->worker.joinable()) s->worker.join();
     cudaSetDevice(s->db->dev);
-    for (Slot& sl : s->slots)
-        if (sl.st) cudaStreamSynchronize(sl.st);
+    for (Exec& e : s->ex)
+        if (e.st) cudaStreamSynchronize(e.st);
     destroy_resources(s);
     s->db->servers.fetch_sub(1);
     delete s;

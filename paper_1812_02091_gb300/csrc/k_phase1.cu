@@ -338,12 +338,12 @@ __device__ __forceinline__ void insert_dj_tie(float (&z)[KCT], int (&s)[KCT], fl
 template <int KCT>
 __device__ __forceinline__ void table_rerank_body(float* __restrict__ D, int ldd, int64_t M, int h, int k, int kc, const float* __restrict__ V,
                const float* __restrict__ Q, int ldv, const float* __restrict__ q_w, float2* __restrict__ tab,
-               int32_t* __restrict__ tab_s)
+               int32_t* __restrict__ tab_s, int64_t tile)
 {
     __shared__ int cj[128][KCT + 1];
     __shared__ float cz[128][KCT + 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t row = (int64_t)blockIdx.x * 128 + tid;
+    const int64_t row = tile * 128 + tid;
     {
         float z[KCT];
         int s[KCT];
@@ -365,7 +365,7 @@ __device__ __forceinline__ void table_rerank_body(float* __restrict__ D, int ldd
     __syncwarp();
     const int nv4 = ldv >> 2;
     for (int r = 0; r < 32; ++r) {
-        const int64_t ur = (int64_t)blockIdx.x * 128 + warp * 32 + r;
+        const int64_t ur = tile * 128 + warp * 32 + r;
         if (ur >= M) break;  // uniform over the warp
         const float4* vr = reinterpret_cast<const float4*>(V + ur * ldv);
         for (int c = 0; c < kc; ++c) {
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(128) k_table_rerank(float* __restrict__ D, int
                const float* __restrict__ Q, int ldv, const float* __restrict__ q_w, float2* __restrict__ tab,
                int32_t* __restrict__ tab_s)
 {
-    table_rerank_body<KCT>(D, ldd, M, h, k, kc, V, Q, ldv, q_w, tab, tab_s);
+    table_rerank_body<KCT>(D, ldd, M, h, k, kc, V, Q, ldv, q_w, tab, tab_s, blockIdx.x);
 }
 
 // ------------------------------------------------------------------ batched forms
@@ -459,14 +459,16 @@ __global__ void k_table_generic_b(const QDesc* __restrict__ qd, const int* __res
     table_generic_body(d.D, d.ldd, M, d.h, d.tk, d.qw, d.tab, nullptr);
 }
 
+// Queries vary fastest (blockIdx.x) so that the blocks of one vocabulary tile for all
+// queries of the batch run together and its FP32 rows are read from HBM once.
 template <int KCT>
 __global__ void __launch_bounds__(128)
 k_table_rerank_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t M, const float* __restrict__ V,
                  int ldv)
 {
-    if ((int)blockIdx.y >= *nq) return;
-    const QDesc& d = qd[blockIdx.y];
-    table_rerank_body<KCT>(d.D, d.ldd, M, d.h, d.tk, d.kc, V, d.Q, ldv, d.qw, d.tab, nullptr);
+    if ((int)blockIdx.x >= *nq) return;
+    const QDesc& d = qd[blockIdx.x];
+    table_rerank_body<KCT>(d.D, d.ldd, M, d.h, d.tk, d.kc, V, d.Q, ldv, d.qw, d.tab, nullptr, blockIdx.y);
 }
 
 }  // namespace
@@ -574,10 +576,11 @@ cudaError_t launch_table_b(const QDesc* qd, const int* nq, int max_q, int64_t M,
     if (max_q <= 0 || M <= 0) return cudaSuccess;
     const dim3 g((unsigned)((M + 127) / 128), (unsigned)max_q);
     if (rerank) {
-        if (max_kc > kRerankMax) return cudaErrorInvalidValue;
-        if (max_kc <= 8) k_table_rerank_b<8><<<g, 128, 0, st>>>(qd, nq, M, V, ldv);
-        else if (max_kc <= 16) k_table_rerank_b<16><<<g, 128, 0, st>>>(qd, nq, M, V, ldv);
-        else k_table_rerank_b<32><<<g, 128, 0, st>>>(qd, nq, M, V, ldv);
+        if (max_kc > kRerankMax || (M + 127) / 128 > 65535) return cudaErrorInvalidValue;
+        const dim3 gq((unsigned)max_q, (unsigned)((M + 127) / 128));
+        if (max_kc <= 8) k_table_rerank_b<8><<<gq, 128, 0, st>>>(qd, nq, M, V, ldv);
+        else if (max_kc <= 16) k_table_rerank_b<16><<<gq, 128, 0, st>>>(qd, nq, M, V, ldv);
+        else k_table_rerank_b<32><<<gq, 128, 0, st>>>(qd, nq, M, V, ldv);
     } else if (max_tk <= 1) k_table_b<1><<<g, 128, 0, st>>>(qd, nq, M);
     else if (max_tk <= 2) k_table_b<2><<<g, 128, 0, st>>>(qd, nq, M);
     else if (max_tk <= 4) k_table_b<4><<<g, 128, 0, st>>>(qd, nq, M);

@@ -105,14 +105,16 @@ def test_server_matches_oracle(emd, work):
 
 
 def test_admission_by_workspace(emd, work):
-    """A pool that holds about two of the largest requests: everything completes, and the
-    workspace in use never exceeds the pool."""
+    """Executors of 512 distance-matrix columns each (a few requests of the workload): every
+    batch stays within its executor's columns, everything completes bit-identical to
+    emd_topk, and a pool too small for one request is refused."""
     w = work
     db = make_db(emd, w, precision="fp32_tc", max_query_h=256)
-    probe = emd.emd_server_create(db, emd.emd_server_options_default(max_inflight=1, max_query_h=256))
-    one = emd.emd_server_stats_get(probe)["pool_bytes"]  # one request of h = 256
-    emd.emd_server_destroy(probe)
-    srv = emd.emd_server_create(db, emd.emd_server_options_default(max_inflight=16, workspace_bytes=2 * one + 4096))
+    vu = emd.emd_db_info_get(db)["v_used"]
+    col = 4 * vu
+    with pytest.raises(emd.EmdError, match="INVALID_ARG"):
+        emd.emd_server_create(db, emd.emd_server_options_default(workspace_bytes=2 * 128 * col))
+    srv = emd.emd_server_create(db, emd.emd_server_options_default(workspace_bytes=2 * 512 * col))
     try:
         ids = list(range(w.queries.n))
         got = serve_all(emd, srv, w, ids, "act", 4, 16)
@@ -121,7 +123,8 @@ def test_admission_by_workspace(emd, work):
             assert np.array_equal(got[i][0], ti[i]) and np.array_equal(got[i][1], td[i])
         st = emd.emd_server_stats_get(srv)
         assert st["completed"] == len(ids) and st["failed"] == 0
-        assert st["pool_used_max"] <= st["pool_bytes"]
+        assert st["pool_bytes"] == 2 * 512 * col
+        assert 0 < st["pool_used_max"] <= 512 * col
         assert st["max_in_flight"] >= 2
     finally:
         emd.emd_server_destroy(srv)
