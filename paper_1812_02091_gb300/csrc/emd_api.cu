@@ -780,11 +780,11 @@ emd_status host_batches(emd_db* db, const emd_queries* q, int meas, int k, int d
 
 // Picks the batched kernels' free parameters (query groups per vocabulary tile and B
 // stages of the tensor-core Phase 1, warps per candidate in the pruned reverse pass) by
-// timing them on a synthetic batch: queries of up to 128 consecutive used vocabulary rows,
-// uniform weights.  Every choice gives bit-identical results; only the time differs.
+// timing them on a synthetic batch of max_batch queries of up to 128 consecutive used
+// vocabulary rows, uniform weights.  Every choice gives bit-identical results; only the time differs.
 emd_status autotune(emd_db* db, const std::vector<int32_t>& used_host)
 {
-    const int nb = std::min(db->opt.max_batch, 32);
+    const int nb = db->opt.max_batch;
     const int h = (int)std::min<int64_t>(std::min<int64_t>(128, db->opt.max_query_h), db->v_used);
     const int k = std::min(4, db->opt.max_table_k);
     const int K = (int)std::min<int64_t>(16, db->n);
@@ -832,9 +832,12 @@ emd_status autotune(emd_db* db, const std::vector<int32_t>& used_host)
         // on short launches would otherwise pick at random)
         const int fit = tc_batch_stages(db->tcfmt, db->kpad / 64);
         float best = 1e30f;
+        std::vector<int> stage_set;
+        for (int sg : {fit, (fit + 2) / 2, 2})
+            if (sg >= 2 && sg <= fit && std::find(stage_set.begin(), stage_set.end(), sg) == stage_set.end())
+                stage_set.push_back(sg);
         for (int gm : {1, 2, 4})
-            for (int sg : {fit, (fit + 2) / 2, 2}) {
-                if (sg < 2 || sg > fit) continue;
+            for (int sg : stage_set) {
                 const float ms = timed([&] {
                     launch_tc_dist_batch(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
                                          db->used_ids, db->v_used, D_, nqd, db->opt.max_batch, db->kpad, gm, sg,
