@@ -313,6 +313,10 @@ def main():
     ap.add_argument("--probe", action="store_true",
                     help="small fixed case for profiler captures: the bench workload's database, --batch "
                          "queries per batch (16 suggested), --warmup + --steps batches, ~1.5 GB on the device")
+    ap.add_argument("--k4", action="store_true",
+                    help="forward sparse pass alone on the serving-size database (workload 5, cut to --k4-docs "
+                         "documents), against the HBM roofline; prints one line")
+    ap.add_argument("--k4-docs", type=int, default=300000)
     ap.add_argument("--precision-steps", type=int, default=5,
                     help="batches per arithmetic in the precision comparison; 0: skip it")
     args = ap.parse_args()
@@ -325,6 +329,8 @@ def main():
         return main_reference(args, rank, world)
     if args.probe:
         return main_probe(args, local)
+    if args.k4:
+        return main_k4(args, local)
 
     import torch
     import paper_1812_02091_gb300 as emd
@@ -622,6 +628,54 @@ def main_probe(args, local):
     print(json.dumps({"probe": "pruned top-K batches of queries with h_q <= 128", "batch": B,
                       "precision": args.precision,
                       "ms_per_batch": [round(1e3 * t, 3) for t in times]}))
+
+
+def main_k4(args, local):
+    """The forward CSR pass (Phase 2+3) on a database much larger than L2: per query sweep
+    8 nnz + 4 (n + 1) + 4 n algorithmic bytes, timed with the library's events over batches of
+    --batch queries (forward direction only, all documents), L2 flushed between batches."""
+    import torch
+    import emd_synth
+    import paper_1812_02091_gb300 as emd
+    torch.cuda.set_device(local)
+    t0 = time.perf_counter()
+    w = emd_synth.config(5, query_limit=args.batch * (args.steps + args.warmup), n_docs=args.k4_docs)
+    gen_s = time.perf_counter() - t0
+    B = args.batch
+    db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
+                           emd.emd_db_options_default(precision=args.precision, device=local, max_query_h=2048,
+                                                      max_batch=B, batch_columns=2048))
+    info = emd.emd_db_info_get(db)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    out = torch.empty((B, w.db.n), dtype=torch.float32, device="cuda")
+    batches = []
+    for s in range(args.warmup + args.steps):
+        sub = w.queries.subset(np.arange(s * B, (s + 1) * B))
+        batches.append((sub.row_ptr, torch.from_numpy(sub.col).cuda(), torch.from_numpy(sub.val).cuda()))
+    for s in range(args.warmup):
+        emd.emd_query_batch_device(db, *batches[s], out, "act", args.k, "fwd", stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    emd.emd_db_profile_reset(db)
+    emd.emd_db_set_profiling(db, True)
+    for s in range(args.warmup, args.warmup + args.steps):
+        flush.fill_(float(s))
+        emd.emd_query_batch_device(db, *batches[s], out, "act", args.k, "fwd", stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    prof = emd.emd_db_profile_get(db)
+    emd.emd_db_destroy(db)
+    nnz, n = info["nnz"], info["n_docs"]
+    sweep = 8.0 * nnz + 4.0 * (n + 1) + 4.0 * n
+    t = prof["ms"]["fwd"] / 1e3
+    achieved = sweep * B * args.steps / t / 1e9
+    pk = peaks()
+    print(json.dumps({"k4": "forward CSR pass (Eq. 6-9), LC-ACT k=%d" % args.k,
+                      "database": f"workload 5 cut to {n} documents: nnz {nnz}, CSR {sweep / 1e6:.0f} MB per sweep, "
+                                  f"v_used {info['v_used']}",
+                      "queries": B * args.steps, "launches": prof["launches"]["fwd"],
+                      "ms_per_query": 1e3 * t / (B * args.steps), "achieved_gbs": achieved,
+                      "peak_gbs": pk["hbm_gbs"], "frac": achieved / pk["hbm_gbs"],
+                      "peak_source": f"{pk['source']} HBM copy", "generation_s": gen_s}))
 
 
 def main_reference(args, rank, world):

@@ -373,7 +373,8 @@ emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, i
                      "top-k table");
         }
         Phase p(db, 3, 1, st);
-        EMD_CUDA(launch_fwd_b(meas, D_, nqd, B, db->row_ptr, db->col, db->val, n, dir == EMD_DIR_FWD, st),
+        EMD_CUDA(launch_fwd_b(meas, D_, nqd, B, db->row_ptr, db->col, db->val, n, dir == EMD_DIR_FWD,
+                              tk_b > 0 && tk_b <= 16, st),
                  "forward pass");
     }
     if (pruned) {
@@ -458,7 +459,7 @@ emd_status alloc_batch_ws(emd_db* db, BatchWS& ws, int max_batch, int64_t cols, 
     ws.b_cols = std::max<int64_t>(round_up(cols, 32), round_up(db->opt.max_query_h, 32));
     ws.b_qrows = ws.b_cols + 32 * B;
     ws.b_prows = ws.b_cols + 96 * B;
-    ws.b_tabcols = std::max<int64_t>(db->opt.max_table_k, 16 * B);
+    ws.b_tabcols = std::max<int64_t>(db->opt.max_table_k, 16 * round_up(B, kFwdGroup));  // whole interleaved groups
     TRYW(dal(&ws.bD, vu * ws.b_cols));
     if (!db->cost_mode) {
         TRYW(dal(&ws.bQ, ws.b_qrows * db->ldm));
@@ -512,6 +513,8 @@ emd_status fill_descriptors(BatchWS& ws, int slot, emd_db* db, const int64_t* rp
                         int64_t* out_idx, float* out_dist, cudaStream_t st)
 {
     const int nb = (int)(j1 - j0);
+    const int tk_b = dir != EMD_DIR_REV ? table_width(meas, k, db->opt.max_query_h) : 0;
+    const bool grouped = tk_b > 0 && tk_b <= 16;
     QDesc* hd = ws.qd_host + (int64_t)slot * ws.max_batch;
     QDesc* dd = ws.qd_dev + (int64_t)slot * ws.max_batch;
     int* nqd = ws.nq_dev + slot;
@@ -541,7 +544,16 @@ emd_status fill_descriptors(BatchWS& ws, int slot, emd_db* db, const int64_t* rp
             }
         }
         d.D = ws.bD + c_D * db->v_used;
-        d.tab = ws.btab + c_T * db->v_used;
+        if (grouped) {
+            const int64_t bs = i - j0;  // position in the sub-batch: group bs / kFwdGroup
+            d.tab = ws.btab + (bs / kFwdGroup) * (db->v_used * tk_b * kFwdGroup) + bs % kFwdGroup;
+            d.tab_rs = tk_b * kFwdGroup;
+            d.tab_es = kFwdGroup;
+        } else {
+            d.tab = ws.btab + c_T * db->v_used;
+            d.tab_rs = d.tk;
+            d.tab_es = 1;
+        }
         d.t_fwd = ws.bt_fwd + (int64_t)b * n;
         d.t_rev = ws.bt_rev + (int64_t)b * n;
         d.t_out = (K > 0 ? ws.bt_out : out_t) + (int64_t)b * n;
@@ -567,6 +579,10 @@ emd_status fill_descriptors(BatchWS& ws, int slot, emd_db* db, const int64_t* rp
         max_tk = std::max(max_tk, d.tk);
         max_kc = std::max(max_kc, d.kc);
     }
+    // the caller sizes sub-batches with batch_fits; never let one overrun the workspace
+    const int64_t tab_used = grouped ? (int64_t)(nb + kFwdGroup - 1) / kFwdGroup * kFwdGroup * tk_b : c_T;
+    if (nb > ws.max_batch || c_D > ws.b_cols || c_Q > ws.b_qrows || c_P > ws.b_prows || tab_used > ws.b_tabcols)
+        return fail(EMD_ERR_INVALID_ARG, "internal: sub-batch of %d queries exceeds the batch workspace", nb);
     ws.nq_host[slot] = nb;
     EMD_CUDA(cudaMemcpyAsync(dd, hd, sizeof(QDesc) * nb, cudaMemcpyHostToDevice, st), "descriptor upload");
     EMD_CUDA(cudaMemcpyAsync(nqd, ws.nq_host + slot, sizeof(int), cudaMemcpyHostToDevice, st), "descriptor upload");
@@ -627,6 +643,8 @@ bool batch_fits(const emd_db* db, const BatchWS& ws, const int64_t* rp, int64_t 
 {
     int64_t cD = 0, cQ = 0, cP = 0, cT = 0;
     if (i1 - i0 > ws.max_batch) return false;
+    const int tk_b = dir != EMD_DIR_REV ? table_width(meas, k, db->opt.max_query_h) : 0;
+    const bool grouped = tk_b > 0 && tk_b <= 16;
     for (int64_t i = i0; i < i1; ++i) {
         const int h = (int)(rp[i + 1] - rp[i]);
         const int64_t ldd = round_up(h, 32);
@@ -635,7 +653,7 @@ bool batch_fits(const emd_db* db, const BatchWS& ws, const int64_t* rp, int64_t 
         cP += round_up(h, 128);
         cT += dir != EMD_DIR_REV ? table_width(meas, k, h) : 0;
     }
-    (void)db;
+    if (grouped) cT = (i1 - i0 + kFwdGroup - 1) / kFwdGroup * kFwdGroup * tk_b;  // interleaved groups
     return cD <= ws.b_cols && cQ <= ws.b_qrows && cP <= ws.b_prows && cT <= ws.b_tabcols;
 }
 
@@ -784,14 +802,16 @@ emd_status host_batches(emd_db* db, const emd_queries* q, int meas, int k, int d
 // vocabulary rows, uniform weights.  Every choice gives bit-identical results; only the time differs.
 emd_status autotune(emd_db* db, const std::vector<int32_t>& used_host)
 {
-    const int nb = db->opt.max_batch;
     const int h = (int)std::min<int64_t>(std::min<int64_t>(128, db->opt.max_query_h), db->v_used);
     const int k = std::min(4, db->opt.max_table_k);
     const int K = (int)std::min<int64_t>(16, db->n);
-    std::vector<int64_t> rp((size_t)nb + 1);
+    // as many queries as one sub-batch of the workspace holds, at most max_batch
+    std::vector<int64_t> rp((size_t)db->opt.max_batch + 1);
+    for (size_t i = 0; i < rp.size(); ++i) rp[i] = (int64_t)i * h;
+    int nb = 1;
+    while (nb < db->opt.max_batch && batch_fits(db, db->bw, rp.data(), 0, nb + 1, EMD_ACT, k, EMD_DIR_MAX)) ++nb;
     std::vector<int32_t> idx((size_t)nb * h);
     std::vector<float> w((size_t)nb * h, 1.0f / (float)h);
-    for (int i = 0; i <= nb; ++i) rp[(size_t)i] = (int64_t)i * h;
     for (int i = 0; i < nb; ++i) {
         const int64_t start = (int64_t)i * (db->v_used / nb);
         for (int j = 0; j < h; ++j) idx[(size_t)i * h + j] = used_host[(size_t)((start + j) % db->v_used)];

@@ -168,7 +168,14 @@ struct QDesc {
     int64_t* out_idx;       // K top-K result
     float* out_dist;
     int h, ldd, qrows, npad, tk, kc;
+    int tab_rs, tab_es;     // table layout: entry l of row u at tab[u * tab_rs + l * tab_es]
 };
+
+// Queries whose forward pass shares one sweep of the CSR (batched form, table width <= 16).
+// Their tables are interleaved by entry -- row u, entry l, query g at
+// base[(u * width + l) * kFwdGroup + g] -- so that one L2 sector holds the first entries of
+// four of them.
+constexpr int kFwdGroup = 8;
 
 cudaError_t launch_gather_rows_b(const QDesc* qd, const int* nq, int max_q, int max_rows, const float* src,
                                  int64_t v, int ld, int m, int* err, cudaStream_t st);
@@ -194,9 +201,10 @@ cudaError_t launch_tc_dist_batch(int fmt, const void* A_hi, const void* A_lo, in
 // (V: the used vocabulary rows, ldv floats each).
 cudaError_t launch_table_b(const QDesc* qd, const int* nq, int max_q, int64_t M, int max_tk, bool rerank,
                            int max_kc, const float* V, int ldv, cudaStream_t st);
-// Forward values into t_out (to_out) or t_fwd.
+// Forward values into t_out (to_out) or t_fwd.  grouped: the tables are interleaved in
+// groups of kFwdGroup queries and each group shares one sweep of the CSR.
 cudaError_t launch_fwd_b(int meas, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
-                         const int32_t* col, const float* val, int64_t n, bool to_out, cudaStream_t st);
+                         const int32_t* col, const float* val, int64_t n, bool to_out, bool grouped, cudaStream_t st);
 // Reverse pass over all documents; dir FWD is not accepted, REV writes t_out, MAX writes
 // t_rev and max(t_fwd, t_rev) into t_out.
 cudaError_t launch_rev_b(int meas, int k, int dir, const QDesc* qd, const int* nq, int max_q,

@@ -237,7 +237,7 @@ __device__ __forceinline__ void insert_dj(float (&z)[KT], int (&s)[KT], float d,
 
 template <int KT>
 __device__ __forceinline__ void table_body(const float* __restrict__ D, int ldd, int64_t M, int h, int k, const float* __restrict__ q_w,
-        float2* __restrict__ tab, int32_t* __restrict__ tab_s)
+        float2* __restrict__ tab, int32_t* __restrict__ tab_s, int rs, int es)
 {
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= M) return;
@@ -257,7 +257,7 @@ __device__ __forceinline__ void table_body(const float* __restrict__ D, int ldd,
     for (int l = 0; l < KT; ++l) {
         if (l < k) {
             const bool valid = s[l] != INT32_MAX;
-            tab[row * k + l] = make_float2(valid ? z[l] : INFINITY, valid ? q_w[s[l]] : 0.f);
+            tab[row * rs + l * es] = make_float2(valid ? z[l] : INFINITY, valid ? q_w[s[l]] : 0.f);
             if (tab_s) tab_s[row * k + l] = valid ? s[l] : -1;
         }
     }
@@ -267,14 +267,14 @@ template <int KT>
 __global__ void __launch_bounds__(128) k_table(const float* __restrict__ D, int ldd, int64_t M, int h, int k, const float* __restrict__ q_w,
         float2* __restrict__ tab, int32_t* __restrict__ tab_s)
 {
-    table_body<KT>(D, ldd, M, h, k, q_w, tab, tab_s);
+    table_body<KT>(D, ldd, M, h, k, q_w, tab, tab_s, k, 1);
 }
 
 // k larger than the register lists: successive minima, each strictly after the previous
 // in (d, j) order.  O(k * h / 32) per lane; used for ICT on small queries.
 __device__ __forceinline__ void table_generic_body(const float* __restrict__ D, int ldd, int64_t M, int h, int k,
                                 const float* __restrict__ q_w, float2* __restrict__ tab,
-                                int32_t* __restrict__ tab_s)
+                                int32_t* __restrict__ tab_s, int rs, int es)
 {
     const int lane = threadIdx.x & 31;
     const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -298,7 +298,7 @@ __device__ __forceinline__ void table_generic_body(const float* __restrict__ D, 
         }
         if (lane == 0) {
             const bool valid = bs != INT32_MAX;
-            tab[row * k + l] = make_float2(valid ? bz : INFINITY, valid ? q_w[bs] : 0.f);
+            tab[row * rs + l * es] = make_float2(valid ? bz : INFINITY, valid ? q_w[bs] : 0.f);
             if (tab_s) tab_s[row * k + l] = valid ? bs : -1;
         }
         pz = bz;
@@ -310,7 +310,7 @@ __global__ void k_table_generic(const float* __restrict__ D, int ldd, int64_t M,
                                 const float* __restrict__ q_w, float2* __restrict__ tab,
                                 int32_t* __restrict__ tab_s)
 {
-    table_generic_body(D, ldd, M, h, k, q_w, tab, tab_s);
+    table_generic_body(D, ldd, M, h, k, q_w, tab, tab_s, k, 1);
 }
 
 // Re-rank form of the table, for approximate distance matrices (BF16 / E4M3 Phase 1).
@@ -338,7 +338,7 @@ __device__ __forceinline__ void insert_dj_tie(float (&z)[KCT], int (&s)[KCT], fl
 template <int KCT>
 __device__ __forceinline__ void table_rerank_body(float* __restrict__ D, int ldd, int64_t M, int h, int k, int kc, const float* __restrict__ V,
                const float* __restrict__ Q, int ldv, const float* __restrict__ q_w, float2* __restrict__ tab,
-               int32_t* __restrict__ tab_s, int64_t tile)
+               int32_t* __restrict__ tab_s, int64_t tile, int rs, int es)
 {
     __shared__ int cj[128][KCT + 1];
     __shared__ float cz[128][KCT + 1];
@@ -401,7 +401,7 @@ __device__ __forceinline__ void table_rerank_body(float* __restrict__ D, int ldd
     for (int l = 0; l < KCT; ++l) {
         if (l < k) {
             const bool valid = s[l] != INT32_MAX;
-            tab[row * k + l] = make_float2(valid ? z[l] : INFINITY, valid ? q_w[s[l]] : 0.f);
+            tab[row * rs + l * es] = make_float2(valid ? z[l] : INFINITY, valid ? q_w[s[l]] : 0.f);
             if (tab_s) tab_s[row * k + l] = valid ? s[l] : -1;
         }
     }
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(128) k_table_rerank(float* __restrict__ D, int
                const float* __restrict__ Q, int ldv, const float* __restrict__ q_w, float2* __restrict__ tab,
                int32_t* __restrict__ tab_s)
 {
-    table_rerank_body<KCT>(D, ldd, M, h, k, kc, V, Q, ldv, q_w, tab, tab_s, blockIdx.x);
+    table_rerank_body<KCT>(D, ldd, M, h, k, kc, V, Q, ldv, q_w, tab, tab_s, blockIdx.x, k, 1);
 }
 
 // ------------------------------------------------------------------ batched forms
@@ -449,14 +449,14 @@ k_table_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t M)
 {
     if ((int)blockIdx.y >= *nq) return;
     const QDesc& d = qd[blockIdx.y];
-    table_body<KT>(d.D, d.ldd, M, d.h, d.tk, d.qw, d.tab, nullptr);
+    table_body<KT>(d.D, d.ldd, M, d.h, d.tk, d.qw, d.tab, nullptr, d.tab_rs, d.tab_es);
 }
 
 __global__ void k_table_generic_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t M)
 {
     if ((int)blockIdx.y >= *nq) return;
     const QDesc& d = qd[blockIdx.y];
-    table_generic_body(d.D, d.ldd, M, d.h, d.tk, d.qw, d.tab, nullptr);
+    table_generic_body(d.D, d.ldd, M, d.h, d.tk, d.qw, d.tab, nullptr, d.tab_rs, d.tab_es);
 }
 
 // Queries vary fastest (blockIdx.x) so that the blocks of one vocabulary tile for all
@@ -468,7 +468,8 @@ k_table_rerank_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64
 {
     if ((int)blockIdx.x >= *nq) return;
     const QDesc& d = qd[blockIdx.x];
-    table_rerank_body<KCT>(d.D, d.ldd, M, d.h, d.tk, d.kc, V, d.Q, ldv, d.qw, d.tab, nullptr, blockIdx.y);
+    table_rerank_body<KCT>(d.D, d.ldd, M, d.h, d.tk, d.kc, V, d.Q, ldv, d.qw, d.tab, nullptr, blockIdx.y, d.tab_rs,
+                           d.tab_es);
 }
 
 }  // namespace

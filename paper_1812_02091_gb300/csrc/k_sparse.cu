@@ -24,45 +24,58 @@ __device__ __forceinline__ float warp_sum(float x)
 // document (t_fwd).  One warp per document, lanes over its nonzeros (coalesced col/val
 // loads), table rows gathered from L2, warp-shuffle sum.
 
+// Cost of one nonzero along its table row T (entries es apart).
 template <int MEAS>
-__device__ __forceinline__ float fwd_cost(float x, const float2* __restrict__ T, int keff)
+__device__ __forceinline__ float fwd_cost_s(float x, const float2* __restrict__ T, int es, int keff)
 {
     if (MEAS == M_RWMD) return x * T[0].x;
     if (MEAS == M_OMR) {
         const float2 t0 = T[0];
         if (t0.x == 0.f && keff >= 2) {
             const float r = x - fminf(x, t0.y);  // free transfer to the overlapping bin
-            return r != 0.f ? r * T[1].x : 0.f;
+            return r != 0.f ? r * T[es].x : 0.f;
         }
         return x * t0.x;
     }
     float r = x, c = 0.f;
     for (int l = 0; l < keff - 1; ++l) {
-        const float2 t = T[l];
+        const float2 t = T[l * es];
         const float tau = fminf(r, t.y);
         c = fmaf(tau, t.x, c);
         r -= tau;
         if (r == 0.f) return c;
     }
-    return fmaf(r, T[keff - 1].x, c);
+    return fmaf(r, T[(keff - 1) * es].x, c);
 }
 
+template <int MEAS>
+__device__ __forceinline__ float fwd_cost(float x, const float2* __restrict__ T, int keff)
+{
+    return fwd_cost_s<MEAS>(x, T, 1, keff);
+}
+
+// Summation order of a document's forward value, shared by every form of the pass: the
+// nonzeros are split into four phases (position e - a mod 4), each summed in CSR order,
+// then (p0 + p1) + (p2 + p3).  The per-query form gives each warp eight documents (lane =
+// 8 x phase + document slot); the grouped form gives each warp one document for eight
+// queries (lane = 8 x phase + query), so both compute every value identically.
 template <int MEAS>
 __device__ __forceinline__ void fwd_body(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                       const float* __restrict__ val, int64_t n, const float2* __restrict__ tab,
                       int k, int keff, float* __restrict__ t_fwd)
 {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, slot = lane & 7, ph = lane >> 3;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t d = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); d < n; d += warps) {
-        const int32_t a = row_ptr[d], b = row_ptr[d + 1];
+    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 8; base < n;
+         base += warps * 8) {
+        const int64_t d = base + slot;
+        const bool valid = d < n;
+        const int32_t a = valid ? row_ptr[d] : 0, b = valid ? row_ptr[d + 1] : 0;
         float acc = 0.f;
-        for (int32_t e = a + lane; e < b; e += 32) {
-            const int32_t u = col[e];
-            acc += fwd_cost<MEAS>(val[e], tab + (int64_t)u * k, keff);
-        }
-        acc = warp_sum(acc);
-        if (lane == 0) t_fwd[d] = acc;
+        for (int32_t e = a + ph; e < b; e += 4) acc += fwd_cost<MEAS>(val[e], tab + (int64_t)col[e] * k, keff);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+        if (ph == 0 && valid) t_fwd[d] = acc;
     }
 }
 
@@ -317,7 +330,7 @@ __device__ __forceinline__ void rev_blk_body(const int32_t* __restrict__ row_ptr
 }
 
 template <int MEAS, int KT, int NJ, int W>
-__global__ void __launch_bounds__(W * 32, 4) k_rev_blk(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+__global__ void __launch_bounds__(W * 32, (W >= 8 ? 2 : 4)) k_rev_blk(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
           const float* __restrict__ val, const float* __restrict__ D, int ldd, int h,
           const float* __restrict__ q_w, int k, const float* __restrict__ t_fwd,
           float* __restrict__ t_rev, float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
@@ -658,6 +671,40 @@ __global__ void k_fwd_b(const QDesc* __restrict__ qd, const int* __restrict__ nq
     fwd_body<MEAS>(row_ptr, col, val, n, d.tab, d.tk, d.tk, to_out ? d.t_out : d.t_fwd);
 }
 
+// One sweep of the CSR for a group of kFwdGroup (8) consecutive queries of the batch: a warp
+// takes a document, lane = 8 x phase + query.  The 8 lanes of a nonzero read the same col /
+// val and adjacent table entries (the group's tables are interleaved by entry), so a gather
+// instruction touches 4 table rows instead of 32; the CSR is read once per group.  Values
+// are bit-identical to the per-query form (same phases, same order).
+template <int MEAS>
+__global__ void k_fwd_g(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t* __restrict__ row_ptr,
+                        const int32_t* __restrict__ col, const float* __restrict__ val, int64_t n, bool to_out)
+{
+    const int q0 = blockIdx.y * kFwdGroup;
+    const int nqv = *nq;
+    if (q0 >= nqv) return;
+    const int lane = threadIdx.x & 31, g = lane & 7, ph = lane >> 3;
+    const bool act = q0 + g < nqv;
+    const QDesc& dq = qd[act ? q0 + g : q0];
+    const float2* tq = dq.tab;
+    const int kq = dq.tk;
+    float* oq = to_out ? dq.t_out : dq.t_fwd;
+    const int rs = dq.tab_rs, es = dq.tab_es;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t d = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); d < n; d += warps) {
+        const int32_t a = row_ptr[d], b = row_ptr[d + 1];
+        float acc = 0.f;
+        for (int32_t e = a + ph; e < b; e += 4) {
+            const int32_t u = col[e];
+            const float x = val[e];
+            if (act) acc += fwd_cost_s<MEAS>(x, tq + (int64_t)u * rs, es, kq);
+        }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+        if (ph == 0 && act) oq[d] = acc;
+    }
+}
+
 // NJ follows the per-query launcher: NJW bins per lane when h > 32, else one.
 template <int MEAS, int KT, int NJW>
 __global__ void __launch_bounds__(256, 2)
@@ -696,7 +743,7 @@ __global__ void k_prune_compact_b(const QDesc* __restrict__ qd, const int* __res
 }
 
 template <int MEAS, int KT, int NJW, int W>
-__global__ void __launch_bounds__(W * 32, 4)
+__global__ void __launch_bounds__(W * 32, (W >= 8 ? 2 : 4))
 k_rev_blk_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t* __restrict__ row_ptr,
             const int32_t* __restrict__ col, const float* __restrict__ val, int k)
 {
@@ -792,8 +839,8 @@ cudaError_t launch_fwd(int meas, const int32_t* row_ptr, const int32_t* col, con
                        cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    const int warps = 8;
-    const int64_t blocks = std::min<int64_t>((n + warps - 1) / warps, 152 * 64);
+    const int warps = 8;  // eight documents per warp
+    const int64_t blocks = std::min<int64_t>((n + 8 * warps - 1) / (8 * warps), 152 * 64);
     dim3 grid((unsigned)std::max<int64_t>(1, blocks));
     switch (meas) {
     case M_RWMD: k_fwd<M_RWMD><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, tab, k, keff, t_fwd); break;
@@ -839,12 +886,22 @@ cudaError_t launch_prune(int meas, int k, const int32_t* row_ptr, const int32_t*
 }
 
 cudaError_t launch_fwd_b(int meas, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
-                         const int32_t* col, const float* val, int64_t n, bool to_out, cudaStream_t st)
+                         const int32_t* col, const float* val, int64_t n, bool to_out, bool grouped, cudaStream_t st)
 {
     if (max_q <= 0 || n <= 0) return cudaSuccess;
     const int warps = 8;
     const int64_t blocks = std::min<int64_t>((n + warps - 1) / warps, 152 * 64);
-    dim3 grid((unsigned)std::max<int64_t>(1, blocks), (unsigned)max_q);
+    if (grouped) {  // one document per warp, eight queries
+        dim3 gg((unsigned)std::max<int64_t>(1, blocks), (unsigned)((max_q + kFwdGroup - 1) / kFwdGroup));
+        switch (meas) {
+        case M_RWMD: k_fwd_g<M_RWMD><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
+        case M_OMR: k_fwd_g<M_OMR><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
+        default: k_fwd_g<M_ACT><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
+        }
+        return cudaGetLastError();
+    }
+    const int64_t qblocks = std::min<int64_t>((n + 8 * warps - 1) / (8 * warps), 152 * 64);  // eight documents per warp
+    dim3 grid((unsigned)std::max<int64_t>(1, qblocks), (unsigned)max_q);
     switch (meas) {
     case M_RWMD: k_fwd_b<M_RWMD><<<grid, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
     case M_OMR: k_fwd_b<M_OMR><<<grid, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
