@@ -639,19 +639,24 @@ def main_k4(args, local):
     import paper_1812_02091_gb300 as emd
     torch.cuda.set_device(local)
     t0 = time.perf_counter()
-    w = emd_synth.config(5, query_limit=args.batch * (args.steps + args.warmup), n_docs=args.k4_docs)
-    gen_s = time.perf_counter() - t0
     B = args.batch
+    need = B * (args.steps + args.warmup)
+    w = emd_synth.config(5, query_limit=8 * need, n_docs=args.k4_docs)
+    gen_s = time.perf_counter() - t0
+    # the sparse pass does not depend on h_q (the table is k wide): queries of at most 256 bins
+    # keep every batch in one sub-batch (one sweep per group of eight) and D small
+    small = np.nonzero(np.diff(w.queries.row_ptr) <= 256)[0][:need]
+    queries = w.queries.subset(small)
     db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
-                           emd.emd_db_options_default(precision=args.precision, device=local, max_query_h=2048,
-                                                      max_batch=B, batch_columns=2048))
+                           emd.emd_db_options_default(precision=args.precision, device=local, max_query_h=256,
+                                                      max_batch=B, batch_columns=B * 256))
     info = emd.emd_db_info_get(db)
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     out = torch.empty((B, w.db.n), dtype=torch.float32, device="cuda")
     batches = []
     for s in range(args.warmup + args.steps):
-        sub = w.queries.subset(np.arange(s * B, (s + 1) * B))
+        sub = queries.subset(np.arange(s * B, (s + 1) * B))
         batches.append((sub.row_ptr, torch.from_numpy(sub.col).cuda(), torch.from_numpy(sub.val).cuda()))
     for s in range(args.warmup):
         emd.emd_query_batch_device(db, *batches[s], out, "act", args.k, "fwd", stream=stream.cuda_stream)
@@ -672,7 +677,8 @@ def main_k4(args, local):
     print(json.dumps({"k4": "forward CSR pass (Eq. 6-9), LC-ACT k=%d" % args.k,
                       "database": f"workload 5 cut to {n} documents: nnz {nnz}, CSR {sweep / 1e6:.0f} MB per sweep, "
                                   f"v_used {info['v_used']}",
-                      "queries": B * args.steps, "launches": prof["launches"]["fwd"],
+                      "queries": f"{B * args.steps} of workload 5's queries with h_q <= 256, batches of {B}",
+                      "launches": prof["launches"]["fwd"],
                       "ms_per_query": 1e3 * t / (B * args.steps), "achieved_gbs": achieved,
                       "peak_gbs": pk["hbm_gbs"], "frac": achieved / pk["hbm_gbs"],
                       "peak_source": f"{pk['source']} HBM copy", "generation_s": gen_s}))

@@ -374,7 +374,7 @@ emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, i
         }
         Phase p(db, 3, 1, st);
         EMD_CUDA(launch_fwd_b(meas, D_, nqd, B, db->row_ptr, db->col, db->val, n, dir == EMD_DIR_FWD,
-                              tk_b > 0 && tk_b <= 16, st),
+                              tk_b > 0 && tk_b <= 16, tk_b, st),
                  "forward pass");
     }
     if (pruned) {

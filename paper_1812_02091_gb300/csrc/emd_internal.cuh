@@ -204,7 +204,8 @@ cudaError_t launch_table_b(const QDesc* qd, const int* nq, int max_q, int64_t M,
 // Forward values into t_out (to_out) or t_fwd.  grouped: the tables are interleaved in
 // groups of kFwdGroup queries and each group shares one sweep of the CSR.
 cudaError_t launch_fwd_b(int meas, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
-                         const int32_t* col, const float* val, int64_t n, bool to_out, bool grouped, cudaStream_t st);
+                         const int32_t* col, const float* val, int64_t n, bool to_out, bool grouped, int max_tk,
+                         cudaStream_t st);
 // Reverse pass over all documents; dir FWD is not accepted, REV writes t_out, MAX writes
 // t_rev and max(t_fwd, t_rev) into t_out.
 cudaError_t launch_rev_b(int meas, int k, int dir, const QDesc* qd, const int* nq, int max_q,

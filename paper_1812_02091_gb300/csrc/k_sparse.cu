@@ -54,12 +54,33 @@ __device__ __forceinline__ float fwd_cost(float x, const float2* __restrict__ T,
     return fwd_cost_s<MEAS>(x, T, 1, keff);
 }
 
+// fwd_cost_s for keff <= KT without branches: the loop over the row is unrolled to KT and
+// each step is predicated on (l < keff - 1 and residual > 0), so lanes whose residual ran
+// out earlier neither diverge nor load.  Same operations in the same order: bit-identical.
+// KT = 0: rows wider than 16, the loop form.
+template <int MEAS, int KT>
+__device__ __forceinline__ float fwd_cost_p(float x, const float2* __restrict__ T, int es, int keff)
+{
+    if (KT == 0 || MEAS != M_ACT) return fwd_cost_s<MEAS>(x, T, es, keff);
+    float r = x, c = 0.f;
+#pragma unroll
+    for (int l = 0; l < (KT > 1 ? KT - 1 : 0); ++l) {
+        if (l < keff - 1 && r != 0.f) {
+            const float2 t = T[l * es];
+            const float tau = fminf(r, t.y);
+            c = fmaf(tau, t.x, c);
+            r -= tau;
+        }
+    }
+    return r != 0.f ? fmaf(r, T[(keff - 1) * es].x, c) : c;
+}
+
 // Summation order of a document's forward value, shared by every form of the pass: the
 // nonzeros are split into four phases (position e - a mod 4), each summed in CSR order,
 // then (p0 + p1) + (p2 + p3).  The per-query form gives each warp eight documents (lane =
 // 8 x phase + document slot); the grouped form gives each warp one document for eight
 // queries (lane = 8 x phase + query), so both compute every value identically.
-template <int MEAS>
+template <int MEAS, int KT>
 __device__ __forceinline__ void fwd_body(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                       const float* __restrict__ val, int64_t n, const float2* __restrict__ tab,
                       int k, int keff, float* __restrict__ t_fwd)
@@ -72,19 +93,19 @@ __device__ __forceinline__ void fwd_body(const int32_t* __restrict__ row_ptr, co
         const bool valid = d < n;
         const int32_t a = valid ? row_ptr[d] : 0, b = valid ? row_ptr[d + 1] : 0;
         float acc = 0.f;
-        for (int32_t e = a + ph; e < b; e += 4) acc += fwd_cost<MEAS>(val[e], tab + (int64_t)col[e] * k, keff);
+        for (int32_t e = a + ph; e < b; e += 4) acc += fwd_cost_p<MEAS, KT>(val[e], tab + (int64_t)col[e] * k, 1, keff);
         acc += __shfl_xor_sync(0xffffffffu, acc, 8);
         acc += __shfl_xor_sync(0xffffffffu, acc, 16);
         if (ph == 0 && valid) t_fwd[d] = acc;
     }
 }
 
-template <int MEAS>
+template <int MEAS, int KT>
 __global__ void k_fwd(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                       const float* __restrict__ val, int64_t n, const float2* __restrict__ tab,
                       int k, int keff, float* __restrict__ t_fwd)
 {
-    fwd_body<MEAS>(row_ptr, col, val, n, tab, k, keff, t_fwd);
+    fwd_body<MEAS, KT>(row_ptr, col, val, n, tab, k, keff, t_fwd);
 }
 
 // ------------------------------------------------------------------ reverse pass
@@ -662,13 +683,13 @@ cudaError_t rev_meas_blk(int k, const int32_t* row_ptr, const int32_t* col, cons
 
 // ------------------------------------------------------------------ batched forms
 
-template <int MEAS>
+template <int MEAS, int KT>
 __global__ void k_fwd_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t* __restrict__ row_ptr,
                         const int32_t* __restrict__ col, const float* __restrict__ val, int64_t n, bool to_out)
 {
     if ((int)blockIdx.y >= *nq) return;
     const QDesc& d = qd[blockIdx.y];
-    fwd_body<MEAS>(row_ptr, col, val, n, d.tab, d.tk, d.tk, to_out ? d.t_out : d.t_fwd);
+    fwd_body<MEAS, KT>(row_ptr, col, val, n, d.tab, d.tk, d.tk, to_out ? d.t_out : d.t_fwd);
 }
 
 // One sweep of the CSR for a group of kFwdGroup (8) consecutive queries of the batch: a warp
@@ -676,7 +697,7 @@ __global__ void k_fwd_b(const QDesc* __restrict__ qd, const int* __restrict__ nq
 // val and adjacent table entries (the group's tables are interleaved by entry), so a gather
 // instruction touches 4 table rows instead of 32; the CSR is read once per group.  Values
 // are bit-identical to the per-query form (same phases, same order).
-template <int MEAS>
+template <int MEAS, int KT>
 __global__ void k_fwd_g(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t* __restrict__ row_ptr,
                         const int32_t* __restrict__ col, const float* __restrict__ val, int64_t n, bool to_out)
 {
@@ -697,7 +718,7 @@ __global__ void k_fwd_g(const QDesc* __restrict__ qd, const int* __restrict__ nq
         for (int32_t e = a + ph; e < b; e += 4) {
             const int32_t u = col[e];
             const float x = val[e];
-            if (act) acc += fwd_cost_s<MEAS>(x, tq + (int64_t)u * rs, es, kq);
+            if (act) acc += fwd_cost_p<MEAS, KT>(x, tq + (int64_t)u * rs, es, kq);
         }
         acc += __shfl_xor_sync(0xffffffffu, acc, 8);
         acc += __shfl_xor_sync(0xffffffffu, acc, 16);
@@ -834,6 +855,19 @@ cudaError_t rev_meas(int k, const int32_t* row_ptr, const int32_t* col, const fl
 
 }  // namespace
 
+// Register width of the forward cost for table width kw (0: the loop form).
+static int fwd_kt(int kw) { return kw <= 1 ? 1 : kw <= 2 ? 2 : kw <= 4 ? 4 : kw <= 8 ? 8 : kw <= 16 ? 16 : 0; }
+
+#define EMD_FWD_KT_SWITCH(KTV, LAUNCH)             \
+    switch (KTV) {                                 \
+    case 1: LAUNCH(1); break;                      \
+    case 2: LAUNCH(2); break;                      \
+    case 4: LAUNCH(4); break;                      \
+    case 8: LAUNCH(8); break;                      \
+    case 16: LAUNCH(16); break;                    \
+    default: LAUNCH(0); break;                     \
+    }
+
 cudaError_t launch_fwd(int meas, const int32_t* row_ptr, const int32_t* col, const float* val,
                        int64_t n, const float2* tab, int k, int keff, float* t_fwd,
                        cudaStream_t st)
@@ -843,9 +877,14 @@ cudaError_t launch_fwd(int meas, const int32_t* row_ptr, const int32_t* col, con
     const int64_t blocks = std::min<int64_t>((n + 8 * warps - 1) / (8 * warps), 152 * 64);
     dim3 grid((unsigned)std::max<int64_t>(1, blocks));
     switch (meas) {
-    case M_RWMD: k_fwd<M_RWMD><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, tab, k, keff, t_fwd); break;
-    case M_OMR: k_fwd<M_OMR><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, tab, k, keff, t_fwd); break;
-    default: k_fwd<M_ACT><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, tab, k, keff, t_fwd); break;
+    case M_RWMD: k_fwd<M_RWMD, 0><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, tab, k, keff, t_fwd); break;
+    case M_OMR: k_fwd<M_OMR, 0><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, tab, k, keff, t_fwd); break;
+    default: {
+#define EMD_L(KT) k_fwd<M_ACT, KT><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, tab, k, keff, t_fwd)
+        EMD_FWD_KT_SWITCH(fwd_kt(keff), EMD_L)
+#undef EMD_L
+        break;
+    }
     }
     return cudaGetLastError();
 }
@@ -886,26 +925,38 @@ cudaError_t launch_prune(int meas, int k, const int32_t* row_ptr, const int32_t*
 }
 
 cudaError_t launch_fwd_b(int meas, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
-                         const int32_t* col, const float* val, int64_t n, bool to_out, bool grouped, cudaStream_t st)
+                         const int32_t* col, const float* val, int64_t n, bool to_out, bool grouped, int max_tk,
+                         cudaStream_t st)
 {
+    const int kt = fwd_kt(max_tk);
     if (max_q <= 0 || n <= 0) return cudaSuccess;
     const int warps = 8;
     const int64_t blocks = std::min<int64_t>((n + warps - 1) / warps, 152 * 64);
     if (grouped) {  // one document per warp, eight queries
         dim3 gg((unsigned)std::max<int64_t>(1, blocks), (unsigned)((max_q + kFwdGroup - 1) / kFwdGroup));
         switch (meas) {
-        case M_RWMD: k_fwd_g<M_RWMD><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
-        case M_OMR: k_fwd_g<M_OMR><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
-        default: k_fwd_g<M_ACT><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
+        case M_RWMD: k_fwd_g<M_RWMD, 0><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
+        case M_OMR: k_fwd_g<M_OMR, 0><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
+        default: {
+#define EMD_L(KT) k_fwd_g<M_ACT, KT><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out)
+            EMD_FWD_KT_SWITCH(kt, EMD_L)
+#undef EMD_L
+            break;
+        }
         }
         return cudaGetLastError();
     }
     const int64_t qblocks = std::min<int64_t>((n + 8 * warps - 1) / (8 * warps), 152 * 64);  // eight documents per warp
     dim3 grid((unsigned)std::max<int64_t>(1, qblocks), (unsigned)max_q);
     switch (meas) {
-    case M_RWMD: k_fwd_b<M_RWMD><<<grid, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
-    case M_OMR: k_fwd_b<M_OMR><<<grid, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
-    default: k_fwd_b<M_ACT><<<grid, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
+    case M_RWMD: k_fwd_b<M_RWMD, 0><<<grid, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
+    case M_OMR: k_fwd_b<M_OMR, 0><<<grid, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
+    default: {
+#define EMD_L(KT) k_fwd_b<M_ACT, KT><<<grid, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out)
+        EMD_FWD_KT_SWITCH(kt, EMD_L)
+#undef EMD_L
+        break;
+    }
     }
     return cudaGetLastError();
 }
