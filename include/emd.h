@@ -253,6 +253,17 @@ emd_status emd_db_set_profiling(emd_db* db, int32_t on);
 emd_status emd_db_profile_get(emd_db* db, emd_profile* out);
 emd_status emd_db_profile_reset(emd_db* db);
 
+/* All-pairs top-K over the database itself, the shape of the paper's evaluation (Section 5:
+ * every histogram ranked against all others).  For each database histogram a, the K smallest
+ * max(fwd(b -> a), fwd(a -> b)) over b != a, ordered by (distance, id), where fwd(x -> y) is
+ * the forward bound (Section 4, Eq. 6-9) with histogram y as the query: the reverse bound of
+ * a pair is the forward bound of the transposed pair, so one forward pass per histogram
+ * gives both directions.  out_idx / out_dist: n_docs x K host arrays.  Needs 4 n_docs^2
+ * bytes of device memory for the forward matrix during the call (OUT_OF_MEMORY otherwise);
+ * every histogram must be within max_query_h bins (INVALID_ARG).  K <= 64, K < n_docs. */
+emd_status emd_all_pairs_topk(emd_db* db, emd_measure meas, int32_t k, int32_t K, int64_t* out_idx,
+                              float* out_dist);
+
 /* ------------------------------------------------------------------ serving
  *
  * A request loop over a resident database.  Single queries are submitted as they arrive; a

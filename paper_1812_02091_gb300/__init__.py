@@ -20,7 +20,7 @@ __all__ = [
     "emd_db_check_device_errors", "emd_phase1_table", "emd_db_set_profiling", "emd_topk_select_static",
     "emd_db_profile_get", "emd_db_profile_reset", "emd_last_error", "emd_version",
     "emd_server_options_default", "emd_server_create", "emd_server_submit", "emd_server_poll",
-    "emd_server_stats_get", "emd_server_stats_reset", "emd_server_destroy", "EmdError",
+    "emd_server_stats_get", "emd_server_stats_reset", "emd_server_destroy", "EmdError", "emd_all_pairs_topk",
     "MEASURES", "DIRECTIONS", "PRECISIONS", "PHASES", "library_path", "load",
 ]
 
@@ -111,6 +111,7 @@ def load():
     L.emd_db_set_profiling.argtypes = [P, i32]
     L.emd_db_profile_get.argtypes = [P, ctypes.POINTER(emd_profile)]
     L.emd_db_profile_reset.argtypes = [P]
+    L.emd_all_pairs_topk.argtypes = [P, i32, i32, i32, P, P]
     L.emd_server_options_default.argtypes = [ctypes.POINTER(emd_server_options)]
     L.emd_server_options_default.restype = None
     L.emd_server_create.argtypes = [P, ctypes.POINTER(emd_server_options), ctypes.POINTER(P)]
@@ -124,7 +125,7 @@ def load():
     for name in ("emd_db_create", "emd_db_destroy", "emd_db_info_get", "emd_query_batch", "emd_topk",
                  "emd_query_batch_device", "emd_topk_device", "emd_db_check_device_errors",
                  "emd_phase1_table", "emd_db_set_profiling", "emd_db_profile_get", "emd_topk_select_static",
-                 "emd_db_profile_reset", "emd_server_create", "emd_server_submit", "emd_server_poll",
+                 "emd_db_profile_reset", "emd_all_pairs_topk", "emd_server_create", "emd_server_submit", "emd_server_poll",
                  "emd_server_stats_get", "emd_server_stats_reset", "emd_server_destroy"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -312,6 +313,17 @@ def emd_db_profile_get(db) -> dict:
 
 def emd_db_profile_reset(db):
     _check(load().emd_db_profile_reset(db))
+
+
+def emd_all_pairs_topk(db, meas="act", k: int = 1, K: int = 16):
+    """Each database histogram against all others (no self-match): (idx int64[n, K],
+    dist float32[n, K]) of the K smallest symmetric bounds."""
+    n = emd_db_info_get(db)["n_docs"]
+    out_idx = np.empty((n, K), dtype=np.int64)
+    out_dist = np.empty((n, K), dtype=np.float32)
+    _check(load().emd_all_pairs_topk(db, _code(MEASURES, meas), int(k), int(K),
+                                     out_idx.ctypes.data_as(ctypes.c_void_p), out_dist.ctypes.data_as(ctypes.c_void_p)))
+    return out_idx, out_dist
 
 
 # ------------------------------------------------------------------------ serving

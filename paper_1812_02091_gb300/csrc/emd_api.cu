@@ -979,6 +979,7 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
     for (int64_t d = 0; d <= n_docs; ++d) rp32[d] = (int32_t)row_ptr[d];
 
     emd_db* db = new emd_db();
+    db->row_ptr_host.assign(row_ptr, row_ptr + n_docs + 1);
     db->opt = opt;
     db->dev = opt.device;
     db->margin = opt.rerank_margin;
@@ -1207,6 +1208,71 @@ emd_status emd_topk_device(emd_db* db, int64_t n_queries, const int64_t* q_row_p
         if (s != EMD_OK) return s;
     }
     return EMD_OK;
+}
+
+emd_status emd_all_pairs_topk(emd_db* db, emd_measure meas, int32_t k, int32_t K, int64_t* out_idx, float* out_dist)
+{
+    g_err.clear();
+    if (!db || !out_idx || !out_dist) return fail(EMD_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lock(db->mu);
+    emd_status s = check_request(db, meas, k, EMD_DIR_FWD);
+    if (s != EMD_OK) return s;
+    const int64_t n = db->n;
+    if (K < 1 || K > kMaxTopK || K >= n) return fail(EMD_ERR_INVALID_ARG, "K must be in 1..min(n_docs - 1, %d)", kMaxTopK);
+    const int64_t* rp = db->row_ptr_host.data();
+    if ((s = check_sizes(db, n, rp, meas, k, EMD_DIR_FWD)) != EMD_OK) return s;
+    EMD_CUDA(cudaSetDevice(db->dev), "cudaSetDevice");
+    cudaStream_t st = db->stream;
+    float* F = nullptr;
+    int32_t* qidx = nullptr;
+    cudaError_t e = cudaMalloc(&F, (size_t)n * (size_t)n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&qidx, (size_t)std::max<int64_t>(db->nnz, 1) * sizeof(int32_t));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (F) cudaFree(F);
+        return fail(EMD_ERR_OUT_OF_MEMORY, "all-pairs: the %lld x %lld forward matrix does not fit", (long long)n,
+                    (long long)n);
+    }
+    struct Free {
+        float* f;
+        int32_t* q;
+        ~Free()
+        {
+            cudaFree(f);
+            cudaFree(q);
+        }
+    } guard{F, qidx};
+    {
+        Phase p(db, 6, 1, st);
+        EMD_CUDA(launch_map_ids(db->col, db->nnz, db->used_ids, qidx, st), "query bins");
+    }
+    // every database histogram as a query: forward values F[a][b] = fwd(b -> a)
+    for (int64_t i0 = 0; i0 < n; i0 += db->opt.max_batch) {
+        const int64_t i1 = std::min<int64_t>(n, i0 + db->opt.max_batch);
+        s = run_batch(db, rp, qidx + rp[i0], db->val + rp[i0], i0, i1, meas, k, EMD_DIR_FWD, 0, F + i0 * n, nullptr,
+                      nullptr, st);
+        if (s != EMD_OK) return s;
+    }
+    {
+        Phase p(db, 6, 1, st);
+        EMD_CUDA(launch_sym_max(F, n, st), "symmetric maximum");
+    }
+    for (int64_t i0 = 0; i0 < n; i0 += db->opt.max_batch) {
+        const int64_t rows = std::min<int64_t>(db->opt.max_batch, n - i0);
+        {
+            Phase p(db, 5, topk_launch_count(n), st);
+            EMD_CUDA(launch_topk_rows(F + i0 * n, rows, n, n, K, db->topk_scratch, db->stage_oidx, db->stage_odist, st),
+                     "top-K");
+        }
+        EMD_CUDA(cudaMemcpyAsync(out_idx + i0 * K, db->stage_oidx, rows * K * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                 st),
+                 "result copy");
+        EMD_CUDA(cudaMemcpyAsync(out_dist + i0 * K, db->stage_odist, rows * K * sizeof(float), cudaMemcpyDeviceToHost,
+                                 st),
+                 "result copy");
+        EMD_CUDA(cudaStreamSynchronize(st), "synchronize");
+    }
+    return read_device_errors(db);
 }
 
 emd_status emd_db_check_device_errors(emd_db* db)

@@ -122,6 +122,7 @@ struct emd_db {
     int32_t* used_ids = nullptr; // v_used, vocabulary id of each used row (ascending)
     float* cost = nullptr;       // v x v ground costs (cost-matrix mode)
     int32_t* row_ptr = nullptr;  // n + 1
+    std::vector<int64_t> row_ptr_host;  // the same offsets on the host (all-pairs batching)
     int32_t* col = nullptr;      // nnz, renumbered into the used vocabulary
     float* val = nullptr;        // nnz
     int* err = nullptr;

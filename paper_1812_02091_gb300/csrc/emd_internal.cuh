@@ -221,6 +221,12 @@ cudaError_t launch_topk_b(const QDesc* qd, const int* nq, int max_q, int64_t n, 
 cudaError_t launch_prune_b(int meas, int k, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
                            const int32_t* col, const float* val, int64_t n, int K, int rev_warps, cudaStream_t st);
 
+// All-pairs form (Section 5's evaluation over the database itself).  Vocabulary ids of
+// the database's nonzeros (used_ids[col[e]]), the query bins of the database histograms.
+cudaError_t launch_map_ids(const int32_t* col, int64_t nnz, const int32_t* used_ids, int32_t* out, cudaStream_t st);
+// F (n x n, row stride n): F[a][b] <- max(F[a][b], F[b][a]) for all a, b and F[a][a] <- +inf.
+cudaError_t launch_sym_max(float* F, int64_t n, cudaStream_t st);
+
 // Failure message for emd_last_error() (defined beside the C ABI).
 emd_status set_error(emd_status st, const char* msg);
 void clear_error();

@@ -1000,6 +1000,62 @@ cudaError_t launch_topk_b(const QDesc* qd, const int* nq, int max_q, int64_t n, 
     return topk_kt_b<64>(qd, nq, max_q, n, K, scratch, fwd_rows, st);
 }
 
+}  // namespace emd
+
+namespace {
+
+__global__ void k_map_ids(const int32_t* __restrict__ col, int64_t nnz, const int32_t* __restrict__ used_ids,
+                          int32_t* __restrict__ out)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = used_ids[col[e]];
+}
+
+// One 32 x 32 tile pair (I, J), I <= J, per block: both tiles through shared memory, the
+// element-wise max written to both (the symmetric bound of Section 5 from the forward values
+// of a pair and of its transpose); the diagonal becomes +inf (no self-match).
+__global__ void k_sym_max(float* __restrict__ F, int64_t n)
+{
+    const int64_t I = blockIdx.y, J = blockIdx.x;
+    if (I > J) return;
+    __shared__ float a[32][33], b[32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8 threads
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t i = I * 32 + r, j = J * 32 + tx;
+        a[r][tx] = (i < n && j < n) ? F[i * n + j] : 0.f;
+        const int64_t i2 = J * 32 + r, j2 = I * 32 + tx;
+        b[r][tx] = (i2 < n && j2 < n) ? F[i2 * n + j2] : 0.f;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t i = I * 32 + r, j = J * 32 + tx;
+        if (i < n && j < n) F[i * n + j] = (i == j) ? INFINITY : fmaxf(a[r][tx], b[tx][r]);
+        const int64_t i2 = J * 32 + r, j2 = I * 32 + tx;
+        if (I != J && i2 < n && j2 < n) F[i2 * n + j2] = fmaxf(b[r][tx], a[tx][r]);
+    }
+}
+
+}  // namespace
+
+namespace emd {
+
+cudaError_t launch_map_ids(const int32_t* col, int64_t nnz, const int32_t* used_ids, int32_t* out, cudaStream_t st)
+{
+    if (nnz <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((nnz + 255) / 256, 152 * 16);
+    k_map_ids<<<(unsigned)blocks, 256, 0, st>>>(col, nnz, used_ids, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sym_max(float* F, int64_t n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t nt = (n + 31) / 32;
+    if (nt > 65535) return cudaErrorInvalidValue;
+    k_sym_max<<<dim3((unsigned)nt, (unsigned)nt), dim3(32, 8), 0, st>>>(F, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_topk_rows(const float* t, int64_t rows, int64_t n, int64_t ldt, int K,
                              unsigned long long* scratch, int64_t* out_idx, float* out_dist,
                              cudaStream_t st)
