@@ -317,6 +317,9 @@ def main():
                     help="forward sparse pass alone on the serving-size database (workload 5, cut to --k4-docs "
                          "documents), against the HBM roofline; prints one line")
     ap.add_argument("--k4-docs", type=int, default=300000)
+    ap.add_argument("--ict", action="store_true",
+                    help="LC-ICT symmetric top-K on workload 2's database and queries beside LC-ACT on the "
+                         "same batches, recall against the oracle; prints one line")
     ap.add_argument("--allpairs", type=int, default=0, choices=[0, 2, 3],
                     help="all-pairs top-K over workload 2 (text) or 3 (images) instead of the bench "
                          "line: every histogram against all others; prints one line")
@@ -336,6 +339,8 @@ def main():
         return main_k4(args, local)
     if args.allpairs:
         return main_allpairs(args, local)
+    if args.ict:
+        return main_ict(args, local)
 
     import torch
     import paper_1812_02091_gb300 as emd
@@ -687,6 +692,65 @@ def main_k4(args, local):
                       "ms_per_query": 1e3 * t / (B * args.steps), "achieved_gbs": achieved,
                       "peak_gbs": pk["hbm_gbs"], "frac": achieved / pk["hbm_gbs"],
                       "peak_source": f"{pk['source']} HBM copy", "generation_s": gen_s}))
+
+
+def main_ict(args, local):
+    """ICT (tables ending where each row's largest database weight is placed) against ACT k
+    on the same batches of workload-2 queries: pruned symmetric top-K, CUDA events, L2
+    flushed between batches; ICT recall against the FP64 oracle on sampled queries."""
+    import torch
+    import emd_synth
+    import paper_1812_02091_gb300 as emd
+    torch.cuda.set_device(local)
+    B, K, steps = args.batch, args.topk, args.steps
+    w = emd_synth.config(2, query_limit=B * (steps + 1))
+    db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
+                           emd.emd_db_options_default(precision=args.precision, device=local, max_query_h=1024,
+                                                      max_batch=B))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    dev = []
+    for s in range(steps + 1):
+        sub = w.queries.subset(np.arange(s * B, (s + 1) * B))
+        dev.append((sub.row_ptr, torch.from_numpy(sub.col).cuda(), torch.from_numpy(sub.val).cuda()))
+    oi = torch.empty((B, K), dtype=torch.int64, device="cuda")
+    od = torch.empty((B, K), dtype=torch.float32, device="cuda")
+    out = {"mode": f"LC-ICT vs LC-ACT k={args.k}, symmetric top-{K} (pruned)", "workload": w.name,
+           "precision": args.precision, "queries": f"{steps} batches of {B}"}
+    first = {}
+    for meas, k in (("ict", 1), ("act", args.k)):
+        emd.emd_topk_device(db, *dev[steps], oi, od, meas, k, "max", K, stream=stream.cuda_stream)  # warm-up
+        torch.cuda.synchronize()
+        emd.emd_db_profile_reset(db)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for s in range(steps):
+            flush.fill_(float(s))
+            ev[s][0].record(stream)
+            emd.emd_topk_device(db, *dev[s], oi, od, meas, k, "max", K, stream=stream.cuda_stream)
+            ev[s][1].record(stream)
+            if s == 0:
+                first[meas] = (oi.cpu().numpy(), od.cpu().numpy())
+        torch.cuda.synchronize()
+        total = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+        prof = emd.emd_db_profile_get(db)
+        out[meas] = {"queries_per_s": B * steps / total, "ms_per_batch": 1e3 * total / steps,
+                     "prune_fallbacks": prof["prune_fallbacks"], "ict_wide": prof["ict_wide"]}
+    emd.emd_db_profile_reset(db)
+    emd.emd_db_set_profiling(db, True)
+    emd.emd_topk_device(db, *dev[0], oi, od, "ict", 1, "max", K, stream=stream.cuda_stream)
+    out["ict"]["phase_ms_one_batch"] = {p: round(v, 3) for p, v in emd.emd_db_profile_get(db)["ms"].items()}
+    emd.emd_db_check_device_errors(db)
+    emd.emd_db_destroy(db)
+    hs = np.diff(w.queries.row_ptr)[:B]
+    oq = [i for i in range(B) if hs[i] <= 400][:2]
+    import oracle
+    rec = []
+    for q in oq:
+        tf, tr = oracle.lc_query_split(w.emb, None, w.db, *w.queries.row(q), "ict", 1, threads=os.cpu_count() or 1)
+        rec.append(recall_at(first["ict"][0][q], np.maximum(tf, tr), K))
+    out["ict"]["top_recall_vs_oracle"] = float(np.mean(rec)) if rec else None
+    out["ict"]["oracle_queries_h"] = [int(hs[q]) for q in oq]
+    print(json.dumps(out))
 
 
 def main_allpairs(args, local):

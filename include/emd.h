@@ -133,6 +133,8 @@ typedef struct {
     int64_t prune_fallbacks; /* of those, queries recomputed over all documents */
     int64_t graph_launches;  /* batch sequences replayed from captured graphs (their kernels are
                                 included in the launch counts) */
+    int64_t ict_wide;        /* ICT queries recomputed with tables of full width h because a
+                                vocabulary row needed more than max_table_k entries */
 } emd_profile;
 
 /* Fill *opt with the defaults listed above.  Never fails. */

@@ -62,7 +62,8 @@ class emd_queries(ctypes.Structure):
 class emd_profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 7), ("launches", ctypes.c_int64 * 7),
                 ("total_launches", ctypes.c_int64), ("pruned_queries", ctypes.c_int64),
-                ("prune_fallbacks", ctypes.c_int64), ("graph_launches", ctypes.c_int64)]
+                ("prune_fallbacks", ctypes.c_int64), ("graph_launches", ctypes.c_int64),
+                ("ict_wide", ctypes.c_int64)]
 
 
 class emd_server_options(ctypes.Structure):
@@ -308,7 +309,8 @@ def emd_db_profile_get(db) -> dict:
     _check(load().emd_db_profile_get(db, ctypes.byref(p)))
     return {"ms": dict(zip(PHASES, list(p.ms))), "launches": dict(zip(PHASES, list(p.launches))),
             "total_launches": int(p.total_launches), "pruned_queries": int(p.pruned_queries),
-            "prune_fallbacks": int(p.prune_fallbacks), "graph_launches": int(p.graph_launches)}
+            "prune_fallbacks": int(p.prune_fallbacks), "graph_launches": int(p.graph_launches),
+            "ict_wide": int(p.ict_wide)}
 
 
 def emd_db_profile_reset(db):

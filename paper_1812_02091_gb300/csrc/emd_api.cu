@@ -128,12 +128,12 @@ struct Phase {
 
 int topk_launch_count(int64_t n) { return topk_blocks(n) > 1 ? 2 : 1; }
 
-int table_width(int meas, int k, int h)
+int table_width(const emd_db* db, int meas, int k, int h)
 {
     switch (meas) {
     case M_RWMD: return 1;
     case M_OMR: return std::min(2, h);
-    case M_ICT: return h;
+    case M_ICT: return db->approx ? h : std::min(h, db->opt.max_table_k);
     default: return std::min(k, h);
     }
 }
@@ -158,12 +158,12 @@ emd_status check_sizes(const emd_db* db, int64_t nq, const int64_t* rp, int meas
         if (h < 1 || h > db->opt.max_query_h)
             return fail(EMD_ERR_INVALID_ARG, "query %lld has %lld bins (allowed 1..%d)", (long long)i,
                         (long long)h, db->opt.max_query_h);
-        if (dir != EMD_DIR_REV && table_width(meas, k, (int)h) > db->opt.max_table_k)
+        if (dir != EMD_DIR_REV && table_width(db, meas, k, (int)h) > db->opt.max_table_k)
             return fail(EMD_ERR_UNSUPPORTED, "forward table width %d exceeds max_table_k %d",
-                        table_width(meas, k, (int)h), db->opt.max_table_k);
-        if (dir != EMD_DIR_REV && db->approx && rerank_width(db, table_width(meas, k, (int)h), (int)h) > kRerankMax)
+                        table_width(db, meas, k, (int)h), db->opt.max_table_k);
+        if (dir != EMD_DIR_REV && db->approx && rerank_width(db, table_width(db, meas, k, (int)h), (int)h) > kRerankMax)
             return fail(EMD_ERR_UNSUPPORTED, "re-rank width %d exceeds %d (approximate precisions)",
-                        rerank_width(db, table_width(meas, k, (int)h), (int)h), kRerankMax);
+                        rerank_width(db, table_width(db, meas, k, (int)h), (int)h), kRerankMax);
     }
     return EMD_OK;
 }
@@ -227,33 +227,44 @@ emd_status run_phase1(emd_db* db, Lane& L, const int32_t* qidx, int h, cudaStrea
 int rerank_width(const emd_db* db, int tk, int h) { return std::min(tk + db->margin, h); }
 
 // The Phase-1 table of width tk from lane L's D (re-ranked for the approximate precisions).
-emd_status run_table(emd_db* db, Lane& L, const float* qw, int h, int tk, int32_t* tab_s, cudaStream_t st)
+emd_status run_table(emd_db* db, Lane& L, const float* qw, int h, int meas, int tk, float2* tab, int32_t* tab_s,
+                     int* over, cudaStream_t st)
 {
     const int ldd = (int)round_up(h, 32);
     Phase p(db, 2, 1, st);
-    if (db->approx)
+    if (meas == M_ICT && !db->approx)
+        EMD_CUDA(launch_table_ict(L.D, ldd, db->v_used, h, tk, qw, db->xmax, tab, tab_s, over, st), "ICT table");
+    else if (db->approx)
         EMD_CUDA(launch_table_rerank(L.D, ldd, db->v_used, h, tk, rerank_width(db, tk, h), db->emb_used, L.Q,
-                                     db->ldm, qw, L.tab, tab_s, st), "top-k table (re-ranked)");
+                                     db->ldm, qw, tab, tab_s, st), "top-k table (re-ranked)");
     else
-        EMD_CUDA(launch_table(L.D, ldd, db->v_used, h, tk, qw, L.tab, tab_s, st), "top-k table");
+        EMD_CUDA(launch_table(L.D, ldd, db->v_used, h, tk, qw, tab, tab_s, st), "top-k table");
     return EMD_OK;
 }
 
 // One query through Phase 1, the forward and/or reverse pass; out_t (n floats) receives
 // the distances.
 emd_status run_query(emd_db* db, Lane& L, const int32_t* qidx, const float* qw, int h, int meas, int k,
-                     int dir, float* out_t, cudaStream_t st)
+                     int dir, float* out_t, int* over, cudaStream_t st)
 {
     emd_status s0 = run_phase1(db, L, qidx, h, st);
     if (s0 != EMD_OK) return s0;
     const int ldd = (int)round_up(h, 32);
     if (dir != EMD_DIR_REV) {
-        const int tk = table_width(meas, k, h);
-        emd_status s1 = run_table(db, L, qw, h, tk, nullptr, st);
+        const bool wide = meas == M_ICT && !db->approx && !over;  // the whole row if needed
+        const int tk = wide ? h : table_width(db, meas, k, h);
+        float2* tab = L.tab;
+        if (tk > db->opt.max_table_k)
+            EMD_CUDA(cudaMallocAsync((void**)&tab, (size_t)db->v_used * tk * sizeof(float2), st), "ICT table memory");
+        emd_status s1 = run_table(db, L, qw, h, meas, tk, tab, nullptr, over, st);
+        if (s1 == EMD_OK) {
+            Phase p(db, 3, 1, st);
+            const cudaError_t e = launch_fwd(meas, db->row_ptr, db->col, db->val, db->n, tab, tk, tk,
+                                             dir == EMD_DIR_FWD ? out_t : L.t_fwd, st);
+            if (e != cudaSuccess) s1 = cuda_fail(e, "forward pass");
+        }
+        if (tab != L.tab) cudaFreeAsync(tab, st);
         if (s1 != EMD_OK) return s1;
-        Phase p(db, 3, 1, st);
-        EMD_CUDA(launch_fwd(meas, db->row_ptr, db->col, db->val, db->n, L.tab, tk, tk,
-                            dir == EMD_DIR_FWD ? out_t : L.t_fwd, st), "forward pass");
     }
     if (dir != EMD_DIR_FWD) {
         Phase p(db, 4, 1, st);
@@ -266,21 +277,21 @@ emd_status run_query(emd_db* db, Lane& L, const int32_t* qidx, const float* qw, 
 
 bool prunable(const emd_db* db, int meas, int k, int dir, int K)
 {
-    return db->opt.prune_topk != 0 && dir == EMD_DIR_MAX && K <= kPruneMaxK && meas != EMD_ICT &&
-           (meas != EMD_ACT || k <= kMaxRegK);
+    return db->opt.prune_topk != 0 && dir == EMD_DIR_MAX && K <= kPruneMaxK &&
+           (meas != EMD_ICT || !db->approx) && (meas != EMD_ACT || k <= kMaxRegK);
 }
 
 // Pruned symmetric top-K of one query (see emd_topk in include/emd.h): forward pass over
 // all documents, forward top-K, candidates within the margin, reverse pass on them, final
 // selection with the certification flag in *ok.
 emd_status run_topk_pruned(emd_db* db, Lane& L, const int32_t* qidx, const float* qw, int h, int meas, int k,
-                           int K, int* ok, int64_t* out_idx, float* out_dist, cudaStream_t st)
+                           int K, int* ok, int* over, int64_t* out_idx, float* out_dist, cudaStream_t st)
 {
     emd_status s = run_phase1(db, L, qidx, h, st);
     if (s != EMD_OK) return s;
     const int ldd = (int)round_up(h, 32);
-    const int tk = table_width(meas, k, h);
-    s = run_table(db, L, qw, h, tk, nullptr, st);
+    const int tk = table_width(db, meas, k, h);
+    s = run_table(db, L, qw, h, meas, tk, L.tab, nullptr, over, st);
     if (s != EMD_OK) return s;
     {
         Phase p(db, 3, 1, st);
@@ -329,7 +340,7 @@ emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, i
     const int* nqd = ws.nq_dev + slot;
     const int64_t n = db->n;
     const int H = db->opt.max_query_h;
-    const int tk_b = dir != EMD_DIR_REV ? table_width(meas, k, H) : 0;
+    const int tk_b = dir != EMD_DIR_REV ? table_width(db, meas, k, H) : 0;
     const int kc_b = db->approx ? std::min(rerank_width(db, tk_b, H), kRerankMax) : tk_b;
     if (db->cost_mode) {
         Phase p(db, 1, 1, st);
@@ -369,8 +380,11 @@ emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, i
     if (dir != EMD_DIR_REV) {
         {
             Phase p(db, 2, 1, st);
-            EMD_CUDA(launch_table_b(D_, nqd, B, db->v_used, tk_b, db->approx, kc_b, db->emb_used, db->ldm, st),
-                     "top-k table");
+            if (meas == M_ICT && !db->approx)
+                EMD_CUDA(launch_table_ict_b(D_, nqd, B, db->v_used, db->xmax, st), "ICT table");
+            else
+                EMD_CUDA(launch_table_b(D_, nqd, B, db->v_used, tk_b, db->approx, kc_b, db->emb_used, db->ldm, st),
+                         "top-k table");
         }
         Phase p(db, 3, 1, st);
         EMD_CUDA(launch_fwd_b(meas, D_, nqd, B, db->row_ptr, db->col, db->val, n, dir == EMD_DIR_FWD,
@@ -480,6 +494,7 @@ emd_status alloc_batch_ws(emd_db* db, BatchWS& ws, int max_batch, int64_t cols, 
     TRYW(dal(&ws.bcand_sym, B * 2 * kPruneCap));
     TRYW(dal(&ws.bcand_count, B));
     TRYW(dal(&ws.cand_ok, B));
+    TRYW(dal(&ws.ict_over, B));
     TRYW(dal(&ws.topk_scratch, B * kTopkScratchRow));
     TRYW(dal(&ws.qd_dev, BatchWS::kDescRing * B));
     TRYW(dal(&ws.nq_dev, BatchWS::kDescRing));
@@ -513,7 +528,7 @@ emd_status fill_descriptors(BatchWS& ws, int slot, emd_db* db, const int64_t* rp
                         int64_t* out_idx, float* out_dist, cudaStream_t st)
 {
     const int nb = (int)(j1 - j0);
-    const int tk_b = dir != EMD_DIR_REV ? table_width(meas, k, db->opt.max_query_h) : 0;
+    const int tk_b = dir != EMD_DIR_REV ? table_width(db, meas, k, db->opt.max_query_h) : 0;
     const bool grouped = tk_b > 0 && tk_b <= 16;
     QDesc* hd = ws.qd_host + (int64_t)slot * ws.max_batch;
     QDesc* dd = ws.qd_dev + (int64_t)slot * ws.max_batch;
@@ -530,7 +545,7 @@ emd_status fill_descriptors(BatchWS& ws, int slot, emd_db* db, const int64_t* rp
         d.ldd = (int)round_up(d.h, 32);
         d.qrows = (int)round_up(d.ldd, kDistBN);
         d.npad = (int)round_up(d.h, 128);
-        d.tk = dir != EMD_DIR_REV ? table_width(meas, k, d.h) : 0;
+        d.tk = dir != EMD_DIR_REV ? table_width(db, meas, k, d.h) : 0;
         d.kc = db->approx && d.tk > 0 ? rerank_width(db, d.tk, d.h) : d.tk;
         d.qidx = qidx + off;
         d.qw = qw + off;
@@ -562,9 +577,10 @@ emd_status fill_descriptors(BatchWS& ws, int slot, emd_db* db, const int64_t* rp
             d.sel_val = ws.bsel_val + (int64_t)b * K;
             d.cand = ws.bcand + (int64_t)b * kPruneCap;
             d.cand_sym = ws.bcand_sym + (int64_t)b * 2 * kPruneCap;
-            d.cand_count = ws.bcand_count + b;
+            d.cand_count = ws.bcand_count + (i - j0);  // position in the sub-batch: zeroed by its sequence
             d.ok = ws.cand_ok + b;
         }
+        if (meas == M_ICT) d.over = ws.ict_over + b;
         if (K > 0) {
             d.out_idx = out_idx + (int64_t)b * K;
             d.out_dist = out_dist + (int64_t)b * K;
@@ -631,6 +647,8 @@ emd_status run_subbatch(emd_db* db, BatchWS& ws, const int64_t* rp, const int32_
     const int slot = ws.desc_slot;
     ws.desc_slot = (slot + 1) % BatchWS::kDescRing;
     EMD_CUDA(cudaEventSynchronize(ws.desc_ev[slot]), "descriptor ring");
+    if (meas == M_ICT)
+        EMD_CUDA(cudaMemsetAsync(ws.ict_over + (j0 - i0), 0, (j1 - j0) * sizeof(int), st), "flag reset");
     emd_status s = fill_descriptors(ws, slot, db, rp, qidx, qw, i0, j0, j1, meas, k, dir, K, pruned, out_t, out_idx,
                                     out_dist, st);
     if (s == EMD_OK) s = run_subbatch_launch(ws, slot, db, (int)(j1 - j0), meas, k, dir, K, pruned, st);
@@ -643,7 +661,7 @@ bool batch_fits(const emd_db* db, const BatchWS& ws, const int64_t* rp, int64_t 
 {
     int64_t cD = 0, cQ = 0, cP = 0, cT = 0;
     if (i1 - i0 > ws.max_batch) return false;
-    const int tk_b = dir != EMD_DIR_REV ? table_width(meas, k, db->opt.max_query_h) : 0;
+    const int tk_b = dir != EMD_DIR_REV ? table_width(db, meas, k, db->opt.max_query_h) : 0;
     const bool grouped = tk_b > 0 && tk_b <= 16;
     for (int64_t i = i0; i < i1; ++i) {
         const int h = (int)(rp[i + 1] - rp[i]);
@@ -651,7 +669,7 @@ bool batch_fits(const emd_db* db, const BatchWS& ws, const int64_t* rp, int64_t 
         cD += ldd;
         cQ += round_up(ldd, kDistBN);
         cP += round_up(h, 128);
-        cT += dir != EMD_DIR_REV ? table_width(meas, k, h) : 0;
+        cT += dir != EMD_DIR_REV ? table_width(db, meas, k, h) : 0;
     }
     if (grouped) cT = (i1 - i0 + kFwdGroup - 1) / kFwdGroup * kFwdGroup * tk_b;  // interleaved groups
     return cD <= ws.b_cols && cQ <= ws.b_qrows && cP <= ws.b_prows && cT <= ws.b_tabcols;
@@ -662,6 +680,7 @@ emd_status run_batch(emd_db* db, const int64_t* rp, const int32_t* qidx, const f
                      float* out_dist, cudaStream_t st)
 {
     const bool pruned = K > 0 && prunable(db, meas, k, dir, K);
+    const bool ict = meas == M_ICT && dir != EMD_DIR_REV && !db->approx;
     if (db->opt.batched) {
         // split into sub-batches that fit the batch workspace
         BatchWS& ws = db->bw;
@@ -675,26 +694,37 @@ emd_status run_batch(emd_db* db, const int64_t* rp, const int32_t* qidx, const f
             j0 = j1;
         }
     } else {
+        if (ict) EMD_CUDA(cudaMemsetAsync(db->ict_over, 0, (i1 - i0) * sizeof(int), st), "flag reset");
         emd_status s = run_lanes(db, rp, qidx, qw, i0, i1, meas, k, dir, K, pruned, out_t, out_idx, out_dist, st);
         if (s != EMD_OK) return s;
+        if (K > 0 && !pruned) {
+            s = select_topk(db, db->stage_out, i1 - i0, K, out_idx, out_dist, st);
+            if (s != EMD_OK) return s;
+        }
     }
-    if (K > 0 && !pruned && !db->opt.batched) return select_topk(db, db->stage_out, i1 - i0, K, out_idx, out_dist, st);
-    if (!pruned) return EMD_OK;
-    std::vector<int> ok((size_t)(i1 - i0), 0);
-    EMD_CUDA(cudaMemcpyAsync(ok.data(), db->opt.batched ? db->bw.cand_ok : db->cand_ok, (i1 - i0) * sizeof(int),
-                             cudaMemcpyDeviceToHost, st),
-             "flag read");
+    if (!pruned && !ict) return EMD_OK;
+    // uncertified pruned queries and ICT queries whose table overflowed: recomputed alone
+    // over all documents (ICT with tables of full width)
+    std::vector<int> ok((size_t)(i1 - i0), 1), over((size_t)(i1 - i0), 0);
+    if (pruned)
+        EMD_CUDA(cudaMemcpyAsync(ok.data(), db->opt.batched ? db->bw.cand_ok : db->cand_ok, (i1 - i0) * sizeof(int),
+                                 cudaMemcpyDeviceToHost, st),
+                 "flag read");
+    if (ict)
+        EMD_CUDA(cudaMemcpyAsync(over.data(), db->opt.batched ? db->bw.ict_over : db->ict_over,
+                                 (i1 - i0) * sizeof(int), cudaMemcpyDeviceToHost, st),
+                 "flag read");
     EMD_CUDA(cudaStreamSynchronize(st), "synchronize");
-    db->pruned_queries += i1 - i0;
+    if (pruned) db->pruned_queries += i1 - i0;
     for (int64_t i = i0; i < i1; ++i) {
-        if (ok[i - i0]) continue;
-        ++db->prune_fallbacks;
+        if (ok[i - i0] && !over[i - i0]) continue;
+        if (over[i - i0]) ++db->ict_wide; else ++db->prune_fallbacks;
         const int64_t off = rp[i] - rp[i0];
         const int h = (int)(rp[i + 1] - rp[i]);
-        emd_status s = run_query(db, db->lanes[0], qidx + off, qw + off, h, meas, k, EMD_DIR_MAX,
-                                 db->stage_out, st);
+        float* dst = K > 0 ? db->stage_out : out_t + (i - i0) * db->n;
+        emd_status s = run_query(db, db->lanes[0], qidx + off, qw + off, h, meas, k, dir, dst, nullptr, st);
         if (s != EMD_OK) return s;
-        s = select_topk(db, db->stage_out, 1, K, out_idx + (i - i0) * K, out_dist + (i - i0) * K, st);
+        if (K > 0) s = select_topk(db, db->stage_out, 1, K, out_idx + (i - i0) * K, out_dist + (i - i0) * K, st);
         if (s != EMD_OK) return s;
     }
     return EMD_OK;
@@ -714,11 +744,11 @@ emd_status run_lanes(emd_db* db, const int64_t* rp, const int32_t* qidx, const f
         const int h = (int)(rp[i + 1] - rp[i]);
         emd_status s;
         if (pruned)
-            s = run_topk_pruned(db, L, qidx + off, qw + off, h, meas, k, K, db->cand_ok + (i - i0),
+            s = run_topk_pruned(db, L, qidx + off, qw + off, h, meas, k, K, db->cand_ok + (i - i0), db->ict_over + (i - i0),
                                 out_idx + (i - i0) * K, out_dist + (i - i0) * K, L.st);
         else
             s = run_query(db, L, qidx + off, qw + off, h, meas, k, dir,
-                          (K > 0 ? db->stage_out : out_t) + (i - i0) * db->n, L.st);
+                          (K > 0 ? db->stage_out : out_t) + (i - i0) * db->n, db->ict_over + (i - i0), L.st);
         if (s != EMD_OK) return s;
     }
     for (int l = 0; l < nl; ++l) {
@@ -1024,6 +1054,14 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
     TRYC(cudaMemcpyAsync(db->row_ptr, rp32.data(), (n_docs + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st), "copy");
     TRYC(cudaMemcpyAsync(db->col, col_used.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st), "copy");
     TRYC(cudaMemcpyAsync(db->val, val, nnz * sizeof(float), cudaMemcpyHostToDevice, st), "copy");
+    {
+        // the largest weight any document puts on each used row: how far an ICT table row
+        // must reach (Algorithm 4 moves at most that much mass out of a bin of the row)
+        std::vector<float> xmax((size_t)vu, 0.f);
+        for (int64_t e = 0; e < nnz; ++e) xmax[col_used[e]] = std::max(xmax[col_used[e]], val[e]);
+        TRY(dalloc(db, &db->xmax, vu));
+        TRYC(cudaMemcpy(db->xmax, xmax.data(), vu * sizeof(float), cudaMemcpyHostToDevice), "copy");
+    }
 
     if (db->cost_mode) {
         TRY(dalloc(db, &db->cost, v * v));
@@ -1087,6 +1125,7 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
     TRY(dalloc(db, &db->tab_s, vu * opt.max_table_k));
     TRY(dalloc(db, &db->topk_scratch, (int64_t)opt.max_batch * kTopkScratchRow));
     TRY(dalloc(db, &db->cand_ok, opt.max_batch));
+    TRY(dalloc(db, &db->ict_over, opt.max_batch));
     if (opt.batched) TRY(alloc_batch_ws(db, db->bw, opt.max_batch, opt.batch_columns, db->allocs, &db->bytes));
     db->stage_bins = (int64_t)opt.max_batch * opt.max_query_h;
     TRY(dalloc(db, &db->stage_idx, db->stage_bins));
@@ -1307,7 +1346,7 @@ emd_status emd_phase1_table(emd_db* db, const int32_t* q_idx, const float* q_w, 
     if (s != EMD_OK) return s;
     if (db->approx && rerank_width(db, k, h_q) > kRerankMax)
         return fail(EMD_ERR_UNSUPPORTED, "re-rank width %d exceeds %d", rerank_width(db, k, h_q), kRerankMax);
-    s = run_table(db, L, db->stage_w, h_q, k, db->tab_s, st);
+    s = run_table(db, L, db->stage_w, h_q, M_ACT, k, L.tab, db->tab_s, nullptr, st);
     if (s != EMD_OK) return s;
     const int64_t cnt = db->v_used * k;
     std::vector<float2> tz((size_t)cnt);
@@ -1339,6 +1378,7 @@ emd_status emd_db_profile_get(emd_db* db, emd_profile* out)
     out->pruned_queries = db->pruned_queries;
     out->prune_fallbacks = db->prune_fallbacks;
     out->graph_launches = db->graph_launches;
+    out->ict_wide = db->ict_wide;
     return EMD_OK;
 }
 
@@ -1349,7 +1389,7 @@ emd_status emd_db_profile_reset(emd_db* db)
     emd_status s = collect_profile(db);
     if (s != EMD_OK) return s;
     for (int p = 0; p < EMD_N_PHASES; ++p) { db->ms[p] = 0.0; db->launches[p] = 0; }
-    db->pruned_queries = db->prune_fallbacks = db->graph_launches = 0;
+    db->pruned_queries = db->prune_fallbacks = db->graph_launches = db->ict_wide = 0;
     return EMD_OK;
 }
 

@@ -94,6 +94,7 @@ struct BatchWS {
     float* bcand_sym = nullptr;   // max_batch x 2 kPruneCap
     int* bcand_count = nullptr;   // max_batch
     int* cand_ok = nullptr;       // max_batch certification flags
+    int* ict_over = nullptr;      // max_batch ICT table overflow flags
     unsigned long long* topk_scratch = nullptr;  // max_batch x kTopkScratchRow
     QDesc* qd_dev = nullptr;      // kDescRing x max_batch descriptors
     int* nq_dev = nullptr;        // kDescRing counts
@@ -146,6 +147,8 @@ struct emd_db {
     // batch workspace (shared by the lanes, one row per query of a batch)
     unsigned long long* topk_scratch = nullptr;  // max_batch x kTopkScratchRow
     int* cand_ok = nullptr;        // max_batch certification flags
+    int* ict_over = nullptr;       // max_batch ICT table overflow flags (lanes path)
+    float* xmax = nullptr;         // v_used, the largest database weight at each used row
     int64_t stage_bins = 0;
     int32_t* stage_idx = nullptr;
     float* stage_w = nullptr;
@@ -169,6 +172,7 @@ struct emd_db {
     // batched form (opt.batched): the workspace of the host-API batches
     emd::BatchWS bw;
     int64_t graph_launches = 0;   // batch sequences replayed from graphs (all workspaces)
+    int64_t ict_wide = 0;         // ICT queries recomputed with full-width tables
 
     // free parameters of the batched kernels (autotune at creation)
     bool autotuned = false;
@@ -186,7 +190,9 @@ struct emd_db {
 
 namespace emd {
 
-int table_width(int meas, int k, int h);
+// Forward table width of a query with h bins.  ICT (FP32 distances): at most max_table_k
+// entries, rows ending where the largest database weight of the row is placed.
+int table_width(const emd_db* db, int meas, int k, int h);
 // Candidates per row re-ranked by the table kernel of the approximate precisions.
 int rerank_width(const emd_db* db, int tk, int h);
 emd_status check_query_values(const emd_db* db, const emd_queries* q);
@@ -194,14 +200,17 @@ bool prunable(const emd_db* db, int meas, int k, int dir, int K);
 int topk_launch_count(int64_t n);
 
 // One query through Phase 1 and the forward and/or reverse pass on lane L's workspace;
-// out_t (n floats, device) receives the distances.  Caller holds db->mu.
+// out_t (n floats, device) receives the distances.  ICT: with `over` (device flag) the
+// table is at most max_table_k wide and *over = 1 marks a query that needed more; without
+// it the table is h wide (temporary device memory when above max_table_k), always exact.
+// Caller holds db->mu.
 emd_status run_query(emd_db* db, Lane& L, const int32_t* qidx, const float* qw, int h, int meas, int k,
-                     int dir, float* out_t, cudaStream_t st);
+                     int dir, float* out_t, int* over, cudaStream_t st);
 
 // Pruned max-direction top-K of one query (K <= kPruneMaxK); *ok (device) receives the
-// certificate.  Caller holds db->mu.
+// certificate, *over the ICT overflow flag.  Caller holds db->mu.
 emd_status run_topk_pruned(emd_db* db, Lane& L, const int32_t* qidx, const float* qw, int h, int meas, int k,
-                           int K, int* ok, int64_t* out_idx, float* out_dist, cudaStream_t st);
+                           int K, int* ok, int* over, int64_t* out_idx, float* out_dist, cudaStream_t st);
 
 // Batch workspaces (emd_api.cu).  alloc_batch_ws records its device allocations in
 // `allocs` (freed by the owner) and adds their size to *bytes; free_batch_ws releases the

@@ -69,6 +69,15 @@ cudaError_t launch_dist_gather(const float* cost, int64_t v, const int32_t* a_id
 cudaError_t launch_table(const float* D, int ldd, int64_t M, int h, int k, const float* q_w,
                          float2* tab, int32_t* tab_s, cudaStream_t st);
 
+// ICT table (Section 3.3, Algorithm 4, in the linear form of Section 4): per row u the
+// smallest D[u, 0..h) in ascending (distance, column) order, only as many as the largest
+// database weight at u, xmax[u], needs before its residual reaches 0 (capacity-limited
+// transfers in FP32, the same steps as the forward pass), at most W entries.  Entries past
+// that point are not written: no database weight at u reaches them.  A row that would need
+// more than W < h entries sets *over = 1 (the query's values are then incomplete).
+cudaError_t launch_table_ict(const float* D, int ldd, int64_t M, int h, int W, const float* q_w,
+                             const float* xmax, float2* tab, int32_t* tab_s, int* over, cudaStream_t st);
+
 // Forward direction (Phase 2 and 3, Eq. 6-9): t_fwd[d] for every document.
 cudaError_t launch_fwd(int meas, const int32_t* row_ptr, const int32_t* col, const float* val,
                        int64_t n, const float2* tab, int k, int keff, float* t_fwd,
@@ -165,6 +174,7 @@ struct QDesc {
     float* cand_sym;        // 2 * kPruneCap: max values, then reverse values
     int* cand_count;
     int* ok;                // certification flag
+    int* over;              // ICT: set to 1 when a table row needed more than tk entries
     int64_t* out_idx;       // K top-K result
     float* out_dist;
     int h, ldd, qrows, npad, tk, kc;
@@ -201,6 +211,9 @@ cudaError_t launch_tc_dist_batch(int fmt, const void* A_hi, const void* A_lo, in
 // (V: the used vocabulary rows, ldv floats each).
 cudaError_t launch_table_b(const QDesc* qd, const int* nq, int max_q, int64_t M, int max_tk, bool rerank,
                            int max_kc, const float* V, int ldv, cudaStream_t st);
+// The ICT table of every query of a batch (width qd[q].tk, overflow flag qd[q].over).
+cudaError_t launch_table_ict_b(const QDesc* qd, const int* nq, int max_q, int64_t M, const float* xmax,
+                               cudaStream_t st);
 // Forward values into t_out (to_out) or t_fwd.  grouped: the tables are interleaved in
 // groups of kFwdGroup queries and each group shares one sweep of the CSR.
 cudaError_t launch_fwd_b(int meas, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,

@@ -62,6 +62,7 @@ struct Exec {
     int64_t* h_oidx = nullptr;
     float* h_odist = nullptr;
     int* h_ok = nullptr;
+    int* h_over = nullptr;          // ICT table overflow flags
     int32_t* d_idx = nullptr;
     float* d_w = nullptr;
     int64_t* d_oidx = nullptr;
@@ -168,6 +169,9 @@ void finish_batch(emd_server* s, Exec& e, emd_status st, const char* why)
 
 // Stages the batch's bins and issues its kernels and result copies (worker thread, s->mu
 // not held).
+// ICT batches whose tables can overflow (FP32 distances) report per-request flags.
+bool ict_batch(const emd_db* db, const Exec& e) { return e.meas == M_ICT && !db->approx; }
+
 emd_status launch_batch(emd_server* s, Exec& e)
 {
     emd_db* db = s->db;
@@ -195,30 +199,35 @@ emd_status launch_batch(emd_server* s, Exec& e)
              "result copy");
     if (e.pruned)
         EMD_CUDA(cudaMemcpyAsync(e.h_ok, e.ws.cand_ok, (size_t)nb * 4, cudaMemcpyDeviceToHost, e.st), "flag copy");
+    if (ict_batch(db, e))
+        EMD_CUDA(cudaMemcpyAsync(e.h_over, e.ws.ict_over, (size_t)nb * 4, cudaMemcpyDeviceToHost, e.st), "flag copy");
     EMD_CUDA(cudaEventRecord(e.done, e.st), "event");
     return EMD_OK;
 }
 
-// Recomputes the batch's uncertified pruned requests over all documents (rare), in place in
-// the pinned results; *count receives how many.
+// Recomputes over all documents, in place in the pinned results, the batch's uncertified
+// pruned requests and its ICT requests whose table overflowed (both rare; ICT with tables of
+// full width); *count receives how many.
 emd_status run_fallbacks(emd_server* s, Exec& e, int* count)
 {
     emd_db* db = s->db;
     *count = 0;
-    if (!e.pruned) return EMD_OK;
+    const bool ict = ict_batch(db, e);
+    if (!e.pruned && !ict) return EMD_OK;
     for (size_t i = 0; i < e.batch.size(); ++i) {
-        if (e.h_ok[i]) continue;
+        const bool over = ict && e.h_over[i];
+        if (!over && (!e.pruned || e.h_ok[i])) continue;
         const Request* r = e.batch[i];
         const int64_t off = e.h_rp[i];
         {
             std::lock_guard<std::mutex> lock(db->mu);
             emd_status st = run_query(db, s->fb, e.d_idx + off, e.d_w + off, r->h, r->meas, r->k, EMD_DIR_MAX,
-                                      s->fb_out, e.st);
+                                      s->fb_out, nullptr, e.st);
             if (st != EMD_OK) return st;
             EMD_CUDA(launch_topk(s->fb_out, db->n, r->K, s->fb.scratch, e.d_oidx + i * r->K, e.d_odist + i * r->K,
                                  e.st),
                      "top-K");
-            db->prune_fallbacks += 1;
+            if (over) db->ict_wide += 1; else db->prune_fallbacks += 1;
         }
         EMD_CUDA(cudaMemcpyAsync(e.h_oidx + i * r->K, e.d_oidx + i * r->K, (size_t)r->K * 8, cudaMemcpyDeviceToHost,
                                  e.st),
@@ -417,7 +426,7 @@ emd_status emd_server_create(emd_db* db, const emd_server_options* opt_in, emd_s
         cudaError_t ce = cudaSuccess;
         const int64_t hb = align256(8 * ((int64_t)mb + 1)) + 2 * align256(4 * e.ws.b_cols) +
                            align256(8 * (int64_t)mb * kMaxTopK) + align256(4 * (int64_t)mb * kMaxTopK) +
-                           align256(4 * (int64_t)mb);
+                           2 * align256(4 * (int64_t)mb);
         if (st == EMD_OK) ce = cudaStreamCreateWithFlags(&e.st, cudaStreamNonBlocking);
         if (st == EMD_OK && ce == cudaSuccess) ce = cudaEventCreateWithFlags(&e.done, cudaEventDisableTiming);
         if (st == EMD_OK && ce == cudaSuccess) ce = cudaHostAlloc((void**)&e.pinned, (size_t)hb, cudaHostAllocDefault);
@@ -441,6 +450,8 @@ emd_status emd_server_create(emd_db* db, const emd_server_options* opt_in, emd_s
         e.h_odist = reinterpret_cast<float*>(p);
         p += align256(4 * (int64_t)mb * kMaxTopK);
         e.h_ok = reinterpret_cast<int*>(p);
+        p += align256(4 * (int64_t)mb);
+        e.h_over = reinterpret_cast<int*>(p);
     }
     if ((st = alloc_lane(s.get(), s->fb)) != EMD_OK || (st = sdal(s.get(), &s->fb_out, db->n)) != EMD_OK) {
         destroy_resources(s.get());
@@ -464,7 +475,7 @@ emd_status emd_server_submit(emd_server* s, const int32_t* idx, const float* w, 
     if (h_q < 1 || h_q > s->opt.max_query_h)
         return fail(EMD_ERR_INVALID_ARG, "h_q must be 1..%d", s->opt.max_query_h);
     if (K < 1 || K > kMaxTopK || K > db->n) return fail(EMD_ERR_INVALID_ARG, "K must be in 1..min(n_docs, %d)", kMaxTopK);
-    const int tk = table_width(meas, k, h_q);
+    const int tk = table_width(db, meas, k, h_q);
     if (tk > db->opt.max_table_k)
         return fail(EMD_ERR_UNSUPPORTED, "forward table width %d exceeds max_table_k %d", tk, db->opt.max_table_k);
     if (db->approx && rerank_width(db, tk, h_q) > kRerankMax)

@@ -306,6 +306,60 @@ __device__ __forceinline__ void table_generic_body(const float* __restrict__ D, 
     }
 }
 
+// One warp per vocabulary row.  Each step finds the next smallest (distance, column) after
+// the previous one (lane-strided scan, shuffle reduction), writes it and moves
+// min(residual, weight) of xmax[row] -- the steps of the forward cost, so for every database
+// weight x <= xmax[row] the forward walk along this row ends (residual 0) within the
+// entries written (fl(r - min(r, w)) is non-decreasing in r).
+__device__ __forceinline__ void table_ict_body(const float* __restrict__ D, int ldd, int64_t M, int h, int W,
+                                               const float* __restrict__ q_w, const float* __restrict__ xmax,
+                                               float2* __restrict__ tab, int32_t* __restrict__ tab_s, int rs,
+                                               int es, int* __restrict__ over)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= M) return;
+    const float* Dr = D + row * ldd;
+    const int lim = min(W, h);
+    float r = xmax[row];
+    float pz = -INFINITY;
+    int ps = -1, l = 0;
+    do {
+        float bz = INFINITY;
+        int bs = INT32_MAX;
+        for (int j = lane; j < h; j += 32) {
+            const float d = Dr[j];
+            const bool after = d > pz || (d == pz && j > ps);
+            if (after && (d < bz || (d == bz && j < bs))) { bz = d; bs = j; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oz = __shfl_xor_sync(0xffffffffu, bz, o);
+            const int os = __shfl_xor_sync(0xffffffffu, bs, o);
+            if (oz < bz || (oz == bz && os < bs)) { bz = oz; bs = os; }
+        }
+        const bool valid = bs != INT32_MAX;  // always while l < h, unless D holds NaN
+        const float w = valid ? q_w[bs] : 0.f;
+        if (lane == 0) {
+            tab[row * rs + (int64_t)l * es] = make_float2(valid ? bz : INFINITY, w);
+            if (tab_s) tab_s[row * W + l] = valid ? bs : -1;
+        }
+        if (!valid) break;
+        r -= fminf(r, w);
+        pz = bz;
+        ps = bs;
+        ++l;
+    } while (r != 0.f && l < lim);
+    if (r != 0.f && lim < h && lane == 0 && over) *over = 1;
+}
+
+__global__ void k_table_ict(const float* __restrict__ D, int ldd, int64_t M, int h, int W,
+                            const float* __restrict__ q_w, const float* __restrict__ xmax, float2* __restrict__ tab,
+                            int32_t* __restrict__ tab_s, int* __restrict__ over)
+{
+    table_ict_body(D, ldd, M, h, W, q_w, xmax, tab, tab_s, W, 1, over);
+}
+
 __global__ void k_table_generic(const float* __restrict__ D, int ldd, int64_t M, int h, int k,
                                 const float* __restrict__ q_w, float2* __restrict__ tab,
                                 int32_t* __restrict__ tab_s)
@@ -452,6 +506,14 @@ k_table_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t M)
     table_body<KT>(d.D, d.ldd, M, d.h, d.tk, d.qw, d.tab, nullptr, d.tab_rs, d.tab_es);
 }
 
+__global__ void k_table_ict_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t M,
+                              const float* __restrict__ xmax)
+{
+    if ((int)blockIdx.y >= *nq) return;
+    const QDesc& d = qd[blockIdx.y];
+    table_ict_body(d.D, d.ldd, M, d.h, d.tk, d.qw, xmax, d.tab, nullptr, d.tab_rs, d.tab_es, d.over);
+}
+
 __global__ void k_table_generic_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t M)
 {
     if ((int)blockIdx.y >= *nq) return;
@@ -523,6 +585,17 @@ cudaError_t launch_table(const float* D, int ldd, int64_t M, int h, int k, const
     return cudaGetLastError();
 }
 
+cudaError_t launch_table_ict(const float* D, int ldd, int64_t M, int h, int W, const float* q_w,
+                             const float* xmax, float2* tab, int32_t* tab_s, int* over, cudaStream_t st)
+{
+    if (M <= 0) return cudaSuccess;
+    if (W < 1 || h < 1) return cudaErrorInvalidValue;
+    const int warps = 8;
+    k_table_ict<<<(unsigned)((M + warps - 1) / warps), warps * 32, 0, st>>>(D, ldd, M, h, W, q_w, xmax, tab, tab_s,
+                                                                           over);
+    return cudaGetLastError();
+}
+
 }  // namespace emd
 
 namespace emd {
@@ -568,6 +641,15 @@ cudaError_t launch_dist_gather_b(const QDesc* qd, const int* nq, int max_q, cons
 {
     if (max_q <= 0 || M <= 0) return cudaSuccess;
     k_dist_gather_b<<<dim3((unsigned)M, (unsigned)max_q), 128, 0, st>>>(qd, nq, cost, v, a_ids, M, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_table_ict_b(const QDesc* qd, const int* nq, int max_q, int64_t M, const float* xmax,
+                               cudaStream_t st)
+{
+    if (max_q <= 0 || M <= 0) return cudaSuccess;
+    const int warps = 8;
+    k_table_ict_b<<<dim3((unsigned)((M + warps - 1) / warps), (unsigned)max_q), warps * 32, 0, st>>>(qd, nq, M, xmax);
     return cudaGetLastError();
 }
 

@@ -778,6 +778,18 @@ k_rev_blk_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int3
                                      d.cand_sym, d.cand, d.cand_count);
 }
 
+// Reverse values of the candidate documents, rows of any width (ICT): one warp each.
+template <int MEAS>
+__global__ void k_rev_generic_cand_b(const QDesc* __restrict__ qd, const int* __restrict__ nq,
+                                     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                     const float* __restrict__ val, int k)
+{
+    if ((int)blockIdx.y >= *nq) return;
+    const QDesc& d = qd[blockIdx.y];
+    rev_generic_body<MEAS>(row_ptr, col, val, kPruneCap, d.D, d.ldd, d.h, d.qw, k, d.t_fwd, d.cand_sym + kPruneCap,
+                           d.cand_sym, d.cand, d.cand_count);
+}
+
 __global__ void k_prune_select_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int K)
 {
     if ((int)blockIdx.x >= *nq) return;
@@ -917,6 +929,7 @@ cudaError_t launch_prune(int meas, int k, const int32_t* row_ptr, const int32_t*
     switch (meas) {
     case M_RWMD: e = rev_meas_blk<M_RWMD>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, st); break;
     case M_OMR: e = rev_meas_blk<M_OMR>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, st); break;
+    case M_ICT: e = rev_meas<M_ICT>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, st); break;
     default: e = rev_meas_blk<M_ACT>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, st); break;
     }
     if (e != cudaSuccess) return e;
@@ -984,6 +997,13 @@ cudaError_t launch_prune_b(int meas, int k, const QDesc* qd, const int* nq, int 
     switch (meas) {
     case M_RWMD: e = rev_meas_blk_b<M_RWMD>(k, rev_warps, qd, nq, max_q, row_ptr, col, val, st); break;
     case M_OMR: e = rev_meas_blk_b<M_OMR>(k, rev_warps, qd, nq, max_q, row_ptr, col, val, st); break;
+    case M_ICT: {
+        const int warps = 8;
+        k_rev_generic_cand_b<M_ICT><<<dim3(kPruneCap / warps, (unsigned)max_q), warps * 32, 0, st>>>(qd, nq, row_ptr,
+                                                                                                   col, val, k);
+        e = cudaGetLastError();
+        break;
+    }
     default: e = rev_meas_blk_b<M_ACT>(k, rev_warps, qd, nq, max_q, row_ptr, col, val, st); break;
     }
     if (e != cudaSuccess) return e;

@@ -277,14 +277,14 @@ def test_invalid_database_rejected(emd):
         emd.emd_db_create(emb, None, np.array([0, 2], np.int64), col[:2], np.array([0.5, 0.6], np.float32))
 
 
-def test_ict_forward_beyond_table_width_is_unsupported(emd, tiny):
-    w, db = tiny
+def test_query_above_max_query_h_is_rejected(emd, tiny):
+    w, db = tiny  # max_query_h = 64
     rng = np.random.default_rng(3)
     c = np.sort(rng.choice(w.v, 70, replace=False)).astype(np.int32)
     x = np.full(70, 1 / 70, np.float32)
     with pytest.raises(emd.EmdError) as e:
         emd.emd_query_batch(db, np.array([0, 70]), c, x, "ict", 1, "max")
-    assert e.value.name in ("UNSUPPORTED", "INVALID_ARG")
+    assert e.value.name == "INVALID_ARG"
 
 
 # --------------------------------------------------------------------- full size (config 2)
@@ -451,3 +451,22 @@ def test_batched_equals_per_query(emd, precision):
         emd.emd_db_destroy(db_q)
         emd.emd_db_destroy(db_b)
         emd.emd_db_destroy(db_c)
+
+
+def test_pruned_topk_over_several_sub_batches(emd):
+    """A batch split into several sub-batches (small batch workspace), called repeatedly:
+    every sub-batch's candidate counts start from zero, so the pruned top-K equals the
+    unpruned one bit for bit on every call."""
+    w = emd_synth.small_text(515, 2500, 48, 1200, 40, 4, 50, 20, 200)
+    q = w.queries
+    db_p = make_db(emd, w, precision="fp32_tc", max_query_h=256, batch_columns=768, max_batch=32)
+    db_u = make_db(emd, w, precision="fp32_tc", max_query_h=256, prune_topk=0)
+    try:
+        ui, ud = emd.emd_topk(db_u, q.row_ptr, q.col, q.val, "act", 4, "max", 12)
+        for _ in range(3):
+            pi, pd = emd.emd_topk(db_p, q.row_ptr, q.col, q.val, "act", 4, "max", 12)
+            assert np.array_equal(pi, ui) and np.array_equal(pd, ud)
+        assert emd.emd_db_profile_get(db_p)["pruned_queries"] == 3 * q.n
+    finally:
+        emd.emd_db_destroy(db_p)
+        emd.emd_db_destroy(db_u)
