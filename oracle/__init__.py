@@ -9,7 +9,9 @@ package.  The product path (the CUDA library and its binding) never loads it.
   * exact EMD (Eq. 1-3) by a small min-cost-flow solver, for tiny histograms;
   * the per-pair definition for one query against a whole database (both directions);
   * the linear-complexity form of Section 4 (Phase 1, Eq. 6-8, Eq. 9) for the forward
-    direction, with the reverse direction gathered from the Phase-1 distances.
+    direction, with the reverse direction gathered from the Phase-1 distances;
+  * the two cheap baselines of Section 5: bag-of-words cosine similarity and the word
+    centroid distance.
 This module compiles it with gcc on first use and wraps it with ctypes.
 """
 from __future__ import annotations
@@ -67,6 +69,10 @@ def lib():
                 f.restype = i32
             L.oracle_phase1.argtypes = [P, i32, P, i64, P, i64, P, P, i32, i32, P, P, P]
             L.oracle_phase1.restype = None
+            L.oracle_bow_db.argtypes = [i64, P, P, P, i64, P, P, i32, P]
+            L.oracle_bow_db.restype = i32
+            L.oracle_wcd_db.argtypes = [P, i32, P, P, P, i64, P, P, i32, P]
+            L.oracle_wcd_db.restype = i32
             _lib = L
     return _lib
 
@@ -228,3 +234,34 @@ def lc_query_split(emb, cost, db, q_idx, q_w, meas: str, k: int = 1, fwd=True, r
     tf = np.concatenate([p[0] for p in parts]) if fwd else None
     tr = np.concatenate([p[1] for p in parts]) if rev else None
     return tf, tr
+
+
+# ----------------------------------------------------------------- Section 5 baselines
+
+def bow_cosine(v: int, db, q_idx, q_w) -> np.ndarray:
+    """Bag-of-words cosine similarity of one query with every database histogram."""
+    rp = np.ascontiguousarray(db.row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(db.col, dtype=np.int32)
+    val = np.ascontiguousarray(db.val, dtype=np.float32)
+    q_idx = np.ascontiguousarray(q_idx, dtype=np.int32)
+    q_w = np.ascontiguousarray(q_w, dtype=np.float32)
+    out = np.empty(len(rp) - 1, dtype=np.float64)
+    if lib().oracle_bow_db(int(v), _p(rp), _p(col), _p(val), len(rp) - 1, _p(q_idx), _p(q_w), len(q_idx),
+                           _p(out)) != 0:
+        raise MemoryError("oracle allocation failed")
+    return out
+
+
+def wcd(emb, db, q_idx, q_w) -> np.ndarray:
+    """Word centroid distance of one query to every database histogram."""
+    emb = np.ascontiguousarray(emb, dtype=np.float32)
+    rp = np.ascontiguousarray(db.row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(db.col, dtype=np.int32)
+    val = np.ascontiguousarray(db.val, dtype=np.float32)
+    q_idx = np.ascontiguousarray(q_idx, dtype=np.int32)
+    q_w = np.ascontiguousarray(q_w, dtype=np.float32)
+    out = np.empty(len(rp) - 1, dtype=np.float64)
+    if lib().oracle_wcd_db(_p(emb), emb.shape[1], _p(rp), _p(col), _p(val), len(rp) - 1, _p(q_idx), _p(q_w),
+                           len(q_idx), _p(out)) != 0:
+        raise MemoryError("oracle allocation failed")
+    return out

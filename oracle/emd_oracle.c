@@ -418,3 +418,67 @@ void oracle_phase1(const float* emb, int32_t m, const float* cost, int64_t v,
     }
     free(buf); free(s); free(Du);
 }
+
+/* ------------------------------------------------------------------ Section 5 baselines */
+
+/* Bag-of-words cosine similarity of the query with every database histogram (Section 5:
+ * the dot product of the two weight vectors after L2 normalisation; it ignores the
+ * embeddings).  Coordinates held by one side only contribute nothing.  A histogram with
+ * zero norm has similarity 0.  Returns 0, or -1 on allocation failure. */
+int32_t oracle_bow_db(int64_t v, const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n,
+                      const int32_t* q_idx, const float* q_w, int32_t hq, double* out)
+{
+    double* dense = (double*)calloc((size_t)(v > 0 ? v : 1), sizeof(double));
+    if (!dense) return -1;
+    double qn = 0.0;
+    for (int32_t j = 0; j < hq; ++j) {
+        dense[q_idx[j]] = (double)q_w[j];
+        qn += (double)q_w[j] * (double)q_w[j];
+    }
+    qn = sqrt(qn);
+    for (int64_t d = 0; d < n; ++d) {
+        double dot = 0.0, dn = 0.0;
+        for (int64_t e = row_ptr[d]; e < row_ptr[d + 1]; ++e) {
+            dot += (double)val[e] * dense[col[e]];
+            dn += (double)val[e] * (double)val[e];
+        }
+        dn = sqrt(dn);
+        out[d] = (qn > 0.0 && dn > 0.0) ? dot / (qn * dn) : 0.0;
+    }
+    free(dense);
+    return 0;
+}
+
+/* Word centroid distance (Section 5, after Kusner et al.): the Euclidean distance between
+ * the weighted averages sum_i p_i E_i / sum_i p_i of the two histograms' embedding vectors.
+ * Returns 0, or -1 on allocation failure. */
+int32_t oracle_wcd_db(const float* emb, int32_t m, const int64_t* row_ptr, const int32_t* col, const float* val,
+                      int64_t n, const int32_t* q_idx, const float* q_w, int32_t hq, double* out)
+{
+    double* cq = (double*)calloc((size_t)(m > 0 ? m : 1), sizeof(double));
+    double* cd = (double*)calloc((size_t)(m > 0 ? m : 1), sizeof(double));
+    if (!cq || !cd) { free(cq); free(cd); return -1; }
+    double sq = 0.0;
+    for (int32_t j = 0; j < hq; ++j) {
+        sq += (double)q_w[j];
+        for (int32_t i = 0; i < m; ++i) cq[i] += (double)q_w[j] * (double)emb[(int64_t)q_idx[j] * m + i];
+    }
+    for (int32_t i = 0; i < m; ++i) cq[i] /= sq;
+    for (int64_t d = 0; d < n; ++d) {
+        double sd = 0.0;
+        for (int32_t i = 0; i < m; ++i) cd[i] = 0.0;
+        for (int64_t e = row_ptr[d]; e < row_ptr[d + 1]; ++e) {
+            sd += (double)val[e];
+            for (int32_t i = 0; i < m; ++i) cd[i] += (double)val[e] * (double)emb[(int64_t)col[e] * m + i];
+        }
+        double s = 0.0;
+        for (int32_t i = 0; i < m; ++i) {
+            const double diff = cd[i] / sd - cq[i];
+            s += diff * diff;
+        }
+        out[d] = sqrt(s);
+    }
+    free(cq);
+    free(cd);
+    return 0;
+}
