@@ -266,6 +266,22 @@ emd_status emd_db_profile_reset(emd_db* db);
 emd_status emd_all_pairs_topk(emd_db* db, emd_measure meas, int32_t k, int32_t K, int64_t* out_idx,
                               float* out_dist);
 
+/* The two cheap baselines the paper compares against (Section 5), on the same resident
+ * database and query format:
+ *   EMD_BOW_COSINE  bag-of-words cosine similarity: the dot product of the two weight
+ *                   vectors after L2 normalisation (no embeddings, any database mode);
+ *   EMD_WCD         word centroid distance: the Euclidean distance between the two
+ *                   weight-averaged embedding vectors (embedding databases only, else
+ *                   EMD_ERR_UNSUPPORTED).
+ * emd_baseline_batch: out is n_queries x n_docs host floats (cosine similarity, or WCD).
+ * emd_baseline_topk: the K nearest documents per query, by 1 - cosine (returned in
+ * out_dist, clamped at 0) or by WCD, ties by lower document id; K <= 64.  Queries as for
+ * emd_query_batch (1..max_query_h bins, distinct ids in range, weights summing to 1). */
+typedef enum { EMD_BOW_COSINE = 0, EMD_WCD = 1 } emd_baseline;
+emd_status emd_baseline_batch(emd_db* db, const emd_queries* q, emd_baseline kind, float* out);
+emd_status emd_baseline_topk(emd_db* db, const emd_queries* q, emd_baseline kind, int32_t K, int64_t* out_idx,
+                             float* out_dist);
+
 /* ------------------------------------------------------------------ serving
  *
  * A request loop over a resident database.  Single queries are submitted as they arrive; a

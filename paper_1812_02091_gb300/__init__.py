@@ -21,6 +21,7 @@ __all__ = [
     "emd_db_profile_get", "emd_db_profile_reset", "emd_last_error", "emd_version",
     "emd_server_options_default", "emd_server_create", "emd_server_submit", "emd_server_poll",
     "emd_server_stats_get", "emd_server_stats_reset", "emd_server_destroy", "EmdError", "emd_all_pairs_topk",
+    "emd_baseline_batch", "emd_baseline_topk",
     "MEASURES", "DIRECTIONS", "PRECISIONS", "PHASES", "library_path", "load",
 ]
 
@@ -113,6 +114,8 @@ def load():
     L.emd_db_profile_get.argtypes = [P, ctypes.POINTER(emd_profile)]
     L.emd_db_profile_reset.argtypes = [P]
     L.emd_all_pairs_topk.argtypes = [P, i32, i32, i32, P, P]
+    L.emd_baseline_batch.argtypes = [P, P, i32, P]
+    L.emd_baseline_topk.argtypes = [P, P, i32, i32, P, P]
     L.emd_server_options_default.argtypes = [ctypes.POINTER(emd_server_options)]
     L.emd_server_options_default.restype = None
     L.emd_server_create.argtypes = [P, ctypes.POINTER(emd_server_options), ctypes.POINTER(P)]
@@ -126,7 +129,8 @@ def load():
     for name in ("emd_db_create", "emd_db_destroy", "emd_db_info_get", "emd_query_batch", "emd_topk",
                  "emd_query_batch_device", "emd_topk_device", "emd_db_check_device_errors",
                  "emd_phase1_table", "emd_db_set_profiling", "emd_db_profile_get", "emd_topk_select_static",
-                 "emd_db_profile_reset", "emd_all_pairs_topk", "emd_server_create", "emd_server_submit", "emd_server_poll",
+                 "emd_db_profile_reset", "emd_all_pairs_topk", "emd_baseline_batch",
+                 "emd_baseline_topk", "emd_server_create", "emd_server_submit", "emd_server_poll",
                  "emd_server_stats_get", "emd_server_stats_reset", "emd_server_destroy"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -325,6 +329,31 @@ def emd_all_pairs_topk(db, meas="act", k: int = 1, K: int = 16):
     out_dist = np.empty((n, K), dtype=np.float32)
     _check(load().emd_all_pairs_topk(db, _code(MEASURES, meas), int(k), int(K),
                                      out_idx.ctypes.data_as(ctypes.c_void_p), out_dist.ctypes.data_as(ctypes.c_void_p)))
+    return out_idx, out_dist
+
+
+BASELINES = {"bow": 0, "wcd": 1}
+
+
+def emd_baseline_batch(db, q_row_ptr, q_idx, q_w, kind="bow", n_docs=None):
+    """Section 5 baselines: BoW cosine similarity ("bow") or word centroid distance ("wcd"),
+    float32[n_queries, n_docs]."""
+    n = n_docs if n_docs is not None else emd_db_info_get(db)["n_docs"]
+    q, keep = _queries(q_row_ptr, q_idx, q_w)
+    out = np.empty((q.n_queries, n), dtype=np.float32)
+    _check(load().emd_baseline_batch(db, ctypes.byref(q), _code(BASELINES, kind),
+                                     out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def emd_baseline_topk(db, q_row_ptr, q_idx, q_w, kind="bow", K: int = 16):
+    """K nearest documents by 1 - cosine ("bow") or by word centroid distance ("wcd")."""
+    q, keep = _queries(q_row_ptr, q_idx, q_w)
+    out_idx = np.empty((q.n_queries, K), dtype=np.int64)
+    out_dist = np.empty((q.n_queries, K), dtype=np.float32)
+    _check(load().emd_baseline_topk(db, ctypes.byref(q), _code(BASELINES, kind), int(K),
+                                    out_idx.ctypes.data_as(ctypes.c_void_p),
+                                    out_dist.ctypes.data_as(ctypes.c_void_p)))
     return out_idx, out_dist
 
 

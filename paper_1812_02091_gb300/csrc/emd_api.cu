@@ -98,34 +98,6 @@ cudaEvent_t take_event(emd_db* db)
     return e;
 }
 
-// Brackets the kernels of one phase with events (when profiling) and counts launches.
-// With several lanes the phases of different queries overlap, so phase sums can exceed
-// the wall time of a batch.
-struct Phase {
-    emd_db* db;
-    int ph;
-    int nlaunch;
-    cudaStream_t st;
-    cudaEvent_t a = nullptr;
-    Phase(emd_db* d, int p, int nl, cudaStream_t s) : db(d), ph(p), nlaunch(nl), st(s)
-    {
-        if (db->profiling) {
-            a = take_event(db);
-            cudaEventRecord(a, st);
-        }
-    }
-    ~Phase()
-    {
-        db->launches[ph] += nlaunch;
-        db->total_launches += nlaunch;
-        if (db->profiling) {
-            cudaEvent_t b = take_event(db);
-            cudaEventRecord(b, st);
-            db->recs.push_back({ph, a, b});
-        }
-    }
-};
-
 int topk_launch_count(int64_t n) { return topk_blocks(n) > 1 ? 2 : 1; }
 
 int table_width(const emd_db* db, int meas, int k, int h)

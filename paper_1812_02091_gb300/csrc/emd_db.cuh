@@ -181,6 +181,16 @@ struct emd_db {
     int tune_rev_warps = 4;    // warps per candidate document in the pruned reverse pass
     std::map<emd::GraphKey, emd::GraphEntry> graphs;
 
+    // Section 5 baselines (allocated and prepared at first use)
+    int32_t* vslot = nullptr;       // v: used-vocabulary slot of each id, -1 if unused
+    float* bow_dense = nullptr;     // ceil(max_batch / 8) x v_used x 8 interleaved query vectors
+    float* doc_inv_norm = nullptr;  // n
+    float* doc_centroid = nullptr;  // n x ldc (word centroid distance)
+    float* q_centroid = nullptr;    // max_batch x ldc
+    int64_t* base_rp = nullptr;     // max_batch + 1 query offsets of a batch
+    int ldc = 0;
+    bool bow_ready = false, wcd_ready = false;
+
     // Serialises the entry points that launch work or touch the counters above (host
     // threads, and the server's worker thread).
     std::mutex mu;
@@ -189,6 +199,36 @@ struct emd_db {
 
 
 namespace emd {
+
+cudaEvent_t take_event(emd_db* db);
+
+// Brackets the kernels of one phase with events (when profiling) and counts launches.
+// With several lanes the phases of different queries overlap, so phase sums can exceed
+// the wall time of a batch.
+struct Phase {
+    emd_db* db;
+    int ph;
+    int nlaunch;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    Phase(emd_db* d, int p, int nl, cudaStream_t s) : db(d), ph(p), nlaunch(nl), st(s)
+    {
+        if (db->profiling) {
+            a = take_event(db);
+            cudaEventRecord(a, st);
+        }
+    }
+    ~Phase()
+    {
+        db->launches[ph] += nlaunch;
+        db->total_launches += nlaunch;
+        if (db->profiling) {
+            cudaEvent_t b = take_event(db);
+            cudaEventRecord(b, st);
+            db->recs.push_back({ph, a, b});
+        }
+    }
+};
 
 // Forward table width of a query with h bins.  ICT (FP32 distances): at most max_table_k
 // entries, rows ending where the largest database weight of the row is placed.
