@@ -306,7 +306,8 @@ def main():
     ap.add_argument("--cpu-queries", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0, help="default: same as --steps")
-    ap.add_argument("--precision", default="fp32_tc", choices=["fp32", "fp32_tc"])
+    ap.add_argument("--precision", default="fp32_tc", choices=["fp32", "fp32_tc", "bf16", "fp8"],
+                    help="Phase-1 arithmetic; bf16 / fp8 only with --probe, --ict, --allpairs")
     ap.add_argument("--serve-rates", default="1000,2000,4000",
                     help="offered request rates (requests/s) of the serving sweep; empty: skip it")
     ap.add_argument("--serve-requests", type=int, default=6000, help="requests per serving rate point")
@@ -336,6 +337,8 @@ def main():
 
     if args.impl == "reference":
         return main_reference(args, rank, world)
+    if args.precision in ("bf16", "fp8") and not (args.probe or args.ict or args.allpairs):
+        ap.error("the bench line runs fp32 or fp32_tc; the approximate forms are timed in its precision_forms")
     if args.probe:
         return main_probe(args, local)
     if args.k4:
@@ -623,7 +626,7 @@ def main_probe(args, local):
     B = args.batch
     db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
                            emd.emd_db_options_default(precision=args.precision, device=local, max_query_h=1024,
-                                                      max_batch=B, batch_columns=max(B * 128, 1024)))
+                                                      max_batch=B, batch_columns=max(B * 128, 1024), autotune=0))
     stream = torch.cuda.current_stream()
     oi = torch.empty((B, args.topk), dtype=torch.int64, device="cuda")
     od = torch.empty((B, args.topk), dtype=torch.float32, device="cuda")

@@ -282,6 +282,18 @@ emd_status emd_baseline_batch(emd_db* db, const emd_queries* q, emd_baseline kin
 emd_status emd_baseline_topk(emd_db* db, const emd_queries* q, emd_baseline kind, int32_t K, int64_t* out_idx,
                              float* out_dist);
 
+/* Database sharding (several processes or devices, each holding a contiguous slice of the
+ * documents in its own emd_db): the exact global top-K from the shards' top-K lists.
+ * Every document of the global top-K is among its own shard's K_shard >= K best, so the K
+ * smallest (distance, global id) pairs of the union are the answer; ties go to the lower
+ * global id, as in emd_topk.  shard_idx[s] / shard_dist[s]: n_queries x K_shard host arrays
+ * of shard s (local ids; negative ids are skipped); id_offset[s]: the global id of shard s's
+ * first document.  out_idx / out_dist: n_queries x K.  Host computation only (no device is
+ * needed); INVALID_ARG when a query has fewer than K results. */
+emd_status emd_topk_merge(int32_t n_shards, const int64_t* const* shard_idx, const float* const* shard_dist,
+                          const int64_t* id_offset, int64_t n_queries, int32_t K_shard, int32_t K,
+                          int64_t* out_idx, float* out_dist);
+
 /* ------------------------------------------------------------------ serving
  *
  * A request loop over a resident database.  Single queries are submitted as they arrive; a

@@ -21,7 +21,7 @@ __all__ = [
     "emd_db_profile_get", "emd_db_profile_reset", "emd_last_error", "emd_version",
     "emd_server_options_default", "emd_server_create", "emd_server_submit", "emd_server_poll",
     "emd_server_stats_get", "emd_server_stats_reset", "emd_server_destroy", "EmdError", "emd_all_pairs_topk",
-    "emd_baseline_batch", "emd_baseline_topk",
+    "emd_baseline_batch", "emd_baseline_topk", "emd_topk_merge",
     "MEASURES", "DIRECTIONS", "PRECISIONS", "PHASES", "library_path", "load",
 ]
 
@@ -114,6 +114,7 @@ def load():
     L.emd_db_profile_get.argtypes = [P, ctypes.POINTER(emd_profile)]
     L.emd_db_profile_reset.argtypes = [P]
     L.emd_all_pairs_topk.argtypes = [P, i32, i32, i32, P, P]
+    L.emd_topk_merge.argtypes = [i32, P, P, P, i64, i32, i32, P, P]
     L.emd_baseline_batch.argtypes = [P, P, i32, P]
     L.emd_baseline_topk.argtypes = [P, P, i32, i32, P, P]
     L.emd_server_options_default.argtypes = [ctypes.POINTER(emd_server_options)]
@@ -130,7 +131,7 @@ def load():
                  "emd_query_batch_device", "emd_topk_device", "emd_db_check_device_errors",
                  "emd_phase1_table", "emd_db_set_profiling", "emd_db_profile_get", "emd_topk_select_static",
                  "emd_db_profile_reset", "emd_all_pairs_topk", "emd_baseline_batch",
-                 "emd_baseline_topk", "emd_server_create", "emd_server_submit", "emd_server_poll",
+                 "emd_baseline_topk", "emd_topk_merge", "emd_server_create", "emd_server_submit", "emd_server_poll",
                  "emd_server_stats_get", "emd_server_stats_reset", "emd_server_destroy"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -329,6 +330,28 @@ def emd_all_pairs_topk(db, meas="act", k: int = 1, K: int = 16):
     out_dist = np.empty((n, K), dtype=np.float32)
     _check(load().emd_all_pairs_topk(db, _code(MEASURES, meas), int(k), int(K),
                                      out_idx.ctypes.data_as(ctypes.c_void_p), out_dist.ctypes.data_as(ctypes.c_void_p)))
+    return out_idx, out_dist
+
+
+def emd_topk_merge(shards, id_offsets, K: int):
+    """Exact global top-K from per-shard results: shards = [(idx int64[nq, Ks], dist
+    float32[nq, Ks]), ...] with local ids, id_offsets = each shard's first global id."""
+    n = len(shards)
+    if n < 1:
+        raise ValueError("no shard")
+    idx = [np.ascontiguousarray(s[0], dtype=np.int64) for s in shards]
+    dist = [np.ascontiguousarray(s[1], dtype=np.float32) for s in shards]
+    nq, ks = idx[0].shape
+    if any(a.shape != (nq, ks) for a in idx + dist):
+        raise ValueError("shard results must all be n_queries x K_shard")
+    pi = (ctypes.c_void_p * n)(*[a.ctypes.data for a in idx])
+    pd = (ctypes.c_void_p * n)(*[a.ctypes.data for a in dist])
+    offs = np.ascontiguousarray(id_offsets, dtype=np.int64)
+    out_idx = np.empty((nq, K), dtype=np.int64)
+    out_dist = np.empty((nq, K), dtype=np.float32)
+    _check(load().emd_topk_merge(n, ctypes.cast(pi, ctypes.c_void_p), ctypes.cast(pd, ctypes.c_void_p),
+                                 offs.ctypes.data_as(ctypes.c_void_p), nq, ks, int(K),
+                                 out_idx.ctypes.data_as(ctypes.c_void_p), out_dist.ctypes.data_as(ctypes.c_void_p)))
     return out_idx, out_dist
 
 
