@@ -184,13 +184,14 @@ emd_status run_phase1(emd_db* db, Lane& L, const int32_t* qidx, int h, cudaStrea
             EMD_CUDA(launch_pack(db->tcfmt, L.Q, db->ldm, db->m, h, round_up(h, 128), db->kpad, L.q_hi,
                                  db->tcfmt == TC_SPLIT ? L.q_lo : nullptr, L.q_scale, st), "query pack");
     }
-    Phase p(db, 1, 1, st);
-    if (db->tc)
+    Phase p(db, 1, db->tc ? 2 : 1, st);
+    if (db->tc) {
         EMD_CUDA(launch_tc_dist(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used, db->used_ids,
                                 db->v_used, L.q_hi, db->tcfmt == TC_SPLIT ? L.q_lo : nullptr, round_up(h, 128),
                                 L.q_scale, L.qnorm, qidx, h, db->kpad, L.D, ldd, db->err, st),
                  "distance matrix (tensor cores)");
-    else
+        EMD_CUDA(launch_zero_ident(qidx, h, db->vslot, L.D, ldd, st), "identical ids");
+    } else
         EMD_CUDA(launch_dist_fp32(db->emb_used, db->v_used, db->ldm, db->norm_used, db->used_ids, L.Q, h,
                                   db->ldm, L.qnorm, qidx, db->m, L.D, ldd, st), "distance matrix");
     return EMD_OK;
@@ -205,12 +206,13 @@ emd_status run_table(emd_db* db, Lane& L, const float* qw, int h, int meas, int 
     const int ldd = (int)round_up(h, 32);
     Phase p(db, 2, 1, st);
     if (meas == M_ICT && !db->approx)
-        EMD_CUDA(launch_table_ict(L.D, ldd, db->v_used, h, tk, qw, db->xmax, tab, tab_s, over, st), "ICT table");
+        EMD_CUDA(launch_table_ict(L.D, ldd, db->v_used, h, tk, qw, db->xmax, tab, tab_s, over, !db->cost_mode, st),
+                 "ICT table");
     else if (db->approx)
         EMD_CUDA(launch_table_rerank(L.D, ldd, db->v_used, h, tk, rerank_width(db, tk, h), db->emb_used, L.Q,
                                      db->ldm, qw, tab, tab_s, st), "top-k table (re-ranked)");
     else
-        EMD_CUDA(launch_table(L.D, ldd, db->v_used, h, tk, qw, tab, tab_s, st), "top-k table");
+        EMD_CUDA(launch_table(L.D, ldd, db->v_used, h, tk, qw, tab, tab_s, !db->cost_mode, st), "top-k table");
     return EMD_OK;
 }
 
@@ -242,7 +244,8 @@ emd_status run_query(emd_db* db, Lane& L, const int32_t* qidx, const float* qw, 
         Phase p(db, 4, 1, st);
         EMD_CUDA(launch_rev(meas, k, db->row_ptr, db->col, db->val, db->n, L.D, ldd, h, qw,
                             L.t_fwd, dir == EMD_DIR_REV ? out_t : L.t_rev,
-                            dir == EMD_DIR_MAX ? out_t : nullptr, nullptr, st), "reverse pass");
+                            dir == EMD_DIR_MAX ? out_t : nullptr, nullptr, !db->cost_mode, st),
+                 "reverse pass");
     }
     return EMD_OK;
 }
@@ -277,7 +280,8 @@ emd_status run_topk_pruned(emd_db* db, Lane& L, const int32_t* qidx, const float
     Phase p(db, 4, 3, st);
     EMD_CUDA(launch_prune(meas, k, db->row_ptr, db->col, db->val, db->n, L.D, ldd, h, qw, L.t_fwd,
                           L.sel_idx, L.sel_val, K, L.cand_idx, L.cand_count, L.cand_sym, out_idx,
-                          out_dist, ok, st), "pruned reverse pass");
+                          out_dist, ok, !db->cost_mode, st),
+             "pruned reverse pass");
     return EMD_OK;
 }
 
@@ -328,13 +332,14 @@ emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, i
                          "query pack");
         }
         if (db->tc && !hd) {
-            Phase p(db, 1, 1, st);
+            Phase p(db, 1, 2, st);
             EMD_CUDA(launch_tc_dist_batch(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
                                           db->used_ids, db->v_used, D_, nqd, B, db->kpad, db->tune_group_mult,
                                           db->tune_stages, db->err, st),
                      "distance matrices (tensor cores, batched)");
+            EMD_CUDA(launch_zero_ident_b(D_, nqd, B, H, db->vslot, st), "identical ids");
         } else if (db->tc) {
-            Phase p(db, 1, nb, st);
+            Phase p(db, 1, nb + 1, st);
             for (int q = 0; q < nb; ++q) {
                 const QDesc& d = hd[q];
                 EMD_CUDA(launch_tc_dist(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
@@ -342,6 +347,7 @@ emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, i
                                         d.h, db->kpad, d.D, d.ldd, db->err, st),
                          "distance matrix (tensor cores)");
             }
+            EMD_CUDA(launch_zero_ident_b(D_, nqd, B, H, db->vslot, st), "identical ids");
         } else {
             Phase p(db, 1, 1, st);
             EMD_CUDA(launch_dist_fp32_b(D_, nqd, B, db->ldd_max, db->emb_used, db->v_used, db->ldm, db->norm_used,
@@ -355,7 +361,7 @@ emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, i
             if (meas == M_ICT && !db->approx)
                 EMD_CUDA(launch_table_ict_b(D_, nqd, B, db->v_used, db->xmax, st), "ICT table");
             else
-                EMD_CUDA(launch_table_b(D_, nqd, B, db->v_used, tk_b, db->approx, kc_b, db->emb_used, db->ldm, st),
+                EMD_CUDA(launch_table_b(D_, nqd, B, db->v_used, tk_b, db->approx, kc_b, H, db->emb_used, db->ldm, st),
                          "top-k table");
         }
         Phase p(db, 3, 1, st);
@@ -553,6 +559,7 @@ emd_status fill_descriptors(BatchWS& ws, int slot, emd_db* db, const int64_t* rp
             d.ok = ws.cand_ok + b;
         }
         if (meas == M_ICT) d.over = ws.ict_over + b;
+        d.sq = db->cost_mode ? 0 : 1;
         if (K > 0) {
             d.out_idx = out_idx + (int64_t)b * K;
             d.out_dist = out_dist + (int64_t)b * K;
@@ -941,6 +948,9 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
         opt.max_table_k > (1 << 16) || opt.max_batch < 1 || opt.max_batch > 4096 || opt.lanes < 1 ||
         opt.lanes > 16 || opt.batch_columns < 1)
         return fail(EMD_ERR_INVALID_ARG, "option out of range");
+    if ((opt.precision == EMD_PREC_BF16 || opt.precision == EMD_PREC_FP8_E4M3) && opt.max_query_h > 6400)
+        return fail(EMD_ERR_INVALID_ARG, "max_query_h above 6400 with an approximate precision (the re-rank "
+                                         "stages 32 bytes per query bin in shared memory)");
     if (row_ptr[0] != 0) return fail(EMD_ERR_INVALID_ARG, "row_ptr[0] != 0");
     const int64_t nnz = row_ptr[n_docs];
     if (nnz >= (1ll << 31)) return fail(EMD_ERR_UNSUPPORTED, "nnz must be < 2^31");
@@ -1023,6 +1033,10 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
     TRY(dalloc(db, &db->err, 1));
     TRYC(cudaMemsetAsync(db->err, 0, sizeof(int), st), "memset");
     TRYC(cudaMemcpyAsync(db->used_ids, used_ids.data(), vu * sizeof(int32_t), cudaMemcpyHostToDevice, st), "copy");
+    TRY(dalloc(db, &db->vslot, v));
+    TRYC(launch_vslot(db->used_ids, vu, v, db->vslot, st), "vocabulary slots");
+    db->total_launches += 1;
+    db->launches[6] += 1;
     TRYC(cudaMemcpyAsync(db->row_ptr, rp32.data(), (n_docs + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st), "copy");
     TRYC(cudaMemcpyAsync(db->col, col_used.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st), "copy");
     TRYC(cudaMemcpyAsync(db->val, val, nnz * sizeof(float), cudaMemcpyHostToDevice, st), "copy");

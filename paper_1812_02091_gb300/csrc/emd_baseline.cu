@@ -20,7 +20,6 @@ cudaError_t launch_bow_sweep(const int32_t* row_ptr, const int32_t* col, const f
                              int64_t ldo, bool as_dist, cudaStream_t st);
 cudaError_t launch_doc_inv_norm(const int32_t* row_ptr, const float* val, int64_t n, float* inv_norm,
                                 cudaStream_t st);
-cudaError_t launch_vslot(const int32_t* used_ids, int64_t v_used, int64_t v, int32_t* vslot, cudaStream_t st);
 cudaError_t launch_doc_centroids(const int32_t* row_ptr, const int32_t* col, const float* val, int64_t n,
                                  const float* E, int lde, int m, float* C, int ldc, cudaStream_t st);
 cudaError_t launch_query_centroids(const int64_t* rp, int nq, const int32_t* idx, const float* w, const float* E,
@@ -60,15 +59,13 @@ emd_status prepare(emd_db* db, int kind)
     if (!db->base_rp) BTRY(balloc(db, &db->base_rp, (int64_t)db->opt.max_batch + 1));
     if (kind == EMD_BOW_COSINE && !db->bow_ready) {
         const int64_t groups = (db->opt.max_batch + kFwdGroup - 1) / kFwdGroup;
-        BTRY(balloc(db, &db->vslot, db->v));
         BTRY(balloc(db, &db->bow_dense, groups * db->v_used * kFwdGroup));
         BTRY(balloc(db, &db->doc_inv_norm, db->n));
         EMD_CUDA(cudaMemsetAsync(db->bow_dense, 0, (size_t)groups * db->v_used * kFwdGroup * sizeof(float), st),
                  "memset");
-        EMD_CUDA(launch_vslot(db->used_ids, db->v_used, db->v, db->vslot, st), "vocabulary slots");
         EMD_CUDA(launch_doc_inv_norm(db->row_ptr, db->val, db->n, db->doc_inv_norm, st), "document norms");
-        db->total_launches += 2;
-        db->launches[6] += 2;
+        db->total_launches += 1;
+        db->launches[6] += 1;
         db->bow_ready = true;
     }
     if (kind == EMD_WCD && !db->wcd_ready) {

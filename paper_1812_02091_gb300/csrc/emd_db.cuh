@@ -149,6 +149,7 @@ struct emd_db {
     int* cand_ok = nullptr;        // max_batch certification flags
     int* ict_over = nullptr;       // max_batch ICT table overflow flags (lanes path)
     float* xmax = nullptr;         // v_used, the largest database weight at each used row
+    int32_t* vslot = nullptr;      // v: used-vocabulary row of each id, -1 if unused
     int64_t stage_bins = 0;
     int32_t* stage_idx = nullptr;
     float* stage_w = nullptr;
@@ -182,7 +183,6 @@ struct emd_db {
     std::map<emd::GraphKey, emd::GraphEntry> graphs;
 
     // Section 5 baselines (allocated and prepared at first use)
-    int32_t* vslot = nullptr;       // v: used-vocabulary slot of each id, -1 if unused
     float* bow_dense = nullptr;     // ceil(max_batch / 8) x v_used x 8 interleaved query vectors
     float* doc_inv_norm = nullptr;  // n
     float* doc_centroid = nullptr;  // n x ldc (word centroid distance)

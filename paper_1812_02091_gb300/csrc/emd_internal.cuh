@@ -15,6 +15,13 @@ constexpr int kWarp = 32;
 // Measures as kernel template arguments (same numbering as emd_measure).
 enum : int { M_RWMD = 0, M_OMR = 1, M_ACT = 2, M_ICT = 3 };
 
+// Phase-1 matrices D of embedding databases hold squared distances |v_u - q_j|^2 (the
+// distance kernels leave the square root to the readers, which take it only for the
+// entries they use: the k table entries of a row, the distances a reverse pass gathers);
+// cost-matrix databases hold the costs themselves.  sq tells a reader which.
+__device__ __forceinline__ float sq_to_dist(float x) { return __fsqrt_rn(fmaxf(x, 0.f)); }
+__device__ __forceinline__ float d_value(float x, bool sq) { return sq ? sq_to_dist(x) : x; }
+
 // Device error latch bits (written by kernels, read by emd_db_check_device_errors).
 enum : int { ERR_BAD_INDEX = 1, ERR_TIMEOUT = 2 };
 
@@ -52,8 +59,8 @@ cudaError_t launch_gather_rows(const float* src, int64_t v, int ld, int m, const
                                int64_t nrows, int64_t nrows_pad, float* dst, float* norm2,
                                int* err, cudaStream_t st);
 
-// D[u, j] = Euclidean distance between A row u and B row j by the norm expansion,
-// exactly 0 when a_ids[u] == b_ids[j]; +inf for j in [N, ldd).
+// D[u, j] = squared Euclidean distance between A row u and B row j by the norm expansion
+// (unclamped), exactly 0 when a_ids[u] == b_ids[j]; +inf for j in [N, ldd).
 cudaError_t launch_dist_fp32(const float* A, int64_t M, int lda, const float* anorm,
                              const int32_t* a_ids, const float* B, int N, int ldb,
                              const float* bnorm, const int32_t* b_ids, int K, float* D,
@@ -65,9 +72,18 @@ cudaError_t launch_dist_gather(const float* cost, int64_t v, const int32_t* a_id
                                cudaStream_t st);
 
 // Phase-1 table (Section 4): per row u the k smallest D[u, 0..h) (ties by column),
-// written as tab[u * k + l] = (z, w = q_w[s]) and optionally tab_s[u * k + l] = s.
+// written as tab[u * k + l] = (z, w = q_w[s]) and optionally tab_s[u * k + l] = s; z is the
+// distance (the square root of the entry when sq).
 cudaError_t launch_table(const float* D, int ldd, int64_t M, int h, int k, const float* q_w,
-                         float2* tab, int32_t* tab_s, cudaStream_t st);
+                         float2* tab, int32_t* tab_s, bool sq, cudaStream_t st);
+
+// vslot[id] = the used-vocabulary row of each vocabulary id (v entries), -1 for unused ids.
+cudaError_t launch_vslot(const int32_t* used_ids, int64_t v_used, int64_t v, int32_t* vslot, cudaStream_t st);
+
+// Exact zeros of identical ids in squared-distance matrices: D[s(j), j] = 0 for every query
+// bin j whose vocabulary id has used row s(j) = vslot[q_idx[j]] >= 0.
+cudaError_t launch_zero_ident(const int32_t* q_idx, int h, const int32_t* vslot, float* D, int ldd,
+                              cudaStream_t st);
 
 // ICT table (Section 3.3, Algorithm 4, in the linear form of Section 4): per row u the
 // smallest D[u, 0..h) in ascending (distance, column) order, only as many as the largest
@@ -76,7 +92,7 @@ cudaError_t launch_table(const float* D, int ldd, int64_t M, int h, int k, const
 // that point are not written: no database weight at u reaches them.  A row that would need
 // more than W < h entries sets *over = 1 (the query's values are then incomplete).
 cudaError_t launch_table_ict(const float* D, int ldd, int64_t M, int h, int W, const float* q_w,
-                             const float* xmax, float2* tab, int32_t* tab_s, int* over, cudaStream_t st);
+                             const float* xmax, float2* tab, int32_t* tab_s, int* over, bool sq, cudaStream_t st);
 
 // Forward direction (Phase 2 and 3, Eq. 6-9): t_fwd[d] for every document.
 cudaError_t launch_fwd(int meas, const int32_t* row_ptr, const int32_t* col, const float* val,
@@ -90,21 +106,20 @@ cudaError_t launch_fwd(int meas, const int32_t* row_ptr, const int32_t* col, con
 cudaError_t launch_rev(int meas, int k, const int32_t* row_ptr, const int32_t* col,
                        const float* val, int64_t n, const float* D, int ldd, int h,
                        const float* q_w, const float* t_fwd, float* t_rev, float* t_max,
-                       const int64_t* doc_ids, cudaStream_t st);
+                       const int64_t* doc_ids, bool sq, cudaStream_t st);
 
 // Exact pruned symmetric top-K (K <= kPruneMaxK).  sel_val holds the K smallest forward
 // values (ascending); the candidates are the documents with fwd <= fwd_K (1 + 2^-7), at
 // most kPruneCap of them, and the reverse pass runs only there.  Writes the K smallest
 // (max(fwd, rev), id) among the candidates and ok = 1 when the K-th is <= that threshold
 // (then no other document can enter) and the candidates did not overflow.  cand holds
-// kPruneCap ids, sym 2 * kPruneCap values, count one int (all workspace).  ICT (k beyond
-// the register lists) is not served here.
+// kPruneCap ids, sym 2 * kPruneCap values, count one int (all workspace).
 constexpr int kPruneMaxK = 16;
 constexpr int kPruneCap = 256;
 cudaError_t launch_prune(int meas, int k, const int32_t* row_ptr, const int32_t* col, const float* val,
                          int64_t n, const float* D, int ldd, int h, const float* q_w, const float* t_fwd,
                          const int64_t* sel_idx, const float* sel_val, int K, int64_t* cand, int* count,
-                         float* sym, int64_t* out_idx, float* out_dist, int* ok, cudaStream_t st);
+                         float* sym, int64_t* out_idx, float* out_dist, int* ok, bool sq, cudaStream_t st);
 
 // Top-K smallest of t[0..n) by (value, index), into out_idx / out_dist (K <= kMaxTopK).
 // scratch must hold kTopkScratchRow uint64 keys.
@@ -175,6 +190,7 @@ struct QDesc {
     int* cand_count;
     int* ok;                // certification flag
     int* over;              // ICT: set to 1 when a table row needed more than tk entries
+    int sq;                 // D holds squared distances (embedding databases)
     int64_t* out_idx;       // K top-K result
     float* out_dist;
     int h, ldd, qrows, npad, tk, kc;
@@ -209,8 +225,11 @@ cudaError_t launch_tc_dist_batch(int fmt, const void* A_hi, const void* A_lo, in
                                  int max_q, int Kpad, int group_mult, int stages, int* err, cudaStream_t st);
 // max_tk: the largest table width of the batch; rerank: the approximate precisions' form
 // (V: the used vocabulary rows, ldv floats each).
+// Exact zeros of identical ids (launch_zero_ident) for every query of a batch.
+cudaError_t launch_zero_ident_b(const QDesc* qd, const int* nq, int max_q, int max_h, const int32_t* vslot,
+                                cudaStream_t st);
 cudaError_t launch_table_b(const QDesc* qd, const int* nq, int max_q, int64_t M, int max_tk, bool rerank,
-                           int max_kc, const float* V, int ldv, cudaStream_t st);
+                           int max_kc, int max_h, const float* V, int ldv, cudaStream_t st);
 // The ICT table of every query of a batch (width qd[q].tk, overflow flag qd[q].over).
 cudaError_t launch_table_ict_b(const QDesc* qd, const int* nq, int max_q, int64_t M, const float* xmax,
                                cudaStream_t st);

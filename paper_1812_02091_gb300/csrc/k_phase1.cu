@@ -6,6 +6,8 @@
 // workloads, and the per-row top-k selection shared by every precision.
 #include <math.h>
 
+#include <algorithm>
+
 #include "emd_internal.cuh"
 
 namespace emd {
@@ -146,7 +148,7 @@ __device__ __forceinline__ void dist_fp32_body(const float* __restrict__ A, int6
         __syncthreads();
     }
 
-    // epilogue: d = sqrt(max(|a|^2 + |b|^2 - 2<a,b>, 0)); identical ids give exactly 0
+    // epilogue: the squared distance |a|^2 + |b|^2 - 2<a,b> (unclamped); identical ids give exactly 0
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int64_t row = m0 + (i < 4 ? tr * 4 + i : 64 + tr * 4 + (i - 4));
@@ -163,8 +165,8 @@ __device__ __forceinline__ void dist_fp32_body(const float* __restrict__ A, int6
                 const int col = col0 + e;
                 float d = INFINITY;
                 if (col < N) {
-                    float d2 = fmaf(-2.f, acc[i][jh * 4 + e], an + bnorm[col]);
-                    d = (aid == b_ids[col]) ? 0.f : sqrtf(fmaxf(d2, 0.f));
+                    const float d2 = fmaf(-2.f, acc[i][jh * 4 + e], an + bnorm[col]);
+                    d = (aid == b_ids[col]) ? 0.f : d2;
                 }
                 o[e] = d;
             }
@@ -220,6 +222,21 @@ __global__ void k_dist_gather(const float* __restrict__ cost, int64_t v,
 // and kept in a branch-free sorted register list of the KT smallest (d, j); strict '<'
 // keeps the earlier column first on equal d, the order the definition uses.
 
+template <int KCT>
+__device__ __forceinline__ void insert_dj_tie(float (&z)[KCT], int (&s)[KCT], float d, int j)
+{
+    bool p[KCT];
+#pragma unroll
+    for (int l = 0; l < KCT; ++l) p[l] = d < z[l] || (d == z[l] && j < s[l]);
+#pragma unroll
+    for (int l = KCT - 1; l > 0; --l) {
+        z[l] = p[l - 1] ? z[l - 1] : (p[l] ? d : z[l]);
+        s[l] = p[l - 1] ? s[l - 1] : (p[l] ? j : s[l]);
+    }
+    z[0] = p[0] ? d : z[0];
+    s[0] = p[0] ? j : s[0];
+}
+
 template <int KT>
 __device__ __forceinline__ void insert_dj(float (&z)[KT], int (&s)[KT], float d, int j)
 {
@@ -237,27 +254,37 @@ __device__ __forceinline__ void insert_dj(float (&z)[KT], int (&s)[KT], float d,
 
 template <int KT>
 __device__ __forceinline__ void table_body(const float* __restrict__ D, int ldd, int64_t M, int h, int k, const float* __restrict__ q_w,
-        float2* __restrict__ tab, int32_t* __restrict__ tab_s, int rs, int es)
+        float2* __restrict__ tab, int32_t* __restrict__ tab_s, int rs, int es, bool sq)
 {
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= M) return;
     const float* Dr = D + row * ldd;
-    float z[KT];
-    int s[KT];
+    // two independent lists (columns 8i..8i+3 and 8i+4..8i+7, ldd % 32 == 0 so both loads
+    // stay in the row) for instruction-level parallelism, merged by (value, column)
+    float z[KT], zb[KT];
+    int s[KT], sb[KT];
 #pragma unroll
-    for (int l = 0; l < KT; ++l) { z[l] = INFINITY; s[l] = INT32_MAX; }
-    for (int j = 0; j < h; j += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(Dr + j);  // ldd % 32 == 0, padding +inf
+    for (int l = 0; l < KT; ++l) { z[l] = zb[l] = INFINITY; s[l] = sb[l] = INT32_MAX; }
+    for (int j = 0; j < h; j += 8) {
+        const float4 v = *reinterpret_cast<const float4*>(Dr + j);
+        const float4 w = *reinterpret_cast<const float4*>(Dr + j + 4);
         insert_dj<KT>(z, s, v.x, j);
+        if (j + 4 < h) insert_dj<KT>(zb, sb, w.x, j + 4);
         if (j + 1 < h) insert_dj<KT>(z, s, v.y, j + 1);
+        if (j + 5 < h) insert_dj<KT>(zb, sb, w.y, j + 5);
         if (j + 2 < h) insert_dj<KT>(z, s, v.z, j + 2);
+        if (j + 6 < h) insert_dj<KT>(zb, sb, w.z, j + 6);
         if (j + 3 < h) insert_dj<KT>(z, s, v.w, j + 3);
+        if (j + 7 < h) insert_dj<KT>(zb, sb, w.w, j + 7);
     }
+#pragma unroll
+    for (int l = 0; l < KT; ++l)
+        if (sb[l] != INT32_MAX) insert_dj_tie<KT>(z, s, zb[l], sb[l]);
 #pragma unroll
     for (int l = 0; l < KT; ++l) {
         if (l < k) {
             const bool valid = s[l] != INT32_MAX;
-            tab[row * rs + l * es] = make_float2(valid ? z[l] : INFINITY, valid ? q_w[s[l]] : 0.f);
+            tab[row * rs + l * es] = make_float2(valid ? d_value(z[l], sq) : INFINITY, valid ? q_w[s[l]] : 0.f);
             if (tab_s) tab_s[row * k + l] = valid ? s[l] : -1;
         }
     }
@@ -265,16 +292,16 @@ __device__ __forceinline__ void table_body(const float* __restrict__ D, int ldd,
 
 template <int KT>
 __global__ void __launch_bounds__(128) k_table(const float* __restrict__ D, int ldd, int64_t M, int h, int k, const float* __restrict__ q_w,
-        float2* __restrict__ tab, int32_t* __restrict__ tab_s)
+        float2* __restrict__ tab, int32_t* __restrict__ tab_s, bool sq)
 {
-    table_body<KT>(D, ldd, M, h, k, q_w, tab, tab_s, k, 1);
+    table_body<KT>(D, ldd, M, h, k, q_w, tab, tab_s, k, 1, sq);
 }
 
 // k larger than the register lists: successive minima, each strictly after the previous
 // in (d, j) order.  O(k * h / 32) per lane; used for ICT on small queries.
 __device__ __forceinline__ void table_generic_body(const float* __restrict__ D, int ldd, int64_t M, int h, int k,
                                 const float* __restrict__ q_w, float2* __restrict__ tab,
-                                int32_t* __restrict__ tab_s, int rs, int es)
+                                int32_t* __restrict__ tab_s, int rs, int es, bool sq)
 {
     const int lane = threadIdx.x & 31;
     const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -298,7 +325,7 @@ __device__ __forceinline__ void table_generic_body(const float* __restrict__ D, 
         }
         if (lane == 0) {
             const bool valid = bs != INT32_MAX;
-            tab[row * rs + l * es] = make_float2(valid ? bz : INFINITY, valid ? q_w[bs] : 0.f);
+            tab[row * rs + l * es] = make_float2(valid ? d_value(bz, sq) : INFINITY, valid ? q_w[bs] : 0.f);
             if (tab_s) tab_s[row * k + l] = valid ? bs : -1;
         }
         pz = bz;
@@ -314,7 +341,7 @@ __device__ __forceinline__ void table_generic_body(const float* __restrict__ D, 
 __device__ __forceinline__ void table_ict_body(const float* __restrict__ D, int ldd, int64_t M, int h, int W,
                                                const float* __restrict__ q_w, const float* __restrict__ xmax,
                                                float2* __restrict__ tab, int32_t* __restrict__ tab_s, int rs,
-                                               int es, int* __restrict__ over)
+                                               int es, int* __restrict__ over, bool sq)
 {
     const int lane = threadIdx.x & 31;
     const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -341,7 +368,7 @@ __device__ __forceinline__ void table_ict_body(const float* __restrict__ D, int 
         const bool valid = bs != INT32_MAX;  // always while l < h, unless D holds NaN
         const float w = valid ? q_w[bs] : 0.f;
         if (lane == 0) {
-            tab[row * rs + (int64_t)l * es] = make_float2(valid ? bz : INFINITY, w);
+            tab[row * rs + (int64_t)l * es] = make_float2(valid ? d_value(bz, sq) : INFINITY, w);
             if (tab_s) tab_s[row * W + l] = valid ? bs : -1;
         }
         if (!valid) break;
@@ -355,55 +382,52 @@ __device__ __forceinline__ void table_ict_body(const float* __restrict__ D, int 
 
 __global__ void k_table_ict(const float* __restrict__ D, int ldd, int64_t M, int h, int W,
                             const float* __restrict__ q_w, const float* __restrict__ xmax, float2* __restrict__ tab,
-                            int32_t* __restrict__ tab_s, int* __restrict__ over)
+                            int32_t* __restrict__ tab_s, int* __restrict__ over, bool sq)
 {
-    table_ict_body(D, ldd, M, h, W, q_w, xmax, tab, tab_s, W, 1, over);
+    table_ict_body(D, ldd, M, h, W, q_w, xmax, tab, tab_s, W, 1, over, sq);
 }
 
 __global__ void k_table_generic(const float* __restrict__ D, int ldd, int64_t M, int h, int k,
                                 const float* __restrict__ q_w, float2* __restrict__ tab,
-                                int32_t* __restrict__ tab_s)
+                                int32_t* __restrict__ tab_s, bool sq)
 {
-    table_generic_body(D, ldd, M, h, k, q_w, tab, tab_s, k, 1);
+    table_generic_body(D, ldd, M, h, k, q_w, tab, tab_s, k, 1, sq);
 }
 
 // Re-rank form of the table, for approximate distance matrices (BF16 / E4M3 Phase 1).
-// Per vocabulary row u: the kc smallest approximate D[u, .] (ties: lower j) are the
-// candidates; their distances are recomputed exactly in FP32 as sqrt(sum_i (V_u,i -
-// Q_j,i)^2) -- differences, not the norm expansion -- and written back into D; the k
-// smallest exact values (ties: lower j) form the table.  Selection runs one thread per
+// Per vocabulary row u: the kc smallest approximate D[u, .] (squared distances; ties: lower
+// j) are the candidates; their squared distances are recomputed exactly in FP32 as
+// sum_i (V_u,i - Q_j,i)^2 -- differences, not the norm expansion -- and written back into D;
+// the k smallest exact values (ties: lower j) form the table, with z = their square roots.  Selection runs one thread per
 // row, the recomputation one warp per row (lanes over float4 slices of the embedding;
 // rows are zero beyond m, so the padded width adds nothing).
-template <int KCT>
-__device__ __forceinline__ void insert_dj_tie(float (&z)[KCT], int (&s)[KCT], float d, int j)
-{
-    bool p[KCT];
-#pragma unroll
-    for (int l = 0; l < KCT; ++l) p[l] = d < z[l] || (d == z[l] && j < s[l]);
-#pragma unroll
-    for (int l = KCT - 1; l > 0; --l) {
-        z[l] = p[l - 1] ? z[l - 1] : (p[l] ? d : z[l]);
-        s[l] = p[l - 1] ? s[l - 1] : (p[l] ? j : s[l]);
-    }
-    z[0] = p[0] ? d : z[0];
-    s[0] = p[0] ? j : s[0];
-}
+
+// Block: kRrRows rows, one thread each.  Selection as in table_body (each thread scans its
+// own row, four entries per load).  Exact sums: over the embedding in chunks of kRrDims
+// dimensions, the chunk of every query row staged in shared memory once per block, each
+// thread holding its own row's chunk in registers and adding the squared differences to
+// each of its kc candidates (sequential over the dimensions).  Then the k smallest exact
+// sums (ties: lower j) are selected and the exact squared distances written back into D.
+// Dynamic shared memory: rerank_smem_bytes(h).
+constexpr int kRrRows = 256, kRrDims = 8;
+
+__host__ __device__ constexpr size_t rerank_smem_bytes(int h) { return (size_t)h * kRrDims * 4; }
 
 template <int KCT>
 __device__ __forceinline__ void table_rerank_body(float* __restrict__ D, int ldd, int64_t M, int h, int k, int kc, const float* __restrict__ V,
                const float* __restrict__ Q, int ldv, const float* __restrict__ q_w, float2* __restrict__ tab,
                int32_t* __restrict__ tab_s, int64_t tile, int rs, int es)
 {
-    __shared__ int cj[128][KCT + 1];
-    __shared__ float cz[128][KCT + 1];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t row = tile * 128 + tid;
+    extern __shared__ float4 qs4[];  // [h][2]: Q[j][d0 .. d0 + 8)
+    const int tid = threadIdx.x;
+    const int64_t row = tile * kRrRows + tid;
+    const bool rok = row < M;
+    int s[KCT];
     {
         float z[KCT];
-        int s[KCT];
 #pragma unroll
         for (int l = 0; l < KCT; ++l) { z[l] = INFINITY; s[l] = INT32_MAX; }
-        if (row < M) {
+        if (rok) {
             const float* Dr = D + row * ldd;
             for (int j = 0; j < h; j += 4) {
                 const float4 v = *reinterpret_cast<const float4*>(Dr + j);
@@ -413,56 +437,70 @@ __device__ __forceinline__ void table_rerank_body(float* __restrict__ D, int ldd
                 if (j + 3 < h) insert_dj<KCT>(z, s, v.w, j + 3);
             }
         }
-#pragma unroll
-        for (int l = 0; l < KCT; ++l) cj[tid][l] = s[l];
     }
-    __syncwarp();
-    const int nv4 = ldv >> 2;
-    for (int r = 0; r < 32; ++r) {
-        const int64_t ur = tile * 128 + warp * 32 + r;
-        if (ur >= M) break;  // uniform over the warp
-        const float4* vr = reinterpret_cast<const float4*>(V + ur * ldv);
-        for (int c = 0; c < kc; ++c) {
-            const int j = cj[warp * 32 + r][c];
-            const float4* qr = reinterpret_cast<const float4*>(Q + (int64_t)j * ldv);
-            float acc = 0.f;
-            for (int i = lane; i < nv4; i += 32) {
-                const float4 a = vr[i], b = qr[i];
-                const float t0 = a.x - b.x, t1 = a.y - b.y, t2 = a.z - b.z, t3 = a.w - b.w;
-                acc = fmaf(t0, t0, acc);
-                acc = fmaf(t1, t1, acc);
-                acc = fmaf(t2, t2, acc);
-                acc = fmaf(t3, t3, acc);
-            }
+    float acc[KCT];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) cz[warp * 32 + r][c] = __fsqrt_rn(acc);
+    for (int l = 0; l < KCT; ++l) acc[l] = 0.f;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int d0 = 0; d0 < ldv; d0 += kRrDims) {
+        __syncthreads();  // the previous chunk's readers are done
+        for (int t = tid; t < 2 * h; t += blockDim.x) {
+            const int dd = d0 + 4 * (t & 1);
+            qs4[t] = dd < ldv ? *reinterpret_cast<const float4*>(Q + (int64_t)(t >> 1) * ldv + dd) : zero4;
+        }
+        float4 v0 = zero4, v1 = zero4;
+        if (rok) {
+            v0 = *reinterpret_cast<const float4*>(V + row * ldv + d0);
+            if (d0 + 4 < ldv) v1 = *reinterpret_cast<const float4*>(V + row * ldv + d0 + 4);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < KCT; ++c) {
+            if (c < kc && s[c] != INT32_MAX) {
+                const float4 a = qs4[2 * s[c]], b = qs4[2 * s[c] + 1];
+                float t = v0.x - a.x;
+                acc[c] = fmaf(t, t, acc[c]);
+                t = v0.y - a.y;
+                acc[c] = fmaf(t, t, acc[c]);
+                t = v0.z - a.z;
+                acc[c] = fmaf(t, t, acc[c]);
+                t = v0.w - a.w;
+                acc[c] = fmaf(t, t, acc[c]);
+                t = v1.x - b.x;
+                acc[c] = fmaf(t, t, acc[c]);
+                t = v1.y - b.y;
+                acc[c] = fmaf(t, t, acc[c]);
+                t = v1.z - b.z;
+                acc[c] = fmaf(t, t, acc[c]);
+                t = v1.w - b.w;
+                acc[c] = fmaf(t, t, acc[c]);
+            }
         }
     }
-    __syncwarp();
-    if (row >= M) return;
+    if (!rok) return;
     float z[KCT];
-    int s[KCT];
+    int s2[KCT];
 #pragma unroll
-    for (int l = 0; l < KCT; ++l) { z[l] = INFINITY; s[l] = INT32_MAX; }
-    for (int c = 0; c < kc; ++c) {
-        const float d = cz[tid][c];
-        const int j = cj[tid][c];
-        D[row * ldd + j] = d;
-        insert_dj_tie<KCT>(z, s, d, j);
+    for (int l = 0; l < KCT; ++l) { z[l] = INFINITY; s2[l] = INT32_MAX; }
+#pragma unroll
+    for (int c = 0; c < KCT; ++c) {
+        if (c < kc && s[c] != INT32_MAX) {
+            D[row * ldd + s[c]] = acc[c];
+            insert_dj_tie<KCT>(z, s2, acc[c], s[c]);
+        }
     }
 #pragma unroll
     for (int l = 0; l < KCT; ++l) {
         if (l < k) {
-            const bool valid = s[l] != INT32_MAX;
-            tab[row * rs + l * es] = make_float2(valid ? z[l] : INFINITY, valid ? q_w[s[l]] : 0.f);
-            if (tab_s) tab_s[row * k + l] = valid ? s[l] : -1;
+            const bool valid = s2[l] != INT32_MAX;
+            tab[row * rs + l * es] = make_float2(valid ? sq_to_dist(z[l]) : INFINITY, valid ? q_w[s2[l]] : 0.f);
+            if (tab_s) tab_s[row * k + l] = valid ? s2[l] : -1;
         }
     }
 }
 
 template <int KCT>
-__global__ void __launch_bounds__(128) k_table_rerank(float* __restrict__ D, int ldd, int64_t M, int h, int k, int kc, const float* __restrict__ V,
+__global__ void __launch_bounds__(kRrRows) k_table_rerank(float* __restrict__ D, int ldd, int64_t M, int h, int k, int kc, const float* __restrict__ V,
                const float* __restrict__ Q, int ldv, const float* __restrict__ q_w, float2* __restrict__ tab,
                int32_t* __restrict__ tab_s)
 {
@@ -503,7 +541,31 @@ k_table_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t M)
 {
     if ((int)blockIdx.y >= *nq) return;
     const QDesc& d = qd[blockIdx.y];
-    table_body<KT>(d.D, d.ldd, M, d.h, d.tk, d.qw, d.tab, nullptr, d.tab_rs, d.tab_es);
+    table_body<KT>(d.D, d.ldd, M, d.h, d.tk, d.qw, d.tab, nullptr, d.tab_rs, d.tab_es, d.sq != 0);
+}
+
+// D[vslot[q_idx[j]], j] = 0 for the query bins whose id is a used vocabulary row.
+__device__ __forceinline__ void zero_ident_body(const int32_t* __restrict__ q_idx, int h,
+                                                const int32_t* __restrict__ vslot, float* __restrict__ D, int ldd)
+{
+    for (int j = threadIdx.x; j < h; j += blockDim.x) {
+        const int32_t s = vslot[q_idx[j]];
+        if (s >= 0) D[(int64_t)s * ldd + j] = 0.f;
+    }
+}
+
+__global__ void k_zero_ident(const int32_t* __restrict__ q_idx, int h, const int32_t* __restrict__ vslot,
+                             float* __restrict__ D, int ldd)
+{
+    zero_ident_body(q_idx, h, vslot, D, ldd);
+}
+
+__global__ void k_zero_ident_b(const QDesc* __restrict__ qd, const int* __restrict__ nq,
+                               const int32_t* __restrict__ vslot)
+{
+    if ((int)blockIdx.x >= *nq) return;
+    const QDesc& d = qd[blockIdx.x];
+    zero_ident_body(d.qidx, d.h, vslot, d.D, d.ldd);
 }
 
 __global__ void k_table_ict_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t M,
@@ -511,20 +573,20 @@ __global__ void k_table_ict_b(const QDesc* __restrict__ qd, const int* __restric
 {
     if ((int)blockIdx.y >= *nq) return;
     const QDesc& d = qd[blockIdx.y];
-    table_ict_body(d.D, d.ldd, M, d.h, d.tk, d.qw, xmax, d.tab, nullptr, d.tab_rs, d.tab_es, d.over);
+    table_ict_body(d.D, d.ldd, M, d.h, d.tk, d.qw, xmax, d.tab, nullptr, d.tab_rs, d.tab_es, d.over, d.sq != 0);
 }
 
 __global__ void k_table_generic_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t M)
 {
     if ((int)blockIdx.y >= *nq) return;
     const QDesc& d = qd[blockIdx.y];
-    table_generic_body(d.D, d.ldd, M, d.h, d.tk, d.qw, d.tab, nullptr, d.tab_rs, d.tab_es);
+    table_generic_body(d.D, d.ldd, M, d.h, d.tk, d.qw, d.tab, nullptr, d.tab_rs, d.tab_es, d.sq != 0);
 }
 
 // Queries vary fastest (blockIdx.x) so that the blocks of one vocabulary tile for all
 // queries of the batch run together and its FP32 rows are read from HBM once.
 template <int KCT>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kRrRows)
 k_table_rerank_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t M, const float* __restrict__ V,
                  int ldv)
 {
@@ -532,6 +594,22 @@ k_table_rerank_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64
     const QDesc& d = qd[blockIdx.x];
     table_rerank_body<KCT>(d.D, d.ldd, M, d.h, d.tk, d.kc, V, d.Q, ldv, d.qw, d.tab, nullptr, blockIdx.y, d.tab_rs,
                            d.tab_es);
+}
+
+// Opt-in dynamic shared memory of the re-rank kernels (above 48 KB for long queries).
+cudaError_t rerank_smem_attr(size_t smem)
+{
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    const int b = (int)std::max<size_t>(smem, 1);
+    cudaError_t e = cudaFuncSetAttribute(k_table_rerank<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_table_rerank<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_table_rerank_b<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_table_rerank<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_table_rerank<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_table_rerank_b<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_table_rerank_b<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_table_rerank_b<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    return e;
 }
 
 }  // namespace
@@ -568,31 +646,39 @@ cudaError_t launch_dist_gather(const float* cost, int64_t v, const int32_t* a_id
 }
 
 cudaError_t launch_table(const float* D, int ldd, int64_t M, int h, int k, const float* q_w,
-                         float2* tab, int32_t* tab_s, cudaStream_t st)
+                         float2* tab, int32_t* tab_s, bool sq, cudaStream_t st)
 {
     if (M <= 0) return cudaSuccess;
     const dim3 tgrid((unsigned)((M + 127) / 128));
-    if (k <= 1) k_table<1><<<tgrid, 128, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
-    else if (k <= 2) k_table<2><<<tgrid, 128, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
-    else if (k <= 4) k_table<4><<<tgrid, 128, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
-    else if (k <= 8) k_table<8><<<tgrid, 128, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
-    else if (k <= 16) k_table<16><<<tgrid, 128, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
+    if (k <= 1) k_table<1><<<tgrid, 128, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s, sq);
+    else if (k <= 2) k_table<2><<<tgrid, 128, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s, sq);
+    else if (k <= 4) k_table<4><<<tgrid, 128, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s, sq);
+    else if (k <= 8) k_table<8><<<tgrid, 128, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s, sq);
+    else if (k <= 16) k_table<16><<<tgrid, 128, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s, sq);
     else {
         const int warps = 8;
         dim3 grid((unsigned)((M + warps - 1) / warps));
-        k_table_generic<<<grid, warps * 32, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s);
+        k_table_generic<<<grid, warps * 32, 0, st>>>(D, ldd, M, h, k, q_w, tab, tab_s, sq);
     }
     return cudaGetLastError();
 }
 
+cudaError_t launch_zero_ident(const int32_t* q_idx, int h, const int32_t* vslot, float* D, int ldd,
+                              cudaStream_t st)
+{
+    if (h <= 0) return cudaSuccess;
+    k_zero_ident<<<1, 256, 0, st>>>(q_idx, h, vslot, D, ldd);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_table_ict(const float* D, int ldd, int64_t M, int h, int W, const float* q_w,
-                             const float* xmax, float2* tab, int32_t* tab_s, int* over, cudaStream_t st)
+                             const float* xmax, float2* tab, int32_t* tab_s, int* over, bool sq, cudaStream_t st)
 {
     if (M <= 0) return cudaSuccess;
     if (W < 1 || h < 1) return cudaErrorInvalidValue;
     const int warps = 8;
     k_table_ict<<<(unsigned)((M + warps - 1) / warps), warps * 32, 0, st>>>(D, ldd, M, h, W, q_w, xmax, tab, tab_s,
-                                                                           over);
+                                                                           over, sq);
     return cudaGetLastError();
 }
 
@@ -605,11 +691,15 @@ cudaError_t launch_table_rerank(float* D, int ldd, int64_t M, int h, int k, int 
                                 cudaStream_t st)
 {
     if (M <= 0) return cudaSuccess;
-    if (k < 1 || kc < k || kc > h || kc > kRerankMax) return cudaErrorInvalidValue;
-    const unsigned grid = (unsigned)((M + 127) / 128);
-    if (kc <= 8) k_table_rerank<8><<<grid, 128, 0, st>>>(D, ldd, M, h, k, kc, V, Q, ldv, q_w, tab, tab_s);
-    else if (kc <= 16) k_table_rerank<16><<<grid, 128, 0, st>>>(D, ldd, M, h, k, kc, V, Q, ldv, q_w, tab, tab_s);
-    else k_table_rerank<32><<<grid, 128, 0, st>>>(D, ldd, M, h, k, kc, V, Q, ldv, q_w, tab, tab_s);
+    if (k < 1 || kc < k || kc > h || kc > kRerankMax || ldv % 4 != 0) return cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)((M + kRrRows - 1) / kRrRows);
+    const size_t smem = rerank_smem_bytes(h);
+    cudaError_t e = rerank_smem_attr(smem);
+    if (e != cudaSuccess) return e;
+    if (kc <= 8) k_table_rerank<8><<<grid, kRrRows, smem, st>>>(D, ldd, M, h, k, kc, V, Q, ldv, q_w, tab, tab_s);
+    else if (kc <= 12) k_table_rerank<12><<<grid, kRrRows, smem, st>>>(D, ldd, M, h, k, kc, V, Q, ldv, q_w, tab, tab_s);
+    else if (kc <= 16) k_table_rerank<16><<<grid, kRrRows, smem, st>>>(D, ldd, M, h, k, kc, V, Q, ldv, q_w, tab, tab_s);
+    else k_table_rerank<32><<<grid, kRrRows, smem, st>>>(D, ldd, M, h, k, kc, V, Q, ldv, q_w, tab, tab_s);
     return cudaGetLastError();
 }
 
@@ -644,6 +734,14 @@ cudaError_t launch_dist_gather_b(const QDesc* qd, const int* nq, int max_q, cons
     return cudaGetLastError();
 }
 
+cudaError_t launch_zero_ident_b(const QDesc* qd, const int* nq, int max_q, int max_h, const int32_t* vslot,
+                                cudaStream_t st)
+{
+    if (max_q <= 0 || max_h <= 0) return cudaSuccess;
+    k_zero_ident_b<<<(unsigned)max_q, 256, 0, st>>>(qd, nq, vslot);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_table_ict_b(const QDesc* qd, const int* nq, int max_q, int64_t M, const float* xmax,
                                cudaStream_t st)
 {
@@ -654,16 +752,21 @@ cudaError_t launch_table_ict_b(const QDesc* qd, const int* nq, int max_q, int64_
 }
 
 cudaError_t launch_table_b(const QDesc* qd, const int* nq, int max_q, int64_t M, int max_tk, bool rerank,
-                           int max_kc, const float* V, int ldv, cudaStream_t st)
+                           int max_kc, int max_h, const float* V, int ldv, cudaStream_t st)
 {
     if (max_q <= 0 || M <= 0) return cudaSuccess;
     const dim3 g((unsigned)((M + 127) / 128), (unsigned)max_q);
     if (rerank) {
-        if (max_kc > kRerankMax || (M + 127) / 128 > 65535) return cudaErrorInvalidValue;
-        const dim3 gq((unsigned)max_q, (unsigned)((M + 127) / 128));
-        if (max_kc <= 8) k_table_rerank_b<8><<<gq, 128, 0, st>>>(qd, nq, M, V, ldv);
-        else if (max_kc <= 16) k_table_rerank_b<16><<<gq, 128, 0, st>>>(qd, nq, M, V, ldv);
-        else k_table_rerank_b<32><<<gq, 128, 0, st>>>(qd, nq, M, V, ldv);
+        const int64_t tiles = (M + kRrRows - 1) / kRrRows;
+        if (max_kc > kRerankMax || tiles > 65535 || ldv % 4 != 0) return cudaErrorInvalidValue;
+        const dim3 gq((unsigned)max_q, (unsigned)tiles);
+        const size_t smem = rerank_smem_bytes(max_h);
+        cudaError_t e = rerank_smem_attr(smem);
+        if (e != cudaSuccess) return e;
+        if (max_kc <= 8) k_table_rerank_b<8><<<gq, kRrRows, smem, st>>>(qd, nq, M, V, ldv);
+        else if (max_kc <= 12) k_table_rerank_b<12><<<gq, kRrRows, smem, st>>>(qd, nq, M, V, ldv);
+        else if (max_kc <= 16) k_table_rerank_b<16><<<gq, kRrRows, smem, st>>>(qd, nq, M, V, ldv);
+        else k_table_rerank_b<32><<<gq, kRrRows, smem, st>>>(qd, nq, M, V, ldv);
     } else if (max_tk <= 1) k_table_b<1><<<g, 128, 0, st>>>(qd, nq, M);
     else if (max_tk <= 2) k_table_b<2><<<g, 128, 0, st>>>(qd, nq, M);
     else if (max_tk <= 4) k_table_b<4><<<g, 128, 0, st>>>(qd, nq, M);

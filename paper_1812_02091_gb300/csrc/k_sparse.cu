@@ -24,18 +24,20 @@ __device__ __forceinline__ float warp_sum(float x)
 // document (t_fwd).  One warp per document, lanes over its nonzeros (coalesced col/val
 // loads), table rows gathered from L2, warp-shuffle sum.
 
-// Cost of one nonzero along its table row T (entries es apart).
+// Cost of one nonzero along its table row T (entries es apart).  Products and sums that the
+// compiler could otherwise contract into an FMA in one kernel and not in another are written
+// with __fmul_rn / __fadd_rn, so every kernel that shares these bodies rounds alike.
 template <int MEAS>
 __device__ __forceinline__ float fwd_cost_s(float x, const float2* __restrict__ T, int es, int keff)
 {
-    if (MEAS == M_RWMD) return x * T[0].x;
+    if (MEAS == M_RWMD) return __fmul_rn(x, T[0].x);
     if (MEAS == M_OMR) {
         const float2 t0 = T[0];
         if (t0.x == 0.f && keff >= 2) {
             const float r = x - fminf(x, t0.y);  // free transfer to the overlapping bin
-            return r != 0.f ? r * T[es].x : 0.f;
+            return r != 0.f ? __fmul_rn(r, T[es].x) : 0.f;
         }
-        return x * t0.x;
+        return __fmul_rn(x, t0.x);
     }
     float r = x, c = 0.f;
     for (int l = 0; l < keff - 1; ++l) {
@@ -93,7 +95,8 @@ __device__ __forceinline__ void fwd_body(const int32_t* __restrict__ row_ptr, co
         const bool valid = d < n;
         const int32_t a = valid ? row_ptr[d] : 0, b = valid ? row_ptr[d + 1] : 0;
         float acc = 0.f;
-        for (int32_t e = a + ph; e < b; e += 4) acc += fwd_cost_p<MEAS, KT>(val[e], tab + (int64_t)col[e] * k, 1, keff);
+        for (int32_t e = a + ph; e < b; e += 4)
+            acc = __fadd_rn(acc, fwd_cost_p<MEAS, KT>(val[e], tab + (int64_t)col[e] * k, 1, keff));
         acc += __shfl_xor_sync(0xffffffffu, acc, 8);
         acc += __shfl_xor_sync(0xffffffffu, acc, 16);
         if (ph == 0 && valid) t_fwd[d] = acc;
@@ -124,17 +127,22 @@ __global__ void k_fwd(const int32_t* __restrict__ row_ptr, const int32_t* __rest
 // Cost of moving source mass qj along a sorted destination list (Alg. 3 / Alg. 1).  The loop
 // runs over the compile-time width with predicates so that the lists stay in registers;
 // transfers after the residual reaches zero add exactly zero.
+// sq: the lists hold squared distances (ordered the same way); they are converted here,
+// KT square roots per query bin instead of one per gathered entry.
 template <int MEAS, int KT>
-__device__ __forceinline__ float rev_cost_sorted(float qj, const float (&z)[KT], const float (&cap)[KT],
-                                                 int keff)
+__device__ __forceinline__ float rev_cost_sorted(float qj, const float (&zs)[KT], const float (&cap)[KT],
+                                                 int keff, bool sq)
 {
-    if (MEAS == M_RWMD) return qj * z[0];
+    float z[KT];
+#pragma unroll
+    for (int l = 0; l < KT; ++l) z[l] = d_value(zs[l], sq);
+    if (MEAS == M_RWMD) return __fmul_rn(qj, z[0]);
     if (MEAS == M_OMR) {
         if (KT >= 2 && z[0] == 0.f && keff >= 2) {
             const float r = qj - fminf(qj, cap[0]);
-            return r != 0.f ? r * z[KT >= 2 ? 1 : 0] : 0.f;
+            return r != 0.f ? __fmul_rn(r, z[KT >= 2 ? 1 : 0]) : 0.f;
         }
-        return qj * z[0];
+        return __fmul_rn(qj, z[0]);
     }
     // z is ascending, so z[keff-1] is the largest of the first keff entries (distances >= 0)
     float r = qj, c = 0.f, zlast = 0.f;
@@ -185,7 +193,7 @@ __device__ __forceinline__ void rev_body(const int32_t* __restrict__ row_ptr, co
       const float* __restrict__ val, int64_t n, const float* __restrict__ D, int ldd, int h,
       const float* __restrict__ q_w, int k, const float* __restrict__ t_fwd,
       float* __restrict__ t_rev, float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
-      const int* __restrict__ n_dev)
+      const int* __restrict__ n_dev, bool sq)
 {
     constexpr int U = 4;  // bins whose loads are in flight together
     const int lane = threadIdx.x & 31;
@@ -235,7 +243,7 @@ __device__ __forceinline__ void rev_body(const int32_t* __restrict__ row_ptr, co
             }
 #pragma unroll
             for (int t = 0; t < NJ; ++t)
-                if (j0 + t < h) total += rev_cost_sorted<MEAS, KT>(q_w[j0 + t], z[t], cap[t], keff);
+                if (j0 + t < h) total = __fadd_rn(total, rev_cost_sorted<MEAS, KT>(q_w[j0 + t], z[t], cap[t], keff, sq));
         }
         total = warp_sum(total);
         if (lane == 0) {
@@ -250,9 +258,9 @@ __global__ void __launch_bounds__(256, 2) k_rev(const int32_t* __restrict__ row_
       const float* __restrict__ val, int64_t n, const float* __restrict__ D, int ldd, int h,
       const float* __restrict__ q_w, int k, const float* __restrict__ t_fwd,
       float* __restrict__ t_rev, float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
-      const int* __restrict__ n_dev)
+      const int* __restrict__ n_dev, bool sq)
 {
-    rev_body<MEAS, KT, NJ>(row_ptr, col, val, n, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev);
+    rev_body<MEAS, KT, NJ>(row_ptr, col, val, n, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev, sq);
 }
 
 // Candidate-list form: a block of W warps per candidate slot.  Warp w scans the w-th
@@ -266,7 +274,7 @@ __device__ __forceinline__ void rev_blk_body(const int32_t* __restrict__ row_ptr
           const float* __restrict__ val, const float* __restrict__ D, int ldd, int h,
           const float* __restrict__ q_w, int k, const float* __restrict__ t_fwd,
           float* __restrict__ t_rev, float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
-          const int* __restrict__ n_dev)
+          const int* __restrict__ n_dev, bool sq)
 {
     constexpr int U = 4;
     __shared__ float sz[W - 1][32 * NJ][KT];
@@ -337,7 +345,7 @@ __device__ __forceinline__ void rev_blk_body(const int32_t* __restrict__ row_ptr
                         insert_sorted<KT>(z[t], cap[t], sz[w][lane * NJ + t][l], sc[w][lane * NJ + t][l]);
 #pragma unroll
             for (int t = 0; t < NJ; ++t)
-                if (j0 + t < h) total += rev_cost_sorted<MEAS, KT>(q_w[j0 + t], z[t], cap[t], keff);
+                if (j0 + t < h) total = __fadd_rn(total, rev_cost_sorted<MEAS, KT>(q_w[j0 + t], z[t], cap[t], keff, sq));
         }
         __syncthreads();
     }
@@ -355,9 +363,9 @@ __global__ void __launch_bounds__(W * 32, (W >= 8 ? 2 : 4)) k_rev_blk(const int3
           const float* __restrict__ val, const float* __restrict__ D, int ldd, int h,
           const float* __restrict__ q_w, int k, const float* __restrict__ t_fwd,
           float* __restrict__ t_rev, float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
-          const int* __restrict__ n_dev)
+          const int* __restrict__ n_dev, bool sq)
 {
-    rev_blk_body<MEAS, KT, NJ, W>(row_ptr, col, val, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev);
+    rev_blk_body<MEAS, KT, NJ, W>(row_ptr, col, val, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev, sq);
 }
 
 // k above the register width (ICT, large k): per lane, successive minima over the
@@ -369,7 +377,7 @@ __device__ __forceinline__ void rev_generic_body(const int32_t* __restrict__ row
                               int ldd, int h, const float* __restrict__ q_w, int k,
                               const float* __restrict__ t_fwd, float* __restrict__ t_rev,
                               float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
-                              const int* __restrict__ n_dev)
+                              const int* __restrict__ n_dev, bool sq)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -393,13 +401,14 @@ __device__ __forceinline__ void rev_generic_body(const int32_t* __restrict__ row
                     const bool after = dd > pz || (dd == pz && pos > pe);
                     if (after && (dd < bz || (dd == bz && pos < be))) { bz = dd; be = pos; bx = val[e]; }
                 }
+                const float zd = d_value(bz, sq);
                 if (l < keff - 1) {
                     const float tau = fminf(r, bx);
-                    c = fmaf(tau, bz, c);
+                    c = fmaf(tau, zd, c);
                     r -= tau;
                     if (r == 0.f) break;
                 } else {
-                    c = fmaf(r, bz, c);
+                    c = fmaf(r, zd, c);
                 }
                 pz = bz;
                 pe = be;
@@ -420,9 +429,9 @@ __global__ void k_rev_generic(const int32_t* __restrict__ row_ptr, const int32_t
                               int ldd, int h, const float* __restrict__ q_w, int k,
                               const float* __restrict__ t_fwd, float* __restrict__ t_rev,
                               float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
-                              const int* __restrict__ n_dev)
+                              const int* __restrict__ n_dev, bool sq)
 {
-    rev_generic_body<MEAS>(row_ptr, col, val, n, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev);
+    rev_generic_body<MEAS>(row_ptr, col, val, n, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev, sq);
 }
 
 // ------------------------------------------------------------------ top-K selection
@@ -665,13 +674,13 @@ __global__ void k_prune_select(const int64_t* __restrict__ cand, const float* __
 template <int MEAS>
 cudaError_t rev_meas_blk(int k, const int32_t* row_ptr, const int32_t* col, const float* val, int slots,
                          const float* D, int ldd, int h, const float* q_w, const float* t_fwd,
-                         float* t_rev, float* t_max, const int64_t* doc_ids, const int* n_dev,
+                         float* t_rev, float* t_max, const int64_t* doc_ids, const int* n_dev, bool sq,
                          cudaStream_t st)
 {
     constexpr int W = 4;
     const int kt = MEAS == M_RWMD ? 1 : (MEAS == M_OMR ? 2 : k);
     const bool wide = h > 32;
-#define EMD_REVB(KT, NJ) k_rev_blk<MEAS, KT, NJ, W><<<slots, W * 32, 0, st>>>(row_ptr, col, val, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev)
+#define EMD_REVB(KT, NJ) k_rev_blk<MEAS, KT, NJ, W><<<slots, W * 32, 0, st>>>(row_ptr, col, val, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev, sq)
     if (kt <= 1) { if (wide) EMD_REVB(1, 4); else EMD_REVB(1, 1); }
     else if (kt <= 2) { if (wide) EMD_REVB(2, 4); else EMD_REVB(2, 1); }
     else if (kt <= 4) { if (wide) EMD_REVB(4, 4); else EMD_REVB(4, 1); }
@@ -718,7 +727,7 @@ __global__ void k_fwd_g(const QDesc* __restrict__ qd, const int* __restrict__ nq
         for (int32_t e = a + ph; e < b; e += 4) {
             const int32_t u = col[e];
             const float x = val[e];
-            if (act) acc += fwd_cost_p<MEAS, KT>(x, tq + (int64_t)u * rs, es, kq);
+            if (act) acc = __fadd_rn(acc, fwd_cost_p<MEAS, KT>(x, tq + (int64_t)u * rs, es, kq));
         }
         acc += __shfl_xor_sync(0xffffffffu, acc, 8);
         acc += __shfl_xor_sync(0xffffffffu, acc, 16);
@@ -738,10 +747,10 @@ k_rev_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t*
     float* t_max = dir == EMD_DIR_MAX ? d.t_out : nullptr;
     if (d.h > 32)
         rev_body<MEAS, KT, NJW>(row_ptr, col, val, n, d.D, d.ldd, d.h, d.qw, k, d.t_fwd, t_rev, t_max, nullptr,
-                                nullptr);
+                                nullptr, d.sq != 0);
     else
         rev_body<MEAS, KT, 1>(row_ptr, col, val, n, d.D, d.ldd, d.h, d.qw, k, d.t_fwd, t_rev, t_max, nullptr,
-                              nullptr);
+                              nullptr, d.sq != 0);
 }
 
 template <int MEAS>
@@ -753,7 +762,8 @@ __global__ void k_rev_generic_b(const QDesc* __restrict__ qd, const int* __restr
     const QDesc& d = qd[blockIdx.y];
     float* t_rev = dir == EMD_DIR_REV ? d.t_out : d.t_rev;
     float* t_max = dir == EMD_DIR_MAX ? d.t_out : nullptr;
-    rev_generic_body<MEAS>(row_ptr, col, val, n, d.D, d.ldd, d.h, d.qw, k, d.t_fwd, t_rev, t_max, nullptr, nullptr);
+    rev_generic_body<MEAS>(row_ptr, col, val, n, d.D, d.ldd, d.h, d.qw, k, d.t_fwd, t_rev, t_max, nullptr, nullptr,
+                           d.sq != 0);
 }
 
 __global__ void k_prune_compact_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t n, int K)
@@ -772,10 +782,10 @@ k_rev_blk_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int3
     const QDesc& d = qd[blockIdx.y];
     if (d.h > 32)
         rev_blk_body<MEAS, KT, NJW, W>(row_ptr, col, val, d.D, d.ldd, d.h, d.qw, k, d.t_fwd, d.cand_sym + kPruneCap,
-                                       d.cand_sym, d.cand, d.cand_count);
+                                       d.cand_sym, d.cand, d.cand_count, d.sq != 0);
     else
         rev_blk_body<MEAS, KT, 1, W>(row_ptr, col, val, d.D, d.ldd, d.h, d.qw, k, d.t_fwd, d.cand_sym + kPruneCap,
-                                     d.cand_sym, d.cand, d.cand_count);
+                                     d.cand_sym, d.cand, d.cand_count, d.sq != 0);
 }
 
 // Reverse values of the candidate documents, rows of any width (ICT): one warp each.
@@ -787,7 +797,7 @@ __global__ void k_rev_generic_cand_b(const QDesc* __restrict__ qd, const int* __
     if ((int)blockIdx.y >= *nq) return;
     const QDesc& d = qd[blockIdx.y];
     rev_generic_body<MEAS>(row_ptr, col, val, kPruneCap, d.D, d.ldd, d.h, d.qw, k, d.t_fwd, d.cand_sym + kPruneCap,
-                           d.cand_sym, d.cand, d.cand_count);
+                           d.cand_sym, d.cand, d.cand_count, d.sq != 0);
 }
 
 __global__ void k_prune_select_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int K)
@@ -847,20 +857,20 @@ template <int MEAS>
 cudaError_t rev_meas(int k, const int32_t* row_ptr, const int32_t* col, const float* val,
                      int64_t n, const float* D, int ldd, int h, const float* q_w,
                      const float* t_fwd, float* t_rev, float* t_max, const int64_t* doc_ids,
-                     const int* n_dev, cudaStream_t st)
+                     const int* n_dev, bool sq, cudaStream_t st)
 {
     const int warps = 8;
     const int64_t blocks = std::min<int64_t>((n + warps - 1) / warps, 152 * 64);
     dim3 grid((unsigned)std::max<int64_t>(1, blocks));
     const int kt = MEAS == M_RWMD ? 1 : (MEAS == M_OMR ? 2 : (MEAS == M_ICT ? 1 << 30 : k));
     const bool wide = h > 32;  // several 32-bin chunks: vector loads of consecutive bins
-#define EMD_REV(KT, NJ) k_rev<MEAS, KT, NJ><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev)
+#define EMD_REV(KT, NJ) k_rev<MEAS, KT, NJ><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev, sq)
     if (kt <= 1) { if (wide) EMD_REV(1, 4); else EMD_REV(1, 1); }
     else if (kt <= 2) { if (wide) EMD_REV(2, 4); else EMD_REV(2, 1); }
     else if (kt <= 4) { if (wide) EMD_REV(4, 4); else EMD_REV(4, 1); }
     else if (kt <= 8) { if (wide) EMD_REV(8, 2); else EMD_REV(8, 1); }
     else if (kt <= 16) EMD_REV(16, 1);
-    else k_rev_generic<MEAS><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev);
+    else k_rev_generic<MEAS><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev, sq);
 #undef EMD_REV
     return cudaGetLastError();
 }
@@ -904,21 +914,21 @@ cudaError_t launch_fwd(int meas, const int32_t* row_ptr, const int32_t* col, con
 cudaError_t launch_rev(int meas, int k, const int32_t* row_ptr, const int32_t* col,
                        const float* val, int64_t n, const float* D, int ldd, int h,
                        const float* q_w, const float* t_fwd, float* t_rev, float* t_max,
-                       const int64_t* doc_ids, cudaStream_t st)
+                       const int64_t* doc_ids, bool sq, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     switch (meas) {
-    case M_RWMD: return rev_meas<M_RWMD>(k, row_ptr, col, val, n, D, ldd, h, q_w, t_fwd, t_rev, t_max, doc_ids, nullptr, st);
-    case M_OMR: return rev_meas<M_OMR>(k, row_ptr, col, val, n, D, ldd, h, q_w, t_fwd, t_rev, t_max, doc_ids, nullptr, st);
-    case M_ICT: return rev_meas<M_ICT>(k, row_ptr, col, val, n, D, ldd, h, q_w, t_fwd, t_rev, t_max, doc_ids, nullptr, st);
-    default: return rev_meas<M_ACT>(k, row_ptr, col, val, n, D, ldd, h, q_w, t_fwd, t_rev, t_max, doc_ids, nullptr, st);
+    case M_RWMD: return rev_meas<M_RWMD>(k, row_ptr, col, val, n, D, ldd, h, q_w, t_fwd, t_rev, t_max, doc_ids, nullptr, sq, st);
+    case M_OMR: return rev_meas<M_OMR>(k, row_ptr, col, val, n, D, ldd, h, q_w, t_fwd, t_rev, t_max, doc_ids, nullptr, sq, st);
+    case M_ICT: return rev_meas<M_ICT>(k, row_ptr, col, val, n, D, ldd, h, q_w, t_fwd, t_rev, t_max, doc_ids, nullptr, sq, st);
+    default: return rev_meas<M_ACT>(k, row_ptr, col, val, n, D, ldd, h, q_w, t_fwd, t_rev, t_max, doc_ids, nullptr, sq, st);
     }
 }
 
 cudaError_t launch_prune(int meas, int k, const int32_t* row_ptr, const int32_t* col, const float* val,
                          int64_t n, const float* D, int ldd, int h, const float* q_w, const float* t_fwd,
                          const int64_t* sel_idx, const float* sel_val, int K, int64_t* cand, int* count,
-                         float* sym, int64_t* out_idx, float* out_dist, int* ok, cudaStream_t st)
+                         float* sym, int64_t* out_idx, float* out_dist, int* ok, bool sq, cudaStream_t st)
 {
     (void)sel_idx;
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), st);
@@ -927,10 +937,10 @@ cudaError_t launch_prune(int meas, int k, const int32_t* row_ptr, const int32_t*
     k_prune_compact<<<blocks, 256, 0, st>>>(t_fwd, n, sel_val, K, kPruneCap, cand, count);
     // reverse pass on the candidate slots (t_rev into sym + kPruneCap, max into sym)
     switch (meas) {
-    case M_RWMD: e = rev_meas_blk<M_RWMD>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, st); break;
-    case M_OMR: e = rev_meas_blk<M_OMR>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, st); break;
-    case M_ICT: e = rev_meas<M_ICT>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, st); break;
-    default: e = rev_meas_blk<M_ACT>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, st); break;
+    case M_RWMD: e = rev_meas_blk<M_RWMD>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, sq, st); break;
+    case M_OMR: e = rev_meas_blk<M_OMR>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, sq, st); break;
+    case M_ICT: e = rev_meas<M_ICT>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, sq, st); break;
+    default: e = rev_meas_blk<M_ACT>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, sq, st); break;
     }
     if (e != cudaSuccess) return e;
     k_prune_select<<<1, kPruneCap, 0, st>>>(cand, sym, count, kPruneCap, sel_val, K, out_idx, out_dist, ok);

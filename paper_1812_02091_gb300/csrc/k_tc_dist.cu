@@ -23,8 +23,9 @@
 // ring of stages; warp 1 allocates TMEM and its lane 0 issues tcgen05.mma (M = 128 rows of
 // V, N <= 128 query columns, K = 16 (32 for E4M3) per instruction) and tcgen05.commit;
 // warps 2..9 read
-// their TMEM lane quarter with tcgen05.ld and write d = sqrt(max(|v|^2 + |q|^2 - 2 v.q, 0)),
-// exactly 0 for identical vocabulary ids.  Every wait is bounded in time; a timeout
+// their TMEM lane quarter with tcgen05.ld and write the squared distance |v|^2 + |q|^2 -
+// 2 v.q (the readers of D take the square root of the entries they use; the exact zeros
+// of identical vocabulary ids are written after the kernel).  Every wait is bounded in time; a timeout
 // latches ERR_TIMEOUT, raises a block-wide abort flag and the block tears down.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -197,9 +198,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// sqrt(max(x, 0)), correctly rounded; shared by the per-query and batched epilogues.
-__device__ __forceinline__ float dist_sqrt(float x) { return __fsqrt_rn(fmaxf(x, 0.f)); }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 {
@@ -392,7 +390,6 @@ k_tc_dist(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_lo, in
             const bool row_ok = u < M;
             const float su = row_ok ? a_scale[u] : 0.f;
             const float nu = row_ok ? a_norm[u] : 0.f;
-            const int32_t idu = row_ok ? a_ids[u] : -1;
             const uint32_t tbase = tmem + (uint32_t)buf * kAcc + ((uint32_t)(q * 32) << 16);
             for (int cc = half * 64; cc < half * 64 + 64 && cc < Nt; cc += 32) {
                 uint32_t r0[32], r1[32];
@@ -405,9 +402,7 @@ k_tc_dist(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_lo, in
                 const bool lok = lcol < N;
                 const float cb_l = lok ? -2.f * b_scale[lcol] : 0.f;
                 const float nb_l = lok ? b_norm[lcol] : 0.f;
-                const int id_l = lok ? b_ids[lcol] : -2;
                 // every lane runs the loop (full-warp shuffles); rows past M only skip the stores
-                const float su2 = su;
                 float* out = D + (row_ok ? u : 0) * ldd + n0 + cc;
 #pragma unroll
                 for (int e4 = 0; e4 < 8; ++e4) {
@@ -417,12 +412,9 @@ k_tc_dist(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_lo, in
                         const int e = e4 * 4 + tt;
                         const float cb = __shfl_sync(0xffffffffu, cb_l, e);
                         const float nb = __shfl_sync(0xffffffffu, nb_l, e);
-                        const int idc = __shfl_sync(0xffffffffu, id_l, e);
                         float dot = __uint_as_float(r0[e]);
                         if (SPLIT) dot = fmaf(__uint_as_float(r1[e]), 1.0f / 2048.0f, dot);
-                        const float d2 = fmaf(cb * su2, dot, nu + nb);
-                        const float d = (idu == idc) ? 0.f : dist_sqrt(d2);
-                        o[tt] = (n0 + cc + e < N) ? d : INFINITY;
+                        o[tt] = fmaf(cb * su, dot, nu + nb);  // squared distance, unclamped
                     }
                     if (row_ok && n0 + cc + e4 * 4 < ldd)
                         *reinterpret_cast<float4*>(out + e4 * 4) = make_float4(o[0], o[1], o[2], o[3]);
@@ -629,7 +621,6 @@ k_tc_dist_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
             const bool row_ok = u < M;
             const float su = row_ok ? a_scale[u] : 0.f;
             const float nu = row_ok ? a_norm[u] : 0.f;
-            const int32_t idu = row_ok ? a_ids[u] : -1;
             int qa, qb;
             qrange(w / m_tiles, qa, qb);
             for (int q = qa; q < qb && ok; ++q) {
@@ -637,7 +628,6 @@ k_tc_dist_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
                 const int N = d.h, ldd = d.ldd;
                 const float* qsc = d.q_scale;
                 const float* qnm = d.qnorm;
-                const int32_t* qid = d.qidx;
                 float* Dq = d.D;
                 for (int n0 = 0; n0 < N; n0 += TC_BN, ++it) {
                     const int Nt = min(TC_BN, (int)round_up(N - n0, 16));
@@ -647,7 +637,6 @@ k_tc_dist_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
                     const bool lok = lcol < N;
                     const float cb_l = lok ? -2.f * qsc[lcol] : 0.f;
                     const float nb_l = lok ? qnm[lcol] : 0.f;
-                    const int id_l = lok ? qid[lcol] : -2;
                     if (!mbar_wait(&tfull[buf], (uint32_t)(it >> 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
                         fail();
                         ok = false;
@@ -673,12 +662,9 @@ k_tc_dist_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
                                 const int er = e - 16 * hh;
                                 const float cb = __shfl_sync(0xffffffffu, cb_l, e);
                                 const float nb = __shfl_sync(0xffffffffu, nb_l, e);
-                                const int idc = __shfl_sync(0xffffffffu, id_l, e);
                                 float dot = __uint_as_float(r0[er]);
                                 if (SPLIT) dot = fmaf(__uint_as_float(r1[er]), 1.0f / 2048.0f, dot);
-                                const float d2 = fmaf(cb * su2, dot, nu + nb);
-                                const float dd = (idu == idc) ? 0.f : dist_sqrt(d2);
-                                o[tt] = (n0 + cc + e < N) ? dd : INFINITY;
+                                o[tt] = fmaf(cb * su2, dot, nu + nb);  // squared distance, unclamped
                             }
                             if (row_ok && n0 + cc + e4 * 4 < ldd)
                                 *reinterpret_cast<float4*>(out + e4 * 4) = make_float4(o[0], o[1], o[2], o[3]);

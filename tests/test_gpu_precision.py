@@ -51,6 +51,27 @@ def make_db(emd, w, **opt):
                              emd.emd_db_options_default(**opt), v=w.v)
 
 
+def entries_match_up_to_ties(s, z, oz2, os2, k, rtol=2e-6):
+    """Table row check where the order of entries whose distances differ by less than the
+    FP32 resolution is not fixed (the device orders by its FP32 squared distance, the
+    oracle by the FP64 distance, both then by column): every device entry l must be one of
+    the oracle's entries tied with the oracle's l-th (oracle table taken k + 8 wide, so a
+    tie group that crosses the k-th entry is seen whole), and no column may repeat."""
+    if len(set(s.tolist())) != len(s):
+        return False
+    n2 = len(oz2)
+    for l in range(k):
+        lo = l
+        while lo > 0 and abs(oz2[lo - 1] - oz2[l]) <= rtol * max(oz2[l], 1e-30):
+            lo -= 1
+        hi = l
+        while hi + 1 < n2 and abs(oz2[hi + 1] - oz2[l]) <= rtol * max(oz2[l], 1e-30):
+            hi += 1
+        if s[l] not in set(os2[lo:hi + 1].tolist()):
+            return False
+    return True
+
+
 @pytest.mark.parametrize("precision", ["bf16", "fp8"])
 def test_table_reranked_exact(emd, work, precision):
     w = work
@@ -60,11 +81,14 @@ def test_table_reranked_exact(emd, work, precision):
             qidx, qw = w.queries.row(qi)
             for k in (1, 4, 16):
                 used, z, s, wt = emd.emd_phase1_table(db, qidx, qw, k)
-                oz, os_, ow = oracle.phase1(w.emb, None, used, qidx, qw, k)
+                k2 = min(k + 8, len(qidx))
+                oz2, os2, _ = oracle.phase1(w.emb, None, used, qidx, qw, k2)
+                oz = oz2[:, :k]
                 bad = ~np.isclose(z, oz, rtol=RTOL, atol=ATOL).all(1)
                 assert bad.mean() <= 1e-3, (qi, k, bad.sum())
-                good = ~bad
-                np.testing.assert_allclose(wt[good], ow[good], rtol=0, atol=0)
+                for r in np.nonzero(~bad)[0]:
+                    assert entries_match_up_to_ties(s[r], z[r], oz2[r], os2[r], k), (qi, k, r)
+                    np.testing.assert_array_equal(wt[r], qw[s[r]])
     finally:
         emd.emd_db_destroy(db)
 
