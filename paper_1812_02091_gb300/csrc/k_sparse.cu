@@ -95,7 +95,16 @@ __device__ __forceinline__ void fwd_body(const int32_t* __restrict__ row_ptr, co
         const bool valid = d < n;
         const int32_t a = valid ? row_ptr[d] : 0, b = valid ? row_ptr[d + 1] : 0;
         float acc = 0.f;
-        for (int32_t e = a + ph; e < b; e += 4)
+        int32_t e = a + ph;
+        for (; e + 12 < b; e += 16) {  // four nonzeros' costs in flight, added in order
+            const int32_t u0 = col[e], u1 = col[e + 4], u2 = col[e + 8], u3 = col[e + 12];
+            const float c0 = fwd_cost_p<MEAS, KT>(val[e], tab + (int64_t)u0 * k, 1, keff);
+            const float c1 = fwd_cost_p<MEAS, KT>(val[e + 4], tab + (int64_t)u1 * k, 1, keff);
+            const float c2 = fwd_cost_p<MEAS, KT>(val[e + 8], tab + (int64_t)u2 * k, 1, keff);
+            const float c3 = fwd_cost_p<MEAS, KT>(val[e + 12], tab + (int64_t)u3 * k, 1, keff);
+            acc = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(acc, c0), c1), c2), c3);
+        }
+        for (; e < b; e += 4)
             acc = __fadd_rn(acc, fwd_cost_p<MEAS, KT>(val[e], tab + (int64_t)col[e] * k, 1, keff));
         acc += __shfl_xor_sync(0xffffffffu, acc, 8);
         acc += __shfl_xor_sync(0xffffffffu, acc, 16);
@@ -724,7 +733,19 @@ __global__ void k_fwd_g(const QDesc* __restrict__ qd, const int* __restrict__ nq
     for (int64_t d = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); d < n; d += warps) {
         const int32_t a = row_ptr[d], b = row_ptr[d + 1];
         float acc = 0.f;
-        for (int32_t e = a + ph; e < b; e += 4) {
+        int32_t e = a + ph;
+        for (; e + 12 < b; e += 16) {  // four nonzeros' costs in flight, added in order
+            const int32_t u0 = col[e], u1 = col[e + 4], u2 = col[e + 8], u3 = col[e + 12];
+            const float x0 = val[e], x1 = val[e + 4], x2 = val[e + 8], x3 = val[e + 12];
+            if (act) {
+                const float c0 = fwd_cost_p<MEAS, KT>(x0, tq + (int64_t)u0 * rs, es, kq);
+                const float c1 = fwd_cost_p<MEAS, KT>(x1, tq + (int64_t)u1 * rs, es, kq);
+                const float c2 = fwd_cost_p<MEAS, KT>(x2, tq + (int64_t)u2 * rs, es, kq);
+                const float c3 = fwd_cost_p<MEAS, KT>(x3, tq + (int64_t)u3 * rs, es, kq);
+                acc = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(acc, c0), c1), c2), c3);
+            }
+        }
+        for (; e < b; e += 4) {
             const int32_t u = col[e];
             const float x = val[e];
             if (act) acc = __fadd_rn(acc, fwd_cost_p<MEAS, KT>(x, tq + (int64_t)u * rs, es, kq));
