@@ -40,36 +40,8 @@ def dense(v, ids, w):
     return x
 
 
-# ----------------------------------------------------------------------- BoW cosine
-
-def test_bow_against_scipy_dense():
-    rng = np.random.default_rng(11)
-    v = 60
-    rows = [random_hist(rng, v, 1, 20) for _ in range(40)]
-    db = csr(rows)
-    for _ in range(10):
-        qi, qw = random_hist(rng, v, 1, 25)
-        got = oracle.bow_cosine(v, db, qi, qw)
-        for d, (ids, w) in enumerate(rows):
-            want = 1.0 - scipy_cosine(dense(v, ids, w), dense(v, qi, qw))
-            assert abs(got[d] - want) <= 1e-12
-
-
-def test_bow_special_cases():
-    v = 10
-    db = csr([([1, 4, 7], [0.2, 0.3, 0.5]), ([0, 2], [0.5, 0.5]), ([0, 1], [0.5, 0.5])])
-    got = oracle.bow_cosine(v, db, np.array([1, 4, 7], np.int32), np.array([0.2, 0.3, 0.5], np.float32))
-    assert abs(got[0] - 1.0) <= 1e-12 and got[1] == 0.0
-    # hand value: p = (1/2, 1/2) on ids {0, 1}, q = 1 on id 0: (1/2) / (1/sqrt(2) * 1) = 1/sqrt(2)
-    got = oracle.bow_cosine(v, db, np.array([0], np.int32), np.array([1.0], np.float32))
-    assert abs(got[2] - 2 ** -0.5) <= 1e-12
-    # scaling the query weights changes nothing
-    a = oracle.bow_cosine(v, db, np.array([0, 1], np.int32), np.array([0.25, 0.75], np.float32))
-    b = oracle.bow_cosine(v, db, np.array([0, 1], np.int32), np.array([0.5, 1.5], np.float32))
-    np.testing.assert_allclose(a, b, rtol=1e-12)
-
-
-# ----------------------------------------------------------------------- WCD
+# ----------------------------------------------------------------------- pins as predicates
+# (also run against mutated copies of the oracle in test_oracle_mutations)
 
 def lp_emd(C, p, q):
     hp, hq = C.shape
@@ -83,17 +55,47 @@ def lp_emd(C, p, q):
     return res.fun
 
 
-def test_wcd_one_bin_is_ground_distance():
+def bow_scipy_pin(bow) -> bool:
+    rng = np.random.default_rng(11)
+    v = 60
+    rows = [random_hist(rng, v, 1, 20) for _ in range(40)]
+    db = csr(rows)
+    for _ in range(10):
+        qi, qw = random_hist(rng, v, 1, 25)
+        got = bow(v, db, qi, qw)
+        for d, (ids, w) in enumerate(rows):
+            want = 1.0 - scipy_cosine(dense(v, ids, w), dense(v, qi, qw))
+            if abs(got[d] - want) > 1e-12:
+                return False
+    return True
+
+
+def bow_special_pins(bow) -> bool:
+    v = 10
+    db = csr([([1, 4, 7], [0.2, 0.3, 0.5]), ([0, 2], [0.5, 0.5]), ([0, 1], [0.5, 0.5])])
+    got = bow(v, db, np.array([1, 4, 7], np.int32), np.array([0.2, 0.3, 0.5], np.float32))
+    if not (abs(got[0] - 1.0) <= 1e-12 and got[1] == 0.0):
+        return False
+    # hand value: p = (1/2, 1/2) on ids {0, 1}, q = 1 on id 0: (1/2) / (1/sqrt(2) * 1) = 1/sqrt(2)
+    got = bow(v, db, np.array([0], np.int32), np.array([1.0], np.float32))
+    if abs(got[2] - 2 ** -0.5) > 1e-12:
+        return False
+    # scaling the query weights changes nothing
+    a = bow(v, db, np.array([0, 1], np.int32), np.array([0.25, 0.75], np.float32))
+    b = bow(v, db, np.array([0, 1], np.int32), np.array([0.5, 1.5], np.float32))
+    return bool(np.allclose(a, b, rtol=1e-12, atol=0))
+
+
+def wcd_one_bin_pin(wcd) -> bool:
     rng = np.random.default_rng(5)
     emb = rng.standard_normal((30, 7)).astype(np.float32)
     db = csr([([u], [1.0]) for u in range(30)])
-    got = oracle.wcd(emb, db, np.array([4], np.int32), np.array([1.0], np.float32))
+    got = wcd(emb, db, np.array([4], np.int32), np.array([1.0], np.float32))
     want = np.linalg.norm(emb.astype(np.float64) - emb[4].astype(np.float64), axis=1)
-    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-15)
-    assert got[4] == 0.0
+    return bool(np.allclose(got, want, rtol=1e-12, atol=1e-15) and got[4] == 0.0)
 
 
-def test_wcd_below_emd():
+def wcd_emd_bound_pin(wcd) -> bool:
     rng = np.random.default_rng(6)
     v, m = 40, 5
     emb = rng.standard_normal((v, m)).astype(np.float32)
@@ -101,24 +103,43 @@ def test_wcd_below_emd():
     db = csr(rows)
     for _ in range(6):
         qi, qw = random_hist(rng, v, 1, 8)
-        got = oracle.wcd(emb, db, qi, qw)
+        got = wcd(emb, db, qi, qw)
         for d, (ids, w) in enumerate(rows):
             C = np.linalg.norm(emb[ids][:, None, :].astype(np.float64) - emb[qi][None, :, :].astype(np.float64), axis=2)
             pw, qq = np.asarray(w, np.float64), np.asarray(qw, np.float64)
-            assert got[d] <= lp_emd(C, pw / pw.sum(), qq / qq.sum()) + 1e-7
+            if got[d] > lp_emd(C, pw / pw.sum(), qq / qq.sum()) + 1e-7:
+                return False
+    return True
 
 
-def test_wcd_translation_invariant_and_hand_value():
+def wcd_translation_and_hand_pins(wcd) -> bool:
     rng = np.random.default_rng(7)
     v, m = 25, 6
     emb = rng.standard_normal((v, m)).astype(np.float32)
     rows = [random_hist(rng, v, 1, 6) for _ in range(12)]
     db = csr(rows)
     qi, qw = random_hist(rng, v, 1, 6)
-    a = oracle.wcd(emb, db, qi, qw)
-    b = oracle.wcd(emb + np.float32(3.0), db, qi, qw)
-    np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-6)
+    a = wcd(emb, db, qi, qw)
+    b = wcd(emb + np.float32(3.0), db, qi, qw)
+    if not np.allclose(a, b, rtol=1e-5, atol=1e-6):
+        return False
     # 1-D: coordinates 0, 1, 3; p = (1/2, 1/2) on {0, 1} has centroid 1/2, q = 1 on {2} has 3
     emb1 = np.array([[0.0], [1.0], [3.0]], np.float32)
-    got = oracle.wcd(emb1, csr([([0, 1], [0.5, 0.5])]), np.array([2], np.int32), np.array([1.0], np.float32))
-    assert abs(got[0] - 2.5) <= 1e-12
+    got = wcd(emb1, csr([([0, 1], [0.5, 0.5])]), np.array([2], np.int32), np.array([1.0], np.float32))
+    return abs(got[0] - 2.5) <= 1e-12
+
+
+BOW_PINS = (bow_scipy_pin, bow_special_pins)
+WCD_PINS = (wcd_one_bin_pin, wcd_emd_bound_pin, wcd_translation_and_hand_pins)
+
+
+# ----------------------------------------------------------------------- the oracle passes them
+
+@pytest.mark.parametrize("pin", BOW_PINS, ids=lambda f: f.__name__)
+def test_bow_pins(pin):
+    assert pin(oracle.bow_cosine)
+
+
+@pytest.mark.parametrize("pin", WCD_PINS, ids=lambda f: f.__name__)
+def test_wcd_pins(pin):
+    assert pin(oracle.wcd)

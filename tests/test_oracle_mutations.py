@@ -10,6 +10,7 @@ import pytest
 
 import emd_synth
 import oracle
+from test_oracle_baselines import BOW_PINS, WCD_PINS
 from test_oracle_pins import CASES, lp, nearest_mask, random_pair
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "emd_oracle.c")
@@ -104,3 +105,64 @@ def test_pairwise_mutation_is_caught(tmp_path, name):
 def test_lc_mutation_is_caught(tmp_path, name):
     w = emd_synth.small_text(77, 300, 8, 40, 2, 3, 12)
     assert not lc_pins_pass(build_mutant(tmp_path, name), w)
+
+
+BASELINE_MUTATIONS = {
+    "bow_no_document_norm": ("out[d] = (qn > 0.0 && dn > 0.0) ? dot / (qn * dn) : 0.0;",
+                             "out[d] = (qn > 0.0 && dn > 0.0) ? dot / qn : 0.0;"),
+    "bow_unsquared_norm": ("dn += (double)val[e] * (double)val[e];", "dn += (double)val[e];"),
+    "bow_query_weight_index": ("dense[q_idx[j]] = (double)q_w[j];", "dense[q_idx[j]] = (double)q_w[0];"),
+    "wcd_sum_not_difference": ("const double diff = cd[i] / sd - cq[i];", "const double diff = cd[i] / sd + cq[i];"),
+    "wcd_query_row_shifted": ("cq[i] += (double)q_w[j] * (double)emb[(int64_t)q_idx[j] * m + i];",
+                              "cq[i] += (double)q_w[j] * (double)emb[(int64_t)q_idx[j] * m + (i + 1) % m];"),
+    "wcd_no_root": ("out[d] = sqrt(s);", "out[d] = s;"),
+}
+
+
+def build_baseline_mutant(tmp_path, name):
+    old, new = BASELINE_MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, name
+    path = tmp_path / f"{name}.c"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / f"lib{name}.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", str(so), str(path), "-lm"])
+    L = ctypes.CDLL(str(so))
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    L.oracle_bow_db.argtypes = [i64, P, P, P, i64, P, P, i32, P]
+    L.oracle_bow_db.restype = i32
+    L.oracle_wcd_db.argtypes = [P, i32, P, P, P, i64, P, P, i32, P]
+    L.oracle_wcd_db.restype = i32
+
+    def bow(v, db, qi, qw):
+        rp = np.ascontiguousarray(db.row_ptr, np.int64)
+        col = np.ascontiguousarray(db.col, np.int32)
+        val = np.ascontiguousarray(db.val, np.float32)
+        qi = np.ascontiguousarray(qi, np.int32)
+        qw = np.ascontiguousarray(qw, np.float32)
+        out = np.empty(len(rp) - 1)
+        L.oracle_bow_db(int(v), _p(rp), _p(col), _p(val), len(rp) - 1, _p(qi), _p(qw), len(qi), _p(out))
+        return out
+
+    def wcd(emb, db, qi, qw):
+        emb = np.ascontiguousarray(emb, np.float32)
+        rp = np.ascontiguousarray(db.row_ptr, np.int64)
+        col = np.ascontiguousarray(db.col, np.int32)
+        val = np.ascontiguousarray(db.val, np.float32)
+        qi = np.ascontiguousarray(qi, np.int32)
+        qw = np.ascontiguousarray(qw, np.float32)
+        out = np.empty(len(rp) - 1)
+        L.oracle_wcd_db(_p(emb), emb.shape[1], _p(rp), _p(col), _p(val), len(rp) - 1, _p(qi), _p(qw), len(qi),
+                        _p(out))
+        return out
+
+    return bow, wcd
+
+
+@pytest.mark.parametrize("name", list(BASELINE_MUTATIONS))
+def test_baseline_mutation_is_caught(tmp_path, name):
+    bow, wcd = build_baseline_mutant(tmp_path, name)
+    if name.startswith("bow_"):
+        assert not all(pin(bow) for pin in BOW_PINS)
+    else:
+        assert not all(pin(wcd) for pin in WCD_PINS)
