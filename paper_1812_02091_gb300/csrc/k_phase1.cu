@@ -346,6 +346,7 @@ __device__ __forceinline__ void table_ict_body(const float* __restrict__ D, int 
     const int lane = threadIdx.x & 31;
     const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= M) return;
+    if (tab[row * rs].y >= 0.f) return;  // finished by the register pass (ict_fast_body)
     const float* Dr = D + row * ldd;
     const int lim = min(W, h);
     float r = xmax[row];
@@ -378,6 +379,72 @@ __device__ __forceinline__ void table_ict_body(const float* __restrict__ D, int 
         ++l;
     } while (r != 0.f && l < lim);
     if (r != 0.f && lim < h && lane == 0 && over) *over = 1;
+}
+
+// Register pass of the ICT table, one thread per row: the row's kIctFast smallest (d, j) in
+// ascending order (strict '<' over ascending j), then the same residual steps as
+// table_ict_body.  A row whose residual reaches 0 within them -- or that has no more
+// entries to take -- is written here in full; any other row gets entry 0 = (NaN, -1), and
+// table_ict_body, which skips rows with a nonnegative entry-0 weight, computes it.  Both
+// write identical entries for a row.
+constexpr int kIctFast = 8;
+
+__device__ __forceinline__ void ict_fast_body(const float* __restrict__ D, int ldd, int64_t M, int h, int W,
+                                              const float* __restrict__ q_w, const float* __restrict__ xmax,
+                                              float2* __restrict__ tab, int32_t* __restrict__ tab_s, int rs, int es,
+                                              int* __restrict__ over, bool sq)
+{
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= M) return;
+    const float* Dr = D + row * ldd;
+    float z[kIctFast];
+    int s[kIctFast];
+#pragma unroll
+    for (int l = 0; l < kIctFast; ++l) { z[l] = INFINITY; s[l] = INT32_MAX; }
+    for (int j = 0; j < h; j += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(Dr + j);  // ldd % 32 == 0
+        insert_dj<kIctFast>(z, s, v.x, j);
+        if (j + 1 < h) insert_dj<kIctFast>(z, s, v.y, j + 1);
+        if (j + 2 < h) insert_dj<kIctFast>(z, s, v.z, j + 2);
+        if (j + 3 < h) insert_dj<kIctFast>(z, s, v.w, j + 3);
+    }
+    const int lim = min(W, h), lf = min(lim, kIctFast);
+    float r = xmax[row];
+    int L = 0;
+    bool go = true;  // the first entry is always taken; then while mass remains
+#pragma unroll
+    for (int l = 0; l < kIctFast; ++l) {
+        if (l < lf && go) {
+            const bool valid = s[l] != INT32_MAX;  // false only where D held NaN
+            L = l + 1;
+            if (valid) {
+                r -= fminf(r, q_w[s[l]]);
+                go = r != 0.f;
+            } else {
+                go = false;
+            }
+        }
+    }
+    if (r != 0.f && lf < lim) {  // needs more than kIctFast entries: the warp pass
+        tab[row * rs] = make_float2(__int_as_float(0x7fc00000), -1.f);
+        return;
+    }
+    if (r != 0.f && lim < h && over) *over = 1;  // more than W entries needed
+#pragma unroll
+    for (int l = 0; l < kIctFast; ++l) {
+        if (l < L) {
+            const bool valid = s[l] != INT32_MAX;
+            tab[row * rs + (int64_t)l * es] = make_float2(valid ? d_value(z[l], sq) : INFINITY, valid ? q_w[s[l]] : 0.f);
+            if (tab_s) tab_s[row * W + l] = valid ? s[l] : -1;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) k_table_ict_fast(const float* __restrict__ D, int ldd, int64_t M, int h, int W,
+                                 const float* __restrict__ q_w, const float* __restrict__ xmax,
+                                 float2* __restrict__ tab, int32_t* __restrict__ tab_s, int* __restrict__ over, bool sq)
+{
+    ict_fast_body(D, ldd, M, h, W, q_w, xmax, tab, tab_s, W, 1, over, sq);
 }
 
 __global__ void k_table_ict(const float* __restrict__ D, int ldd, int64_t M, int h, int W,
@@ -568,6 +635,14 @@ __global__ void k_zero_ident_b(const QDesc* __restrict__ qd, const int* __restri
     zero_ident_body(d.qidx, d.h, vslot, d.D, d.ldd);
 }
 
+__global__ void __launch_bounds__(128) k_table_ict_fast_b(const QDesc* __restrict__ qd, const int* __restrict__ nq,
+                                                          int64_t M, const float* __restrict__ xmax)
+{
+    if ((int)blockIdx.y >= *nq) return;
+    const QDesc& d = qd[blockIdx.y];
+    ict_fast_body(d.D, d.ldd, M, d.h, d.tk, d.qw, xmax, d.tab, nullptr, d.tab_rs, d.tab_es, d.over, d.sq != 0);
+}
+
 __global__ void k_table_ict_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t M,
                               const float* __restrict__ xmax)
 {
@@ -677,6 +752,7 @@ cudaError_t launch_table_ict(const float* D, int ldd, int64_t M, int h, int W, c
     if (M <= 0) return cudaSuccess;
     if (W < 1 || h < 1) return cudaErrorInvalidValue;
     const int warps = 8;
+    k_table_ict_fast<<<(unsigned)((M + 127) / 128), 128, 0, st>>>(D, ldd, M, h, W, q_w, xmax, tab, tab_s, over, sq);
     k_table_ict<<<(unsigned)((M + warps - 1) / warps), warps * 32, 0, st>>>(D, ldd, M, h, W, q_w, xmax, tab, tab_s,
                                                                            over, sq);
     return cudaGetLastError();
@@ -747,6 +823,7 @@ cudaError_t launch_table_ict_b(const QDesc* qd, const int* nq, int max_q, int64_
 {
     if (max_q <= 0 || M <= 0) return cudaSuccess;
     const int warps = 8;
+    k_table_ict_fast_b<<<dim3((unsigned)((M + 127) / 128), (unsigned)max_q), 128, 0, st>>>(qd, nq, M, xmax);
     k_table_ict_b<<<dim3((unsigned)((M + warps - 1) / warps), (unsigned)max_q), warps * 32, 0, st>>>(qd, nq, M, xmax);
     return cudaGetLastError();
 }
