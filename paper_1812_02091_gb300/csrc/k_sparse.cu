@@ -379,7 +379,45 @@ __global__ void __launch_bounds__(W * 32, (W >= 8 ? 2 : 4)) k_rev_blk(const int3
 
 // k above the register width (ICT, large k): per lane, successive minima over the
 // document's bins, each strictly after the previous in (distance, bin position) order,
-// until the source mass is placed.  O(steps * h_d) per query bin.
+// until the source mass is placed.  O(steps * h_d) per query bin.  The query bins are
+// taken in tiles of 32 (lane = bin within the tile); a lane's costs are summed per tile
+// residue t mod kRevW, and the kRevW partial sums are then added in order -- the same
+// arithmetic whether one warp walks all tiles (rev_generic_body) or kRevW warps split them
+// (rev_generic_blk_body, for candidate lists).
+constexpr int kRevW = 8;
+
+template <int MEAS>
+__device__ __forceinline__ float rev_generic_bin(const int32_t* __restrict__ col, const float* __restrict__ val,
+                                                 int32_t a, int32_t b, int keff, const float* __restrict__ D, int ldd,
+                                                 int j, float qj, bool sq)
+{
+    float r = qj, c = 0.f;
+    float pz = -INFINITY;
+    int pe = -1;
+    for (int l = 0; l < keff; ++l) {
+        float bz = INFINITY, bx = 0.f;
+        int be = INT32_MAX;
+        for (int32_t e = a; e < b; ++e) {
+            const float dv = D[(int64_t)col[e] * ldd + j];
+            const int pos = e - a;
+            const bool after = dv > pz || (dv == pz && pos > pe);
+            if (after && (dv < bz || (dv == bz && pos < be))) { bz = dv; be = pos; bx = val[e]; }
+        }
+        const float zd = d_value(bz, sq);
+        if (l < keff - 1) {
+            const float tau = fminf(r, bx);
+            c = fmaf(tau, zd, c);
+            r -= tau;
+            if (r == 0.f) break;
+        } else {
+            c = fmaf(r, zd, c);
+        }
+        pz = bz;
+        pe = be;
+    }
+    return c;
+}
+
 template <int MEAS>
 __device__ __forceinline__ void rev_generic_body(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                               const float* __restrict__ val, int64_t n, const float* __restrict__ D,
@@ -396,40 +434,75 @@ __device__ __forceinline__ void rev_generic_body(const int32_t* __restrict__ row
         const int32_t a = row_ptr[dd], b = row_ptr[dd + 1];
         const int hd = b - a;
         const int keff = MEAS == M_ICT ? hd : min(k, hd);
-        float total = 0.f;
-        for (int j = lane; j < h; j += 32) {
-            float r = q_w[j], c = 0.f;
-            float pz = -INFINITY;
-            int pe = -1;
-            for (int l = 0; l < keff; ++l) {
-                float bz = INFINITY, bx = 0.f;
-                int be = INT32_MAX;
-                for (int32_t e = a; e < b; ++e) {
-                    const float dd = D[(int64_t)col[e] * ldd + j];
-                    const int pos = e - a;
-                    const bool after = dd > pz || (dd == pz && pos > pe);
-                    if (after && (dd < bz || (dd == bz && pos < be))) { bz = dd; be = pos; bx = val[e]; }
-                }
-                const float zd = d_value(bz, sq);
-                if (l < keff - 1) {
-                    const float tau = fminf(r, bx);
-                    c = fmaf(tau, zd, c);
-                    r -= tau;
-                    if (r == 0.f) break;
-                } else {
-                    c = fmaf(r, zd, c);
-                }
-                pz = bz;
-                pe = be;
+        float part[kRevW];
+#pragma unroll
+        for (int w = 0; w < kRevW; ++w) part[w] = 0.f;
+        for (int t0 = 0; t0 * 32 < h; t0 += kRevW) {
+#pragma unroll
+            for (int w = 0; w < kRevW; ++w) {
+                const int j = (t0 + w) * 32 + lane;
+                if (j < h) part[w] = __fadd_rn(part[w], rev_generic_bin<MEAS>(col, val, a, b, keff, D, ldd, j, q_w[j], sq));
             }
-            total += c;
         }
+        float total = part[0];
+#pragma unroll
+        for (int w = 1; w < kRevW; ++w) total = __fadd_rn(total, part[w]);
         total = warp_sum(total);
         if (lane == 0) {
             t_rev[d] = total;
             if (t_max) t_max[d] = fmaxf(t_fwd[dd], total);
         }
     }
+}
+
+// Candidate-list form: a block of kRevW warps per slot, warp w taking the query-bin tiles
+// t = w, w + kRevW, ...; warp 0 adds the partial sums in warp order.  Same values as
+// rev_generic_body.
+template <int MEAS>
+__device__ __forceinline__ void rev_generic_blk_body(const int32_t* __restrict__ row_ptr,
+                                                     const int32_t* __restrict__ col, const float* __restrict__ val,
+                                                     const float* __restrict__ D, int ldd, int h,
+                                                     const float* __restrict__ q_w, int k,
+                                                     const float* __restrict__ t_fwd, float* __restrict__ t_rev,
+                                                     float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
+                                                     const int* __restrict__ n_dev, bool sq)
+{
+    __shared__ float sp[kRevW][32];
+    const int slot = blockIdx.x;
+    if (slot >= min(*n_dev, (int)gridDim.x)) return;  // uniform over the block
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t dd = doc_ids[slot];
+    const int32_t a = row_ptr[dd], b = row_ptr[dd + 1];
+    const int hd = b - a;
+    const int keff = MEAS == M_ICT ? hd : min(k, hd);
+    float part = 0.f;
+    for (int t = warp; t * 32 < h; t += kRevW) {
+        const int j = t * 32 + lane;
+        if (j < h) part = __fadd_rn(part, rev_generic_bin<MEAS>(col, val, a, b, keff, D, ldd, j, q_w[j], sq));
+    }
+    sp[warp][lane] = part;
+    __syncthreads();
+    if (warp == 0) {
+        float total = sp[0][lane];
+#pragma unroll
+        for (int w = 1; w < kRevW; ++w) total = __fadd_rn(total, sp[w][lane]);
+        total = warp_sum(total);
+        if (lane == 0) {
+            t_rev[slot] = total;
+            if (t_max) t_max[slot] = fmaxf(t_fwd[dd], total);
+        }
+    }
+}
+
+template <int MEAS>
+__global__ void __launch_bounds__(kRevW * 32) k_rev_generic_blk(const int32_t* __restrict__ row_ptr,
+                                  const int32_t* __restrict__ col, const float* __restrict__ val,
+                                  const float* __restrict__ D, int ldd, int h, const float* __restrict__ q_w, int k,
+                                  const float* __restrict__ t_fwd, float* __restrict__ t_rev,
+                                  float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
+                                  const int* __restrict__ n_dev, bool sq)
+{
+    rev_generic_blk_body<MEAS>(row_ptr, col, val, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev, sq);
 }
 
 template <int MEAS>
@@ -809,16 +882,17 @@ k_rev_blk_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int3
                                      d.cand_sym, d.cand, d.cand_count, d.sq != 0);
 }
 
-// Reverse values of the candidate documents, rows of any width (ICT): one warp each.
+// Reverse values of the candidate documents, rows of any width (ICT): a block of kRevW
+// warps each.
 template <int MEAS>
-__global__ void k_rev_generic_cand_b(const QDesc* __restrict__ qd, const int* __restrict__ nq,
-                                     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                                     const float* __restrict__ val, int k)
+__global__ void __launch_bounds__(kRevW * 32)
+k_rev_generic_cand_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t* __restrict__ row_ptr,
+                     const int32_t* __restrict__ col, const float* __restrict__ val, int k)
 {
     if ((int)blockIdx.y >= *nq) return;
     const QDesc& d = qd[blockIdx.y];
-    rev_generic_body<MEAS>(row_ptr, col, val, kPruneCap, d.D, d.ldd, d.h, d.qw, k, d.t_fwd, d.cand_sym + kPruneCap,
-                           d.cand_sym, d.cand, d.cand_count, d.sq != 0);
+    rev_generic_blk_body<MEAS>(row_ptr, col, val, d.D, d.ldd, d.h, d.qw, k, d.t_fwd, d.cand_sym + kPruneCap,
+                               d.cand_sym, d.cand, d.cand_count, d.sq != 0);
 }
 
 __global__ void k_prune_select_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int K)
@@ -960,7 +1034,11 @@ cudaError_t launch_prune(int meas, int k, const int32_t* row_ptr, const int32_t*
     switch (meas) {
     case M_RWMD: e = rev_meas_blk<M_RWMD>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, sq, st); break;
     case M_OMR: e = rev_meas_blk<M_OMR>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, sq, st); break;
-    case M_ICT: e = rev_meas<M_ICT>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, sq, st); break;
+    case M_ICT:
+        k_rev_generic_blk<M_ICT><<<kPruneCap, kRevW * 32, 0, st>>>(row_ptr, col, val, D, ldd, h, q_w, k, t_fwd,
+                                                                  sym + kPruneCap, sym, cand, count, sq);
+        e = cudaGetLastError();
+        break;
     default: e = rev_meas_blk<M_ACT>(k, row_ptr, col, val, kPruneCap, D, ldd, h, q_w, t_fwd, sym + kPruneCap, sym, cand, count, sq, st); break;
     }
     if (e != cudaSuccess) return e;
@@ -1028,13 +1106,11 @@ cudaError_t launch_prune_b(int meas, int k, const QDesc* qd, const int* nq, int 
     switch (meas) {
     case M_RWMD: e = rev_meas_blk_b<M_RWMD>(k, rev_warps, qd, nq, max_q, row_ptr, col, val, st); break;
     case M_OMR: e = rev_meas_blk_b<M_OMR>(k, rev_warps, qd, nq, max_q, row_ptr, col, val, st); break;
-    case M_ICT: {
-        const int warps = 8;
-        k_rev_generic_cand_b<M_ICT><<<dim3(kPruneCap / warps, (unsigned)max_q), warps * 32, 0, st>>>(qd, nq, row_ptr,
-                                                                                                   col, val, k);
+    case M_ICT:
+        k_rev_generic_cand_b<M_ICT><<<dim3(kPruneCap, (unsigned)max_q), kRevW * 32, 0, st>>>(qd, nq, row_ptr, col,
+                                                                                            val, k);
         e = cudaGetLastError();
         break;
-    }
     default: e = rev_meas_blk_b<M_ACT>(k, rev_warps, qd, nq, max_q, row_ptr, col, val, st); break;
     }
     if (e != cudaSuccess) return e;
