@@ -98,6 +98,14 @@ cudaEvent_t take_event(emd_db* db)
     return e;
 }
 
+// Whether a batch's forward tables are interleaved in groups of kFwdGroup queries (one CSR
+// sweep per group): register-width tables, and ICT tables (the loop form) when a group of
+// them fits the workspace's table columns.
+bool grouped_tables(const BatchWS& ws, int meas, int tk_b)
+{
+    return tk_b > 0 && (tk_b <= 16 || (meas == M_ICT && (int64_t)kFwdGroup * tk_b <= ws.b_tabcols));
+}
+
 int topk_launch_count(int64_t n) { return topk_blocks(n) > 1 ? 2 : 1; }
 
 int table_width(const emd_db* db, int meas, int k, int h)
@@ -366,7 +374,7 @@ emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, i
         }
         Phase p(db, 3, 1, st);
         EMD_CUDA(launch_fwd_b(meas, D_, nqd, B, db->row_ptr, db->col, db->val, n, dir == EMD_DIR_FWD,
-                              tk_b > 0 && tk_b <= 16, tk_b, st),
+                              grouped_tables(ws, meas, tk_b), tk_b, st),
                  "forward pass");
     }
     if (pruned) {
@@ -507,7 +515,7 @@ emd_status fill_descriptors(BatchWS& ws, int slot, emd_db* db, const int64_t* rp
 {
     const int nb = (int)(j1 - j0);
     const int tk_b = dir != EMD_DIR_REV ? table_width(db, meas, k, db->opt.max_query_h) : 0;
-    const bool grouped = tk_b > 0 && tk_b <= 16;
+    const bool grouped = grouped_tables(ws, meas, tk_b);
     QDesc* hd = ws.qd_host + (int64_t)slot * ws.max_batch;
     QDesc* dd = ws.qd_dev + (int64_t)slot * ws.max_batch;
     int* nqd = ws.nq_dev + slot;
@@ -641,7 +649,7 @@ bool batch_fits(const emd_db* db, const BatchWS& ws, const int64_t* rp, int64_t 
     int64_t cD = 0, cQ = 0, cP = 0, cT = 0;
     if (i1 - i0 > ws.max_batch) return false;
     const int tk_b = dir != EMD_DIR_REV ? table_width(db, meas, k, db->opt.max_query_h) : 0;
-    const bool grouped = tk_b > 0 && tk_b <= 16;
+    const bool grouped = grouped_tables(ws, meas, tk_b);
     for (int64_t i = i0; i < i1; ++i) {
         const int h = (int)(rp[i + 1] - rp[i]);
         const int64_t ldd = round_up(h, 32);

@@ -397,17 +397,27 @@ __device__ __forceinline__ void ict_fast_body(const float* __restrict__ D, int l
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= M) return;
     const float* Dr = D + row * ldd;
-    float z[kIctFast];
-    int s[kIctFast];
+    // two independent lists (columns 8i..8i+3 and 8i+4..8i+7; ldd % 32 == 0 keeps both loads
+    // in the row), merged by (value, column)
+    float z[kIctFast], zb[kIctFast];
+    int s[kIctFast], sb[kIctFast];
 #pragma unroll
-    for (int l = 0; l < kIctFast; ++l) { z[l] = INFINITY; s[l] = INT32_MAX; }
-    for (int j = 0; j < h; j += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(Dr + j);  // ldd % 32 == 0
+    for (int l = 0; l < kIctFast; ++l) { z[l] = zb[l] = INFINITY; s[l] = sb[l] = INT32_MAX; }
+    for (int j = 0; j < h; j += 8) {
+        const float4 v = *reinterpret_cast<const float4*>(Dr + j);
+        const float4 w = *reinterpret_cast<const float4*>(Dr + j + 4);
         insert_dj<kIctFast>(z, s, v.x, j);
+        if (j + 4 < h) insert_dj<kIctFast>(zb, sb, w.x, j + 4);
         if (j + 1 < h) insert_dj<kIctFast>(z, s, v.y, j + 1);
+        if (j + 5 < h) insert_dj<kIctFast>(zb, sb, w.y, j + 5);
         if (j + 2 < h) insert_dj<kIctFast>(z, s, v.z, j + 2);
+        if (j + 6 < h) insert_dj<kIctFast>(zb, sb, w.z, j + 6);
         if (j + 3 < h) insert_dj<kIctFast>(z, s, v.w, j + 3);
+        if (j + 7 < h) insert_dj<kIctFast>(zb, sb, w.w, j + 7);
     }
+#pragma unroll
+    for (int l = 0; l < kIctFast; ++l)
+        if (sb[l] != INT32_MAX) insert_dj_tie<kIctFast>(z, s, zb[l], sb[l]);
     const int lim = min(W, h), lf = min(lim, kIctFast);
     float r = xmax[row];
     int L = 0;
