@@ -44,7 +44,10 @@ typedef enum {
 /* Which lower bound.  RWMD is ACT with k = 1 (Alg. 3); OMR is Alg. 1 (k ignored);
  * ACT is Alg. 3 with top-k width k, i.e. k-1 capacity-limited transfers and the rest of
  * the mass to the k-th nearest (the evaluation's "ACT-j" is k = j+1); ICT is Alg. 2,
- * equal to ACT with k = the destination's histogram size. */
+ * equal to ACT with k = the destination's histogram size.  In the forward direction an ICT
+ * table row holds only the nearest query bins that the row's largest database weight can
+ * reach (Section 4 form of Alg. 2: the transfers stop once the mass is placed), at most
+ * max_table_k of them; a query that needs more is recomputed with rows of full width. */
 typedef enum { EMD_RWMD = 0, EMD_OMR = 1, EMD_ACT = 2, EMD_ICT = 3 } emd_measure;
 
 /* FWD moves each database histogram's mass into the query (the direction of the
@@ -79,7 +82,8 @@ typedef struct {
     emd_precision precision; /* default EMD_PREC_FP32 */
     int32_t rerank_margin;   /* BF16/FP8 only: extra candidates re-ranked in FP32 (default 8) */
     int32_t max_query_h;     /* largest query histogram accepted; sizes the workspace (default 2048) */
-    int32_t max_table_k;     /* largest forward top-k table width; ICT needs h_q <= this (default 64) */
+    int32_t max_table_k;     /* largest forward table width: k of ACT, and the entries an ICT row may
+                                hold before the query is recomputed at full width (default 64) */
     int32_t max_batch;       /* queries staged per device pass (default 64) */
     int32_t prune_topk;      /* 1 (default): exact pruned max-direction top-K for K <= 16 */
     int32_t lanes;           /* per-query pipelines, each with its own stream and workspace
@@ -175,7 +179,8 @@ emd_status emd_db_info_get(const emd_db* db, emd_db_info* out);
  *   out_dist  host float [n_queries * n_docs], row-major by query
  * Synchronous: returns after the results are in out_dist.
  * Errors: INVALID_ARG (bad query: weight < 0, sum off by > 1e-5, id out of range or
- * repeated, h_q out of range, k < 1), UNSUPPORTED (ICT forward with h_q > max_table_k),
+ * repeated, h_q out of range, k < 1), UNSUPPORTED (ACT with k > max_table_k; with the
+ * approximate precisions, ICT forward with h_q > max_table_k or a re-rank width above 32),
  * CUDA. */
 emd_status emd_query_batch(emd_db* db, const emd_queries* q, emd_measure meas, int32_t k,
                            emd_direction dir, float* out_dist);
