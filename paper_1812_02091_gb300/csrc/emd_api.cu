@@ -194,9 +194,9 @@ emd_status run_phase1(emd_db* db, Lane& L, const int32_t* qidx, int h, cudaStrea
     }
     Phase p(db, 1, db->tc ? 2 : 1, st);
     if (db->tc) {
-        EMD_CUDA(launch_tc_dist(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used, db->used_ids,
-                                db->v_used, L.q_hi, db->tcfmt == TC_SPLIT ? L.q_lo : nullptr, round_up(h, 128),
-                                L.q_scale, L.qnorm, qidx, h, db->kpad, L.D, ldd, db->err, st),
+        EMD_CUDA(launch_tc_dist(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used, db->v_used,
+                                L.q_hi, db->tcfmt == TC_SPLIT ? L.q_lo : nullptr, round_up(h, 128), L.q_scale,
+                                L.qnorm, h, db->kpad, L.D, ldd, db->err, st),
                  "distance matrix (tensor cores)");
         EMD_CUDA(launch_zero_ident(qidx, h, db->vslot, L.D, ldd, st), "identical ids");
     } else
@@ -342,8 +342,8 @@ emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, i
         if (db->tc && !hd) {
             Phase p(db, 1, 2, st);
             EMD_CUDA(launch_tc_dist_batch(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
-                                          db->used_ids, db->v_used, D_, nqd, B, db->kpad, db->tune_group_mult,
-                                          db->tune_stages, db->err, st),
+                                          db->v_used, D_, nqd, B, db->kpad, db->tune_group_mult, db->tune_stages,
+                                          db->err, st),
                      "distance matrices (tensor cores, batched)");
             EMD_CUDA(launch_zero_ident_b(D_, nqd, B, H, db->vslot, st), "identical ids");
         } else if (db->tc) {
@@ -351,8 +351,8 @@ emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, i
             for (int q = 0; q < nb; ++q) {
                 const QDesc& d = hd[q];
                 EMD_CUDA(launch_tc_dist(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
-                                        db->used_ids, db->v_used, d.q_hi, d.q_lo, d.npad, d.q_scale, d.qnorm, d.qidx,
-                                        d.h, db->kpad, d.D, d.ldd, db->err, st),
+                                        db->v_used, d.q_hi, d.q_lo, d.npad, d.q_scale, d.qnorm, d.h, db->kpad, d.D,
+                                        d.ldd, db->err, st),
                          "distance matrix (tensor cores)");
             }
             EMD_CUDA(launch_zero_ident_b(D_, nqd, B, H, db->vslot, st), "identical ids");
@@ -877,8 +877,7 @@ emd_status autotune(emd_db* db, const std::vector<int32_t>& used_host)
             for (int sg : stage_set) {
                 const float ms = timed([&] {
                     launch_tc_dist_batch(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
-                                         db->used_ids, db->v_used, D_, nqd, db->opt.max_batch, db->kpad, gm, sg,
-                                         db->err, st);
+                                         db->v_used, D_, nqd, db->opt.max_batch, db->kpad, gm, sg, db->err, st);
                 });
                 if (ms < 0.95f * best) {
                     best = ms;

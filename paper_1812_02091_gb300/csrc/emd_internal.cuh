@@ -140,11 +140,11 @@ constexpr int TC_E4M3 = 2;   // FP8 E4M3, one product: approximate
 
 // Tensor-core distance matrix.  Operands are panels in the canonical K-major core-matrix
 // layout (see launch_pack) with Mpad / Npad rows (multiples of 128) and Kpad = m rounded
-// up to 64; A_lo / B_lo only for TC_SPLIT.  D[u, j] as launch_dist_fp32, +inf for j in
-// [N, ldd).
+// up to 64; A_lo / B_lo only for TC_SPLIT.  D[u, j] = the squared distance by the norm
+// expansion (unclamped); the zeros of identical ids are left to launch_zero_ident.
 cudaError_t launch_tc_dist(int fmt, const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
-                           const float* a_norm, const int32_t* a_ids, int64_t M, const void* B_hi, const void* B_lo,
-                           int64_t Npad, const float* b_scale, const float* b_norm, const int32_t* b_ids, int N,
+                           const float* a_norm, int64_t M, const void* B_hi, const void* B_lo,
+                           int64_t Npad, const float* b_scale, const float* b_norm, int N,
                            int Kpad, float* D, int ldd, int* err, cudaStream_t st);
 
 // Pack R rows of an FP32 matrix (ld floats per row, m used) into format `fmt` panels of
@@ -221,7 +221,7 @@ int tc_batch_stages(int fmt, int KC);
 // vocabulary re-reads); stages caps the B ring (0: as many as fit).  Same results for any
 // choice.
 cudaError_t launch_tc_dist_batch(int fmt, const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
-                                 const float* a_norm, const int32_t* a_ids, int64_t M, const QDesc* qd, const int* nq,
+                                 const float* a_norm, int64_t M, const QDesc* qd, const int* nq,
                                  int max_q, int Kpad, int group_mult, int stages, int* err, cudaStream_t st);
 // max_tk: the largest table width of the batch; rerank: the approximate precisions' form
 // (V: the used vocabulary rows, ldv floats each).

@@ -216,9 +216,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 template <int FMT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_tc_dist(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_lo, int64_t Mpad,
-          const float* __restrict__ a_scale, const float* __restrict__ a_norm, const int32_t* __restrict__ a_ids,
+          const float* __restrict__ a_scale, const float* __restrict__ a_norm,
           int64_t M, const uint8_t* __restrict__ B_hi, const uint8_t* __restrict__ B_lo, int64_t Npad,
-          const float* __restrict__ b_scale, const float* __restrict__ b_norm, const int32_t* __restrict__ b_ids,
+          const float* __restrict__ b_scale, const float* __restrict__ b_norm,
           int N, int KC, int stages, float* __restrict__ D, int ldd, int* __restrict__ err)
 {
     constexpr bool SPLIT = FMT == TC_SPLIT;
@@ -446,7 +446,7 @@ template <int FMT>
 __global__ void __launch_bounds__(TCB_THREADS, 1)
 k_tc_dist_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_lo, int64_t Mpad,
                 const float* __restrict__ a_scale, const float* __restrict__ a_norm,
-                const int32_t* __restrict__ a_ids, int64_t M, const QDesc* __restrict__ qd,
+                int64_t M, const QDesc* __restrict__ qd,
                 const int* __restrict__ nq_dev, int groups, int KC, int stages, int* __restrict__ err)
 {
     constexpr bool SPLIT = FMT == TC_SPLIT;
@@ -808,16 +808,16 @@ cudaError_t launch_pack(int fmt, const float* src, int ld, int m, int64_t R, int
 
 template <int FMT>
 static cudaError_t tc_launch(dim3 grid, size_t smem, cudaStream_t st, const void* A_hi, const void* A_lo,
-                             int64_t Mpad, const float* a_scale, const float* a_norm, const int32_t* a_ids, int64_t M,
+                             int64_t Mpad, const float* a_scale, const float* a_norm, int64_t M,
                              const void* B_hi, const void* B_lo, int64_t Npad, const float* b_scale,
-                             const float* b_norm, const int32_t* b_ids, int N, int KC, int stages, float* D, int ldd,
+                             const float* b_norm, int N, int KC, int stages, float* D, int ldd,
                              int* err)
 {
     cudaError_t e = cudaFuncSetAttribute(k_tc_dist<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_tc_dist<FMT><<<grid, TC_THREADS, smem, st>>>(
-        static_cast<const uint8_t*>(A_hi), static_cast<const uint8_t*>(A_lo), Mpad, a_scale, a_norm, a_ids, M,
-        static_cast<const uint8_t*>(B_hi), static_cast<const uint8_t*>(B_lo), Npad, b_scale, b_norm, b_ids, N, KC,
+        static_cast<const uint8_t*>(A_hi), static_cast<const uint8_t*>(A_lo), Mpad, a_scale, a_norm, M,
+        static_cast<const uint8_t*>(B_hi), static_cast<const uint8_t*>(B_lo), Npad, b_scale, b_norm, N, KC,
         stages, D, ldd, err);
     return cudaGetLastError();
 }
@@ -840,19 +840,19 @@ int tc_batch_stages(int fmt, int KC)
 
 template <int FMT>
 static cudaError_t tc_batch_launch(dim3 grid, size_t smem, cudaStream_t st, const void* A_hi, const void* A_lo,
-                                   int64_t Mpad, const float* a_scale, const float* a_norm, const int32_t* a_ids,
+                                   int64_t Mpad, const float* a_scale, const float* a_norm,
                                    int64_t M, const QDesc* qd, const int* nq, int groups, int KC, int stages, int* err)
 {
     cudaError_t e = cudaFuncSetAttribute(k_tc_dist_batch<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_tc_dist_batch<FMT><<<grid, TCB_THREADS, smem, st>>>(static_cast<const uint8_t*>(A_hi),
                                                          static_cast<const uint8_t*>(A_lo), Mpad, a_scale, a_norm,
-                                                         a_ids, M, qd, nq, groups, KC, stages, err);
+                                                         M, qd, nq, groups, KC, stages, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_dist_batch(int fmt, const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
-                                 const float* a_norm, const int32_t* a_ids, int64_t M, const QDesc* qd, const int* nq,
+                                 const float* a_norm, int64_t M, const QDesc* qd, const int* nq,
                                  int max_q, int Kpad, int group_mult, int stages_req, int* err, cudaStream_t st)
 {
     if (M <= 0 || max_q <= 0) return cudaSuccess;
@@ -868,21 +868,21 @@ cudaError_t launch_tc_dist_batch(int fmt, const void* A_hi, const void* A_lo, in
     dim3 grid((unsigned)std::min<int64_t>((int64_t)m_tiles * groups, sms));
     switch (fmt) {
     case TC_SPLIT:
-        return tc_batch_launch<TC_SPLIT>(grid, smem, st, A_hi, A_lo, Mpad, a_scale, a_norm, a_ids, M, qd, nq, groups,
+        return tc_batch_launch<TC_SPLIT>(grid, smem, st, A_hi, A_lo, Mpad, a_scale, a_norm, M, qd, nq, groups,
                                          KC, stages, err);
     case TC_BF16:
-        return tc_batch_launch<TC_BF16>(grid, smem, st, A_hi, nullptr, Mpad, a_scale, a_norm, a_ids, M, qd, nq,
+        return tc_batch_launch<TC_BF16>(grid, smem, st, A_hi, nullptr, Mpad, a_scale, a_norm, M, qd, nq,
                                         groups, KC, stages, err);
     case TC_E4M3:
-        return tc_batch_launch<TC_E4M3>(grid, smem, st, A_hi, nullptr, Mpad, a_scale, a_norm, a_ids, M, qd, nq,
+        return tc_batch_launch<TC_E4M3>(grid, smem, st, A_hi, nullptr, Mpad, a_scale, a_norm, M, qd, nq,
                                         groups, KC, stages, err);
     default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_tc_dist(int fmt, const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
-                           const float* a_norm, const int32_t* a_ids, int64_t M, const void* B_hi, const void* B_lo,
-                           int64_t Npad, const float* b_scale, const float* b_norm, const int32_t* b_ids, int N,
+                           const float* a_norm, int64_t M, const void* B_hi, const void* B_lo,
+                           int64_t Npad, const float* b_scale, const float* b_norm, int N,
                            int Kpad, float* D, int ldd, int* err, cudaStream_t st)
 {
     if (M <= 0 || N <= 0) return cudaSuccess;
@@ -894,14 +894,14 @@ cudaError_t launch_tc_dist(int fmt, const void* A_hi, const void* A_lo, int64_t 
     dim3 grid((unsigned)std::min<int64_t>(tiles, sm_count()));
     switch (fmt) {
     case TC_SPLIT:
-        return tc_launch<TC_SPLIT>(grid, smem, st, A_hi, A_lo, Mpad, a_scale, a_norm, a_ids, M, B_hi, B_lo, Npad,
-                                   b_scale, b_norm, b_ids, N, KC, stages, D, ldd, err);
+        return tc_launch<TC_SPLIT>(grid, smem, st, A_hi, A_lo, Mpad, a_scale, a_norm, M, B_hi, B_lo, Npad,
+                                   b_scale, b_norm, N, KC, stages, D, ldd, err);
     case TC_BF16:
-        return tc_launch<TC_BF16>(grid, smem, st, A_hi, nullptr, Mpad, a_scale, a_norm, a_ids, M, B_hi, nullptr,
-                                  Npad, b_scale, b_norm, b_ids, N, KC, stages, D, ldd, err);
+        return tc_launch<TC_BF16>(grid, smem, st, A_hi, nullptr, Mpad, a_scale, a_norm, M, B_hi, nullptr,
+                                  Npad, b_scale, b_norm, N, KC, stages, D, ldd, err);
     case TC_E4M3:
-        return tc_launch<TC_E4M3>(grid, smem, st, A_hi, nullptr, Mpad, a_scale, a_norm, a_ids, M, B_hi, nullptr,
-                                  Npad, b_scale, b_norm, b_ids, N, KC, stages, D, ldd, err);
+        return tc_launch<TC_E4M3>(grid, smem, st, A_hi, nullptr, Mpad, a_scale, a_norm, M, B_hi, nullptr,
+                                  Npad, b_scale, b_norm, N, KC, stages, D, ldd, err);
     default: return cudaErrorInvalidValue;
     }
 }
