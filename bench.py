@@ -263,12 +263,13 @@ def serve_point(emd, srv, queries, order, rate, n_req, k, K, seed):
             "busy_retries": busy[0], "prune_fallbacks": st["prune_fallbacks"]}
 
 
-def serving_sweep(emd, w, opts, precision, rates, n_req, k, K, plain_saturation=True):
+def serving_sweep(emd, w, opts, precision, rates, n_req, k, K, plain_saturation=True, queries=None,
+                  database="workload 2 (text V=1e5, n=2e4)", requests="workload 4 queries", sat_req=4096):
     import emd_synth
-    queries = emd_synth.mixed_queries()
+    queries = emd_synth.mixed_queries() if queries is None else queries
     order = np.random.default_rng(7).permutation(queries.n)
-    out = {"database": "workload 2 (text V=1e5, n=2e4)",
-           "requests": "workload 4 queries: h_q log-uniform 5..2000, cycled in a fixed shuffled order",
+    out = {"database": database,
+           "requests": f"{requests}: h_q log-uniform 5..2000, cycled in a fixed shuffled order",
            "measure": f"LC-ACT k={k}, max of both directions, top-{K}",
            "server": "continuous batching: two executors, batches formed from the queue head while the "
                      "executor's distance-matrix columns hold them (16384 columns each), graph-replayed",
@@ -284,7 +285,7 @@ def serving_sweep(emd, w, opts, precision, rates, n_req, k, K, plain_saturation=
                 p = serve_point(emd, srv, queries, order, r, n_req, k, K, 100 + j)
                 p["precision"] = prec
                 out["points"].append(p)
-        sat = serve_point(emd, srv, queries, order, None, min(n_req, 4096), k, K, 99)
+        sat = serve_point(emd, srv, queries, order, None, min(n_req, sat_req), k, K, 99)
         sat["precision"] = prec
         out["saturation_" + prec] = sat
         emd.emd_server_destroy(srv)
@@ -324,6 +325,9 @@ def main():
     ap.add_argument("--baselines", action="store_true",
                     help="BoW cosine and word centroid distance top-K on workload 2 (Section 5 baselines) "
                          "beside LC-ACT; prints one line")
+    ap.add_argument("--serve5", action="store_true",
+                    help="serving sweep on the serving-size database (workload 5: V=2e5, n=1e6) with its own "
+                         "queries, --serve-rates, --serve-requests per point; prints one line")
     ap.add_argument("--allpairs", type=int, default=0, choices=[0, 2, 3],
                     help="all-pairs top-K over workload 2 (text) or 3 (images) instead of the bench "
                          "line: every histogram against all others; prints one line")
@@ -349,6 +353,8 @@ def main():
         return main_ict(args, local)
     if args.baselines:
         return main_baselines(args, local)
+    if args.serve5:
+        return main_serve5(args, local)
 
     import torch
     import paper_1812_02091_gb300 as emd
@@ -759,6 +765,26 @@ def main_ict(args, local):
     out["ict"]["top_recall_vs_oracle"] = float(np.mean(rec)) if rec else None
     out["ict"]["oracle_queries_h"] = [int(hs[q]) for q in oq]
     print(json.dumps(out))
+
+
+def main_serve5(args, local):
+    """The serving configuration at full size: workload 5 (V=2e5, m=300, n=1e6, nnz ~1.1e8)
+    resident, requests of workload 5's queries (h_q log-uniform 5..2000) through emd_server_*,
+    open-loop Poisson arrivals; plus a saturation point of the plain FP32 path."""
+    import torch
+    import emd_synth
+    import paper_1812_02091_gb300 as emd
+    torch.cuda.set_device(local)
+    t0 = time.perf_counter()
+    w = emd_synth.config(5, query_limit=4096)
+    gen_s = time.perf_counter() - t0
+    rates = [float(r) for r in args.serve_rates.split(",") if r.strip()]
+    opts = dict(device=local, max_query_h=2048, max_batch=args.batch)
+    out = serving_sweep(emd, w, opts, args.precision, rates, args.serve_requests, args.k, args.topk,
+                        queries=w.queries, database=f"workload 5 ({w.name}, nnz {w.db.nnz})",
+                        requests="workload 5 queries", sat_req=2048)
+    out["generation_s"] = gen_s
+    print(json.dumps({"serve5": out}))
 
 
 def main_baselines(args, local):
