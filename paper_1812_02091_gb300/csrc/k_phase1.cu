@@ -480,13 +480,13 @@ __global__ void k_table_generic(const float* __restrict__ D, int ldd, int64_t M,
 // rows are zero beyond m, so the padded width adds nothing).
 
 // Block: kRrRows rows, one thread each.  Selection as in table_body (each thread scans its
-// own row, four entries per load).  Exact sums: over the embedding in chunks of kRrDims
+// own row, four entries per load).  Exact sums: over the embedding in chunks of kRrDims (4)
 // dimensions, the chunk of every query row staged in shared memory once per block, each
 // thread holding its own row's chunk in registers and adding the squared differences to
 // each of its kc candidates (sequential over the dimensions).  Then the k smallest exact
 // sums (ties: lower j) are selected and the exact squared distances written back into D.
 // Dynamic shared memory: rerank_smem_bytes(h).
-constexpr int kRrRows = 256, kRrDims = 8;
+constexpr int kRrRows = 256, kRrDims = 4;
 
 __host__ __device__ constexpr size_t rerank_smem_bytes(int h) { return (size_t)h * kRrDims * 4; }
 
@@ -495,7 +495,7 @@ __device__ __forceinline__ void table_rerank_body(float* __restrict__ D, int ldd
                const float* __restrict__ Q, int ldv, const float* __restrict__ q_w, float2* __restrict__ tab,
                int32_t* __restrict__ tab_s, int64_t tile, int rs, int es)
 {
-    extern __shared__ float4 qs4[];  // [h][2]: Q[j][d0 .. d0 + 8)
+    extern __shared__ float4 qs4[];  // [h]: Q[j][d0 .. d0 + 4)
     const int tid = threadIdx.x;
     const int64_t row = tile * kRrRows + tid;
     const bool rok = row < M;
@@ -518,38 +518,24 @@ __device__ __forceinline__ void table_rerank_body(float* __restrict__ D, int ldd
     float acc[KCT];
 #pragma unroll
     for (int l = 0; l < KCT; ++l) acc[l] = 0.f;
-    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int d0 = 0; d0 < ldv; d0 += kRrDims) {
+    for (int d0 = 0; d0 < ldv; d0 += kRrDims) {  // ldv % 4 == 0
         __syncthreads();  // the previous chunk's readers are done
-        for (int t = tid; t < 2 * h; t += blockDim.x) {
-            const int dd = d0 + 4 * (t & 1);
-            qs4[t] = dd < ldv ? *reinterpret_cast<const float4*>(Q + (int64_t)(t >> 1) * ldv + dd) : zero4;
-        }
-        float4 v0 = zero4, v1 = zero4;
-        if (rok) {
-            v0 = *reinterpret_cast<const float4*>(V + row * ldv + d0);
-            if (d0 + 4 < ldv) v1 = *reinterpret_cast<const float4*>(V + row * ldv + d0 + 4);
-        }
+        for (int j = tid; j < h; j += blockDim.x)
+            qs4[j] = *reinterpret_cast<const float4*>(Q + (int64_t)j * ldv + d0);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (rok) v = *reinterpret_cast<const float4*>(V + row * ldv + d0);
         __syncthreads();
 #pragma unroll
         for (int c = 0; c < KCT; ++c) {
             if (c < kc && s[c] != INT32_MAX) {
-                const float4 a = qs4[2 * s[c]], b = qs4[2 * s[c] + 1];
-                float t = v0.x - a.x;
+                const float4 a = qs4[s[c]];
+                float t = v.x - a.x;
                 acc[c] = fmaf(t, t, acc[c]);
-                t = v0.y - a.y;
+                t = v.y - a.y;
                 acc[c] = fmaf(t, t, acc[c]);
-                t = v0.z - a.z;
+                t = v.z - a.z;
                 acc[c] = fmaf(t, t, acc[c]);
-                t = v0.w - a.w;
-                acc[c] = fmaf(t, t, acc[c]);
-                t = v1.x - b.x;
-                acc[c] = fmaf(t, t, acc[c]);
-                t = v1.y - b.y;
-                acc[c] = fmaf(t, t, acc[c]);
-                t = v1.z - b.z;
-                acc[c] = fmaf(t, t, acc[c]);
-                t = v1.w - b.w;
+                t = v.w - a.w;
                 acc[c] = fmaf(t, t, acc[c]);
             }
         }
