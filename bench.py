@@ -323,7 +323,7 @@ def main():
                     help="LC-ICT symmetric top-K on workload 2's database and queries beside LC-ACT on the "
                          "same batches, recall against the oracle; prints one line")
     ap.add_argument("--baselines", action="store_true",
-                    help="BoW cosine and word centroid distance top-K on workload 2 (Section 5 baselines) "
+                    help="BoW cosine and word centroid distance top-K on workload 2 (Section 6 baselines) "
                          "beside LC-ACT; prints one line")
     ap.add_argument("--serve5", action="store_true",
                     help="serving sweep on the serving-size database (workload 5: V=2e5, n=1e6) with its own "
@@ -788,7 +788,7 @@ def main_serve5(args, local):
 
 
 def main_baselines(args, local):
-    """Section 5 baselines on workload 2: BoW cosine and WCD top-K through the host API
+    """Section 6 baselines on workload 2: BoW cosine and WCD top-K through the host API
     (timed end to end per batch of --batch queries), the kernel times from the library's
     events, the BoW sweep against the HBM roofline (per group of eight queries one pass over
     the CSR: 8 nnz + 4 (n + 1) + 4 n + 4 n x 8 bytes), and recall against the oracle."""
@@ -803,7 +803,7 @@ def main_baselines(args, local):
                            emd.emd_db_options_default(device=local, max_query_h=1024, max_batch=B))
     info = emd.emd_db_info_get(db)
     subs = [w.queries.subset(np.arange(s * B, (s + 1) * B)) for s in range(steps + 1)]
-    out = {"mode": f"Section 5 baselines, top-{K}", "workload": w.name, "queries": f"{steps} batches of {B}"}
+    out = {"mode": f"Section 6 baselines, top-{K}", "workload": w.name, "queries": f"{steps} batches of {B}"}
     pk = peaks()
     for kind in ("bow", "wcd"):
         emd.emd_baseline_topk(db, subs[steps].row_ptr, subs[steps].col, subs[steps].val, kind, K)  # warm-up
@@ -843,7 +843,7 @@ def main_baselines(args, local):
 
 
 def main_allpairs(args, local):
-    """emd_all_pairs_topk on a whole workload database (the evaluation shape of Section 5):
+    """emd_all_pairs_topk on a whole workload database (the evaluation shape of Section 6):
     one timed call after one warm-up call, then one profiled call for the phase split."""
     import torch
     import emd_synth

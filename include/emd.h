@@ -1,14 +1,14 @@
 /*
  * emd.h -- C ABI of the GB300 (sm_103a) library for the linear-complexity EMD lower
  * bounds of Atasu & Mittelholzer, "Low-Complexity Data-Parallel Earth Mover's Distance
- * Approximations" (ICML 2019): LC-RWMD, OMR (Alg. 1), LC-ACT (Alg. 3, Section 4) and
+ * Approximations" (ICML 2019): LC-RWMD, OMR (Alg. 1), LC-ACT (Alg. 3, Section 5) and
  * ICT (Alg. 2), for query histograms against a device-resident database of sparse
  * histograms, in either direction or the maximum of both, plus top-K neighbours.
  *
- * Problem statement (Section 2.2 and Section 5): one query histogram q is compared with
+ * Problem statement (Section 2.2 and Section 6): one query histogram q is compared with
  * n database histograms over a vocabulary of v coordinates with m-dimensional
- * embeddings; the ground cost is the Euclidean distance between embeddings (Section 5)
- * or, in cost-matrix mode, any nonnegative v x v matrix (Section 3, remark on p-th
+ * embeddings; the ground cost is the Euclidean distance between embeddings (Section 6)
+ * or, in cost-matrix mode, any nonnegative v x v matrix (Section 4, remark on p-th
  * Wasserstein distances).  Every histogram is L1-normalised (Section 2).
  *
  * Conventions shared by every entry point
@@ -46,16 +46,16 @@ typedef enum {
  * the mass to the k-th nearest (the evaluation's "ACT-j" is k = j+1); ICT is Alg. 2,
  * equal to ACT with k = the destination's histogram size.  In the forward direction an ICT
  * table row holds only the nearest query bins that the row's largest database weight can
- * reach (Section 4 form of Alg. 2: the transfers stop once the mass is placed), at most
+ * reach (Section 5 form of Alg. 2: the transfers stop once the mass is placed), at most
  * max_table_k of them; a query that needs more is recomputed with rows of full width. */
 typedef enum { EMD_RWMD = 0, EMD_OMR = 1, EMD_ACT = 2, EMD_ICT = 3 } emd_measure;
 
 /* FWD moves each database histogram's mass into the query (the direction of the
- * linear-complexity Phase 2, Section 4); REV moves the query's mass into each database
- * histogram; MAX is the symmetric bound max(FWD, REV) of Sections 3 and 5. */
+ * linear-complexity Phase 2, Section 5); REV moves the query's mass into each database
+ * histogram; MAX is the symmetric bound max(FWD, REV) of Sections 4 and 6. */
 typedef enum { EMD_DIR_FWD = 0, EMD_DIR_REV = 1, EMD_DIR_MAX = 2 } emd_direction;
 
-/* Arithmetic of the Phase-1 distance matrix (Section 4).  FP32 is the plain method (FP32
+/* Arithmetic of the Phase-1 distance matrix (Section 5).  FP32 is the plain method (FP32
  * FFMA on the CUDA cores).  FP32_TC computes the same FP32-grade distances on the tensor
  * cores: each embedding row is scaled by its absmax and split into two FP16 parts
  * (hi + lo * 2^-11), and the three products hi*hi, hi*lo, lo*hi are accumulated in FP32,
@@ -144,7 +144,7 @@ typedef struct {
 /* Fill *opt with the defaults listed above.  Never fails. */
 void emd_db_options_default(emd_db_options* opt);
 
-/* Build the device-resident database (Section 4: X in CSR form; V, the embeddings).
+/* Build the device-resident database (Section 5: X in CSR form; V, the embeddings).
  *   emb          host float [v * m] row-major embeddings, or NULL in cost-matrix mode
  *   v, m         vocabulary size (>= 1) and embedding width (1..4096; ignored if emb NULL)
  *   cost_matrix  host float [v * v] row-major nonnegative ground costs with a zero
@@ -171,8 +171,8 @@ emd_status emd_db_destroy(emd_db* db);
 /* Sizes and memory of the handle.  INVALID_ARG on NULL arguments. */
 emd_status emd_db_info_get(const emd_db* db, emd_db_info* out);
 
-/* Distances from each query to every database histogram (Section 4: the vector t of
- * size n per query; Section 5: the maximum of both directions for EMD_DIR_MAX).
+/* Distances from each query to every database histogram (Section 5: the vector t of
+ * size n per query; Section 6: the maximum of both directions for EMD_DIR_MAX).
  *   q         host query batch (see emd_queries); every h_q in 1..max_query_h
  *   meas, k   measure and top-k width (k >= 1; ignored by RWMD, OMR, ICT)
  *   dir       direction
@@ -185,7 +185,7 @@ emd_status emd_db_info_get(const emd_db* db, emd_db_info* out);
 emd_status emd_query_batch(emd_db* db, const emd_queries* q, emd_measure meas, int32_t k,
                            emd_direction dir, float* out_dist);
 
-/* The K nearest database histograms of each query (Section 5, top-l neighbours), in
+/* The K nearest database histograms of each query (Section 6, top-l neighbours), in
  * ascending (distance, document id) order.
  * For EMD_DIR_MAX with K <= 16 (and prune_topk set) the reverse direction is evaluated
  * only where it can matter: max(fwd, rev) >= fwd, so the documents are taken in ascending
@@ -245,7 +245,7 @@ emd_status emd_topk_select_static(const float* t_dev, int64_t n_rows, int64_t n,
  * EMD_OK, or INVALID_ARG when a kernel met an out-of-range id, or CUDA. */
 emd_status emd_db_check_device_errors(emd_db* db);
 
-/* Phase-1 table of one query, for inspection (Section 4: Z, S and W, each v_used x k,
+/* Phase-1 table of one query, for inspection (Section 5: Z, S and W, each v_used x k,
  * rows in used-vocabulary order = ascending vocabulary id).
  *   used_ids  host int32 [v_used] (may be NULL): vocabulary id of each table row
  *   z, w      host float [v_used * k]; s host int32 [v_used * k] (query bin index)
@@ -260,10 +260,10 @@ emd_status emd_db_set_profiling(emd_db* db, int32_t on);
 emd_status emd_db_profile_get(emd_db* db, emd_profile* out);
 emd_status emd_db_profile_reset(emd_db* db);
 
-/* All-pairs top-K over the database itself, the shape of the paper's evaluation (Section 5:
+/* All-pairs top-K over the database itself, the shape of the paper's evaluation (Section 6:
  * every histogram ranked against all others).  For each database histogram a, the K smallest
  * max(fwd(b -> a), fwd(a -> b)) over b != a, ordered by (distance, id), where fwd(x -> y) is
- * the forward bound (Section 4, Eq. 6-9) with histogram y as the query: the reverse bound of
+ * the forward bound (Section 5, Eq. 6-9) with histogram y as the query: the reverse bound of
  * a pair is the forward bound of the transposed pair, so one forward pass per histogram
  * gives both directions.  out_idx / out_dist: n_docs x K host arrays.  Needs 4 n_docs^2
  * bytes of device memory for the forward matrix during the call (OUT_OF_MEMORY otherwise);
@@ -271,7 +271,7 @@ emd_status emd_db_profile_reset(emd_db* db);
 emd_status emd_all_pairs_topk(emd_db* db, emd_measure meas, int32_t k, int32_t K, int64_t* out_idx,
                               float* out_dist);
 
-/* The two cheap baselines the paper compares against (Section 5), on the same resident
+/* The two cheap baselines the paper compares against (Section 6), on the same resident
  * database and query format:
  *   EMD_BOW_COSINE  bag-of-words cosine similarity: the dot product of the two weight
  *                   vectors after L2 normalisation (no embeddings, any database mode);
@@ -305,7 +305,7 @@ emd_status emd_topk_merge(int32_t n_shards, const int64_t* const* shard_idx, con
  * worker thread forms batches from the head of the queue -- requests with the head's
  * (measure, k, K), in arrival order -- and runs each on one of two executors, each with its
  * own batch workspace and stream, with the batched kernel sequence of emd_topk (direction
- * EMD_DIR_MAX, Section 5).  Requests that arrive while a batch is on the GPU join the next
+ * EMD_DIR_MAX, Section 6).  Requests that arrive while a batch is on the GPU join the next
  * batch as soon as an executor is free (continuous batching).  Every query of a batch is
  * computed exactly as alone, so a result is bit-identical whether it was served alone or in
  * any mix, and equals emd_topk's.

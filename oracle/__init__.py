@@ -8,9 +8,9 @@ package.  The product path (the CUDA library and its binding) never loads it.
     (Section 2.1) for a given cost matrix;
   * exact EMD (Eq. 1-3) by a small min-cost-flow solver, for tiny histograms;
   * the per-pair definition for one query against a whole database (both directions);
-  * the linear-complexity form of Section 4 (Phase 1, Eq. 6-8, Eq. 9) for the forward
+  * the linear-complexity form of Section 5 (Phase 1, Eq. 6-8, Eq. 9) for the forward
     direction, with the reverse direction gathered from the Phase-1 distances;
-  * the two cheap baselines of Section 5: bag-of-words cosine similarity and the word
+  * the two cheap baselines of Section 6: bag-of-words cosine similarity and the word
     centroid distance.
 This module compiles it with gcc on first use and wraps it with ctypes.
 """
@@ -159,7 +159,7 @@ def pair_db(emb, cost, db, q_idx, q_w, meas: str, k: int = 1, fwd=True, rev=True
 
 
 def lc_query(emb, cost, db, q_idx, q_w, meas: str, k: int = 1, fwd=True, rev=True):
-    """Linear-complexity form (Section 4) for one query."""
+    """Linear-complexity form (Section 5) for one query."""
     return _run("oracle_lc_query", emb, cost, db, q_idx, q_w, meas, k, fwd, rev)
 
 
@@ -177,7 +177,7 @@ def phase1(emb, cost, rows, q_idx, q_w, kk: int):
 
 
 def symmetric(t_fwd, t_rev):
-    """Section 5: the symmetric measure is the maximum of the two directions."""
+    """Section 6: the symmetric measure is the maximum of the two directions."""
     return np.maximum(t_fwd, t_rev)
 
 
@@ -236,7 +236,7 @@ def lc_query_split(emb, cost, db, q_idx, q_w, meas: str, k: int = 1, fwd=True, r
     return tf, tr
 
 
-# ----------------------------------------------------------------- Section 5 baselines
+# ----------------------------------------------------------------- Section 6 baselines
 
 def bow_cosine(v: int, db, q_idx, q_w) -> np.ndarray:
     """Bag-of-words cosine similarity of one query with every database histogram."""

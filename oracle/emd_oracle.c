@@ -31,7 +31,7 @@
 
 /* ------------------------------------------------------------------ ground cost */
 
-/* Section 5: the transportation cost between two coordinates is the Euclidean (L2)
+/* Section 6: the transportation cost between two coordinates is the Euclidean (L2)
  * distance of their embedding vectors. */
 static double euclid(const float* a, const float* b, int32_t m)
 {
@@ -286,7 +286,7 @@ int32_t oracle_pair_db(const float* emb, int32_t m, const float* cost, int64_t v
     return 0;
 }
 
-/* ------------------------------------------------------------------ LC-ACT (Section 4) */
+/* ------------------------------------------------------------------ LC-ACT (Section 5) */
 
 /* Linear-complexity form for one query against the database.
  *
@@ -398,7 +398,7 @@ int32_t oracle_lc_query(const float* emb, int32_t m, const float* cost, int64_t 
     return 0;
 }
 
-/* Phase 1 alone (for inspecting the Z / S / W tables of Section 4): rows are the given
+/* Phase 1 alone (for inspecting the Z / S / W tables of Section 5): rows are the given
  * vocabulary ids; outputs are rows x kk, row-major. */
 void oracle_phase1(const float* emb, int32_t m, const float* cost, int64_t v,
                    const int32_t* rows, int64_t nrows, const int32_t* q_idx, const float* q_w,
@@ -419,9 +419,9 @@ void oracle_phase1(const float* emb, int32_t m, const float* cost, int64_t v,
     free(buf); free(s); free(Du);
 }
 
-/* ------------------------------------------------------------------ Section 5 baselines */
+/* ------------------------------------------------------------------ Section 6 baselines */
 
-/* Bag-of-words cosine similarity of the query with every database histogram (Section 5:
+/* Bag-of-words cosine similarity of the query with every database histogram (Section 6:
  * the dot product of the two weight vectors after L2 normalisation; it ignores the
  * embeddings).  Coordinates held by one side only contribute nothing.  A histogram with
  * zero norm has similarity 0.  Returns 0, or -1 on allocation failure. */
@@ -449,7 +449,7 @@ int32_t oracle_bow_db(int64_t v, const int64_t* row_ptr, const int32_t* col, con
     return 0;
 }
 
-/* Word centroid distance (Section 5, after Kusner et al.): the Euclidean distance between
+/* Word centroid distance (Section 6, after Kusner et al.): the Euclidean distance between
  * the weighted averages sum_i p_i E_i / sum_i p_i of the two histograms' embedding vectors.
  * Returns 0, or -1 on allocation failure. */
 int32_t oracle_wcd_db(const float* emb, int32_t m, const int64_t* row_ptr, const int32_t* col, const float* val,

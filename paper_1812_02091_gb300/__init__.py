@@ -281,7 +281,12 @@ def emd_topk_device(db, q_row_ptr_host, q_idx_dev, q_w_dev, out_idx_dev, out_dis
 def emd_topk_select_static(t_dev, K: int, out_idx_dev, out_dist_dev, stream=None):
     """Top-K of each row of a device distance matrix [n_rows, n], without any allocation
     (scratch is a fixed array inside the library; see include/emd.h)."""
+    if t_dev.dim() not in (1, 2):
+        raise ValueError("t_dev must be 1-D (one row) or 2-D [n_rows, n]")
     n_rows, n = (t_dev.shape[0], t_dev.shape[1]) if t_dev.dim() == 2 else (1, t_dev.shape[0])
+    for name, o in (("out_idx_dev", out_idx_dev), ("out_dist_dev", out_dist_dev)):
+        if o.numel() < n_rows * int(K):
+            raise ValueError(f"{name} holds {o.numel()} elements, fewer than n_rows * K = {n_rows * int(K)}")
     _check(load().emd_topk_select_static(_dev(t_dev, "float32"), n_rows, n, int(K),
                                          _dev(out_idx_dev, "int64"), _dev(out_dist_dev, "float32"),
                                          _stream(stream)))
@@ -359,7 +364,7 @@ BASELINES = {"bow": 0, "wcd": 1}
 
 
 def emd_baseline_batch(db, q_row_ptr, q_idx, q_w, kind="bow", n_docs=None):
-    """Section 5 baselines: BoW cosine similarity ("bow") or word centroid distance ("wcd"),
+    """Section 6 baselines: BoW cosine similarity ("bow") or word centroid distance ("wcd"),
     float32[n_queries, n_docs]."""
     n = n_docs if n_docs is not None else emd_db_info_get(db)["n_docs"]
     q, keep = _queries(q_row_ptr, q_idx, q_w)

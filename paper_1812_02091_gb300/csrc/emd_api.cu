@@ -1049,7 +1049,7 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
     TRYC(cudaMemcpyAsync(db->val, val, nnz * sizeof(float), cudaMemcpyHostToDevice, st), "copy");
     {
         // the largest weight any document puts on each used row: how far an ICT table row
-        // must reach (Algorithm 4 moves at most that much mass out of a bin of the row)
+        // must reach (Algorithm 2 moves at most that much mass out of a bin of the row)
         std::vector<float> xmax((size_t)vu, 0.f);
         for (int64_t e = 0; e < nnz; ++e) xmax[col_used[e]] = std::max(xmax[col_used[e]], val[e]);
         TRY(dalloc(db, &db->xmax, vu));

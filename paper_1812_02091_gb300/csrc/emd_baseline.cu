@@ -1,4 +1,4 @@
-// Entry points of the Section 5 baselines (bag-of-words cosine similarity, word centroid
+// Entry points of the Section 6 baselines (bag-of-words cosine similarity, word centroid
 // distance) on the resident database; see include/emd.h.
 
 #include <cuda_runtime.h>

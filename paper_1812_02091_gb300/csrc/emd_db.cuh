@@ -182,7 +182,7 @@ struct emd_db {
     int tune_rev_warps = 4;    // warps per candidate document in the pruned reverse pass
     std::map<emd::GraphKey, emd::GraphEntry> graphs;
 
-    // Section 5 baselines (allocated and prepared at first use)
+    // Section 6 baselines (allocated and prepared at first use)
     float* bow_dense = nullptr;     // ceil(max_batch / 8) x v_used x 8 interleaved query vectors
     float* doc_inv_norm = nullptr;  // n
     float* doc_centroid = nullptr;  // n x ldc (word centroid distance)

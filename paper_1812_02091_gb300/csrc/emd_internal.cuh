@@ -71,7 +71,7 @@ cudaError_t launch_dist_gather(const float* cost, int64_t v, const int32_t* a_id
                                const int32_t* b_ids, int N, float* D, int ldd, int* err,
                                cudaStream_t st);
 
-// Phase-1 table (Section 4): per row u the k smallest D[u, 0..h) (ties by column),
+// Phase-1 table (Section 5): per row u the k smallest D[u, 0..h) (ties by column),
 // written as tab[u * k + l] = (z, w = q_w[s]) and optionally tab_s[u * k + l] = s; z is the
 // distance (the square root of the entry when sq).
 cudaError_t launch_table(const float* D, int ldd, int64_t M, int h, int k, const float* q_w,
@@ -85,7 +85,7 @@ cudaError_t launch_vslot(const int32_t* used_ids, int64_t v_used, int64_t v, int
 cudaError_t launch_zero_ident(const int32_t* q_idx, int h, const int32_t* vslot, float* D, int ldd,
                               cudaStream_t st);
 
-// ICT table (Section 3.3, Algorithm 4, in the linear form of Section 4): per row u the
+// ICT table (Section 4.2, Algorithm 2, in the linear form of Section 5): per row u the
 // smallest D[u, 0..h) in ascending (distance, column) order, only as many as the largest
 // database weight at u, xmax[u], needs before its residual reaches 0 (capacity-limited
 // transfers in FP32, the same steps as the forward pass), at most W entries.  Entries past
@@ -253,7 +253,7 @@ cudaError_t launch_topk_b(const QDesc* qd, const int* nq, int max_q, int64_t n, 
 cudaError_t launch_prune_b(int meas, int k, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
                            const int32_t* col, const float* val, int64_t n, int K, int rev_warps, cudaStream_t st);
 
-// All-pairs form (Section 5's evaluation over the database itself).  Vocabulary ids of
+// All-pairs form (Section 6's evaluation over the database itself).  Vocabulary ids of
 // the database's nonzeros (used_ids[col[e]]), the query bins of the database histograms.
 cudaError_t launch_map_ids(const int32_t* col, int64_t nnz, const int32_t* used_ids, int32_t* out, cudaStream_t st);
 // F (n x n, row stride n): F[a][b] <- max(F[a][b], F[b][a]) for all a, b and F[a][a] <- +inf.

@@ -1,4 +1,4 @@
-// The two cheap baselines of Section 5, on the database resident for the EMD bounds:
+// The two cheap baselines of Section 6, on the database resident for the EMD bounds:
 //
 //  * bag-of-words cosine similarity: the dot product of the query's and each document's
 //    weights after L2 normalisation (no embeddings).  The query side is scattered into a

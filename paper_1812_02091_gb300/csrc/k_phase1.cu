@@ -1,4 +1,4 @@
-// Phase 1 of LC-ACT (Section 4): the distance matrix D between the used vocabulary and
+// Phase 1 of LC-ACT (Section 5): the distance matrix D between the used vocabulary and
 // the query's coordinates, and the per-row top-k table (Z, S, W).
 //
 // This file holds the plain FP32 path: a register-tiled SIMT distance kernel (FP32 FFMA,

@@ -1,4 +1,4 @@
-// Sparse passes over the database (Section 4, Phase 2 and 3; Section 5, the reverse
+// Sparse passes over the database (Section 5, Phase 2 and 3; Section 6, the reverse
 // direction and the symmetric maximum) and the top-K neighbour selection.
 #include <math.h>
 
@@ -1139,7 +1139,7 @@ __global__ void k_map_ids(const int32_t* __restrict__ col, int64_t nnz, const in
 }
 
 // One 32 x 32 tile pair (I, J), I <= J, per block: both tiles through shared memory, the
-// element-wise max written to both (the symmetric bound of Section 5 from the forward values
+// element-wise max written to both (the symmetric bound of Section 6 from the forward values
 // of a pair and of its transpose); the diagonal becomes +inf (no self-match).
 __global__ void k_sym_max(float* __restrict__ F, int64_t n)
 {

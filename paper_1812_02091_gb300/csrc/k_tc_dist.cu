@@ -1,5 +1,5 @@
-// Phase 1 of LC-ACT (Section 4) on the 5th-generation tensor cores of sm_103a: the
-// distance matrix D = dist(V, Q) from the product V Q^T (Section 4: "a matrix-matrix
+// Phase 1 of LC-ACT (Section 5) on the 5th-generation tensor cores of sm_103a: the
+// distance matrix D = dist(V, Q) from the product V Q^T (Section 5: "a matrix-matrix
 // multiplication between V and the transpose of Q") with FP32 accumulators in TMEM.
 //
 // Operands carry a per-row absmax scale s (x = s * stored value).  Three operand formats:

@@ -1,5 +1,5 @@
 """All-pairs top-K over the database itself (emd_all_pairs_topk): every histogram ranked
-against all others, as in the evaluation of Section 5, against the oracle.
+against all others, as in the evaluation of Section 6, against the oracle.
 
 The device computes one forward pass per histogram and takes the reverse bound of a pair
 as the forward bound of the transposed pair; the oracle computes both directions of each
@@ -66,7 +66,7 @@ def test_all_pairs_text(emd, precision, meas, k):
 
 
 def test_all_pairs_images(emd):
-    """Cost-matrix mode (28 x 28 pixel grid, Section 5 image workload)."""
+    """Cost-matrix mode (28 x 28 pixel grid, Section 6 image workload)."""
     w = emd_synth.config(3, query_limit=1, n_docs=200)
     db = make_db(emd, w, max_query_h=784)
     try:

@@ -1,4 +1,4 @@
-"""The Section 5 baselines on the device (bag-of-words cosine similarity, word centroid
+"""The Section 6 baselines on the device (bag-of-words cosine similarity, word centroid
 distance) against the FP64 oracle."""
 import numpy as np
 import pytest

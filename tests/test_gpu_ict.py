@@ -1,9 +1,9 @@
-"""ICT (Section 3.3, Algorithm 4) at full query sizes, against the oracle.
+"""ICT (Section 4.2, Algorithm 2) at full query sizes, against the oracle.
 
 The forward table of a vocabulary row holds the row's nearest query bins in ascending
 order only as far as the largest database weight of that row needs (its residual reaches
 0), at most max_table_k entries; a query for which some row needs more is recomputed with
-tables of full width h.  Either way the forward values are those of Algorithm 4 with every
+tables of full width h.  Either way the forward values are those of Algorithm 2 with every
 destination available, so they are checked against the oracle's ICT at the FP32
 tolerance, and the narrow and full-width forms against each other bit for bit."""
 import numpy as np
@@ -110,7 +110,7 @@ def test_ict_topk_pruned(emd, work, want):
 
 
 def test_ict_above_act(emd, work):
-    """ACT is non-decreasing in k and reaches ICT at k = h (Section 3.3): on the device,
+    """ACT is non-decreasing in k and reaches ICT at k = h (Section 4.2): on the device,
     forward ICT >= forward ACT for k = 1, 4, 16 within rounding."""
     w = work
     db = make_db(emd, w, precision="fp32_tc", max_query_h=512)

@@ -164,7 +164,7 @@ def test_identical_histogram_is_at_zero(emd, tiny):
 
 
 def test_full_overlap_rwmd_zero_omr_positive(emd):
-    """Section 3 / Table 5: same support, different weights -> RWMD 0, OMR > 0."""
+    """Section 4 / Table 5: same support, different weights -> RWMD 0, OMR > 0."""
     w = emd_synth.config(3, query_limit=1, n_docs=64)
     db = make_db(emd, w, max_query_h=784)
     try:

@@ -2,7 +2,7 @@
 depend on the mix of requests in flight, admission by workspace memory, queue limits and
 argument checks.
 
-Each request is the symmetric top-K (max of both directions, Section 5) with the same
+Each request is the symmetric top-K (max of both directions, Section 6) with the same
 kernel sequence as emd_topk, so a result served alone, served among many overlapping
 requests, and returned by emd_topk must be bit-identical.
 """

@@ -1,4 +1,4 @@
-"""Pins for the oracle's two Section 5 baselines (bag-of-words cosine similarity, word
+"""Pins for the oracle's two Section 6 baselines (bag-of-words cosine similarity, word
 centroid distance) against facts that do not come from the oracle:
   * BoW: scipy's cosine distance on dense weight vectors, p = q gives 1, disjoint supports
     give 0, invariance to scaling the weights, a hand-computed value;

@@ -1,4 +1,4 @@
-"""The linear-complexity form (Section 4: Phase 1, Eq. 6-8, Eq. 9) reaches the per-pair
+"""The linear-complexity form (Section 5: Phase 1, Eq. 6-8, Eq. 9) reaches the per-pair
 definition (Algorithms 1-3) exactly: a vocabulary row's top-k over the query is the same
 set whether computed once for the vocabulary or per pair (Section 2.2).  Only the
 summation order differs, so the two agree to FP64 round-off."""
@@ -45,7 +45,7 @@ def test_lc_form_equals_pairwise_image(image_small, meas, k):
 
 
 def test_image_rwmd_vanishes_on_full_overlap(image_small):
-    """Section 3 / Table 5: a query whose support equals a document's support has RWMD 0
+    """Section 4 / Table 5: a query whose support equals a document's support has RWMD 0
     to that document in both directions, while OMR stays positive."""
     w = image_small
     cols, vals = w.db.row(0)

@@ -121,7 +121,7 @@ def test_rwmd_is_outflow_only_optimum(hp, hq, ov, seed):
 
 @pytest.mark.parametrize("hp,hq,ov,seed", CASES)
 def test_omr_is_optimum_with_overlap_edges_capped(hp, hq, ov, seed):
-    """Section 3.1: OMR imposes Eq. 4 only between overlapping coordinates (C = 0)."""
+    """Section 4.1: OMR imposes Eq. 4 only between overlapping coordinates (C = 0)."""
     p, q, C = random_pair(np.random.default_rng(seed), hp, hq, ov)
     assert oracle.omr(p, q, C) == pytest.approx(lp(C, p, q, C == 0.0), rel=1e-9, abs=1e-12)
 
@@ -186,7 +186,7 @@ def test_identical_histograms_are_at_distance_zero(seed):
 @pytest.mark.parametrize("seed", range(8))
 def test_effectiveness_omr_versus_rwmd(seed):
     """Appendix A: with an effective cost, OMR = 0 only for p = q; RWMD is 0 whenever the
-    supports coincide (Section 3, Table 5)."""
+    supports coincide (Section 4, Table 5)."""
     rng = np.random.default_rng(4000 + seed)
     h = int(rng.integers(2, 9))
     p, q, C = random_pair(rng, h, h, overlap=h)

@@ -65,3 +65,40 @@ def test_static_scratch_rejects_sizes_beyond_its_limit(setup):
     assert e.value.name == "INVALID_ARG" and "64 rows" in str(e.value)
     with pytest.raises(emd.EmdError):
         emd.emd_topk_select_static(big[:2], 65, oi, od)
+
+
+def test_static_scratch_after_a_larger_call(setup):
+    """Calls that use fewer rows or fewer blocks than the previous one must ignore what
+    that call left in the shared array: 5 rows over 20000 values (several blocks per
+    row), then 1 row over 4096 values (two blocks) and 1 row over 1500 values (one
+    block), each against a stable numpy argsort."""
+    import torch
+    emd, db, w, q, qi, qw, t, s = setup
+    K = 16
+    oi = torch.empty((q.n, K), dtype=torch.int64, device="cuda")
+    od = torch.empty((q.n, K), dtype=torch.float32, device="cuda")
+    emd.emd_topk_select_static(t, K, oi, od, stream=s)
+    rng = np.random.default_rng(17)
+    for n in (4096, 1500):
+        x = rng.uniform(0.0, 1.0, n).astype(np.float32)
+        x[rng.integers(0, n, 8)] = 0.25  # repeated values: ties go to the lower index
+        xt = torch.from_numpy(x).cuda()
+        oi1 = torch.full((1, K), -7, dtype=torch.int64, device="cuda")
+        od1 = torch.full((1, K), -7.0, dtype=torch.float32, device="cuda")
+        emd.emd_topk_select_static(xt, K, oi1, od1, stream=s)
+        torch.cuda.synchronize()
+        want = np.argsort(x, kind="stable")[:K]
+        np.testing.assert_array_equal(oi1.cpu().numpy()[0], want, err_msg=f"n={n}")
+        np.testing.assert_array_equal(od1.cpu().numpy()[0], x[want])
+
+
+def test_static_wrapper_rejects_bad_shapes(setup):
+    import torch
+    emd, *_ = setup
+    t3 = torch.zeros((2, 3, 100), dtype=torch.float32, device="cuda")
+    oi = torch.empty((2, 4), dtype=torch.int64, device="cuda")
+    od = torch.empty((2, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError):
+        emd.emd_topk_select_static(t3, 4, oi, od)
+    with pytest.raises(ValueError):
+        emd.emd_topk_select_static(t3[0], 8, oi, od)  # outputs hold 8 < 3 x 8 elements
