@@ -24,8 +24,11 @@ Recipe (all numpy PCG64):
 """
 from __future__ import annotations
 
+import ctypes
 import dataclasses
 import hashlib
+import os
+import subprocess
 
 import numpy as np
 
@@ -140,7 +143,58 @@ def _zipf_sets_chunk(rng, cdf, lengths):
     return result
 
 
-def zipf_histograms(rng, V: int, lengths: np.ndarray, s: float = 1.1, chunk: int = 50000) -> Histograms:
+_HELPER_SRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_zipf.c")
+_HELPER_LIB = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libzipf.so")
+_helper = None
+
+
+def _zipf_helper():
+    """The C form of the per-row selection (emd_synth/_zipf.c, compiled with gcc on first
+    use), or None when no C compiler is available (the numpy form is used then)."""
+    global _helper
+    if _helper is not None:
+        return _helper or None
+    try:
+        os.makedirs(os.path.dirname(_HELPER_LIB), exist_ok=True)
+        if not os.path.exists(_HELPER_LIB) or os.path.getmtime(_HELPER_LIB) < os.path.getmtime(_HELPER_SRC):
+            tmp = _HELPER_LIB + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _HELPER_SRC],
+                                  stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            os.replace(tmp, _HELPER_LIB)
+        L = ctypes.CDLL(_HELPER_LIB)
+        P, i64 = ctypes.c_void_p, ctypes.c_int64
+        L.zipf_first_distinct.argtypes = [P, i64, P, P, P, i64, P, i64, P, P, P, P]
+        L.zipf_first_distinct.restype = None
+        _helper = L
+    except (OSError, subprocess.CalledProcessError):
+        _helper = False
+    return _helper or None
+
+
+def _zipf_rows_c(L, rng, cdf, lengths, col, offsets, stamp, tag):
+    """Same rows, same random draws as _zipf_sets_chunk, with the per-row selection in C;
+    rows are written into col at their offsets.  Returns the next free stamp tag."""
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    V = cdf.shape[0]
+    todo = np.arange(lengths.shape[0])
+    factor = 2.0
+    buf = np.empty(max(1, int(lengths.max()) if lengths.size else 1), dtype=np.int32)
+    while todo.size:
+        lens = np.ascontiguousarray(lengths[todo], dtype=np.int64)
+        draws = np.ceil(lens * factor).astype(np.int64) + 8
+        u = rng.random(int(draws.sum()))
+        off = np.ascontiguousarray(offsets[todo], dtype=np.int64)
+        ok = np.zeros(todo.size, dtype=np.uint8)
+        L.zipf_first_distinct(p(cdf), V, p(u), p(draws), p(lens), todo.size, p(stamp), tag, p(col), p(off), p(ok),
+                              p(buf))
+        tag += todo.size
+        todo = todo[ok == 0]
+        factor *= 2.0
+    return tag
+
+
+def zipf_histograms(rng, V: int, lengths: np.ndarray, s: float = 1.1, chunk: int = 50000,
+                    use_c: bool = True) -> Histograms:
     if np.any(lengths > V):
         raise ValueError("histogram longer than the vocabulary")
     cdf = zipf_cdf(V, s)
@@ -148,10 +202,16 @@ def zipf_histograms(rng, V: int, lengths: np.ndarray, s: float = 1.1, chunk: int
     row_ptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(lengths, out=row_ptr[1:])
     col = np.empty(int(row_ptr[-1]), dtype=np.int32)
+    L = _zipf_helper() if use_c else None
+    stamp = np.full(V, -1, dtype=np.int64) if L else None
+    tag = 0
     for a in range(0, n, chunk):
         b = min(n, a + chunk)
-        sets = _zipf_sets_chunk(rng, cdf, lengths[a:b])
-        col[row_ptr[a]:row_ptr[b]] = np.concatenate(sets)
+        if L:
+            tag = _zipf_rows_c(L, rng, cdf, lengths[a:b], col, row_ptr[a:b], stamp, tag)
+        else:
+            sets = _zipf_sets_chunk(rng, cdf, lengths[a:b])
+            col[row_ptr[a]:row_ptr[b]] = np.concatenate(sets)
     counts = rng.integers(1, 6, size=col.shape[0]).astype(np.float64)
     sums = np.add.reduceat(counts, row_ptr[:-1]) if n else np.zeros(0)
     val = (counts / np.repeat(sums, lengths)).astype(np.float32)

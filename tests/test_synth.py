@@ -45,3 +45,16 @@ def test_mixed_query_lengths_are_log_uniform():
     L = emd_synth._lengths(rng, 20000, emd_synth.QUERY_LEN_MIXED)
     assert L.min() >= 5 and L.max() <= 2000
     assert 250 < L.mean() < 420 and 80 < np.median(L) < 120
+
+
+def test_c_row_selection_equals_numpy_form():
+    """The C helper and the numpy form of the successive-sampling step give the same
+    histograms from the same seed (including rows that need a second round of draws)."""
+    for V, n, law in ((60, 300, ("uniform", 40, 60)), (5000, 700, ("loguniform", 5, 2000)),
+                      (100000, 2000, ("lognormal", 100.0, 0.5, 10, 1000))):
+        lens = np.minimum(emd_synth._lengths(np.random.Generator(np.random.PCG64(3)), n, law), V)
+        a = emd_synth.zipf_histograms(np.random.Generator(np.random.PCG64(9)), V, lens, chunk=257, use_c=False)
+        b = emd_synth.zipf_histograms(np.random.Generator(np.random.PCG64(9)), V, lens, chunk=257, use_c=True)
+        assert np.array_equal(a.row_ptr, b.row_ptr)
+        assert np.array_equal(a.col, b.col)
+        assert np.array_equal(a.val, b.val)
