@@ -69,6 +69,10 @@ def lib():
                 f.restype = i32
             L.oracle_phase1.argtypes = [P, i32, P, i64, P, i64, P, P, i32, i32, P, P, P]
             L.oracle_phase1.restype = None
+            L.oracle_lc_phase23.argtypes = [P, P, P, i64, P, P, P, i32, i32, i32, P]
+            L.oracle_lc_phase23.restype = i32
+            L.oracle_lc_rev.argtypes = [P, P, P, i64, P, P, P, i32, i32, i32, P]
+            L.oracle_lc_rev.restype = i32
             L.oracle_bow_db.argtypes = [i64, P, P, P, i64, P, P, i32, P]
             L.oracle_bow_db.restype = i32
             L.oracle_wcd_db.argtypes = [P, i32, P, P, P, i64, P, P, i32, P]
@@ -234,6 +238,187 @@ def lc_query_split(emb, cost, db, q_idx, q_w, meas: str, k: int = 1, fwd=True, r
     tf = np.concatenate([p[0] for p in parts]) if fwd else None
     tr = np.concatenate([p[1] for p in parts]) if rev else None
     return tf, tr
+
+
+def table_width(meas: str, k: int, hq: int) -> int:
+    """Columns of the Phase-1 tables of a query with hq bins (as oracle_lc_query sizes them)."""
+    kk = {"rwmd": 1, "omr": 2, "ict": hq}.get(meas, min(k, hq))
+    return min(kk, hq)
+
+
+class LcPrep:
+    """What the split forms reuse across queries of one database: contiguous copies of
+    its arrays, the used vocabulary (ascending ids, Section 2.2) and the table row of
+    every vocabulary id."""
+
+    def __init__(self, emb, cost, db):
+        self.emb, self.cost, self.rp, self.col, self.val = _db_args(emb, cost, db)
+        self.used = np.unique(self.col).astype(np.int32)
+        self.v = self.emb.shape[0] if self.cost is None else self.cost.shape[0]
+        self.row_of_id = np.full(self.v, -1, dtype=np.int64)
+        self.row_of_id[self.used] = np.arange(len(self.used))
+        self.n = len(self.rp) - 1
+
+
+def prepare(emb, cost, db) -> LcPrep:
+    return LcPrep(emb, cost, db)
+
+
+def _phase23(P, Z, W, kk, meas, hq, threads):
+    """Phase 2 and 3 (oracle_lc_phase23) on document slices, on threads."""
+    L = lib()
+    bounds = np.linspace(0, P.n, threads + 1).astype(np.int64)
+    tf = np.empty(P.n)
+
+    def one(i):
+        d0, d1 = int(bounds[i]), int(bounds[i + 1])
+        if d1 > d0:
+            a = int(P.rp[d0])
+            sub_rp = np.ascontiguousarray(P.rp[d0:d1 + 1] - a)
+            out = np.empty(d1 - d0)
+            if L.oracle_lc_phase23(_p(sub_rp), _p(P.col[a:]), _p(P.val[a:]), d1 - d0, _p(P.row_of_id), _p(Z), _p(W),
+                                   kk, MEASURES[meas], hq, _p(out)) != 0:
+                raise MemoryError("oracle allocation failed")
+            tf[d0:d1] = out
+
+    with concurrent.futures.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(one, range(threads)))
+    return tf
+
+
+def lc_forward_split(emb, cost, db, q_idx, q_w, meas: str, k: int = 1, threads: int | None = None,
+                     prep: LcPrep | None = None):
+    """Forward values (Section 5: Phase 1, then Phase 2 and 3) of one query against the
+    whole database, the work spread over threads without changing any value: Phase 1
+    (oracle_phase1) on slices of the used vocabulary's rows, then Phase 2 and 3
+    (oracle_lc_phase23) on slices of the documents.  Each table row and each document is
+    computed by the same steps as in oracle_lc_query, so the values are identical to its
+    forward output (tests/test_oracle_lc.py)."""
+    threads = max(1, threads or os.cpu_count() or 1)
+    P = prep or LcPrep(emb, cost, db)
+    q_idx = np.ascontiguousarray(q_idx, dtype=np.int32)
+    q_w = np.ascontiguousarray(q_w, dtype=np.float32)
+    hq = len(q_idx)
+    kk = table_width(meas, k, hq)
+    vu = len(P.used)
+    Z = np.empty((vu, kk)); W = np.empty((vu, kk)); S = np.empty((vu, kk), dtype=np.int32)
+    m = P.emb.shape[1]
+    L = lib()
+    rb = np.linspace(0, vu, threads + 1).astype(np.int64)
+
+    def p1(i):
+        a, b = int(rb[i]), int(rb[i + 1])
+        if b > a:
+            L.oracle_phase1(_p(P.emb), m, _p(P.cost), P.v, _p(P.used[a:b]), b - a, _p(q_idx), _p(q_w), hq, kk,
+                            _p(Z[a:b]), _p(S[a:b]), _p(W[a:b]))
+
+    with concurrent.futures.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(p1, range(threads)))
+    return _phase23(P, Z, W, kk, meas, hq, threads)
+
+
+def lc_query_full_split(emb, cost, db, q_idx, q_w, meas: str, k: int = 1, threads: int | None = None,
+                        prep: LcPrep | None = None):
+    """Both directions for every document, as oracle_lc_query computes them, spread over
+    threads: the Phase-1 block D (oracle_cost_block on slices of the used vocabulary's
+    rows), each row's first kk entries in (distance, position) order (a stable sort),
+    Phase 2 and 3 (oracle_lc_phase23) and the reverse direction (oracle_lc_rev) on slices
+    of the documents.  Identical to oracle_lc_query (tests/test_oracle_lc.py)."""
+    threads = max(1, threads or os.cpu_count() or 1)
+    P = prep or LcPrep(emb, cost, db)
+    q_idx = np.ascontiguousarray(q_idx, dtype=np.int32)
+    q_w = np.ascontiguousarray(q_w, dtype=np.float32)
+    hq = len(q_idx)
+    kk = table_width(meas, k, hq)
+    vu = len(P.used)
+    D = np.empty((vu, hq))
+    Z = np.empty((vu, kk)); W = np.empty((vu, kk))
+    qw64 = q_w.astype(np.float64)
+    m = P.emb.shape[1]
+    L = lib()
+    rb = np.linspace(0, vu, threads + 1).astype(np.int64)
+
+    def p1(i):
+        a, b = int(rb[i]), int(rb[i + 1])
+        if b > a:
+            L.oracle_cost_block(_p(P.emb), m, _p(P.cost), P.v, _p(P.used[a:b]), b - a, _p(q_idx), hq, _p(D[a:b]))
+            order = np.argsort(D[a:b], axis=1, kind="stable")[:, :kk]
+            Z[a:b] = np.take_along_axis(D[a:b], order, axis=1)
+            W[a:b] = qw64[order]
+
+    with concurrent.futures.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(p1, range(threads)))
+    tf = _phase23(P, Z, W, kk, meas, hq, threads)
+    tr = np.empty(P.n)
+    bounds = np.linspace(0, P.n, threads + 1).astype(np.int64)
+
+    def rev(i):
+        d0, d1 = int(bounds[i]), int(bounds[i + 1])
+        if d1 > d0:
+            a = int(P.rp[d0])
+            sub_rp = np.ascontiguousarray(P.rp[d0:d1 + 1] - a)
+            out = np.empty(d1 - d0)
+            if L.oracle_lc_rev(_p(sub_rp), _p(P.col[a:]), _p(P.val[a:]), d1 - d0, _p(P.row_of_id), _p(D), _p(q_w), hq,
+                               MEASURES[meas], int(k), _p(out)) != 0:
+                raise MemoryError("oracle allocation failed")
+            tr[d0:d1] = out
+
+    with concurrent.futures.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(rev, range(threads)))
+    return tf, tr
+
+
+class SymTopK:
+    """Exact top-K of max(fwd, rev) for one query (Section 6: top-l search with the
+    symmetric bound), from oracle routines only: the forward values of every document
+    (lc_forward_split), then the reverse values by the per-pair definition (pair_db on one
+    document) in ascending forward order.  Since max(fwd, rev) >= fwd, once the next
+    forward value exceeds the K-th smallest symmetric value found so far, no remaining
+    document can enter the top-K (strictly larger, so not even by the id order)."""
+
+    def __init__(self, emb, cost, db, q_idx, q_w, meas: str, k: int, K: int, threads: int | None = None,
+                 prep: LcPrep | None = None):
+        self.args = (emb, cost, db, np.asarray(q_idx), np.asarray(q_w), meas, k)
+        self.threads = max(1, threads or os.cpu_count() or 1)
+        self.fwd = lc_forward_split(emb, cost, db, q_idx, q_w, meas, k, self.threads, prep)
+        self.rev = {}
+        n = len(self.fwd)
+        order = np.lexsort((np.arange(n), self.fwd))
+        pos, chunk = 0, 4 * self.threads
+        while pos < n:
+            kth = self.kth(K)
+            take = [int(d) for d in order[pos:pos + chunk] if self.fwd[d] <= kth]
+            if not take:
+                break
+            self.reverse(take)
+            pos += chunk
+        keys = sorted((self.sym(d), d) for d in self.rev)
+        self.idx = np.array([d for _, d in keys[:K]], dtype=np.int64)
+        self.dist = np.array([v for v, _ in keys[:K]])
+
+    def kth(self, K):
+        vals = sorted(self.sym(d) for d in self.rev)
+        return vals[K - 1] if len(vals) >= K else np.inf
+
+    def sym(self, d: int) -> float:
+        return max(self.fwd[d], self.rev[d])
+
+    def reverse(self, docs):
+        """Reverse values (per-pair definition) of the given documents, on threads."""
+        emb, cost, db, q_idx, q_w, meas, k = self.args
+        docs = [int(d) for d in docs if int(d) not in self.rev]
+
+        def one(d):
+            return d, pair_db(emb, cost, _slice(db, d, d + 1), q_idx, q_w, meas, k, fwd=False, rev=True)[1][0]
+
+        with concurrent.futures.ThreadPoolExecutor(max_workers=self.threads) as ex:
+            for d, r in ex.map(one, docs):
+                self.rev[d] = r
+
+    def sym_of(self, docs) -> np.ndarray:
+        """Symmetric values of any documents (reverse values computed where missing)."""
+        self.reverse(docs)
+        return np.array([self.sym(int(d)) for d in docs])
 
 
 # ----------------------------------------------------------------- Section 6 baselines

@@ -398,6 +398,75 @@ int32_t oracle_lc_query(const float* emb, int32_t m, const float* cost, int64_t 
     return 0;
 }
 
+/* Phase 2 (Eq. 6-8) and Phase 3 (Eq. 9) alone, from Phase-1 tables computed elsewhere
+ * (oracle_phase1 on the rows of the used vocabulary): the same steps, in the same order,
+ * as the forward part of oracle_lc_query.  Table row r belongs to vocabulary id used[r];
+ * row_of_id[c] = r for every column id c of the database (v entries).  Z and W are
+ * (number of rows) x kk.  Returns 0, or -1 on allocation failure. */
+int32_t oracle_lc_phase23(const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n,
+                          const int64_t* row_of_id, const double* Z, const double* W, int32_t kk,
+                          int32_t measure, int32_t hq, double* t_fwd)
+{
+    int64_t nnz = row_ptr[n];
+    double* X = (double*)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+    if (!X) return -1;
+    for (int64_t e = 0; e < nnz; ++e) X[e] = (double)val[e]; /* X^(0) = X */
+    for (int64_t d = 0; d < n; ++d) t_fwd[d] = 0.0;          /* t^(0) = 0 */
+    /* Phase 2 */
+    for (int32_t l = 0; l < kk - 1; ++l) {
+        for (int64_t d = 0; d < n; ++d) {
+            for (int64_t e = row_ptr[d]; e < row_ptr[d + 1]; ++e) {
+                int64_t u = row_of_id[col[e]];
+                int32_t ku = measure == ORACLE_OMR ? ((Z[u * kk] == 0.0 && hq > 1) ? 2 : 1) : kk;
+                if (l >= ku - 1) continue;
+                double y = fmin(X[e], W[u * kk + l]);  /* Eq. 6 (R5) */
+                X[e] = X[e] - y;                         /* Eq. 7 */
+                t_fwd[d] = t_fwd[d] + y * Z[u * kk + l]; /* Eq. 8 */
+            }
+        }
+    }
+    /* Phase 3 (Eq. 9) */
+    for (int64_t d = 0; d < n; ++d)
+        for (int64_t e = row_ptr[d]; e < row_ptr[d + 1]; ++e) {
+            int64_t u = row_of_id[col[e]];
+            int32_t ku = measure == ORACLE_OMR ? ((Z[u * kk] == 0.0 && hq > 1) ? 2 : 1) : kk;
+            t_fwd[d] = t_fwd[d] + X[e] * Z[u * kk + (ku - 1)];
+        }
+    free(X);
+    return 0;
+}
+
+/* The reverse direction of oracle_lc_query alone, from a Phase-1 distance block computed
+ * elsewhere: D is (number of rows) x hq, row r for vocabulary id used[r], row_of_id[c] = r
+ * for every column id c of the database.  For each document the same steps as in
+ * oracle_lc_query: the pairwise algorithm with the query as source and the document as
+ * destination, cost block gathered from D.  Returns 0, or -1 on allocation failure. */
+int32_t oracle_lc_rev(const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n,
+                      const int64_t* row_of_id, const double* D, const float* q_w, int32_t hq,
+                      int32_t measure, int32_t k, double* t_rev)
+{
+    double* qw = (double*)malloc(sizeof(double) * (size_t)hq);
+    if (!qw) return -1;
+    for (int32_t j = 0; j < hq; ++j) qw[j] = (double)q_w[j];
+    for (int64_t d = 0; d < n; ++d) {
+        int64_t a = row_ptr[d];
+        int32_t hd = (int32_t)(row_ptr[d + 1] - a);
+        double* pw = (double*)malloc(sizeof(double) * (size_t)(hd > 0 ? hd : 1));
+        double* CT = (double*)malloc(sizeof(double) * (size_t)(hd > 0 ? hd : 1) * hq);
+        if (!pw || !CT) { free(CT); free(pw); free(qw); return -1; }
+        for (int32_t i = 0; i < hd; ++i) {
+            pw[i] = (double)val[a + i];
+            const double* Du = D + row_of_id[col[a + i]] * hq;
+            for (int32_t j = 0; j < hq; ++j) CT[(int64_t)j * hd + i] = Du[j];
+        }
+        t_rev[d] = oracle_measure(measure, qw, hq, pw, hd, CT, k);
+        free(CT);
+        free(pw);
+    }
+    free(qw);
+    return 0;
+}
+
 /* Phase 1 alone (for inspecting the Z / S / W tables of Section 5): rows are the given
  * vocabulary ids; outputs are rows x kk, row-major. */
 void oracle_phase1(const float* emb, int32_t m, const float* cost, int64_t v,

@@ -69,3 +69,65 @@ def test_phase1_tables_match_sorted_rows(tiny):
         np.testing.assert_array_equal(S[r], order)
         np.testing.assert_array_equal(Z[r], C[r, order])
         np.testing.assert_array_equal(W[r], qw[order].astype(np.float64))
+
+
+@pytest.mark.parametrize("meas,k", [("rwmd", 1), ("omr", 1), ("act", 2), ("act", 4), ("act", 9), ("ict", 1)])
+def test_split_forward_equals_lc_query(tiny, meas, k):
+    """lc_forward_split (Phase 1 on vocabulary-row slices, Phase 2 and 3 on document
+    slices, on threads) takes the same steps per table row and per document as
+    oracle_lc_query, so its forward values are identical."""
+    for qi in (0, 4, 9):
+        qidx, qw = tiny.queries.row(qi)
+        lf, _ = oracle.lc_query(tiny.emb, None, tiny.db, qidx, qw, meas, k, rev=False)
+        for threads in (1, 3, 8):
+            sf = oracle.lc_forward_split(tiny.emb, None, tiny.db, qidx, qw, meas, k, threads=threads)
+            np.testing.assert_array_equal(sf, lf)
+
+
+def test_split_forward_equals_lc_query_images(image_small):
+    w = image_small
+    qidx, qw = w.queries.row(1)
+    for meas, k in (("act", 3), ("omr", 1)):
+        lf, _ = oracle.lc_query(w.emb, w.cost, w.db, qidx, qw, meas, k, rev=False)
+        np.testing.assert_array_equal(oracle.lc_forward_split(w.emb, w.cost, w.db, qidx, qw, meas, k, threads=4), lf)
+
+
+@pytest.mark.parametrize("meas,k,K", [("act", 2, 10), ("act", 4, 16), ("omr", 1, 5), ("ict", 1, 16), ("rwmd", 1, 1)])
+def test_certified_symmetric_topk_equals_brute_force(tiny, meas, k, K):
+    """SymTopK evaluates the reverse direction only in ascending forward order until the
+    certificate holds; its top-K equals the top-K of max(fwd, rev) over all documents
+    (per-pair definition), ids in (distance, id) order, distances to FP64 round-off."""
+    for qi in range(tiny.queries.n):
+        qidx, qw = tiny.queries.row(qi)
+        pf, pr = oracle.pair_db(tiny.emb, None, tiny.db, qidx, qw, meas, k)
+        want_i, want_d = oracle.topk(np.maximum(pf, pr), K)
+        got = oracle.SymTopK(tiny.emb, None, tiny.db, qidx, qw, meas, k, K, threads=4)
+        np.testing.assert_array_equal(got.idx, want_i)
+        np.testing.assert_allclose(got.dist, want_d, rtol=1e-12, atol=0)
+        assert len(got.rev) < tiny.db.n  # the certificate stopped the scan early
+        extra = [3, 500, 999]
+        np.testing.assert_allclose(got.sym_of(extra), np.maximum(pf, pr)[extra], rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("meas,k", [("rwmd", 1), ("omr", 1), ("act", 3), ("act", 40), ("ict", 1)])
+def test_full_split_equals_lc_query(tiny, meas, k):
+    """lc_query_full_split (cost block on row slices, stable sort of each row, Phase 2 and 3
+    and the reverse direction on document slices) equals oracle_lc_query bit for bit."""
+    prep = oracle.prepare(tiny.emb, None, tiny.db)
+    for qi in (1, 5, 8):
+        qidx, qw = tiny.queries.row(qi)
+        lf, lr = oracle.lc_query(tiny.emb, None, tiny.db, qidx, qw, meas, k)
+        for threads in (1, 5):
+            sf, sr = oracle.lc_query_full_split(tiny.emb, None, tiny.db, qidx, qw, meas, k, threads=threads, prep=prep)
+            np.testing.assert_array_equal(sf, lf)
+            np.testing.assert_array_equal(sr, lr)
+
+
+def test_full_split_equals_lc_query_images(image_small):
+    w = image_small
+    qidx, qw = w.queries.row(2)
+    for meas, k in (("act", 5), ("ict", 1)):
+        lf, lr = oracle.lc_query(w.emb, w.cost, w.db, qidx, qw, meas, k)
+        sf, sr = oracle.lc_query_full_split(w.emb, w.cost, w.db, qidx, qw, meas, k, threads=3)
+        np.testing.assert_array_equal(sf, lf)
+        np.testing.assert_array_equal(sr, lr)
