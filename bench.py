@@ -1,13 +1,17 @@
-"""Benchmark: LC-ACT top-16 neighbour queries per second on the text-like workload at
-scale (vocabulary 100000 x 300 FP32 unit embeddings, 20000 database histograms of
-log-normal size, median 100; 1000 queries of the same law), FP32 plain method, the
-symmetric bound max(fwd, rev), k = 4.
+"""Benchmark: LC-ACT (k = 4) top-16 neighbour queries per second on the serving-size
+database (workload 5: vocabulary 200000 x 300 FP32 unit embeddings, 1000000 database
+histograms of log-normal size, median 100, nnz ~1.13e8; queries h_q log-uniform 5..2000),
+symmetric bound max(fwd, rev), against the plain FP32 path at equal top-16 recall, with
+p50/p99 serving latency.
 
-A step is one batch of B queries through the whole path (query staging, Phase-1 distance
-matrix, top-k table, forward sparse pass, reverse pass + max, top-16 selection).  The
-top-16 of max(fwd, rev) is exact and pruned: the reverse pass runs on the 63 best forward
-candidates and the answer is certified against the 64th forward value (fallback: all
-documents).  The same batches are also timed with the reverse pass over every document.
+A step is one batch of B queries through the whole path (query staging, Phase-1 distances,
+top-k table, forward sparse pass, reverse pass + max, top-16 selection), inputs resident in
+HBM, CUDA events on the launch stream, L2 flushed between steps.  The top-16 of max(fwd,
+rev) is exact: the reverse pass runs on the best forward candidates and a certificate
+guards the answer (fallback: all documents).  Beside the headline form the same batches
+run in the other Phase-1 arithmetics (plain FP32 SIMT, BF16, FP8-E4M3); a stratified
+subset of the queries is checked against the FP64 oracle (a child process on cores of its
+own, while the GPU work runs); every form gets an open-loop serving sweep.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -35,8 +39,9 @@ if ROOT not in sys.path:
 
 METRIC = "LC-ACT queries/s vs plain FP32 path at equal top-16 recall; p50/p99 latency"
 UNIT = "queries/s"
-WORKLOAD = ("text V=100000 m=300 FP32 unit embeddings, n=20000 docs (nnz~2.26e6, log-normal "
-            "h median 100), 1000 queries of the same law")
+WORKLOAD5 = ("serving database (config 5): V=200000 vocabulary, m=300 FP32 unit embeddings, n=1000000 docs "
+             "(log-normal h median 100, nnz~1.13e8), queries h_q log-uniform 5..2000")
+QUERY_POOL = 4096  # workload-5 queries generated for the timed batches and the serving requests
 
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
@@ -136,20 +141,7 @@ def recorded_traffic(kernel_file: str, phase: str):
     return rec.get("bytes_per_launch") if rec.get("source_sha256") == sha else None
 
 
-# ------------------------------------------------------------------ CPU oracle leg
-
-def oracle_sample(w, qids, meas, k, threads):
-    """The FP64 oracle, unchanged, on a bounded sample of queries: each query's database is
-    cut into `threads` document slices run concurrently (results identical to one call)."""
-    import oracle
-    t0 = time.perf_counter()
-    res = []
-    for qi in qids:
-        idx, wt = w.queries.row(int(qi))
-        tf, tr = oracle.lc_query_split(w.emb, None, w.db, idx, wt, meas, k, threads=threads)
-        res.append(np.maximum(tf, tr))
-    return time.perf_counter() - t0, res
-
+# ------------------------------------------------------------------ oracle helpers
 
 def recall_at(gpu_idx, want, K):
     """Top-K recall against the oracle with ties at the K-th distance counted as hits."""
@@ -158,56 +150,6 @@ def recall_at(gpu_idx, want, K):
     truth = set(int(i) for i in order[:K])
     hits = sum(1 for i in gpu_idx if int(i) in truth or abs(want[int(i)] - dK) <= 1e-5 * dK + 1e-9)
     return hits / K
-
-
-# ------------------------------------------------------------------ precision forms
-
-def precision_forms(emd, torch, w, opts, k, K, steps, batch, flush, threads, n_oracle=2):
-    """Workload 4: mixed-size queries (h_q log-uniform 5..2000) on the workload-2 database,
-    pruned symmetric top-K in each Phase-1 arithmetic on the same batches; queries/s from
-    CUDA events (L2 flushed between batches), top-K recall and the relative error of the
-    returned distances against the FP64 oracle on sampled queries."""
-    import types
-    import emd_synth
-    mixed = emd_synth.mixed_queries(steps * batch)
-    hs = np.diff(mixed.row_ptr)
-    dev = []
-    for s in range(steps):
-        sub = mixed.subset(np.arange(s * batch, (s + 1) * batch))
-        dev.append((sub.row_ptr, torch.from_numpy(sub.col).cuda(), torch.from_numpy(sub.val).cuda()))
-    oq = [i for i in range(batch) if hs[i] <= 400][:n_oracle]
-    _, want = oracle_sample(types.SimpleNamespace(emb=w.emb, db=w.db, queries=mixed), oq, "act", k, threads)
-    stream = torch.cuda.current_stream()
-    out = {"queries": f"{steps} batches of {batch} workload-4 queries (h_q log-uniform 5..2000, mean "
-                      f"{hs.mean():.0f} here)",
-           "oracle_queries": [int(hs[i]) for i in oq], "forms": {}}
-    for prec in ("fp32", "fp32_tc", "bf16", "fp8"):
-        db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
-                               emd.emd_db_options_default(precision=prec, **opts))
-        oi = torch.empty((batch, K), dtype=torch.int64, device="cuda")
-        od = torch.empty((batch, K), dtype=torch.float32, device="cuda")
-        for s in range(min(2, steps)):
-            emd.emd_topk_device(db, *dev[s], oi, od, "act", k, "max", K, stream=stream.cuda_stream)
-        torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        first = None
-        for s in range(steps):
-            flush.fill_(float(s))
-            ev[s][0].record(stream)
-            emd.emd_topk_device(db, *dev[s], oi, od, "act", k, "max", K, stream=stream.cuda_stream)
-            ev[s][1].record(stream)
-            if s == 0:
-                first = (oi.clone(), od.clone())
-        torch.cuda.synchronize()
-        emd.emd_db_check_device_errors(db)
-        total = sum(a.elapsed_time(b) for a, b in ev) / 1e3
-        gi, gd = first[0].cpu().numpy(), first[1].cpu().numpy()
-        rec = [recall_at(gi[q], want[j], K) for j, q in enumerate(oq)]
-        err = [float(np.max(np.abs(gd[q] - want[j][gi[q]]) / want[j][gi[q]])) for j, q in enumerate(oq)]
-        out["forms"][prec] = {"queries_per_s": batch * steps / total, "ms_per_batch": 1e3 * total / steps,
-                              "top16_recall": float(np.mean(rec)), "max_rel_err_top16_dist": max(err)}
-        emd.emd_db_destroy(db)
-    return out
 
 
 # ------------------------------------------------------------------ serving
@@ -263,37 +205,115 @@ def serve_point(emd, srv, queries, order, rate, n_req, k, K, seed):
             "busy_retries": busy[0], "prune_fallbacks": st["prune_fallbacks"]}
 
 
-def serving_sweep(emd, w, opts, precision, rates, n_req, k, K, plain_saturation=True, queries=None,
-                  database="workload 2 (text V=1e5, n=2e4)", requests="workload 4 queries", sat_req=4096):
-    import emd_synth
-    queries = emd_synth.mixed_queries() if queries is None else queries
-    order = np.random.default_rng(7).permutation(queries.n)
-    out = {"database": database,
-           "requests": f"{requests}: h_q log-uniform 5..2000, cycled in a fixed shuffled order",
-           "measure": f"LC-ACT k={k}, max of both directions, top-{K}",
-           "server": "continuous batching: two executors, batches formed from the queue head while the "
-                     "executor's distance-matrix columns hold them (16384 columns each), graph-replayed",
-           "points": []}
-    forms = [(precision, True)] + ([("fp32", False)] if plain_saturation and precision != "fp32" else [])
-    for prec, sweep in forms:
-        db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
-                               emd.emd_db_options_default(precision=prec, **opts))
-        srv = emd.emd_server_create(db, emd.emd_server_options_default())
-        serve_point(emd, srv, queries, order, None, 256, k, K, 1)  # warm-up
-        if sweep:
-            for j, r in enumerate(rates):
-                p = serve_point(emd, srv, queries, order, r, n_req, k, K, 100 + j)
-                p["precision"] = prec
-                out["points"].append(p)
-        sat = serve_point(emd, srv, queries, order, None, min(n_req, sat_req), k, K, 99)
-        sat["precision"] = prec
-        out["saturation_" + prec] = sat
-        emd.emd_server_destroy(srv)
-        emd.emd_db_destroy(db)
-    return out
-
-
 # ------------------------------------------------------------------ main
+
+def oracle_subset(hs: np.ndarray, count: int, seed: int = 1812) -> np.ndarray:
+    """A seeded subset of the query pool stratified by size: at least four queries (an
+    eighth) with h_q > 1000, a quarter with 300 < h_q <= 1000, the rest with h_q <= 300."""
+    rng = np.random.default_rng(seed)
+    groups = [np.nonzero(hs > 1000)[0], np.nonzero((hs > 300) & (hs <= 1000))[0], np.nonzero(hs <= 300)[0]]
+    n_long = min(len(groups[0]), max(4, count // 8))
+    n_mid = min(len(groups[1]), count // 4)
+    n_short = min(len(groups[2]), count - n_long - n_mid)
+    pick = [rng.choice(g, c, replace=False) for g, c in zip(groups, (n_long, n_mid, n_short)) if c > 0]
+    return np.sort(np.concatenate(pick)).astype(np.int64)
+
+
+def _oracle_worker(conn, cores, cid, query_limit, qids, meas, k, K):
+    """Child process (spawned before any GPU work): the exact top-K of max(fwd, rev) of the
+    subset queries by the FP64 oracle (oracle.SymTopK), on its own cores; afterwards it
+    answers requests for the oracle values of further documents (the ones a GPU form
+    returned outside the oracle's top-K, for the tie rule)."""
+    try:
+        os.sched_setaffinity(0, cores)
+    except (AttributeError, OSError):
+        pass
+    import emd_synth
+    import oracle
+    w = emd_synth.config(cid, query_limit=query_limit)
+    prep = oracle.prepare(w.emb, None, w.db)
+    res = {}
+    t0 = time.perf_counter()
+    for q in qids:
+        qi, qw = w.queries.row(int(q))
+        res[int(q)] = oracle.SymTopK(w.emb, None, w.db, qi, qw, meas, k, K, threads=len(cores), prep=prep)
+    wall = time.perf_counter() - t0
+    conn.send(("ready", {q: (r.idx, r.dist) for q, r in res.items()}, wall, len(cores)))
+    while True:
+        msg = conn.recv()
+        if msg[0] != "sym":
+            break
+        conn.send(("sym", {q: res[q].sym_of(docs) for q, docs in msg[1].items()}))
+
+
+class OracleLeg:
+    """The oracle subset of the bench, computed in a spawned child on cores of its own while
+    the GPU work runs in this process on the remaining cores."""
+
+    def __init__(self, cid, query_limit, qids, meas, k, K):
+        import multiprocessing as mp
+        ncpu = os.cpu_count() or 1
+        try:
+            avail = sorted(os.sched_getaffinity(0))
+        except AttributeError:
+            avail = list(range(ncpu))
+        keep = max(2, min(4, len(avail) // 4))
+        self.parent_cores = avail[:keep] if len(avail) > 4 else avail
+        self.cores = avail[keep:] if len(avail) > 4 else avail
+        ctx = mp.get_context("spawn")
+        self.conn, child = ctx.Pipe()
+        self.proc = ctx.Process(target=_oracle_worker, args=(child, self.cores, cid, query_limit, list(map(int, qids)),
+                                                             meas, k, K), daemon=True)
+        self.proc.start()
+        if len(avail) > 4:
+            try:
+                os.sched_setaffinity(0, self.parent_cores)
+            except OSError:
+                pass
+        self.ready = None
+
+    def results(self):
+        if self.ready is None:
+            tag, top, wall, cores = self.conn.recv()
+            self.ready = (top, wall, cores)
+        return self.ready
+
+    def sym(self, req):
+        self.results()
+        self.conn.send(("sym", req))
+        return self.conn.recv()[1]
+
+    def close(self):
+        try:
+            self.conn.send(("stop",))
+        except (BrokenPipeError, OSError):
+            pass
+        self.proc.join(timeout=30)
+
+
+def recall_against(top_idx, top_dist, gpu_idx, gpu_dist, extra, K):
+    """Top-K recall of one GPU answer against the oracle's exact top-K: a returned document
+    counts when it is in the oracle's top-K or ties with its K-th value (|d - d_K| <=
+    1e-5 d_K + 1e-9, the oracle's own distances); also the largest relative error of the
+    returned distances against the oracle's values of the same documents."""
+    truth = {int(d): float(v) for d, v in zip(top_idx[:K], top_dist[:K])}
+    dK = float(top_dist[K - 1])
+    hits, err = 0, 0.0
+    for d, g in zip(gpu_idx[:K], gpu_dist[:K]):
+        d = int(d)
+        want = truth[d] if d in truth else float(extra[d])
+        hits += 1 if (d in truth or abs(want - dK) <= 1e-5 * dK + 1e-9) else 0
+        err = max(err, abs(float(g) - want) / max(want, 1e-30))
+    return hits / K, err
+
+
+def bench_config(args, world):
+    """The `config` of the bench line, the same for both arms."""
+    return {"workload": WORKLOAD5, "measure": f"LC-ACT k={args.k} (Alg. 3 top-k width)",
+            "direction": "max(fwd, rev), exact top-K", "top_k": args.topk, "batch_queries": args.batch,
+            "parallelism": f"replicas x{world}, queries sharded",
+            "l2": "inputs larger than L2 (0.9 GB CSR, 0.36 GB embeddings) and L2 flushed between steps"}
+
 
 def main():
     ap = argparse.ArgumentParser()
@@ -304,16 +324,22 @@ def main():
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--k", type=int, default=4)
     ap.add_argument("--topk", type=int, default=16)
-    ap.add_argument("--cpu-queries", type=int, default=3)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-columns", type=int, default=32768,
+                    help="distance-matrix columns of one batch workspace (device memory 4 x v_used x columns)")
+    ap.add_argument("--oracle-queries", type=int, default=16,
+                    help="size of the stratified query subset checked against the FP64 oracle (0: none)")
     ap.add_argument("--e2e-steps", type=int, default=0, help="default: same as --steps")
     ap.add_argument("--precision", default="fp32_tc", choices=["fp32", "fp32_tc", "bf16", "fp8"],
-                    help="Phase-1 arithmetic; bf16 / fp8 only with --probe, --ict, --allpairs")
-    ap.add_argument("--serve-rates", default="1000,2000,4000",
+                    help="Phase-1 arithmetic of the headline form")
+    ap.add_argument("--forms", default="fp32,bf16,fp8",
+                    help="further Phase-1 arithmetics measured on the same batches (fp32 = the plain path)")
+    ap.add_argument("--serve-rates", default="500,1000",
                     help="offered request rates (requests/s) of the serving sweep; empty: skip it")
-    ap.add_argument("--serve-requests", type=int, default=6000, help="requests per serving rate point")
+    ap.add_argument("--serve-requests", type=int, default=10000, help="requests per serving rate point")
+    ap.add_argument("--serve-forms", default="fp32_tc,fp32,bf16,fp8", help="forms that get a serving sweep")
+    ap.add_argument("--w2-steps", type=int, default=10, help="batches of the workload-2 extra line (0: skip)")
     ap.add_argument("--probe", action="store_true",
-                    help="small fixed case for profiler captures: the bench workload's database, --batch "
+                    help="small fixed case for profiler captures: workload 2's database, --batch "
                          "queries per batch (16 suggested), --warmup + --steps batches, ~1.5 GB on the device")
     ap.add_argument("--k4", action="store_true",
                     help="forward sparse pass alone on the serving-size database (workload 5, cut to --k4-docs "
@@ -325,24 +351,15 @@ def main():
     ap.add_argument("--baselines", action="store_true",
                     help="BoW cosine and word centroid distance top-K on workload 2 (Section 6 baselines) "
                          "beside LC-ACT; prints one line")
-    ap.add_argument("--serve5", action="store_true",
-                    help="serving sweep on the serving-size database (workload 5: V=2e5, n=1e6) with its own "
-                         "queries, --serve-rates, --serve-requests per point; prints one line")
     ap.add_argument("--allpairs", type=int, default=0, choices=[0, 2, 3],
                     help="all-pairs top-K over workload 2 (text) or 3 (images) instead of the bench "
                          "line: every histogram against all others; prints one line")
-    ap.add_argument("--precision-steps", type=int, default=5,
-                    help="batches per arithmetic in the precision comparison; 0: skip it")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     rank, world, local = env_rank()
-    import emd_synth
-
     if args.impl == "reference":
         return main_reference(args, rank, world)
-    if args.precision in ("bf16", "fp8") and not (args.probe or args.ict or args.allpairs):
-        ap.error("the bench line runs fp32 or fp32_tc; the approximate forms are timed in its precision_forms")
     if args.probe:
         return main_probe(args, local)
     if args.k4:
@@ -353,8 +370,21 @@ def main():
         return main_ict(args, local)
     if args.baselines:
         return main_baselines(args, local)
-    if args.serve5:
-        return main_serve5(args, local)
+    return main_bench(args, rank, world, local)
+
+
+def main_bench(args, rank, world, local):
+    import emd_synth
+    t_gen = time.perf_counter()
+    w = emd_synth.config(5, query_limit=QUERY_POOL)
+    gen_s = time.perf_counter() - t_gen
+    hs_pool = np.diff(w.queries.row_ptr)
+    K = args.topk
+    leg = None
+    sub = np.zeros(0, np.int64)
+    if rank == 0 and world == 1 and args.oracle_queries > 0:
+        sub = oracle_subset(hs_pool, args.oracle_queries)
+        leg = OracleLeg(5, QUERY_POOL, sub, "act", args.k, K)
 
     import torch
     import paper_1812_02091_gb300 as emd
@@ -365,28 +395,27 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    w = emd_synth.config(2)
-    opts = dict(device=local, max_query_h=2048, max_batch=args.batch)
-    db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
-                           emd.emd_db_options_default(precision=args.precision, **opts))
-    info = emd.emd_db_info_get(db)
+    opts = dict(device=local, max_query_h=2048, max_batch=args.batch, batch_columns=args.batch_columns)
     my_ids = shard(w.queries.n, rank, world)
     total_steps = args.warmup + args.steps
     batches = batches_for(my_ids, args.batch, total_steps)
-
-    # inputs resident in HBM before the timed region
     dev_batches = []
     for b in batches:
-        sub = w.queries.subset(b)
-        dev_batches.append((sub.row_ptr, torch.from_numpy(sub.col).cuda(), torch.from_numpy(sub.val).cuda(),
-                            int(sub.nnz), np.diff(sub.row_ptr)))
-    K = args.topk
+        s_ = w.queries.subset(b)
+        dev_batches.append((s_.row_ptr, torch.from_numpy(s_.col).cuda(), torch.from_numpy(s_.val).cuda(),
+                            int(s_.nnz), np.diff(s_.row_ptr)))
+    sq = w.queries.subset(sub) if len(sub) else None
+    sub_dev = (sq.row_ptr, torch.from_numpy(sq.col).cuda(), torch.from_numpy(sq.val).cuda()) if sq else None
     oi = torch.empty((args.batch, K), dtype=torch.int64, device="cuda")
     od = torch.empty((args.batch, K), dtype=torch.float32, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
     stream = torch.cuda.current_stream()
 
-    def run_steps(handle, steps, keep=0, profile=False):
+    def make_db(prec):
+        return emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
+                                 emd.emd_db_options_default(precision=prec, **opts))
+
+    def run_steps(handle, steps, profile=False):
         """Warm up, then time `steps` batches with CUDA events on the launch stream, L2
         flushed between steps outside the events; with `profile`, per-phase times from the
         library's own events (on the streams the kernels run on)."""
@@ -402,7 +431,6 @@ def main():
         launches0 = emd.emd_db_profile_get(handle)["total_launches"]
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        kept = []
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
@@ -411,134 +439,74 @@ def main():
             starts[s].record(stream)
             step(args.warmup + s)
             ends[s].record(stream)
-            if s < keep:
-                kept.append((args.warmup + s, oi.clone(), od.clone()))
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         emd.emd_db_set_profiling(handle, False)
         prof = emd.emd_db_profile_get(handle)
+        emd.emd_db_check_device_errors(handle)
         step_ms = np.array([x.elapsed_time(y) for x, y in zip(starts, ends)])
         total = float(step_ms.sum())
         if dist:
             t = torch.tensor([total], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             total = float(t.item())
-        return step_ms, total, prof, prof["total_launches"] - launches0, kept
+        return step_ms, total, prof, prof["total_launches"] - launches0
 
+    def subset_answers(handle):
+        if sub_dev is None:
+            return None
+        si = torch.empty((len(sub), K), dtype=torch.int64, device="cuda")
+        sd = torch.empty((len(sub), K), dtype=torch.float32, device="cuda")
+        emd.emd_topk_device(handle, *sub_dev, si, sd, "act", args.k, "max", K, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        return si.cpu().numpy(), sd.cpu().numpy()
+
+    rates = [float(x) for x in args.serve_rates.split(",") if x.strip()]
+    serve_forms = [f for f in args.serve_forms.split(",") if f.strip()]
+    order = np.random.default_rng(7).permutation(w.queries.n)
+    answers, forms, serving = {}, {}, {"database": w.name, "points": [], "saturation": {},
+                                       "requests": f"workload 5 queries (h_q log-uniform 5..2000), a pool of "
+                                                   f"{w.queries.n} cycled in a fixed shuffled order, "
+                                                   f"{args.serve_requests} per rate point",
+                                       "measure": f"LC-ACT k={args.k}, max of both directions, top-{K}",
+                                       "server": "continuous batching: two executors, batches formed from the "
+                                                 "queue head while the executor's distance-matrix columns hold "
+                                                 f"them ({args.batch_columns} columns each), graph-replayed"}
+
+    def serve(handle, prec):
+        if rank != 0 or not rates or prec not in serve_forms:
+            return
+        srv = emd.emd_server_create(handle, emd.emd_server_options_default())
+        serve_point(emd, srv, w.queries, order, None, 256, args.k, K, 1)  # warm-up
+        for j, r in enumerate(rates):
+            p = serve_point(emd, srv, w.queries, order, r, args.serve_requests, args.k, K, 100 + j)
+            p["precision"] = prec
+            serving["points"].append(p)
+        sat = serve_point(emd, srv, w.queries, order, None, 4096, args.k, K, 99)
+        serving["saturation"][prec] = sat
+        emd.emd_server_destroy(srv)
+
+    # ---- the headline form
+    t_db = time.perf_counter()
+    db = make_db(args.precision)
+    db_s = time.perf_counter() - t_db
+    info = emd.emd_db_info_get(db)
     with ClockSampler(local) as clk:
-        step_ms, total_ms, prof_main, gpu_launches, results = run_steps(db, args.steps, keep=4)
+        step_ms, total_ms, prof_main, gpu_launches = run_steps(db, args.steps)
     queries_done = args.batch * args.steps * world
     value = queries_done / (total_ms / 1e3)
+    steps_prof = min(args.steps, 5)
+    _, total_p, prof, _ = run_steps(db, steps_prof, profile=True)
+    answers[args.precision] = subset_answers(db)
 
-    # per-kernel durations: the same batches on one lane (no overlap between queries), so
-    # each phase's events bracket its own kernels only
-    db_serial = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
-                                  emd.emd_db_options_default(precision=args.precision, lanes=1, **opts))
-    steps_serial = min(args.steps, 5)
-    step_s, total_s, prof, _, _ = run_steps(db_serial, steps_serial, profile=True)
-    emd.emd_db_destroy(db_serial)
-
-    # the plain FP32 path (FP32 FFMA distance tiles) on the same batches
-    plain, res_p = None, None
-    if args.precision != "fp32":
-        db_plain = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
-                                     emd.emd_db_options_default(precision="fp32", **opts))
-        steps_plain = min(args.steps, 5)
-        step_p, total_p, prof_p, _, res_p = run_steps(db_plain, steps_plain, keep=1)
-        emd.emd_db_destroy(db_plain)
-        plain = {"value": args.batch * steps_plain * world / (total_p / 1e3), "unit": UNIT,
-                 "ms_per_step": total_p / steps_plain, "steps": steps_plain,
-                 "top16_identical_to_main": bool(torch.equal(res_p[0][1], results[0][1]))}
-
-    # the same batches with the reverse pass over every document (no pruning)
-    db_all = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
-                               emd.emd_db_options_default(prune_topk=0, precision=args.precision, **opts))
-    steps_all = min(args.steps, 5)
-    step_all, total_all, prof_all, _, res_all = run_steps(db_all, steps_all, keep=1)
-    emd.emd_db_destroy(db_all)
-    same_as_pruned = bool(torch.equal(res_all[0][1], results[0][1]))
-    unpruned = {"value": args.batch * steps_all * world / (total_all / 1e3), "unit": UNIT,
-                "ms_per_step": total_all / steps_all, "steps": steps_all,
-                "top16_identical_to_pruned": same_as_pruned}
-
-    # the Phase-1 arithmetics side by side on mixed-size queries (rank 0, N = 1 only)
-    forms = None
-    if rank == 0 and world == 1 and args.precision_steps > 0:
-        forms = precision_forms(emd, torch, w, opts, args.k, K, args.precision_steps, args.batch, flush,
-                                os.cpu_count() or 1)
-
-    # per-phase achieved figures over the timed region
-    timed = dev_batches[args.warmup:args.warmup + steps_serial]
-    sum_h = sum(int(b[4].sum()) for b in timed)
-    nq = args.batch * steps_serial
-    m, vu, nnz, n = w.m, info["v_used"], info["nnz"], info["n_docs"]
-    pk = peaks()
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12  # TFLOP/s
-    phase = prof["ms"]
-    dist_flops = 2.0 * vu * m * sum_h
-    kpad = -(-m // 64) * 64
-    mpad = -(-vu // 128) * 128
-    # tensor-core form: three FP16 products (hi*hi, hi*lo, lo*hi) per FP32-grade product, on
-    # padded tiles (rows to 128, K to 64, each query's columns to 16)
-    tc_exec_flops = 3 * 2.0 * mpad * kpad * sum(int(((b[4] + 15) // 16 * 16).sum()) for b in timed)
-    fwd_bytes = nq * (8.0 * nnz + 4.0 * (n + 1) + 4.0 * n)
-    if args.precision == "fp32":
-        dist_row = {"bound": "alu", "achieved": dist_flops / (phase["distance"] / 1e3) / 1e12,
-                    "peak": alu_peak, "unit": "TFLOP/s", "kernel_file": "k_phase1.cu",
-                    "per_launch": dist_flops / steps_serial,
-                    "peak_source": "FP32 SIMT: 152 SMs x 128 lanes x 2 FLOP x max SM clock"}
-    else:
-        t_dist = phase["distance"] / 1e3
-        dist_row = {"bound": "tensor", "achieved": dist_flops / t_dist / 1e12,
-                    "peak": pk["bf16_tflops"] / 3, "unit": "TFLOP/s", "kernel_file": "k_tc_dist.cu",
-                    "per_launch": dist_flops / steps_serial,
-                    "peak_source": (f"{pk['source']} dense BF16 burst {pk['bf16_tflops']} TFLOP/s (FP16 runs at the "
-                                    "same rate) / 3: the FP16 hi/lo split executes three products per FP32-grade "
-                                    "product; achieved = algorithmic 2 v_used h_q m FLOP per query"),
-                    "executed_tflops": tc_exec_flops / t_dist / 1e12,
-                    "executed_frac_of_raw_peak": tc_exec_flops / t_dist / 1e12 / pk["bf16_tflops"]}
-    rows = {
-        "distance": dist_row,
-        "fwd": {"bound": "hbm", "achieved": fwd_bytes / (phase["fwd"] / 1e3) / 1e9,
-                "peak": pk["hbm_gbs"], "unit": "GB/s", "kernel_file": "k_sparse.cu",
-                "per_launch": fwd_bytes / steps_serial},
-    }
-    dominant = max(("stage", "distance", "table", "fwd", "rev", "topk"), key=lambda p: phase[p])
-    if dominant in rows:
-        r = rows[dominant]
-        roofline = {"bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"], "unit": r["unit"],
-                    "frac": r["achieved"] / r["peak"], "kernel": dominant,
-                    "peak_source": r.get("peak_source", f"{pk['source']} HBM copy"),
-                    "traffic": recorded_traffic(r["kernel_file"], dominant),
-                    "launches_timed": prof["launches"][dominant], "algorithmic_per_launch": r["per_launch"]}
-        for extra in ("executed_tflops", "executed_frac_of_raw_peak"):
-            if extra in r:
-                roofline[extra] = r[extra]
-    else:
-        # the reverse pass gathers D rows from L2 and the table kernel reads L2-resident D:
-        # neither has an HBM or ALU roofline claim
-        roofline = {"bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": None,
-                    "kernel": dominant, "traffic": None, "note": f"{dominant} dominates (L2-bound)"}
-    phases = {p: {"ms_per_step": phase[p] / steps_serial, "launches": prof["launches"][p]}
-              for p in ("stage", "distance", "table", "fwd", "rev", "topk")}
-    phases["measured_on"] = f"{steps_serial} steps on one lane (serial), profiling events"
-    phases["serial_ms_per_step"] = total_s / steps_serial
-    phases["pruned_queries"] = prof["pruned_queries"]
-    phases["prune_fallbacks"] = prof["prune_fallbacks"]
-    phases["distance"]["algorithmic_tflops"] = dist_flops / (phase["distance"] / 1e3) / 1e12
-    if args.precision != "fp32":
-        phases["distance"]["tensor_tflops_executed"] = tc_exec_flops / (phase["distance"] / 1e3) / 1e12
-    phases["fwd"]["gbs"] = rows["fwd"]["achieved"]
     # end to end through the public host API, pinned host buffers
     e2e_steps = args.e2e_steps or args.steps
     host_in = []
     for s in range(e2e_steps):
-        b = batches[(args.warmup + s) % len(batches)]
-        sub = w.queries.subset(b)
-        pi = torch.from_numpy(sub.col).pin_memory().numpy()
-        pw = torch.from_numpy(sub.val).pin_memory().numpy()
-        host_in.append((sub.row_ptr, pi, pw))
+        s_ = w.queries.subset(batches[(args.warmup + s) % len(batches)])
+        host_in.append((s_.row_ptr, torch.from_numpy(s_.col).pin_memory().numpy(),
+                        torch.from_numpy(s_.val).pin_memory().numpy()))
     ho_i = torch.empty((args.batch, K), dtype=torch.int64).pin_memory().numpy()
     ho_d = torch.empty((args.batch, K), dtype=torch.float32).pin_memory().numpy()
     emd.emd_topk(db, *host_in[0], "act", args.k, "max", K, out_idx=ho_i, out_dist=ho_d)
@@ -553,35 +521,142 @@ def main():
         t = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    h2d = float(np.mean([hi[1].nbytes + hi[2].nbytes for hi in host_in]))
-    d2h = float(ho_i.nbytes + ho_d.nbytes)
-    e2e = {"value": args.batch * e2e_steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h, "api": "emd_topk (host buffers, synchronous)"}
+    e2e = {"value": args.batch * e2e_steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": float(np.mean([hi[1].nbytes + hi[2].nbytes for hi in host_in])),
+           "d2h_bytes_per_step": float(ho_i.nbytes + ho_d.nbytes), "api": "emd_topk (host buffers, synchronous)"}
+    serve(db, args.precision)
+    emd.emd_db_destroy(db)
 
-    # serving: open-loop arrivals of mixed-size queries through emd_server_* (rank 0 only)
-    serving = None
-    rates = [float(x) for x in args.serve_rates.split(",") if x.strip()]
-    if rank == 0 and rates:
-        serving = serving_sweep(emd, w, opts, args.precision, rates, args.serve_requests, args.k, K)
+    # ---- the other Phase-1 arithmetics on the same batches (the plain FP32 path first)
+    form_steps = min(args.steps, 5)
+    for prec in [f for f in args.forms.split(",") if f.strip() and f != args.precision]:
+        h = make_db(prec)
+        _, tot, prof_f, _ = run_steps(h, form_steps)
+        forms[prec] = {"value": args.batch * form_steps * world / (tot / 1e3), "unit": UNIT,
+                       "ms_per_step": tot / form_steps, "steps": form_steps,
+                       "prune_fallbacks": prof_f["prune_fallbacks"]}
+        answers[prec] = subset_answers(h)
+        serve(h, prec)
+        emd.emd_db_destroy(h)
 
-    # CPU oracle baseline + recall on the same sampled queries (rank 0, N = 1 only)
-    cpu = None
+    # ---- workload 2 (the text database at the scale of the paper's 20 Newsgroups) as an extra line
+    w2line = None
+    if args.w2_steps > 0 and rank == 0:
+        w2 = emd_synth.config(2)
+        h2 = emd.emd_db_create(w2.emb, None, w2.db.row_ptr, w2.db.col, w2.db.val,
+                               emd.emd_db_options_default(precision=args.precision, device=local, max_query_h=2048,
+                                                          max_batch=args.batch))
+        b2 = batches_for(np.arange(w2.queries.n), args.batch, args.warmup + args.w2_steps)
+        d2 = []
+        for b in b2:
+            s_ = w2.queries.subset(b)
+            d2.append((s_.row_ptr, torch.from_numpy(s_.col).cuda(), torch.from_numpy(s_.val).cuda()))
+        for s in range(args.warmup):
+            emd.emd_topk_device(h2, *d2[s], oi, od, "act", args.k, "max", K, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.w2_steps)]
+        for s in range(args.w2_steps):
+            flush.fill_(float(s))
+            ev[s][0].record(stream)
+            emd.emd_topk_device(h2, *d2[args.warmup + s], oi, od, "act", args.k, "max", K, stream=stream.cuda_stream)
+            ev[s][1].record(stream)
+        torch.cuda.synchronize()
+        emd.emd_db_check_device_errors(h2)
+        t2 = sum(a_.elapsed_time(b_) for a_, b_ in ev) / 1e3
+        w2line = {"workload": w2.name + " (1000 queries of the same law, log-normal h median 100)",
+                  "value": args.batch * args.w2_steps / t2, "unit": UNIT, "steps": args.w2_steps,
+                  "precision": args.precision}
+        emd.emd_db_destroy(h2)
+
+    # ---- per-phase achieved figures of the headline form (profiling pass)
+    timed = dev_batches[args.warmup:args.warmup + steps_prof]
+    sum_h = sum(int(b[4].sum()) for b in timed)
+    nq = args.batch * steps_prof
+    m, vu, nnz, n = w.m, info["v_used"], info["nnz"], info["n_docs"]
+    pk = peaks()
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12  # TFLOP/s
+    phase = prof["ms"]
+    dist_flops = 2.0 * vu * m * sum_h
+    kpad = -(-m // 64) * 64
+    mpad = -(-vu // 128) * 128
+    tc_exec_flops = 3 * 2.0 * mpad * kpad * sum(int(((b[4] + 15) // 16 * 16).sum()) for b in timed)
+    fwd_bytes = nq * (8.0 * nnz + 4.0 * (n + 1) + 4.0 * n)
+    if args.precision == "fp32":
+        dist_row = {"bound": "alu", "achieved": dist_flops / (phase["distance"] / 1e3) / 1e12, "peak": alu_peak,
+                    "unit": "TFLOP/s", "kernel_file": "k_phase1.cu", "per_launch": dist_flops / steps_prof,
+                    "peak_source": "FP32 SIMT: 152 SMs x 128 lanes x 2 FLOP x max SM clock"}
+    else:
+        t_dist = phase["distance"] / 1e3
+        dist_row = {"bound": "tensor", "achieved": dist_flops / t_dist / 1e12, "peak": pk["bf16_tflops"],
+                    "unit": "TFLOP/s", "kernel_file": "k_tc_dist.cu", "per_launch": dist_flops / steps_prof,
+                    "peak_source": (f"{pk['source']} dense BF16 burst {pk['bf16_tflops']} TFLOP/s (FP16 runs at the "
+                                    "same rate); achieved = algorithmic 2 v_used h_q m FLOP per query (the FP16 "
+                                    "hi/lo split executes three products per algorithmic one)"),
+                    "executed_tflops": tc_exec_flops / t_dist / 1e12,
+                    "executed_frac_of_raw_peak": tc_exec_flops / t_dist / 1e12 / pk["bf16_tflops"]}
+    rows = {"distance": dist_row,
+            "fwd": {"bound": "hbm", "achieved": fwd_bytes / (phase["fwd"] / 1e3) / 1e9, "peak": pk["hbm_gbs"],
+                    "unit": "GB/s", "kernel_file": "k_sparse.cu", "per_launch": fwd_bytes / steps_prof,
+                    "peak_source": f"{pk['source']} HBM copy; per query sweep 8 nnz + 4 (n + 1) + 4 n bytes"}}
+
+    def roof(name):
+        r = rows[name]
+        out = {"bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"], "unit": r["unit"],
+               "frac": r["achieved"] / r["peak"], "kernel": name, "peak_source": r["peak_source"],
+               "traffic": recorded_traffic(r["kernel_file"], name), "launches_timed": prof["launches"][name],
+               "algorithmic_per_launch": r["per_launch"]}
+        for extra in ("executed_tflops", "executed_frac_of_raw_peak"):
+            if extra in r:
+                out[extra] = r[extra]
+        return out
+
+    dominant = max(("stage", "distance", "table", "fwd", "rev", "topk"), key=lambda p: phase[p])
+    if dominant in rows:
+        roofline = roof(dominant)
+    else:
+        roofline = {"bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": None,
+                    "kernel": dominant, "traffic": None, "note": f"{dominant} dominates"}
+    phases = {p: {"ms_per_step": phase[p] / steps_prof, "launches": prof["launches"][p]}
+              for p in ("stage", "distance", "table", "fwd", "rev", "topk")}
+    phases["measured_on"] = f"{steps_prof} steps, profiling events (kernels launched directly, not from graphs)"
+    phases["profiled_ms_per_step"] = total_p / steps_prof
+    phases["pruned_queries"] = prof["pruned_queries"]
+    phases["prune_fallbacks"] = prof["prune_fallbacks"]
+
+    # ---- the oracle subset: recall and distance error of every form
     recall = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        threads = os.cpu_count() or 1
-        s0, gi, _ = results[0]
-        sample_ids = batches[s0][:args.cpu_queries]
-        wall, want = oracle_sample(w, sample_ids, "act", args.k, threads)
-        cpu = {"value": len(sample_ids) / wall, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": (f"{len(sample_ids)} queries of the benchmark workload, each against all "
-                          f"{n} documents, LC-ACT k={args.k} both directions + max in FP64; "
-                          f"database split into {threads} document slices run concurrently")}
-        g = gi.cpu().numpy()
-        recall = {"top16_recall": float(np.mean([recall_at(g[i], want[i], K) for i in range(len(want))])),
-                  "queries": len(want), "vs": "FP64 oracle"}
-        if plain is not None:
-            gp = res_p[0][1].cpu().numpy()
-            plain["top16_recall"] = float(np.mean([recall_at(gp[i], want[i], K) for i in range(len(want))]))
+    cpu = None
+    if leg is not None:
+        top, wall, cores = leg.results()
+        req = {}
+        for prec, ans in answers.items():
+            for j, q in enumerate(sub):
+                extra = [int(d) for d in ans[0][j] if int(d) not in set(map(int, top[int(q)][0]))]
+                req.setdefault(int(q), set()).update(extra)
+        sym = leg.sym({q: sorted(v) for q, v in req.items()}) if req else {}
+        recall = {"oracle": "FP64 oracle, exact top-16 of max(fwd, rev) (forward values of every document, "
+                            "reverse values by the per-pair definition until the order certifies the answer)",
+                  "queries": int(len(sub)), "h_q": [int(hs_pool[q]) for q in sub], "forms": {}}
+        for prec, ans in answers.items():
+            recs, errs = [], []
+            for j, q in enumerate(sub):
+                extra = dict(zip(sorted(req.get(int(q), [])), sym.get(int(q), [])))
+                r_, e_ = recall_against(top[int(q)][0], top[int(q)][1], ans[0][j], ans[1][j], extra, K)
+                recs.append(r_)
+                errs.append(e_)
+            recall["forms"][prec] = {"top16_recall": float(np.mean(recs)), "min_query_recall": float(np.min(recs)),
+                                     "max_rel_err_returned_dist": float(np.max(errs))}
+        cpu = {"value": len(sub) / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": (f"the {len(sub)} subset queries of the workload (h_q {int(hs_pool[sub].min())}.."
+                          f"{int(hs_pool[sub].max())}), each the exact top-{K} of max(fwd, rev) against all "
+                          f"{n} documents in FP64 on {cores} host cores (run beside the GPU work, on cores of "
+                          "its own)")}
+        leg.close()
+    main_recall = recall["forms"].get(args.precision) if recall else None
+    for prec, f in forms.items():
+        if recall and prec in recall["forms"]:
+            f.update(recall["forms"][prec])
+    plain = forms.get("fp32")
 
     lat = np.array(step_ms) / args.batch
     if rank == 0:
@@ -589,18 +664,16 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else "f16x3-split/f32-acc",
+            "dtype": {"fp32": "f32", "fp32_tc": "f16x3-split/f32-acc", "bf16": "bf16/f32-acc+f32-rerank",
+                      "fp8": "e4m3/f32-acc+f32-rerank"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "measure": f"LC-ACT k={args.k} (Alg. 3 top-k width)",
-                       "direction": "max(fwd, rev); exact pruned top-K (reverse pass on the 63 best forward candidates, certified)",
-                       "top_k": K, "batch_queries": args.batch,
-                       "precision": {"fp32": "fp32 plain (FFMA tiles)",
-                                     "fp32_tc": "FP32-grade on tcgen05: FP16 hi+lo split, 3 products, FP32 TMEM accumulators"}[args.precision],
-                       "parallelism": f"replicas x{world}, queries sharded",
-                       "l2": "flushed between steps (256 MB write outside the timed events)",
-                       "v_used": vu, "nnz": nnz, "mean_h_q_timed": sum_h / nq,
-                       "autotuned": {kk: info[kk] for kk in ("autotuned", "tc_group_mult", "tc_stages", "rev_warps")}},
+            "config": bench_config(args, world),
+            "form": {"fp32": "plain FP32 (FFMA tiles)",
+                     "fp32_tc": "FP32-grade on tcgen05: FP16 hi+lo split, 3 products, FP32 TMEM accumulators",
+                     "bf16": "BF16 tcgen05 product, exact FP32 re-rank", "fp8": "E4M3 tcgen05 product, exact FP32 "
+                                                                              "re-rank"}[args.precision],
             "roofline": roofline,
+            "roofline_k4": roof("fwd"),
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(gpu_launches),
@@ -608,15 +681,19 @@ def main():
             "clocks": clk.summary(),
             "latency_ms_per_query_in_batch": {"p50": float(np.percentile(lat, 50)),
                                               "p99": float(np.percentile(lat, 99))},
-            "phases": phases,
-            "recall": recall,
-            "unpruned_all_docs": unpruned,
-            "serving": serving,
-            "precision_forms": forms,
+            "recall": main_recall,
             "plain_fp32": plain,
+            "forms": forms,
+            "oracle_subset": recall,
+            "serving": serving if rank == 0 and rates else None,
+            "phases": phases,
+            "workload2": w2line,
+            "database": {"v_used": vu, "nnz": nnz, "n_docs": n, "mean_h_q_timed": sum_h / nq,
+                         "generation_s": gen_s, "db_create_s": db_s,
+                         "autotuned": {kk: info[kk] for kk in ("autotuned", "tc_group_mult", "tc_stages",
+                                                                "rev_warps")}},
         }
         print(json.dumps(line))
-    emd.emd_db_destroy(db)
     if dist:
         dist.destroy_process_group()
 
@@ -767,26 +844,6 @@ def main_ict(args, local):
     print(json.dumps(out))
 
 
-def main_serve5(args, local):
-    """The serving configuration at full size: workload 5 (V=2e5, m=300, n=1e6, nnz ~1.1e8)
-    resident, requests of workload 5's queries (h_q log-uniform 5..2000) through emd_server_*,
-    open-loop Poisson arrivals; plus a saturation point of the plain FP32 path."""
-    import torch
-    import emd_synth
-    import paper_1812_02091_gb300 as emd
-    torch.cuda.set_device(local)
-    t0 = time.perf_counter()
-    w = emd_synth.config(5, query_limit=4096)
-    gen_s = time.perf_counter() - t0
-    rates = [float(r) for r in args.serve_rates.split(",") if r.strip()]
-    opts = dict(device=local, max_query_h=2048, max_batch=args.batch)
-    out = serving_sweep(emd, w, opts, args.precision, rates, args.serve_requests, args.k, args.topk,
-                        queries=w.queries, database=f"workload 5 ({w.name}, nnz {w.db.nnz})",
-                        requests="workload 5 queries", sat_req=2048)
-    out["generation_s"] = gen_s
-    print(json.dumps({"serve5": out}))
-
-
 def main_baselines(args, local):
     """Section 6 baselines on workload 2: BoW cosine and WCD top-K through the host API
     (timed end to end per batch of --batch queries), the kernel times from the library's
@@ -874,31 +931,42 @@ def main_allpairs(args, local):
 
 
 def main_reference(args, rank, world):
-    """The oracle as it stands, on the host cores: one query per step (its database cut
-    into document slices evaluated concurrently), same metric and unit."""
+    """The oracle as it stands, on the host cores: each step is the exact top-K of
+    max(fwd, rev) of one workload-5 query against all documents (oracle.SymTopK, threads
+    over all host cores); queries of at most 150 bins, so that the run stays within a few
+    minutes (the oracle's cost grows with h_q, so this flatters it).  Same metric, unit
+    and config as the GPU arm."""
     if rank != 0:
         return
     import emd_synth
-    w = emd_synth.config(2)
+    import oracle
+    w = emd_synth.config(5, query_limit=QUERY_POOL)
+    hs = np.diff(w.queries.row_ptr)
+    pool = np.nonzero(hs <= 150)[0]
     threads = os.cpu_count() or 1
-    ids = np.arange(w.queries.n)
+    prep = oracle.prepare(w.emb, None, w.db)
+
+    def step(i):
+        q = int(pool[i % len(pool)])
+        qi, qw = w.queries.row(q)
+        oracle.SymTopK(w.emb, None, w.db, qi, qw, "act", args.k, args.topk, threads=threads, prep=prep)
+
     for s in range(args.warmup):
-        oracle_sample(w, [ids[s % len(ids)]], "act", args.k, threads)
+        step(s)
     t0 = time.perf_counter()
     for s in range(args.steps):
-        oracle_sample(w, [ids[(args.warmup + s) % len(ids)]], "act", args.k, threads)
+        step(args.warmup + s)
     wall = time.perf_counter() - t0
     value = args.steps / wall
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": WORKLOAD, "measure": f"LC-ACT k={args.k} (Alg. 3 top-k width)",
-                   "direction": "max(fwd, rev)", "top_k": args.topk, "batch_queries": 1,
-                   "precision": "fp64 oracle"},
+        "config": bench_config(args, world),
+        "form": "FP64 oracle on the host cores, one query per step",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"{args.steps} queries, one per step, all {w.db.n} documents, "
-                                   f"database split into {threads} slices run concurrently"},
+                         "sample": f"{args.steps} workload-5 queries with h_q <= 150 (one per step), each the "
+                                   f"exact top-{args.topk} of max(fwd, rev) against all {w.db.n} documents"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))

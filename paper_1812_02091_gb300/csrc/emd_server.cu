@@ -3,7 +3,7 @@
 // Requests are single queries.  A worker thread forms batches from the head of the queue
 // and runs each on one of two executors -- a batch workspace of its own, pinned staging
 // and a stream -- with the same batched kernel sequence as the host entry points (Phase 1,
-// table, forward pass, pruned reverse pass and top-K of Sections 5-5, replayed from a
+// table, forward pass, pruned reverse pass and top-K of Sections 5-6, replayed from a
 // captured graph).  While one batch is on the GPU the next one collects the requests that
 // arrived meanwhile (continuous batching), admitted in arrival order as long as the
 // executor's workspace -- its distance-matrix columns, i.e. device memory -- can hold them.
