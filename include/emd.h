@@ -101,6 +101,13 @@ typedef struct {
     int32_t autotune;        /* batched form: 1 (default) times the free parameters of the batched
                                 kernels on a synthetic batch at creation and keeps the fastest
                                 (results do not depend on them); 0: fixed defaults */
+    int32_t fused_phase1;    /* batched pruned top-K (EMD_DIR_MAX, K <= 16) in precision FP32_TC
+                                with RWMD, OMR or ACT (k <= 16): 1 (default) keeps each row's k
+                                smallest distances in the tensor-core product's epilogue and
+                                computes the reverse direction's distances only on the candidate
+                                documents' rows (exactly the entries the full matrix would hold),
+                                so no v_used x h_q matrix is written; 0: the full matrix and a
+                                separate table pass.  Results are bit-identical either way */
 } emd_db_options;
 
 typedef struct {

@@ -45,7 +45,8 @@ class emd_db_options(ctypes.Structure):
                 ("rerank_margin", ctypes.c_int32), ("max_query_h", ctypes.c_int32),
                 ("max_table_k", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("prune_topk", ctypes.c_int32), ("lanes", ctypes.c_int32), ("batched", ctypes.c_int32),
-                ("batch_columns", ctypes.c_int32), ("graphs", ctypes.c_int32), ("autotune", ctypes.c_int32)]
+                ("batch_columns", ctypes.c_int32), ("graphs", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("fused_phase1", ctypes.c_int32)]
 
 
 class emd_db_info(ctypes.Structure):

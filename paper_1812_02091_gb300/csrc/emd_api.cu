@@ -106,6 +106,10 @@ bool grouped_tables(const BatchWS& ws, int meas, int tk_b)
     return tk_b > 0 && (tk_b <= 16 || (meas == M_ICT && (int64_t)kFwdGroup * tk_b <= ws.b_tabcols));
 }
 
+// Row width of a query's table in the grouped, query-major layout (the forward kernel's
+// register width), or 0 for the entry-interleaved layout of wide ICT tables.
+int grouped_width(int meas, int tk_b) { return meas == M_ICT && tk_b > 16 ? 0 : fwd_reg_width(tk_b); }
+
 int topk_launch_count(int64_t n) { return topk_blocks(n) > 1 ? 2 : 1; }
 
 int table_width(const emd_db* db, int meas, int k, int h)
@@ -198,7 +202,7 @@ emd_status run_phase1(emd_db* db, Lane& L, const int32_t* qidx, int h, cudaStrea
                                 L.q_hi, db->tcfmt == TC_SPLIT ? L.q_lo : nullptr, round_up(h, 128), L.q_scale,
                                 L.qnorm, h, db->kpad, L.D, ldd, db->err, st),
                  "distance matrix (tensor cores)");
-        EMD_CUDA(launch_zero_ident(qidx, h, db->vslot, L.D, ldd, st), "identical ids");
+        EMD_CUDA(launch_zero_ident(qidx, h, db->vslot, db->v, L.D, ldd, st), "identical ids");
     } else
         EMD_CUDA(launch_dist_fp32(db->emb_used, db->v_used, db->ldm, db->norm_used, db->used_ids, L.Q, h,
                                   db->ldm, L.qnorm, qidx, db->m, L.D, ldd, st), "distance matrix");
@@ -326,6 +330,60 @@ emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, i
     const int H = db->opt.max_query_h;
     const int tk_b = dir != EMD_DIR_REV ? table_width(db, meas, k, H) : 0;
     const int kc_b = db->approx ? std::min(rerank_width(db, tk_b, H), kRerankMax) : tk_b;
+    if (pruned && ws.fused && !hd && meas != M_ICT && tk_b <= 16) {
+        // fused form: the table from the product's epilogue; the reverse direction's distances
+        // on the candidate documents' rows only
+        {
+            Phase p(db, 0, 2, st);
+            EMD_CUDA(launch_gather_rows_b(D_, nqd, B, db->qrows_max, db->emb, db->v, db->ldm, db->m, db->err, st),
+                     "query gather");
+            EMD_CUDA(launch_pack_b(db->tcfmt, D_, nqd, B, (int)round_up(H, 128), db->ldm, db->m, db->kpad, st),
+                     "query pack");
+        }
+        {
+            Phase p(db, 1, 2, st);
+            EMD_CUDA(launch_qpos_b(D_, nqd, B, db->vslot, db->v, true, st), "identical ids");
+            EMD_CUDA(launch_tc_table_batch(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
+                                           db->v_used, D_, nqd, B, db->kpad, tk_b, db->tune_group_mult,
+                                           db->tune_stages, db->err, st),
+                     "Phase-1 table (tensor cores, fused)");
+        }
+        {
+            Phase p(db, 3, 1, st);
+            EMD_CUDA(launch_fwd_b(meas, D_, nqd, B, db->row_ptr, db->col, db->val, n, false,
+                                  grouped_tables(ws, meas, tk_b), tk_b, st),
+                     "forward pass");
+        }
+        {
+            Phase p(db, 5, topk_launch_count(n), st);
+            EMD_CUDA(launch_topk_b(D_, nqd, B, n, K, ws.topk_scratch, true, st), "forward top-K");
+        }
+        EMD_CUDA(cudaMemsetAsync(ws.bcand_count, 0, sizeof(int) * B, st), "candidate counts");
+        EMD_CUDA(cudaMemsetAsync(ws.bncrows, 0, sizeof(int) * B, st), "candidate rows");
+        {
+            Phase p(db, 4, 1, st);
+            EMD_CUDA(launch_prune_compact_b(D_, nqd, B, n, K, st), "candidates");
+        }
+        {
+            Phase p(db, 1, 3, st);
+            EMD_CUDA(launch_cand_rows_b(D_, nqd, B, db->row_ptr, db->col, false, st), "candidate rows");
+            EMD_CUDA(launch_cand_pack_b(D_, nqd, B, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
+                                        db->kpad, st),
+                     "candidate panels");
+            EMD_CUDA(launch_tc_cand_batch(D_, nqd, B, db->kpad, db->tune_stages, db->err, st),
+                     "candidate distances (tensor cores)");
+        }
+        {
+            Phase p(db, 4, 2, st);
+            EMD_CUDA(launch_prune_mapped_b(meas, k, D_, nqd, B, db->row_ptr, db->col, db->val, K, db->tune_rev_warps,
+                                           st),
+                     "pruned reverse pass");
+        }
+        Phase p(db, 6, 2, st);
+        EMD_CUDA(launch_cand_rows_b(D_, nqd, B, db->row_ptr, db->col, true, st), "candidate reset");
+        EMD_CUDA(launch_qpos_b(D_, nqd, B, db->vslot, db->v, false, st), "identical ids");
+        return EMD_OK;
+    }
     if (db->cost_mode) {
         Phase p(db, 1, 1, st);
         EMD_CUDA(launch_dist_gather_b(D_, nqd, B, db->cost, db->v, db->used_ids, db->v_used, db->err, st),
@@ -345,7 +403,7 @@ emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, i
                                           db->v_used, D_, nqd, B, db->kpad, db->tune_group_mult, db->tune_stages,
                                           db->err, st),
                      "distance matrices (tensor cores, batched)");
-            EMD_CUDA(launch_zero_ident_b(D_, nqd, B, H, db->vslot, st), "identical ids");
+            EMD_CUDA(launch_zero_ident_b(D_, nqd, B, H, db->vslot, db->v, st), "identical ids");
         } else if (db->tc) {
             Phase p(db, 1, nb + 1, st);
             for (int q = 0; q < nb; ++q) {
@@ -355,7 +413,7 @@ emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, i
                                         d.ldd, db->err, st),
                          "distance matrix (tensor cores)");
             }
-            EMD_CUDA(launch_zero_ident_b(D_, nqd, B, H, db->vslot, st), "identical ids");
+            EMD_CUDA(launch_zero_ident_b(D_, nqd, B, H, db->vslot, db->v, st), "identical ids");
         } else {
             Phase p(db, 1, 1, st);
             EMD_CUDA(launch_dist_fp32_b(D_, nqd, B, db->ldd_max, db->emb_used, db->v_used, db->ldm, db->norm_used,
@@ -484,6 +542,23 @@ emd_status alloc_batch_ws(emd_db* db, BatchWS& ws, int max_batch, int64_t cols, 
     TRYW(dal(&ws.topk_scratch, B * kTopkScratchRow));
     TRYW(dal(&ws.qd_dev, BatchWS::kDescRing * B));
     TRYW(dal(&ws.nq_dev, BatchWS::kDescRing));
+    ws.fused = db->tc && db->tcfmt == TC_SPLIT && !db->cost_mode && db->opt.fused_phase1 != 0 &&
+               tc_batch_stages(db->tcfmt, db->kpad / 64) >= 2;
+    if (ws.fused) {
+        TRYW(dal(&ws.bqpos, B * vu));
+        TRYW(dal(&ws.brmap, B * vu));
+        TRYW(dal(&ws.bcrows, B * kCandRows));
+        TRYW(dal(&ws.bncrows, B));
+        TRYW(dal(&ws.bc_hi, B * kCandRows * db->kpad));
+        TRYW(dal(&ws.bc_lo, B * kCandRows * db->kpad));
+        TRYW(dal(&ws.bc_scale, B * kCandRows));
+        TRYW(dal(&ws.bc_norm, B * kCandRows));
+        TRYW(dal(&ws.bDc, (int64_t)kCandRows * ws.b_cols));
+        // the row maps start (and every batch leaves them) at -1
+        EMD_CUDA(cudaMemset(ws.bqpos, 0xff, sizeof(int32_t) * B * vu), "memset");
+        EMD_CUDA(cudaMemset(ws.brmap, 0xff, sizeof(int32_t) * B * vu), "memset");
+        EMD_CUDA(cudaDeviceSynchronize(), "synchronize");
+    }
 #undef TRYW
     EMD_CUDA(cudaHostAlloc((void**)&ws.qd_host, sizeof(QDesc) * BatchWS::kDescRing * B, cudaHostAllocDefault),
              "pinned descriptors");
@@ -516,6 +591,7 @@ emd_status fill_descriptors(BatchWS& ws, int slot, emd_db* db, const int64_t* rp
     const int nb = (int)(j1 - j0);
     const int tk_b = dir != EMD_DIR_REV ? table_width(db, meas, k, db->opt.max_query_h) : 0;
     const bool grouped = grouped_tables(ws, meas, tk_b);
+    const int lw_b = grouped_width(meas, tk_b);
     QDesc* hd = ws.qd_host + (int64_t)slot * ws.max_batch;
     QDesc* dd = ws.qd_dev + (int64_t)slot * ws.max_batch;
     int* nqd = ws.nq_dev + slot;
@@ -545,8 +621,13 @@ emd_status fill_descriptors(BatchWS& ws, int slot, emd_db* db, const int64_t* rp
             }
         }
         d.D = ws.bD + c_D * db->v_used;
-        if (grouped) {
+        if (grouped && lw_b > 0) {
             const int64_t bs = i - j0;  // position in the sub-batch: group bs / kFwdGroup
+            d.tab = ws.btab + (bs / kFwdGroup) * (db->v_used * lw_b * kFwdGroup) + (bs % kFwdGroup) * lw_b;
+            d.tab_rs = lw_b * kFwdGroup;
+            d.tab_es = 1;
+        } else if (grouped) {
+            const int64_t bs = i - j0;
             d.tab = ws.btab + (bs / kFwdGroup) * (db->v_used * tk_b * kFwdGroup) + bs % kFwdGroup;
             d.tab_rs = tk_b * kFwdGroup;
             d.tab_es = kFwdGroup;
@@ -567,6 +648,18 @@ emd_status fill_descriptors(BatchWS& ws, int slot, emd_db* db, const int64_t* rp
             d.ok = ws.cand_ok + b;
         }
         if (meas == M_ICT) d.over = ws.ict_over + b;
+        if (ws.fused) {
+            const int64_t bs = i - j0;  // position in the sub-batch
+            d.qpos = ws.bqpos + bs * db->v_used;
+            d.rmap = ws.brmap + bs * db->v_used;
+            d.crows = ws.bcrows + bs * kCandRows;
+            d.ncrows = ws.bncrows + bs;  // zeroed by the sub-batch's sequence
+            d.c_hi = ws.bc_hi + bs * kCandRows * db->kpad;
+            d.c_lo = ws.bc_lo + bs * kCandRows * db->kpad;
+            d.c_scale = ws.bc_scale + bs * kCandRows;
+            d.c_norm = ws.bc_norm + bs * kCandRows;
+            d.Dc = ws.bDc + c_D * kCandRows;
+        }
         d.sq = db->cost_mode ? 0 : 1;
         if (K > 0) {
             d.out_idx = out_idx + (int64_t)b * K;
@@ -583,7 +676,7 @@ emd_status fill_descriptors(BatchWS& ws, int slot, emd_db* db, const int64_t* rp
         max_kc = std::max(max_kc, d.kc);
     }
     // the caller sizes sub-batches with batch_fits; never let one overrun the workspace
-    const int64_t tab_used = grouped ? (int64_t)(nb + kFwdGroup - 1) / kFwdGroup * kFwdGroup * tk_b : c_T;
+    const int64_t tab_used = grouped ? (int64_t)(nb + kFwdGroup - 1) / kFwdGroup * kFwdGroup * (lw_b ? lw_b : tk_b) : c_T;
     if (nb > ws.max_batch || c_D > ws.b_cols || c_Q > ws.b_qrows || c_P > ws.b_prows || tab_used > ws.b_tabcols)
         return fail(EMD_ERR_INVALID_ARG, "internal: sub-batch of %d queries exceeds the batch workspace", nb);
     ws.nq_host[slot] = nb;
@@ -658,7 +751,10 @@ bool batch_fits(const emd_db* db, const BatchWS& ws, const int64_t* rp, int64_t 
         cP += round_up(h, 128);
         cT += dir != EMD_DIR_REV ? table_width(db, meas, k, h) : 0;
     }
-    if (grouped) cT = (i1 - i0 + kFwdGroup - 1) / kFwdGroup * kFwdGroup * tk_b;  // interleaved groups
+    if (grouped) {  // whole groups of kFwdGroup tables
+        const int lw = grouped_width(meas, tk_b);
+        cT = (i1 - i0 + kFwdGroup - 1) / kFwdGroup * kFwdGroup * (lw ? lw : tk_b);
+    }
     return cD <= ws.b_cols && cQ <= ws.b_qrows && cP <= ws.b_prows && cT <= ws.b_tabcols;
 }
 
@@ -929,6 +1025,7 @@ void emd_db_options_default(emd_db_options* opt)
     opt->batch_columns = 16384;
     opt->graphs = 1;
     opt->autotune = 1;
+    opt->fused_phase1 = 1;
 }
 
 emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* cost_matrix,

@@ -96,6 +96,17 @@ struct BatchWS {
     int* cand_ok = nullptr;       // max_batch certification flags
     int* ict_over = nullptr;      // max_batch ICT table overflow flags
     unsigned long long* topk_scratch = nullptr;  // max_batch x kTopkScratchRow
+    // fused pruned path (allocated when the database can use it)
+    bool fused = false;
+    int32_t* bqpos = nullptr;     // max_batch x v_used, -1 between batches
+    int32_t* brmap = nullptr;     // max_batch x v_used, -1 between batches
+    int32_t* bcrows = nullptr;    // max_batch x kCandRows
+    int* bncrows = nullptr;       // max_batch
+    __half* bc_hi = nullptr;      // max_batch x kCandRows x kpad
+    __half* bc_lo = nullptr;
+    float* bc_scale = nullptr;    // max_batch x kCandRows
+    float* bc_norm = nullptr;
+    float* bDc = nullptr;         // kCandRows x b_cols
     QDesc* qd_dev = nullptr;      // kDescRing x max_batch descriptors
     int* nq_dev = nullptr;        // kDescRing counts
     QDesc* qd_host = nullptr;     // pinned mirror of the ring

@@ -82,7 +82,7 @@ cudaError_t launch_vslot(const int32_t* used_ids, int64_t v_used, int64_t v, int
 
 // Exact zeros of identical ids in squared-distance matrices: D[s(j), j] = 0 for every query
 // bin j whose vocabulary id has used row s(j) = vslot[q_idx[j]] >= 0.
-cudaError_t launch_zero_ident(const int32_t* q_idx, int h, const int32_t* vslot, float* D, int ldd,
+cudaError_t launch_zero_ident(const int32_t* q_idx, int h, const int32_t* vslot, int64_t v, float* D, int ldd,
                               cudaStream_t st);
 
 // ICT table (Section 4.2, Algorithm 2, in the linear form of Section 5): per row u the
@@ -195,13 +195,33 @@ struct QDesc {
     float* out_dist;
     int h, ldd, qrows, npad, tk, kc;
     int tab_rs, tab_es;     // table layout: entry l of row u at tab[u * tab_rs + l * tab_es]
+    // fused form of the pruned path (Phase-1 table in the product's epilogue, no full matrix)
+    int32_t* qpos;          // v_used: the query bin whose vocabulary id is used row u, else -1
+    int32_t* rmap;          // v_used: row of used row u in the candidate block, else -1
+    int32_t* crows;         // kCandRows used rows of the candidate documents
+    int* ncrows;            // their count (may exceed kCandRows: the query is then recomputed)
+    void* c_hi;             // kCandRows x Kpad packed FP16-split panels of those rows
+    void* c_lo;
+    float* c_scale;         // kCandRows scales and squared norms
+    float* c_norm;
+    float* Dc;              // kCandRows x ldd squared distances of those rows to the query's bins
 };
 
-// Queries whose forward pass shares one sweep of the CSR (batched form, table width <= 16).
-// Their tables are interleaved by entry -- row u, entry l, query g at
-// base[(u * width + l) * kFwdGroup + g] -- so that one L2 sector holds the first entries of
-// four of them.
+// Largest number of distinct used rows among the candidate documents of one query in the
+// fused pruned path (their distance block is computed exactly; beyond it the query is
+// recomputed over all documents with the full distance matrix).
+constexpr int kCandRows = 16384;
+
+// Queries whose forward pass shares one sweep of the CSR (batched form).  Tables of width
+// <= 16 are stored query-major within a row -- row u, query g, entry l at
+// base[(u * kFwdGroup + g) * W + l] with W the register width of the table (1, 2, 4, 8 or
+// 16) -- so that a lane reads its query's first entries with vector loads; ICT tables of
+// other widths are interleaved by entry, base[(u * width + l) * kFwdGroup + g].
 constexpr int kFwdGroup = 8;
+__host__ __device__ inline int fwd_reg_width(int kw)
+{
+    return kw <= 1 ? 1 : kw <= 2 ? 2 : kw <= 4 ? 4 : kw <= 8 ? 8 : kw <= 16 ? 16 : 0;
+}
 
 cudaError_t launch_gather_rows_b(const QDesc* qd, const int* nq, int max_q, int max_rows, const float* src,
                                  int64_t v, int ld, int m, int* err, cudaStream_t st);
@@ -226,8 +246,36 @@ cudaError_t launch_tc_dist_batch(int fmt, const void* A_hi, const void* A_lo, in
 // max_tk: the largest table width of the batch; rerank: the approximate precisions' form
 // (V: the used vocabulary rows, ldv floats each).
 // Exact zeros of identical ids (launch_zero_ident) for every query of a batch.
-cudaError_t launch_zero_ident_b(const QDesc* qd, const int* nq, int max_q, int max_h, const int32_t* vslot,
+cudaError_t launch_zero_ident_b(const QDesc* qd, const int* nq, int max_q, int max_h, const int32_t* vslot, int64_t v,
                                 cudaStream_t st);
+
+// ---- fused pruned path (tensor-core precision FP32_TC; RWMD, OMR, ACT with tables of width
+// <= 16): the Phase-1 table from the product's epilogue, the reverse direction from an exact
+// block over the candidate documents' rows only.  No v_used x h_q matrix is written.
+// qd[q].qpos for every query of a batch: set (qpos[vslot[q_idx[j]]] = j) or cleared (-1).
+cudaError_t launch_qpos_b(const QDesc* qd, const int* nq, int max_q, const int32_t* vslot, int64_t v, bool set,
+                          cudaStream_t st);
+// The table of every query (qd[q].tab, width qd[q].tk <= max_tk <= 16); format TC_SPLIT.
+cudaError_t launch_tc_table_batch(int fmt, const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
+                                  const float* a_norm, int64_t M, const QDesc* qd, const int* nq, int max_q, int Kpad,
+                                  int max_tk, int group_mult, int stages, int* err, cudaStream_t st);
+// Candidate compaction of the pruned path alone (counts must be zeroed).
+cudaError_t launch_prune_compact_b(const QDesc* qd, const int* nq, int max_q, int64_t n, int K, cudaStream_t st);
+// The distinct used rows of the candidate documents (qd[q].crows, ncrows zeroed, rmap), or
+// with reset the row map returned to -1.
+cudaError_t launch_cand_rows_b(const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr, const int32_t* col,
+                               bool reset, cudaStream_t st);
+// Their FP16-split panel rows, scales and norms gathered from the vocabulary panels.
+cudaError_t launch_cand_pack_b(const QDesc* qd, const int* nq, int max_q, const void* a_hi, const void* a_lo,
+                               int64_t Mpad, const float* a_scale, const float* a_norm, int Kpad, cudaStream_t st);
+// Their squared distances to the query's bins (qd[q].Dc, ldd columns), exact zeros of
+// identical ids from qd[q].qpos.
+cudaError_t launch_tc_cand_batch(const QDesc* qd, const int* nq, int max_q, int Kpad, int stages, int* err,
+                                 cudaStream_t st);
+// Reverse pass on the candidates through the row map, then the final selection (queries
+// whose block overflowed are reported uncertified).
+cudaError_t launch_prune_mapped_b(int meas, int k, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
+                                  const int32_t* col, const float* val, int K, int rev_warps, cudaStream_t st);
 cudaError_t launch_table_b(const QDesc* qd, const int* nq, int max_q, int64_t M, int max_tk, bool rerank,
                            int max_kc, int max_h, const float* V, int ldv, cudaStream_t st);
 // The ICT table of every query of a batch (width qd[q].tk, overflow flag qd[q].over).

@@ -607,28 +607,45 @@ k_table_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t M)
     table_body<KT>(d.D, d.ldd, M, d.h, d.tk, d.qw, d.tab, nullptr, d.tab_rs, d.tab_es, d.sq != 0);
 }
 
-// D[vslot[q_idx[j]], j] = 0 for the query bins whose id is a used vocabulary row.
+// D[vslot[q_idx[j]], j] = 0 for the query bins whose id is a used vocabulary row (ids
+// outside 0..v-1 are skipped; the query gather latches them as errors).
 __device__ __forceinline__ void zero_ident_body(const int32_t* __restrict__ q_idx, int h,
-                                                const int32_t* __restrict__ vslot, float* __restrict__ D, int ldd)
+                                                const int32_t* __restrict__ vslot, int64_t v, float* __restrict__ D,
+                                                int ldd)
 {
     for (int j = threadIdx.x; j < h; j += blockDim.x) {
-        const int32_t s = vslot[q_idx[j]];
+        const int32_t id = q_idx[j];
+        const int32_t s = (id >= 0 && id < v) ? vslot[id] : -1;
         if (s >= 0) D[(int64_t)s * ldd + j] = 0.f;
     }
 }
 
-__global__ void k_zero_ident(const int32_t* __restrict__ q_idx, int h, const int32_t* __restrict__ vslot,
+__global__ void k_zero_ident(const int32_t* __restrict__ q_idx, int h, const int32_t* __restrict__ vslot, int64_t v,
                              float* __restrict__ D, int ldd)
 {
-    zero_ident_body(q_idx, h, vslot, D, ldd);
+    zero_ident_body(q_idx, h, vslot, v, D, ldd);
 }
 
 __global__ void k_zero_ident_b(const QDesc* __restrict__ qd, const int* __restrict__ nq,
-                               const int32_t* __restrict__ vslot)
+                               const int32_t* __restrict__ vslot, int64_t v)
 {
     if ((int)blockIdx.x >= *nq) return;
     const QDesc& d = qd[blockIdx.x];
-    zero_ident_body(d.qidx, d.h, vslot, d.D, d.ldd);
+    zero_ident_body(d.qidx, d.h, vslot, v, d.D, d.ldd);
+}
+
+// The fused path's map from used row to query bin: qpos[vslot[q_idx[j]]] = j (set) or -1
+// (clear, restoring the state every batch starts from).
+__global__ void k_qpos_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t* __restrict__ vslot,
+                         int64_t v, bool set)
+{
+    if ((int)blockIdx.x >= *nq) return;
+    const QDesc& d = qd[blockIdx.x];
+    for (int j = threadIdx.x; j < d.h; j += blockDim.x) {
+        const int32_t id = d.qidx[j];
+        const int32_t s = (id >= 0 && id < v) ? vslot[id] : -1;
+        if (s >= 0) d.qpos[s] = set ? j : -1;
+    }
 }
 
 __global__ void __launch_bounds__(128) k_table_ict_fast_b(const QDesc* __restrict__ qd, const int* __restrict__ nq,
@@ -734,11 +751,11 @@ cudaError_t launch_table(const float* D, int ldd, int64_t M, int h, int k, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_zero_ident(const int32_t* q_idx, int h, const int32_t* vslot, float* D, int ldd,
+cudaError_t launch_zero_ident(const int32_t* q_idx, int h, const int32_t* vslot, int64_t v, float* D, int ldd,
                               cudaStream_t st)
 {
     if (h <= 0) return cudaSuccess;
-    k_zero_ident<<<1, 256, 0, st>>>(q_idx, h, vslot, D, ldd);
+    k_zero_ident<<<1, 256, 0, st>>>(q_idx, h, vslot, v, D, ldd);
     return cudaGetLastError();
 }
 
@@ -806,11 +823,19 @@ cudaError_t launch_dist_gather_b(const QDesc* qd, const int* nq, int max_q, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_zero_ident_b(const QDesc* qd, const int* nq, int max_q, int max_h, const int32_t* vslot,
+cudaError_t launch_zero_ident_b(const QDesc* qd, const int* nq, int max_q, int max_h, const int32_t* vslot, int64_t v,
                                 cudaStream_t st)
 {
     if (max_q <= 0 || max_h <= 0) return cudaSuccess;
-    k_zero_ident_b<<<(unsigned)max_q, 256, 0, st>>>(qd, nq, vslot);
+    k_zero_ident_b<<<(unsigned)max_q, 256, 0, st>>>(qd, nq, vslot, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_qpos_b(const QDesc* qd, const int* nq, int max_q, const int32_t* vslot, int64_t v, bool set,
+                          cudaStream_t st)
+{
+    if (max_q <= 0) return cudaSuccess;
+    k_qpos_b<<<(unsigned)max_q, 256, 0, st>>>(qd, nq, vslot, v, set);
     return cudaGetLastError();
 }
 

@@ -283,7 +283,7 @@ __device__ __forceinline__ void rev_blk_body(const int32_t* __restrict__ row_ptr
           const float* __restrict__ val, const float* __restrict__ D, int ldd, int h,
           const float* __restrict__ q_w, int k, const float* __restrict__ t_fwd,
           float* __restrict__ t_rev, float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
-          const int* __restrict__ n_dev, bool sq)
+          const int* __restrict__ n_dev, bool sq, const int32_t* __restrict__ rmap = nullptr)
 {
     constexpr int U = 4;
     __shared__ float sz[W - 1][32 * NJ][KT];
@@ -318,7 +318,7 @@ __device__ __forceinline__ void rev_blk_body(const int32_t* __restrict__ row_ptr
                 for (int s = 0; s < U; ++s) {
                     const int32_t ui = __shfl_sync(0xffffffffu, u, i + s);
                     xv[s] = __shfl_sync(0xffffffffu, x, i + s);
-                    load_vec(D + (int64_t)ui * ldd + j0, jin, dv[s]);
+                    load_vec(D + (rmap ? (int64_t)rmap[ui] : (int64_t)ui) * ldd + j0, jin, dv[s]);
                 }
 #pragma unroll
                 for (int s = 0; s < U; ++s)
@@ -329,7 +329,7 @@ __device__ __forceinline__ void rev_blk_body(const int32_t* __restrict__ row_ptr
                 const int32_t ui = __shfl_sync(0xffffffffu, u, i);
                 const float xi = __shfl_sync(0xffffffffu, x, i);
                 float dv[NJ];
-                load_vec(D + (int64_t)ui * ldd + j0, jin, dv);
+                load_vec(D + (rmap ? (int64_t)rmap[ui] : (int64_t)ui) * ldd + j0, jin, dv);
 #pragma unroll
                 for (int t = 0; t < NJ; ++t) insert_sorted<KT>(z[t], cap[t], dv[t], xi);
             }
@@ -723,7 +723,7 @@ __global__ void k_prune_compact(const float* __restrict__ t_fwd, int64_t n, cons
 __device__ __forceinline__ void prune_select_body(const int64_t* __restrict__ cand, const float* __restrict__ sym,
                                const int* __restrict__ count, int cap, const float* __restrict__ sel_val,
                                int K, int64_t* __restrict__ out_idx, float* __restrict__ out_dist,
-                               int* __restrict__ ok)
+                               int* __restrict__ ok, bool complete = true)
 {
     __shared__ unsigned long long key[kPruneCap];
     __shared__ float kth;
@@ -742,7 +742,7 @@ __device__ __forceinline__ void prune_select_body(const int64_t* __restrict__ ca
     }
     if (i < c && r == K - 1) kth = __uint_as_float((unsigned)(me >> 32));
     __syncthreads();
-    if (i == 0) *ok = (*count <= cap && c >= K && kth <= prune_theta(sel_val[K - 1])) ? 1 : 0;
+    if (i == 0) *ok = (complete && *count <= cap && c >= K && kth <= prune_theta(sel_val[K - 1])) ? 1 : 0;
 }
 
 __global__ void k_prune_select(const int64_t* __restrict__ cand, const float* __restrict__ sym,
@@ -829,6 +829,118 @@ __global__ void k_fwd_g(const QDesc* __restrict__ qd, const int* __restrict__ nq
     }
 }
 
+// Cost of one nonzero from table entries already in registers (the first min(KT, 4) of its
+// row; entries 4.. of wider rows are loaded here, only while mass remains).  The same
+// operations in the same order as fwd_cost_p, so the values are bit-identical.
+template <int MEAS, int KT>
+__device__ __forceinline__ float fwd_cost_reg(float x, const float2 (&E)[KT < 4 ? KT : 4],
+                                              const float2* __restrict__ T, int keff)
+{
+    constexpr int KR = KT < 4 ? KT : 4;
+    if (MEAS == M_RWMD) return __fmul_rn(x, E[0].x);
+    if (MEAS == M_OMR) {
+        if (E[0].x == 0.f && keff >= 2) {
+            const float r = x - fminf(x, E[0].y);
+            return r != 0.f ? __fmul_rn(r, E[KR > 1 ? 1 : 0].x) : 0.f;
+        }
+        return __fmul_rn(x, E[0].x);
+    }
+    float r = x, c = 0.f;
+#pragma unroll
+    for (int l = 0; l < (KT > 1 ? KT - 1 : 0); ++l) {
+        if (l < keff - 1 && r != 0.f) {
+            const float2 t = l < KR ? E[l < KR ? l : 0] : T[l];
+            const float tau = fminf(r, t.y);
+            c = fmaf(tau, t.x, c);
+            r -= tau;
+        }
+    }
+    if (r == 0.f) return c;
+    const int lk = keff - 1;
+    float zl;
+    if (lk < KR) {
+        zl = E[0].x;
+#pragma unroll
+        for (int l = 1; l < KR; ++l) zl = lk == l ? E[l].x : zl;
+    } else {
+        zl = T[lk].x;
+    }
+    return fmaf(r, zl, c);
+}
+
+// Forward pass of a group of kFwdGroup queries in one sweep of the CSR, tables of width
+// <= KT (1, 2, 4, 8, 16) stored query-major within a row: query g's entries of row u at
+// tab + u * tab_rs + l (tab_rs = 8 KT, the query's own offset g KT is in its descriptor), so
+// a lane reads its first min(KT, 4) entries with independent vector loads before any
+// arithmetic -- no chain of dependent loads per nonzero.  A warp takes a document; the
+// column ids and weights of 32 consecutive nonzeros are read with one coalesced load per
+// lane and handed to the lanes that use them by shuffles (lane = 8 x phase + query, phase
+// = nonzero position mod 4).  Each phase sums its nonzeros in CSR order, then (p0 + p1) +
+// (p2 + p3): the order of every other form of the pass, so values are bit-identical.
+template <int MEAS, int KT>
+__global__ void __launch_bounds__(256, 3)
+k_fwd_gv(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t* __restrict__ row_ptr,
+         const int32_t* __restrict__ col, const float* __restrict__ val, int64_t n, bool to_out)
+{
+    constexpr int KR = KT < 4 ? KT : 4;
+    const int q0 = blockIdx.y * kFwdGroup;
+    const int nqv = *nq;
+    if (q0 >= nqv) return;
+    const int lane = threadIdx.x & 31, g = lane & 7, ph = lane >> 3;
+    const bool act = q0 + g < nqv;
+    const QDesc& dq = qd[act ? q0 + g : q0];
+    const float2* tq = dq.tab;
+    const int kq = dq.tk;
+    float* oq = to_out ? dq.t_out : dq.t_fwd;
+    const int rs = dq.tab_rs;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t d = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); d < n; d += warps) {
+        const int32_t a = row_ptr[d], b = row_ptr[d + 1];
+        float acc = 0.f;
+        for (int32_t eb = a; eb < b; eb += 32) {
+            const bool lin = eb + lane < b;
+            const int32_t cu = lin ? col[eb + lane] : 0;
+            const float cx = lin ? val[eb + lane] : 0.f;
+#pragma unroll
+            for (int r = 0; r < 8; r += 4) {  // four nonzeros per lane in flight
+                float2 E[4][KR];
+                float xs[4];
+                int32_t us[4];
+                bool ok[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int src = 4 * (r + i) + ph;
+                    us[i] = __shfl_sync(0xffffffffu, cu, src);
+                    xs[i] = __shfl_sync(0xffffffffu, cx, src);
+                    ok[i] = act && eb + src < b;
+                    const float2* T = tq + (int64_t)us[i] * rs;
+                    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if constexpr (KR == 4) {
+                        const float4 v0 = ok[i] ? *reinterpret_cast<const float4*>(T) : z4;
+                        const float4 v1 = ok[i] ? *reinterpret_cast<const float4*>(T + 2) : z4;
+                        E[i][0] = make_float2(v0.x, v0.y);
+                        E[i][1] = make_float2(v0.z, v0.w);
+                        E[i][2] = make_float2(v1.x, v1.y);
+                        E[i][3] = make_float2(v1.z, v1.w);
+                    } else if constexpr (KR == 2) {
+                        const float4 v0 = ok[i] ? *reinterpret_cast<const float4*>(T) : z4;
+                        E[i][0] = make_float2(v0.x, v0.y);
+                        E[i][1] = make_float2(v0.z, v0.w);
+                    } else {
+                        E[i][0] = ok[i] ? T[0] : make_float2(0.f, 0.f);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (ok[i]) acc = __fadd_rn(acc, fwd_cost_reg<MEAS, KT>(xs[i], E[i], tq + (int64_t)us[i] * rs, kq));
+            }
+        }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+        if (ph == 0 && act) oq[d] = acc;
+    }
+}
+
 // NJ follows the per-query launcher: NJW bins per lane when h > 32, else one.
 template <int MEAS, int KT, int NJW>
 __global__ void __launch_bounds__(256, 2)
@@ -867,19 +979,25 @@ __global__ void k_prune_compact_b(const QDesc* __restrict__ qd, const int* __res
     prune_compact_body(d.t_fwd, n, d.sel_val, K, kPruneCap, d.cand, d.cand_count);
 }
 
-template <int MEAS, int KT, int NJW, int W>
+// MAPPED: the distances come from the query's candidate-row block (fused path): used row u
+// is row rmap[u] of Dc.  A query whose candidate documents hold more than kCandRows distinct
+// rows has no complete block; it is skipped here and reported uncertified by the selection.
+template <int MEAS, int KT, int NJW, int W, bool MAPPED>
 __global__ void __launch_bounds__(W * 32, (W >= 8 ? 2 : 4))
 k_rev_blk_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t* __restrict__ row_ptr,
             const int32_t* __restrict__ col, const float* __restrict__ val, int k)
 {
     if ((int)blockIdx.y >= *nq) return;
     const QDesc& d = qd[blockIdx.y];
+    if (MAPPED && *d.ncrows > kCandRows) return;
+    const float* D = MAPPED ? d.Dc : d.D;
+    const int32_t* rmap = MAPPED ? d.rmap : nullptr;
     if (d.h > 32)
-        rev_blk_body<MEAS, KT, NJW, W>(row_ptr, col, val, d.D, d.ldd, d.h, d.qw, k, d.t_fwd, d.cand_sym + kPruneCap,
-                                       d.cand_sym, d.cand, d.cand_count, d.sq != 0);
+        rev_blk_body<MEAS, KT, NJW, W>(row_ptr, col, val, D, d.ldd, d.h, d.qw, k, d.t_fwd, d.cand_sym + kPruneCap,
+                                       d.cand_sym, d.cand, d.cand_count, d.sq != 0, rmap);
     else
-        rev_blk_body<MEAS, KT, 1, W>(row_ptr, col, val, d.D, d.ldd, d.h, d.qw, k, d.t_fwd, d.cand_sym + kPruneCap,
-                                     d.cand_sym, d.cand, d.cand_count, d.sq != 0);
+        rev_blk_body<MEAS, KT, 1, W>(row_ptr, col, val, D, d.ldd, d.h, d.qw, k, d.t_fwd, d.cand_sym + kPruneCap,
+                                     d.cand_sym, d.cand, d.cand_count, d.sq != 0, rmap);
 }
 
 // Reverse values of the candidate documents, rows of any width (ICT): a block of kRevW
@@ -895,11 +1013,12 @@ k_rev_generic_cand_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, c
                                d.cand_sym, d.cand, d.cand_count, d.sq != 0);
 }
 
-__global__ void k_prune_select_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int K)
+__global__ void k_prune_select_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int K, bool mapped)
 {
     if ((int)blockIdx.x >= *nq) return;
     const QDesc& d = qd[blockIdx.x];
-    prune_select_body(d.cand, d.cand_sym, d.cand_count, kPruneCap, d.sel_val, K, d.out_idx, d.out_dist, d.ok);
+    prune_select_body(d.cand, d.cand_sym, d.cand_count, kPruneCap, d.sel_val, K, d.out_idx, d.out_dist, d.ok,
+                      !mapped || *d.ncrows <= kCandRows);
 }
 
 template <int MEAS>
@@ -921,13 +1040,13 @@ cudaError_t rev_meas_b(int k, int dir, const QDesc* qd, const int* nq, int max_q
     return cudaGetLastError();
 }
 
-template <int MEAS, int W>
+template <int MEAS, int W, bool MAPPED>
 cudaError_t rev_meas_blk_bw(int k, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
                             const int32_t* col, const float* val, cudaStream_t st)
 {
     const int kt = MEAS == M_RWMD ? 1 : (MEAS == M_OMR ? 2 : k);
     const dim3 grid(kPruneCap, (unsigned)max_q);
-#define EMD_REVBQ(KT, NJ) k_rev_blk_b<MEAS, KT, NJ, W><<<grid, W * 32, 0, st>>>(qd, nq, row_ptr, col, val, k)
+#define EMD_REVBQ(KT, NJ) k_rev_blk_b<MEAS, KT, NJ, W, MAPPED><<<grid, W * 32, 0, st>>>(qd, nq, row_ptr, col, val, k)
     if (kt <= 1) EMD_REVBQ(1, 4);
     else if (kt <= 2) EMD_REVBQ(2, 4);
     else if (kt <= 4) EMD_REVBQ(4, 4);
@@ -939,13 +1058,46 @@ cudaError_t rev_meas_blk_bw(int k, const QDesc* qd, const int* nq, int max_q, co
 
 // Warps per candidate document: 2, 4 or 8 (the merge in chunk order makes the result
 // independent of the choice).
-template <int MEAS>
+template <int MEAS, bool MAPPED = false>
 cudaError_t rev_meas_blk_b(int k, int warps, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
                            const int32_t* col, const float* val, cudaStream_t st)
 {
-    if (warps <= 2) return rev_meas_blk_bw<MEAS, 2>(k, qd, nq, max_q, row_ptr, col, val, st);
-    if (warps <= 4) return rev_meas_blk_bw<MEAS, 4>(k, qd, nq, max_q, row_ptr, col, val, st);
-    return rev_meas_blk_bw<MEAS, 8>(k, qd, nq, max_q, row_ptr, col, val, st);
+    if (warps <= 2) return rev_meas_blk_bw<MEAS, 2, MAPPED>(k, qd, nq, max_q, row_ptr, col, val, st);
+    if (warps <= 4) return rev_meas_blk_bw<MEAS, 4, MAPPED>(k, qd, nq, max_q, row_ptr, col, val, st);
+    return rev_meas_blk_bw<MEAS, 8, MAPPED>(k, qd, nq, max_q, row_ptr, col, val, st);
+}
+
+// Candidate rows of the fused pruned path: every used row of every candidate document of
+// query q gets a row of q's candidate block (first come, first served: the block's row
+// order does not matter, each entry is computed independently).  A block per candidate
+// document.
+__global__ void k_cand_rows_b(const QDesc* __restrict__ qd, const int* __restrict__ nq,
+                              const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col)
+{
+    if ((int)blockIdx.y >= *nq) return;
+    const QDesc& d = qd[blockIdx.y];
+    if ((int)blockIdx.x >= min(*d.cand_count, kPruneCap)) return;
+    const int64_t doc = d.cand[blockIdx.x];
+    for (int32_t e = row_ptr[doc] + (int32_t)threadIdx.x; e < row_ptr[doc + 1]; e += blockDim.x) {
+        const int32_t u = col[e];
+        if (atomicCAS(&d.rmap[u], -1, -2) == -1) {
+            const int idx = atomicAdd(d.ncrows, 1);
+            if (idx < kCandRows) d.crows[idx] = u;
+            atomicExch(&d.rmap[u], idx);
+        }
+    }
+}
+
+// Returns the row map of the candidate documents' rows to -1 (the state every batch
+// starts from).
+__global__ void k_cand_reset_b(const QDesc* __restrict__ qd, const int* __restrict__ nq,
+                               const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col)
+{
+    if ((int)blockIdx.y >= *nq) return;
+    const QDesc& d = qd[blockIdx.y];
+    if ((int)blockIdx.x >= min(*d.cand_count, kPruneCap)) return;
+    const int64_t doc = d.cand[blockIdx.x];
+    for (int32_t e = row_ptr[doc] + (int32_t)threadIdx.x; e < row_ptr[doc + 1]; e += blockDim.x) d.rmap[col[e]] = -1;
 }
 
 template <int MEAS>
@@ -973,7 +1125,7 @@ cudaError_t rev_meas(int k, const int32_t* row_ptr, const int32_t* col, const fl
 }  // namespace
 
 // Register width of the forward cost for table width kw (0: the loop form).
-static int fwd_kt(int kw) { return kw <= 1 ? 1 : kw <= 2 ? 2 : kw <= 4 ? 4 : kw <= 8 ? 8 : kw <= 16 ? 16 : 0; }
+static int fwd_kt(int kw) { return fwd_reg_width(kw); }
 
 #define EMD_FWD_KT_SWITCH(KTV, LAUNCH)             \
     switch (KTV) {                                 \
@@ -1057,11 +1209,19 @@ cudaError_t launch_fwd_b(int meas, const QDesc* qd, const int* nq, int max_q, co
     if (grouped) {  // one document per warp, eight queries
         dim3 gg((unsigned)std::max<int64_t>(1, blocks), (unsigned)((max_q + kFwdGroup - 1) / kFwdGroup));
         switch (meas) {
-        case M_RWMD: k_fwd_g<M_RWMD, 0><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
-        case M_OMR: k_fwd_g<M_OMR, 0><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
+        case M_RWMD: k_fwd_gv<M_RWMD, 1><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
+        case M_OMR: k_fwd_gv<M_OMR, 2><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
+        case M_ICT: k_fwd_g<M_ACT, 0><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
         default: {
-#define EMD_L(KT) k_fwd_g<M_ACT, KT><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out)
-            EMD_FWD_KT_SWITCH(kt, EMD_L)
+#define EMD_L(KT) k_fwd_gv<M_ACT, KT><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out)
+            switch (kt) {
+            case 1: EMD_L(1); break;
+            case 2: EMD_L(2); break;
+            case 4: EMD_L(4); break;
+            case 8: EMD_L(8); break;
+            case 16: EMD_L(16); break;
+            default: k_fwd_g<M_ACT, 0><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
+            }
 #undef EMD_L
             break;
         }
@@ -1114,7 +1274,43 @@ cudaError_t launch_prune_b(int meas, int k, const QDesc* qd, const int* nq, int 
     default: e = rev_meas_blk_b<M_ACT>(k, rev_warps, qd, nq, max_q, row_ptr, col, val, st); break;
     }
     if (e != cudaSuccess) return e;
-    k_prune_select_b<<<(unsigned)max_q, kPruneCap, 0, st>>>(qd, nq, K);
+    k_prune_select_b<<<(unsigned)max_q, kPruneCap, 0, st>>>(qd, nq, K, false);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prune_compact_b(const QDesc* qd, const int* nq, int max_q, int64_t n, int K, cudaStream_t st)
+{
+    if (max_q <= 0) return cudaSuccess;
+    const int blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256), 152 * 4);
+    k_prune_compact_b<<<dim3((unsigned)blocks, (unsigned)max_q), 256, 0, st>>>(qd, nq, n, K);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cand_rows_b(const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr, const int32_t* col,
+                               bool reset, cudaStream_t st)
+{
+    if (max_q <= 0) return cudaSuccess;
+    const dim3 g(kPruneCap, (unsigned)max_q);
+    if (reset)
+        k_cand_reset_b<<<g, 128, 0, st>>>(qd, nq, row_ptr, col);
+    else
+        k_cand_rows_b<<<g, 128, 0, st>>>(qd, nq, row_ptr, col);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prune_mapped_b(int meas, int k, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
+                                  const int32_t* col, const float* val, int K, int rev_warps, cudaStream_t st)
+{
+    if (max_q <= 0) return cudaSuccess;
+    cudaError_t e;
+    switch (meas) {
+    case M_RWMD: e = rev_meas_blk_b<M_RWMD, true>(k, rev_warps, qd, nq, max_q, row_ptr, col, val, st); break;
+    case M_OMR: e = rev_meas_blk_b<M_OMR, true>(k, rev_warps, qd, nq, max_q, row_ptr, col, val, st); break;
+    case M_ACT: e = rev_meas_blk_b<M_ACT, true>(k, rev_warps, qd, nq, max_q, row_ptr, col, val, st); break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    k_prune_select_b<<<(unsigned)max_q, kPruneCap, 0, st>>>(qd, nq, K, true);
     return cudaGetLastError();
 }
 

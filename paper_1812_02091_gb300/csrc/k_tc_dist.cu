@@ -686,6 +686,614 @@ k_tc_dist_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
     }
 }
 
+// ------------------------------------------------------------------ fused Phase-1 table
+//
+// Phase 1 with the per-row top-k folded into the product's epilogue (Section 5, Fig. 6:
+// V Q^T, then per row the k smallest with their query bins): the squared distances of a
+// vocabulary row to a query's bins never leave the registers of the thread that owns the
+// row, which keeps the KT smallest (value, bin) pairs and writes only the table (z =
+// square root, w = the bin's weight).
+//
+// Work item = (vocabulary row tile, query group) as in k_tc_dist_batch, same operand
+// panels, copies, MMA order and epilogue arithmetic, so every squared distance is
+// bit-identical to the batched matrix kernel's (and the exact zero of an identical
+// vocabulary id is applied to the same entry).  The item's column tiles run in two
+// streams: each query belongs to one stream, a stream takes the group's next query when
+// its current one is done, and tiles are issued alternately from the two streams.  Stream
+// s has TMEM accumulator buffer s and epilogue warpgroup s (warps 2+4s .. 5+4s, one per
+// TMEM lane quarter), so all tiles of a query reach the same 128 threads and a row's list
+// lives in one thread for the whole query: no merge across threads.  A thread sees its
+// row's columns in increasing bin order and inserts only strictly smaller values, so ties
+// keep the lower bin -- the order the table kernel applies to the matrix.
+constexpr int TCT_THREADS = 64 + 32 * 8;  // copy warp, MMA warp, two epilogue warpgroups
+
+// The interleaved two-stream tile order of one work item (every role walks it alike).
+// Scalar fields (no arrays indexed at run time, which would live in local memory).
+struct TileSeq {
+    int qb, nextq, cq0, cq1, c0, c1, turn;
+    __device__ __forceinline__ void init(int qa, int qb_)
+    {
+        qb = qb_;
+        nextq = qa;
+        cq0 = cq1 = -1;
+        c0 = c1 = 0;
+        turn = 0;
+    }
+    // Next tile (query q, first column n0, stream s); false when the item is done.
+    __device__ __forceinline__ bool next(const QDesc* __restrict__ qd, int& q, int& n0, int& s)
+    {
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int st = turn ^ t;
+            int cq = st ? cq1 : cq0, c = st ? c1 : c0;
+            if (cq < 0 && nextq < qb) {
+                cq = nextq++;
+                c = 0;
+            }
+            if (cq >= 0) {
+                q = cq;
+                n0 = c;
+                s = st;
+                c += TC_BN;
+                if (c >= qd[cq].h) cq = -1;
+                if (st) { cq1 = cq; c1 = c; } else { cq0 = cq; c0 = c; }
+                turn = st ^ 1;
+                return true;
+            }
+            if (st) { cq1 = cq; c1 = c; } else { cq0 = cq; c0 = c; }
+        }
+        return false;
+    }
+};
+
+// Sorted insertion of (d, j) into the KT smallest; strict '<' keeps the earlier bin first.
+template <int KT>
+__device__ __forceinline__ void tc_insert(float (&z)[KT], int (&s)[KT], float d, int j)
+{
+    bool p[KT];
+#pragma unroll
+    for (int l = 0; l < KT; ++l) p[l] = d < z[l];
+#pragma unroll
+    for (int l = KT - 1; l > 0; --l) {
+        z[l] = p[l - 1] ? z[l - 1] : (p[l] ? d : z[l]);
+        s[l] = p[l - 1] ? s[l - 1] : (p[l] ? j : s[l]);
+    }
+    z[0] = p[0] ? d : z[0];
+    s[0] = p[0] ? j : s[0];
+}
+
+template <int FMT, int KT>
+__global__ void __launch_bounds__(TCT_THREADS, 1)
+k_tc_table_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_lo, int64_t Mpad,
+                 const float* __restrict__ a_scale, const float* __restrict__ a_norm, int64_t M,
+                 const QDesc* __restrict__ qd, const int* __restrict__ nq_dev, int groups, int KC, int stages,
+                 int* __restrict__ err)
+{
+    constexpr bool SPLIT = FMT == TC_SPLIT;
+    constexpr uint32_t EB = TcFmt<FMT>::EB;
+    constexpr int kParts = (int)TcFmt<FMT>::parts;
+    constexpr uint32_t kABytes = TC_BM * EB;
+    constexpr uint32_t kBBytes = TC_BN * EB;
+    constexpr uint32_t kSbo = 8 * EB;
+    constexpr uint32_t kAChunk = kParts * kABytes;
+    constexpr uint32_t kBStage = kParts * kBBytes;
+    constexpr uint32_t kAcc = SPLIT ? 256 : 128;
+    constexpr uint32_t kCols = 2 * kAcc;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* apanel = smem;
+    uint8_t* bring = apanel + (size_t)KC * kAChunk;
+    uint64_t* full = reinterpret_cast<uint64_t*>(bring + (size_t)stages * kBStage);
+    uint64_t* empty = full + stages;
+    uint64_t* tfull = empty + stages;   // [2] stream s's accumulator ready
+    uint64_t* tempty = tfull + 2;       // [2] stream s's accumulator drained (4 warps)
+    uint64_t* afull = tempty + 2;
+    uint64_t* afree = afull + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(afree + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nq = *nq_dev;
+    const int m_tiles = (int)(Mpad / TC_BM);
+    const int total = m_tiles * groups;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
+        mbar_init(afull, 1);
+        mbar_init(afree, 1);
+        *abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, kCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    auto fail = [&]() {
+        atomicOr(err, ERR_TIMEOUT);
+        *abort_flag = 1;
+    };
+    auto qrange = [&](int g, int& qa, int& qb) {
+        qa = (int)((int64_t)g * nq / groups);
+        qb = (int)((int64_t)(g + 1) * nq / groups);
+    };
+
+    if (warp == 0 && lane == 0) {
+        int64_t gb = 0;
+        int items = 0;
+        bool ok = true;
+        for (int w = blockIdx.x; w < total && ok && !*abort_flag; w += gridDim.x, ++items) {
+            const int64_t m0 = (int64_t)(w % m_tiles) * TC_BM;
+            if (items > 0 && !mbar_wait(afree, (uint32_t)(items - 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                fail();
+                break;
+            }
+            mbar_expect_tx(afull, (uint32_t)KC * kAChunk);
+            for (int c = 0; c < KC; ++c) {
+                uint8_t* ast = apanel + (size_t)c * kAChunk;
+                bulk_g2s(ast, A_hi + ((int64_t)c * Mpad + m0) * EB, kABytes, afull);
+                if (SPLIT) bulk_g2s(ast + kABytes, A_lo + ((int64_t)c * Mpad + m0) * EB, kABytes, afull);
+            }
+            int qa, qb, q, n0, s;
+            qrange(w / m_tiles, qa, qb);
+            TileSeq ts;
+            ts.init(qa, qb);
+            while (ok && ts.next(qd, q, n0, s)) {
+                const QDesc& d = qd[q];
+                const int Nt = min(TC_BN, (int)round_up(d.h - n0, 16));
+                const uint32_t b_bytes = (uint32_t)Nt * EB;
+                const uint8_t* bh = static_cast<const uint8_t*>(d.q_hi);
+                const uint8_t* bl = static_cast<const uint8_t*>(d.q_lo);
+                for (int c = 0; c < KC; ++c, ++gb) {
+                    const int st = (int)(gb % stages);
+                    if (gb >= stages &&
+                        !mbar_wait(&empty[st], (uint32_t)((gb / stages) - 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* bst = bring + (size_t)st * kBStage;
+                    mbar_expect_tx(&full[st], (uint32_t)kParts * b_bytes);
+                    bulk_g2s(bst, bh + ((int64_t)c * d.npad + n0) * EB, b_bytes, &full[st]);
+                    if (SPLIT) bulk_g2s(bst + kBBytes, bl + ((int64_t)c * d.npad + n0) * EB, b_bytes, &full[st]);
+                }
+            }
+        }
+        const uint64_t tail = global_ns() + TC_TIMEOUT_NS;
+        for (int64_t c = gb > stages ? gb - stages : 0; c < gb; ++c)
+            if (!mbar_wait(&full[c % stages], (uint32_t)(c / stages) & 1u, tail)) atomicOr(err, ERR_TIMEOUT);
+        if (items > 0 && !mbar_wait(afull, (uint32_t)(items - 1) & 1u, tail)) atomicOr(err, ERR_TIMEOUT);
+    } else if (warp == 1 && lane == 0) {
+        int64_t gb = 0;
+        int cnt0 = 0, cnt1 = 0, items = 0;  // tiles issued per stream
+        bool ok = true;
+        for (int w = blockIdx.x; w < total && ok && !*abort_flag; w += gridDim.x, ++items) {
+            if (!mbar_wait(afull, (uint32_t)items & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                fail();
+                break;
+            }
+            int qa, qb, q, n0, s;
+            qrange(w / m_tiles, qa, qb);
+            TileSeq ts;
+            ts.init(qa, qb);
+            while (ok && ts.next(qd, q, n0, s)) {
+                const int Nt = min(TC_BN, (int)round_up(qd[q].h - n0, 16));
+                const uint32_t idesc = (1u << 4) | (TcFmt<FMT>::atype << 7) | (TcFmt<FMT>::atype << 10) |
+                                       ((uint32_t)(Nt >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+                const int cs = s ? cnt1 : cnt0;
+                if (cs >= 1 && !mbar_wait(&tempty[s], (uint32_t)(cs - 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                    fail();
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t acc0 = tmem + (uint32_t)s * kAcc;
+                for (int c = 0; c < KC; ++c, ++gb) {
+                    const int st = (int)(gb % stages);
+                    if (!mbar_wait(&full[st], (uint32_t)(gb / stages) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(apanel + (size_t)c * kAChunk);
+                    const uint32_t sa_lo = sa + kABytes;
+                    const uint32_t sb = smem_u32(bring + (size_t)st * kBStage);
+                    const uint32_t sb_lo = sb + kBBytes;
+#pragma unroll
+                    for (int ks = 0; ks < (int)TcFmt<FMT>::mmas; ++ks) {
+                        const uint32_t ko = (uint32_t)ks * 256u;
+                        const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+                        const uint64_t da = smem_desc(sa + ko, kSbo), db = smem_desc(sb + ko, kSbo);
+                        mma_issue<FMT>(acc0, da, db, idesc, acc);
+                        if (SPLIT) {
+                            mma_issue<FMT>(acc0 + 128, da, smem_desc(sb_lo + ko, kSbo), idesc, acc);
+                            mma_issue<FMT>(acc0 + 128, smem_desc(sa_lo + ko, kSbo), db, idesc, 1u);
+                        }
+                    }
+                    mma_commit(&empty[st]);
+                }
+                if (!ok) break;
+                mma_commit(&tfull[s]);
+                if (s) ++cnt1; else ++cnt0;
+            }
+            mma_commit(afree);
+        }
+    } else if (warp >= 2) {
+        // epilogue: warpgroup sme = stream sme; warp w reads TMEM lane quarter w % 4
+        const int qw4 = warp & 3;
+        const int sme = (warp - 2) >> 2;
+        const int row = qw4 * 32 + lane;
+        int cnt = 0;
+        bool ok = true;
+        float z[KT];
+        int sj[KT];
+        for (int w = blockIdx.x; w < total && ok && !*abort_flag; w += gridDim.x) {
+            const int64_t m0 = (int64_t)(w % m_tiles) * TC_BM;
+            const int64_t u = m0 + row;
+            const bool row_ok = u < M;
+            const float su = row_ok ? a_scale[u] : 0.f;
+            const float nu = row_ok ? a_norm[u] : 0.f;
+            int qa, qb, q, n0, s;
+            qrange(w / m_tiles, qa, qb);
+            TileSeq ts;
+            ts.init(qa, qb);
+            while (ok && ts.next(qd, q, n0, s)) {
+                if (s != sme) continue;
+                const QDesc& d = qd[q];
+                const int N = d.h;
+                const int Nt = min(TC_BN, (int)round_up(N - n0, 16));
+                if (n0 == 0) {
+#pragma unroll
+                    for (int l = 0; l < KT; ++l) {
+                        z[l] = INFINITY;
+                        sj[l] = INT32_MAX;
+                    }
+                }
+                // the query bin of this row's own vocabulary id, if any: its squared distance is 0
+                const int jstar = row_ok ? d.qpos[u] : -1;
+                // lane l holds the constants of columns n0 + 32 c + l, broadcast by shuffles
+                float cbl[4], nbl[4];
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    const int col = n0 + 32 * c4 + lane;
+                    const bool cok = col < N;
+                    cbl[c4] = cok ? -2.f * d.q_scale[col] : 0.f;
+                    nbl[c4] = cok ? d.qnorm[col] : 0.f;
+                }
+                if (!mbar_wait(&tfull[sme], (uint32_t)cnt & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                    fail();
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tbase = tmem + (uint32_t)sme * kAcc + ((uint32_t)(qw4 * 32) << 16);
+#pragma unroll
+                for (int cc = 0; cc < TC_BN; cc += 16) {
+                    if (cc < Nt) {
+                        uint32_t r0[16], r1[16];
+                        tmem_ld16(tbase + (uint32_t)cc, r0);
+                        if (SPLIT) tmem_ld16(tbase + 128u + (uint32_t)cc, r1);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const int jc = cc + e;
+                            const float cb = __shfl_sync(0xffffffffu, cbl[jc >> 5], jc & 31);
+                            const float nb = __shfl_sync(0xffffffffu, nbl[jc >> 5], jc & 31);
+                            float dot = __uint_as_float(r0[e]);
+                            if (SPLIT) dot = fmaf(__uint_as_float(r1[e]), 1.0f / 2048.0f, dot);
+                            const int j = n0 + jc;
+                            float d2 = fmaf(cb * su, dot, nu + nb);  // as k_tc_dist_batch writes it
+                            d2 = j == jstar ? 0.f : d2;
+                            if (j < N && d2 < z[KT - 1]) tc_insert<KT>(z, sj, d2, j);
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[sme]);
+                ++cnt;
+                if (n0 + TC_BN >= N && row_ok) {  // the query's last tile: write its table row
+#pragma unroll
+                    for (int l = 0; l < KT; ++l) {
+                        if (l < d.tk) {
+                            const bool valid = sj[l] != INT32_MAX;
+                            d.tab[u * d.tab_rs + (int64_t)l * d.tab_es] =
+                                make_float2(valid ? sq_to_dist(z[l]) : INFINITY, valid ? d.qw[sj[l]] : 0.f);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kCols);
+    }
+}
+
+// ------------------------------------------------------------------ candidate-row block
+//
+// The reverse direction of the fused pruned path needs D only on the used rows of the
+// candidate documents.  Their packed panel rows are gathered (k_cand_pack_b) and this
+// kernel computes their squared distances to the query's bins with the same operands, MMA
+// order and epilogue as k_tc_dist_batch, so each entry equals the full matrix's entry.
+// Work item = (query q, 128-row tile r of q's candidate rows); items past a query's row
+// count are skipped by every role alike.
+template <int FMT>
+__global__ void __launch_bounds__(TCB_THREADS, 1)
+k_tc_cand_batch(const QDesc* __restrict__ qd, const int* __restrict__ nq_dev, int max_q, int KC, int stages,
+                int* __restrict__ err)
+{
+    constexpr bool SPLIT = FMT == TC_SPLIT;
+    constexpr uint32_t EB = TcFmt<FMT>::EB;
+    constexpr int kParts = (int)TcFmt<FMT>::parts;
+    constexpr uint32_t kABytes = TC_BM * EB;
+    constexpr uint32_t kBBytes = TC_BN * EB;
+    constexpr uint32_t kSbo = 8 * EB;
+    constexpr uint32_t kAChunk = kParts * kABytes;
+    constexpr uint32_t kBStage = kParts * kBBytes;
+    constexpr uint32_t kAcc = SPLIT ? 256 : 128;
+    constexpr uint32_t kCols = 2 * kAcc;
+    constexpr int kRT = kCandRows / TC_BM;  // row tiles per query
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* apanel = smem;
+    uint8_t* bring = apanel + (size_t)KC * kAChunk;
+    uint64_t* full = reinterpret_cast<uint64_t*>(bring + (size_t)stages * kBStage);
+    uint64_t* empty = full + stages;
+    uint64_t* tfull = empty + stages;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* afull = tempty + 2;
+    uint64_t* afree = afull + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(afree + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nq = *nq_dev;
+    const int total = max_q * kRT;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], TCB_EPI_WARPS);
+        }
+        mbar_init(afull, 1);
+        mbar_init(afree, 1);
+        *abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, kCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    auto fail = [&]() {
+        atomicOr(err, ERR_TIMEOUT);
+        *abort_flag = 1;
+    };
+    // rows of item w (0 when the item is past its query's candidate rows)
+    auto item_rows = [&](int w) -> int {
+        const int q = w / kRT, r = w % kRT;
+        if (q >= nq) return 0;
+        const int nr = min(*qd[q].ncrows, kCandRows);
+        return max(0, min(TC_BM, nr - r * TC_BM));
+    };
+
+    if (warp == 0 && lane == 0) {
+        int64_t gb = 0;
+        int items = 0;
+        bool ok = true;
+        for (int w = blockIdx.x; w < total && ok && !*abort_flag; w += gridDim.x) {
+            if (item_rows(w) == 0) continue;
+            const QDesc& d = qd[w / kRT];
+            const int64_t m0 = (int64_t)(w % kRT) * TC_BM;
+            if (items > 0 && !mbar_wait(afree, (uint32_t)(items - 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                fail();
+                break;
+            }
+            const uint8_t* ah = static_cast<const uint8_t*>(d.c_hi);
+            const uint8_t* al = static_cast<const uint8_t*>(d.c_lo);
+            mbar_expect_tx(afull, (uint32_t)KC * kAChunk);
+            for (int c = 0; c < KC; ++c) {
+                uint8_t* ast = apanel + (size_t)c * kAChunk;
+                bulk_g2s(ast, ah + ((int64_t)c * kCandRows + m0) * EB, kABytes, afull);
+                if (SPLIT) bulk_g2s(ast + kABytes, al + ((int64_t)c * kCandRows + m0) * EB, kABytes, afull);
+            }
+            ++items;
+            const uint8_t* bh = static_cast<const uint8_t*>(d.q_hi);
+            const uint8_t* bl = static_cast<const uint8_t*>(d.q_lo);
+            for (int n0 = 0; n0 < d.h && ok; n0 += TC_BN) {
+                const int Nt = min(TC_BN, (int)round_up(d.h - n0, 16));
+                const uint32_t b_bytes = (uint32_t)Nt * EB;
+                for (int c = 0; c < KC; ++c, ++gb) {
+                    const int s = (int)(gb % stages);
+                    if (gb >= stages &&
+                        !mbar_wait(&empty[s], (uint32_t)((gb / stages) - 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* bst = bring + (size_t)s * kBStage;
+                    mbar_expect_tx(&full[s], (uint32_t)kParts * b_bytes);
+                    bulk_g2s(bst, bh + ((int64_t)c * d.npad + n0) * EB, b_bytes, &full[s]);
+                    if (SPLIT) bulk_g2s(bst + kBBytes, bl + ((int64_t)c * d.npad + n0) * EB, b_bytes, &full[s]);
+                }
+            }
+        }
+        const uint64_t tail = global_ns() + TC_TIMEOUT_NS;
+        for (int64_t c = gb > stages ? gb - stages : 0; c < gb; ++c)
+            if (!mbar_wait(&full[c % stages], (uint32_t)(c / stages) & 1u, tail)) atomicOr(err, ERR_TIMEOUT);
+        if (items > 0 && !mbar_wait(afull, (uint32_t)(items - 1) & 1u, tail)) atomicOr(err, ERR_TIMEOUT);
+    } else if (warp == 1 && lane == 0) {
+        int64_t gb = 0;
+        int it = 0, items = 0;
+        bool ok = true;
+        for (int w = blockIdx.x; w < total && ok && !*abort_flag; w += gridDim.x) {
+            if (item_rows(w) == 0) continue;
+            const int h = qd[w / kRT].h;
+            if (!mbar_wait(afull, (uint32_t)items & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                fail();
+                break;
+            }
+            ++items;
+            for (int n0 = 0; n0 < h && ok; n0 += TC_BN, ++it) {
+                const int Nt = min(TC_BN, (int)round_up(h - n0, 16));
+                const uint32_t idesc = (1u << 4) | (TcFmt<FMT>::atype << 7) | (TcFmt<FMT>::atype << 10) |
+                                       ((uint32_t)(Nt >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+                const int buf = it & 1;
+                if (it >= 2 && !mbar_wait(&tempty[buf], (uint32_t)((it >> 1) - 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                    fail();
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t acc0 = tmem + (uint32_t)buf * kAcc;
+                for (int c = 0; c < KC; ++c, ++gb) {
+                    const int s = (int)(gb % stages);
+                    if (!mbar_wait(&full[s], (uint32_t)(gb / stages) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(apanel + (size_t)c * kAChunk);
+                    const uint32_t sa_lo = sa + kABytes;
+                    const uint32_t sb = smem_u32(bring + (size_t)s * kBStage);
+                    const uint32_t sb_lo = sb + kBBytes;
+#pragma unroll
+                    for (int ks = 0; ks < (int)TcFmt<FMT>::mmas; ++ks) {
+                        const uint32_t ko = (uint32_t)ks * 256u;
+                        const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+                        const uint64_t da = smem_desc(sa + ko, kSbo), db = smem_desc(sb + ko, kSbo);
+                        mma_issue<FMT>(acc0, da, db, idesc, acc);
+                        if (SPLIT) {
+                            mma_issue<FMT>(acc0 + 128, da, smem_desc(sb_lo + ko, kSbo), idesc, acc);
+                            mma_issue<FMT>(acc0 + 128, smem_desc(sa_lo + ko, kSbo), db, idesc, 1u);
+                        }
+                    }
+                    mma_commit(&empty[s]);
+                }
+                mma_commit(&tfull[buf]);
+            }
+            mma_commit(afree);
+        }
+    } else if (warp >= 2) {
+        const int qw4 = warp & 3;
+        const int cc = ((warp - 2) >> 2) * 32;
+        const int row = qw4 * 32 + lane;
+        int it = 0;
+        bool ok = true;
+        for (int w = blockIdx.x; w < total && ok && !*abort_flag; w += gridDim.x) {
+            const int nr = item_rows(w);
+            if (nr == 0) continue;
+            const QDesc& d = qd[w / kRT];
+            const int64_t u = (int64_t)(w % kRT) * TC_BM + row;  // candidate row
+            const bool row_ok = row < nr;
+            const float su = row_ok ? d.c_scale[u] : 0.f;
+            const float nu = row_ok ? d.c_norm[u] : 0.f;
+            const int jstar = row_ok ? d.qpos[d.crows[u]] : -1;
+            const int N = d.h, ldd = d.ldd;
+            for (int n0 = 0; n0 < N; n0 += TC_BN, ++it) {
+                const int Nt = min(TC_BN, (int)round_up(N - n0, 16));
+                const int buf = it & 1;
+                const int lcol = n0 + cc + lane;
+                const bool lok = lcol < N;
+                const float cb_l = lok ? -2.f * d.q_scale[lcol] : 0.f;
+                const float nb_l = lok ? d.qnorm[lcol] : 0.f;
+                if (!mbar_wait(&tfull[buf], (uint32_t)(it >> 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                    fail();
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                if (cc < Nt) {
+                    const uint32_t tbase = tmem + (uint32_t)buf * kAcc + ((uint32_t)(qw4 * 32) << 16);
+                    float* out = d.Dc + (row_ok ? u : 0) * ldd + n0 + cc;
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        uint32_t r0[16], r1[16];
+                        tmem_ld16(tbase + (uint32_t)(cc + 16 * hh), r0);
+                        if (SPLIT) tmem_ld16(tbase + 128u + (uint32_t)(cc + 16 * hh), r1);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int e4 = 4 * hh; e4 < 4 * hh + 4; ++e4) {
+                            float o[4];
+#pragma unroll
+                            for (int tt = 0; tt < 4; ++tt) {
+                                const int e = e4 * 4 + tt;
+                                const int er = e - 16 * hh;
+                                const float cb = __shfl_sync(0xffffffffu, cb_l, e);
+                                const float nb = __shfl_sync(0xffffffffu, nb_l, e);
+                                float dot = __uint_as_float(r0[er]);
+                                if (SPLIT) dot = fmaf(__uint_as_float(r1[er]), 1.0f / 2048.0f, dot);
+                                o[tt] = fmaf(cb * su, dot, nu + nb);
+                                o[tt] = n0 + cc + e == jstar ? 0.f : o[tt];
+                            }
+                            if (row_ok && n0 + cc + e4 * 4 < ldd)
+                                *reinterpret_cast<float4*>(out + e4 * 4) = make_float4(o[0], o[1], o[2], o[3]);
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[buf]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kCols);
+    }
+}
+
+// Gathers the packed FP16-split panel rows (hi and lo), scales and squared norms of each
+// query's candidate rows (qd[q].crows) from the vocabulary panels: one warp per row, 16-byte
+// pieces (a row's 8 consecutive K elements of one core matrix).
+__global__ void k_cand_pack_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, const uint8_t* __restrict__ a_hi,
+                              const uint8_t* __restrict__ a_lo, int64_t Mpad, const float* __restrict__ a_scale,
+                              const float* __restrict__ a_norm, int KC)
+{
+    if ((int)blockIdx.y >= *nq) return;
+    const QDesc& d = qd[blockIdx.y];
+    const int nr = min(*d.ncrows, kCandRows);
+    const int lane = threadIdx.x & 31;
+    const int warps = (int)(gridDim.x * (blockDim.x >> 5));
+    uint8_t* ch = static_cast<uint8_t*>(d.c_hi);
+    uint8_t* cl = static_cast<uint8_t*>(d.c_lo);
+    for (int i = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); i < nr; i += warps) {
+        const int64_t u = d.crows[i];
+        for (int p = lane; p < KC * 8; p += 32) {  // piece p: chunk p / 8, core matrix p % 8
+            const int64_t c = p >> 3, kk = p & 7;
+            const int64_t src = 2 * (c * Mpad * 64 + (u >> 3) * 512 + kk * 64 + (u & 7) * 8);
+            const int64_t dst = 2 * (c * (int64_t)kCandRows * 64 + (int64_t)(i >> 3) * 512 + kk * 64 + (i & 7) * 8);
+            *reinterpret_cast<uint4*>(ch + dst) = *reinterpret_cast<const uint4*>(a_hi + src);
+            *reinterpret_cast<uint4*>(cl + dst) = *reinterpret_cast<const uint4*>(a_lo + src);
+        }
+        if (lane == 0) {
+            d.c_scale[i] = a_scale[u];
+            d.c_norm[i] = a_norm[u];
+        }
+    }
+}
+
 // Pack rows of an FP32 matrix (ld floats per row, first m used) into the canonical layout
 // above.  For 2-byte formats element (r, k) of a matrix with Rpad rows lives at byte
 // 2 * ((k/64)*Rpad*64 + (r/8)*512 + ((k%64)/8)*64 + (r%8)*8 + k%8); for E4M3 at byte
@@ -904,6 +1512,76 @@ cudaError_t launch_tc_dist(int fmt, const void* A_hi, const void* A_lo, int64_t 
                                   Npad, b_scale, b_norm, N, KC, stages, D, ldd, err);
     default: return cudaErrorInvalidValue;
     }
+}
+
+}  // namespace emd
+
+namespace emd {
+
+template <int FMT, int KT>
+static cudaError_t tc_table_launch(dim3 grid, size_t smem, cudaStream_t st, const void* A_hi, const void* A_lo,
+                                   int64_t Mpad, const float* a_scale, const float* a_norm, int64_t M, const QDesc* qd,
+                                   const int* nq, int groups, int KC, int stages, int* err)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_tc_table_batch<FMT, KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_tc_table_batch<FMT, KT><<<grid, TCT_THREADS, smem, st>>>(static_cast<const uint8_t*>(A_hi),
+                                                               static_cast<const uint8_t*>(A_lo), Mpad, a_scale,
+                                                               a_norm, M, qd, nq, groups, KC, stages, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_table_batch(int fmt, const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
+                                  const float* a_norm, int64_t M, const QDesc* qd, const int* nq, int max_q, int Kpad,
+                                  int max_tk, int group_mult, int stages_req, int* err, cudaStream_t st)
+{
+    if (M <= 0 || max_q <= 0) return cudaSuccess;
+    if (fmt != TC_SPLIT || max_tk < 1 || max_tk > 16) return cudaErrorInvalidValue;
+    const int KC = Kpad / 64;
+    const int fit = tc_batch_stages(fmt, KC);
+    if (fit < 2) return cudaErrorInvalidValue;
+    const int stages = stages_req >= 2 ? std::min(stages_req, fit) : fit;
+    const size_t smem = tc_batch_smem_bytes(fmt, stages, KC);
+    const int m_tiles = (int)(Mpad / TC_BM);
+    const int sms = sm_count();
+    const int groups = std::max(1, std::min(max_q, std::max(1, group_mult) * ((2 * sms + m_tiles - 1) / m_tiles)));
+    const dim3 grid((unsigned)std::min<int64_t>((int64_t)m_tiles * groups, sms));
+#define EMD_TT(KT) \
+    return tc_table_launch<TC_SPLIT, KT>(grid, smem, st, A_hi, A_lo, Mpad, a_scale, a_norm, M, qd, nq, groups, KC, stages, err)
+    if (max_tk <= 1) EMD_TT(1);
+    if (max_tk <= 2) EMD_TT(2);
+    if (max_tk <= 4) EMD_TT(4);
+    if (max_tk <= 8) EMD_TT(8);
+    EMD_TT(16);
+#undef EMD_TT
+}
+
+cudaError_t launch_cand_pack_b(const QDesc* qd, const int* nq, int max_q, const void* a_hi, const void* a_lo,
+                               int64_t Mpad, const float* a_scale, const float* a_norm, int Kpad, cudaStream_t st)
+{
+    if (max_q <= 0) return cudaSuccess;
+    const dim3 g(256, (unsigned)max_q);
+    k_cand_pack_b<<<g, 256, 0, st>>>(qd, nq, static_cast<const uint8_t*>(a_hi), static_cast<const uint8_t*>(a_lo), Mpad,
+                                     a_scale, a_norm, Kpad / 64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_cand_batch(const QDesc* qd, const int* nq, int max_q, int Kpad, int stages_req, int* err,
+                                 cudaStream_t st)
+{
+    if (max_q <= 0) return cudaSuccess;
+    const int KC = Kpad / 64;
+    const int fit = tc_batch_stages(TC_SPLIT, KC);
+    if (fit < 2) return cudaErrorInvalidValue;
+    const int stages = stages_req >= 2 ? std::min(stages_req, fit) : fit;
+    const size_t smem = tc_batch_smem_bytes(TC_SPLIT, stages, KC);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_cand_batch<TC_SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)std::min<int64_t>((int64_t)max_q * (kCandRows / TC_BM), sm_count()));
+    k_tc_cand_batch<TC_SPLIT><<<grid, TCB_THREADS, smem, st>>>(qd, nq, max_q, KC, stages, err);
+    return cudaGetLastError();
 }
 
 }  // namespace emd

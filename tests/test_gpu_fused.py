@@ -1,0 +1,124 @@
+"""The fused form of the batched pruned top-K path (precision FP32_TC): the Phase-1 table is
+taken in the tensor-core product's epilogue and the reverse direction reads an exact
+distance block over the candidate documents' rows only, so no v_used x h_q matrix is
+written.  Every distance it uses is computed by the same operands, MMA order and epilogue
+arithmetic as the full matrix's entry, and the table keeps the k smallest by (value, bin)
+as the table kernel does, so the answers must be bit-identical to the materialized form
+(fused_phase1 = 0), which the other tests check against the FP64 oracle; the oracle
+comparison at full query sizes runs through this path too (test_gpu_mixed)."""
+import numpy as np
+import pytest
+
+import emd_synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def emd():
+    import paper_1812_02091_gb300 as m
+    from paper_1812_02091_gb300 import _build
+    _build.build()
+    m.load()
+    return m
+
+
+def pair(emd, w, **opt):
+    base = dict(precision="fp32_tc", autotune=0, **opt)
+    f = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
+                          emd.emd_db_options_default(fused_phase1=1, **base), v=w.v)
+    m = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
+                          emd.emd_db_options_default(fused_phase1=0, **base), v=w.v)
+    return f, m
+
+
+def same_topk(emd, f, m, q, meas, k, K):
+    a = emd.emd_topk(f, q.row_ptr, q.col, q.val, meas, k, "max", K)
+    b = emd.emd_topk(m, q.row_ptr, q.col, q.val, meas, k, "max", K)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+    return a
+
+
+@pytest.fixture(scope="module")
+def text():
+    w = emd_synth.config(2, query_limit=48)
+    return w
+
+
+@pytest.mark.parametrize("meas,k", [("act", 1), ("act", 2), ("act", 3), ("act", 4), ("act", 8), ("act", 16),
+                                    ("rwmd", 1), ("omr", 1)])
+def test_fused_equals_materialized_text(emd, text, meas, k):
+    f, m = pair(emd, text, max_query_h=1024)
+    try:
+        emd.emd_db_profile_reset(f)
+        same_topk(emd, f, m, text.queries, meas, k, 16)
+        prof = emd.emd_db_profile_get(f)
+        assert prof["pruned_queries"] == text.queries.n and prof["prune_fallbacks"] == 0
+        emd.emd_db_check_device_errors(f)
+    finally:
+        emd.emd_db_destroy(f)
+        emd.emd_db_destroy(m)
+
+
+def test_fused_equals_materialized_mixed_sizes(emd):
+    """Queries of h_q 5..2000 (up to 16 column tiles, several sub-batches per call, both
+    tile streams of the fused kernel busy with queries of very different lengths)."""
+    w = emd_synth.config(2, query_limit=1)
+    q = emd_synth.mixed_queries(80)
+    f, m = pair(emd, w, max_query_h=2048, batch_columns=8192)
+    try:
+        for K in (16, 5):
+            same_topk(emd, f, m, q, "act", 4, K)
+        emd.emd_db_check_device_errors(f)
+    finally:
+        emd.emd_db_destroy(f)
+        emd.emd_db_destroy(m)
+
+
+def test_fused_small_ragged(emd):
+    """Embedding width 37 (one 64-wide K chunk), query sizes 1..150 (one or two column
+    tiles with ragged tails), batches of 1..13 queries, every K up to 16."""
+    w = emd_synth.small_text(5150, 1500, 37, 900, 13, 1, 60, 1, 150)
+    f, m = pair(emd, w, max_query_h=256)
+    try:
+        for K in (1, 7, 16):
+            for nq in (1, 5, 13):
+                sub = w.queries.subset(np.arange(nq))
+                same_topk(emd, f, m, sub, "act", 3, K)
+        emd.emd_db_check_device_errors(f)
+    finally:
+        emd.emd_db_destroy(f)
+        emd.emd_db_destroy(m)
+
+
+def test_fused_candidate_row_overflow(emd):
+    """Twenty documents of 1000 distinct vocabulary rows each, all on a circle at the same
+    distance from the query's single bin: every document is a candidate and together they
+    hold 20000 distinct rows, more than the candidate block holds.  The query is reported
+    uncertified and recomputed over all documents; the answer equals the materialized form."""
+    V, per, ndoc = 20001, 1000, 20
+    t = np.arange(V - 1) * (2 * np.pi / (V - 1))
+    emb = np.zeros((V, 3), np.float32)
+    emb[:-1, 0] = 0.6 * np.cos(t)
+    emb[:-1, 1] = 0.6 * np.sin(t)
+    emb[:-1, 2] = 0.8
+    emb[-1] = (0.0, 0.0, 1.0)  # the query's bin
+    rp = np.arange(ndoc + 1, dtype=np.int64) * per
+    col = np.arange(ndoc * per, dtype=np.int32)
+    rng = np.random.default_rng(3)
+    val = rng.integers(1, 6, ndoc * per).astype(np.float64)
+    val = (val / np.repeat(np.add.reduceat(val, rp[:-1]), per)).astype(np.float32)
+    db_hist = emd_synth.Histograms(rp, col, val)
+    w = emd_synth.Workload("circle", V, 3, emb, None, db_hist, db_hist, (1,), 16)
+    q = emd_synth.Histograms(np.array([0, 1], np.int64), np.array([V - 1], np.int32), np.array([1.0], np.float32))
+    f, m = pair(emd, w, max_query_h=32)
+    try:
+        emd.emd_db_profile_reset(f)
+        same_topk(emd, f, m, q, "act", 2, 16)
+        prof = emd.emd_db_profile_get(f)
+        assert prof["prune_fallbacks"] == 1
+        emd.emd_db_check_device_errors(f)
+    finally:
+        emd.emd_db_destroy(f)
+        emd.emd_db_destroy(m)
