@@ -33,10 +33,17 @@ def pair(emd, w, **opt):
 
 
 def same_topk(emd, f, m, q, meas, k, K):
+    """Equal answers, and equal certificate decisions: the queries the fused form leaves
+    uncertified (recomputed over all documents) are those the materialized form does."""
+    emd.emd_db_profile_reset(f)
+    emd.emd_db_profile_reset(m)
     a = emd.emd_topk(f, q.row_ptr, q.col, q.val, meas, k, "max", K)
     b = emd.emd_topk(m, q.row_ptr, q.col, q.val, meas, k, "max", K)
     np.testing.assert_array_equal(a[0], b[0])
     np.testing.assert_array_equal(a[1], b[1])
+    pf, pm = emd.emd_db_profile_get(f), emd.emd_db_profile_get(m)
+    assert pf["pruned_queries"] == pm["pruned_queries"] == q.n
+    assert pf["prune_fallbacks"] == pm["prune_fallbacks"], (pf["prune_fallbacks"], pm["prune_fallbacks"])
     return a
 
 
@@ -51,10 +58,7 @@ def text():
 def test_fused_equals_materialized_text(emd, text, meas, k):
     f, m = pair(emd, text, max_query_h=1024)
     try:
-        emd.emd_db_profile_reset(f)
         same_topk(emd, f, m, text.queries, meas, k, 16)
-        prof = emd.emd_db_profile_get(f)
-        assert prof["pruned_queries"] == text.queries.n and prof["prune_fallbacks"] == 0
         emd.emd_db_check_device_errors(f)
     finally:
         emd.emd_db_destroy(f)
@@ -115,9 +119,13 @@ def test_fused_candidate_row_overflow(emd):
     f, m = pair(emd, w, max_query_h=32)
     try:
         emd.emd_db_profile_reset(f)
-        same_topk(emd, f, m, q, "act", 2, 16)
-        prof = emd.emd_db_profile_get(f)
-        assert prof["prune_fallbacks"] == 1
+        emd.emd_db_profile_reset(m)
+        a = emd.emd_topk(f, q.row_ptr, q.col, q.val, "act", 2, "max", 16)
+        b = emd.emd_topk(m, q.row_ptr, q.col, q.val, "act", 2, "max", 16)
+        np.testing.assert_array_equal(a[0], b[0])
+        np.testing.assert_array_equal(a[1], b[1])
+        assert emd.emd_db_profile_get(f)["prune_fallbacks"] == 1  # the block overflowed
+        assert emd.emd_db_profile_get(m)["prune_fallbacks"] == 0  # 20 candidates, certified
         emd.emd_db_check_device_errors(f)
     finally:
         emd.emd_db_destroy(f)
