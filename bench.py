@@ -622,6 +622,7 @@ def main_bench(args, rank, world, local):
     phases["profiled_ms_per_step"] = total_p / steps_prof
     phases["pruned_queries"] = prof["pruned_queries"]
     phases["prune_fallbacks"] = prof["prune_fallbacks"]
+    phases["fused_retries"] = prof["fused_retries"]
 
     # ---- the oracle subset: recall and distance error of every form
     recall = None
@@ -691,7 +692,7 @@ def main_bench(args, rank, world, local):
             "database": {"v_used": vu, "nnz": nnz, "n_docs": n, "mean_h_q_timed": sum_h / nq,
                          "generation_s": gen_s, "db_create_s": db_s,
                          "autotuned": {kk: info[kk] for kk in ("autotuned", "tc_group_mult", "tc_stages",
-                                                                "rev_warps")}},
+                                                                "rev_warps", "fwd_kernel")}},
         }
         print(json.dumps(line))
     if dist:
@@ -734,7 +735,8 @@ def main_probe(args, local):
 def main_k4(args, local):
     """The forward CSR pass (Phase 2+3) on a database much larger than L2: per query sweep
     8 nnz + 4 (n + 1) + 4 n algorithmic bytes, timed with the library's events over batches of
-    --batch queries (forward direction only, all documents), L2 flushed between batches."""
+    --batch queries (forward direction only, all documents), L2 flushed between batches, for
+    each form of the grouped sweep (fwd_kernel 1..3) and the autotuner's choice."""
     import torch
     import emd_synth
     import paper_1812_02091_gb300 as emd
@@ -748,10 +750,6 @@ def main_k4(args, local):
     # keep every batch in one sub-batch (one sweep per group of eight) and D small
     small = np.nonzero(np.diff(w.queries.row_ptr) <= 256)[0][:need]
     queries = w.queries.subset(small)
-    db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
-                           emd.emd_db_options_default(precision=args.precision, device=local, max_query_h=256,
-                                                      max_batch=B, batch_columns=B * 256))
-    info = emd.emd_db_info_get(db)
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     out = torch.empty((B, w.db.n), dtype=torch.float32, device="cuda")
@@ -759,30 +757,41 @@ def main_k4(args, local):
     for s in range(args.warmup + args.steps):
         sub = queries.subset(np.arange(s * B, (s + 1) * B))
         batches.append((sub.row_ptr, torch.from_numpy(sub.col).cuda(), torch.from_numpy(sub.val).cuda()))
-    for s in range(args.warmup):
-        emd.emd_query_batch_device(db, *batches[s], out, "act", args.k, "fwd", stream=stream.cuda_stream)
-    torch.cuda.synchronize()
-    emd.emd_db_profile_reset(db)
-    emd.emd_db_set_profiling(db, True)
-    for s in range(args.warmup, args.warmup + args.steps):
-        flush.fill_(float(s))
-        emd.emd_query_batch_device(db, *batches[s], out, "act", args.k, "fwd", stream=stream.cuda_stream)
-    torch.cuda.synchronize()
-    prof = emd.emd_db_profile_get(db)
-    emd.emd_db_destroy(db)
-    nnz, n = info["nnz"], info["n_docs"]
-    sweep = 8.0 * nnz + 4.0 * (n + 1) + 4.0 * n
-    t = prof["ms"]["fwd"] / 1e3
-    achieved = sweep * B * args.steps / t / 1e9
     pk = peaks()
-    print(json.dumps({"k4": "forward CSR pass (Eq. 6-9), LC-ACT k=%d" % args.k,
-                      "database": f"workload 5 cut to {n} documents: nnz {nnz}, CSR {sweep / 1e6:.0f} MB per sweep, "
-                                  f"v_used {info['v_used']}",
+    res = {}
+    ref = None
+    for fk in (0, 1, 2, 3):
+        db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
+                               emd.emd_db_options_default(precision=args.precision, device=local, max_query_h=256,
+                                                          max_batch=B, batch_columns=B * 256, fwd_kernel=fk))
+        info = emd.emd_db_info_get(db)
+        for s in range(args.warmup):
+            emd.emd_query_batch_device(db, *batches[s], out, "act", args.k, "fwd", stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        emd.emd_db_profile_reset(db)
+        emd.emd_db_set_profiling(db, True)
+        for s in range(args.warmup, args.warmup + args.steps):
+            flush.fill_(float(s))
+            emd.emd_query_batch_device(db, *batches[s], out, "act", args.k, "fwd", stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        prof = emd.emd_db_profile_get(db)
+        emd.emd_db_check_device_errors(db)
+        emd.emd_db_destroy(db)
+        got = out.cpu().numpy()
+        same = True if ref is None else bool(np.array_equal(got, ref))
+        ref = got if ref is None else ref
+        nnz, n = info["nnz"], info["n_docs"]
+        sweep = 8.0 * nnz + 4.0 * (n + 1) + 4.0 * n
+        t = prof["ms"]["fwd"] / 1e3
+        achieved = sweep * B * args.steps / t / 1e9
+        res["auto" if fk == 0 else f"fwd_kernel={fk}"] = {
+            "chosen": info["fwd_kernel"], "ms_per_batch": 1e3 * t / args.steps, "ms_per_query": 1e3 * t / (B * args.steps),
+            "achieved_gbs": achieved, "frac": achieved / pk["hbm_gbs"], "same_values_as_auto": same}
+    print(json.dumps({"k4": "forward CSR pass (Eq. 6-9), LC-ACT k=%d, per form of the grouped sweep" % args.k,
+                      "database": f"workload 5 cut to {n} documents: nnz {nnz}, CSR {sweep / 1e6:.0f} MB per sweep",
                       "queries": f"{B * args.steps} of workload 5's queries with h_q <= 256, batches of {B}",
-                      "launches": prof["launches"]["fwd"],
-                      "ms_per_query": 1e3 * t / (B * args.steps), "achieved_gbs": achieved,
-                      "peak_gbs": pk["hbm_gbs"], "frac": achieved / pk["hbm_gbs"],
-                      "peak_source": f"{pk['source']} HBM copy", "generation_s": gen_s}))
+                      "peak_gbs": pk["hbm_gbs"], "peak_source": f"{pk['source']} HBM copy",
+                      "forms": res, "generation_s": gen_s}))
 
 
 def main_ict(args, local):

@@ -108,6 +108,11 @@ typedef struct {
                                 documents' rows (exactly the entries the full matrix would hold),
                                 so no v_used x h_q matrix is written; 0: the full matrix and a
                                 separate table pass.  Results are bit-identical either way */
+    int32_t fwd_kernel;      /* form of the batched forward sweep (Phase 2+3 over the CSR for a
+                                group of eight queries): 0 (default) the autotuner's choice; 1 each
+                                table entry loaded when the residual mass needs it; 2 query-major
+                                table rows, four entries loaded up front; 3 the first two entries up
+                                front, column ids and weights read 32 at a time.  Same results */
 } emd_db_options;
 
 typedef struct {
@@ -120,6 +125,7 @@ typedef struct {
                                        (multiple of the load-balance minimum) */
     int32_t tc_stages;              /* its query-chunk stages (0: as many as fit) */
     int32_t rev_warps;              /* pruned reverse pass: warps per candidate document */
+    int32_t fwd_kernel;             /* the batched forward sweep's form (1..3, see emd_db_options) */
 } emd_db_info;
 
 /* A batch of query histograms in CSR form: query i has bins
@@ -146,6 +152,9 @@ typedef struct {
                                 included in the launch counts) */
     int64_t ict_wide;        /* ICT queries recomputed with tables of full width h because a
                                 vocabulary row needed more than max_table_k entries */
+    int64_t fused_retries;   /* pruned queries of the fused form whose candidate documents held
+                                more distinct rows than its exact distance block; each was run
+                                again with the full distance matrix (its answer is unchanged) */
 } emd_profile;
 
 /* Fill *opt with the defaults listed above.  Never fails. */

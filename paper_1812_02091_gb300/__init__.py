@@ -46,14 +46,14 @@ class emd_db_options(ctypes.Structure):
                 ("max_table_k", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("prune_topk", ctypes.c_int32), ("lanes", ctypes.c_int32), ("batched", ctypes.c_int32),
                 ("batch_columns", ctypes.c_int32), ("graphs", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("fused_phase1", ctypes.c_int32)]
+                ("fused_phase1", ctypes.c_int32), ("fwd_kernel", ctypes.c_int32)]
 
 
 class emd_db_info(ctypes.Structure):
     _fields_ = [("v", ctypes.c_int64), ("v_used", ctypes.c_int64), ("n_docs", ctypes.c_int64),
                 ("nnz", ctypes.c_int64), ("m", ctypes.c_int32), ("cost_matrix_mode", ctypes.c_int32),
                 ("device_bytes", ctypes.c_int64), ("autotuned", ctypes.c_int32), ("tc_group_mult", ctypes.c_int32),
-                ("tc_stages", ctypes.c_int32), ("rev_warps", ctypes.c_int32)]
+                ("tc_stages", ctypes.c_int32), ("rev_warps", ctypes.c_int32), ("fwd_kernel", ctypes.c_int32)]
 
 
 class emd_queries(ctypes.Structure):
@@ -65,7 +65,7 @@ class emd_profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 7), ("launches", ctypes.c_int64 * 7),
                 ("total_launches", ctypes.c_int64), ("pruned_queries", ctypes.c_int64),
                 ("prune_fallbacks", ctypes.c_int64), ("graph_launches", ctypes.c_int64),
-                ("ict_wide", ctypes.c_int64)]
+                ("ict_wide", ctypes.c_int64), ("fused_retries", ctypes.c_int64)]
 
 
 class emd_server_options(ctypes.Structure):
@@ -321,7 +321,7 @@ def emd_db_profile_get(db) -> dict:
     return {"ms": dict(zip(PHASES, list(p.ms))), "launches": dict(zip(PHASES, list(p.launches))),
             "total_launches": int(p.total_launches), "pruned_queries": int(p.pruned_queries),
             "prune_fallbacks": int(p.prune_fallbacks), "graph_launches": int(p.graph_launches),
-            "ict_wide": int(p.ict_wide)}
+            "ict_wide": int(p.ict_wide), "fused_retries": int(p.fused_retries)}
 
 
 def emd_db_profile_reset(db):

@@ -108,7 +108,11 @@ bool grouped_tables(const BatchWS& ws, int meas, int tk_b)
 
 // Row width of a query's table in the grouped, query-major layout (the forward kernel's
 // register width), or 0 for the entry-interleaved layout of wide ICT tables.
-int grouped_width(int meas, int tk_b) { return meas == M_ICT && tk_b > 16 ? 0 : fwd_reg_width(tk_b); }
+int grouped_width(const emd_db* db, int meas, int tk_b)
+{
+    if (db->tune_fwd != kFwdRowMajor || (meas == M_ICT && tk_b > 16)) return 0;
+    return fwd_reg_width(tk_b);
+}
 
 int topk_launch_count(int64_t n) { return topk_blocks(n) > 1 ? 2 : 1; }
 
@@ -321,7 +325,7 @@ emd_status run_lanes(emd_db* db, const int64_t* rp, const int32_t* qidx, const f
 // queries with these parameters and can be captured into a graph.  hd (host descriptors of
 // nb queries) only when Phase 1 must run per query.
 emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, int K, int dir, bool pruned, const QDesc* hd,
-                           int nb, int qcap, cudaStream_t st)
+                           int nb, int qcap, cudaStream_t st, bool allow_fused = true)
 {
     const int B = qcap;  // grids cover qcap queries (>= the batch's count)
     const QDesc* D_ = ws.qd_dev + (int64_t)slot * ws.max_batch;
@@ -330,7 +334,7 @@ emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, i
     const int H = db->opt.max_query_h;
     const int tk_b = dir != EMD_DIR_REV ? table_width(db, meas, k, H) : 0;
     const int kc_b = db->approx ? std::min(rerank_width(db, tk_b, H), kRerankMax) : tk_b;
-    if (pruned && ws.fused && !hd && meas != M_ICT && tk_b <= 16) {
+    if (pruned && allow_fused && ws.fused && !hd && meas != M_ICT && tk_b <= 16) {
         // fused form: the table from the product's epilogue; the reverse direction's distances
         // on the candidate documents' rows only
         {
@@ -351,7 +355,7 @@ emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, i
         {
             Phase p(db, 3, 1, st);
             EMD_CUDA(launch_fwd_b(meas, D_, nqd, B, db->row_ptr, db->col, db->val, n, false,
-                                  grouped_tables(ws, meas, tk_b), tk_b, st),
+                                  grouped_tables(ws, meas, tk_b), tk_b, st, db->tune_fwd),
                      "forward pass");
         }
         {
@@ -432,7 +436,7 @@ emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, i
         }
         Phase p(db, 3, 1, st);
         EMD_CUDA(launch_fwd_b(meas, D_, nqd, B, db->row_ptr, db->col, db->val, n, dir == EMD_DIR_FWD,
-                              grouped_tables(ws, meas, tk_b), tk_b, st),
+                              grouped_tables(ws, meas, tk_b), tk_b, st, db->tune_fwd),
                  "forward pass");
     }
     if (pruned) {
@@ -460,13 +464,13 @@ emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, i
 // Captures launch_sequence for these parameters into an executable graph (on the handle's
 // capture stream); the launch counts of one replay are kept beside it.
 emd_status capture_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, int K, int dir, bool pruned, int qcap,
-                            GraphEntry* g)
+                            GraphEntry* g, bool allow_fused)
 {
     int64_t l0[EMD_N_PHASES], t0 = db->total_launches;
     for (int p = 0; p < EMD_N_PHASES; ++p) l0[p] = db->launches[p];
     cudaStream_t cs = ws.cap_stream;
     EMD_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "graph capture");
-    emd_status s = launch_sequence(ws, db, slot, meas, k, K, dir, pruned, nullptr, 0, qcap, cs);
+    emd_status s = launch_sequence(ws, db, slot, meas, k, K, dir, pruned, nullptr, 0, qcap, cs, allow_fused);
     cudaGraph_t graph = nullptr;
     const cudaError_t e = cudaStreamEndCapture(cs, &graph);
     for (int p = 0; p < EMD_N_PHASES; ++p) {
@@ -591,7 +595,7 @@ emd_status fill_descriptors(BatchWS& ws, int slot, emd_db* db, const int64_t* rp
     const int nb = (int)(j1 - j0);
     const int tk_b = dir != EMD_DIR_REV ? table_width(db, meas, k, db->opt.max_query_h) : 0;
     const bool grouped = grouped_tables(ws, meas, tk_b);
-    const int lw_b = grouped_width(meas, tk_b);
+    const int lw_b = grouped_width(db, meas, tk_b);
     QDesc* hd = ws.qd_host + (int64_t)slot * ws.max_batch;
     QDesc* dd = ws.qd_dev + (int64_t)slot * ws.max_batch;
     int* nqd = ws.nq_dev + slot;
@@ -688,7 +692,7 @@ emd_status fill_descriptors(BatchWS& ws, int slot, emd_db* db, const int64_t* rp
 
 // Runs the sub-batch whose descriptors fill_descriptors put in `slot` (nb queries).
 emd_status run_subbatch_launch(BatchWS& ws, int slot, emd_db* db, int nb, int meas, int k, int dir, int K, bool pruned,
-                               cudaStream_t st)
+                               cudaStream_t st, bool allow_fused)
 {
     const QDesc* hd = ws.qd_host + (int64_t)slot * ws.max_batch;
     int qcap = 1;  // size class of the batch: the next power of two
@@ -698,19 +702,20 @@ emd_status run_subbatch_launch(BatchWS& ws, int slot, emd_db* db, int nb, int me
         // embeddings too wide for the batched panel: Phase 1 per query, the rest batched
         return launch_sequence(ws, db, slot, meas, k, K, dir, pruned, hd, nb, qcap, st);
     }
-    if (!db->opt.graphs || db->profiling) return launch_sequence(ws, db, slot, meas, k, K, dir, pruned, nullptr, 0, qcap, st);
-    const GraphKey key{meas, k, K, dir, pruned ? 1 : 0, slot, qcap};
+    if (!db->opt.graphs || db->profiling)
+        return launch_sequence(ws, db, slot, meas, k, K, dir, pruned, nullptr, 0, qcap, st, allow_fused);
+    const GraphKey key{meas, k, K, dir, pruned ? 1 : 0, slot, qcap, allow_fused ? 1 : 0};
     auto it = ws.graphs.find(key);
     if (it == ws.graphs.end()) {
         GraphEntry g;
-        emd_status cs = capture_sequence(ws, db, slot, meas, k, K, dir, pruned, qcap, &g);
+        emd_status cs = capture_sequence(ws, db, slot, meas, k, K, dir, pruned, qcap, &g, allow_fused);
         if (cs != EMD_OK) {
             g_err.clear();
             g.exec = nullptr;  // capture refused: this key launches directly from now on
         }
         it = ws.graphs.emplace(key, g).first;
     }
-    if (!it->second.exec) return launch_sequence(ws, db, slot, meas, k, K, dir, pruned, nullptr, 0, qcap, st);
+    if (!it->second.exec) return launch_sequence(ws, db, slot, meas, k, K, dir, pruned, nullptr, 0, qcap, st, allow_fused);
     EMD_CUDA(cudaGraphLaunch(it->second.exec, st), "graph launch");
     for (int p = 0; p < EMD_N_PHASES; ++p) db->launches[p] += it->second.launches[p];
     db->total_launches += it->second.total;
@@ -722,7 +727,7 @@ emd_status run_subbatch_launch(BatchWS& ws, int slot, emd_db* db, int nb, int me
 // descriptors) has finished, whatever stream it ran on.
 emd_status run_subbatch(emd_db* db, BatchWS& ws, const int64_t* rp, const int32_t* qidx, const float* qw, int64_t i0,
                         int64_t j0, int64_t j1, int meas, int k, int dir, int K, bool pruned, float* out_t,
-                        int64_t* out_idx, float* out_dist, cudaStream_t st)
+                        int64_t* out_idx, float* out_dist, cudaStream_t st, bool allow_fused)
 {
     const int slot = ws.desc_slot;
     ws.desc_slot = (slot + 1) % BatchWS::kDescRing;
@@ -731,9 +736,24 @@ emd_status run_subbatch(emd_db* db, BatchWS& ws, const int64_t* rp, const int32_
         EMD_CUDA(cudaMemsetAsync(ws.ict_over + (j0 - i0), 0, (j1 - j0) * sizeof(int), st), "flag reset");
     emd_status s = fill_descriptors(ws, slot, db, rp, qidx, qw, i0, j0, j1, meas, k, dir, K, pruned, out_t, out_idx,
                                     out_dist, st);
-    if (s == EMD_OK) s = run_subbatch_launch(ws, slot, db, (int)(j1 - j0), meas, k, dir, K, pruned, st);
+    if (s == EMD_OK) s = run_subbatch_launch(ws, slot, db, (int)(j1 - j0), meas, k, dir, K, pruned, st, allow_fused);
     EMD_CUDA(cudaEventRecord(ws.desc_ev[slot], st), "descriptor ring");
     return s;
+}
+
+emd_status retry_materialized(emd_db* db, BatchWS& ws, const int64_t* rp, const int32_t* qidx, const float* qw,
+                              int64_t i0, int64_t i, int meas, int k, int K, int64_t* out_idx, float* out_dist,
+                              cudaStream_t st, int* ok)
+{
+    const int64_t off = rp[i] - rp[i0];
+    // a sub-batch of its own: query i with offsets relative to itself, outputs at row i - i0
+    const int64_t rp1[2] = {0, rp[i + 1] - rp[i]};
+    emd_status s = run_subbatch(db, ws, rp1, qidx + off, qw + off, 0, 0, 1, meas, k, EMD_DIR_MAX, K, true, nullptr,
+                                out_idx + (i - i0) * K, out_dist + (i - i0) * K, st, false);
+    if (s != EMD_OK) return s;
+    EMD_CUDA(cudaMemcpyAsync(ok, ws.cand_ok, sizeof(int), cudaMemcpyDeviceToHost, st), "flag read");
+    EMD_CUDA(cudaStreamSynchronize(st), "synchronize");
+    return EMD_OK;
 }
 
 bool batch_fits(const emd_db* db, const BatchWS& ws, const int64_t* rp, int64_t i0, int64_t i1, int meas, int k,
@@ -752,7 +772,7 @@ bool batch_fits(const emd_db* db, const BatchWS& ws, const int64_t* rp, int64_t 
         cT += dir != EMD_DIR_REV ? table_width(db, meas, k, h) : 0;
     }
     if (grouped) {  // whole groups of kFwdGroup tables
-        const int lw = grouped_width(meas, tk_b);
+        const int lw = grouped_width(db, meas, tk_b);
         cT = (i1 - i0 + kFwdGroup - 1) / kFwdGroup * kFwdGroup * (lw ? lw : tk_b);
     }
     return cD <= ws.b_cols && cQ <= ws.b_qrows && cP <= ws.b_prows && cT <= ws.b_tabcols;
@@ -800,7 +820,13 @@ emd_status run_batch(emd_db* db, const int64_t* rp, const int32_t* qidx, const f
     EMD_CUDA(cudaStreamSynchronize(st), "synchronize");
     if (pruned) db->pruned_queries += i1 - i0;
     for (int64_t i = i0; i < i1; ++i) {
-        if (ok[i - i0] && !over[i - i0]) continue;
+        if (db->opt.batched && pruned && ok[i - i0] == 2) {  // the fused candidate block overflowed
+            ++db->fused_retries;
+            emd_status s = retry_materialized(db, db->bw, rp, qidx, qw, i0, i, meas, k, K, out_idx, out_dist, st,
+                                              &ok[i - i0]);
+            if (s != EMD_OK) return s;
+        }
+        if (ok[i - i0] == 1 && !over[i - i0]) continue;
         if (over[i - i0]) ++db->ict_wide; else ++db->prune_fallbacks;
         const int64_t off = rp[i] - rp[i0];
         const int h = (int)(rp[i + 1] - rp[i]);
@@ -996,6 +1022,31 @@ emd_status autotune(emd_db* db, const std::vector<int32_t>& used_host)
             }
         }
     }
+    if (db->opt.fwd_kernel == 0) {
+        // the grouped forward sweep: each variant with its own table layout (descriptors and
+        // tables rebuilt), timed on the same batch
+        float best = 1e30f;
+        int choice = kFwdChain;
+        for (int v : {kFwdChain, kFwdCoalesced, kFwdRowMajor}) {
+            db->tune_fwd = v;
+            s = fill_descriptors(ws, 0, db, rp.data(), db->stage_idx, db->stage_w, 0, 0, nb, EMD_ACT, k, EMD_DIR_MAX,
+                                 K, pruned, nullptr, db->stage_oidx, db->stage_odist, st);
+            if (s == EMD_OK)
+                s = launch_sequence(ws, db, 0, EMD_ACT, k, K, EMD_DIR_MAX, pruned, per_query_tc ? ws.qd_host : nullptr,
+                                    nb, ws.max_batch, st);
+            if (s != EMD_OK) return s;
+            const int tk = table_width(db, EMD_ACT, k, db->opt.max_query_h);
+            const float ms = timed([&] {
+                launch_fwd_b(EMD_ACT, D_, nqd, db->opt.max_batch, db->row_ptr, db->col, db->val, db->n, false,
+                             grouped_tables(ws, EMD_ACT, tk), tk, st, v);
+            });
+            if (ms < 0.95f * best) {
+                best = ms;
+                choice = v;
+            }
+        }
+        db->tune_fwd = choice;
+    }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     EMD_CUDA(cudaStreamSynchronize(st), "synchronize");
@@ -1026,6 +1077,7 @@ void emd_db_options_default(emd_db_options* opt)
     opt->graphs = 1;
     opt->autotune = 1;
     opt->fused_phase1 = 1;
+    opt->fwd_kernel = 0;
 }
 
 emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* cost_matrix,
@@ -1052,6 +1104,8 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
         opt.max_table_k > (1 << 16) || opt.max_batch < 1 || opt.max_batch > 4096 || opt.lanes < 1 ||
         opt.lanes > 16 || opt.batch_columns < 1)
         return fail(EMD_ERR_INVALID_ARG, "option out of range");
+    if (opt.fwd_kernel < 0 || opt.fwd_kernel > kFwdVariants)
+        return fail(EMD_ERR_INVALID_ARG, "fwd_kernel must be 0..%d", kFwdVariants);
     if ((opt.precision == EMD_PREC_BF16 || opt.precision == EMD_PREC_FP8_E4M3) && opt.max_query_h > 6400)
         return fail(EMD_ERR_INVALID_ARG, "max_query_h above 6400 with an approximate precision (the re-rank "
                                          "stages 32 bytes per query bin in shared memory)");
@@ -1098,6 +1152,7 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
     db->row_ptr_host.assign(row_ptr, row_ptr + n_docs + 1);
     db->opt = opt;
     db->dev = opt.device;
+    db->tune_fwd = opt.fwd_kernel > 0 ? opt.fwd_kernel - 1 : kFwdCoalesced;
     db->margin = opt.rerank_margin;
     db->v = v;
     db->v_used = (int64_t)used_ids.size();
@@ -1253,6 +1308,7 @@ emd_status emd_db_info_get(const emd_db* db, emd_db_info* out)
     out->tc_group_mult = db->tune_group_mult;
     out->tc_stages = db->tune_stages;
     out->rev_warps = db->tune_rev_warps;
+    out->fwd_kernel = db->tune_fwd + 1;
     return EMD_OK;
 }
 
@@ -1469,6 +1525,7 @@ emd_status emd_db_profile_get(emd_db* db, emd_profile* out)
     out->prune_fallbacks = db->prune_fallbacks;
     out->graph_launches = db->graph_launches;
     out->ict_wide = db->ict_wide;
+    out->fused_retries = db->fused_retries;
     return EMD_OK;
 }
 
@@ -1479,7 +1536,7 @@ emd_status emd_db_profile_reset(emd_db* db)
     emd_status s = collect_profile(db);
     if (s != EMD_OK) return s;
     for (int p = 0; p < EMD_N_PHASES; ++p) { db->ms[p] = 0.0; db->launches[p] = 0; }
-    db->pruned_queries = db->prune_fallbacks = db->graph_launches = db->ict_wide = 0;
+    db->pruned_queries = db->prune_fallbacks = db->graph_launches = db->ict_wide = db->fused_retries = 0;
     return EMD_OK;
 }
 

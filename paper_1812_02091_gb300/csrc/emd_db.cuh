@@ -51,8 +51,10 @@ namespace emd {
 // One captured batch sequence (launch_sequence) and the kernel launches it holds.
 struct GraphKey {
     int meas, k, K, dir, pruned, slot, qcap;  // qcap: queries the grids cover (power of two)
+    int fused;                                // fused pruned path allowed
     bool operator<(const GraphKey& o) const
     {
+        if (fused != o.fused) return fused < o.fused;
         if (meas != o.meas) return meas < o.meas;
         if (k != o.k) return k < o.k;
         if (K != o.K) return K < o.K;
@@ -185,12 +187,14 @@ struct emd_db {
     emd::BatchWS bw;
     int64_t graph_launches = 0;   // batch sequences replayed from graphs (all workspaces)
     int64_t ict_wide = 0;         // ICT queries recomputed with full-width tables
+    int64_t fused_retries = 0;    // pruned queries rerun with the full matrix (candidate block overflow)
 
     // free parameters of the batched kernels (autotune at creation)
     bool autotuned = false;
     int tune_group_mult = 1;   // query groups per vocabulary tile, times the balance minimum
     int tune_stages = 0;       // B stages of the batched tensor-core kernel (0: as many as fit)
     int tune_rev_warps = 4;    // warps per candidate document in the pruned reverse pass
+    int tune_fwd = 2;          // form of the grouped forward sweep (kFwdChain / kFwdRowMajor / kFwdCoalesced)
     std::map<emd::GraphKey, emd::GraphEntry> graphs;
 
     // Section 6 baselines (allocated and prepared at first use)
@@ -276,7 +280,12 @@ void free_batch_ws(BatchWS& ws);
 // i0; certification flags in ws.cand_ok[i - i0] on the pruned path.  Caller holds db->mu.
 emd_status run_subbatch(emd_db* db, BatchWS& ws, const int64_t* rp, const int32_t* qidx, const float* qw,
                         int64_t i0, int64_t j0, int64_t j1, int meas, int k, int dir, int K, bool pruned,
-                        float* out_t, int64_t* out_idx, float* out_dist, cudaStream_t st);
+                        float* out_t, int64_t* out_idx, float* out_dist, cudaStream_t st, bool allow_fused = true);
+// Pruned query i (of the batch starting at i0) whose fused candidate block overflowed: run
+// again alone on ws with the full distance matrix; *ok receives its new certification flag.
+emd_status retry_materialized(emd_db* db, BatchWS& ws, const int64_t* rp, const int32_t* qidx, const float* qw,
+                              int64_t i0, int64_t i, int meas, int k, int K, int64_t* out_idx, float* out_dist,
+                              cudaStream_t st, int* ok);
 // Whether the batch (rp entries i0..i1) fits one sub-batch of ws.
 bool batch_fits(const emd_db* db, const BatchWS& ws, const int64_t* rp, int64_t i0, int64_t i1, int meas, int k,
                 int dir);

@@ -210,7 +210,7 @@ struct QDesc {
 // Largest number of distinct used rows among the candidate documents of one query in the
 // fused pruned path (their distance block is computed exactly; beyond it the query is
 // recomputed over all documents with the full distance matrix).
-constexpr int kCandRows = 16384;
+constexpr int kCandRows = 32768;
 
 // Queries whose forward pass shares one sweep of the CSR (batched form).  Tables of width
 // <= 16 are stored query-major within a row -- row u, query g, entry l at
@@ -282,10 +282,16 @@ cudaError_t launch_table_b(const QDesc* qd, const int* nq, int max_q, int64_t M,
 cudaError_t launch_table_ict_b(const QDesc* qd, const int* nq, int max_q, int64_t M, const float* xmax,
                                cudaStream_t st);
 // Forward values into t_out (to_out) or t_fwd.  grouped: the tables are interleaved in
-// groups of kFwdGroup queries and each group shares one sweep of the CSR.
+// groups of kFwdGroup queries and each group shares one sweep of the CSR.  variant: the form
+// of the grouped sweep (same values for each; the grouped table layout follows it, see
+// fwd_layout_rowmajor):
+//   kFwdChain     entry-interleaved rows, each entry loaded once the residual needs it
+//   kFwdRowMajor  query-major rows, the first four entries loaded up front (vector loads)
+//   kFwdCoalesced entry-interleaved rows, the first two entries up front, coalesced CSR reads
+enum : int { kFwdChain = 0, kFwdRowMajor = 1, kFwdCoalesced = 2, kFwdVariants = 3 };
 cudaError_t launch_fwd_b(int meas, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
                          const int32_t* col, const float* val, int64_t n, bool to_out, bool grouped, int max_tk,
-                         cudaStream_t st);
+                         cudaStream_t st, int variant);
 // Reverse pass over all documents; dir FWD is not accepted, REV writes t_out, MAX writes
 // t_rev and max(t_fwd, t_rev) into t_out.
 cudaError_t launch_rev_b(int meas, int k, int dir, const QDesc* qd, const int* nq, int max_q,

@@ -216,8 +216,27 @@ emd_status run_fallbacks(emd_server* s, Exec& e, int* count)
     if (!e.pruned && !ict) return EMD_OK;
     for (size_t i = 0; i < e.batch.size(); ++i) {
         const bool over = ict && e.h_over[i];
-        if (!over && (!e.pruned || e.h_ok[i])) continue;
         const Request* r = e.batch[i];
+        if (!over && e.pruned && e.h_ok[i] == 2) {  // the fused candidate block overflowed
+            {
+                std::lock_guard<std::mutex> lock(db->mu);
+                ++db->fused_retries;
+                emd_status st = retry_materialized(db, e.ws, e.h_rp, e.d_idx, e.d_w, 0, (int64_t)i, r->meas, r->k,
+                                                   r->K, e.d_oidx, e.d_odist, e.st, &e.h_ok[i]);
+                if (st != EMD_OK) return st;
+            }
+            if (e.h_ok[i] == 1) {
+                EMD_CUDA(cudaMemcpyAsync(e.h_oidx + i * r->K, e.d_oidx + i * r->K, (size_t)r->K * 8,
+                                         cudaMemcpyDeviceToHost, e.st),
+                         "result copy");
+                EMD_CUDA(cudaMemcpyAsync(e.h_odist + i * r->K, e.d_odist + i * r->K, (size_t)r->K * 4,
+                                         cudaMemcpyDeviceToHost, e.st),
+                         "result copy");
+                EMD_CUDA(cudaStreamSynchronize(e.st), "synchronize");
+                continue;
+            }
+        }
+        if (!over && (!e.pruned || e.h_ok[i] == 1)) continue;
         const int64_t off = e.h_rp[i];
         {
             std::lock_guard<std::mutex> lock(db->mu);

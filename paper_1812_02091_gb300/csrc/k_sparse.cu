@@ -742,7 +742,9 @@ __device__ __forceinline__ void prune_select_body(const int64_t* __restrict__ ca
     }
     if (i < c && r == K - 1) kth = __uint_as_float((unsigned)(me >> 32));
     __syncthreads();
-    if (i == 0) *ok = (complete && *count <= cap && c >= K && kth <= prune_theta(sel_val[K - 1])) ? 1 : 0;
+    // 1: certified; 0: not certified (recompute over all documents); 2: the candidate
+    // block of the fused path overflowed (retry with the full distance matrix)
+    if (i == 0) *ok = !complete ? 2 : (*count <= cap && c >= K && kth <= prune_theta(sel_val[K - 1])) ? 1 : 0;
 }
 
 __global__ void k_prune_select(const int64_t* __restrict__ cand, const float* __restrict__ sym,
@@ -829,19 +831,18 @@ __global__ void k_fwd_g(const QDesc* __restrict__ qd, const int* __restrict__ nq
     }
 }
 
-// Cost of one nonzero from table entries already in registers (the first min(KT, 4) of its
-// row; entries 4.. of wider rows are loaded here, only while mass remains).  The same
+// Cost of one nonzero from the first KR entries of its table row already in registers
+// (entries KR.. are loaded here, only while mass remains; entry l at T[l * es]).  The same
 // operations in the same order as fwd_cost_p, so the values are bit-identical.
-template <int MEAS, int KT>
-__device__ __forceinline__ float fwd_cost_reg(float x, const float2 (&E)[KT < 4 ? KT : 4],
-                                              const float2* __restrict__ T, int keff)
+template <int MEAS, int KT, int KR>
+__device__ __forceinline__ float fwd_cost_reg(float x, const float2 (&E)[KR], const float2* __restrict__ T, int es,
+                                              int keff)
 {
-    constexpr int KR = KT < 4 ? KT : 4;
     if (MEAS == M_RWMD) return __fmul_rn(x, E[0].x);
     if (MEAS == M_OMR) {
         if (E[0].x == 0.f && keff >= 2) {
             const float r = x - fminf(x, E[0].y);
-            return r != 0.f ? __fmul_rn(r, E[KR > 1 ? 1 : 0].x) : 0.f;
+            return r != 0.f ? __fmul_rn(r, (KR > 1 ? E[KR > 1 ? 1 : 0] : T[es]).x) : 0.f;
         }
         return __fmul_rn(x, E[0].x);
     }
@@ -849,7 +850,7 @@ __device__ __forceinline__ float fwd_cost_reg(float x, const float2 (&E)[KT < 4 
 #pragma unroll
     for (int l = 0; l < (KT > 1 ? KT - 1 : 0); ++l) {
         if (l < keff - 1 && r != 0.f) {
-            const float2 t = l < KR ? E[l < KR ? l : 0] : T[l];
+            const float2 t = l < KR ? E[l < KR ? l : 0] : T[l * es];
             const float tau = fminf(r, t.y);
             c = fmaf(tau, t.x, c);
             r -= tau;
@@ -863,7 +864,7 @@ __device__ __forceinline__ float fwd_cost_reg(float x, const float2 (&E)[KT < 4 
 #pragma unroll
         for (int l = 1; l < KR; ++l) zl = lk == l ? E[l].x : zl;
     } else {
-        zl = T[lk].x;
+        zl = T[lk * es].x;
     }
     return fmaf(r, zl, c);
 }
@@ -932,7 +933,64 @@ k_fwd_gv(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t
                 }
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
-                    if (ok[i]) acc = __fadd_rn(acc, fwd_cost_reg<MEAS, KT>(xs[i], E[i], tq + (int64_t)us[i] * rs, kq));
+                    if (ok[i]) acc = __fadd_rn(acc, fwd_cost_reg<MEAS, KT, KR>(xs[i], E[i], tq + (int64_t)us[i] * rs, 1, kq));
+            }
+        }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+        if (ph == 0 && act) oq[d] = acc;
+    }
+}
+
+// Forward pass of a group of kFwdGroup queries, entry-interleaved tables (row u, entry l,
+// query g at tab[u * tab_rs + l * kFwdGroup], so the group's entry l of a row is 64
+// contiguous bytes): the column ids and weights of 32 nonzeros are read with one coalesced
+// load and handed out by shuffles as in k_fwd_gv; the first two entries of each row are
+// loaded before any arithmetic, later ones only while mass remains.  Fewer registers than
+// k_fwd_gv (more resident warps), fewer bytes per nonzero.  Same values as every other form.
+template <int MEAS, int KT>
+__global__ void __launch_bounds__(256, 4)
+k_fwd_gc(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t* __restrict__ row_ptr,
+         const int32_t* __restrict__ col, const float* __restrict__ val, int64_t n, bool to_out)
+{
+    constexpr int KR = KT < 2 ? KT : 2;
+    const int q0 = blockIdx.y * kFwdGroup;
+    const int nqv = *nq;
+    if (q0 >= nqv) return;
+    const int lane = threadIdx.x & 31, g = lane & 7, ph = lane >> 3;
+    const bool act = q0 + g < nqv;
+    const QDesc& dq = qd[act ? q0 + g : q0];
+    const float2* tq = dq.tab;
+    const int kq = dq.tk;
+    float* oq = to_out ? dq.t_out : dq.t_fwd;
+    const int rs = dq.tab_rs, es = dq.tab_es;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t d = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); d < n; d += warps) {
+        const int32_t a = row_ptr[d], b = row_ptr[d + 1];
+        float acc = 0.f;
+        for (int32_t eb = a; eb < b; eb += 32) {
+            const bool lin = eb + lane < b;
+            const int32_t cu = lin ? col[eb + lane] : 0;
+            const float cx = lin ? val[eb + lane] : 0.f;
+#pragma unroll
+            for (int r = 0; r < 8; r += 4) {  // four nonzeros per lane in flight
+                float2 E[4][KR];
+                float xs[4];
+                int32_t us[4];
+                bool ok[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int src = 4 * (r + i) + ph;
+                    us[i] = __shfl_sync(0xffffffffu, cu, src);
+                    xs[i] = __shfl_sync(0xffffffffu, cx, src);
+                    ok[i] = act && eb + src < b;
+                    const float2* T = tq + (int64_t)us[i] * rs;
+#pragma unroll
+                    for (int l = 0; l < KR; ++l) E[i][l] = ok[i] ? T[l * es] : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (ok[i]) acc = __fadd_rn(acc, fwd_cost_reg<MEAS, KT, KR>(xs[i], E[i], tq + (int64_t)us[i] * rs, es, kq));
             }
         }
         acc += __shfl_xor_sync(0xffffffffu, acc, 8);
@@ -1200,7 +1258,7 @@ cudaError_t launch_prune(int meas, int k, const int32_t* row_ptr, const int32_t*
 
 cudaError_t launch_fwd_b(int meas, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
                          const int32_t* col, const float* val, int64_t n, bool to_out, bool grouped, int max_tk,
-                         cudaStream_t st)
+                         cudaStream_t st, int variant)
 {
     const int kt = fwd_kt(max_tk);
     if (max_q <= 0 || n <= 0) return cudaSuccess;
@@ -1208,24 +1266,41 @@ cudaError_t launch_fwd_b(int meas, const QDesc* qd, const int* nq, int max_q, co
     const int64_t blocks = std::min<int64_t>((n + warps - 1) / warps, 152 * 64);
     if (grouped) {  // one document per warp, eight queries
         dim3 gg((unsigned)std::max<int64_t>(1, blocks), (unsigned)((max_q + kFwdGroup - 1) / kFwdGroup));
-        switch (meas) {
-        case M_RWMD: k_fwd_gv<M_RWMD, 1><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
-        case M_OMR: k_fwd_gv<M_OMR, 2><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
-        case M_ICT: k_fwd_g<M_ACT, 0><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
-        default: {
-#define EMD_L(KT) k_fwd_gv<M_ACT, KT><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out)
-            switch (kt) {
-            case 1: EMD_L(1); break;
-            case 2: EMD_L(2); break;
-            case 4: EMD_L(4); break;
-            case 8: EMD_L(8); break;
-            case 16: EMD_L(16); break;
-            default: k_fwd_g<M_ACT, 0><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
-            }
+        const int m = meas == M_ICT ? M_ACT : meas;  // ICT tables: the ACT steps over the written entries
+        const int kw = meas == M_RWMD ? 1 : meas == M_OMR ? 2 : (meas == M_ICT && kt == 0 ? 0 : kt);
+        if (kw == 0 || variant == kFwdChain) {  // entry-interleaved rows, loads while mass remains
+            switch (m) {
+            case M_RWMD: k_fwd_g<M_RWMD, 0><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
+            case M_OMR: k_fwd_g<M_OMR, 0><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
+            default: {
+#define EMD_L(KT) k_fwd_g<M_ACT, KT><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out)
+                EMD_FWD_KT_SWITCH(kw, EMD_L)
 #undef EMD_L
-            break;
+                break;
+            }
+            }
+            return cudaGetLastError();
         }
+#define EMD_GV(M, KT)                                                                                       \
+    do {                                                                                                    \
+        if (variant == kFwdRowMajor)                                                                        \
+            k_fwd_gv<M, KT><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out);               \
+        else                                                                                                \
+            k_fwd_gc<M, KT><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out);               \
+    } while (0)
+        switch (m) {
+        case M_RWMD: EMD_GV(M_RWMD, 1); break;
+        case M_OMR: EMD_GV(M_OMR, 2); break;
+        default:
+            switch (kw) {
+            case 1: EMD_GV(M_ACT, 1); break;
+            case 2: EMD_GV(M_ACT, 2); break;
+            case 4: EMD_GV(M_ACT, 4); break;
+            case 8: EMD_GV(M_ACT, 8); break;
+            default: EMD_GV(M_ACT, 16); break;
+            }
         }
+#undef EMD_GV
         return cudaGetLastError();
     }
     const int64_t qblocks = std::min<int64_t>((n + 8 * warps - 1) / (8 * warps), 152 * 64);  // eight documents per warp

@@ -130,3 +130,27 @@ def test_fused_candidate_row_overflow(emd):
     finally:
         emd.emd_db_destroy(f)
         emd.emd_db_destroy(m)
+
+
+def test_forward_sweep_forms_bit_identical(emd):
+    """The three forms of the grouped forward sweep (fwd_kernel 1..3; their table layouts
+    differ) give the same forward values and the same pruned top-K, bit for bit."""
+    w = emd_synth.small_text(6161, 2500, 48, 1500, 19, 2, 200, 1, 300)
+    q = w.queries
+    outs = []
+    for fk in (1, 2, 3):
+        db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
+                               emd.emd_db_options_default(precision="fp32_tc", max_query_h=512, autotune=0,
+                                                          fwd_kernel=fk), v=w.v)
+        try:
+            assert emd.emd_db_info_get(db)["fwd_kernel"] == fk
+            res = []
+            for meas, k in (("act", 4), ("act", 16), ("act", 7), ("omr", 1), ("rwmd", 1)):
+                res.append(emd.emd_query_batch(db, q.row_ptr, q.col, q.val, meas, k, "fwd"))
+                res.extend(emd.emd_topk(db, q.row_ptr, q.col, q.val, meas, k, "max", 16))
+            outs.append(res)
+        finally:
+            emd.emd_db_destroy(db)
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            np.testing.assert_array_equal(a, b)
