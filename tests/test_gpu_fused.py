@@ -97,11 +97,14 @@ def test_fused_small_ragged(emd):
 
 
 def test_fused_candidate_row_overflow(emd):
-    """Twenty documents of 1000 distinct vocabulary rows each, all on a circle at the same
+    """Forty documents of 1000 distinct vocabulary rows each, all on a circle at the same
     distance from the query's single bin: every document is a candidate and together they
-    hold 20000 distinct rows, more than the candidate block holds.  The query is reported
-    uncertified and recomputed over all documents; the answer equals the materialized form."""
-    V, per, ndoc = 20001, 1000, 20
+    hold 40000 distinct rows, more than the candidate block holds (kCandRows = 32768).  The
+    query is rerun with the full distance matrix (a retry, not a recompute over all
+    documents: the forty candidates certify there) and the answer equals the materialized
+    form's."""
+    per, ndoc = 1000, 40
+    V = per * ndoc + 1
     t = np.arange(V - 1) * (2 * np.pi / (V - 1))
     emb = np.zeros((V, 3), np.float32)
     emb[:-1, 0] = 0.6 * np.cos(t)
@@ -124,8 +127,9 @@ def test_fused_candidate_row_overflow(emd):
         b = emd.emd_topk(m, q.row_ptr, q.col, q.val, "act", 2, "max", 16)
         np.testing.assert_array_equal(a[0], b[0])
         np.testing.assert_array_equal(a[1], b[1])
-        assert emd.emd_db_profile_get(f)["prune_fallbacks"] == 1  # the block overflowed
-        assert emd.emd_db_profile_get(m)["prune_fallbacks"] == 0  # 20 candidates, certified
+        pf, pm = emd.emd_db_profile_get(f), emd.emd_db_profile_get(m)
+        assert pf["fused_retries"] == 1 and pf["prune_fallbacks"] == 0  # the block overflowed, the retry certified
+        assert pm["fused_retries"] == 0 and pm["prune_fallbacks"] == 0
         emd.emd_db_check_device_errors(f)
     finally:
         emd.emd_db_destroy(f)
