@@ -334,23 +334,43 @@ emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, i
     const int H = db->opt.max_query_h;
     const int tk_b = dir != EMD_DIR_REV ? table_width(db, meas, k, H) : 0;
     const int kc_b = db->approx ? std::min(rerank_width(db, tk_b, H), kRerankMax) : tk_b;
-    if (pruned && allow_fused && ws.fused && !hd && meas != M_ICT && tk_b <= 16) {
-        // fused form: the table from the product's epilogue; the reverse direction's distances
-        // on the candidate documents' rows only
+    if (pruned && allow_fused && ws.fused && !hd && meas != M_ICT && tk_b <= 16 &&
+        (!db->approx || kc_b <= kCandPerRow)) {
+        // fused form: the table from the product's epilogue (approximate formats: candidates
+        // re-ranked exactly); the reverse direction's distances on the candidate documents' rows
+        // only, exact in the FP16 split
         {
-            Phase p(db, 0, 2, st);
+            Phase p(db, 0, db->approx ? 3 : 2, st);
+            const int prow = (int)round_up(H, 128);
             EMD_CUDA(launch_gather_rows_b(D_, nqd, B, db->qrows_max, db->emb, db->v, db->ldm, db->m, db->err, st),
                      "query gather");
-            EMD_CUDA(launch_pack_b(db->tcfmt, D_, nqd, B, (int)round_up(H, 128), db->ldm, db->m, db->kpad, st),
-                     "query pack");
+            EMD_CUDA(launch_pack_b(db->tcfmt, D_, nqd, B, prow, db->ldm, db->m, db->kpad, st), "query pack");
+            if (db->approx)
+                EMD_CUDA(launch_pack_b(TC_SPLIT, D_, nqd, B, prow, db->ldm, db->m, db->kpad, st, true),
+                         "query pack (split)");
         }
         {
             Phase p(db, 1, 2, st);
             EMD_CUDA(launch_qpos_b(D_, nqd, B, db->vslot, db->v, true, st), "identical ids");
             EMD_CUDA(launch_tc_table_batch(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
-                                           db->v_used, D_, nqd, B, db->kpad, tk_b, db->tune_group_mult,
-                                           db->tune_stages, db->err, st),
-                     "Phase-1 table (tensor cores, fused)");
+                                           db->v_used, D_, nqd, B, db->kpad, db->approx ? kc_b : tk_b,
+                                           db->tune_group_mult, db->tune_stages, db->err, st),
+                     db->approx ? "Phase-1 candidates (tensor cores, fused)" : "Phase-1 table (tensor cores, fused)");
+        }
+        if (db->approx) {
+            // BF16: certified rows exact by construction; E4M3's rounding bound is too wide for a
+            // certificate, its tables are the re-ranked candidates (R15)
+            const bool certify = db->tcfmt == TC_BF16;
+            const double u = 1.0 / 256.0;
+            const float eps_rel = (float)(2.0 * (2.0 * u + u * u + 4e-5) * (1.0 + 1.0 / 1024.0));
+            const float eps_abs = (float)(8.0 / 16777216.0);
+            EMD_CUDA(cudaMemsetAsync(ws.brr_count, 0, sizeof(int) * B, st), "re-rank rows");
+            Phase p(db, 2, certify ? 2 : 1, st);
+            EMD_CUDA(launch_rerank_cand_b(D_, nqd, B, db->v_used, H, db->emb_used, db->ldm, db->norm_used, certify,
+                                          eps_rel, eps_abs, st),
+                     "top-k table (re-ranked candidates)");
+            if (certify)
+                EMD_CUDA(launch_rerank_full_b(D_, nqd, B, tk_b, db->emb_used, db->ldm, st), "top-k table (full rows)");
         }
         {
             Phase p(db, 3, 1, st);
@@ -371,7 +391,7 @@ emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, i
         {
             Phase p(db, 1, 3, st);
             EMD_CUDA(launch_cand_rows_b(D_, nqd, B, db->row_ptr, db->col, false, st), "candidate rows");
-            EMD_CUDA(launch_cand_pack_b(D_, nqd, B, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
+            EMD_CUDA(launch_cand_pack_b(D_, nqd, B, db->as_hi, db->as_lo, db->mpad, db->as_scale, db->norm_used,
                                         db->kpad, st),
                      "candidate panels");
             EMD_CUDA(launch_tc_cand_batch(D_, nqd, B, db->kpad, db->tune_stages, db->err, st),
@@ -546,8 +566,8 @@ emd_status alloc_batch_ws(emd_db* db, BatchWS& ws, int max_batch, int64_t cols, 
     TRYW(dal(&ws.topk_scratch, B * kTopkScratchRow));
     TRYW(dal(&ws.qd_dev, BatchWS::kDescRing * B));
     TRYW(dal(&ws.nq_dev, BatchWS::kDescRing));
-    ws.fused = db->tc && db->tcfmt == TC_SPLIT && !db->cost_mode && db->opt.fused_phase1 != 0 &&
-               tc_batch_stages(db->tcfmt, db->kpad / 64) >= 2;
+    ws.fused = db->tc && !db->cost_mode && db->opt.fused_phase1 != 0 && db->as_hi != nullptr &&
+               tc_batch_stages(db->tcfmt, db->kpad / 64) >= 2 && tc_batch_stages(TC_SPLIT, db->kpad / 64) >= 2;
     if (ws.fused) {
         TRYW(dal(&ws.bqpos, B * vu));
         TRYW(dal(&ws.brmap, B * vu));
@@ -558,6 +578,15 @@ emd_status alloc_batch_ws(emd_db* db, BatchWS& ws, int max_batch, int64_t cols, 
         TRYW(dal(&ws.bc_scale, B * kCandRows));
         TRYW(dal(&ws.bc_norm, B * kCandRows));
         TRYW(dal(&ws.bDc, (int64_t)kCandRows * ws.b_cols));
+        if (db->approx) {
+            TRYW(dal(&ws.bqs_hi, ws.b_prows * db->kpad));
+            TRYW(dal(&ws.bqs_lo, ws.b_prows * db->kpad));
+            TRYW(dal(&ws.bqs_scale, ws.b_prows));
+            TRYW(dal(&ws.bcb, B * vu * kCandPerRow));
+            TRYW(dal(&ws.bcmax, B * vu));
+            TRYW(dal(&ws.brr, B * vu));
+            TRYW(dal(&ws.brr_count, B));
+        }
         // the row maps start (and every batch leaves them) at -1
         EMD_CUDA(cudaMemset(ws.bqpos, 0xff, sizeof(int32_t) * B * vu), "memset");
         EMD_CUDA(cudaMemset(ws.brmap, 0xff, sizeof(int32_t) * B * vu), "memset");
@@ -663,6 +692,19 @@ emd_status fill_descriptors(BatchWS& ws, int slot, emd_db* db, const int64_t* rp
             d.c_scale = ws.bc_scale + bs * kCandRows;
             d.c_norm = ws.bc_norm + bs * kCandRows;
             d.Dc = ws.bDc + c_D * kCandRows;
+            if (db->approx) {
+                d.qs_hi = ws.bqs_hi + c_P * db->kpad;
+                d.qs_lo = ws.bqs_lo + c_P * db->kpad;
+                d.qs_scale = ws.bqs_scale + c_P;
+                d.cbin = ws.bcb + bs * db->v_used * kCandPerRow;
+                d.camax = ws.bcmax + bs * db->v_used;
+                d.rr = ws.brr + bs * db->v_used;
+                d.rr_count = ws.brr_count + bs;
+            } else {
+                d.qs_hi = d.q_hi;
+                d.qs_lo = d.q_lo;
+                d.qs_scale = d.q_scale;
+            }
         }
         d.sq = db->cost_mode ? 0 : 1;
         if (K > 0) {
@@ -1241,6 +1283,20 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
                  "embedding pack");
             db->total_launches += 1;
             db->launches[6] += 1;
+            if (db->approx && opt.batched && opt.fused_phase1) {
+                TRY(dalloc(db, &db->as_hi, db->mpad * db->kpad));
+                TRY(dalloc(db, &db->as_lo, db->mpad * db->kpad));
+                TRY(dalloc(db, &db->as_scale, db->mpad));
+                TRYC(launch_pack(TC_SPLIT, db->emb_used, ldm, m, vu, db->mpad, db->kpad, db->as_hi, db->as_lo,
+                                 db->as_scale, st),
+                     "embedding pack (split)");
+                db->total_launches += 1;
+                db->launches[6] += 1;
+            } else if (!db->approx) {
+                db->as_hi = db->a_hi;
+                db->as_lo = db->a_lo;
+                db->as_scale = db->a_scale;
+            }
         }
     }
 

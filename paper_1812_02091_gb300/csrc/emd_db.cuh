@@ -109,6 +109,13 @@ struct BatchWS {
     float* bc_scale = nullptr;    // max_batch x kCandRows
     float* bc_norm = nullptr;
     float* bDc = nullptr;         // kCandRows x b_cols
+    __half* bqs_hi = nullptr;     // split query panels (BF16 / E4M3 databases), b_prows x kpad
+    __half* bqs_lo = nullptr;
+    float* bqs_scale = nullptr;
+    int32_t* bcb = nullptr;       // max_batch x v_used x kCandPerRow candidate bins
+    float* bcmax = nullptr;       // max_batch x v_used
+    int32_t* brr = nullptr;       // max_batch x v_used uncertified rows
+    int* brr_count = nullptr;     // max_batch
     QDesc* qd_dev = nullptr;      // kDescRing x max_batch descriptors
     int* nq_dev = nullptr;        // kDescRing counts
     QDesc* qd_host = nullptr;     // pinned mirror of the ring
@@ -151,6 +158,11 @@ struct emd_db {
     __half* a_hi = nullptr;      // mpad x kpad packed panels (2-byte elements; E4M3 uses half the bytes)
     __half* a_lo = nullptr;      // TC_SPLIT only
     float* a_scale = nullptr;    // mpad
+    // FP16-split panels of the used vocabulary for the fused path's exact candidate block: the
+    // panels above for FP32_TC, a copy in the split format for BF16 / E4M3 databases
+    __half* as_hi = nullptr;
+    __half* as_lo = nullptr;
+    float* as_scale = nullptr;
 
     // per-lane workspace
     int ldd_max = 0, qrows_max = 0;

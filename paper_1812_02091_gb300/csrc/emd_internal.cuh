@@ -205,7 +205,22 @@ struct QDesc {
     float* c_scale;         // kCandRows scales and squared norms
     float* c_norm;
     float* Dc;              // kCandRows x ldd squared distances of those rows to the query's bins
+    // FP16-split query panels for the candidate block (the query panels above when the
+    // database's format is the split; separate ones for BF16 / E4M3 databases)
+    void* qs_hi;
+    void* qs_lo;
+    float* qs_scale;
+    // fused approximate formats: per used row the kc candidate bins of the product's epilogue
+    // (kCandPerRow apart) and the kc-th approximate squared distance; rows the re-rank cannot
+    // certify (rr, count rr_count) are recomputed exactly over all bins
+    int32_t* cbin;
+    float* camax;
+    int32_t* rr;
+    int* rr_count;
 };
+
+// Candidate bins kept per vocabulary row by the fused approximate forms (k + margin <= 16).
+constexpr int kCandPerRow = 16;
 
 // Largest number of distinct used rows among the candidate documents of one query in the
 // fused pruned path (their distance block is computed exactly; beyond it the query is
@@ -226,7 +241,7 @@ __host__ __device__ inline int fwd_reg_width(int kw)
 cudaError_t launch_gather_rows_b(const QDesc* qd, const int* nq, int max_q, int max_rows, const float* src,
                                  int64_t v, int ld, int m, int* err, cudaStream_t st);
 cudaError_t launch_pack_b(int fmt, const QDesc* qd, const int* nq, int max_q, int max_rows, int ld, int m,
-                          int Kpad, cudaStream_t st);
+                          int Kpad, cudaStream_t st, bool to_split = false);
 cudaError_t launch_dist_fp32_b(const QDesc* qd, const int* nq, int max_q, int max_ldd, const float* A, int64_t M,
                                int lda, const float* anorm, const int32_t* a_ids, int K, cudaStream_t st);
 cudaError_t launch_dist_gather_b(const QDesc* qd, const int* nq, int max_q, const float* cost, int64_t v,
@@ -271,6 +286,17 @@ cudaError_t launch_cand_pack_b(const QDesc* qd, const int* nq, int max_q, const 
 // Their squared distances to the query's bins (qd[q].Dc, ldd columns), exact zeros of
 // identical ids from qd[q].qpos.
 cudaError_t launch_tc_cand_batch(const QDesc* qd, const int* nq, int max_q, int Kpad, int stages, int* err,
+                                 cudaStream_t st);
+// Fused approximate forms: the table from each row's candidate bins (qd[q].cbin), exact
+// squared distances sum (V_u - Q_j)^2 in FP32; with certify (BF16), a row is certified when
+// its kc-th approximate value minus the rounding bound eps_rel |v_u| max|q| + eps_abs (|v_u|^2
+// + max|q|^2) exceeds the k-th exact value: then no bin outside the candidates can be among
+// the k nearest.  Other rows go to qd[q].rr (rr_count zeroed) for launch_rerank_full_b.
+cudaError_t launch_rerank_cand_b(const QDesc* qd, const int* nq, int max_q, int64_t M, int max_h, const float* V,
+                                 int ldv, const float* vnorm, bool certify, float eps_rel, float eps_abs,
+                                 cudaStream_t st);
+// The table rows listed in qd[q].rr recomputed exactly over all bins (same sums as above).
+cudaError_t launch_rerank_full_b(const QDesc* qd, const int* nq, int max_q, int max_tk, const float* V, int ldv,
                                  cudaStream_t st);
 // Reverse pass on the candidates through the row map, then the final selection (queries
 // whose block overflowed are reported uncertified).

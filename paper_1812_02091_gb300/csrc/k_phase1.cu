@@ -684,6 +684,151 @@ k_table_rerank_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64
                            d.tab_es);
 }
 
+// Fused approximate forms: the re-rank from the candidate bins the product's epilogue kept
+// (qd[q].cbin, kc per row) instead of a scan of the distance matrix; exact sums as in
+// table_rerank_body (same dimension order, so the same values), k smallest by (value, bin).
+// Certificate (BF16): every bin outside the candidates has an approximate squared distance of
+// at least camax (the kc-th smallest), hence an exact one of at least camax - eps; when that
+// exceeds the k-th exact value (with its own FP32 rounding allowed for) the row is exact.
+// Uncertified rows are listed for k_rerank_full_b.  Block: kRrRows rows of one query.
+template <int KCT>
+__global__ void __launch_bounds__(kRrRows)
+k_rerank_cand_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t M, const float* __restrict__ V,
+                int ldv, const float* __restrict__ vnorm, bool certify, float eps_rel, float eps_abs)
+{
+    if ((int)blockIdx.x >= *nq) return;
+    const QDesc& d = qd[blockIdx.x];
+    extern __shared__ float4 qs4[];  // [h]: Q[j][d0 .. d0 + 4)
+    __shared__ float wmax[kRrRows / 32];
+    const int tid = threadIdx.x;
+    const int64_t row = (int64_t)blockIdx.y * kRrRows + tid;
+    const bool rok = row < M;
+    const int h = d.h, k = d.tk, kc = d.kc;
+    float qmax = 0.f;  // largest squared norm of the query's bins
+    if (certify) {
+        float qm = 0.f;
+        for (int j = tid; j < h; j += blockDim.x) qm = fmaxf(qm, d.qnorm[j]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) qm = fmaxf(qm, __shfl_xor_sync(0xffffffffu, qm, o));
+        if ((tid & 31) == 0) wmax[tid >> 5] = qm;
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < kRrRows / 32; ++w) qmax = fmaxf(qmax, wmax[w]);
+    }
+    int s[KCT];
+#pragma unroll
+    for (int c = 0; c < KCT; ++c) s[c] = (rok && c < kc) ? d.cbin[row * kCandPerRow + c] : INT32_MAX;
+    float acc[KCT];
+#pragma unroll
+    for (int c = 0; c < KCT; ++c) acc[c] = 0.f;
+    for (int d0 = 0; d0 < ldv; d0 += kRrDims) {
+        __syncthreads();
+        for (int j = tid; j < h; j += blockDim.x) qs4[j] = *reinterpret_cast<const float4*>(d.Q + (int64_t)j * ldv + d0);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (rok) v = *reinterpret_cast<const float4*>(V + row * ldv + d0);
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < KCT; ++c) {
+            if (s[c] != INT32_MAX) {
+                const float4 a = qs4[s[c]];
+                float t = v.x - a.x;
+                acc[c] = fmaf(t, t, acc[c]);
+                t = v.y - a.y;
+                acc[c] = fmaf(t, t, acc[c]);
+                t = v.z - a.z;
+                acc[c] = fmaf(t, t, acc[c]);
+                t = v.w - a.w;
+                acc[c] = fmaf(t, t, acc[c]);
+            }
+        }
+    }
+    if (!rok) return;
+    float z[KCT];
+    int s2[KCT];
+#pragma unroll
+    for (int l = 0; l < KCT; ++l) { z[l] = INFINITY; s2[l] = INT32_MAX; }
+#pragma unroll
+    for (int c = 0; c < KCT; ++c)
+        if (s[c] != INT32_MAX) insert_dj_tie<KCT>(z, s2, acc[c], s[c]);
+    float ek = INFINITY;
+#pragma unroll
+    for (int l = 0; l < KCT; ++l) {
+        if (l < k) {
+            const bool valid = s2[l] != INT32_MAX;
+            d.tab[row * d.tab_rs + l * d.tab_es] = make_float2(valid ? sq_to_dist(z[l]) : INFINITY, valid ? d.qw[s2[l]] : 0.f);
+        }
+        if (l == k - 1) ek = z[l];
+    }
+    if (certify) {
+        const float nv = vnorm[row];
+        const float eps = eps_rel * sqrtf(nv * qmax) + eps_abs * (nv + qmax);
+        if (!(d.camax[row] - eps > ek * (1.0f + 4e-5f))) {
+            const int idx = atomicAdd(d.rr_count, 1);
+            d.rr[idx] = (int32_t)row;
+        }
+    }
+}
+
+// Exact table rows over all bins for the rows the certificate left out: a warp per row,
+// each lane the exact squared distances (sums as above) of bins lane, lane + 32, ... kept as
+// its KT smallest (bins ascending per lane, so ties keep the lower bin), then k successive
+// minima across the warp by (value, bin).
+template <int KT>
+__global__ void __launch_bounds__(256)
+k_rerank_full_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, const float* __restrict__ V, int ldv)
+{
+    if ((int)blockIdx.y >= *nq) return;
+    const QDesc& d = qd[blockIdx.y];
+    const int cnt = *d.rr_count;
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)(gridDim.x * (blockDim.x >> 5));
+    for (int t = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); t < cnt; t += nw) {
+        const int64_t row = d.rr[t];
+        const float* vr = V + row * ldv;
+        float z[KT];
+        int s[KT];
+#pragma unroll
+        for (int l = 0; l < KT; ++l) { z[l] = INFINITY; s[l] = INT32_MAX; }
+        for (int j = lane; j < d.h; j += 32) {
+            const float* qr = d.Q + (int64_t)j * ldv;
+            float acc = 0.f;
+            for (int d0 = 0; d0 < ldv; d0 += 4) {
+                const float4 v = *reinterpret_cast<const float4*>(vr + d0);
+                const float4 a = *reinterpret_cast<const float4*>(qr + d0);
+                float e = v.x - a.x;
+                acc = fmaf(e, e, acc);
+                e = v.y - a.y;
+                acc = fmaf(e, e, acc);
+                e = v.z - a.z;
+                acc = fmaf(e, e, acc);
+                e = v.w - a.w;
+                acc = fmaf(e, e, acc);
+            }
+            if (acc < z[KT - 1]) insert_dj<KT>(z, s, acc, j);
+        }
+        for (int l = 0; l < d.tk; ++l) {
+            float bz = z[0];
+            int bs = s[0];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float oz = __shfl_xor_sync(0xffffffffu, bz, o);
+                const int os = __shfl_xor_sync(0xffffffffu, bs, o);
+                if (oz < bz || (oz == bz && os < bs)) { bz = oz; bs = os; }
+            }
+            if (lane == 0) {
+                const bool valid = bs != INT32_MAX;
+                d.tab[row * d.tab_rs + l * d.tab_es] = make_float2(valid ? sq_to_dist(bz) : INFINITY, valid ? d.qw[bs] : 0.f);
+            }
+            if (s[0] == bs && bs != INT32_MAX) {  // the owner pops its head
+#pragma unroll
+                for (int q = 0; q < KT - 1; ++q) { z[q] = z[q + 1]; s[q] = s[q + 1]; }
+                z[KT - 1] = INFINITY;
+                s[KT - 1] = INT32_MAX;
+            }
+        }
+    }
+}
+
 // Opt-in dynamic shared memory of the re-rank kernels (above 48 KB for long queries).
 cudaError_t rerank_smem_attr(size_t smem)
 {
@@ -697,6 +842,7 @@ cudaError_t rerank_smem_attr(size_t smem)
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_table_rerank_b<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_table_rerank_b<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_table_rerank_b<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rerank_cand_b<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     return e;
 }
 
@@ -874,6 +1020,40 @@ cudaError_t launch_table_b(const QDesc* qd, const int* nq, int max_q, int64_t M,
         const int warps = 8;
         k_table_generic_b<<<dim3((unsigned)((M + warps - 1) / warps), (unsigned)max_q), warps * 32, 0, st>>>(qd, nq, M);
     }
+    return cudaGetLastError();
+}
+
+}  // namespace emd
+
+namespace emd {
+
+cudaError_t launch_rerank_cand_b(const QDesc* qd, const int* nq, int max_q, int64_t M, int max_h, const float* V,
+                                 int ldv, const float* vnorm, bool certify, float eps_rel, float eps_abs,
+                                 cudaStream_t st)
+{
+    if (max_q <= 0 || M <= 0) return cudaSuccess;
+    const int64_t tiles = (M + kRrRows - 1) / kRrRows;
+    if (tiles > 65535 || ldv % 4 != 0) return cudaErrorInvalidValue;
+    const size_t smem = rerank_smem_bytes(max_h);
+    cudaError_t e = rerank_smem_attr(smem);
+    if (e != cudaSuccess) return e;
+    k_rerank_cand_b<16><<<dim3((unsigned)max_q, (unsigned)tiles), kRrRows, smem, st>>>(qd, nq, M, V, ldv, vnorm,
+                                                                                       certify, eps_rel, eps_abs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rerank_full_b(const QDesc* qd, const int* nq, int max_q, int max_tk, const float* V, int ldv,
+                                 cudaStream_t st)
+{
+    if (max_q <= 0) return cudaSuccess;
+    if (max_tk > 16 || ldv % 4 != 0) return cudaErrorInvalidValue;
+    const dim3 g(64, (unsigned)max_q);
+    if (max_tk <= 4)
+        k_rerank_full_b<4><<<g, 256, 0, st>>>(qd, nq, V, ldv);
+    else if (max_tk <= 8)
+        k_rerank_full_b<8><<<g, 256, 0, st>>>(qd, nq, V, ldv);
+    else
+        k_rerank_full_b<16><<<g, 256, 0, st>>>(qd, nq, V, ldv);
     return cudaGetLastError();
 }
 

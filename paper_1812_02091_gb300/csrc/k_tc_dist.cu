@@ -762,7 +762,11 @@ __device__ __forceinline__ void tc_insert(float (&z)[KT], int (&s)[KT], float d,
     s[0] = p[0] ? j : s[0];
 }
 
-template <int FMT, int KT>
+// CAND (approximate formats): instead of the table, each row's kc = qd[q].kc smallest
+// approximate values are kept and written as candidate bins (cbin, kCandPerRow per row)
+// with the kc-th approximate value (camax; +inf when every bin is a candidate), for the
+// exact re-rank and its certificate.
+template <int FMT, int KT, bool CAND>
 __global__ void __launch_bounds__(TCT_THREADS, 1)
 k_tc_table_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_lo, int64_t Mpad,
                  const float* __restrict__ a_scale, const float* __restrict__ a_norm, int64_t M,
@@ -1002,12 +1006,23 @@ k_tc_table_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A
                 if (lane == 0) mbar_arrive(&tempty[sme]);
                 ++cnt;
                 if (n0 + TC_BN >= N && row_ok) {  // the query's last tile: write its table row
+                    if (CAND) {
+                        const int kc = d.kc;
 #pragma unroll
-                    for (int l = 0; l < KT; ++l) {
-                        if (l < d.tk) {
-                            const bool valid = sj[l] != INT32_MAX;
-                            d.tab[u * d.tab_rs + (int64_t)l * d.tab_es] =
-                                make_float2(valid ? sq_to_dist(z[l]) : INFINITY, valid ? d.qw[sj[l]] : 0.f);
+                        for (int l = 0; l < KT; ++l)
+                            if (l < kc) d.cbin[u * kCandPerRow + l] = sj[l];
+                        float zc = z[0];
+#pragma unroll
+                        for (int l = 1; l < KT; ++l) zc = l == kc - 1 ? z[l] : zc;
+                        d.camax[u] = kc < N ? zc : INFINITY;
+                    } else {
+#pragma unroll
+                        for (int l = 0; l < KT; ++l) {
+                            if (l < d.tk) {
+                                const bool valid = sj[l] != INT32_MAX;
+                                d.tab[u * d.tab_rs + (int64_t)l * d.tab_es] =
+                                    make_float2(valid ? sq_to_dist(z[l]) : INFINITY, valid ? d.qw[sj[l]] : 0.f);
+                            }
                         }
                     }
                 }
@@ -1116,8 +1131,8 @@ k_tc_cand_batch(const QDesc* __restrict__ qd, const int* __restrict__ nq_dev, in
                 if (SPLIT) bulk_g2s(ast + kABytes, al + ((int64_t)c * kCandRows + m0) * EB, kABytes, afull);
             }
             ++items;
-            const uint8_t* bh = static_cast<const uint8_t*>(d.q_hi);
-            const uint8_t* bl = static_cast<const uint8_t*>(d.q_lo);
+            const uint8_t* bh = static_cast<const uint8_t*>(d.qs_hi);
+            const uint8_t* bl = static_cast<const uint8_t*>(d.qs_lo);
             for (int n0 = 0; n0 < d.h && ok; n0 += TC_BN) {
                 const int Nt = min(TC_BN, (int)round_up(d.h - n0, 16));
                 const uint32_t b_bytes = (uint32_t)Nt * EB;
@@ -1214,7 +1229,7 @@ k_tc_cand_batch(const QDesc* __restrict__ qd, const int* __restrict__ nq_dev, in
                 const int buf = it & 1;
                 const int lcol = n0 + cc + lane;
                 const bool lok = lcol < N;
-                const float cb_l = lok ? -2.f * d.q_scale[lcol] : 0.f;
+                const float cb_l = lok ? -2.f * d.qs_scale[lcol] : 0.f;
                 const float nb_l = lok ? d.qnorm[lcol] : 0.f;
                 if (!mbar_wait(&tfull[buf], (uint32_t)(it >> 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
                     fail();
@@ -1342,13 +1357,19 @@ __global__ void k_pack(const float* __restrict__ src, int ld, int m, int64_t R, 
     pack_body<FMT>(src, ld, m, R, Rpad, Kpad, hi, lo, scale);
 }
 
+// to_split: into the query's FP16-split panels of the candidate block (qs_*).
 template <int FMT>
-__global__ void k_pack_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int ld, int m, int Kpad)
+__global__ void k_pack_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int ld, int m, int Kpad,
+                         bool to_split)
 {
     if ((int)blockIdx.y >= *nq) return;
     const QDesc& d = qd[blockIdx.y];
-    pack_body<FMT>(d.Q, ld, m, d.h, d.npad, Kpad, static_cast<uint8_t*>(d.q_hi), static_cast<uint8_t*>(d.q_lo),
-                   d.q_scale);
+    if (to_split)
+        pack_body<FMT>(d.Q, ld, m, d.h, d.npad, Kpad, static_cast<uint8_t*>(d.qs_hi), static_cast<uint8_t*>(d.qs_lo),
+                       d.qs_scale);
+    else
+        pack_body<FMT>(d.Q, ld, m, d.h, d.npad, Kpad, static_cast<uint8_t*>(d.q_hi), static_cast<uint8_t*>(d.q_lo),
+                       d.q_scale);
 }
 
 }  // namespace
@@ -1383,15 +1404,15 @@ int tc_dist_stages(int fmt, int KC)
 }
 
 cudaError_t launch_pack_b(int fmt, const QDesc* qd, const int* nq, int max_q, int max_rows, int ld, int m,
-                          int Kpad, cudaStream_t st)
+                          int Kpad, cudaStream_t st, bool to_split)
 {
     if (max_q <= 0 || max_rows <= 0) return cudaSuccess;
     const int warps = 8;
     const dim3 g((unsigned)((max_rows + warps - 1) / warps), (unsigned)max_q);
     switch (fmt) {
-    case TC_SPLIT: k_pack_b<TC_SPLIT><<<g, warps * 32, 0, st>>>(qd, nq, ld, m, Kpad); break;
-    case TC_BF16: k_pack_b<TC_BF16><<<g, warps * 32, 0, st>>>(qd, nq, ld, m, Kpad); break;
-    case TC_E4M3: k_pack_b<TC_E4M3><<<g, warps * 32, 0, st>>>(qd, nq, ld, m, Kpad); break;
+    case TC_SPLIT: k_pack_b<TC_SPLIT><<<g, warps * 32, 0, st>>>(qd, nq, ld, m, Kpad, to_split); break;
+    case TC_BF16: k_pack_b<TC_BF16><<<g, warps * 32, 0, st>>>(qd, nq, ld, m, Kpad, false); break;
+    case TC_E4M3: k_pack_b<TC_E4M3><<<g, warps * 32, 0, st>>>(qd, nq, ld, m, Kpad, false); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -1518,17 +1539,17 @@ cudaError_t launch_tc_dist(int fmt, const void* A_hi, const void* A_lo, int64_t 
 
 namespace emd {
 
-template <int FMT, int KT>
+template <int FMT, int KT, bool CAND>
 static cudaError_t tc_table_launch(dim3 grid, size_t smem, cudaStream_t st, const void* A_hi, const void* A_lo,
                                    int64_t Mpad, const float* a_scale, const float* a_norm, int64_t M, const QDesc* qd,
                                    const int* nq, int groups, int KC, int stages, int* err)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_table_batch<FMT, KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_tc_table_batch<FMT, KT, CAND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_tc_table_batch<FMT, KT><<<grid, TCT_THREADS, smem, st>>>(static_cast<const uint8_t*>(A_hi),
-                                                               static_cast<const uint8_t*>(A_lo), Mpad, a_scale,
-                                                               a_norm, M, qd, nq, groups, KC, stages, err);
+    k_tc_table_batch<FMT, KT, CAND><<<grid, TCT_THREADS, smem, st>>>(static_cast<const uint8_t*>(A_hi),
+                                                                     static_cast<const uint8_t*>(A_lo), Mpad, a_scale,
+                                                                     a_norm, M, qd, nq, groups, KC, stages, err);
     return cudaGetLastError();
 }
 
@@ -1537,7 +1558,7 @@ cudaError_t launch_tc_table_batch(int fmt, const void* A_hi, const void* A_lo, i
                                   int max_tk, int group_mult, int stages_req, int* err, cudaStream_t st)
 {
     if (M <= 0 || max_q <= 0) return cudaSuccess;
-    if (fmt != TC_SPLIT || max_tk < 1 || max_tk > 16) return cudaErrorInvalidValue;
+    if (max_tk < 1 || max_tk > 16) return cudaErrorInvalidValue;
     const int KC = Kpad / 64;
     const int fit = tc_batch_stages(fmt, KC);
     if (fit < 2) return cudaErrorInvalidValue;
@@ -1547,8 +1568,17 @@ cudaError_t launch_tc_table_batch(int fmt, const void* A_hi, const void* A_lo, i
     const int sms = sm_count();
     const int groups = std::max(1, std::min(max_q, std::max(1, group_mult) * ((2 * sms + m_tiles - 1) / m_tiles)));
     const dim3 grid((unsigned)std::min<int64_t>((int64_t)m_tiles * groups, sms));
+    // approximate formats keep max_tk = the candidate count in candidate mode (at most 16)
+    if (fmt == TC_BF16)
+        return tc_table_launch<TC_BF16, 16, true>(grid, smem, st, A_hi, nullptr, Mpad, a_scale, a_norm, M, qd, nq,
+                                                  groups, KC, stages, err);
+    if (fmt == TC_E4M3)
+        return tc_table_launch<TC_E4M3, 16, true>(grid, smem, st, A_hi, nullptr, Mpad, a_scale, a_norm, M, qd, nq,
+                                                  groups, KC, stages, err);
+    if (fmt != TC_SPLIT) return cudaErrorInvalidValue;
 #define EMD_TT(KT) \
-    return tc_table_launch<TC_SPLIT, KT>(grid, smem, st, A_hi, A_lo, Mpad, a_scale, a_norm, M, qd, nq, groups, KC, stages, err)
+    return tc_table_launch<TC_SPLIT, KT, false>(grid, smem, st, A_hi, A_lo, Mpad, a_scale, a_norm, M, qd, nq, groups, KC, \
+                                                stages, err)
     if (max_tk <= 1) EMD_TT(1);
     if (max_tk <= 2) EMD_TT(2);
     if (max_tk <= 4) EMD_TT(4);

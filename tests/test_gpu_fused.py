@@ -158,3 +158,47 @@ def test_forward_sweep_forms_bit_identical(emd):
     for other in outs[1:]:
         for a, b in zip(outs[0], other):
             np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_fused_approximate_forms_against_oracle(emd, precision):
+    """Fused pruned top-K in the approximate formats on the text workload (V = 1e5, m = 300):
+    the product's epilogue keeps each row's k + 8 smallest approximate distances, the table
+    is their exact FP32 re-rank, and the reverse direction reads the exact FP16-split block
+    of the candidate rows.  BF16 certifies every row (or recomputes it over all bins), so its
+    top-16 meets the FP32 tolerance: identical to the oracle's outside the tie group of the
+    16th distance, every returned distance within 1e-5.  E4M3's bound is too wide for the
+    certificate; its returned distances are held to the forward rounding bound of R15 and
+    its recall against the oracle is reported."""
+    import os
+    import oracle
+    w = emd_synth.config(2, query_limit=24)
+    q = w.queries
+    K = 16
+    db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
+                           emd.emd_db_options_default(precision=precision, max_query_h=1024), v=w.v)
+    try:
+        gi, gd = emd.emd_topk(db, q.row_ptr, q.col, q.val, "act", 4, "max", K)
+        emd.emd_db_check_device_errors(db)
+    finally:
+        emd.emd_db_destroy(db)
+    prep = oracle.prepare(w.emb, None, w.db)
+    threads = os.cpu_count() or 1
+    recalls = []
+    for i in range(q.n):
+        ref = oracle.SymTopK(w.emb, None, w.db, *q.row(i), "act", 4, K, threads=threads, prep=prep)
+        dK = ref.dist[K - 1]
+        got_sym = ref.sym_of(gi[i])
+        tie = np.abs(got_sym - dK) <= 1e-5 * dK + 1e-9
+        truth = set(int(d) for d in ref.idx)
+        hits = sum(1 for d, t in zip(gi[i], tie) if int(d) in truth or t)
+        recalls.append(hits / K)
+        rel = np.abs(gd[i] - got_sym) / got_sym
+        if precision == "bf16":
+            ref_tie = np.abs(ref.dist - dK) <= 1e-5 * dK + 1e-9
+            assert {int(d) for d, t in zip(ref.idx, ref_tie) if not t} <= {int(d) for d in gi[i]}, i
+            assert rel.max() <= 1e-5, (i, rel.max())
+        else:
+            assert rel.max() <= 2 * (2 * 2.0 ** -4 + 2.0 ** -8), (i, rel.max())
+    print(f"{precision} fused: top-{K} recall {np.mean(recalls):.4f} (min {np.min(recalls):.4f}) over {q.n} queries")
+    assert np.mean(recalls) >= (1.0 if precision == "bf16" else 0.9)
