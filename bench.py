@@ -326,7 +326,7 @@ def main():
     ap.add_argument("--topk", type=int, default=16)
     ap.add_argument("--batch-columns", type=int, default=32768,
                     help="distance-matrix columns of one batch workspace (device memory 4 x v_used x columns)")
-    ap.add_argument("--oracle-queries", type=int, default=16,
+    ap.add_argument("--oracle-queries", type=int, default=32,
                     help="size of the stratified query subset checked against the FP64 oracle (0: none)")
     ap.add_argument("--e2e-steps", type=int, default=0, help="default: same as --steps")
     ap.add_argument("--precision", default="fp32_tc", choices=["fp32", "fp32_tc", "bf16", "fp8"],
@@ -563,9 +563,19 @@ def main_bench(args, rank, world, local):
         torch.cuda.synchronize()
         emd.emd_db_check_device_errors(h2)
         t2 = sum(a_.elapsed_time(b_) for a_, b_ in ev) / 1e3
+        # per-phase device time of the same batches (profiling launches each kernel directly)
+        emd.emd_db_profile_reset(h2)
+        emd.emd_db_set_profiling(h2, True)
+        for s in range(args.w2_steps):
+            emd.emd_topk_device(h2, *d2[args.warmup + s], oi, od, "act", args.k, "max", K, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        emd.emd_db_set_profiling(h2, False)
+        pr2 = emd.emd_db_profile_get(h2)
         w2line = {"workload": w2.name + " (1000 queries of the same law, log-normal h median 100)",
                   "value": args.batch * args.w2_steps / t2, "unit": UNIT, "steps": args.w2_steps,
-                  "precision": args.precision}
+                  "precision": args.precision,
+                  "phase_ms_per_batch": {p_: round(v / args.w2_steps, 4) for p_, v in pr2["ms"].items()},
+                  "prune_fallbacks": pr2["prune_fallbacks"], "fused_retries": pr2["fused_retries"]}
         emd.emd_db_destroy(h2)
 
     # ---- per-phase achieved figures of the headline form (profiling pass)
@@ -675,6 +685,7 @@ def main_bench(args, rank, world, local):
                                                                               "re-rank"}[args.precision],
             "roofline": roofline,
             "roofline_k4": roof("fwd"),
+            "roofline_phase1": roof("distance"),
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(gpu_launches),
@@ -736,7 +747,7 @@ def main_k4(args, local):
     """The forward CSR pass (Phase 2+3) on a database much larger than L2: per query sweep
     8 nnz + 4 (n + 1) + 4 n algorithmic bytes, timed with the library's events over batches of
     --batch queries (forward direction only, all documents), L2 flushed between batches, for
-    each form of the grouped sweep (fwd_kernel 1..3) and the autotuner's choice."""
+    each form of the grouped sweep (fwd_kernel 1..4) and the autotuner's choice."""
     import torch
     import emd_synth
     import paper_1812_02091_gb300 as emd
@@ -760,7 +771,7 @@ def main_k4(args, local):
     pk = peaks()
     res = {}
     ref = None
-    for fk in (0, 1, 2, 3):
+    for fk in (0, 1, 2, 3, 4):
         db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
                                emd.emd_db_options_default(precision=args.precision, device=local, max_query_h=256,
                                                           max_batch=B, batch_columns=B * 256, fwd_kernel=fk))

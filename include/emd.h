@@ -118,7 +118,8 @@ typedef struct {
                                 group of eight queries): 0 (default) the autotuner's choice; 1 each
                                 table entry loaded when the residual mass needs it; 2 query-major
                                 table rows, four entries loaded up front; 3 the first two entries up
-                                front, column ids and weights read 32 at a time.  Same results */
+                                front, column ids and weights read 32 at a time; 4 as 1 with each
+                                lane's next column ids and weights read ahead.  Same results */
 } emd_db_options;
 
 typedef struct {
@@ -131,7 +132,7 @@ typedef struct {
                                        (multiple of the load-balance minimum) */
     int32_t tc_stages;              /* its query-chunk stages (0: as many as fit) */
     int32_t rev_warps;              /* pruned reverse pass: warps per candidate document */
-    int32_t fwd_kernel;             /* the batched forward sweep's form (1..3, see emd_db_options) */
+    int32_t fwd_kernel;             /* the batched forward sweep's form (1..4, see emd_db_options) */
 } emd_db_info;
 
 /* A batch of query histograms in CSR form: query i has bins

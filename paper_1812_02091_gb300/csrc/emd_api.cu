@@ -1069,7 +1069,7 @@ emd_status autotune(emd_db* db, const std::vector<int32_t>& used_host)
         // tables rebuilt), timed on the same batch
         float best = 1e30f;
         int choice = kFwdChain;
-        for (int v : {kFwdChain, kFwdCoalesced, kFwdRowMajor}) {
+        for (int v : {kFwdChain, kFwdPrefetch, kFwdCoalesced, kFwdRowMajor}) {
             db->tune_fwd = v;
             s = fill_descriptors(ws, 0, db, rp.data(), db->stage_idx, db->stage_w, 0, 0, nb, EMD_ACT, k, EMD_DIR_MAX,
                                  K, pruned, nullptr, db->stage_oidx, db->stage_odist, st);
@@ -1194,7 +1194,7 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
     db->row_ptr_host.assign(row_ptr, row_ptr + n_docs + 1);
     db->opt = opt;
     db->dev = opt.device;
-    db->tune_fwd = opt.fwd_kernel > 0 ? opt.fwd_kernel - 1 : kFwdCoalesced;
+    db->tune_fwd = opt.fwd_kernel > 0 ? opt.fwd_kernel - 1 : kFwdChain;
     db->margin = opt.rerank_margin;
     db->v = v;
     db->v_used = (int64_t)used_ids.size();

@@ -206,7 +206,7 @@ struct emd_db {
     int tune_group_mult = 1;   // query groups per vocabulary tile, times the balance minimum
     int tune_stages = 0;       // B stages of the batched tensor-core kernel (0: as many as fit)
     int tune_rev_warps = 4;    // warps per candidate document in the pruned reverse pass
-    int tune_fwd = 2;          // form of the grouped forward sweep (kFwdChain / kFwdRowMajor / kFwdCoalesced)
+    int tune_fwd = 0;          // form of the grouped forward sweep (kFwd*)
     std::map<emd::GraphKey, emd::GraphEntry> graphs;
 
     // Section 6 baselines (allocated and prepared at first use)

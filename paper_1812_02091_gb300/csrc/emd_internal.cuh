@@ -314,7 +314,8 @@ cudaError_t launch_table_ict_b(const QDesc* qd, const int* nq, int max_q, int64_
 //   kFwdChain     entry-interleaved rows, each entry loaded once the residual needs it
 //   kFwdRowMajor  query-major rows, the first four entries loaded up front (vector loads)
 //   kFwdCoalesced entry-interleaved rows, the first two entries up front, coalesced CSR reads
-enum : int { kFwdChain = 0, kFwdRowMajor = 1, kFwdCoalesced = 2, kFwdVariants = 3 };
+//   kFwdPrefetch  the entry chain with each lane's next four column ids and weights read ahead
+enum : int { kFwdChain = 0, kFwdRowMajor = 1, kFwdCoalesced = 2, kFwdPrefetch = 3, kFwdVariants = 4 };
 cudaError_t launch_fwd_b(int meas, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
                          const int32_t* col, const float* val, int64_t n, bool to_out, bool grouped, int max_tk,
                          cudaStream_t st, int variant);

@@ -942,6 +942,69 @@ k_fwd_gv(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t
     }
 }
 
+// The entry-chain sweep of k_fwd_g with the CSR read one group ahead: each lane (four
+// nonzeros of its phase per step) loads the column ids and weights of its next four
+// nonzeros before it evaluates the current ones, so the DRAM latency of the stream overlaps
+// the table gathers.  Same steps and summation order as k_fwd_g: bit-identical.
+template <int MEAS, int KT>
+__global__ void k_fwd_gp(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t* __restrict__ row_ptr,
+                         const int32_t* __restrict__ col, const float* __restrict__ val, int64_t n, bool to_out)
+{
+    const int q0 = blockIdx.y * kFwdGroup;
+    const int nqv = *nq;
+    if (q0 >= nqv) return;
+    const int lane = threadIdx.x & 31, g = lane & 7, ph = lane >> 3;
+    const bool act = q0 + g < nqv;
+    const QDesc& dq = qd[act ? q0 + g : q0];
+    const float2* tq = dq.tab;
+    const int kq = dq.tk;
+    float* oq = to_out ? dq.t_out : dq.t_fwd;
+    const int rs = dq.tab_rs, es = dq.tab_es;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t d = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); d < n; d += warps) {
+        const int32_t a = row_ptr[d], b = row_ptr[d + 1];
+        float acc = 0.f;
+        int32_t e = a + ph;
+        int32_t pu[4];
+        float px[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const bool v = e + 4 * i < b;
+            pu[i] = v ? col[e + 4 * i] : 0;
+            px[i] = v ? val[e + 4 * i] : 0.f;
+        }
+        while (e < b) {
+            int32_t u[4];
+            float x[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                u[i] = pu[i];
+                x[i] = px[i];
+            }
+            const int32_t en = e + 16;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const bool v = en + 4 * i < b;
+                pu[i] = v ? col[en + 4 * i] : 0;
+                px[i] = v ? val[en + 4 * i] : 0.f;
+            }
+            if (act) {
+                float c[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    c[i] = e + 4 * i < b ? fwd_cost_p<MEAS, KT>(x[i], tq + (int64_t)u[i] * rs, es, kq) : 0.f;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (e + 4 * i < b) acc = __fadd_rn(acc, c[i]);
+            }
+            e = en;
+        }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+        if (ph == 0 && act) oq[d] = acc;
+    }
+}
+
 // Forward pass of a group of kFwdGroup queries, entry-interleaved tables (row u, entry l,
 // query g at tab[u * tab_rs + l * kFwdGroup], so the group's entry l of a row is 64
 // contiguous bytes): the column ids and weights of 32 nonzeros are read with one coalesced
@@ -1268,6 +1331,19 @@ cudaError_t launch_fwd_b(int meas, const QDesc* qd, const int* nq, int max_q, co
         dim3 gg((unsigned)std::max<int64_t>(1, blocks), (unsigned)((max_q + kFwdGroup - 1) / kFwdGroup));
         const int m = meas == M_ICT ? M_ACT : meas;  // ICT tables: the ACT steps over the written entries
         const int kw = meas == M_RWMD ? 1 : meas == M_OMR ? 2 : (meas == M_ICT && kt == 0 ? 0 : kt);
+        if (variant == kFwdPrefetch) {  // the entry chain with the CSR read one group ahead
+            switch (m) {
+            case M_RWMD: k_fwd_gp<M_RWMD, 0><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
+            case M_OMR: k_fwd_gp<M_OMR, 0><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
+            default: {
+#define EMD_L(KT) k_fwd_gp<M_ACT, KT><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out)
+                EMD_FWD_KT_SWITCH(kw, EMD_L)
+#undef EMD_L
+                break;
+            }
+            }
+            return cudaGetLastError();
+        }
         if (kw == 0 || variant == kFwdChain) {  // entry-interleaved rows, loads while mass remains
             switch (m) {
             case M_RWMD: k_fwd_g<M_RWMD, 0><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;

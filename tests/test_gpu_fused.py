@@ -137,12 +137,12 @@ def test_fused_candidate_row_overflow(emd):
 
 
 def test_forward_sweep_forms_bit_identical(emd):
-    """The three forms of the grouped forward sweep (fwd_kernel 1..3; their table layouts
+    """The four forms of the grouped forward sweep (fwd_kernel 1..4; their table layouts
     differ) give the same forward values and the same pruned top-K, bit for bit."""
     w = emd_synth.small_text(6161, 2500, 48, 1500, 19, 2, 200, 1, 300)
     q = w.queries
     outs = []
-    for fk in (1, 2, 3):
+    for fk in (1, 2, 3, 4):
         db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
                                emd.emd_db_options_default(precision="fp32_tc", max_query_h=512, autotune=0,
                                                           fwd_kernel=fk), v=w.v)
