@@ -102,18 +102,22 @@ typedef struct {
                                 kernels on a synthetic batch at creation and keeps the fastest
                                 (results do not depend on them); 0: fixed defaults */
     int32_t fused_phase1;    /* batched pruned top-K (EMD_DIR_MAX, K <= 16) with RWMD, OMR or ACT
-                                (k <= 16) in the tensor-core precisions: 1 (default) keeps each
-                                row's k smallest distances (FP32_TC) or k + rerank_margin <= 16
-                                smallest approximate ones (BF16, FP8_E4M3) in the product's
-                                epilogue, and computes the reverse direction's distances only on
-                                the candidate documents' rows, in the FP32-grade split, so no
-                                v_used x h_q matrix is written.  FP32_TC: bit-identical to 0.
-                                BF16: each table row is re-ranked exactly and certified (the
-                                k + margin-th approximate value minus the operand-rounding bound
-                                exceeds the k-th exact value) or recomputed exactly over all bins,
-                                so results meet the FP32 tolerance.  FP8_E4M3: the re-ranked
+                                (k <= 16), tensor-core precisions.  The fused form keeps each row's
+                                k smallest distances (FP32_TC) or k + rerank_margin <= 16 smallest
+                                approximate ones (BF16, FP8_E4M3) in the product's epilogue, and
+                                computes the reverse direction's distances only on the candidate
+                                documents' rows, in the FP32-grade split, so no v_used x h_q
+                                matrix is written.  FP32_TC: bit-identical to the full-matrix
+                                form.  BF16: each table row is re-ranked exactly and certified
+                                (the k + margin-th approximate value minus the operand-rounding
+                                bound exceeds the k-th exact value) or recomputed exactly over all
+                                bins, so results meet the FP32 tolerance.  FP8_E4M3: the re-ranked
                                 candidates as the table (no certificate), exact reverse distances.
-                                0: the full matrix and a separate table pass */
+                                0: always the full matrix and a separate table pass; 1 (default):
+                                the fused form for FP32_TC; 2: also for BF16 and FP8_E4M3 (exact
+                                but, on the serving-size database, slower than their full-matrix
+                                form: the wide candidate lists and their FP32 re-rank cost about
+                                what the cheaper product saves) */
     int32_t fwd_kernel;      /* form of the batched forward sweep (Phase 2+3 over the CSR for a
                                 group of eight queries): 0 (default) the autotuner's choice; 1 each
                                 table entry loaded when the residual mass needs it; 2 query-major

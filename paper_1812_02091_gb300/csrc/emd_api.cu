@@ -566,7 +566,7 @@ emd_status alloc_batch_ws(emd_db* db, BatchWS& ws, int max_batch, int64_t cols, 
     TRYW(dal(&ws.topk_scratch, B * kTopkScratchRow));
     TRYW(dal(&ws.qd_dev, BatchWS::kDescRing * B));
     TRYW(dal(&ws.nq_dev, BatchWS::kDescRing));
-    ws.fused = db->tc && !db->cost_mode && db->opt.fused_phase1 != 0 && db->as_hi != nullptr &&
+    ws.fused = db->tc && !db->cost_mode && db->opt.fused_phase1 >= (db->approx ? 2 : 1) && db->as_hi != nullptr &&
                tc_batch_stages(db->tcfmt, db->kpad / 64) >= 2 && tc_batch_stages(TC_SPLIT, db->kpad / 64) >= 2;
     if (ws.fused) {
         TRYW(dal(&ws.bqpos, B * vu));
@@ -1146,6 +1146,7 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
         opt.max_table_k > (1 << 16) || opt.max_batch < 1 || opt.max_batch > 4096 || opt.lanes < 1 ||
         opt.lanes > 16 || opt.batch_columns < 1)
         return fail(EMD_ERR_INVALID_ARG, "option out of range");
+    if (opt.fused_phase1 < 0 || opt.fused_phase1 > 2) return fail(EMD_ERR_INVALID_ARG, "fused_phase1 must be 0..2");
     if (opt.fwd_kernel < 0 || opt.fwd_kernel > kFwdVariants)
         return fail(EMD_ERR_INVALID_ARG, "fwd_kernel must be 0..%d", kFwdVariants);
     if ((opt.precision == EMD_PREC_BF16 || opt.precision == EMD_PREC_FP8_E4M3) && opt.max_query_h > 6400)
@@ -1283,7 +1284,7 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
                  "embedding pack");
             db->total_launches += 1;
             db->launches[6] += 1;
-            if (db->approx && opt.batched && opt.fused_phase1) {
+            if (db->approx && opt.batched && opt.fused_phase1 >= 2) {
                 TRY(dalloc(db, &db->as_hi, db->mpad * db->kpad));
                 TRY(dalloc(db, &db->as_lo, db->mpad * db->kpad));
                 TRY(dalloc(db, &db->as_scale, db->mpad));

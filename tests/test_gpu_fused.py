@@ -176,7 +176,7 @@ def test_fused_approximate_forms_against_oracle(emd, precision):
     q = w.queries
     K = 16
     db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
-                           emd.emd_db_options_default(precision=precision, max_query_h=1024), v=w.v)
+                           emd.emd_db_options_default(precision=precision, max_query_h=1024, fused_phase1=2), v=w.v)
     try:
         gi, gd = emd.emd_topk(db, q.row_ptr, q.col, q.val, "act", 4, "max", K)
         emd.emd_db_check_device_errors(db)
