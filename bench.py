@@ -345,6 +345,8 @@ def main():
                     help="forward sparse pass alone on the serving-size database (workload 5, cut to --k4-docs "
                          "documents), against the HBM roofline; prints one line")
     ap.add_argument("--k4-docs", type=int, default=300000)
+    ap.add_argument("--k4-forms", default="0,1,2,3,4",
+                    help="forms of the grouped sweep the --k4 mode times (0 = the autotuner's choice)")
     ap.add_argument("--ict", action="store_true",
                     help="LC-ICT symmetric top-K on workload 2's database and queries beside LC-ACT on the "
                          "same batches, recall against the oracle; prints one line")
@@ -771,7 +773,7 @@ def main_k4(args, local):
     pk = peaks()
     res = {}
     ref = None
-    for fk in (0, 1, 2, 3, 4):
+    for fk in [int(f) for f in args.k4_forms.split(",") if f.strip()]:
         db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
                                emd.emd_db_options_default(precision=args.precision, device=local, max_query_h=256,
                                                           max_batch=B, batch_columns=B * 256, fwd_kernel=fk))
