@@ -341,10 +341,15 @@ def main():
     ap.add_argument("--probe", action="store_true",
                     help="small fixed case for profiler captures: workload 2's database, --batch "
                          "queries per batch (16 suggested), --warmup + --steps batches, ~1.5 GB on the device")
+    ap.add_argument("--probe-h", type=int, default=128,
+                    help="--probe: largest h_q of the probe queries (128: one column tile each; 1024: the whole "
+                         "workload-2 query law, batch workspace of 16384 columns)")
     ap.add_argument("--k4", action="store_true",
                     help="forward sparse pass alone on the serving-size database (workload 5, cut to --k4-docs "
                          "documents), against the HBM roofline; prints one line")
     ap.add_argument("--k4-docs", type=int, default=300000)
+    ap.add_argument("--k4-hmax", type=int, default=2048,
+                    help="--k4: largest h_q of the timed queries (2048: workload 5's whole query law)")
     ap.add_argument("--k4-forms", default="0,1,2,3,4",
                     help="forms of the grouped sweep the --k4 mode times (0 = the autotuner's choice)")
     ap.add_argument("--ict", action="store_true",
@@ -723,12 +728,14 @@ def main_probe(args, local):
     B = args.batch
     db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
                            emd.emd_db_options_default(precision=args.precision, device=local, max_query_h=1024,
-                                                      max_batch=B, batch_columns=max(B * 128, 1024), autotune=0))
+                                                      max_batch=B, autotune=0,
+                                                      batch_columns=max(B * 128, 1024) if args.probe_h <= 128
+                                                      else max(B * 128, 16384)))
     stream = torch.cuda.current_stream()
     oi = torch.empty((B, args.topk), dtype=torch.int64, device="cuda")
     od = torch.empty((B, args.topk), dtype=torch.float32, device="cuda")
     times = []
-    small = np.nonzero(np.diff(w.queries.row_ptr) <= 128)[0]  # one column tile each: fixed batches
+    small = np.nonzero(np.diff(w.queries.row_ptr) <= args.probe_h)[0]  # 128: one column tile each
     for s in range(args.warmup + args.steps):
         sub = w.queries.subset(small[np.arange(s * B, (s + 1) * B) % len(small)])
         qi, qw = torch.from_numpy(sub.col).cuda(), torch.from_numpy(sub.val).cuda()
@@ -740,7 +747,7 @@ def main_probe(args, local):
         times.append(time.perf_counter() - t0)
     emd.emd_db_check_device_errors(db)
     emd.emd_db_destroy(db)
-    print(json.dumps({"probe": "pruned top-K batches of queries with h_q <= 128", "batch": B,
+    print(json.dumps({"probe": f"pruned top-K batches of queries with h_q <= {args.probe_h}", "batch": B,
                       "precision": args.precision,
                       "ms_per_batch": [round(1e3 * t, 3) for t in times]}))
 
@@ -759,9 +766,8 @@ def main_k4(args, local):
     need = B * (args.steps + args.warmup)
     w = emd_synth.config(5, query_limit=8 * need, n_docs=args.k4_docs)
     gen_s = time.perf_counter() - t0
-    # the sparse pass does not depend on h_q (the table is k wide): queries of at most 256 bins
-    # keep every batch in one sub-batch (one sweep per group of eight) and D small
-    small = np.nonzero(np.diff(w.queries.row_ptr) <= 256)[0][:need]
+    # workload 5's queries (h_q log-uniform 5..2000) in order; --k4-hmax 256 keeps short ones
+    small = np.nonzero(np.diff(w.queries.row_ptr) <= args.k4_hmax)[0][:need]
     queries = w.queries.subset(small)
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
@@ -775,8 +781,11 @@ def main_k4(args, local):
     ref = None
     for fk in [int(f) for f in args.k4_forms.split(",") if f.strip()]:
         db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
-                               emd.emd_db_options_default(precision=args.precision, device=local, max_query_h=256,
-                                                          max_batch=B, batch_columns=B * 256, fwd_kernel=fk))
+                               emd.emd_db_options_default(precision=args.precision, device=local,
+                                                          max_query_h=args.k4_hmax, max_batch=B,
+                                                          batch_columns=max(B * 256, min(args.batch_columns,
+                                                                                         B * args.k4_hmax)),
+                                                          fwd_kernel=fk))
         info = emd.emd_db_info_get(db)
         for s in range(args.warmup):
             emd.emd_query_batch_device(db, *batches[s], out, "act", args.k, "fwd", stream=stream.cuda_stream)
@@ -799,10 +808,12 @@ def main_k4(args, local):
         achieved = sweep * B * args.steps / t / 1e9
         res["auto" if fk == 0 else f"fwd_kernel={fk}"] = {
             "chosen": info["fwd_kernel"], "ms_per_batch": 1e3 * t / args.steps, "ms_per_query": 1e3 * t / (B * args.steps),
-            "achieved_gbs": achieved, "frac": achieved / pk["hbm_gbs"], "same_values_as_auto": same}
+            "achieved_gbs": achieved, "frac": achieved / pk["hbm_gbs"], "same_values_as_first": same,
+            "last_batch_sha256": hashlib.sha256(got.tobytes()).hexdigest()[:16]}
     print(json.dumps({"k4": "forward CSR pass (Eq. 6-9), LC-ACT k=%d, per form of the grouped sweep" % args.k,
                       "database": f"workload 5 cut to {n} documents: nnz {nnz}, CSR {sweep / 1e6:.0f} MB per sweep",
-                      "queries": f"{B * args.steps} of workload 5's queries with h_q <= 256, batches of {B}",
+                      "queries": f"{B * args.steps} of workload 5's queries with h_q <= {args.k4_hmax}, "
+                                 f"batches of {B}",
                       "peak_gbs": pk["hbm_gbs"], "peak_source": f"{pk['source']} HBM copy",
                       "forms": res, "generation_s": gen_s}))
 

@@ -631,8 +631,20 @@ emd_status fill_descriptors(BatchWS& ws, int slot, emd_db* db, const int64_t* rp
     const int64_t n = db->n;
     int max_rows = 0, max_npad = 0, max_ldd = 0, max_tk = 0, max_kc = 0;
     int64_t c_D = 0, c_Q = 0, c_P = 0, c_T = 0;
-    for (int64_t i = j0; i < j1; ++i) {
-        QDesc& d = hd[i - j0];
+    // Descriptor position p holds query order[p].  With grouped tables the forward sweep runs
+    // a group of kFwdGroup consecutive positions in one warp, whose lanes step through the
+    // longest transfer chain of the group (longer for larger h_q, whose capacities are
+    // smaller), so the queries are placed by h_q, largest first: groups of alike lengths.
+    // Every output is addressed per query (b = i - i0), so results do not depend on the order.
+    std::vector<int64_t>& order = ws.order;
+    order.resize((size_t)nb);
+    for (int p = 0; p < nb; ++p) order[p] = j0 + p;
+    if (grouped)
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int64_t x, int64_t y) { return rp[x + 1] - rp[x] > rp[y + 1] - rp[y]; });
+    for (int p = 0; p < nb; ++p) {
+        const int64_t i = order[p];
+        QDesc& d = hd[p];
         memset(&d, 0, sizeof(d));
         const int64_t off = rp[i] - rp[i0];
         const int b = (int)(i - i0);
@@ -655,12 +667,12 @@ emd_status fill_descriptors(BatchWS& ws, int slot, emd_db* db, const int64_t* rp
         }
         d.D = ws.bD + c_D * db->v_used;
         if (grouped && lw_b > 0) {
-            const int64_t bs = i - j0;  // position in the sub-batch: group bs / kFwdGroup
+            const int64_t bs = p;  // position in the sub-batch: group bs / kFwdGroup
             d.tab = ws.btab + (bs / kFwdGroup) * (db->v_used * lw_b * kFwdGroup) + (bs % kFwdGroup) * lw_b;
             d.tab_rs = lw_b * kFwdGroup;
             d.tab_es = 1;
         } else if (grouped) {
-            const int64_t bs = i - j0;
+            const int64_t bs = p;
             d.tab = ws.btab + (bs / kFwdGroup) * (db->v_used * tk_b * kFwdGroup) + bs % kFwdGroup;
             d.tab_rs = tk_b * kFwdGroup;
             d.tab_es = kFwdGroup;
@@ -677,12 +689,12 @@ emd_status fill_descriptors(BatchWS& ws, int slot, emd_db* db, const int64_t* rp
             d.sel_val = ws.bsel_val + (int64_t)b * K;
             d.cand = ws.bcand + (int64_t)b * kPruneCap;
             d.cand_sym = ws.bcand_sym + (int64_t)b * 2 * kPruneCap;
-            d.cand_count = ws.bcand_count + (i - j0);  // position in the sub-batch: zeroed by its sequence
+            d.cand_count = ws.bcand_count + p;  // position in the sub-batch: zeroed by its sequence
             d.ok = ws.cand_ok + b;
         }
         if (meas == M_ICT) d.over = ws.ict_over + b;
         if (ws.fused) {
-            const int64_t bs = i - j0;  // position in the sub-batch
+            const int64_t bs = p;  // position in the sub-batch
             d.qpos = ws.bqpos + bs * db->v_used;
             d.rmap = ws.brmap + bs * db->v_used;
             d.crows = ws.bcrows + bs * kCandRows;

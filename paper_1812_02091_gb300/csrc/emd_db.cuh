@@ -79,6 +79,7 @@ namespace emd {
 struct BatchWS {
     static constexpr int kDescRing = 4;
     int max_batch = 0;
+    std::vector<int64_t> order;   // host: query of each descriptor position (fill_descriptors)
     int64_t b_cols = 0, b_qrows = 0, b_prows = 0, b_tabcols = 0;
     float* bD = nullptr;          // v_used x b_cols: the batch's distance matrices side by side
     float* bQ = nullptr;          // b_qrows x ldm
