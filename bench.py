@@ -307,6 +307,11 @@ def recall_against(top_idx, top_dist, gpu_idx, gpu_dist, extra, K):
     return hits / K, err
 
 
+def pair_opt(args):
+    """--tc-pair as a database option (nothing when left to the library's default)."""
+    return {} if getattr(args, "tc_pair", None) is None else {"tc_pair": args.tc_pair}
+
+
 def bench_config(args, world):
     """The `config` of the bench line, the same for both arms."""
     return {"workload": WORKLOAD5, "measure": f"LC-ACT k={args.k} (Alg. 3 top-k width)",
@@ -341,6 +346,9 @@ def main():
     ap.add_argument("--probe", action="store_true",
                     help="small fixed case for profiler captures: workload 2's database, --batch "
                          "queries per batch (16 suggested), --warmup + --steps batches, ~1.5 GB on the device")
+    ap.add_argument("--tc-pair", type=int, default=None,
+                    help="fused FP32_TC table on SM pairs: 0 off, 1 64-column tiles, 2 128-column tiles "
+                         "(default: the library's default)")
     ap.add_argument("--probe-h", type=int, default=128,
                     help="--probe: largest h_q of the probe queries (128: one column tile each; 1024: the whole "
                          "workload-2 query law, batch workspace of 16384 columns)")
@@ -420,7 +428,7 @@ def main_bench(args, rank, world, local):
 
     def make_db(prec):
         return emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
-                                 emd.emd_db_options_default(precision=prec, **opts))
+                                 emd.emd_db_options_default(precision=prec, **opts, **pair_opt(args)))
 
     def run_steps(handle, steps, profile=False):
         """Warm up, then time `steps` batches with CUDA events on the launch stream, L2
@@ -552,7 +560,7 @@ def main_bench(args, rank, world, local):
         w2 = emd_synth.config(2)
         h2 = emd.emd_db_create(w2.emb, None, w2.db.row_ptr, w2.db.col, w2.db.val,
                                emd.emd_db_options_default(precision=args.precision, device=local, max_query_h=2048,
-                                                          max_batch=args.batch))
+                                                          max_batch=args.batch, **pair_opt(args)))
         b2 = batches_for(np.arange(w2.queries.n), args.batch, args.warmup + args.w2_steps)
         d2 = []
         for b in b2:
@@ -728,7 +736,7 @@ def main_probe(args, local):
     B = args.batch
     db = emd.emd_db_create(w.emb, None, w.db.row_ptr, w.db.col, w.db.val,
                            emd.emd_db_options_default(precision=args.precision, device=local, max_query_h=1024,
-                                                      max_batch=B, autotune=0,
+                                                      max_batch=B, autotune=0, **pair_opt(args),
                                                       batch_columns=max(B * 128, 1024) if args.probe_h <= 128
                                                       else max(B * 128, 16384)))
     stream = torch.cuda.current_stream()

@@ -124,6 +124,11 @@ typedef struct {
                                 table rows, four entries loaded up front; 3 the first two entries up
                                 front, column ids and weights read 32 at a time; 4 as 1 with each
                                 lane's next column ids and weights read ahead.  Same results */
+    int32_t tc_pair;         /* the fused FP32_TC table (fused_phase1 >= 1) on clusters of two SMs
+                                (tcgen05 cta_group::2: 256 vocabulary rows per product, each SM
+                                staging half of each query chunk): 0 (default) one SM per tile;
+                                1 pairs with 64-column tiles; 2 pairs with 128-column tiles.
+                                Same results */
 } emd_db_options;
 
 typedef struct {
@@ -137,6 +142,7 @@ typedef struct {
     int32_t tc_stages;              /* its query-chunk stages (0: as many as fit) */
     int32_t rev_warps;              /* pruned reverse pass: warps per candidate document */
     int32_t fwd_kernel;             /* the batched forward sweep's form (1..4, see emd_db_options) */
+    int32_t tc_pair;                /* the fused table's SM-pair form in use (0..2, see emd_db_options) */
 } emd_db_info;
 
 /* A batch of query histograms in CSR form: query i has bins

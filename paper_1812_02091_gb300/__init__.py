@@ -46,14 +46,15 @@ class emd_db_options(ctypes.Structure):
                 ("max_table_k", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("prune_topk", ctypes.c_int32), ("lanes", ctypes.c_int32), ("batched", ctypes.c_int32),
                 ("batch_columns", ctypes.c_int32), ("graphs", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("fused_phase1", ctypes.c_int32), ("fwd_kernel", ctypes.c_int32)]
+                ("fused_phase1", ctypes.c_int32), ("fwd_kernel", ctypes.c_int32), ("tc_pair", ctypes.c_int32)]
 
 
 class emd_db_info(ctypes.Structure):
     _fields_ = [("v", ctypes.c_int64), ("v_used", ctypes.c_int64), ("n_docs", ctypes.c_int64),
                 ("nnz", ctypes.c_int64), ("m", ctypes.c_int32), ("cost_matrix_mode", ctypes.c_int32),
                 ("device_bytes", ctypes.c_int64), ("autotuned", ctypes.c_int32), ("tc_group_mult", ctypes.c_int32),
-                ("tc_stages", ctypes.c_int32), ("rev_warps", ctypes.c_int32), ("fwd_kernel", ctypes.c_int32)]
+                ("tc_stages", ctypes.c_int32), ("rev_warps", ctypes.c_int32), ("fwd_kernel", ctypes.c_int32),
+                ("tc_pair", ctypes.c_int32)]
 
 
 class emd_queries(ctypes.Structure):

@@ -101,6 +101,13 @@ cudaEvent_t take_event(emd_db* db)
 // Whether a batch's forward tables are interleaved in groups of kFwdGroup queries (one CSR
 // sweep per group): register-width tables, and ICT tables (the loop form) when a group of
 // them fits the workspace's table columns.
+// The fused FP32_TC table runs on SM pairs when the option asks for it and the panel fits.
+bool use_tc_pair(const emd_db* db)
+{
+    return db->opt.tc_pair > 0 && db->tc && db->tcfmt == TC_SPLIT && !db->cost_mode && db->mpad % 256 == 0 &&
+           tc_table_pair_fits(db->kpad);
+}
+
 bool grouped_tables(const BatchWS& ws, int meas, int tk_b)
 {
     return tk_b > 0 && (tk_b <= 16 || (meas == M_ICT && (int64_t)kFwdGroup * tk_b <= ws.b_tabcols));
@@ -352,10 +359,17 @@ emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, i
         {
             Phase p(db, 1, 2, st);
             EMD_CUDA(launch_qpos_b(D_, nqd, B, db->vslot, db->v, true, st), "identical ids");
-            EMD_CUDA(launch_tc_table_batch(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
-                                           db->v_used, D_, nqd, B, db->kpad, db->approx ? kc_b : tk_b,
-                                           db->tune_group_mult, db->tune_stages, db->err, st),
-                     db->approx ? "Phase-1 candidates (tensor cores, fused)" : "Phase-1 table (tensor cores, fused)");
+            if (use_tc_pair(db))
+                EMD_CUDA(launch_tc_table_pair(db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used, db->v_used,
+                                              D_, nqd, B, db->kpad, tk_b, db->tune_group_mult,
+                                              db->opt.tc_pair == 1 ? 64 : 128, db->err, st),
+                         "Phase-1 table (tensor cores on SM pairs, fused)");
+            else
+                EMD_CUDA(launch_tc_table_batch(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
+                                               db->v_used, D_, nqd, B, db->kpad, db->approx ? kc_b : tk_b,
+                                               db->tune_group_mult, db->tune_stages, db->err, st),
+                         db->approx ? "Phase-1 candidates (tensor cores, fused)"
+                                    : "Phase-1 table (tensor cores, fused)");
         }
         if (db->approx) {
             // BF16: certified rows exact by construction; E4M3's rounding bound is too wide for a
@@ -931,6 +945,8 @@ emd_status read_device_errors(emd_db* db)
         cudaMemcpy(db->err, &zero, sizeof(int), cudaMemcpyHostToDevice);
         if (h_err & ERR_TIMEOUT)
             return fail(EMD_ERR_TIMEOUT, "a tensor-core pipeline wait exceeded its time limit");
+        if (h_err & ERR_PAIR_TMEM)
+            return fail(EMD_ERR_CUDA, "the SM-pair Phase-1 kernel found different TMEM addresses in a pair");
         return fail(EMD_ERR_INVALID_ARG, "a kernel met a vocabulary id outside 0..%lld", (long long)db->v - 1);
     }
     return EMD_OK;
@@ -1132,6 +1148,7 @@ void emd_db_options_default(emd_db_options* opt)
     opt->autotune = 1;
     opt->fused_phase1 = 1;
     opt->fwd_kernel = 0;
+    opt->tc_pair = 0;
 }
 
 emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* cost_matrix,
@@ -1161,6 +1178,7 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
     if (opt.fused_phase1 < 0 || opt.fused_phase1 > 2) return fail(EMD_ERR_INVALID_ARG, "fused_phase1 must be 0..2");
     if (opt.fwd_kernel < 0 || opt.fwd_kernel > kFwdVariants)
         return fail(EMD_ERR_INVALID_ARG, "fwd_kernel must be 0..%d", kFwdVariants);
+    if (opt.tc_pair < 0 || opt.tc_pair > 2) return fail(EMD_ERR_INVALID_ARG, "tc_pair must be 0..2");
     if ((opt.precision == EMD_PREC_BF16 || opt.precision == EMD_PREC_FP8_E4M3) && opt.max_query_h > 6400)
         return fail(EMD_ERR_INVALID_ARG, "max_query_h above 6400 with an approximate precision (the re-rank "
                                          "stages 32 bytes per query bin in shared memory)");
@@ -1287,7 +1305,7 @@ emd_status emd_db_create(const float* emb, int64_t v, int32_t m, const float* co
                                                           : TC_E4M3;
             db->approx = db->tcfmt != TC_SPLIT;
             db->kpad = (int)round_up(m, 64);
-            db->mpad = round_up(vu, 128);
+            db->mpad = round_up(vu, 256);  // whole row tiles of 128, and of 256 for the SM-pair form
             TRY(dalloc(db, &db->a_hi, db->mpad * db->kpad));
             if (db->tcfmt == TC_SPLIT) TRY(dalloc(db, &db->a_lo, db->mpad * db->kpad));
             TRY(dalloc(db, &db->a_scale, db->mpad));
@@ -1378,6 +1396,7 @@ emd_status emd_db_info_get(const emd_db* db, emd_db_info* out)
     out->tc_stages = db->tune_stages;
     out->rev_warps = db->tune_rev_warps;
     out->fwd_kernel = db->tune_fwd + 1;
+    out->tc_pair = use_tc_pair(db) ? db->opt.tc_pair : 0;
     return EMD_OK;
 }
 

@@ -23,7 +23,7 @@ __device__ __forceinline__ float sq_to_dist(float x) { return __fsqrt_rn(fmaxf(x
 __device__ __forceinline__ float d_value(float x, bool sq) { return sq ? sq_to_dist(x) : x; }
 
 // Device error latch bits (written by kernels, read by emd_db_check_device_errors).
-enum : int { ERR_BAD_INDEX = 1, ERR_TIMEOUT = 2 };
+enum : int { ERR_BAD_INDEX = 1, ERR_TIMEOUT = 2, ERR_PAIR_TMEM = 4 };
 
 // Distance-matrix tiling of the FP32 SIMT kernel.
 constexpr int kDistBM = 128;
@@ -271,6 +271,12 @@ cudaError_t launch_zero_ident_b(const QDesc* qd, const int* nq, int max_q, int m
 cudaError_t launch_qpos_b(const QDesc* qd, const int* nq, int max_q, const int32_t* vslot, int64_t v, bool set,
                           cudaStream_t st);
 // The table of every query (qd[q].tab, width qd[q].tk <= max_tk <= 16); format TC_SPLIT.
+// The fused table on clusters of two SMs (tcgen05 cta_group::2, M = 256 per product): FP16
+// split only; Mpad a multiple of 256; bn = 64 or 128 (the pair's largest column tile).
+bool tc_table_pair_fits(int Kpad);
+cudaError_t launch_tc_table_pair(const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
+                                 const float* a_norm, int64_t M, const QDesc* qd, const int* nq, int max_q, int Kpad,
+                                 int max_tk, int group_mult, int bn, int* err, cudaStream_t st);
 cudaError_t launch_tc_table_batch(int fmt, const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
                                   const float* a_norm, int64_t M, const QDesc* qd, const int* nq, int max_q, int Kpad,
                                   int max_tk, int group_mult, int stages, int* err, cudaStream_t st);

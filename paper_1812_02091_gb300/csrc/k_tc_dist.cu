@@ -710,9 +710,10 @@ constexpr int TCT_THREADS = 64 + 32 * 8;  // copy warp, MMA warp, two epilogue w
 // The interleaved two-stream tile order of one work item (every role walks it alike).
 // Scalar fields (no arrays indexed at run time, which would live in local memory).
 struct TileSeq {
-    int qb, nextq, cq0, cq1, c0, c1, turn;
-    __device__ __forceinline__ void init(int qa, int qb_)
+    int qb, nextq, cq0, cq1, c0, c1, turn, bn;
+    __device__ __forceinline__ void init(int qa, int qb_, int bn_ = TC_BN)
     {
+        bn = bn_;
         qb = qb_;
         nextq = qa;
         cq0 = cq1 = -1;
@@ -734,7 +735,7 @@ struct TileSeq {
                 q = cq;
                 n0 = c;
                 s = st;
-                c += TC_BN;
+                c += bn;
                 if (c >= qd[cq].h) cq = -1;
                 if (st) { cq1 = cq; c1 = c; } else { cq0 = cq; c0 = c; }
                 turn = st ^ 1;
@@ -1034,6 +1035,415 @@ k_tc_table_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, kCols);
+    }
+}
+
+// ------------------------------------------------------------------ fused table on SM pairs
+//
+// The fused Phase-1 table of k_tc_table_batch on a cluster of two CTAs (two SMs) issuing
+// tcgen05.mma.cta_group::2: M = 256 vocabulary rows per product, each CTA holding its own 128
+// rows in shared memory and its own TMEM accumulators, and half of each query chunk's columns
+// -- the pair's tensor cores read the other half from the peer CTA's shared memory.  Each SM
+// therefore stages half the query bytes per product of the single-CTA form, and twice as
+// many chunk stages fit beside the resident vocabulary panel; that ring, not the tensor pipe,
+// bounds the single-CTA form.  Per CTA the arithmetic of a row is unchanged (same operands,
+// K order, accumulator split and epilogue), so the tables are bit-identical to it.
+//
+// Roles in both CTAs: warp 0 lane 0 copies this CTA's vocabulary rows and its half of each
+// chunk; warp 1 allocates TMEM for the pair; warps 2..9 drain this CTA's accumulators (two
+// tile streams as in k_tc_table_batch).  In the leader (rank 0) warp 1 lane 0 issues the
+// pair's MMAs and commits to both CTAs' barriers; in the peer it forwards the completion of
+// its own copies to the leader (an arrive on the leader's barrier after its local wait).  The
+// peer's epilogue warps release an accumulator with arrives on the leader's barrier.  Every
+// wait is bounded; both CTAs meet at a cluster barrier before TMEM is released and before
+// either exits, so no remote arrive targets a finished CTA.
+constexpr int TCP_THREADS = 64 + 32 * 8;
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Shared::cluster address of the same shared-memory object in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// A wait on a barrier that the peer CTA arrives on (acquire at cluster scope).
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, uint64_t deadline)
+{
+    while (!mbar_try_wait_cluster(bar, parity))
+        if (global_ns() > deadline) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t* slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void mma_issue_pair(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                               uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrive on the barrier at this offset in both CTAs once the pair's MMAs so far are done.
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"((uint16_t)3)
+        : "memory");
+}
+
+// BN: the pair's largest column tile (64 or 128); each CTA stages BN / 2 columns of a chunk.
+template <int KT, int BN>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TCP_THREADS, 1)
+k_tc_table_pair(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_lo, int64_t Mpad,
+                const float* __restrict__ a_scale, const float* __restrict__ a_norm, int64_t M,
+                const QDesc* __restrict__ qd, const int* __restrict__ nq_dev, int groups, int KC, int stages,
+                int* __restrict__ err)
+{
+    constexpr uint32_t EB = 128;  // FP16 split: bytes of a 64-element row segment
+    constexpr uint32_t kABytes = TC_BM * EB;
+    constexpr uint32_t kBBytes = (BN / 2) * EB;
+    constexpr uint32_t kSbo = 8 * EB;
+    constexpr uint32_t kAChunk = 2 * kABytes;
+    constexpr uint32_t kBStage = 2 * kBBytes;
+    constexpr uint32_t kAcc = 2 * BN;  // per stream: hi.hi, then the cross terms
+    constexpr uint32_t kCols = 2 * kAcc;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* apanel = smem;
+    uint8_t* bring = apanel + (size_t)KC * kAChunk;
+    uint64_t* full = reinterpret_cast<uint64_t*>(bring + (size_t)stages * kBStage);  // own copies landed
+    uint64_t* pfull = full + stages;    // leader: the peer's copies of the stage landed
+    uint64_t* empty = pfull + stages;   // the pair's MMAs on the stage done (both CTAs)
+    uint64_t* tfull = empty + stages;   // [2] stream s's accumulators ready (both CTAs)
+    uint64_t* tempty = tfull + 2;       // [2] leader: stream s drained by 8 warps of the pair
+    uint64_t* afull = tempty + 2;       // own vocabulary rows landed
+    uint64_t* pafull = afull + 1;       // leader: the peer's rows landed
+    uint64_t* afree = pafull + 1;       // the pair's MMAs on the item done (both CTAs)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(afree + 1);
+    uint32_t* peer_tmem = tmem_slot + 1;  // leader: the peer's TMEM address
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(peer_tmem + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const int nq = *nq_dev;
+    const int pairs = (int)(Mpad / (2 * TC_BM));
+    const int total = pairs * groups;
+    const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&pfull[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 8);
+        }
+        mbar_init(afull, 1);
+        mbar_init(pafull, 1);
+        mbar_init(afree, 1);
+        *peer_tmem = 0xFFFFFFFFu;
+        *abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) tmem_alloc_pair(tmem_slot, kCols);
+    tc_fence_before();
+    cluster_sync_all();  // barriers of both CTAs initialised, TMEM allocated in both
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    // the pair must hold its accumulators at the same TMEM address: each CTA hands its own to
+    // the other, and both skip every role (issuing nothing) when they differ
+    if (threadIdx.x == 0) {
+        const uint32_t dst = peer_addr(peer_tmem, rank ^ 1u);
+        asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(dst), "r"(tmem) : "memory");
+    }
+    cluster_sync_all();
+    const bool pair_ok = *peer_tmem == tmem;
+    if (!pair_ok && threadIdx.x == 0 && rank == 0) atomicOr(err, ERR_PAIR_TMEM);
+
+    auto fail = [&]() {
+        atomicOr(err, ERR_TIMEOUT);
+        *abort_flag = 1;
+    };
+    auto qrange = [&](int g, int& qa, int& qb) {
+        qa = (int)((int64_t)g * nq / groups);
+        qb = (int)((int64_t)(g + 1) * nq / groups);
+    };
+    if (warp == 0 && lane == 0 && pair_ok) {
+        int64_t gb = 0;
+        int items = 0;
+        bool ok = true;
+        for (int w = cid; w < total && ok && !*abort_flag; w += ncl, ++items) {
+            const int64_t m0 = (int64_t)(w % pairs) * (2 * TC_BM) + (int64_t)rank * TC_BM;
+            if (items > 0 && !mbar_wait_cluster(afree, (uint32_t)(items - 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                fail();
+                break;
+            }
+            mbar_expect_tx(afull, (uint32_t)KC * kAChunk);
+            for (int c = 0; c < KC; ++c) {
+                uint8_t* ast = apanel + (size_t)c * kAChunk;
+                bulk_g2s(ast, A_hi + ((int64_t)c * Mpad + m0) * EB, kABytes, afull);
+                bulk_g2s(ast + kABytes, A_lo + ((int64_t)c * Mpad + m0) * EB, kABytes, afull);
+            }
+            int qa, qb, q, n0, s;
+            qrange(w / pairs, qa, qb);
+            TileSeq ts;
+            ts.init(qa, qb, BN);
+            while (ok && ts.next(qd, q, n0, s)) {
+                const QDesc& d = qd[q];
+                const int Nt = min(BN, (int)round_up(d.h - n0, 16));
+                const int nh = Nt >> 1;  // this CTA's columns: n0 + rank * nh ..
+                const uint32_t b_bytes = (uint32_t)nh * EB;
+                const int64_t c0 = n0 + (int64_t)rank * nh;
+                const uint8_t* bh = static_cast<const uint8_t*>(d.q_hi);
+                const uint8_t* bl = static_cast<const uint8_t*>(d.q_lo);
+                for (int c = 0; c < KC; ++c, ++gb) {
+                    const int st = (int)(gb % stages);
+                    if (gb >= stages && !mbar_wait_cluster(&empty[st], (uint32_t)((gb / stages) - 1) & 1u,
+                                                           global_ns() + TC_TIMEOUT_NS)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* bst = bring + (size_t)st * kBStage;
+                    mbar_expect_tx(&full[st], 2u * b_bytes);
+                    bulk_g2s(bst, bh + ((int64_t)c * d.npad + c0) * EB, b_bytes, &full[st]);
+                    bulk_g2s(bst + kBBytes, bl + ((int64_t)c * d.npad + c0) * EB, b_bytes, &full[st]);
+                }
+            }
+        }
+        const uint64_t tail = global_ns() + TC_TIMEOUT_NS;
+        for (int64_t c = gb > stages ? gb - stages : 0; c < gb; ++c)
+            if (!mbar_wait(&full[c % stages], (uint32_t)(c / stages) & 1u, tail)) atomicOr(err, ERR_TIMEOUT);
+        if (items > 0 && !mbar_wait(afull, (uint32_t)(items - 1) & 1u, tail)) atomicOr(err, ERR_TIMEOUT);
+    } else if (warp == 1 && lane == 0 && rank == 1 && pair_ok) {
+        // peer: forward the completion of its own copies to the leader, in the copy order
+        const uint32_t r_pfull = peer_addr(pfull, 0), r_pafull = peer_addr(pafull, 0);
+        int64_t gb = 0;
+        int items = 0;
+        bool ok = true;
+        for (int w = cid; w < total && ok && !*abort_flag; w += ncl, ++items) {
+            if (!mbar_wait(afull, (uint32_t)items & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                fail();
+                break;
+            }
+            mbar_arrive_cluster(r_pafull);
+            int qa, qb, q, n0, s;
+            qrange(w / pairs, qa, qb);
+            TileSeq ts;
+            ts.init(qa, qb, BN);
+            while (ok && ts.next(qd, q, n0, s)) {
+                for (int c = 0; c < KC; ++c, ++gb) {
+                    const int st = (int)(gb % stages);
+                    if (!mbar_wait(&full[st], (uint32_t)(gb / stages) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_cluster(r_pfull + (uint32_t)st * 8u);
+                }
+            }
+        }
+    } else if (warp == 1 && lane == 0 && rank == 0 && pair_ok) {
+        int64_t gb = 0;
+        int cnt0 = 0, cnt1 = 0, items = 0;  // tiles issued per stream
+        bool ok = true;
+        for (int w = cid; w < total && ok && !*abort_flag; w += ncl, ++items) {
+            if (!mbar_wait(afull, (uint32_t)items & 1u, global_ns() + TC_TIMEOUT_NS) ||
+                !mbar_wait_cluster(pafull, (uint32_t)items & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                fail();
+                break;
+            }
+            int qa, qb, q, n0, s;
+            qrange(w / pairs, qa, qb);
+            TileSeq ts;
+            ts.init(qa, qb, BN);
+            while (ok && ts.next(qd, q, n0, s)) {
+                const int Nt = min(BN, (int)round_up(qd[q].h - n0, 16));
+                const uint32_t idesc = (1u << 4) | ((uint32_t)(Nt >> 3) << 17) | ((uint32_t)((2 * TC_BM) >> 4) << 24);
+                const int cs = s ? cnt1 : cnt0;
+                if (cs >= 1 &&
+                    !mbar_wait_cluster(&tempty[s], (uint32_t)(cs - 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                    fail();
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t acc0 = tmem + (uint32_t)s * kAcc;
+                for (int c = 0; c < KC; ++c, ++gb) {
+                    const int st = (int)(gb % stages);
+                    if (!mbar_wait(&full[st], (uint32_t)(gb / stages) & 1u, global_ns() + TC_TIMEOUT_NS) ||
+                        !mbar_wait_cluster(&pfull[st], (uint32_t)(gb / stages) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(apanel + (size_t)c * kAChunk);
+                    const uint32_t sa_lo = sa + kABytes;
+                    const uint32_t sb = smem_u32(bring + (size_t)st * kBStage);
+                    const uint32_t sb_lo = sb + kBBytes;
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {
+                        const uint32_t ko = (uint32_t)ks * 256u;
+                        const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+                        const uint64_t da = smem_desc(sa + ko, kSbo), db = smem_desc(sb + ko, kSbo);
+                        mma_issue_pair(acc0, da, db, idesc, acc);
+                        mma_issue_pair(acc0 + BN, da, smem_desc(sb_lo + ko, kSbo), idesc, acc);
+                        mma_issue_pair(acc0 + BN, smem_desc(sa_lo + ko, kSbo), db, idesc, 1u);
+                    }
+                    mma_commit_pair(&empty[st]);
+                }
+                if (!ok) break;
+                mma_commit_pair(&tfull[s]);
+                if (s) ++cnt1; else ++cnt0;
+            }
+            mma_commit_pair(afree);
+        }
+    } else if (warp >= 2 && pair_ok) {
+        // epilogue: warpgroup sme = stream sme; warp w reads TMEM lane quarter w % 4
+        const int qw4 = warp & 3;
+        const int sme = (warp - 2) >> 2;
+        const int row = qw4 * 32 + lane;
+        const uint32_t r_tempty = rank == 0 ? smem_u32(&tempty[sme]) : peer_addr(&tempty[sme], 0);
+        int cnt = 0;
+        bool ok = true;
+        float z[KT];
+        int sj[KT];
+        int jstar = -1;
+        for (int w = cid; w < total && ok && !*abort_flag; w += ncl) {
+            const int64_t m0 = (int64_t)(w % pairs) * (2 * TC_BM) + (int64_t)rank * TC_BM;
+            const int64_t u = m0 + row;
+            const bool row_ok = u < M;
+            const float su = row_ok ? a_scale[u] : 0.f;
+            const float nu = row_ok ? a_norm[u] : 0.f;
+            int qa, qb, q, n0, s;
+            qrange(w / pairs, qa, qb);
+            TileSeq ts;
+            ts.init(qa, qb, BN);
+            while (ok && ts.next(qd, q, n0, s)) {
+                if (s != sme) continue;
+                const QDesc& d = qd[q];
+                const int N = d.h;
+                const int Nt = min(BN, (int)round_up(N - n0, 16));
+                if (n0 == 0) {
+#pragma unroll
+                    for (int l = 0; l < KT; ++l) {
+                        z[l] = INFINITY;
+                        sj[l] = INT32_MAX;
+                    }
+                    // the query bin of this row's own vocabulary id, if any: its squared distance is 0
+                    jstar = row_ok ? d.qpos[u] : -1;
+                }
+                // lane l holds the constants of columns n0 + 32 c + l, broadcast by shuffles
+                float cbl[BN / 32], nbl[BN / 32];
+#pragma unroll
+                for (int c4 = 0; c4 < BN / 32; ++c4) {
+                    const int col = n0 + 32 * c4 + lane;
+                    const bool cok = col < N;
+                    cbl[c4] = cok ? -2.f * d.q_scale[col] : 0.f;
+                    nbl[c4] = cok ? d.qnorm[col] : 0.f;
+                }
+                if (!mbar_wait_cluster(&tfull[sme], (uint32_t)cnt & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                    fail();
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tbase = tmem + (uint32_t)sme * kAcc + ((uint32_t)(qw4 * 32) << 16);
+#pragma unroll
+                for (int cc = 0; cc < BN; cc += 16) {
+                    if (cc < Nt) {
+                        uint32_t r0[16], r1[16];
+                        tmem_ld16(tbase + (uint32_t)cc, r0);
+                        tmem_ld16(tbase + (uint32_t)BN + (uint32_t)cc, r1);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const int jc = cc + e;
+                            const float cb = __shfl_sync(0xffffffffu, cbl[jc >> 5], jc & 31);
+                            const float nb = __shfl_sync(0xffffffffu, nbl[jc >> 5], jc & 31);
+                            float dot = __uint_as_float(r0[e]);
+                            dot = fmaf(__uint_as_float(r1[e]), 1.0f / 2048.0f, dot);
+                            const int j = n0 + jc;
+                            float d2 = fmaf(cb * su, dot, nu + nb);  // as k_tc_dist_batch writes it
+                            d2 = j == jstar ? 0.f : d2;
+                            if (j < N && d2 < z[KT - 1]) tc_insert<KT>(z, sj, d2, j);
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(r_tempty);
+                ++cnt;
+                if (n0 + BN >= N && row_ok) {  // the query's last tile: write its table row
+#pragma unroll
+                    for (int l = 0; l < KT; ++l) {
+                        if (l < d.tk) {
+                            const bool valid = sj[l] != INT32_MAX;
+                            d.tab[u * d.tab_rs + (int64_t)l * d.tab_es] =
+                                make_float2(valid ? sq_to_dist(z[l]) : INFINITY, valid ? d.qw[sj[l]] : 0.f);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();  // no remote arrive may reach a CTA that has left
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem, kCols);
     }
 }
 
@@ -1585,6 +1995,65 @@ cudaError_t launch_tc_table_batch(int fmt, const void* A_hi, const void* A_lo, i
     if (max_tk <= 8) EMD_TT(8);
     EMD_TT(16);
 #undef EMD_TT
+}
+
+static size_t tcp_smem_bytes(int bn, int stages, int KC)
+{
+    return 1024 + (size_t)KC * 2 * TC_BM * 128 + (size_t)stages * 2 * (bn / 2) * 128 + (3 * (size_t)stages + 7) * 8 +
+           16;
+}
+
+static int tcp_stages(int bn, int KC)
+{
+    const size_t budget = 227 * 1024;
+    int s = 8;
+    while (s >= 2 && tcp_smem_bytes(bn, s, KC) > budget) --s;
+    return s >= 2 ? s : 0;
+}
+
+bool tc_table_pair_fits(int Kpad) { return tcp_stages(128, Kpad / 64) >= 2 && tcp_stages(64, Kpad / 64) >= 2; }
+
+template <int KT, int BN>
+static cudaError_t tc_pair_launch(dim3 grid, size_t smem, cudaStream_t st, const void* A_hi, const void* A_lo,
+                                  int64_t Mpad, const float* a_scale, const float* a_norm, int64_t M, const QDesc* qd,
+                                  const int* nq, int groups, int KC, int stages, int* err)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_tc_table_pair<KT, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_tc_table_pair<KT, BN><<<grid, TCP_THREADS, smem, st>>>(static_cast<const uint8_t*>(A_hi),
+                                                             static_cast<const uint8_t*>(A_lo), Mpad, a_scale, a_norm,
+                                                             M, qd, nq, groups, KC, stages, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_table_pair(const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
+                                 const float* a_norm, int64_t M, const QDesc* qd, const int* nq, int max_q, int Kpad,
+                                 int max_tk, int group_mult, int bn, int* err, cudaStream_t st)
+{
+    if (M <= 0 || max_q <= 0) return cudaSuccess;
+    if (max_tk < 1 || max_tk > 16 || (bn != 64 && bn != 128) || Mpad % (2 * TC_BM) != 0)
+        return cudaErrorInvalidValue;
+    const int KC = Kpad / 64;
+    const int stages = tcp_stages(bn, KC);
+    if (stages < 2) return cudaErrorInvalidValue;
+    const size_t smem = tcp_smem_bytes(bn, stages, KC);
+    const int pairs = (int)(Mpad / (2 * TC_BM));
+    const int clusters_max = std::max(1, sm_count() / 2);
+    const int groups =
+        std::max(1, std::min(max_q, std::max(1, group_mult) * ((2 * clusters_max + pairs - 1) / pairs)));
+    const dim3 grid((unsigned)(2 * std::min<int64_t>((int64_t)pairs * groups, clusters_max)));
+#define EMD_TP(KT)                                                                                                    \
+    return bn == 64 ? tc_pair_launch<KT, 64>(grid, smem, st, A_hi, A_lo, Mpad, a_scale, a_norm, M, qd, nq, groups, KC, \
+                                             stages, err)                                                              \
+                    : tc_pair_launch<KT, 128>(grid, smem, st, A_hi, A_lo, Mpad, a_scale, a_norm, M, qd, nq, groups,    \
+                                              KC, stages, err)
+    if (max_tk <= 1) EMD_TP(1);
+    if (max_tk <= 2) EMD_TP(2);
+    if (max_tk <= 4) EMD_TP(4);
+    if (max_tk <= 8) EMD_TP(8);
+    EMD_TP(16);
+#undef EMD_TP
 }
 
 cudaError_t launch_cand_pack_b(const QDesc* qd, const int* nq, int max_q, const void* a_hi, const void* a_lo,
