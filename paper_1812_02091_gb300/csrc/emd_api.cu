@@ -581,7 +581,7 @@ emd_status alloc_batch_ws(emd_db* db, BatchWS& ws, int max_batch, int64_t cols, 
     TRYW(dal(&ws.qd_dev, BatchWS::kDescRing * B));
     TRYW(dal(&ws.nq_dev, BatchWS::kDescRing));
     ws.fused = db->tc && !db->cost_mode && db->opt.fused_phase1 >= (db->approx ? 2 : 1) && db->as_hi != nullptr &&
-               tc_batch_stages(db->tcfmt, db->kpad / 64) >= 2 && tc_batch_stages(TC_SPLIT, db->kpad / 64) >= 2;
+               tc_table_fits(db->tcfmt, db->kpad) && tc_batch_stages(TC_SPLIT, db->kpad / 64) >= 2;
     if (ws.fused) {
         TRYW(dal(&ws.bqpos, B * vu));
         TRYW(dal(&ws.brmap, B * vu));

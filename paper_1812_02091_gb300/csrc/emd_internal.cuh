@@ -274,6 +274,8 @@ cudaError_t launch_qpos_b(const QDesc* qd, const int* nq, int max_q, const int32
 // The fused table on clusters of two SMs (tcgen05 cta_group::2, M = 256 per product): FP16
 // split only; Mpad a multiple of 256; bn = 64 or 128 (the pair's largest column tile).
 bool tc_table_pair_fits(int Kpad);
+// The one-SM fused table kernel fits beside this panel width (format fmt).
+bool tc_table_fits(int fmt, int Kpad);
 cudaError_t launch_tc_table_pair(const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
                                  const float* a_norm, int64_t M, const QDesc* qd, const int* nq, int max_q, int Kpad,
                                  int max_tk, int group_mult, int bn, int* err, cudaStream_t st);

@@ -199,6 +199,22 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// 32 consecutive TMEM columns of this thread's lane from registers (32x32b shape).
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+        "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+        "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+        "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -705,7 +721,7 @@ k_tc_dist_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
 // lives in one thread for the whole query: no merge across threads.  A thread sees its
 // row's columns in increasing bin order and inserts only strictly smaller values, so ties
 // keep the lower bin -- the order the table kernel applies to the matrix.
-constexpr int TCT_THREADS = 64 + 32 * 8;  // copy warp, MMA warp, two epilogue warpgroups
+constexpr int TCT_THREADS = 64 + 32 * 16;  // copy warp, MMA warp, two epilogue warpgroups per stream
 
 // The interleaved two-stream tile order of one work item (every role walks it alike).
 // Scalar fields (no arrays indexed at run time, which would live in local memory).
@@ -763,6 +779,23 @@ __device__ __forceinline__ void tc_insert(float (&z)[KT], int (&s)[KT], float d,
     s[0] = p[0] ? j : s[0];
 }
 
+// Insertion by (value, bin): merging two lists whose bins interleave keeps the k smallest
+// pairs of their union, the set a scan of all columns in bin order keeps.
+template <int KT>
+__device__ __forceinline__ void tc_insert_key(float (&z)[KT], int (&s)[KT], float d, int j)
+{
+    bool p[KT];
+#pragma unroll
+    for (int l = 0; l < KT; ++l) p[l] = d < z[l] || (d == z[l] && j < s[l]);
+#pragma unroll
+    for (int l = KT - 1; l > 0; --l) {
+        z[l] = p[l - 1] ? z[l - 1] : (p[l] ? d : z[l]);
+        s[l] = p[l - 1] ? s[l - 1] : (p[l] ? j : s[l]);
+    }
+    z[0] = p[0] ? d : z[0];
+    s[0] = p[0] ? j : s[0];
+}
+
 // CAND (approximate formats): instead of the table, each row's kc = qd[q].kc smallest
 // approximate values are kept and written as candidate bins (cbin, kCandPerRow per row)
 // with the kc-th approximate value (camax; +inf when every bin is a candidate), for the
@@ -794,7 +827,8 @@ k_tc_table_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A
     uint64_t* tempty = tfull + 2;       // [2] stream s's accumulator drained (4 warps)
     uint64_t* afull = tempty + 2;
     uint64_t* afree = afull + 1;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(afree + 1);
+    uint64_t* xbar = afree + 1;         // [2][4] per stream and lane quarter: the upper half's list is in TMEM
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(xbar + 8);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -809,10 +843,11 @@ k_tc_table_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 4);
+            mbar_init(&tempty[b], 8);
         }
         mbar_init(afull, 1);
         mbar_init(afree, 1);
+        for (int x = 0; x < 8; ++x) mbar_init(&xbar[x], 1);
         *abort_flag = 0;
         mbar_fence_init();
     }
@@ -933,14 +968,20 @@ k_tc_table_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A
             mma_commit(afree);
         }
     } else if (warp >= 2) {
-        // epilogue: warpgroup sme = stream sme; warp w reads TMEM lane quarter w % 4
+        // epilogue: stream sme = warps 2 + 8 sme .. 9 + 8 sme; warp w reads TMEM lane quarter
+        // w % 4; the lower four take columns 0..63 of each tile, the upper four 64..127
+        const int ew = warp - 2;
         const int qw4 = warp & 3;
-        const int sme = (warp - 2) >> 2;
+        const int sme = ew >> 3;
+        const int half = (ew >> 2) & 1;
+        const int cb0 = half * (TC_BN / 2);
         const int row = qw4 * 32 + lane;
-        int cnt = 0;
+        uint64_t* xb = &xbar[sme * 4 + qw4];
+        int cnt = 0, nx = 0;
         bool ok = true;
         float z[KT];
         int sj[KT];
+        int jstar = -1;
         for (int w = blockIdx.x; w < total && ok && !*abort_flag; w += gridDim.x) {
             const int64_t m0 = (int64_t)(w % m_tiles) * TC_BM;
             const int64_t u = m0 + row;
@@ -962,17 +1003,17 @@ k_tc_table_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A
                         z[l] = INFINITY;
                         sj[l] = INT32_MAX;
                     }
+                    // the query bin of this row's own vocabulary id, if any: its squared distance is 0
+                    jstar = row_ok ? d.qpos[u] : -1;
                 }
-                // the query bin of this row's own vocabulary id, if any: its squared distance is 0
-                const int jstar = row_ok ? d.qpos[u] : -1;
-                // lane l holds the constants of columns n0 + 32 c + l, broadcast by shuffles
-                float cbl[4], nbl[4];
+                // lane l holds the constants of columns n0 + cb0 + 32 c + l, broadcast by shuffles
+                float cbl[2], nbl[2];
 #pragma unroll
-                for (int c4 = 0; c4 < 4; ++c4) {
-                    const int col = n0 + 32 * c4 + lane;
+                for (int c2 = 0; c2 < 2; ++c2) {
+                    const int col = n0 + cb0 + 32 * c2 + lane;
                     const bool cok = col < N;
-                    cbl[c4] = cok ? -2.f * d.q_scale[col] : 0.f;
-                    nbl[c4] = cok ? d.qnorm[col] : 0.f;
+                    cbl[c2] = cok ? -2.f * d.q_scale[col] : 0.f;
+                    nbl[c2] = cok ? d.qnorm[col] : 0.f;
                 }
                 if (!mbar_wait(&tfull[sme], (uint32_t)cnt & 1u, global_ns() + TC_TIMEOUT_NS)) {
                     fail();
@@ -982,11 +1023,11 @@ k_tc_table_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A
                 tc_fence_after();
                 const uint32_t tbase = tmem + (uint32_t)sme * kAcc + ((uint32_t)(qw4 * 32) << 16);
 #pragma unroll
-                for (int cc = 0; cc < TC_BN; cc += 16) {
-                    if (cc < Nt) {
+                for (int cc = 0; cc < TC_BN / 2; cc += 16) {
+                    if (cb0 + cc < Nt) {
                         uint32_t r0[16], r1[16];
-                        tmem_ld16(tbase + (uint32_t)cc, r0);
-                        if (SPLIT) tmem_ld16(tbase + 128u + (uint32_t)cc, r1);
+                        tmem_ld16(tbase + (uint32_t)(cb0 + cc), r0);
+                        if (SPLIT) tmem_ld16(tbase + 128u + (uint32_t)(cb0 + cc), r1);
                         tmem_wait_ld();
 #pragma unroll
                         for (int e = 0; e < 16; ++e) {
@@ -995,18 +1036,51 @@ k_tc_table_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A
                             const float nb = __shfl_sync(0xffffffffu, nbl[jc >> 5], jc & 31);
                             float dot = __uint_as_float(r0[e]);
                             if (SPLIT) dot = fmaf(__uint_as_float(r1[e]), 1.0f / 2048.0f, dot);
-                            const int j = n0 + jc;
+                            const int j = n0 + cb0 + jc;
                             float d2 = fmaf(cb * su, dot, nu + nb);  // as k_tc_dist_batch writes it
                             d2 = j == jstar ? 0.f : d2;
                             if (j < N && d2 < z[KT - 1]) tc_insert<KT>(z, sj, d2, j);
                         }
                     }
                 }
+                const bool last = n0 + TC_BN >= N;
+                if (last && N > TC_BN / 2) {
+                    // the query's last tile: the upper half hands its list to the lower half
+                    // through its own (already drained) TMEM columns cb0 .. cb0 + 31
+                    if (half == 1) {
+                        uint32_t x[32];
+#pragma unroll
+                        for (int l = 0; l < 16; ++l) {
+                            x[l] = __float_as_uint(l < KT ? z[l < KT ? l : 0] : INFINITY);
+                            x[16 + l] = (uint32_t)(l < KT ? sj[l < KT ? l : 0] : INT32_MAX);
+                        }
+                        tmem_st32(tbase + (uint32_t)cb0, x);
+                        tmem_wait_st();
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(xb);
+                    } else {
+                        if (!mbar_wait(xb, (uint32_t)nx & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                            fail();
+                            ok = false;
+                        } else {
+                            tc_fence_after();
+                            uint32_t x[32];
+                            tmem_ld32(tbase + (uint32_t)(TC_BN / 2), x);
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int l = 0; l < KT; ++l)
+                                tc_insert_key<KT>(z, sj, __uint_as_float(x[l]), (int)x[16 + l]);
+                        }
+                    }
+                    ++nx;
+                }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[sme]);
                 ++cnt;
-                if (n0 + TC_BN >= N && row_ok) {  // the query's last tile: write its table row
+                if (!ok) break;
+                if (last && half == 0 && row_ok) {  // write the query's table row
                     if (CAND) {
                         const int kc = d.kc;
 #pragma unroll
@@ -1877,6 +1951,17 @@ int tc_batch_stages(int fmt, int KC)
     return s >= 2 ? s : 0;
 }
 
+// The fused table kernel: the matrix kernel's layout plus eight list-exchange barriers.
+static size_t tct_smem_bytes(int fmt, int stages, int KC) { return tc_batch_smem_bytes(fmt, stages, KC) + 8 * 8; }
+
+static int tct_stages(int fmt, int KC)
+{
+    const size_t budget = 227 * 1024;
+    int s = 8;
+    while (s >= 2 && tct_smem_bytes(fmt, s, KC) > budget) --s;
+    return s >= 2 ? s : 0;
+}
+
 template <int FMT>
 static cudaError_t tc_batch_launch(dim3 grid, size_t smem, cudaStream_t st, const void* A_hi, const void* A_lo,
                                    int64_t Mpad, const float* a_scale, const float* a_norm,
@@ -1970,10 +2055,10 @@ cudaError_t launch_tc_table_batch(int fmt, const void* A_hi, const void* A_lo, i
     if (M <= 0 || max_q <= 0) return cudaSuccess;
     if (max_tk < 1 || max_tk > 16) return cudaErrorInvalidValue;
     const int KC = Kpad / 64;
-    const int fit = tc_batch_stages(fmt, KC);
+    const int fit = tct_stages(fmt, KC);
     if (fit < 2) return cudaErrorInvalidValue;
     const int stages = stages_req >= 2 ? std::min(stages_req, fit) : fit;
-    const size_t smem = tc_batch_smem_bytes(fmt, stages, KC);
+    const size_t smem = tct_smem_bytes(fmt, stages, KC);
     const int m_tiles = (int)(Mpad / TC_BM);
     const int sms = sm_count();
     const int groups = std::max(1, std::min(max_q, std::max(1, group_mult) * ((2 * sms + m_tiles - 1) / m_tiles)));
@@ -2010,6 +2095,8 @@ static int tcp_stages(int bn, int KC)
     while (s >= 2 && tcp_smem_bytes(bn, s, KC) > budget) --s;
     return s >= 2 ? s : 0;
 }
+
+bool tc_table_fits(int fmt, int Kpad) { return tct_stages(fmt, Kpad / 64) >= 2; }
 
 bool tc_table_pair_fits(int Kpad) { return tcp_stages(128, Kpad / 64) >= 2 && tcp_stages(64, Kpad / 64) >= 2; }
 
