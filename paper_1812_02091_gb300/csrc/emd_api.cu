@@ -361,12 +361,12 @@ emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, i
             EMD_CUDA(launch_qpos_b(D_, nqd, B, db->vslot, db->v, true, st), "identical ids");
             if (use_tc_pair(db))
                 EMD_CUDA(launch_tc_table_pair(db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used, db->v_used,
-                                              D_, nqd, B, db->kpad, tk_b, db->tune_group_mult,
+                                              D_, nqd, B, db->kpad, db->m, tk_b, db->tune_group_mult,
                                               db->opt.tc_pair == 1 ? 64 : 128, db->err, st),
                          "Phase-1 table (tensor cores on SM pairs, fused)");
             else
                 EMD_CUDA(launch_tc_table_batch(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
-                                               db->v_used, D_, nqd, B, db->kpad, db->approx ? kc_b : tk_b,
+                                               db->v_used, D_, nqd, B, db->kpad, db->m, db->approx ? kc_b : tk_b,
                                                db->tune_group_mult, db->tune_stages, db->err, st),
                          db->approx ? "Phase-1 candidates (tensor cores, fused)"
                                     : "Phase-1 table (tensor cores, fused)");
@@ -438,7 +438,8 @@ emd_status launch_sequence(BatchWS& ws, emd_db* db, int slot, int meas, int k, i
         if (db->tc && !hd) {
             Phase p(db, 1, 2, st);
             EMD_CUDA(launch_tc_dist_batch(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
-                                          db->v_used, D_, nqd, B, db->kpad, db->tune_group_mult, db->tune_stages,
+                                          db->v_used, D_, nqd, B, db->kpad, db->m, db->tune_group_mult,
+                                          db->tune_stages,
                                           db->err, st),
                      "distance matrices (tensor cores, batched)");
             EMD_CUDA(launch_zero_ident_b(D_, nqd, B, H, db->vslot, db->v, st), "identical ids");
@@ -1069,7 +1070,8 @@ emd_status autotune(emd_db* db, const std::vector<int32_t>& used_host)
             for (int sg : stage_set) {
                 const float ms = timed([&] {
                     launch_tc_dist_batch(db->tcfmt, db->a_hi, db->a_lo, db->mpad, db->a_scale, db->norm_used,
-                                         db->v_used, D_, nqd, db->opt.max_batch, db->kpad, gm, sg, db->err, st);
+                                         db->v_used, D_, nqd, db->opt.max_batch, db->kpad, db->m, gm, sg, db->err,
+                                         st);
                 });
                 if (ms < 0.95f * best) {
                     best = ms;

@@ -257,7 +257,7 @@ int tc_batch_stages(int fmt, int KC);
 // choice.
 cudaError_t launch_tc_dist_batch(int fmt, const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
                                  const float* a_norm, int64_t M, const QDesc* qd, const int* nq,
-                                 int max_q, int Kpad, int group_mult, int stages, int* err, cudaStream_t st);
+                                 int max_q, int Kpad, int m, int group_mult, int stages, int* err, cudaStream_t st);
 // max_tk: the largest table width of the batch; rerank: the approximate precisions' form
 // (V: the used vocabulary rows, ldv floats each).
 // Exact zeros of identical ids (launch_zero_ident) for every query of a batch.
@@ -278,10 +278,10 @@ bool tc_table_pair_fits(int Kpad);
 bool tc_table_fits(int fmt, int Kpad);
 cudaError_t launch_tc_table_pair(const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
                                  const float* a_norm, int64_t M, const QDesc* qd, const int* nq, int max_q, int Kpad,
-                                 int max_tk, int group_mult, int bn, int* err, cudaStream_t st);
+                                 int m, int max_tk, int group_mult, int bn, int* err, cudaStream_t st);
 cudaError_t launch_tc_table_batch(int fmt, const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
                                   const float* a_norm, int64_t M, const QDesc* qd, const int* nq, int max_q, int Kpad,
-                                  int max_tk, int group_mult, int stages, int* err, cudaStream_t st);
+                                  int m, int max_tk, int group_mult, int stages, int* err, cudaStream_t st);
 // Candidate compaction of the pruned path alone (counts must be zeroed).
 cudaError_t launch_prune_compact_b(const QDesc* qd, const int* nq, int max_q, int64_t n, int K, cudaStream_t st);
 // The distinct used rows of the candidate documents (qd[q].crows, ncrows zeroed, rmap), or

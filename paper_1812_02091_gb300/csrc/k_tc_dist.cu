@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(TCB_THREADS, 1)
 k_tc_dist_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_lo, int64_t Mpad,
                 const float* __restrict__ a_scale, const float* __restrict__ a_norm,
                 int64_t M, const QDesc* __restrict__ qd,
-                const int* __restrict__ nq_dev, int groups, int KC, int stages, int* __restrict__ err)
+                const int* __restrict__ nq_dev, int groups, int KC, int stages, int klast, int* __restrict__ err)
 {
     constexpr bool SPLIT = FMT == TC_SPLIT;
     constexpr uint32_t EB = TcFmt<FMT>::EB;
@@ -607,6 +607,7 @@ k_tc_dist_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
                         const uint32_t sb_lo = sb + kBBytes;
 #pragma unroll
                         for (int ks = 0; ks < (int)TcFmt<FMT>::mmas; ++ks) {
+                            if (c == KC - 1 && ks >= klast) break;  // the last chunk's zero K steps
                             const uint32_t ko = (uint32_t)ks * 256u;
                             const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
                             const uint64_t da = smem_desc(sa + ko, kSbo), db = smem_desc(sb + ko, kSbo);
@@ -805,7 +806,7 @@ __global__ void __launch_bounds__(TCT_THREADS, 1)
 k_tc_table_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_lo, int64_t Mpad,
                  const float* __restrict__ a_scale, const float* __restrict__ a_norm, int64_t M,
                  const QDesc* __restrict__ qd, const int* __restrict__ nq_dev, int groups, int KC, int stages,
-                 int* __restrict__ err)
+                 int klast, int* __restrict__ err)
 {
     constexpr bool SPLIT = FMT == TC_SPLIT;
     constexpr uint32_t EB = TcFmt<FMT>::EB;
@@ -950,6 +951,7 @@ k_tc_table_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A
                     const uint32_t sb_lo = sb + kBBytes;
 #pragma unroll
                     for (int ks = 0; ks < (int)TcFmt<FMT>::mmas; ++ks) {
+                        if (c == KC - 1 && ks >= klast) break;  // the last chunk's zero K steps
                         const uint32_t ko = (uint32_t)ks * 256u;
                         const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
                         const uint64_t da = smem_desc(sa + ko, kSbo), db = smem_desc(sb + ko, kSbo);
@@ -1219,7 +1221,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TCP_THREADS, 1)
 k_tc_table_pair(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_lo, int64_t Mpad,
                 const float* __restrict__ a_scale, const float* __restrict__ a_norm, int64_t M,
                 const QDesc* __restrict__ qd, const int* __restrict__ nq_dev, int groups, int KC, int stages,
-                int* __restrict__ err)
+                int klast, int* __restrict__ err)
 {
     constexpr uint32_t EB = 128;  // FP16 split: bytes of a 64-element row segment
     constexpr uint32_t kABytes = TC_BM * EB;
@@ -1408,6 +1410,7 @@ k_tc_table_pair(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
                     const uint32_t sb_lo = sb + kBBytes;
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks) {
+                        if (c == KC - 1 && ks >= klast) break;  // the last chunk's zero K steps
                         const uint32_t ko = (uint32_t)ks * 256u;
                         const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
                         const uint64_t da = smem_desc(sa + ko, kSbo), db = smem_desc(sb + ko, kSbo);
@@ -1935,6 +1938,15 @@ static cudaError_t tc_launch(dim3 grid, size_t smem, cudaStream_t st, const void
     return cudaGetLastError();
 }
 
+// MMAs of the last 64-element K chunk that touch data (m elements of K, the rest zero
+// padding): zero steps add exact zeros, so leaving them out changes no value.
+static int last_chunk_steps(int fmt, int m, int KC)
+{
+    const int step = fmt == TC_E4M3 ? 32 : 16, mmas = 64 / step;
+    if (m <= 0) return mmas;
+    return std::max(1, std::min(mmas, (m - 64 * (KC - 1) + step - 1) / step));
+}
+
 size_t tc_batch_smem_bytes(int fmt, int stages, int KC)
 {
     const size_t eb = fmt == TC_E4M3 ? 64 : 128;
@@ -1965,22 +1977,24 @@ static int tct_stages(int fmt, int KC)
 template <int FMT>
 static cudaError_t tc_batch_launch(dim3 grid, size_t smem, cudaStream_t st, const void* A_hi, const void* A_lo,
                                    int64_t Mpad, const float* a_scale, const float* a_norm,
-                                   int64_t M, const QDesc* qd, const int* nq, int groups, int KC, int stages, int* err)
+                                   int64_t M, const QDesc* qd, const int* nq, int groups, int KC, int stages, int klast,
+                                   int* err)
 {
     cudaError_t e = cudaFuncSetAttribute(k_tc_dist_batch<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_tc_dist_batch<FMT><<<grid, TCB_THREADS, smem, st>>>(static_cast<const uint8_t*>(A_hi),
                                                          static_cast<const uint8_t*>(A_lo), Mpad, a_scale, a_norm,
-                                                         M, qd, nq, groups, KC, stages, err);
+                                                         M, qd, nq, groups, KC, stages, klast, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_dist_batch(int fmt, const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
                                  const float* a_norm, int64_t M, const QDesc* qd, const int* nq,
-                                 int max_q, int Kpad, int group_mult, int stages_req, int* err, cudaStream_t st)
+                                 int max_q, int Kpad, int m, int group_mult, int stages_req, int* err, cudaStream_t st)
 {
     if (M <= 0 || max_q <= 0) return cudaSuccess;
     const int KC = Kpad / 64;
+    const int klast = last_chunk_steps(fmt, m, KC);
     const int fit = tc_batch_stages(fmt, KC);
     if (fit < 2) return cudaErrorInvalidValue;
     const int stages = stages_req >= 2 ? std::min(stages_req, fit) : fit;
@@ -1993,13 +2007,13 @@ cudaError_t launch_tc_dist_batch(int fmt, const void* A_hi, const void* A_lo, in
     switch (fmt) {
     case TC_SPLIT:
         return tc_batch_launch<TC_SPLIT>(grid, smem, st, A_hi, A_lo, Mpad, a_scale, a_norm, M, qd, nq, groups,
-                                         KC, stages, err);
+                                         KC, stages, klast, err);
     case TC_BF16:
         return tc_batch_launch<TC_BF16>(grid, smem, st, A_hi, nullptr, Mpad, a_scale, a_norm, M, qd, nq,
-                                        groups, KC, stages, err);
+                                        groups, KC, stages, klast, err);
     case TC_E4M3:
         return tc_batch_launch<TC_E4M3>(grid, smem, st, A_hi, nullptr, Mpad, a_scale, a_norm, M, qd, nq,
-                                        groups, KC, stages, err);
+                                        groups, KC, stages, klast, err);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -2037,24 +2051,25 @@ namespace emd {
 template <int FMT, int KT, bool CAND>
 static cudaError_t tc_table_launch(dim3 grid, size_t smem, cudaStream_t st, const void* A_hi, const void* A_lo,
                                    int64_t Mpad, const float* a_scale, const float* a_norm, int64_t M, const QDesc* qd,
-                                   const int* nq, int groups, int KC, int stages, int* err)
+                                   const int* nq, int groups, int KC, int stages, int klast, int* err)
 {
     cudaError_t e = cudaFuncSetAttribute(k_tc_table_batch<FMT, KT, CAND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     k_tc_table_batch<FMT, KT, CAND><<<grid, TCT_THREADS, smem, st>>>(static_cast<const uint8_t*>(A_hi),
                                                                      static_cast<const uint8_t*>(A_lo), Mpad, a_scale,
-                                                                     a_norm, M, qd, nq, groups, KC, stages, err);
+                                                                     a_norm, M, qd, nq, groups, KC, stages, klast, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_table_batch(int fmt, const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
                                   const float* a_norm, int64_t M, const QDesc* qd, const int* nq, int max_q, int Kpad,
-                                  int max_tk, int group_mult, int stages_req, int* err, cudaStream_t st)
+                                  int m, int max_tk, int group_mult, int stages_req, int* err, cudaStream_t st)
 {
     if (M <= 0 || max_q <= 0) return cudaSuccess;
     if (max_tk < 1 || max_tk > 16) return cudaErrorInvalidValue;
     const int KC = Kpad / 64;
+    const int klast = last_chunk_steps(fmt, m, KC);
     const int fit = tct_stages(fmt, KC);
     if (fit < 2) return cudaErrorInvalidValue;
     const int stages = stages_req >= 2 ? std::min(stages_req, fit) : fit;
@@ -2066,14 +2081,14 @@ cudaError_t launch_tc_table_batch(int fmt, const void* A_hi, const void* A_lo, i
     // approximate formats keep max_tk = the candidate count in candidate mode (at most 16)
     if (fmt == TC_BF16)
         return tc_table_launch<TC_BF16, 16, true>(grid, smem, st, A_hi, nullptr, Mpad, a_scale, a_norm, M, qd, nq,
-                                                  groups, KC, stages, err);
+                                                  groups, KC, stages, klast, err);
     if (fmt == TC_E4M3)
         return tc_table_launch<TC_E4M3, 16, true>(grid, smem, st, A_hi, nullptr, Mpad, a_scale, a_norm, M, qd, nq,
-                                                  groups, KC, stages, err);
+                                                  groups, KC, stages, klast, err);
     if (fmt != TC_SPLIT) return cudaErrorInvalidValue;
 #define EMD_TT(KT) \
     return tc_table_launch<TC_SPLIT, KT, false>(grid, smem, st, A_hi, A_lo, Mpad, a_scale, a_norm, M, qd, nq, groups, KC, \
-                                                stages, err)
+                                                stages, klast, err)
     if (max_tk <= 1) EMD_TT(1);
     if (max_tk <= 2) EMD_TT(2);
     if (max_tk <= 4) EMD_TT(4);
@@ -2103,25 +2118,26 @@ bool tc_table_pair_fits(int Kpad) { return tcp_stages(128, Kpad / 64) >= 2 && tc
 template <int KT, int BN>
 static cudaError_t tc_pair_launch(dim3 grid, size_t smem, cudaStream_t st, const void* A_hi, const void* A_lo,
                                   int64_t Mpad, const float* a_scale, const float* a_norm, int64_t M, const QDesc* qd,
-                                  const int* nq, int groups, int KC, int stages, int* err)
+                                  const int* nq, int groups, int KC, int stages, int klast, int* err)
 {
     cudaError_t e = cudaFuncSetAttribute(k_tc_table_pair<KT, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     k_tc_table_pair<KT, BN><<<grid, TCP_THREADS, smem, st>>>(static_cast<const uint8_t*>(A_hi),
                                                              static_cast<const uint8_t*>(A_lo), Mpad, a_scale, a_norm,
-                                                             M, qd, nq, groups, KC, stages, err);
+                                                             M, qd, nq, groups, KC, stages, klast, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_table_pair(const void* A_hi, const void* A_lo, int64_t Mpad, const float* a_scale,
                                  const float* a_norm, int64_t M, const QDesc* qd, const int* nq, int max_q, int Kpad,
-                                 int max_tk, int group_mult, int bn, int* err, cudaStream_t st)
+                                 int m, int max_tk, int group_mult, int bn, int* err, cudaStream_t st)
 {
     if (M <= 0 || max_q <= 0) return cudaSuccess;
     if (max_tk < 1 || max_tk > 16 || (bn != 64 && bn != 128) || Mpad % (2 * TC_BM) != 0)
         return cudaErrorInvalidValue;
     const int KC = Kpad / 64;
+    const int klast = last_chunk_steps(TC_SPLIT, m, KC);
     const int stages = tcp_stages(bn, KC);
     if (stages < 2) return cudaErrorInvalidValue;
     const size_t smem = tcp_smem_bytes(bn, stages, KC);
@@ -2132,9 +2148,9 @@ cudaError_t launch_tc_table_pair(const void* A_hi, const void* A_lo, int64_t Mpa
     const dim3 grid((unsigned)(2 * std::min<int64_t>((int64_t)pairs * groups, clusters_max)));
 #define EMD_TP(KT)                                                                                                    \
     return bn == 64 ? tc_pair_launch<KT, 64>(grid, smem, st, A_hi, A_lo, Mpad, a_scale, a_norm, M, qd, nq, groups, KC, \
-                                             stages, err)                                                              \
+                                             stages, klast, err)                                                              \
                     : tc_pair_launch<KT, 128>(grid, smem, st, A_hi, A_lo, Mpad, a_scale, a_norm, M, qd, nq, groups,    \
-                                              KC, stages, err)
+                                              KC, stages, klast, err)
     if (max_tk <= 1) EMD_TP(1);
     if (max_tk <= 2) EMD_TP(2);
     if (max_tk <= 4) EMD_TP(4);
