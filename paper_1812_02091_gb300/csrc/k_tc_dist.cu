@@ -524,6 +524,8 @@ k_tc_dist_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
 
     if (warp == 0 && lane == 0) {
         int64_t gb = 0;
+        int rs = 0;          // ring stage gb % stages
+        uint32_t rp = 0;     // its round's parity (gb / stages) & 1
         int items = 0;
         bool ok = true;
         for (int w = blockIdx.x; w < total && ok && !*abort_flag; w += gridDim.x, ++items) {
@@ -547,10 +549,10 @@ k_tc_dist_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
                 for (int n0 = 0; n0 < d.h && ok; n0 += TC_BN) {
                     const int Nt = min(TC_BN, (int)round_up(d.h - n0, 16));
                     const uint32_t b_bytes = (uint32_t)Nt * EB;
-                    for (int c = 0; c < KC; ++c, ++gb) {
-                        const int s = (int)(gb % stages);
+                    for (int c = 0; c < KC; ++c, ++gb, rs = rs + 1 == stages ? (rp ^= 1u, 0) : rs + 1) {
+                        const int s = rs;
                         if (gb >= stages &&
-                            !mbar_wait(&empty[s], (uint32_t)((gb / stages) - 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                            !mbar_wait(&empty[s], rp ^ 1u, global_ns() + TC_TIMEOUT_NS)) {
                             fail();
                             ok = false;
                             break;
@@ -570,6 +572,8 @@ k_tc_dist_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
         if (items > 0 && !mbar_wait(afull, (uint32_t)(items - 1) & 1u, tail)) atomicOr(err, ERR_TIMEOUT);
     } else if (warp == 1 && lane == 0) {
         int64_t gb = 0;
+        int rs = 0;          // ring stage gb % stages
+        uint32_t rp = 0;     // its round's parity (gb / stages) & 1
         int it = 0, items = 0;
         bool ok = true;
         for (int w = blockIdx.x; w < total && ok && !*abort_flag; w += gridDim.x, ++items) {
@@ -593,9 +597,9 @@ k_tc_dist_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
                     }
                     tc_fence_after();
                     const uint32_t acc0 = tmem + (uint32_t)buf * kAcc;
-                    for (int c = 0; c < KC; ++c, ++gb) {
-                        const int s = (int)(gb % stages);
-                        if (!mbar_wait(&full[s], (uint32_t)(gb / stages) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                    for (int c = 0; c < KC; ++c, ++gb, rs = rs + 1 == stages ? (rp ^= 1u, 0) : rs + 1) {
+                        const int s = rs;
+                        if (!mbar_wait(&full[s], rp, global_ns() + TC_TIMEOUT_NS)) {
                             fail();
                             ok = false;
                             break;
@@ -869,6 +873,8 @@ k_tc_table_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A
 
     if (warp == 0 && lane == 0) {
         int64_t gb = 0;
+        int rs = 0;          // ring stage gb % stages
+        uint32_t rp = 0;     // its round's parity (gb / stages) & 1
         int items = 0;
         bool ok = true;
         for (int w = blockIdx.x; w < total && ok && !*abort_flag; w += gridDim.x, ++items) {
@@ -893,10 +899,10 @@ k_tc_table_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A
                 const uint32_t b_bytes = (uint32_t)Nt * EB;
                 const uint8_t* bh = static_cast<const uint8_t*>(d.q_hi);
                 const uint8_t* bl = static_cast<const uint8_t*>(d.q_lo);
-                for (int c = 0; c < KC; ++c, ++gb) {
-                    const int st = (int)(gb % stages);
+                for (int c = 0; c < KC; ++c, ++gb, rs = rs + 1 == stages ? (rp ^= 1u, 0) : rs + 1) {
+                    const int st = rs;
                     if (gb >= stages &&
-                        !mbar_wait(&empty[st], (uint32_t)((gb / stages) - 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                        !mbar_wait(&empty[st], rp ^ 1u, global_ns() + TC_TIMEOUT_NS)) {
                         fail();
                         ok = false;
                         break;
@@ -914,6 +920,8 @@ k_tc_table_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A
         if (items > 0 && !mbar_wait(afull, (uint32_t)(items - 1) & 1u, tail)) atomicOr(err, ERR_TIMEOUT);
     } else if (warp == 1 && lane == 0) {
         int64_t gb = 0;
+        int rs = 0;          // ring stage gb % stages
+        uint32_t rp = 0;     // its round's parity (gb / stages) & 1
         int cnt0 = 0, cnt1 = 0, items = 0;  // tiles issued per stream
         bool ok = true;
         for (int w = blockIdx.x; w < total && ok && !*abort_flag; w += gridDim.x, ++items) {
@@ -937,9 +945,9 @@ k_tc_table_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A
                 }
                 tc_fence_after();
                 const uint32_t acc0 = tmem + (uint32_t)s * kAcc;
-                for (int c = 0; c < KC; ++c, ++gb) {
-                    const int st = (int)(gb % stages);
-                    if (!mbar_wait(&full[st], (uint32_t)(gb / stages) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                for (int c = 0; c < KC; ++c, ++gb, rs = rs + 1 == stages ? (rp ^= 1u, 0) : rs + 1) {
+                    const int st = rs;
+                    if (!mbar_wait(&full[st], rp, global_ns() + TC_TIMEOUT_NS)) {
                         fail();
                         ok = false;
                         break;
@@ -1296,6 +1304,8 @@ k_tc_table_pair(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
     };
     if (warp == 0 && lane == 0 && pair_ok) {
         int64_t gb = 0;
+        int rs = 0;          // ring stage gb % stages
+        uint32_t rp = 0;     // its round's parity (gb / stages) & 1
         int items = 0;
         bool ok = true;
         for (int w = cid; w < total && ok && !*abort_flag; w += ncl, ++items) {
@@ -1322,9 +1332,9 @@ k_tc_table_pair(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
                 const int64_t c0 = n0 + (int64_t)rank * nh;
                 const uint8_t* bh = static_cast<const uint8_t*>(d.q_hi);
                 const uint8_t* bl = static_cast<const uint8_t*>(d.q_lo);
-                for (int c = 0; c < KC; ++c, ++gb) {
-                    const int st = (int)(gb % stages);
-                    if (gb >= stages && !mbar_wait_cluster(&empty[st], (uint32_t)((gb / stages) - 1) & 1u,
+                for (int c = 0; c < KC; ++c, ++gb, rs = rs + 1 == stages ? (rp ^= 1u, 0) : rs + 1) {
+                    const int st = rs;
+                    if (gb >= stages && !mbar_wait_cluster(&empty[st], rp ^ 1u,
                                                            global_ns() + TC_TIMEOUT_NS)) {
                         fail();
                         ok = false;
@@ -1345,6 +1355,8 @@ k_tc_table_pair(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
         // peer: forward the completion of its own copies to the leader, in the copy order
         const uint32_t r_pfull = peer_addr(pfull, 0), r_pafull = peer_addr(pafull, 0);
         int64_t gb = 0;
+        int rs = 0;          // ring stage gb % stages
+        uint32_t rp = 0;     // its round's parity (gb / stages) & 1
         int items = 0;
         bool ok = true;
         for (int w = cid; w < total && ok && !*abort_flag; w += ncl, ++items) {
@@ -1358,9 +1370,9 @@ k_tc_table_pair(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
             TileSeq ts;
             ts.init(qa, qb, BN);
             while (ok && ts.next(qd, q, n0, s)) {
-                for (int c = 0; c < KC; ++c, ++gb) {
-                    const int st = (int)(gb % stages);
-                    if (!mbar_wait(&full[st], (uint32_t)(gb / stages) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                for (int c = 0; c < KC; ++c, ++gb, rs = rs + 1 == stages ? (rp ^= 1u, 0) : rs + 1) {
+                    const int st = rs;
+                    if (!mbar_wait(&full[st], rp, global_ns() + TC_TIMEOUT_NS)) {
                         fail();
                         ok = false;
                         break;
@@ -1371,6 +1383,8 @@ k_tc_table_pair(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
         }
     } else if (warp == 1 && lane == 0 && rank == 0 && pair_ok) {
         int64_t gb = 0;
+        int rs = 0;          // ring stage gb % stages
+        uint32_t rp = 0;     // its round's parity (gb / stages) & 1
         int cnt0 = 0, cnt1 = 0, items = 0;  // tiles issued per stream
         bool ok = true;
         for (int w = cid; w < total && ok && !*abort_flag; w += ncl, ++items) {
@@ -1395,10 +1409,10 @@ k_tc_table_pair(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
                 }
                 tc_fence_after();
                 const uint32_t acc0 = tmem + (uint32_t)s * kAcc;
-                for (int c = 0; c < KC; ++c, ++gb) {
-                    const int st = (int)(gb % stages);
-                    if (!mbar_wait(&full[st], (uint32_t)(gb / stages) & 1u, global_ns() + TC_TIMEOUT_NS) ||
-                        !mbar_wait_cluster(&pfull[st], (uint32_t)(gb / stages) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                for (int c = 0; c < KC; ++c, ++gb, rs = rs + 1 == stages ? (rp ^= 1u, 0) : rs + 1) {
+                    const int st = rs;
+                    if (!mbar_wait(&full[st], rp, global_ns() + TC_TIMEOUT_NS) ||
+                        !mbar_wait_cluster(&pfull[st], rp, global_ns() + TC_TIMEOUT_NS)) {
                         fail();
                         ok = false;
                         break;
@@ -1599,6 +1613,8 @@ k_tc_cand_batch(const QDesc* __restrict__ qd, const int* __restrict__ nq_dev, in
 
     if (warp == 0 && lane == 0) {
         int64_t gb = 0;
+        int rs = 0;          // ring stage gb % stages
+        uint32_t rp = 0;     // its round's parity (gb / stages) & 1
         int items = 0;
         bool ok = true;
         for (int w = blockIdx.x; w < total && ok && !*abort_flag; w += gridDim.x) {
@@ -1623,10 +1639,10 @@ k_tc_cand_batch(const QDesc* __restrict__ qd, const int* __restrict__ nq_dev, in
             for (int n0 = 0; n0 < d.h && ok; n0 += TC_BN) {
                 const int Nt = min(TC_BN, (int)round_up(d.h - n0, 16));
                 const uint32_t b_bytes = (uint32_t)Nt * EB;
-                for (int c = 0; c < KC; ++c, ++gb) {
-                    const int s = (int)(gb % stages);
+                for (int c = 0; c < KC; ++c, ++gb, rs = rs + 1 == stages ? (rp ^= 1u, 0) : rs + 1) {
+                    const int s = rs;
                     if (gb >= stages &&
-                        !mbar_wait(&empty[s], (uint32_t)((gb / stages) - 1) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                        !mbar_wait(&empty[s], rp ^ 1u, global_ns() + TC_TIMEOUT_NS)) {
                         fail();
                         ok = false;
                         break;
@@ -1644,6 +1660,8 @@ k_tc_cand_batch(const QDesc* __restrict__ qd, const int* __restrict__ nq_dev, in
         if (items > 0 && !mbar_wait(afull, (uint32_t)(items - 1) & 1u, tail)) atomicOr(err, ERR_TIMEOUT);
     } else if (warp == 1 && lane == 0) {
         int64_t gb = 0;
+        int rs = 0;          // ring stage gb % stages
+        uint32_t rp = 0;     // its round's parity (gb / stages) & 1
         int it = 0, items = 0;
         bool ok = true;
         for (int w = blockIdx.x; w < total && ok && !*abort_flag; w += gridDim.x) {
@@ -1666,9 +1684,9 @@ k_tc_cand_batch(const QDesc* __restrict__ qd, const int* __restrict__ nq_dev, in
                 }
                 tc_fence_after();
                 const uint32_t acc0 = tmem + (uint32_t)buf * kAcc;
-                for (int c = 0; c < KC; ++c, ++gb) {
-                    const int s = (int)(gb % stages);
-                    if (!mbar_wait(&full[s], (uint32_t)(gb / stages) & 1u, global_ns() + TC_TIMEOUT_NS)) {
+                for (int c = 0; c < KC; ++c, ++gb, rs = rs + 1 == stages ? (rp ^= 1u, 0) : rs + 1) {
+                    const int s = rs;
+                    if (!mbar_wait(&full[s], rp, global_ns() + TC_TIMEOUT_NS)) {
                         fail();
                         ok = false;
                         break;
