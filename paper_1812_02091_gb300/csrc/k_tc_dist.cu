@@ -370,15 +370,20 @@ k_tc_dist(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_lo, in
                 const uint32_t sa_lo = sa + kABytes;
                 const uint32_t sb = smem_u32(bpanel + (size_t)c * kBChunk);
                 const uint32_t sb_lo = sb + kBBytes;
+                // descriptors of the chunk's first K step; a step of 16 elements (256 B) adds 16 to the
+                // address field (addresses stay below 2^18, so no carry leaves the 14-bit field)
+                const uint64_t dA0 = smem_desc(sa, kSbo), dB0 = smem_desc(sb, kSbo);
+                const uint64_t dAl0 = smem_desc(sa_lo, kSbo), dBl0 = smem_desc(sb_lo, kSbo);
 #pragma unroll
                 for (int ks = 0; ks < (int)TcFmt<FMT>::mmas; ++ks) {  // each MMA: 2 core matrices = 256 B of K
                     const uint32_t ko = (uint32_t)ks * 256u;
                     const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
-                    const uint64_t da = smem_desc(sa + ko, kSbo), db = smem_desc(sb + ko, kSbo);
+                    const uint64_t kd = (uint64_t)(ko >> 4);
+                    const uint64_t da = dA0 + kd, db = dB0 + kd;
                     mma_issue<FMT>(acc0, da, db, idesc, acc);
                     if (SPLIT) {
-                        mma_issue<FMT>(acc0 + 128, da, smem_desc(sb_lo + ko, kSbo), idesc, acc);
-                        mma_issue<FMT>(acc0 + 128, smem_desc(sa_lo + ko, kSbo), db, idesc, 1u);
+                        mma_issue<FMT>(acc0 + 128, da, dBl0 + kd, idesc, acc);
+                        mma_issue<FMT>(acc0 + 128, dAl0 + kd, db, idesc, 1u);
                     }
                 }
                 mma_commit(&empty[s]);
@@ -609,16 +614,21 @@ k_tc_dist_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
                         const uint32_t sa_lo = sa + kABytes;
                         const uint32_t sb = smem_u32(bring + (size_t)s * kBStage);
                         const uint32_t sb_lo = sb + kBBytes;
+                        // descriptors of the chunk's first K step; a step of 16 elements (256 B) adds 16 to the
+                        // address field (addresses stay below 2^18, so no carry leaves the 14-bit field)
+                        const uint64_t dA0 = smem_desc(sa, kSbo), dB0 = smem_desc(sb, kSbo);
+                        const uint64_t dAl0 = smem_desc(sa_lo, kSbo), dBl0 = smem_desc(sb_lo, kSbo);
 #pragma unroll
                         for (int ks = 0; ks < (int)TcFmt<FMT>::mmas; ++ks) {
                             if (c == KC - 1 && ks >= klast) break;  // the last chunk's zero K steps
                             const uint32_t ko = (uint32_t)ks * 256u;
                             const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
-                            const uint64_t da = smem_desc(sa + ko, kSbo), db = smem_desc(sb + ko, kSbo);
+                            const uint64_t kd = (uint64_t)(ko >> 4);
+                            const uint64_t da = dA0 + kd, db = dB0 + kd;
                             mma_issue<FMT>(acc0, da, db, idesc, acc);
                             if (SPLIT) {
-                                mma_issue<FMT>(acc0 + 128, da, smem_desc(sb_lo + ko, kSbo), idesc, acc);
-                                mma_issue<FMT>(acc0 + 128, smem_desc(sa_lo + ko, kSbo), db, idesc, 1u);
+                                mma_issue<FMT>(acc0 + 128, da, dBl0 + kd, idesc, acc);
+                                mma_issue<FMT>(acc0 + 128, dAl0 + kd, db, idesc, 1u);
                             }
                         }
                         mma_commit(&empty[s]);
@@ -957,16 +967,21 @@ k_tc_table_batch(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A
                     const uint32_t sa_lo = sa + kABytes;
                     const uint32_t sb = smem_u32(bring + (size_t)st * kBStage);
                     const uint32_t sb_lo = sb + kBBytes;
+                    // descriptors of the chunk's first K step; a step of 16 elements (256 B) adds 16 to the
+                    // address field (addresses stay below 2^18, so no carry leaves the 14-bit field)
+                    const uint64_t dA0 = smem_desc(sa, kSbo), dB0 = smem_desc(sb, kSbo);
+                    const uint64_t dAl0 = smem_desc(sa_lo, kSbo), dBl0 = smem_desc(sb_lo, kSbo);
 #pragma unroll
                     for (int ks = 0; ks < (int)TcFmt<FMT>::mmas; ++ks) {
                         if (c == KC - 1 && ks >= klast) break;  // the last chunk's zero K steps
                         const uint32_t ko = (uint32_t)ks * 256u;
                         const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
-                        const uint64_t da = smem_desc(sa + ko, kSbo), db = smem_desc(sb + ko, kSbo);
+                        const uint64_t kd = (uint64_t)(ko >> 4);
+                        const uint64_t da = dA0 + kd, db = dB0 + kd;
                         mma_issue<FMT>(acc0, da, db, idesc, acc);
                         if (SPLIT) {
-                            mma_issue<FMT>(acc0 + 128, da, smem_desc(sb_lo + ko, kSbo), idesc, acc);
-                            mma_issue<FMT>(acc0 + 128, smem_desc(sa_lo + ko, kSbo), db, idesc, 1u);
+                            mma_issue<FMT>(acc0 + 128, da, dBl0 + kd, idesc, acc);
+                            mma_issue<FMT>(acc0 + 128, dAl0 + kd, db, idesc, 1u);
                         }
                     }
                     mma_commit(&empty[st]);
@@ -1422,15 +1437,20 @@ k_tc_table_pair(const uint8_t* __restrict__ A_hi, const uint8_t* __restrict__ A_
                     const uint32_t sa_lo = sa + kABytes;
                     const uint32_t sb = smem_u32(bring + (size_t)st * kBStage);
                     const uint32_t sb_lo = sb + kBBytes;
+                    // descriptors of the chunk's first K step; a step of 16 elements (256 B) adds 16 to the
+                    // address field (addresses stay below 2^18, so no carry leaves the 14-bit field)
+                    const uint64_t dA0 = smem_desc(sa, kSbo), dB0 = smem_desc(sb, kSbo);
+                    const uint64_t dAl0 = smem_desc(sa_lo, kSbo), dBl0 = smem_desc(sb_lo, kSbo);
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks) {
                         if (c == KC - 1 && ks >= klast) break;  // the last chunk's zero K steps
                         const uint32_t ko = (uint32_t)ks * 256u;
                         const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
-                        const uint64_t da = smem_desc(sa + ko, kSbo), db = smem_desc(sb + ko, kSbo);
+                        const uint64_t kd = (uint64_t)(ko >> 4);
+                        const uint64_t da = dA0 + kd, db = dB0 + kd;
                         mma_issue_pair(acc0, da, db, idesc, acc);
-                        mma_issue_pair(acc0 + BN, da, smem_desc(sb_lo + ko, kSbo), idesc, acc);
-                        mma_issue_pair(acc0 + BN, smem_desc(sa_lo + ko, kSbo), db, idesc, 1u);
+                        mma_issue_pair(acc0 + BN, da, dBl0 + kd, idesc, acc);
+                        mma_issue_pair(acc0 + BN, dAl0 + kd, db, idesc, 1u);
                     }
                     mma_commit_pair(&empty[st]);
                 }
@@ -1696,15 +1716,20 @@ k_tc_cand_batch(const QDesc* __restrict__ qd, const int* __restrict__ nq_dev, in
                     const uint32_t sa_lo = sa + kABytes;
                     const uint32_t sb = smem_u32(bring + (size_t)s * kBStage);
                     const uint32_t sb_lo = sb + kBBytes;
+                    // descriptors of the chunk's first K step; a step of 16 elements (256 B) adds 16 to the
+                    // address field (addresses stay below 2^18, so no carry leaves the 14-bit field)
+                    const uint64_t dA0 = smem_desc(sa, kSbo), dB0 = smem_desc(sb, kSbo);
+                    const uint64_t dAl0 = smem_desc(sa_lo, kSbo), dBl0 = smem_desc(sb_lo, kSbo);
 #pragma unroll
                     for (int ks = 0; ks < (int)TcFmt<FMT>::mmas; ++ks) {
                         const uint32_t ko = (uint32_t)ks * 256u;
                         const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
-                        const uint64_t da = smem_desc(sa + ko, kSbo), db = smem_desc(sb + ko, kSbo);
+                        const uint64_t kd = (uint64_t)(ko >> 4);
+                        const uint64_t da = dA0 + kd, db = dB0 + kd;
                         mma_issue<FMT>(acc0, da, db, idesc, acc);
                         if (SPLIT) {
-                            mma_issue<FMT>(acc0 + 128, da, smem_desc(sb_lo + ko, kSbo), idesc, acc);
-                            mma_issue<FMT>(acc0 + 128, smem_desc(sa_lo + ko, kSbo), db, idesc, 1u);
+                            mma_issue<FMT>(acc0 + 128, da, dBl0 + kd, idesc, acc);
+                            mma_issue<FMT>(acc0 + 128, dAl0 + kd, db, idesc, 1u);
                         }
                     }
                     mma_commit(&empty[s]);
