@@ -358,6 +358,7 @@ def main():
     ap.add_argument("--k4-docs", type=int, default=300000)
     ap.add_argument("--k4-hmax", type=int, default=2048,
                     help="--k4: largest h_q of the timed queries (2048: workload 5's whole query law)")
+    ap.add_argument("--k4-hmin", type=int, default=1, help="--k4: smallest h_q of the timed queries")
     ap.add_argument("--k4-forms", default="0,1,2,3,4",
                     help="forms of the grouped sweep the --k4 mode times (0 = the autotuner's choice)")
     ap.add_argument("--ict", action="store_true",
@@ -775,7 +776,10 @@ def main_k4(args, local):
     w = emd_synth.config(5, query_limit=8 * need, n_docs=args.k4_docs)
     gen_s = time.perf_counter() - t0
     # workload 5's queries (h_q log-uniform 5..2000) in order; --k4-hmax 256 keeps short ones
-    small = np.nonzero(np.diff(w.queries.row_ptr) <= args.k4_hmax)[0][:need]
+    hq = np.diff(w.queries.row_ptr)
+    small = np.nonzero((hq <= args.k4_hmax) & (hq >= args.k4_hmin))[0][:need]
+    if len(small) < need:
+        raise SystemExit(f"--k4: only {len(small)} queries with {args.k4_hmin} <= h_q <= {args.k4_hmax}, {need} needed")
     queries = w.queries.subset(small)
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
@@ -820,8 +824,8 @@ def main_k4(args, local):
             "last_batch_sha256": hashlib.sha256(got.tobytes()).hexdigest()[:16]}
     print(json.dumps({"k4": "forward CSR pass (Eq. 6-9), LC-ACT k=%d, per form of the grouped sweep" % args.k,
                       "database": f"workload 5 cut to {n} documents: nnz {nnz}, CSR {sweep / 1e6:.0f} MB per sweep",
-                      "queries": f"{B * args.steps} of workload 5's queries with h_q <= {args.k4_hmax}, "
-                                 f"batches of {B}",
+                      "queries": f"{B * args.steps} of workload 5's queries with {args.k4_hmin} <= h_q <= "
+                                 f"{args.k4_hmax}, batches of {B}",
                       "peak_gbs": pk["hbm_gbs"], "peak_source": f"{pk['source']} HBM copy",
                       "forms": res, "generation_s": gen_s}))
 
