@@ -308,8 +308,13 @@ def recall_against(top_idx, top_dist, gpu_idx, gpu_dist, extra, K):
 
 
 def pair_opt(args):
-    """--tc-pair as a database option (nothing when left to the library's default)."""
-    return {} if getattr(args, "tc_pair", None) is None else {"tc_pair": args.tc_pair}
+    """--tc-pair and --fused-phase1 as database options (nothing when left to the library's defaults)."""
+    out = {}
+    if getattr(args, "tc_pair", None) is not None:
+        out["tc_pair"] = args.tc_pair
+    if getattr(args, "fused_phase1", None) is not None:
+        out["fused_phase1"] = args.fused_phase1
+    return out
 
 
 def bench_config(args, world):
@@ -346,6 +351,8 @@ def main():
     ap.add_argument("--probe", action="store_true",
                     help="small fixed case for profiler captures: workload 2's database, --batch "
                          "queries per batch (16 suggested), --warmup + --steps batches, ~1.5 GB on the device")
+    ap.add_argument("--fused-phase1", type=int, default=None,
+                    help="database option fused_phase1 for every form (0, 1, 2; default: the library's default)")
     ap.add_argument("--tc-pair", type=int, default=None,
                     help="fused FP32_TC table on SM pairs: 0 off, 1 64-column tiles, 2 128-column tiles "
                          "(default: the library's default)")
