@@ -629,7 +629,7 @@ def main_bench(args, rank, world, local):
                     "executed_frac_of_raw_peak": tc_exec_flops / t_dist / 1e12 / pk["bf16_tflops"]}
     rows = {"distance": dist_row,
             "fwd": {"bound": "hbm", "achieved": fwd_bytes / (phase["fwd"] / 1e3) / 1e9, "peak": pk["hbm_gbs"],
-                    "unit": "GB/s", "kernel_file": "k_sparse.cu", "per_launch": fwd_bytes / steps_prof,
+                    "unit": "GB/s", "kernel_file": "k_forward.cu", "per_launch": fwd_bytes / steps_prof,
                     "peak_source": f"{pk['source']} HBM copy; per query sweep 8 nnz + 4 (n + 1) + 4 n bytes"}}
 
     def roof(name):

@@ -1,1286 +1,9 @@
-// Sparse passes over the database (Section 5, Phase 2 and 3; Section 6, the reverse
-// direction and the symmetric maximum) and the top-K neighbour selection.
-#include <math.h>
-
-#include <algorithm>
-
-#include "emd_internal.cuh"
+// Sparse passes over the database (Section 5; Section 6, the reverse direction and the
+// symmetric maximum) and the top-K neighbour selection: the per-query launchers, the
+// all-pairs helpers and the allocation-free top-K entry point.
+#include "k_sparse_dev.cuh"
 
 namespace emd {
-namespace {
-
-__device__ __forceinline__ float warp_sum(float x)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-}
-
-// ------------------------------------------------------------------ forward pass
-//
-// Phase 2 (Eq. 6-8) and Phase 3 (Eq. 9) evaluated per nonzero: a database weight x at
-// vocabulary row u is moved into the query along row u's table, k-1 capacity-limited
-// transfers then the rest at the k-th distance.  The per-nonzero costs are summed per
-// document (t_fwd).  One warp per document, lanes over its nonzeros (coalesced col/val
-// loads), table rows gathered from L2, warp-shuffle sum.
-
-// Cost of one nonzero along its table row T (entries es apart).  Products and sums that the
-// compiler could otherwise contract into an FMA in one kernel and not in another are written
-// with __fmul_rn / __fadd_rn, so every kernel that shares these bodies rounds alike.
-template <int MEAS>
-__device__ __forceinline__ float fwd_cost_s(float x, const float2* __restrict__ T, int es, int keff)
-{
-    if (MEAS == M_RWMD) return __fmul_rn(x, T[0].x);
-    if (MEAS == M_OMR) {
-        const float2 t0 = T[0];
-        if (t0.x == 0.f && keff >= 2) {
-            const float r = x - fminf(x, t0.y);  // free transfer to the overlapping bin
-            return r != 0.f ? __fmul_rn(r, T[es].x) : 0.f;
-        }
-        return __fmul_rn(x, t0.x);
-    }
-    float r = x, c = 0.f;
-    for (int l = 0; l < keff - 1; ++l) {
-        const float2 t = T[l * es];
-        const float tau = fminf(r, t.y);
-        c = fmaf(tau, t.x, c);
-        r -= tau;
-        if (r == 0.f) return c;
-    }
-    return fmaf(r, T[(keff - 1) * es].x, c);
-}
-
-template <int MEAS>
-__device__ __forceinline__ float fwd_cost(float x, const float2* __restrict__ T, int keff)
-{
-    return fwd_cost_s<MEAS>(x, T, 1, keff);
-}
-
-// fwd_cost_s for keff <= KT without branches: the loop over the row is unrolled to KT and
-// each step is predicated on (l < keff - 1 and residual > 0), so lanes whose residual ran
-// out earlier neither diverge nor load.  Same operations in the same order: bit-identical.
-// KT = 0: rows wider than 16, the loop form.
-template <int MEAS, int KT>
-__device__ __forceinline__ float fwd_cost_p(float x, const float2* __restrict__ T, int es, int keff)
-{
-    if (KT == 0 || MEAS != M_ACT) return fwd_cost_s<MEAS>(x, T, es, keff);
-    float r = x, c = 0.f;
-#pragma unroll
-    for (int l = 0; l < (KT > 1 ? KT - 1 : 0); ++l) {
-        if (l < keff - 1 && r != 0.f) {
-            const float2 t = T[l * es];
-            const float tau = fminf(r, t.y);
-            c = fmaf(tau, t.x, c);
-            r -= tau;
-        }
-    }
-    return r != 0.f ? fmaf(r, T[(keff - 1) * es].x, c) : c;
-}
-
-// Summation order of a document's forward value, shared by every form of the pass: the
-// nonzeros are split into four phases (position e - a mod 4), each summed in CSR order,
-// then (p0 + p1) + (p2 + p3).  The per-query form gives each warp eight documents (lane =
-// 8 x phase + document slot); the grouped form gives each warp one document for eight
-// queries (lane = 8 x phase + query), so both compute every value identically.
-template <int MEAS, int KT>
-__device__ __forceinline__ void fwd_body(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                      const float* __restrict__ val, int64_t n, const float2* __restrict__ tab,
-                      int k, int keff, float* __restrict__ t_fwd)
-{
-    const int lane = threadIdx.x & 31, slot = lane & 7, ph = lane >> 3;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 8; base < n;
-         base += warps * 8) {
-        const int64_t d = base + slot;
-        const bool valid = d < n;
-        const int32_t a = valid ? row_ptr[d] : 0, b = valid ? row_ptr[d + 1] : 0;
-        float acc = 0.f;
-        int32_t e = a + ph;
-        for (; e + 12 < b; e += 16) {  // four nonzeros' costs in flight, added in order
-            const int32_t u0 = col[e], u1 = col[e + 4], u2 = col[e + 8], u3 = col[e + 12];
-            const float c0 = fwd_cost_p<MEAS, KT>(val[e], tab + (int64_t)u0 * k, 1, keff);
-            const float c1 = fwd_cost_p<MEAS, KT>(val[e + 4], tab + (int64_t)u1 * k, 1, keff);
-            const float c2 = fwd_cost_p<MEAS, KT>(val[e + 8], tab + (int64_t)u2 * k, 1, keff);
-            const float c3 = fwd_cost_p<MEAS, KT>(val[e + 12], tab + (int64_t)u3 * k, 1, keff);
-            acc = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(acc, c0), c1), c2), c3);
-        }
-        for (; e < b; e += 4)
-            acc = __fadd_rn(acc, fwd_cost_p<MEAS, KT>(val[e], tab + (int64_t)col[e] * k, 1, keff));
-        acc += __shfl_xor_sync(0xffffffffu, acc, 8);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 16);
-        if (ph == 0 && valid) t_fwd[d] = acc;
-    }
-}
-
-template <int MEAS, int KT>
-__global__ void k_fwd(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                      const float* __restrict__ val, int64_t n, const float2* __restrict__ tab,
-                      int k, int keff, float* __restrict__ t_fwd)
-{
-    fwd_body<MEAS, KT>(row_ptr, col, val, n, tab, k, keff, t_fwd);
-}
-
-// ------------------------------------------------------------------ reverse pass
-//
-// The query's bins are the sources (mass q_j), the document's bins the destinations
-// (capacities x_u), the cost block D[supp(d), j] is gathered from the Phase-1 matrix.
-// One warp per document.  Lane l of a pass handles the NJ consecutive query bins
-// j = jbase + NJ*l .. +NJ-1 and keeps, for each, a register list of the KT smallest
-// (distance, capacity) over the document's bins, visited in CSR order.  A D row segment
-// for one document bin is one NJ-float vector load per lane (a warp reads 128*NJ
-// contiguous bytes); four bins' loads are issued before their insertions.  Insertion is
-// branch-free: with 32*NJ lists per warp some list almost always changes, so a branch
-// would diverge on nearly every bin.  Strict '<' keeps the earlier bin first on equal
-// distance.
-
-// Cost of moving source mass qj along a sorted destination list (Alg. 3 / Alg. 1).  The loop
-// runs over the compile-time width with predicates so that the lists stay in registers;
-// transfers after the residual reaches zero add exactly zero.
-// sq: the lists hold squared distances (ordered the same way); they are converted here,
-// KT square roots per query bin instead of one per gathered entry.
-template <int MEAS, int KT>
-__device__ __forceinline__ float rev_cost_sorted(float qj, const float (&zs)[KT], const float (&cap)[KT],
-                                                 int keff, bool sq)
-{
-    float z[KT];
-#pragma unroll
-    for (int l = 0; l < KT; ++l) z[l] = d_value(zs[l], sq);
-    if (MEAS == M_RWMD) return __fmul_rn(qj, z[0]);
-    if (MEAS == M_OMR) {
-        if (KT >= 2 && z[0] == 0.f && keff >= 2) {
-            const float r = qj - fminf(qj, cap[0]);
-            return r != 0.f ? __fmul_rn(r, z[KT >= 2 ? 1 : 0]) : 0.f;
-        }
-        return __fmul_rn(qj, z[0]);
-    }
-    // z is ascending, so z[keff-1] is the largest of the first keff entries (distances >= 0)
-    float r = qj, c = 0.f, zlast = 0.f;
-#pragma unroll
-    for (int l = 0; l < KT; ++l) {
-        const bool capped = l < keff - 1;
-        const float tau = fminf(r, cap[l]);
-        c = capped ? fmaf(tau, z[l], c) : c;
-        r = capped ? r - tau : r;
-        zlast = fmaxf(zlast, l < keff ? z[l] : 0.f);
-    }
-    return r != 0.f ? fmaf(r, zlast, c) : c;
-}
-
-// Insert (d, x) into the ascending list z (payload c), keeping the KT smallest.
-template <int KT>
-__device__ __forceinline__ void insert_sorted(float (&z)[KT], float (&c)[KT], float d, float x)
-{
-    bool p[KT];
-#pragma unroll
-    for (int l = 0; l < KT; ++l) p[l] = d < z[l];
-#pragma unroll
-    for (int l = KT - 1; l > 0; --l) {
-        z[l] = p[l - 1] ? z[l - 1] : (p[l] ? d : z[l]);
-        c[l] = p[l - 1] ? c[l - 1] : (p[l] ? x : c[l]);
-    }
-    z[0] = p[0] ? d : z[0];
-    c[0] = p[0] ? x : c[0];
-}
-
-__device__ __forceinline__ void load_vec(const float* p, bool ok, float (&o)[1])
-{
-    o[0] = ok ? *p : INFINITY;
-}
-__device__ __forceinline__ void load_vec(const float* p, bool ok, float (&o)[2])
-{
-    const float2 v = ok ? *reinterpret_cast<const float2*>(p) : make_float2(INFINITY, INFINITY);
-    o[0] = v.x; o[1] = v.y;
-}
-__device__ __forceinline__ void load_vec(const float* p, bool ok, float (&o)[4])
-{
-    const float4 v = ok ? *reinterpret_cast<const float4*>(p) : make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
-    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-}
-
-template <int MEAS, int KT, int NJ>
-__device__ __forceinline__ void rev_body(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-      const float* __restrict__ val, int64_t n, const float* __restrict__ D, int ldd, int h,
-      const float* __restrict__ q_w, int k, const float* __restrict__ t_fwd,
-      float* __restrict__ t_rev, float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
-      const int* __restrict__ n_dev, bool sq)
-{
-    constexpr int U = 4;  // bins whose loads are in flight together
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    if (n_dev) n = min(n, (int64_t)*n_dev);  // slots filled on the device (candidate lists)
-    for (int64_t d = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); d < n; d += warps) {
-        const int64_t dd = doc_ids ? doc_ids[d] : d;  // document of this output slot
-        const int32_t a = row_ptr[dd], b = row_ptr[dd + 1];
-        const int hd = b - a;
-        const int keff = MEAS == M_RWMD ? 1 : (MEAS == M_OMR ? min(2, hd) : min(k, hd));
-        float total = 0.f;
-        for (int jbase = 0; jbase < h; jbase += 32 * NJ) {
-            const int j0 = jbase + lane * NJ;
-            const bool jin = j0 < ldd;  // ldd % 32 == 0 and NJ | 32: the whole vector is in the row
-            float z[NJ][KT], cap[NJ][KT];
-#pragma unroll
-            for (int t = 0; t < NJ; ++t)
-#pragma unroll
-                for (int l = 0; l < KT; ++l) { z[t][l] = INFINITY; cap[t][l] = 0.f; }
-            for (int32_t eb = a; eb < b; eb += 32) {
-                const int32_t e = eb + lane;
-                const int32_t u = e < b ? col[e] : 0;
-                const float x = e < b ? val[e] : 0.f;
-                const int cnt = min(32, b - eb);
-                int i = 0;
-                for (; i + U <= cnt; i += U) {
-                    float dv[U][NJ], xv[U];
-#pragma unroll
-                    for (int s = 0; s < U; ++s) {
-                        const int32_t ui = __shfl_sync(0xffffffffu, u, i + s);
-                        xv[s] = __shfl_sync(0xffffffffu, x, i + s);
-                        load_vec(D + (int64_t)ui * ldd + j0, jin, dv[s]);
-                    }
-#pragma unroll
-                    for (int s = 0; s < U; ++s)
-#pragma unroll
-                        for (int t = 0; t < NJ; ++t) insert_sorted<KT>(z[t], cap[t], dv[s][t], xv[s]);
-                }
-                for (; i < cnt; ++i) {
-                    const int32_t ui = __shfl_sync(0xffffffffu, u, i);
-                    const float xi = __shfl_sync(0xffffffffu, x, i);
-                    float dv[NJ];
-                    load_vec(D + (int64_t)ui * ldd + j0, jin, dv);
-#pragma unroll
-                    for (int t = 0; t < NJ; ++t) insert_sorted<KT>(z[t], cap[t], dv[t], xi);
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < NJ; ++t)
-                if (j0 + t < h) total = __fadd_rn(total, rev_cost_sorted<MEAS, KT>(q_w[j0 + t], z[t], cap[t], keff, sq));
-        }
-        total = warp_sum(total);
-        if (lane == 0) {
-            t_rev[d] = total;
-            if (t_max) t_max[d] = fmaxf(t_fwd[dd], total);
-        }
-    }
-}
-
-template <int MEAS, int KT, int NJ>
-__global__ void __launch_bounds__(256, 2) k_rev(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-      const float* __restrict__ val, int64_t n, const float* __restrict__ D, int ldd, int h,
-      const float* __restrict__ q_w, int k, const float* __restrict__ t_fwd,
-      float* __restrict__ t_rev, float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
-      const int* __restrict__ n_dev, bool sq)
-{
-    rev_body<MEAS, KT, NJ>(row_ptr, col, val, n, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev, sq);
-}
-
-// Candidate-list form: a block of W warps per candidate slot.  Warp w scans the w-th
-// contiguous chunk of the document's bins; warp 0 then inserts the other chunks' lists in
-// chunk order.  Strict '<' keeps an earlier chunk's entry ahead of an equal distance from a
-// later one, so the merged list (and the cost, summed in the same lane order) is
-// bit-identical to the one-warp kernel above.  W times the warps on a few hundred
-// documents, whose single-warp scans are latency-bound.
-template <int MEAS, int KT, int NJ, int W>
-__device__ __forceinline__ void rev_blk_body(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-          const float* __restrict__ val, const float* __restrict__ D, int ldd, int h,
-          const float* __restrict__ q_w, int k, const float* __restrict__ t_fwd,
-          float* __restrict__ t_rev, float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
-          const int* __restrict__ n_dev, bool sq, const int32_t* __restrict__ rmap = nullptr)
-{
-    constexpr int U = 4;
-    __shared__ float sz[W - 1][32 * NJ][KT];
-    __shared__ float sc[W - 1][32 * NJ][KT];
-    const int slot = blockIdx.x;
-    if (slot >= min(*n_dev, (int)gridDim.x)) return;  // uniform over the block
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t dd = doc_ids[slot];
-    const int32_t a = row_ptr[dd], b = row_ptr[dd + 1];
-    const int hd = b - a;
-    const int keff = MEAS == M_RWMD ? 1 : (MEAS == M_OMR ? min(2, hd) : min(k, hd));
-    const int chunk = (hd + W - 1) / W;
-    const int32_t ca = a + min(hd, warp * chunk), cb = a + min(hd, (warp + 1) * chunk);
-    float total = 0.f;
-    for (int jbase = 0; jbase < h; jbase += 32 * NJ) {
-        const int j0 = jbase + lane * NJ;
-        const bool jin = j0 < ldd;
-        float z[NJ][KT], cap[NJ][KT];
-#pragma unroll
-        for (int t = 0; t < NJ; ++t)
-#pragma unroll
-            for (int l = 0; l < KT; ++l) { z[t][l] = INFINITY; cap[t][l] = 0.f; }
-        for (int32_t eb = ca; eb < cb; eb += 32) {
-            const int32_t e = eb + lane;
-            const int32_t u = e < cb ? col[e] : 0;
-            const float x = e < cb ? val[e] : 0.f;
-            const int cnt = min(32, cb - eb);
-            int i = 0;
-            for (; i + U <= cnt; i += U) {
-                float dv[U][NJ], xv[U];
-#pragma unroll
-                for (int s = 0; s < U; ++s) {
-                    const int32_t ui = __shfl_sync(0xffffffffu, u, i + s);
-                    xv[s] = __shfl_sync(0xffffffffu, x, i + s);
-                    load_vec(D + (rmap ? (int64_t)rmap[ui] : (int64_t)ui) * ldd + j0, jin, dv[s]);
-                }
-#pragma unroll
-                for (int s = 0; s < U; ++s)
-#pragma unroll
-                    for (int t = 0; t < NJ; ++t) insert_sorted<KT>(z[t], cap[t], dv[s][t], xv[s]);
-            }
-            for (; i < cnt; ++i) {
-                const int32_t ui = __shfl_sync(0xffffffffu, u, i);
-                const float xi = __shfl_sync(0xffffffffu, x, i);
-                float dv[NJ];
-                load_vec(D + (rmap ? (int64_t)rmap[ui] : (int64_t)ui) * ldd + j0, jin, dv);
-#pragma unroll
-                for (int t = 0; t < NJ; ++t) insert_sorted<KT>(z[t], cap[t], dv[t], xi);
-            }
-        }
-        if (warp > 0) {
-#pragma unroll
-            for (int t = 0; t < NJ; ++t)
-#pragma unroll
-                for (int l = 0; l < KT; ++l) {
-                    sz[warp - 1][lane * NJ + t][l] = z[t][l];
-                    sc[warp - 1][lane * NJ + t][l] = cap[t][l];
-                }
-        }
-        __syncthreads();
-        if (warp == 0) {
-#pragma unroll
-            for (int w = 0; w < W - 1; ++w)
-#pragma unroll
-                for (int t = 0; t < NJ; ++t)
-#pragma unroll
-                    for (int l = 0; l < KT; ++l)
-                        insert_sorted<KT>(z[t], cap[t], sz[w][lane * NJ + t][l], sc[w][lane * NJ + t][l]);
-#pragma unroll
-            for (int t = 0; t < NJ; ++t)
-                if (j0 + t < h) total = __fadd_rn(total, rev_cost_sorted<MEAS, KT>(q_w[j0 + t], z[t], cap[t], keff, sq));
-        }
-        __syncthreads();
-    }
-    if (warp == 0) {
-        total = warp_sum(total);
-        if (lane == 0) {
-            t_rev[slot] = total;
-            if (t_max) t_max[slot] = fmaxf(t_fwd[dd], total);
-        }
-    }
-}
-
-template <int MEAS, int KT, int NJ, int W>
-__global__ void __launch_bounds__(W * 32, (W >= 8 ? 2 : 4)) k_rev_blk(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-          const float* __restrict__ val, const float* __restrict__ D, int ldd, int h,
-          const float* __restrict__ q_w, int k, const float* __restrict__ t_fwd,
-          float* __restrict__ t_rev, float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
-          const int* __restrict__ n_dev, bool sq)
-{
-    rev_blk_body<MEAS, KT, NJ, W>(row_ptr, col, val, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev, sq);
-}
-
-// k above the register width (ICT, large k): per lane, successive minima over the
-// document's bins, each strictly after the previous in (distance, bin position) order,
-// until the source mass is placed.  O(steps * h_d) per query bin.  The query bins are
-// taken in tiles of 32 (lane = bin within the tile); a lane's costs are summed per tile
-// residue t mod kRevW, and the kRevW partial sums are then added in order -- the same
-// arithmetic whether one warp walks all tiles (rev_generic_body) or kRevW warps split them
-// (rev_generic_blk_body, for candidate lists).
-constexpr int kRevW = 8;
-
-template <int MEAS>
-__device__ __forceinline__ float rev_generic_bin(const int32_t* __restrict__ col, const float* __restrict__ val,
-                                                 int32_t a, int32_t b, int keff, const float* __restrict__ D, int ldd,
-                                                 int j, float qj, bool sq)
-{
-    float r = qj, c = 0.f;
-    float pz = -INFINITY;
-    int pe = -1;
-    for (int l = 0; l < keff; ++l) {
-        float bz = INFINITY, bx = 0.f;
-        int be = INT32_MAX;
-        for (int32_t e = a; e < b; ++e) {
-            const float dv = D[(int64_t)col[e] * ldd + j];
-            const int pos = e - a;
-            const bool after = dv > pz || (dv == pz && pos > pe);
-            if (after && (dv < bz || (dv == bz && pos < be))) { bz = dv; be = pos; bx = val[e]; }
-        }
-        const float zd = d_value(bz, sq);
-        if (l < keff - 1) {
-            const float tau = fminf(r, bx);
-            c = fmaf(tau, zd, c);
-            r -= tau;
-            if (r == 0.f) break;
-        } else {
-            c = fmaf(r, zd, c);
-        }
-        pz = bz;
-        pe = be;
-    }
-    return c;
-}
-
-template <int MEAS>
-__device__ __forceinline__ void rev_generic_body(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                              const float* __restrict__ val, int64_t n, const float* __restrict__ D,
-                              int ldd, int h, const float* __restrict__ q_w, int k,
-                              const float* __restrict__ t_fwd, float* __restrict__ t_rev,
-                              float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
-                              const int* __restrict__ n_dev, bool sq)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    if (n_dev) n = min(n, (int64_t)*n_dev);
-    for (int64_t d = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); d < n; d += warps) {
-        const int64_t dd = doc_ids ? doc_ids[d] : d;
-        const int32_t a = row_ptr[dd], b = row_ptr[dd + 1];
-        const int hd = b - a;
-        const int keff = MEAS == M_ICT ? hd : min(k, hd);
-        float part[kRevW];
-#pragma unroll
-        for (int w = 0; w < kRevW; ++w) part[w] = 0.f;
-        for (int t0 = 0; t0 * 32 < h; t0 += kRevW) {
-#pragma unroll
-            for (int w = 0; w < kRevW; ++w) {
-                const int j = (t0 + w) * 32 + lane;
-                if (j < h) part[w] = __fadd_rn(part[w], rev_generic_bin<MEAS>(col, val, a, b, keff, D, ldd, j, q_w[j], sq));
-            }
-        }
-        float total = part[0];
-#pragma unroll
-        for (int w = 1; w < kRevW; ++w) total = __fadd_rn(total, part[w]);
-        total = warp_sum(total);
-        if (lane == 0) {
-            t_rev[d] = total;
-            if (t_max) t_max[d] = fmaxf(t_fwd[dd], total);
-        }
-    }
-}
-
-// Candidate-list form: a block of kRevW warps per slot, warp w taking the query-bin tiles
-// t = w, w + kRevW, ...; warp 0 adds the partial sums in warp order.  Same values as
-// rev_generic_body.
-template <int MEAS>
-__device__ __forceinline__ void rev_generic_blk_body(const int32_t* __restrict__ row_ptr,
-                                                     const int32_t* __restrict__ col, const float* __restrict__ val,
-                                                     const float* __restrict__ D, int ldd, int h,
-                                                     const float* __restrict__ q_w, int k,
-                                                     const float* __restrict__ t_fwd, float* __restrict__ t_rev,
-                                                     float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
-                                                     const int* __restrict__ n_dev, bool sq)
-{
-    __shared__ float sp[kRevW][32];
-    const int slot = blockIdx.x;
-    if (slot >= min(*n_dev, (int)gridDim.x)) return;  // uniform over the block
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t dd = doc_ids[slot];
-    const int32_t a = row_ptr[dd], b = row_ptr[dd + 1];
-    const int hd = b - a;
-    const int keff = MEAS == M_ICT ? hd : min(k, hd);
-    float part = 0.f;
-    for (int t = warp; t * 32 < h; t += kRevW) {
-        const int j = t * 32 + lane;
-        if (j < h) part = __fadd_rn(part, rev_generic_bin<MEAS>(col, val, a, b, keff, D, ldd, j, q_w[j], sq));
-    }
-    sp[warp][lane] = part;
-    __syncthreads();
-    if (warp == 0) {
-        float total = sp[0][lane];
-#pragma unroll
-        for (int w = 1; w < kRevW; ++w) total = __fadd_rn(total, sp[w][lane]);
-        total = warp_sum(total);
-        if (lane == 0) {
-            t_rev[slot] = total;
-            if (t_max) t_max[slot] = fmaxf(t_fwd[dd], total);
-        }
-    }
-}
-
-template <int MEAS>
-__global__ void __launch_bounds__(kRevW * 32) k_rev_generic_blk(const int32_t* __restrict__ row_ptr,
-                                  const int32_t* __restrict__ col, const float* __restrict__ val,
-                                  const float* __restrict__ D, int ldd, int h, const float* __restrict__ q_w, int k,
-                                  const float* __restrict__ t_fwd, float* __restrict__ t_rev,
-                                  float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
-                                  const int* __restrict__ n_dev, bool sq)
-{
-    rev_generic_blk_body<MEAS>(row_ptr, col, val, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev, sq);
-}
-
-template <int MEAS>
-__global__ void k_rev_generic(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                              const float* __restrict__ val, int64_t n, const float* __restrict__ D,
-                              int ldd, int h, const float* __restrict__ q_w, int k,
-                              const float* __restrict__ t_fwd, float* __restrict__ t_rev,
-                              float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
-                              const int* __restrict__ n_dev, bool sq)
-{
-    rev_generic_body<MEAS>(row_ptr, col, val, n, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev, sq);
-}
-
-// ------------------------------------------------------------------ top-K selection
-//
-// Keys are (float bits of the distance << 32) | document id: distances are >= 0, so the
-// unsigned order of the keys is the (distance, id) order and every key is unique.
-// Each thread keeps a sorted register list of its KT smallest keys; the block merges the
-// lists pairwise in shared memory (log2(threads) levels).  With several blocks per query
-// the block results go to scratch and one more block merges them.
-
-template <int KT>
-__device__ __forceinline__ void list_insert(unsigned long long (&L)[KT], unsigned long long key)
-{
-    if (key < L[KT - 1]) {
-        L[KT - 1] = key;
-#pragma unroll
-        for (int l = KT - 1; l > 0; --l) {
-            if (L[l] < L[l - 1]) { unsigned long long t = L[l]; L[l] = L[l - 1]; L[l - 1] = t; }
-        }
-    }
-}
-
-template <int KT>
-__device__ void block_merge_and_emit(unsigned long long (&L)[KT], int K, unsigned long long* out_keys,
-                                     int64_t* out_idx, float* out_dist)
-{
-    extern __shared__ unsigned long long sm[];  // [blockDim.x][KT]
-    const int tid = threadIdx.x;
-#pragma unroll
-    for (int l = 0; l < KT; ++l) sm[tid * KT + l] = L[l];
-    __syncthreads();
-    for (int active = blockDim.x; active > 1; active >>= 1) {
-        const int half = active >> 1;
-        if (tid < half) {
-            const unsigned long long* A = sm + tid * KT;
-            const unsigned long long* B = sm + (tid + half) * KT;
-            unsigned long long M[KT];
-            int ia = 0, ib = 0;
-#pragma unroll
-            for (int l = 0; l < KT; ++l) {
-                const unsigned long long x = A[ia], y = B[ib];
-                if (x <= y) { M[l] = x; ++ia; } else { M[l] = y; ++ib; }
-            }
-#pragma unroll
-            for (int l = 0; l < KT; ++l) sm[tid * KT + l] = M[l];
-        }
-        __syncthreads();
-    }
-    if (tid == 0) {
-        for (int l = 0; l < K; ++l) {
-            const unsigned long long key = sm[l];
-            if (out_keys) out_keys[l] = key;
-            if (out_idx) {
-                out_idx[l] = (key == ~0ull) ? -1 : (int64_t)(key & 0xffffffffull);
-                out_dist[l] = (key == ~0ull) ? INFINITY : __uint_as_float((unsigned)(key >> 32));
-            }
-        }
-    }
-}
-
-template <int KT>
-__device__ __forceinline__ void topk_values_body(const float* __restrict__ t, int64_t n, int K, int64_t per_block,
-                                                 unsigned long long* __restrict__ scratch_row,
-                                                 int64_t* __restrict__ out_idx, float* __restrict__ out_dist)
-{
-    unsigned long long L[KT];
-#pragma unroll
-    for (int l = 0; l < KT; ++l) L[l] = ~0ull;
-    const int64_t lo = (int64_t)blockIdx.x * per_block;
-    const int64_t hi = min(n, lo + per_block);
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const unsigned long long key =
-            ((unsigned long long)__float_as_uint(t[i]) << 32) | (unsigned long long)(uint32_t)i;
-        list_insert<KT>(L, key);
-    }
-    if (gridDim.x == 1)
-        block_merge_and_emit<KT>(L, K, nullptr, out_idx, out_dist);
-    else
-        block_merge_and_emit<KT>(L, KT, scratch_row + (int64_t)blockIdx.x * KT, nullptr, nullptr);
-}
-
-template <int KT>
-__device__ __forceinline__ void topk_keys_body(const unsigned long long* __restrict__ keys, int64_t count, int K,
-                                               int64_t* __restrict__ out_idx, float* __restrict__ out_dist)
-{
-    unsigned long long L[KT];
-#pragma unroll
-    for (int l = 0; l < KT; ++l) L[l] = ~0ull;
-    for (int64_t i = threadIdx.x; i < count; i += blockDim.x) list_insert<KT>(L, keys[i]);
-    block_merge_and_emit<KT>(L, K, nullptr, out_idx, out_dist);
-}
-
-template <int KT>
-__global__ void __launch_bounds__(kTopkThreads)
-k_topk_values(const float* __restrict__ t, int64_t n, int64_t ldt, int K, int64_t per_block,
-              unsigned long long* __restrict__ scratch, int64_t* __restrict__ out_idx,
-              float* __restrict__ out_dist)
-{
-    const int64_t row = blockIdx.y;
-    topk_values_body<KT>(t + row * ldt, n, K, per_block, scratch + row * kTopkScratchRow, out_idx + row * K,
-                         out_dist + row * K);
-}
-
-template <int KT>
-__global__ void __launch_bounds__(kTopkThreads)
-k_topk_keys(const unsigned long long* __restrict__ keys, int64_t count, int K,
-            int64_t* __restrict__ out_idx, float* __restrict__ out_dist)
-{
-    const int64_t row = blockIdx.x;
-    topk_keys_body<KT>(keys + row * kTopkScratchRow, count, K, out_idx + row * K, out_dist + row * K);
-}
-
-// Batched forms: row q of the batch reads qd[q].t_fwd and writes sel_idx / sel_val (the
-// forward top-K of the pruned path, fwd_rows) or reads t_out and writes out_idx / out_dist.
-template <int KT>
-__global__ void __launch_bounds__(kTopkThreads)
-k_topk_values_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t n, int K, int64_t per_block,
-                unsigned long long* __restrict__ scratch, bool fwd_rows)
-{
-    if ((int)blockIdx.y >= *nq) return;
-    const QDesc& d = qd[blockIdx.y];
-    topk_values_body<KT>(fwd_rows ? d.t_fwd : d.t_out, n, K, per_block,
-                         scratch + (int64_t)blockIdx.y * kTopkScratchRow, fwd_rows ? d.sel_idx : d.out_idx,
-                         fwd_rows ? d.sel_val : d.out_dist);
-}
-
-template <int KT>
-__global__ void __launch_bounds__(kTopkThreads)
-k_topk_keys_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t count, int K,
-              const unsigned long long* __restrict__ scratch, bool fwd_rows)
-{
-    if ((int)blockIdx.x >= *nq) return;
-    const QDesc& d = qd[blockIdx.x];
-    topk_keys_body<KT>(scratch + (int64_t)blockIdx.x * kTopkScratchRow, count, K, fwd_rows ? d.sel_idx : d.out_idx,
-                       fwd_rows ? d.sel_val : d.out_dist);
-}
-
-template <int KT>
-cudaError_t topk_kt_b(const QDesc* qd, const int* nq, int max_q, int64_t n, int K, unsigned long long* scratch,
-                      bool fwd_rows, cudaStream_t st)
-{
-    const size_t smem = (size_t)kTopkThreads * KT * sizeof(unsigned long long);
-    const int blocks = topk_blocks(n);
-    const int64_t per_block = (n + blocks - 1) / blocks;
-    if (smem > 48 * 1024) {
-        cudaFuncSetAttribute(k_topk_values_b<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_topk_keys_b<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    }
-    k_topk_values_b<KT><<<dim3(blocks, (unsigned)max_q), kTopkThreads, smem, st>>>(qd, nq, n, K, per_block, scratch,
-                                                                                    fwd_rows);
-    if (blocks > 1)
-        k_topk_keys_b<KT><<<(unsigned)max_q, kTopkThreads, smem, st>>>(qd, nq, (int64_t)blocks * KT, K, scratch,
-                                                                        fwd_rows);
-    return cudaGetLastError();
-}
-
-template <int KT>
-cudaError_t topk_kt(const float* t, int64_t rows, int64_t n, int64_t ldt, int K,
-                    unsigned long long* scratch, int64_t* out_idx, float* out_dist, cudaStream_t st)
-{
-    const size_t smem = (size_t)kTopkThreads * KT * sizeof(unsigned long long);
-    const int blocks = topk_blocks(n);
-    const int64_t per_block = (n + blocks - 1) / blocks;
-    if (smem > 48 * 1024) {
-        cudaFuncSetAttribute(k_topk_values<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_topk_keys<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    }
-    k_topk_values<KT><<<dim3(blocks, (unsigned)rows), kTopkThreads, smem, st>>>(t, n, ldt, K, per_block, scratch,
-                                                                                 out_idx, out_dist);
-    if (blocks > 1)
-        k_topk_keys<KT><<<(unsigned)rows, kTopkThreads, smem, st>>>(scratch, (int64_t)blocks * KT, K, out_idx,
-                                                                     out_dist);
-    return cudaGetLastError();
-}
-
-// ------------------------------------------------------------------ pruned symmetric top-K
-//
-// max(fwd, rev) >= fwd.  With theta = fwd_K * (1 + 2^-7) (fwd_K the K-th smallest forward
-// value), the candidates are the documents with fwd <= theta; every other document has
-// sym >= fwd > theta.  Once the K-th smallest symmetric value among the candidates is
-// <= theta, no other document can enter the top-K, not even by the id tie-break.
-
-__device__ __forceinline__ float prune_theta(float fwd_k) { return fwd_k * (1.0f + 0.0078125f); }
-
-__device__ __forceinline__ void prune_compact_body(const float* __restrict__ t_fwd, int64_t n, const float* __restrict__ sel_val,
-                                int K, int cap, int64_t* __restrict__ cand, int* __restrict__ count)
-{
-    const float theta = prune_theta(sel_val[K - 1]);
-    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < n; d += (int64_t)gridDim.x * blockDim.x) {
-        if (t_fwd[d] <= theta) {
-            const int pos = atomicAdd(count, 1);
-            if (pos < cap) cand[pos] = d;
-        }
-    }
-}
-
-__global__ void k_prune_compact(const float* __restrict__ t_fwd, int64_t n, const float* __restrict__ sel_val,
-                                int K, int cap, int64_t* __restrict__ cand, int* __restrict__ count)
-{
-    prune_compact_body(t_fwd, n, sel_val, K, cap, cand, count);
-}
-
-// Final selection over the candidates: thread i ranks candidate i in (sym, id) order
-// against the other filled slots (one 64-bit key compare each: distances are >= 0, so the
-// key order is the (distance, id) order); ranks < K are written; ok = no overflow and
-// K-th <= theta.
-__device__ __forceinline__ void prune_select_body(const int64_t* __restrict__ cand, const float* __restrict__ sym,
-                               const int* __restrict__ count, int cap, const float* __restrict__ sel_val,
-                               int K, int64_t* __restrict__ out_idx, float* __restrict__ out_dist,
-                               int* __restrict__ ok, bool complete = true)
-{
-    __shared__ unsigned long long key[kPruneCap];
-    __shared__ float kth;
-    const int c = min(*count, cap);
-    const int i = threadIdx.x;
-    const unsigned long long me =
-        i < c ? ((unsigned long long)__float_as_uint(sym[i]) << 32) | (unsigned long long)(uint32_t)cand[i] : ~0ull;
-    key[i] = me;
-    if (i == 0) kth = INFINITY;
-    __syncthreads();
-    int r = 0;
-    for (int j = 0; j < c; ++j) r += key[j] < me ? 1 : 0;
-    if (i < c && r < K) {
-        out_idx[r] = (int64_t)(me & 0xffffffffull);
-        out_dist[r] = __uint_as_float((unsigned)(me >> 32));
-    }
-    if (i < c && r == K - 1) kth = __uint_as_float((unsigned)(me >> 32));
-    __syncthreads();
-    // 1: certified; 0: not certified (recompute over all documents); 2: the candidate
-    // block of the fused path overflowed (retry with the full distance matrix)
-    if (i == 0) *ok = !complete ? 2 : (*count <= cap && c >= K && kth <= prune_theta(sel_val[K - 1])) ? 1 : 0;
-}
-
-__global__ void k_prune_select(const int64_t* __restrict__ cand, const float* __restrict__ sym,
-                               const int* __restrict__ count, int cap, const float* __restrict__ sel_val,
-                               int K, int64_t* __restrict__ out_idx, float* __restrict__ out_dist,
-                               int* __restrict__ ok)
-{
-    prune_select_body(cand, sym, count, cap, sel_val, K, out_idx, out_dist, ok);
-}
-
-template <int MEAS>
-cudaError_t rev_meas_blk(int k, const int32_t* row_ptr, const int32_t* col, const float* val, int slots,
-                         const float* D, int ldd, int h, const float* q_w, const float* t_fwd,
-                         float* t_rev, float* t_max, const int64_t* doc_ids, const int* n_dev, bool sq,
-                         cudaStream_t st)
-{
-    constexpr int W = 4;
-    const int kt = MEAS == M_RWMD ? 1 : (MEAS == M_OMR ? 2 : k);
-    const bool wide = h > 32;
-#define EMD_REVB(KT, NJ) k_rev_blk<MEAS, KT, NJ, W><<<slots, W * 32, 0, st>>>(row_ptr, col, val, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev, sq)
-    if (kt <= 1) { if (wide) EMD_REVB(1, 4); else EMD_REVB(1, 1); }
-    else if (kt <= 2) { if (wide) EMD_REVB(2, 4); else EMD_REVB(2, 1); }
-    else if (kt <= 4) { if (wide) EMD_REVB(4, 4); else EMD_REVB(4, 1); }
-    else if (kt <= 8) { if (wide) EMD_REVB(8, 2); else EMD_REVB(8, 1); }
-    else EMD_REVB(16, 1);
-#undef EMD_REVB
-    return cudaGetLastError();
-}
-
-// ------------------------------------------------------------------ batched forms
-
-template <int MEAS, int KT>
-__global__ void k_fwd_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t* __restrict__ row_ptr,
-                        const int32_t* __restrict__ col, const float* __restrict__ val, int64_t n, bool to_out)
-{
-    if ((int)blockIdx.y >= *nq) return;
-    const QDesc& d = qd[blockIdx.y];
-    fwd_body<MEAS, KT>(row_ptr, col, val, n, d.tab, d.tk, d.tk, to_out ? d.t_out : d.t_fwd);
-}
-
-// One sweep of the CSR for a group of kFwdGroup (8) consecutive queries of the batch: a warp
-// takes a document, lane = 8 x phase + query.  The 8 lanes of a nonzero read the same col /
-// val and adjacent table entries (the group's tables are interleaved by entry), so a gather
-// instruction touches 4 table rows instead of 32; the CSR is read once per group.  Values
-// are bit-identical to the per-query form (same phases, same order).  The sweep is bound by
-// the latency of its dependent gathers, not by bandwidth: 32 registers give 8 blocks (all 64
-// warps) per SM, and two nonzeros per lane per step fit in them (four spill or cost occupancy;
-// measured on 1e6 documents, 64 mixed-size queries: 19.6 ms at 6 blocks and four nonzeros,
-// 16.9 ms at 8 blocks and two).
-template <int MEAS, int KT>
-__global__ void __launch_bounds__(256, 8)
-k_fwd_g(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t* __restrict__ row_ptr,
-        const int32_t* __restrict__ col, const float* __restrict__ val, int64_t n, bool to_out)
-{
-    const int q0 = blockIdx.y * kFwdGroup;
-    const int nqv = *nq;
-    if (q0 >= nqv) return;
-    const int lane = threadIdx.x & 31, g = lane & 7, ph = lane >> 3;
-    const bool act = q0 + g < nqv;
-    const QDesc& dq = qd[act ? q0 + g : q0];
-    const float2* tq = dq.tab;
-    const int kq = dq.tk;
-    float* oq = to_out ? dq.t_out : dq.t_fwd;
-    const int rs = dq.tab_rs, es = dq.tab_es;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t d = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); d < n; d += warps) {
-        const int32_t a = row_ptr[d], b = row_ptr[d + 1];
-        float acc = 0.f;
-        int32_t e = a + ph;
-        for (; e + 4 < b; e += 8) {  // two nonzeros' costs in flight, added in order
-            const int32_t u0 = col[e], u1 = col[e + 4];
-            const float x0 = val[e], x1 = val[e + 4];
-            if (act) {
-                const float c0 = fwd_cost_p<MEAS, KT>(x0, tq + (int64_t)u0 * rs, es, kq);
-                const float c1 = fwd_cost_p<MEAS, KT>(x1, tq + (int64_t)u1 * rs, es, kq);
-                acc = __fadd_rn(__fadd_rn(acc, c0), c1);
-            }
-        }
-        if (e < b) {
-            const int32_t u = col[e];
-            const float x = val[e];
-            if (act) acc = __fadd_rn(acc, fwd_cost_p<MEAS, KT>(x, tq + (int64_t)u * rs, es, kq));
-        }
-        acc += __shfl_xor_sync(0xffffffffu, acc, 8);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 16);
-        if (ph == 0 && act) oq[d] = acc;
-    }
-}
-
-// Cost of one nonzero from the first KR entries of its table row already in registers
-// (entries KR.. are loaded here, only while mass remains; entry l at T[l * es]).  The same
-// operations in the same order as fwd_cost_p, so the values are bit-identical.
-template <int MEAS, int KT, int KR>
-__device__ __forceinline__ float fwd_cost_reg(float x, const float2 (&E)[KR], const float2* __restrict__ T, int es,
-                                              int keff)
-{
-    if (MEAS == M_RWMD) return __fmul_rn(x, E[0].x);
-    if (MEAS == M_OMR) {
-        if (E[0].x == 0.f && keff >= 2) {
-            const float r = x - fminf(x, E[0].y);
-            return r != 0.f ? __fmul_rn(r, (KR > 1 ? E[KR > 1 ? 1 : 0] : T[es]).x) : 0.f;
-        }
-        return __fmul_rn(x, E[0].x);
-    }
-    float r = x, c = 0.f;
-#pragma unroll
-    for (int l = 0; l < (KT > 1 ? KT - 1 : 0); ++l) {
-        if (l < keff - 1 && r != 0.f) {
-            const float2 t = l < KR ? E[l < KR ? l : 0] : T[l * es];
-            const float tau = fminf(r, t.y);
-            c = fmaf(tau, t.x, c);
-            r -= tau;
-        }
-    }
-    if (r == 0.f) return c;
-    const int lk = keff - 1;
-    float zl;
-    if (lk < KR) {
-        zl = E[0].x;
-#pragma unroll
-        for (int l = 1; l < KR; ++l) zl = lk == l ? E[l].x : zl;
-    } else {
-        zl = T[lk * es].x;
-    }
-    return fmaf(r, zl, c);
-}
-
-// Forward pass of a group of kFwdGroup queries in one sweep of the CSR, tables of width
-// <= KT (1, 2, 4, 8, 16) stored query-major within a row: query g's entries of row u at
-// tab + u * tab_rs + l (tab_rs = 8 KT, the query's own offset g KT is in its descriptor), so
-// a lane reads its first min(KT, 4) entries with independent vector loads before any
-// arithmetic -- no chain of dependent loads per nonzero.  A warp takes a document; the
-// column ids and weights of 32 consecutive nonzeros are read with one coalesced load per
-// lane and handed to the lanes that use them by shuffles (lane = 8 x phase + query, phase
-// = nonzero position mod 4).  Each phase sums its nonzeros in CSR order, then (p0 + p1) +
-// (p2 + p3): the order of every other form of the pass, so values are bit-identical.
-template <int MEAS, int KT>
-__global__ void __launch_bounds__(256, 3)
-k_fwd_gv(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t* __restrict__ row_ptr,
-         const int32_t* __restrict__ col, const float* __restrict__ val, int64_t n, bool to_out)
-{
-    constexpr int KR = KT < 4 ? KT : 4;
-    const int q0 = blockIdx.y * kFwdGroup;
-    const int nqv = *nq;
-    if (q0 >= nqv) return;
-    const int lane = threadIdx.x & 31, g = lane & 7, ph = lane >> 3;
-    const bool act = q0 + g < nqv;
-    const QDesc& dq = qd[act ? q0 + g : q0];
-    const float2* tq = dq.tab;
-    const int kq = dq.tk;
-    float* oq = to_out ? dq.t_out : dq.t_fwd;
-    const int rs = dq.tab_rs;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t d = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); d < n; d += warps) {
-        const int32_t a = row_ptr[d], b = row_ptr[d + 1];
-        float acc = 0.f;
-        for (int32_t eb = a; eb < b; eb += 32) {
-            const bool lin = eb + lane < b;
-            const int32_t cu = lin ? col[eb + lane] : 0;
-            const float cx = lin ? val[eb + lane] : 0.f;
-#pragma unroll
-            for (int r = 0; r < 8; r += 4) {  // four nonzeros per lane in flight
-                float2 E[4][KR];
-                float xs[4];
-                int32_t us[4];
-                bool ok[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int src = 4 * (r + i) + ph;
-                    us[i] = __shfl_sync(0xffffffffu, cu, src);
-                    xs[i] = __shfl_sync(0xffffffffu, cx, src);
-                    ok[i] = act && eb + src < b;
-                    const float2* T = tq + (int64_t)us[i] * rs;
-                    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if constexpr (KR == 4) {
-                        const float4 v0 = ok[i] ? *reinterpret_cast<const float4*>(T) : z4;
-                        const float4 v1 = ok[i] ? *reinterpret_cast<const float4*>(T + 2) : z4;
-                        E[i][0] = make_float2(v0.x, v0.y);
-                        E[i][1] = make_float2(v0.z, v0.w);
-                        E[i][2] = make_float2(v1.x, v1.y);
-                        E[i][3] = make_float2(v1.z, v1.w);
-                    } else if constexpr (KR == 2) {
-                        const float4 v0 = ok[i] ? *reinterpret_cast<const float4*>(T) : z4;
-                        E[i][0] = make_float2(v0.x, v0.y);
-                        E[i][1] = make_float2(v0.z, v0.w);
-                    } else {
-                        E[i][0] = ok[i] ? T[0] : make_float2(0.f, 0.f);
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    if (ok[i]) acc = __fadd_rn(acc, fwd_cost_reg<MEAS, KT, KR>(xs[i], E[i], tq + (int64_t)us[i] * rs, 1, kq));
-            }
-        }
-        acc += __shfl_xor_sync(0xffffffffu, acc, 8);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 16);
-        if (ph == 0 && act) oq[d] = acc;
-    }
-}
-
-// The entry-chain sweep of k_fwd_g with the CSR read one group ahead: each lane (four
-// nonzeros of its phase per step) loads the column ids and weights of its next four
-// nonzeros before it evaluates the current ones, so the DRAM latency of the stream overlaps
-// the table gathers.  Same steps and summation order as k_fwd_g: bit-identical.
-template <int MEAS, int KT>
-__global__ void k_fwd_gp(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t* __restrict__ row_ptr,
-                         const int32_t* __restrict__ col, const float* __restrict__ val, int64_t n, bool to_out)
-{
-    const int q0 = blockIdx.y * kFwdGroup;
-    const int nqv = *nq;
-    if (q0 >= nqv) return;
-    const int lane = threadIdx.x & 31, g = lane & 7, ph = lane >> 3;
-    const bool act = q0 + g < nqv;
-    const QDesc& dq = qd[act ? q0 + g : q0];
-    const float2* tq = dq.tab;
-    const int kq = dq.tk;
-    float* oq = to_out ? dq.t_out : dq.t_fwd;
-    const int rs = dq.tab_rs, es = dq.tab_es;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t d = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); d < n; d += warps) {
-        const int32_t a = row_ptr[d], b = row_ptr[d + 1];
-        float acc = 0.f;
-        int32_t e = a + ph;
-        int32_t pu[4];
-        float px[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const bool v = e + 4 * i < b;
-            pu[i] = v ? col[e + 4 * i] : 0;
-            px[i] = v ? val[e + 4 * i] : 0.f;
-        }
-        while (e < b) {
-            int32_t u[4];
-            float x[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                u[i] = pu[i];
-                x[i] = px[i];
-            }
-            const int32_t en = e + 16;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const bool v = en + 4 * i < b;
-                pu[i] = v ? col[en + 4 * i] : 0;
-                px[i] = v ? val[en + 4 * i] : 0.f;
-            }
-            if (act) {
-                float c[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    c[i] = e + 4 * i < b ? fwd_cost_p<MEAS, KT>(x[i], tq + (int64_t)u[i] * rs, es, kq) : 0.f;
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    if (e + 4 * i < b) acc = __fadd_rn(acc, c[i]);
-            }
-            e = en;
-        }
-        acc += __shfl_xor_sync(0xffffffffu, acc, 8);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 16);
-        if (ph == 0 && act) oq[d] = acc;
-    }
-}
-
-// Forward pass of a group of kFwdGroup queries, entry-interleaved tables (row u, entry l,
-// query g at tab[u * tab_rs + l * kFwdGroup], so the group's entry l of a row is 64
-// contiguous bytes): the column ids and weights of 32 nonzeros are read with one coalesced
-// load and handed out by shuffles as in k_fwd_gv; the first two entries of each row are
-// loaded before any arithmetic, later ones only while mass remains.  Fewer registers than
-// k_fwd_gv (more resident warps), fewer bytes per nonzero.  Same values as every other form.
-template <int MEAS, int KT>
-__global__ void __launch_bounds__(256, 4)
-k_fwd_gc(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t* __restrict__ row_ptr,
-         const int32_t* __restrict__ col, const float* __restrict__ val, int64_t n, bool to_out)
-{
-    constexpr int KR = KT < 2 ? KT : 2;
-    const int q0 = blockIdx.y * kFwdGroup;
-    const int nqv = *nq;
-    if (q0 >= nqv) return;
-    const int lane = threadIdx.x & 31, g = lane & 7, ph = lane >> 3;
-    const bool act = q0 + g < nqv;
-    const QDesc& dq = qd[act ? q0 + g : q0];
-    const float2* tq = dq.tab;
-    const int kq = dq.tk;
-    float* oq = to_out ? dq.t_out : dq.t_fwd;
-    const int rs = dq.tab_rs, es = dq.tab_es;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t d = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); d < n; d += warps) {
-        const int32_t a = row_ptr[d], b = row_ptr[d + 1];
-        float acc = 0.f;
-        for (int32_t eb = a; eb < b; eb += 32) {
-            const bool lin = eb + lane < b;
-            const int32_t cu = lin ? col[eb + lane] : 0;
-            const float cx = lin ? val[eb + lane] : 0.f;
-#pragma unroll
-            for (int r = 0; r < 8; r += 4) {  // four nonzeros per lane in flight
-                float2 E[4][KR];
-                float xs[4];
-                int32_t us[4];
-                bool ok[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int src = 4 * (r + i) + ph;
-                    us[i] = __shfl_sync(0xffffffffu, cu, src);
-                    xs[i] = __shfl_sync(0xffffffffu, cx, src);
-                    ok[i] = act && eb + src < b;
-                    const float2* T = tq + (int64_t)us[i] * rs;
-#pragma unroll
-                    for (int l = 0; l < KR; ++l) E[i][l] = ok[i] ? T[l * es] : make_float2(0.f, 0.f);
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    if (ok[i]) acc = __fadd_rn(acc, fwd_cost_reg<MEAS, KT, KR>(xs[i], E[i], tq + (int64_t)us[i] * rs, es, kq));
-            }
-        }
-        acc += __shfl_xor_sync(0xffffffffu, acc, 8);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 16);
-        if (ph == 0 && act) oq[d] = acc;
-    }
-}
-
-// NJ follows the per-query launcher: NJW bins per lane when h > 32, else one.
-template <int MEAS, int KT, int NJW>
-__global__ void __launch_bounds__(256, 2)
-k_rev_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t* __restrict__ row_ptr,
-        const int32_t* __restrict__ col, const float* __restrict__ val, int64_t n, int k, int dir)
-{
-    if ((int)blockIdx.y >= *nq) return;
-    const QDesc& d = qd[blockIdx.y];
-    float* t_rev = dir == EMD_DIR_REV ? d.t_out : d.t_rev;
-    float* t_max = dir == EMD_DIR_MAX ? d.t_out : nullptr;
-    if (d.h > 32)
-        rev_body<MEAS, KT, NJW>(row_ptr, col, val, n, d.D, d.ldd, d.h, d.qw, k, d.t_fwd, t_rev, t_max, nullptr,
-                                nullptr, d.sq != 0);
-    else
-        rev_body<MEAS, KT, 1>(row_ptr, col, val, n, d.D, d.ldd, d.h, d.qw, k, d.t_fwd, t_rev, t_max, nullptr,
-                              nullptr, d.sq != 0);
-}
-
-template <int MEAS>
-__global__ void k_rev_generic_b(const QDesc* __restrict__ qd, const int* __restrict__ nq,
-                                const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                                const float* __restrict__ val, int64_t n, int k, int dir)
-{
-    if ((int)blockIdx.y >= *nq) return;
-    const QDesc& d = qd[blockIdx.y];
-    float* t_rev = dir == EMD_DIR_REV ? d.t_out : d.t_rev;
-    float* t_max = dir == EMD_DIR_MAX ? d.t_out : nullptr;
-    rev_generic_body<MEAS>(row_ptr, col, val, n, d.D, d.ldd, d.h, d.qw, k, d.t_fwd, t_rev, t_max, nullptr, nullptr,
-                           d.sq != 0);
-}
-
-__global__ void k_prune_compact_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int64_t n, int K)
-{
-    if ((int)blockIdx.y >= *nq) return;
-    const QDesc& d = qd[blockIdx.y];
-    prune_compact_body(d.t_fwd, n, d.sel_val, K, kPruneCap, d.cand, d.cand_count);
-}
-
-// MAPPED: the distances come from the query's candidate-row block (fused path): used row u
-// is row rmap[u] of Dc.  A query whose candidate documents hold more than kCandRows distinct
-// rows has no complete block; it is skipped here and reported uncertified by the selection.
-template <int MEAS, int KT, int NJW, int W, bool MAPPED>
-__global__ void __launch_bounds__(W * 32, (W >= 8 ? 2 : 4))
-k_rev_blk_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t* __restrict__ row_ptr,
-            const int32_t* __restrict__ col, const float* __restrict__ val, int k)
-{
-    if ((int)blockIdx.y >= *nq) return;
-    const QDesc& d = qd[blockIdx.y];
-    if (MAPPED && *d.ncrows > kCandRows) return;
-    const float* D = MAPPED ? d.Dc : d.D;
-    const int32_t* rmap = MAPPED ? d.rmap : nullptr;
-    if (d.h > 32)
-        rev_blk_body<MEAS, KT, NJW, W>(row_ptr, col, val, D, d.ldd, d.h, d.qw, k, d.t_fwd, d.cand_sym + kPruneCap,
-                                       d.cand_sym, d.cand, d.cand_count, d.sq != 0, rmap);
-    else
-        rev_blk_body<MEAS, KT, 1, W>(row_ptr, col, val, D, d.ldd, d.h, d.qw, k, d.t_fwd, d.cand_sym + kPruneCap,
-                                     d.cand_sym, d.cand, d.cand_count, d.sq != 0, rmap);
-}
-
-// Reverse values of the candidate documents, rows of any width (ICT): a block of kRevW
-// warps each.
-template <int MEAS>
-__global__ void __launch_bounds__(kRevW * 32)
-k_rev_generic_cand_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t* __restrict__ row_ptr,
-                     const int32_t* __restrict__ col, const float* __restrict__ val, int k)
-{
-    if ((int)blockIdx.y >= *nq) return;
-    const QDesc& d = qd[blockIdx.y];
-    rev_generic_blk_body<MEAS>(row_ptr, col, val, d.D, d.ldd, d.h, d.qw, k, d.t_fwd, d.cand_sym + kPruneCap,
-                               d.cand_sym, d.cand, d.cand_count, d.sq != 0);
-}
-
-__global__ void k_prune_select_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, int K, bool mapped)
-{
-    if ((int)blockIdx.x >= *nq) return;
-    const QDesc& d = qd[blockIdx.x];
-    prune_select_body(d.cand, d.cand_sym, d.cand_count, kPruneCap, d.sel_val, K, d.out_idx, d.out_dist, d.ok,
-                      !mapped || *d.ncrows <= kCandRows);
-}
-
-template <int MEAS>
-cudaError_t rev_meas_b(int k, int dir, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
-                       const int32_t* col, const float* val, int64_t n, cudaStream_t st)
-{
-    const int warps = 8;
-    const int64_t blocks = std::min<int64_t>((n + warps - 1) / warps, 152 * 64);
-    dim3 grid((unsigned)std::max<int64_t>(1, blocks), (unsigned)max_q);
-    const int kt = MEAS == M_RWMD ? 1 : (MEAS == M_OMR ? 2 : (MEAS == M_ICT ? 1 << 30 : k));
-#define EMD_REVQ(KT, NJ) k_rev_b<MEAS, KT, NJ><<<grid, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, k, dir)
-    if (kt <= 1) EMD_REVQ(1, 4);
-    else if (kt <= 2) EMD_REVQ(2, 4);
-    else if (kt <= 4) EMD_REVQ(4, 4);
-    else if (kt <= 8) EMD_REVQ(8, 2);
-    else if (kt <= 16) EMD_REVQ(16, 1);
-    else k_rev_generic_b<MEAS><<<grid, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, k, dir);
-#undef EMD_REVQ
-    return cudaGetLastError();
-}
-
-template <int MEAS, int W, bool MAPPED>
-cudaError_t rev_meas_blk_bw(int k, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
-                            const int32_t* col, const float* val, cudaStream_t st)
-{
-    const int kt = MEAS == M_RWMD ? 1 : (MEAS == M_OMR ? 2 : k);
-    const dim3 grid(kPruneCap, (unsigned)max_q);
-#define EMD_REVBQ(KT, NJ) k_rev_blk_b<MEAS, KT, NJ, W, MAPPED><<<grid, W * 32, 0, st>>>(qd, nq, row_ptr, col, val, k)
-    if (kt <= 1) EMD_REVBQ(1, 4);
-    else if (kt <= 2) EMD_REVBQ(2, 4);
-    else if (kt <= 4) EMD_REVBQ(4, 4);
-    else if (kt <= 8) EMD_REVBQ(8, 2);
-    else EMD_REVBQ(16, 1);
-#undef EMD_REVBQ
-    return cudaGetLastError();
-}
-
-// Warps per candidate document: 2, 4 or 8 (the merge in chunk order makes the result
-// independent of the choice).
-template <int MEAS, bool MAPPED = false>
-cudaError_t rev_meas_blk_b(int k, int warps, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
-                           const int32_t* col, const float* val, cudaStream_t st)
-{
-    if (warps <= 2) return rev_meas_blk_bw<MEAS, 2, MAPPED>(k, qd, nq, max_q, row_ptr, col, val, st);
-    if (warps <= 4) return rev_meas_blk_bw<MEAS, 4, MAPPED>(k, qd, nq, max_q, row_ptr, col, val, st);
-    return rev_meas_blk_bw<MEAS, 8, MAPPED>(k, qd, nq, max_q, row_ptr, col, val, st);
-}
-
-// Candidate rows of the fused pruned path: every used row of every candidate document of
-// query q gets a row of q's candidate block (first come, first served: the block's row
-// order does not matter, each entry is computed independently).  A block per candidate
-// document.
-__global__ void k_cand_rows_b(const QDesc* __restrict__ qd, const int* __restrict__ nq,
-                              const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col)
-{
-    if ((int)blockIdx.y >= *nq) return;
-    const QDesc& d = qd[blockIdx.y];
-    if ((int)blockIdx.x >= min(*d.cand_count, kPruneCap)) return;
-    const int64_t doc = d.cand[blockIdx.x];
-    for (int32_t e = row_ptr[doc] + (int32_t)threadIdx.x; e < row_ptr[doc + 1]; e += blockDim.x) {
-        const int32_t u = col[e];
-        if (atomicCAS(&d.rmap[u], -1, -2) == -1) {
-            const int idx = atomicAdd(d.ncrows, 1);
-            if (idx < kCandRows) d.crows[idx] = u;
-            atomicExch(&d.rmap[u], idx);
-        }
-    }
-}
-
-// Returns the row map of the candidate documents' rows to -1 (the state every batch
-// starts from).
-__global__ void k_cand_reset_b(const QDesc* __restrict__ qd, const int* __restrict__ nq,
-                               const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col)
-{
-    if ((int)blockIdx.y >= *nq) return;
-    const QDesc& d = qd[blockIdx.y];
-    if ((int)blockIdx.x >= min(*d.cand_count, kPruneCap)) return;
-    const int64_t doc = d.cand[blockIdx.x];
-    for (int32_t e = row_ptr[doc] + (int32_t)threadIdx.x; e < row_ptr[doc + 1]; e += blockDim.x) d.rmap[col[e]] = -1;
-}
-
-template <int MEAS>
-cudaError_t rev_meas(int k, const int32_t* row_ptr, const int32_t* col, const float* val,
-                     int64_t n, const float* D, int ldd, int h, const float* q_w,
-                     const float* t_fwd, float* t_rev, float* t_max, const int64_t* doc_ids,
-                     const int* n_dev, bool sq, cudaStream_t st)
-{
-    const int warps = 8;
-    const int64_t blocks = std::min<int64_t>((n + warps - 1) / warps, 152 * 64);
-    dim3 grid((unsigned)std::max<int64_t>(1, blocks));
-    const int kt = MEAS == M_RWMD ? 1 : (MEAS == M_OMR ? 2 : (MEAS == M_ICT ? 1 << 30 : k));
-    const bool wide = h > 32;  // several 32-bin chunks: vector loads of consecutive bins
-#define EMD_REV(KT, NJ) k_rev<MEAS, KT, NJ><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev, sq)
-    if (kt <= 1) { if (wide) EMD_REV(1, 4); else EMD_REV(1, 1); }
-    else if (kt <= 2) { if (wide) EMD_REV(2, 4); else EMD_REV(2, 1); }
-    else if (kt <= 4) { if (wide) EMD_REV(4, 4); else EMD_REV(4, 1); }
-    else if (kt <= 8) { if (wide) EMD_REV(8, 2); else EMD_REV(8, 1); }
-    else if (kt <= 16) EMD_REV(16, 1);
-    else k_rev_generic<MEAS><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, D, ldd, h, q_w, k, t_fwd, t_rev, t_max, doc_ids, n_dev, sq);
-#undef EMD_REV
-    return cudaGetLastError();
-}
-
-}  // namespace
-
-// Register width of the forward cost for table width kw (0: the loop form).
-static int fwd_kt(int kw) { return fwd_reg_width(kw); }
-
-#define EMD_FWD_KT_SWITCH(KTV, LAUNCH)             \
-    switch (KTV) {                                 \
-    case 1: LAUNCH(1); break;                      \
-    case 2: LAUNCH(2); break;                      \
-    case 4: LAUNCH(4); break;                      \
-    case 8: LAUNCH(8); break;                      \
-    case 16: LAUNCH(16); break;                    \
-    default: LAUNCH(0); break;                     \
-    }
-
-cudaError_t launch_fwd(int meas, const int32_t* row_ptr, const int32_t* col, const float* val,
-                       int64_t n, const float2* tab, int k, int keff, float* t_fwd,
-                       cudaStream_t st)
-{
-    if (n <= 0) return cudaSuccess;
-    const int warps = 8;  // eight documents per warp
-    const int64_t blocks = std::min<int64_t>((n + 8 * warps - 1) / (8 * warps), 152 * 64);
-    dim3 grid((unsigned)std::max<int64_t>(1, blocks));
-    switch (meas) {
-    case M_RWMD: k_fwd<M_RWMD, 0><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, tab, k, keff, t_fwd); break;
-    case M_OMR: k_fwd<M_OMR, 0><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, tab, k, keff, t_fwd); break;
-    default: {
-#define EMD_L(KT) k_fwd<M_ACT, KT><<<grid, warps * 32, 0, st>>>(row_ptr, col, val, n, tab, k, keff, t_fwd)
-        EMD_FWD_KT_SWITCH(fwd_kt(keff), EMD_L)
-#undef EMD_L
-        break;
-    }
-    }
-    return cudaGetLastError();
-}
 
 cudaError_t launch_rev(int meas, int k, const int32_t* row_ptr, const int32_t* col,
                        const float* val, int64_t n, const float* D, int ldd, int h,
@@ -1322,162 +45,8 @@ cudaError_t launch_prune(int meas, int k, const int32_t* row_ptr, const int32_t*
     return cudaGetLastError();
 }
 
-cudaError_t launch_fwd_b(int meas, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
-                         const int32_t* col, const float* val, int64_t n, bool to_out, bool grouped, int max_tk,
-                         cudaStream_t st, int variant)
-{
-    const int kt = fwd_kt(max_tk);
-    if (max_q <= 0 || n <= 0) return cudaSuccess;
-    const int warps = 8;
-    const int64_t blocks = std::min<int64_t>((n + warps - 1) / warps, 152 * 64);
-    if (grouped) {  // one document per warp, eight queries
-        dim3 gg((unsigned)std::max<int64_t>(1, blocks), (unsigned)((max_q + kFwdGroup - 1) / kFwdGroup));
-        const int m = meas == M_ICT ? M_ACT : meas;  // ICT tables: the ACT steps over the written entries
-        const int kw = meas == M_RWMD ? 1 : meas == M_OMR ? 2 : (meas == M_ICT && kt == 0 ? 0 : kt);
-        if (variant == kFwdPrefetch) {  // the entry chain with the CSR read one group ahead
-            switch (m) {
-            case M_RWMD: k_fwd_gp<M_RWMD, 0><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
-            case M_OMR: k_fwd_gp<M_OMR, 0><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
-            default: {
-#define EMD_L(KT) k_fwd_gp<M_ACT, KT><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out)
-                EMD_FWD_KT_SWITCH(kw, EMD_L)
-#undef EMD_L
-                break;
-            }
-            }
-            return cudaGetLastError();
-        }
-        if (kw == 0 || variant == kFwdChain) {  // entry-interleaved rows, loads while mass remains
-            switch (m) {
-            case M_RWMD: k_fwd_g<M_RWMD, 0><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
-            case M_OMR: k_fwd_g<M_OMR, 0><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
-            default: {
-#define EMD_L(KT) k_fwd_g<M_ACT, KT><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out)
-                EMD_FWD_KT_SWITCH(kw, EMD_L)
-#undef EMD_L
-                break;
-            }
-            }
-            return cudaGetLastError();
-        }
-#define EMD_GV(M, KT)                                                                                       \
-    do {                                                                                                    \
-        if (variant == kFwdRowMajor)                                                                        \
-            k_fwd_gv<M, KT><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out);               \
-        else                                                                                                \
-            k_fwd_gc<M, KT><<<gg, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out);               \
-    } while (0)
-        switch (m) {
-        case M_RWMD: EMD_GV(M_RWMD, 1); break;
-        case M_OMR: EMD_GV(M_OMR, 2); break;
-        default:
-            switch (kw) {
-            case 1: EMD_GV(M_ACT, 1); break;
-            case 2: EMD_GV(M_ACT, 2); break;
-            case 4: EMD_GV(M_ACT, 4); break;
-            case 8: EMD_GV(M_ACT, 8); break;
-            default: EMD_GV(M_ACT, 16); break;
-            }
-        }
-#undef EMD_GV
-        return cudaGetLastError();
-    }
-    const int64_t qblocks = std::min<int64_t>((n + 8 * warps - 1) / (8 * warps), 152 * 64);  // eight documents per warp
-    dim3 grid((unsigned)std::max<int64_t>(1, qblocks), (unsigned)max_q);
-    switch (meas) {
-    case M_RWMD: k_fwd_b<M_RWMD, 0><<<grid, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
-    case M_OMR: k_fwd_b<M_OMR, 0><<<grid, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out); break;
-    default: {
-#define EMD_L(KT) k_fwd_b<M_ACT, KT><<<grid, warps * 32, 0, st>>>(qd, nq, row_ptr, col, val, n, to_out)
-        EMD_FWD_KT_SWITCH(kt, EMD_L)
-#undef EMD_L
-        break;
-    }
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_rev_b(int meas, int k, int dir, const QDesc* qd, const int* nq, int max_q,
-                         const int32_t* row_ptr, const int32_t* col, const float* val, int64_t n, cudaStream_t st)
-{
-    if (max_q <= 0 || n <= 0) return cudaSuccess;
-    if (dir != EMD_DIR_REV && dir != EMD_DIR_MAX) return cudaErrorInvalidValue;
-    switch (meas) {
-    case M_RWMD: return rev_meas_b<M_RWMD>(k, dir, qd, nq, max_q, row_ptr, col, val, n, st);
-    case M_OMR: return rev_meas_b<M_OMR>(k, dir, qd, nq, max_q, row_ptr, col, val, n, st);
-    case M_ICT: return rev_meas_b<M_ICT>(k, dir, qd, nq, max_q, row_ptr, col, val, n, st);
-    default: return rev_meas_b<M_ACT>(k, dir, qd, nq, max_q, row_ptr, col, val, n, st);
-    }
-}
-
-cudaError_t launch_prune_b(int meas, int k, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
-                           const int32_t* col, const float* val, int64_t n, int K, int rev_warps, cudaStream_t st)
-{
-    if (max_q <= 0) return cudaSuccess;
-    const int blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256), 152 * 4);
-    k_prune_compact_b<<<dim3((unsigned)blocks, (unsigned)max_q), 256, 0, st>>>(qd, nq, n, K);
-    cudaError_t e;
-    switch (meas) {
-    case M_RWMD: e = rev_meas_blk_b<M_RWMD>(k, rev_warps, qd, nq, max_q, row_ptr, col, val, st); break;
-    case M_OMR: e = rev_meas_blk_b<M_OMR>(k, rev_warps, qd, nq, max_q, row_ptr, col, val, st); break;
-    case M_ICT:
-        k_rev_generic_cand_b<M_ICT><<<dim3(kPruneCap, (unsigned)max_q), kRevW * 32, 0, st>>>(qd, nq, row_ptr, col,
-                                                                                            val, k);
-        e = cudaGetLastError();
-        break;
-    default: e = rev_meas_blk_b<M_ACT>(k, rev_warps, qd, nq, max_q, row_ptr, col, val, st); break;
-    }
-    if (e != cudaSuccess) return e;
-    k_prune_select_b<<<(unsigned)max_q, kPruneCap, 0, st>>>(qd, nq, K, false);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_prune_compact_b(const QDesc* qd, const int* nq, int max_q, int64_t n, int K, cudaStream_t st)
-{
-    if (max_q <= 0) return cudaSuccess;
-    const int blocks = (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256), 152 * 4);
-    k_prune_compact_b<<<dim3((unsigned)blocks, (unsigned)max_q), 256, 0, st>>>(qd, nq, n, K);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_cand_rows_b(const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr, const int32_t* col,
-                               bool reset, cudaStream_t st)
-{
-    if (max_q <= 0) return cudaSuccess;
-    const dim3 g(kPruneCap, (unsigned)max_q);
-    if (reset)
-        k_cand_reset_b<<<g, 128, 0, st>>>(qd, nq, row_ptr, col);
-    else
-        k_cand_rows_b<<<g, 128, 0, st>>>(qd, nq, row_ptr, col);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_prune_mapped_b(int meas, int k, const QDesc* qd, const int* nq, int max_q, const int32_t* row_ptr,
-                                  const int32_t* col, const float* val, int K, int rev_warps, cudaStream_t st)
-{
-    if (max_q <= 0) return cudaSuccess;
-    cudaError_t e;
-    switch (meas) {
-    case M_RWMD: e = rev_meas_blk_b<M_RWMD, true>(k, rev_warps, qd, nq, max_q, row_ptr, col, val, st); break;
-    case M_OMR: e = rev_meas_blk_b<M_OMR, true>(k, rev_warps, qd, nq, max_q, row_ptr, col, val, st); break;
-    case M_ACT: e = rev_meas_blk_b<M_ACT, true>(k, rev_warps, qd, nq, max_q, row_ptr, col, val, st); break;
-    default: return cudaErrorInvalidValue;
-    }
-    if (e != cudaSuccess) return e;
-    k_prune_select_b<<<(unsigned)max_q, kPruneCap, 0, st>>>(qd, nq, K, true);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_topk_b(const QDesc* qd, const int* nq, int max_q, int64_t n, int K,
-                          unsigned long long* scratch, bool fwd_rows, cudaStream_t st)
-{
-    if (max_q <= 0) return cudaSuccess;
-    if (K <= 16) return topk_kt_b<16>(qd, nq, max_q, n, K, scratch, fwd_rows, st);
-    if (K <= 32) return topk_kt_b<32>(qd, nq, max_q, n, K, scratch, fwd_rows, st);
-    return topk_kt_b<64>(qd, nq, max_q, n, K, scratch, fwd_rows, st);
-}
-
 }  // namespace emd
+
 
 namespace {
 
