@@ -716,8 +716,10 @@ __global__ void k_prune_compact_b(const QDesc* __restrict__ qd, const int* __res
 // MAPPED: the distances come from the query's candidate-row block (fused path): used row u
 // is row rmap[u] of Dc.  A query whose candidate documents hold more than kCandRows distinct
 // rows has no complete block; it is skipped here and reported uncertified by the selection.
+// 24 resident warps per SM whatever W (80 registers, no spills; the unbounded form took 106-112
+// and left 16): the gathers of the distance block are latency-bound.
 template <int MEAS, int KT, int NJW, int W, bool MAPPED>
-__global__ void __launch_bounds__(W * 32, (W >= 8 ? 2 : 4))
+__global__ void __launch_bounds__(W * 32, (W >= 8 ? 3 : (W >= 4 ? 6 : 12)))
 k_rev_blk_b(const QDesc* __restrict__ qd, const int* __restrict__ nq, const int32_t* __restrict__ row_ptr,
             const int32_t* __restrict__ col, const float* __restrict__ val, int k)
 {
