@@ -266,8 +266,10 @@ __device__ __forceinline__ void rev_blk_body(const int32_t* __restrict__ row_ptr
     }
 }
 
+// 24 resident warps per SM whatever W, as the batched form (80 registers, no spills).
 template <int MEAS, int KT, int NJ, int W>
-__global__ void __launch_bounds__(W * 32, (W >= 8 ? 2 : 4)) k_rev_blk(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+__global__ void __launch_bounds__(W * 32, (W >= 8 ? 3 : (W >= 4 ? 6 : 12)))
+k_rev_blk(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
           const float* __restrict__ val, const float* __restrict__ D, int ldd, int h,
           const float* __restrict__ q_w, int k, const float* __restrict__ t_fwd,
           float* __restrict__ t_rev, float* __restrict__ t_max, const int64_t* __restrict__ doc_ids,
